@@ -1,0 +1,398 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by geometry.
+
+Each check is chosen so that a plausible mistake in the oracle (a dropped
+cost term, a flipped orientation sign, an off-by-one generator id, swapped
+x/y, a wrong cone or segment-foot rule) fails at least one of them:
+
+* closed forms in empty scenes (Sec. 3: lambda* is the Euclidean distance to
+  the closest source; Sec. 4: the distance rule for segment sources);
+* a hand-derived worked example around one square (tests/golden) and an
+  analytic enumeration of all paths around one square;
+* two sources split on the perpendicular bisector (parent ids);
+* invariants: lambda*(p) = cost(parent) + |p - parent|, the parent sees p,
+  1-Lipschitz between mutually visible pixels, path length = field value,
+  vertex costs >= straight-line distance to the nearest source;
+* the cone restriction changes no distance;
+* agreement with a second independent algorithm (Procedures 1-4 restated
+  sequentially with another exact visibility method) and with Floyd-Warshall.
+"""
+import json
+import math
+import os
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import scenegen as sg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def centres(scene):
+    (Wx, Wy), (Nx, Ny) = scene.world, scene.grid
+    x = (np.arange(Nx) + 0.5) * Wx / Nx
+    y = (np.arange(Ny) + 0.5) * Wy / Ny
+    X, Y = np.meshgrid(x, y)
+    return X, Y
+
+
+# ---------------------------------------------------------------------------
+# closed forms
+# ---------------------------------------------------------------------------
+
+def test_empty_points_closed_form(oracle_mod):
+    s = sg.empty_scene(W=64, N=64, points=[(10.0, 50.0), (47.0, 13.0), (30.0, 31.0)])
+    d, p, d2, _ = oracle_mod.Oracle(s).field()
+    X, Y = centres(s)
+    D = np.stack([np.hypot(X - px, Y - py) for px, py in s.points])
+    np.testing.assert_allclose(d, D.min(0), rtol=1e-15, atol=0)
+    clear = (np.sort(D, 0)[1] - D.min(0)) > 1e-9
+    assert np.array_equal(p[clear], D.argmin(0)[clear])
+
+
+def test_empty_segment_closed_form(oracle_mod):
+    A, B = np.array([12.0, 20.0]), np.array([50.0, 41.0])
+    s = sg.empty_scene(W=64, N=64, points=[(5.0, 60.0)], segs=[(*A, *B)])
+    d, p, _, _ = oracle_mod.Oracle(s).field()
+    X, Y = centres(s)
+    u = B - A
+    t = ((X - A[0]) * u[0] + (Y - A[1]) * u[1]) / (u @ u)
+    perp = np.abs(u[0] * (Y - A[1]) - u[1] * (X - A[0])) / np.hypot(*u)
+    dA = np.hypot(X - A[0], Y - A[1])
+    dB = np.hypot(X - B[0], Y - B[1])
+    dseg = np.where(t <= 0, dA, np.where(t >= 1, dB, perp))
+    dpt = np.hypot(X - 5.0, Y - 60.0)
+    np.testing.assert_allclose(d, np.minimum(dseg, dpt), rtol=1e-13, atol=1e-12)
+    # ids: point 0, then segment endpoint A 1, endpoint B 2, interior 3
+    exp = np.where(dpt < dseg, 0, np.where(t <= 0, 1, np.where(t >= 1, 2, 3)))
+    clear = np.abs(dpt - dseg) > 1e-6
+    assert np.array_equal(p[clear], exp[clear])
+
+
+def test_two_sources_bisector(oracle_mod):
+    s = sg.empty_scene(W=64, N=64, points=[(9.0, 21.0), (52.0, 37.0)])
+    _, p, _, _ = oracle_mod.Oracle(s).field()
+    # exact integer side test on the doubled lattice (centres are half-integers)
+    jj, ii = np.mgrid[0:64, 0:64]
+    cx, cy = 2 * ii + 1, 2 * jj + 1
+    d0 = (cx - 18) ** 2 + (cy - 42) ** 2
+    d1 = (cx - 104) ** 2 + (cy - 74) ** 2
+    exp = np.where(d0 < d1, 0, np.where(d1 < d0, 1, 0))
+    assert np.array_equal(p, exp)
+
+
+def test_golden_hand_square(oracle_mod):
+    fix = json.load(open(os.path.join(GOLDEN, "single_square_hand.json")))
+    sc = fix["scene"]
+    s = sg.Scene(tuple(sc["world"]), tuple(sc["grid"]), [np.array(q) for q in sc["polys"]],
+                 np.array(sc["points"]), np.zeros((0, 4)))
+    o = oracle_mod.Oracle(s)
+    ij = np.array([c["ij"] for c in fix["cases"]], np.int32)
+    d, p, _, _ = o.pixels(ij)
+    for k, c in enumerate(fix["cases"]):
+        if c["dist"] is None:
+            assert math.isinf(d[k]) and p[k] == -1
+        else:
+            assert abs(d[k] - c["dist"]) <= 1e-12 * c["dist"], c["why"]
+            assert p[k] == c["parent"], c["why"]
+
+
+def _square_blocks(a, b, box):
+    """Open segment a-b meets the open box? Liang-Barsky in exact rationals."""
+    x0, y0, x1, y1 = box
+    lo, hi = Fr(0), Fr(1)
+    for p0, dp, lo_b, hi_b in ((a[0], b[0] - a[0], x0, x1), (a[1], b[1] - a[1], y0, y1)):
+        p0, dp = Fr(p0), Fr(dp)
+        if dp == 0:
+            if not (lo_b < p0 < hi_b):
+                return False
+            continue
+        t1, t2 = (lo_b - p0) / dp, (hi_b - p0) / dp
+        lo, hi = max(lo, min(t1, t2)), min(hi, max(t1, t2))
+    return lo < hi
+
+
+def test_single_square_analytic(oracle_mod):
+    box = (24, 24, 40, 40)
+    src = (10.0, 30.0)
+    s = sg.single_square(W=64, N=64, square=box, source=src)
+    d, _, _, _ = oracle_mod.Oracle(s).field()
+    corners = [(24, 24), (40, 24), (40, 40), (24, 40)]
+    adj = {0: (1, 3), 1: (0, 2), 2: (1, 3), 3: (0, 2)}
+    X, Y = centres(s)
+    half = [Fr(2 * i + 1, 2) for i in range(64)]
+    for j in range(0, 64, 3):
+        for i in range(0, 64, 3):
+            pt = (half[i], half[j])
+            if box[0] < pt[0] < box[2] and box[1] < pt[1] < box[3]:
+                assert math.isinf(d[j, i])
+                continue
+            best = math.inf
+            if not _square_blocks(src, pt, box):
+                best = math.hypot(X[j, i] - src[0], Y[j, i] - src[1])
+            for a in range(4):
+                if _square_blocks(src, corners[a], box):
+                    continue
+                ca = math.hypot(corners[a][0] - src[0], corners[a][1] - src[1])
+                if not _square_blocks(corners[a], pt, box):
+                    best = min(best, ca + math.hypot(X[j, i] - corners[a][0], Y[j, i] - corners[a][1]))
+                for b in adj[a]:
+                    cb = ca + 16.0
+                    if not _square_blocks(corners[b], pt, box):
+                        best = min(best, cb + math.hypot(X[j, i] - corners[b][0], Y[j, i] - corners[b][1]))
+            assert abs(d[j, i] - best) <= 1e-12 * best, (i, j, d[j, i], best)
+
+
+# ---------------------------------------------------------------------------
+# invariants
+# ---------------------------------------------------------------------------
+
+def _invariants(o, scene, ij, d, p):
+    n_src = o.n_src
+    for k in range(len(ij)):
+        if not np.isfinite(d[k]):
+            continue
+        i, j = ij[k]
+        g = p[k]
+        x = (i + 0.5) * scene.world[0] / scene.grid[0]
+        y = (j + 0.5) * scene.world[1] / scene.grid[1]
+        if o.kind[g] == 3:  # segment interior: perpendicular distance
+            A = scene.segs[o.sidx[g], :2]
+            B = scene.segs[o.sidx[g], 2:]
+            u = B - A
+            val = abs(u[0] * (y - A[1]) - u[1] * (x - A[0])) / np.hypot(*u)
+        else:
+            val = o.cost[g] + math.hypot(x - o.txy[g, 0], y - o.txy[g, 1])
+            assert o.visible(o.pixel_lattice(i, j), o.lxy[g]), (i, j, g)
+        assert abs(val - d[k]) <= 1e-12 * max(d[k], 1.0)
+        if g >= n_src:
+            assert o.cost[g] > 0
+
+
+def test_invariants_rects(oracle_mod):
+    s = sg.plain_rects(3)
+    o = oracle_mod.Oracle(s)
+    d, p, _, _ = o.field()
+    jj, ii = np.mgrid[0:256:5, 0:256:5]
+    ij = np.stack([ii.ravel(), jj.ravel()], 1)
+    _invariants(o, s, ij, d[jj.ravel(), ii.ravel()], p[jj.ravel(), ii.ravel()])
+    # vertex costs are at least the straight-line distance to the source
+    src = s.points[0]
+    v = slice(o.n_src, o.n_gen)
+    fin = np.isfinite(o.cost[v])
+    eu = np.hypot(o.txy[v, 0] - src[0], o.txy[v, 1] - src[1])
+    assert np.all(o.cost[v][fin] >= eu[fin] - 1e-9)
+
+
+def test_invariants_polys_sample(oracle_mod):
+    s = sg.plain_polys(1, n_polys=60, N=256)
+    o = oracle_mod.Oracle(s)
+    rng = np.random.default_rng(5)
+    ij = rng.integers(0, 256, size=(1500, 2)).astype(np.int32)
+    d, p, _, _ = o.pixels(ij)
+    _invariants(o, s, ij, d, p)
+
+
+def test_lipschitz_and_triangle(oracle_mod):
+    s = sg.plain_rects(1)
+    o = oracle_mod.Oracle(s)
+    d, _, _, _ = o.field()
+    rng = np.random.default_rng(2)
+    checked = 0
+    for _ in range(4000):
+        a = rng.integers(0, 256, 2)
+        b = a + rng.integers(-20, 21, 2)
+        if np.any(b < 0) or np.any(b >= 256):
+            continue
+        da, db = d[a[1], a[0]], d[b[1], b[0]]
+        if not (np.isfinite(da) and np.isfinite(db)):
+            continue
+        if not o.visible(o.pixel_lattice(*a), o.pixel_lattice(*b)):
+            continue
+        dist = math.hypot(*(a - b))  # pixel size 1
+        assert abs(da - db) <= dist + 1e-9
+        checked += 1
+    assert checked > 1000
+
+
+def test_path_length_equals_field(oracle_mod):
+    s = sg.plain_polys(2, n_polys=80, n_segs=2, N=256)
+    o = oracle_mod.Oracle(s)
+    rng = np.random.default_rng(9)
+    ij = rng.integers(0, 256, size=(600, 2)).astype(np.int32)
+    d, p, _, _ = o.pixels(ij)
+    h = s.world[0] / s.grid[0]
+    for k in range(len(ij)):
+        if not np.isfinite(d[k]):
+            continue
+        x = np.array([(ij[k, 0] + 0.5) * h, (ij[k, 1] + 0.5) * h])
+        g, total = p[k], 0.0
+        while o.kind[g] == 4:  # walk obstacle vertices back to the source
+            total += math.hypot(*(x - o.txy[g]))
+            x = o.txy[g]
+            g = o.parent[g]
+        if o.kind[g] == 3:
+            A = s.segs[o.sidx[g], :2]
+            B = s.segs[o.sidx[g], 2:]
+            u = B - A
+            total += abs(u[0] * (x[1] - A[1]) - u[1] * (x[0] - A[0])) / np.hypot(*u)
+        else:
+            total += math.hypot(*(x - o.txy[g]))
+        assert abs(total - d[k]) <= 1e-9 * max(1.0, d[k])
+
+
+def test_cone_restriction_keeps_distances(oracle_mod):
+    for s in (sg.plain_rects(4), sg.plain_polys(3, n_polys=70, N=256)):
+        a = oracle_mod.Oracle(s, use_cone=True)
+        b = oracle_mod.Oracle(s, use_cone=False)
+        fa = np.isfinite(a.cost)
+        assert np.array_equal(fa, np.isfinite(b.cost))
+        np.testing.assert_allclose(a.cost[fa], b.cost[fa], rtol=1e-12)
+        da, _, _, _ = a.field()
+        db, _, _, _ = b.field()
+        f = np.isfinite(da)
+        assert np.array_equal(f, np.isfinite(db))
+        np.testing.assert_allclose(da[f], db[f], rtol=1e-12)
+
+
+def test_maze_vertex_generators(oracle_mod):
+    """Maze walls overlap at posts: only convex corners of the union of walls
+    become generators, each position once (dead ends give 2, L-turns give 1)."""
+    m = sg.maze(0, cells=6, cell=256, N=96)
+    o = oracle_mod.Oracle(m)
+    v = o.lxy[o.n_src:]
+    assert len({tuple(x) for x in v.tolist()}) == len(v)
+    # every generator corner has exactly one covered quadrant (axis-aligned walls)
+    boxes = [(p[:, 0].min(), p[:, 1].min(), p[:, 0].max(), p[:, 1].max()) for p in m.polys]
+    for (x, y) in (v // o.S).tolist():
+        covered = 0
+        for qx, qy in ((1, 1), (-1, 1), (-1, -1), (1, -1)):
+            px, py = x + 0.5 * qx, y + 0.5 * qy
+            covered += any(b[0] < px < b[2] and b[1] < py < b[3] for b in boxes)
+        assert covered == 1
+
+
+# ---------------------------------------------------------------------------
+# second algorithm: Procedures 1-4 restated sequentially; Floyd-Warshall
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,n_segs", [(0, 0), (1, 1), (2, 1), (3, 2)])
+def test_sequential_procedures_agree(oracle_mod, seed, n_segs):
+    from oracle.sequential import Sequential
+    s = sg.tiny(seed, W=32, N=32, n_polys=3, n_points=1 + (seed % 2), n_segs=n_segs)
+    o = oracle_mod.Oracle(s)
+    d, p, d2, _ = o.field()
+    F, L, vd, _ = Sequential(s).run()
+    fin = np.isfinite(d)
+    assert np.array_equal(fin, np.isfinite(F))
+    np.testing.assert_allclose(F[fin], d[fin], rtol=1e-12)
+    tie = (d2 - d) <= 1e-4 * s.world[0] * math.sqrt(2)
+    assert np.all((L == p)[fin & ~tie])
+    fv = np.isfinite(o.cost)
+    np.testing.assert_allclose(vd[fv], o.cost[fv], rtol=1e-12)
+
+
+def test_dijkstra_vs_floyd_warshall(oracle_mod):
+    from oracle.sequential import Sequential
+    for seed in range(3):
+        s = sg.tiny(10 + seed, W=40, N=8, n_polys=4, n_points=2, n_segs=1)
+        o = oracle_mod.Oracle(s, use_cone=False)
+        q = Sequential(s)
+        n = len(q.ent)
+        D = np.full((n, n), np.inf)
+        np.fill_diagonal(D, 0.0)
+        M = q.visibility_matrix()
+        for u in range(n):
+            for v in range(q.n_src, n):
+                if M[u, v]:
+                    D[u, v] = q.edge_length(u, v)
+                    if u >= q.n_src:
+                        D[v, u] = D[u, v]
+        for k in range(n):
+            D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+        fw = D[:q.n_src].min(0)
+        fin = np.isfinite(o.cost)
+        assert np.array_equal(fin, np.isfinite(fw))
+        np.testing.assert_allclose(o.cost[fin], fw[fin], rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# visibility predicate: boundary contact is allowed, interiors block
+# ---------------------------------------------------------------------------
+
+def test_visibility_cases(oracle_mod):
+    s = sg.single_square(W=64, N=64, square=(24, 24, 40, 40), source=(10.0, 30.0))
+    o = oracle_mod.Oracle(s)
+    S = o.S
+    P = lambda x, y: (int(x * S), int(y * S))  # noqa: E731
+    assert o.visible(P(10, 24), P(50, 24))        # runs along the bottom edge
+    assert o.visible(P(24, 10), P(24, 50))        # runs along the left edge
+    assert not o.visible(P(24, 24), P(40, 40))    # diagonal through the interior
+    assert o.visible(P(16, 16), P(24, 24))        # ends on a corner from outside
+    assert not o.visible(P(16, 16), P(32, 32))    # through a corner into the interior
+    assert o.visible(P(20, 44), P(44, 20)) is False or True  # defined, any result ok
+    assert o.visible(P(16, 32), P(32, 48))        # grazes corner (24,40) exactly
+    assert not o.visible(P(16, 31), P(32, 47))    # passes just inside that corner
+    assert o.visible(P(24, 24), P(40, 24))        # edge between two corners
+    assert not o.visible(P(30, 10), P(30, 50))    # straight through
+
+
+def test_oracle_rejects_bad_scenes(oracle_mod):
+    sq = np.array([(10, 10), (20, 10), (20, 20), (10, 20)])
+    with pytest.raises(oracle_mod.OracleError):  # source inside an obstacle
+        oracle_mod.Oracle(sg.Scene((32, 32), (32, 32), [sq], [(15.0, 15.0)], np.zeros((0, 4))))
+    with pytest.raises(oracle_mod.OracleError):  # source on the boundary
+        oracle_mod.Oracle(sg.Scene((32, 32), (32, 32), [sq], [(10.0, 15.0)], np.zeros((0, 4))))
+    with pytest.raises(oracle_mod.OracleError):  # segment crossing an obstacle
+        oracle_mod.Oracle(sg.Scene((32, 32), (32, 32), [sq], [(2.0, 2.0)], [(5.0, 15.0, 25.0, 15.0)]))
+    nonconvex = np.array([(0, 0), (10, 0), (5, 2), (10, 10), (0, 10)])
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Oracle(sg.Scene((32, 32), (32, 32), [nonconvex], [(20.0, 20.0)], np.zeros((0, 4))))
+
+
+# ---------------------------------------------------------------------------
+# gradient of the agent loss
+# ---------------------------------------------------------------------------
+
+def test_gradient_empty_closed_form(oracle_mod):
+    s = sg.empty_scene(W=64, N=64, points=[(12.3, 40.7), (50.1, 20.2)])
+    o = oracle_mod.Oracle(s)
+    rng = np.random.default_rng(1)
+    agents = rng.integers(0, 64, size=(500, 2)).astype(np.int32)
+    loss, gp, _ = o.agent_loss_and_grad(agents)
+    X = agents[:, 0] + 0.5
+    Y = agents[:, 1] + 0.5
+    D = np.stack([np.hypot(X - px, Y - py) for px, py in s.points])
+    lab = D.argmin(0)
+    exp = np.zeros((2, 2))
+    for k in range(2):
+        sel = lab == k
+        exp[k, 0] = np.sum((s.points[k, 0] - X[sel]) / D[k, sel]) / len(agents)
+        exp[k, 1] = np.sum((s.points[k, 1] - Y[sel]) / D[k, sel]) / len(agents)
+    assert abs(loss - D.min(0).mean()) < 1e-12
+    np.testing.assert_allclose(gp, exp, atol=1e-12)
+
+
+def test_gradient_matches_central_differences(oracle_mod):
+    s = sg.plain_polys(4, W=512, N=128, n_polys=12, n_points=2, n_segs=1)
+    rng = np.random.default_rng(3)
+    agents = rng.integers(0, 128, size=(400, 2)).astype(np.int32)
+    o = oracle_mod.Oracle(s)
+    d, _, _, _ = o.pixels(agents)
+    agents = agents[np.isfinite(d)]
+    loss, gp, gs = o.agent_loss_and_grad(agents)
+    h = 1e-3
+    fd_p = np.zeros_like(gp)
+    fd_s = np.zeros_like(gs)
+    for arr, fd in ((s.points, fd_p), (s.segs, fd_s)):
+        for idx in np.ndindex(arr.shape):
+            old = arr[idx]
+            arr[idx] = old + h
+            lp = oracle_mod.Oracle(s).agent_loss_and_grad(agents)[0]
+            arr[idx] = old - h
+            lm = oracle_mod.Oracle(s).agent_loss_and_grad(agents)[0]
+            arr[idx] = old
+            fd[idx] = (lp - lm) / (2 * h)
+    np.testing.assert_allclose(gp, fd_p, atol=1e-3)
+    np.testing.assert_allclose(gs, fd_s, atol=1e-3)
