@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Benchmark: shortest-path-map throughput (Mpixel/s) on one or more GB300s.
+
+Default workload: the 4096 x 4096 maze (64 x 64 cells, 16-unit walls, one
+exit segment + 4 point sources, seed 0). One step = one spm_compute: the
+vertex-cost fixpoint, tile culling and the pixel pass for the whole grid, with
+the scene already resident in HBM. The L2 is flushed (a 256 MiB write)
+between timed steps; each step is timed with CUDA events on the compute
+stream. Under torchrun every rank computes its own replica (the path has no
+exchange step), so per-GPU work is fixed ("weak" scaling) and value is the
+pixels of all ranks over the slowest rank's time.
+
+--impl reference times the CPU FP64 oracle on the host cores instead (a
+bounded pixel sample per step, extrapolated to the full grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen as sg  # noqa: E402
+
+METRIC = "SPM Mpixel/s at 4096^2"
+UNIT = "Mpixel/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP32 lanes per SM x SMs x 2 flops per FMA; clock from the measured peaks file
+FP32_LANES, N_SMS = 128, 152
+FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
+
+
+def workload(name: str):
+    if name == "maze4096":
+        return sg.maze(0), "maze 64x64 cells, 4096^2 px, 16384^2 world, 1 segment + 4 points"
+    if name == "polys1024":
+        return sg.plain_polys(0), "200 convex polygons, 1024^2 px, 4096^2 world, 3 points + 2 segments"
+    if name == "rects256":
+        return sg.plain_rects(0), "8 rectangles, 256^2 px, 256^2 world, 1 point"
+    if name == "diff2048":
+        return sg.differentiable(0, n_agents=10), "150 convex polygons, 2048^2 px, 8192^2 world"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(scene, n_pixels: int, seed: int, nthreads: int):
+    """Oracle throughput estimate on the host: vertex phase + a seeded pixel
+    sample, extrapolated to the full grid. Returns (Mpixel/s, seconds used)."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle(scene, nthreads=nthreads)
+    t_build = time.perf_counter() - t0
+    Nx, Ny = scene.grid
+    rng = np.random.default_rng(seed)
+    ij = np.stack([rng.integers(0, Nx, n_pixels), rng.integers(0, Ny, n_pixels)], 1).astype(np.int32)
+    t1 = time.perf_counter()
+    o.pixels(ij)
+    t_pix = time.perf_counter() - t1
+    full = t_build + t_pix * (Nx * Ny) / n_pixels
+    return (Nx * Ny) / full / 1e6, t_build + t_pix
+
+
+def run_reference(args, cfg_desc, scene):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_oracle()
+    nthreads = oracle.default_threads()
+    for w in range(args.warmup):
+        cpu_oracle_rate(scene, args.ref_pixels, 1000 + w, nthreads)
+    rates, used = [], 0.0
+    for k in range(args.steps):
+        r, t = cpu_oracle_rate(scene, args.ref_pixels, k, nthreads)
+        rates.append(r)
+        used += t
+    value = float(np.mean(rates))
+    Nx, Ny = scene.grid
+    sample = (f"per step: oracle vertex phase + {args.ref_pixels} seeded pixels of the "
+              f"{Nx}x{Ny} grid, extrapolated to the full grid")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * Nx * Ny / (value * 1e6), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "scene": cfg_desc, "grid": [Nx, Ny]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="maze4096",
+                    choices=["maze4096", "polys1024", "rects256", "diff2048"])
+    ap.add_argument("--cpu-pixels", type=int, default=200_000,
+                    help="oracle pixel sample for the cpu_baseline leg")
+    ap.add_argument("--ref-pixels", type=int, default=40_000,
+                    help="oracle pixel sample per step for --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    scene, cfg_desc = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, cfg_desc, scene)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1805_08500_gb300 as spm
+
+    s = spm.Scene(scene)
+    Nx, Ny = scene.grid
+    npx = Nx * Ny
+    d_out, p_out = s.empty_outputs()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    info = s.info()
+    launches_per_step = (6 if info["n_vert"] > 0 else 2) + 1
+
+    for _ in range(args.warmup):
+        s.compute(d_out, p_out, stream)
+    s.sync(stream)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    phases = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            s.compute(d_out, p_out, stream)
+            ev[k][1].record(stream)
+            phases.append(s.phase_ms())  # waits for this step's pixel pass
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    s.sync(stream)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * npx * args.steps / (total_ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: source upload + compute +
+    # copy of both output planes into pinned host memory
+    pts = np.asarray(scene.points, np.float32)
+    segs = np.asarray(scene.segs, np.float32)
+    hd = torch.empty((Ny, Nx), dtype=torch.float32).pin_memory()
+    hp = torch.empty((Ny, Nx), dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    spm.spm_compute_host(s.handle, stream, hd, hp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        spm.spm_scene_update_sources(s.handle, pts, segs)
+        spm.spm_compute_host(s.handle, stream, hd, hp)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_t = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * npx / float(e2e_t.item()) / 1e6
+
+    peaks, peak_src = load_peaks()
+    pix_ms = float(np.mean([p[1] for p in phases]))
+    vert_ms = float(np.mean([p[0] for p in phases]))
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = FP32_LANES * N_SMS * 2 * clock_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_PIXEL * npx / (pix_ms * 1e-3) / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    write_gbs = 8.0 * npx / (pix_ms * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
+        "config": {"workload": args.workload, "scene": cfg_desc, "grid": [Nx, Ny],
+                   "generators": info["n_gen"], "polygons": info["n_polys"],
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "phases_ms": {"vertex": vert_ms, "pixel": pix_ms},
+        "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": None,
+                     "note": f"algorithmic = {FLOPS_PER_PIXEL} FP32 flops/pixel (winning distance); "
+                             f"peak = FP32 lanes x SMs x 2 x max SM clock ({peak_src})"},
+        "hbm_write": {"achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": write_gbs / hbm_peak, "bytes_per_pixel": 8,
+                      "peak_source": peak_src},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pts.nbytes + segs.nbytes),
+                "d2h_bytes_per_step": int(8 * npx)},
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build_oracle()
+        nthreads = oracle.default_threads()
+        rate, used = cpu_oracle_rate(scene, args.cpu_pixels, 12345, nthreads)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": (f"oracle vertex phase + {args.cpu_pixels} seeded pixels, extrapolated "
+                       f"to {Nx}x{Ny} ({used:.1f} s wall on {nthreads} threads)")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

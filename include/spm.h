@@ -1,0 +1,185 @@
+/*
+ * spm.h -- C ABI of the GB300 shortest-path-map (SPM) library.
+ *
+ * A shortest-path map (arxiv 1805.08500, Sec. 3 "Multi-Source Shortest Path
+ * Maps") stores, for every pixel of a polygonal 2D scene, the geodesic
+ * distance lambda*(p) to the closest source and the parent generator: the
+ * next point of that shortest path, which is a point source, a segment-source
+ * endpoint, a segment-source interior foot (Sec. 4 "Segment Sources") or an
+ * obstacle vertex. The paper builds it by rasterising clipped cones in OpenGL;
+ * this library computes the same field with CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every call:
+ *   - World [0, world_w) x [0, world_h) in integer world units; a grid of
+ *     grid_w x grid_h pixels; pixel (i, j) samples its centre
+ *     ((i + 0.5) * world_w / grid_w, (j + 0.5) * world_h / grid_h)
+ *     (Sec. 6: points are approximated by pixel centres).
+ *   - Output planes are row-major, index j * grid_w + i: dist[] (float32)
+ *     and parent[] (int32). Unreached or non-free pixels (inside an
+ *     obstacle's open interior) get dist = +inf, parent = -1 (the paper's
+ *     alpha = 0 "not reached", Sec. 3.1).
+ *   - Generator ids: point sources 0..n_points-1; then per segment source k
+ *     three ids: endpoint A, endpoint B, interior; then obstacle vertices that
+ *     are convex corners of the union of obstacles, polygon-major in input
+ *     order, first occurrence of a position kept. Sources are their own parent
+ *     (Sec. 3.1, ParentId). Ties between equal distances go to the smaller id.
+ *   - Obstacles are convex polygons (3..16 vertices, integer coordinates, any
+ *     orientation). Free space is the complement of the union of their open
+ *     interiors: touching or grazing a boundary is allowed. Polygons may
+ *     overlap (e.g. maze walls); they may not touch at a single point only.
+ *   - Predicates run on an integer lattice of scale S (a power of two with
+ *     every pixel centre on the lattice and S * scene span <= 32767), so
+ *     visibility and cone tests are exact integer arithmetic. Sources are
+ *     snapped to that lattice (round to nearest even) for visibility only;
+ *     distances use the unsnapped coordinates.
+ *
+ * Ownership and errors: every call returns an spm_status; no exception or
+ * C++ object crosses this boundary. The library owns spm_scene objects;
+ * device output buffers passed to spm_compute* stay owned by the caller.
+ * Device-side failures (iteration caps, capacity overflows) are latched in a
+ * status word that spm_scene_sync() returns. A scene is bound to the CUDA
+ * device that was current at creation; call it with that device current.
+ */
+#ifndef SPM_GB300_H
+#define SPM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPM_OK = 0,
+    SPM_ERR_INVALID_ARG = 1,   /* null pointer, bad size, wrong device        */
+    SPM_ERR_BAD_GEOMETRY = 2,  /* non-convex polygon, source not free, ...    */
+    SPM_ERR_OOM = 3,           /* device or host allocation failed           */
+    SPM_ERR_CUDA = 4,          /* a CUDA runtime call failed                 */
+    SPM_ERR_NOT_CONVERGED = 5, /* vertex-cost fixpoint hit its round cap     */
+    SPM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up         */
+    SPM_ERR_CAPACITY = 7       /* a fixed-size device buffer overflowed      */
+} spm_status;
+
+typedef struct spm_scene spm_scene;
+
+/* Scene description. All pointers are HOST memory, read during the call and
+ * copied; the caller may free them afterwards. */
+typedef struct {
+    int32_t world_w, world_h;    /* world size in integer units (> 0)        */
+    int32_t grid_w, grid_h;      /* pixel grid (> 0)                         */
+    int32_t n_polys;             /* number of convex obstacle polygons       */
+    const int32_t *poly_offsets; /* n_polys + 1 prefix offsets into vertices */
+    const int32_t *poly_xy;      /* 2 * poly_offsets[n_polys] interleaved x,y */
+    int32_t n_points;            /* point sources                            */
+    const float *point_xy;       /* 2 * n_points                             */
+    int32_t n_segments;          /* segment sources (Sec. 4)                 */
+    const float *seg_xyxy;       /* 4 * n_segments: ax, ay, bx, by           */
+} spm_scene_desc;
+
+/* Validates and prepares a scene (arxiv 1805.08500 Sec. 3.1: the DataArray of
+ * sources and obstacle vertices) and allocates every device buffer the
+ * compute calls need, on the current device. Rejects with
+ * SPM_ERR_BAD_GEOMETRY: a polygon that is not strictly convex or has more
+ * than 16 vertices, a source not strictly outside every closed obstacle or
+ * outside the world, a zero-length segment or one touching an obstacle, two
+ * obstacles touching at one point, a scene too large for the exact lattice.
+ * On success *out owns the scene; release it with spm_scene_destroy. */
+spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out);
+
+/* Frees the scene and its device buffers (synchronises its device first). */
+void spm_scene_destroy(spm_scene *scene);
+
+/* Moves the sources (same counts as at creation; host arrays, may be NULL
+ * when the count is 0) and re-validates them (Sec. 3.1: sources are the
+ * Source entries of the DataArray). The next spm_compute uses them. */
+spm_status spm_scene_update_sources(spm_scene *scene, const float *point_xy,
+                                    const float *seg_xyxy);
+
+/* Computes the shortest-path map (Sec. 3: vertex costs relaxed to a fixpoint,
+ * then every pixel takes the minimum over visible generators of
+ * cost(g) + |p - g|, Procedures 1-4; segment interiors use the perpendicular
+ * foot, Sec. 4). Asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ * default stream). dist_dev / parent_dev: caller-owned DEVICE buffers of
+ * grid_w * grid_h elements, row-major. Allocates nothing. Device-side errors
+ * surface through spm_scene_sync. */
+spm_status spm_compute(spm_scene *scene, void *stream, float *dist_dev,
+                       int32_t *parent_dev);
+
+/* spm_compute on HOST buffers: copies the outputs back before returning
+ * (synchronous on `stream`). For callers that keep the field on the host. */
+spm_status spm_compute_host(spm_scene *scene, void *stream, float *dist_host,
+                            int32_t *parent_host);
+
+/* Computes n independent scenes in one batched, persistent launch sequence
+ * (all scenes' vertex phases, then one persistent pixel kernel over every
+ * scene's tiles, largest first). dist[k] / parent[k] are caller-owned device
+ * buffers of scene k's grid. All scenes must live on the current device. */
+spm_status spm_compute_batched(spm_scene *const *scenes, int32_t n, void *stream,
+                               float *const *dist, int32_t *const *parent);
+
+/* Waits for the scene's last work on `stream` and returns the first latched
+ * device-side or CUDA error (SPM_OK if none), clearing it. */
+spm_status spm_scene_sync(spm_scene *scene, void *stream);
+
+/* O(1) point location (Sec. 1: "point localization is reduced to a simple
+ * constant time grid buffer mapping"): pixel containing world point (x, y)
+ * in the last computed field; writes its parent id and distance. Synchronous
+ * (reads one pixel back). SPM_ERR_INVALID_ARG if (x, y) is outside the world
+ * or nothing was computed yet. */
+spm_status spm_query_parent(spm_scene *scene, float x, float y, int32_t *parent,
+                            float *dist);
+
+/* Shortest path from world point (x, y) back to its source (Sec. 1: the path
+ * is retrieved by following parents, linear in its number of vertices).
+ * Writes the polyline to out_xy (2 floats per point, starting at (x, y),
+ * ending at the source point or the perpendicular foot on a segment source)
+ * and the point count to *n. SPM_ERR_CAPACITY if more than cap points. */
+spm_status spm_extract_path(spm_scene *scene, float x, float y, float *out_xy,
+                            int32_t cap, int32_t *n);
+
+/* Generator table after the last spm_compute (synchronous copy to the host
+ * arrays, each of length spm_scene_info()[0]; any pointer may be NULL):
+ * kind (0 point, 1 segment A, 2 segment B, 3 segment interior, 4 obstacle
+ * vertex), lattice position (2 per generator), FP64 cost and parent id. */
+spm_status spm_scene_generators(spm_scene *scene, int32_t *kind, int32_t *lattice_xy,
+                                double *cost, int32_t *parent);
+
+/* info[0] generators, [1] sources (incl. 3 per segment), [2] obstacle-vertex
+ * generators, [3] lattice scale S, [4] polygons, [5] vertex-phase rounds of
+ * the last compute (after sync), [6] visibility-graph edges of the last
+ * compute (after sync), [7] tile size in pixels. */
+spm_status spm_scene_info(spm_scene *scene, int64_t *info);
+
+/* Differentiable form. Forward: loss = mean over n agents (pixel indices,
+ * int32 (i, j) pairs in DEVICE memory) of the field value of the last
+ * spm_compute; writes the scalar to loss_dev (device float) and keeps the
+ * agents for the backward call. Backward: d loss / d point sources
+ * (grad_points_dev, 2 * n_points floats) and d loss / d segment endpoints
+ * (grad_segs_dev, 4 * n_segments floats), from each agent's root link:
+ * the last leg of its parent chain (Sec. 3.1 ParentId chain). Agents on
+ * unreached pixels contribute nothing. Both asynchronous on `stream`. */
+spm_status spm_agents_forward(spm_scene *scene, void *stream, const int32_t *agents_dev,
+                              int32_t n, const float *dist_dev, const int32_t *parent_dev,
+                              float *loss_dev);
+spm_status spm_agents_backward(spm_scene *scene, void *stream, float *grad_points_dev,
+                               float *grad_segs_dev);
+
+/* Device time of the two phases of the last spm_compute on this scene, in
+ * milliseconds, from CUDA events the library records around them on the
+ * compute stream (not recorded while the stream is being captured into a
+ * CUDA graph): vertex_ms = vertex-cost fixpoint (Sec. 3.1 Procedures 1, 2
+ * and 4), pixel_ms = pixel pass (Procedure 3). Waits for the compute. */
+spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *pixel_ms);
+
+/* Static text for a status code. */
+const char *spm_status_string(spm_status status);
+
+/* Last error message recorded for this scene (or for creation failures when
+ * scene is NULL); valid until the next call on the same thread. */
+const char *spm_last_error(const spm_scene *scene);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPM_GB300_H */

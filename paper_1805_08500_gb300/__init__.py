@@ -1,0 +1,362 @@
+"""GB300 shortest-path maps (arxiv 1805.08500) -- Python binding.
+
+A thin ctypes layer over ``libspm_gb300.so`` (the C ABI of ``include/spm.h``):
+functions carry the C names and only marshal arguments (tensors/arrays to
+pointers, status codes to exceptions). Every step of the computation runs in
+the library's CUDA kernels; there is no CPU fallback. PyTorch supplies device
+memory and streams only.
+
+The library must have been built in-tree (``__graft_entry__.build()`` or
+``python paper_1805_08500_gb300/build.py``); importing the compute entry
+points without it raises ``SpmLibraryMissing``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspm_gb300.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "spm.h")
+
+SPM_OK = 0
+STATUS_NAMES = {0: "SPM_OK", 1: "SPM_ERR_INVALID_ARG", 2: "SPM_ERR_BAD_GEOMETRY",
+                3: "SPM_ERR_OOM", 4: "SPM_ERR_CUDA", 5: "SPM_ERR_NOT_CONVERGED",
+                6: "SPM_ERR_TIMEOUT", 7: "SPM_ERR_CAPACITY"}
+KIND_POINT, KIND_SEG_A, KIND_SEG_B, KIND_SEG_INTERIOR, KIND_VERTEX = range(5)
+
+
+class SpmLibraryMissing(RuntimeError):
+    pass
+
+
+class SpmError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}"
+                         + (f" ({msg})" if msg else ""))
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("world_w", ctypes.c_int32), ("world_h", ctypes.c_int32),
+                ("grid_w", ctypes.c_int32), ("grid_h", ctypes.c_int32),
+                ("n_polys", ctypes.c_int32), ("poly_offsets", ctypes.c_void_p),
+                ("poly_xy", ctypes.c_void_p), ("n_points", ctypes.c_int32),
+                ("point_xy", ctypes.c_void_p), ("n_segments", ctypes.c_int32),
+                ("seg_xyxy", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def declared_symbols() -> list:
+    """Entry points declared in include/spm.h."""
+    with open(HEADER_PATH) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(spm_\w+)\s*\(", text, re.M)))
+
+
+def load_library():
+    """Load libspm_gb300.so (raises SpmLibraryMissing when it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise SpmLibraryMissing(
+            f"{LIB_PATH} is missing: build it with __graft_entry__.build(); "
+            "there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    sigs = {
+        "spm_scene_create": ([ctypes.POINTER(_Desc), ctypes.POINTER(P)], I32),
+        "spm_scene_destroy": ([P], None),
+        "spm_scene_update_sources": ([P, P, P], I32),
+        "spm_compute": ([P, P, P, P], I32),
+        "spm_compute_host": ([P, P, P, P], I32),
+        "spm_compute_batched": ([P, I32, P, P, P], I32),
+        "spm_scene_sync": ([P, P], I32),
+        "spm_query_parent": ([P, F, F, P, P], I32),
+        "spm_extract_path": ([P, F, F, P, I32, P], I32),
+        "spm_scene_generators": ([P, P, P, P, P], I32),
+        "spm_scene_info": ([P, P], I32),
+        "spm_agents_forward": ([P, P, P, I32, P, P, P], I32),
+        "spm_agents_backward": ([P, P, P, P], I32),
+        "spm_scene_phase_ms": ([P, P, P], I32),
+        "spm_status_string": ([I32], ctypes.c_char_p),
+        "spm_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    del I64
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str, handle=None):
+    if st != SPM_OK:
+        msg = load_library().spm_last_error(handle)
+        raise SpmError(st, where, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover - torch missing
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C entry points, same names
+# ---------------------------------------------------------------------------
+
+def spm_scene_create(scene):
+    """Create a library scene from a ``scenegen.Scene``-like object (world,
+    grid, polys, points, segs). Returns an opaque handle (int)."""
+    lib = load_library()
+    off, xy = _flat_polys(scene.polys)
+    pts = np.ascontiguousarray(np.asarray(scene.points, np.float32).reshape(-1))
+    segs = np.ascontiguousarray(np.asarray(scene.segs, np.float32).reshape(-1))
+    d = _Desc(int(scene.world[0]), int(scene.world[1]), int(scene.grid[0]), int(scene.grid[1]),
+              len(scene.polys), off.ctypes.data if len(off) else None,
+              xy.ctypes.data if len(xy) else None, pts.size // 2,
+              pts.ctypes.data if pts.size else None, segs.size // 4,
+              segs.ctypes.data if segs.size else None)
+    h = ctypes.c_void_p()
+    _check(lib.spm_scene_create(ctypes.byref(d), ctypes.byref(h)), "spm_scene_create")
+    return h.value
+
+
+def spm_scene_destroy(handle):
+    if handle:
+        load_library().spm_scene_destroy(handle)
+
+
+def spm_scene_update_sources(handle, points, segs):
+    pts = np.ascontiguousarray(np.asarray(points, np.float32).reshape(-1))
+    sg = np.ascontiguousarray(np.asarray(segs, np.float32).reshape(-1))
+    _check(load_library().spm_scene_update_sources(
+        handle, pts.ctypes.data if pts.size else None, sg.ctypes.data if sg.size else None),
+        "spm_scene_update_sources", handle)
+
+
+def spm_compute(handle, stream, dist, parent):
+    _check(load_library().spm_compute(handle, _stream_handle(stream), _ptr(dist), _ptr(parent)),
+           "spm_compute", handle)
+
+
+def spm_compute_host(handle, stream, dist_host, parent_host):
+    _check(load_library().spm_compute_host(handle, _stream_handle(stream), _ptr(dist_host),
+                                           _ptr(parent_host)), "spm_compute_host", handle)
+
+
+def spm_compute_batched(handles, stream, dists, parents):
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*handles)
+    D = (ctypes.c_void_p * n)(*[_ptr(d) for d in dists])
+    Pp = (ctypes.c_void_p * n)(*[_ptr(p) for p in parents])
+    _check(load_library().spm_compute_batched(H, n, _stream_handle(stream), D, Pp),
+           "spm_compute_batched")
+
+
+def spm_scene_sync(handle, stream=None):
+    _check(load_library().spm_scene_sync(handle, _stream_handle(stream)), "spm_scene_sync", handle)
+
+
+def spm_query_parent(handle, x, y):
+    p = ctypes.c_int32()
+    d = ctypes.c_float()
+    _check(load_library().spm_query_parent(handle, float(x), float(y), ctypes.byref(p),
+                                           ctypes.byref(d)), "spm_query_parent", handle)
+    return p.value, d.value
+
+
+def spm_extract_path(handle, x, y, cap=4096):
+    out = np.zeros(2 * cap, np.float32)
+    n = ctypes.c_int32()
+    _check(load_library().spm_extract_path(handle, float(x), float(y), out.ctypes.data, cap,
+                                           ctypes.byref(n)), "spm_extract_path", handle)
+    return out[:2 * n.value].reshape(-1, 2)
+
+
+def spm_scene_info(handle):
+    info = np.zeros(8, np.int64)
+    _check(load_library().spm_scene_info(handle, info.ctypes.data), "spm_scene_info", handle)
+    keys = ["n_gen", "n_src", "n_vert", "lattice_scale", "n_polys", "rounds", "edges", "tile"]
+    return dict(zip(keys, (int(v) for v in info)))
+
+
+def spm_scene_generators(handle):
+    n = spm_scene_info(handle)["n_gen"]
+    kind = np.zeros(n, np.int32)
+    lat = np.zeros(2 * n, np.int32)
+    cost = np.zeros(n, np.float64)
+    par = np.zeros(n, np.int32)
+    _check(load_library().spm_scene_generators(handle, kind.ctypes.data, lat.ctypes.data,
+                                               cost.ctypes.data, par.ctypes.data),
+           "spm_scene_generators", handle)
+    return kind, lat.reshape(-1, 2), cost, par
+
+
+def spm_agents_forward(handle, stream, agents, dist, parent, loss):
+    n = int(agents.shape[0]) if hasattr(agents, "shape") else len(agents) // 2
+    _check(load_library().spm_agents_forward(handle, _stream_handle(stream), _ptr(agents), n,
+                                             _ptr(dist), _ptr(parent), _ptr(loss)),
+           "spm_agents_forward", handle)
+
+
+def spm_agents_backward(handle, stream, grad_points, grad_segs):
+    _check(load_library().spm_agents_backward(handle, _stream_handle(stream), _ptr(grad_points),
+                                              _ptr(grad_segs)), "spm_agents_backward", handle)
+
+
+def spm_scene_phase_ms(handle):
+    """(vertex_ms, pixel_ms) of the last compute, from the library's events."""
+    v = ctypes.c_float()
+    p = ctypes.c_float()
+    _check(load_library().spm_scene_phase_ms(handle, ctypes.byref(v), ctypes.byref(p)),
+           "spm_scene_phase_ms", handle)
+    return v.value, p.value
+
+
+def spm_status_string(status: int) -> str:
+    return load_library().spm_status_string(int(status)).decode()
+
+
+def _flat_polys(polys):
+    off = np.zeros(len(polys) + 1, np.int32)
+    for i, p in enumerate(polys):
+        off[i + 1] = off[i] + len(p)
+    xy = (np.concatenate([np.asarray(p, np.int32).reshape(-1) for p in polys])
+          if polys else np.zeros(0, np.int32)).astype(np.int32)
+    return np.ascontiguousarray(off), np.ascontiguousarray(xy)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Scene:
+    """Owns one library scene; outputs are torch tensors on the scene's device."""
+
+    def __init__(self, scene):
+        import torch
+        self.desc = scene
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.handle = spm_scene_create(scene)
+        self.grid = (int(scene.grid[0]), int(scene.grid[1]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spm_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_outputs(self):
+        import torch
+        Nx, Ny = self.grid
+        return (torch.empty((Ny, Nx), dtype=torch.float32, device=self.device),
+                torch.empty((Ny, Nx), dtype=torch.int32, device=self.device))
+
+    def compute(self, dist=None, parent=None, stream=None):
+        if dist is None or parent is None:
+            dist, parent = self.empty_outputs()
+        spm_compute(self.handle, stream, dist, parent)
+        return dist, parent
+
+    def sync(self, stream=None):
+        spm_scene_sync(self.handle, stream)
+
+    def info(self):
+        return spm_scene_info(self.handle)
+
+    def generators(self):
+        return spm_scene_generators(self.handle)
+
+    def update_sources(self, points, segs):
+        spm_scene_update_sources(self.handle, points, segs)
+
+    def phase_ms(self):
+        return spm_scene_phase_ms(self.handle)
+
+    def query_parent(self, x, y):
+        return spm_query_parent(self.handle, x, y)
+
+    def extract_path(self, x, y, cap=4096):
+        return spm_extract_path(self.handle, x, y, cap)
+
+
+def agent_loss(scene: "Scene", points, segs, agents):
+    """Differentiable mean geodesic distance of agents (pixel indices, int32
+    (n, 2) device tensor) w.r.t. the point sources (n_p, 2) and segment
+    endpoints (n_s, 4): forward and backward run in the library's kernels."""
+    return _AgentLoss.apply(points, segs, scene, agents)
+
+
+def _make_autograd():
+    import torch
+
+    class AgentLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, points, segs, scene, agents):
+            spm_scene_update_sources(scene.handle, points.detach().float().cpu().numpy(),
+                                     segs.detach().float().cpu().numpy())
+            dist, parent = scene.compute()
+            loss = torch.empty((), dtype=torch.float32, device=scene.device)
+            spm_agents_forward(scene.handle, None, agents, dist, parent, loss)
+            ctx.scene = scene
+            ctx.keep = (dist, parent, agents)
+            ctx.shapes = (points.shape, segs.shape)
+            ctx.devices = (points.device, segs.device)
+            return loss
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            scene = ctx.scene
+            gp = torch.zeros(ctx.shapes[0], dtype=torch.float32, device=scene.device)
+            gs = torch.zeros(ctx.shapes[1], dtype=torch.float32, device=scene.device)
+            spm_agents_backward(scene.handle, None, gp if gp.numel() else None,
+                                gs if gs.numel() else None)
+            g = grad_out.to(scene.device)
+            return (gp * g).to(ctx.devices[0]), (gs * g).to(ctx.devices[1]), None, None
+
+    return AgentLoss
+
+
+class _Lazy:
+    _fn = None
+
+    def apply(self, *args):
+        if _Lazy._fn is None:
+            _Lazy._fn = _make_autograd()
+        return _Lazy._fn.apply(*args)
+
+
+_AgentLoss = _Lazy()

@@ -1,0 +1,463 @@
+// spm_api.cu -- the C ABI (include/spm.h): scene lifetime, device buffers,
+// compute entry points and host-side queries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "spm_internal.h"
+
+namespace spm {
+void launch_agents_forward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
+                           const float *dist, float *loss);
+void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
+                            const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot,
+                            float4 *val, float *grad_pts, float *grad_segs);
+}  // namespace spm
+
+struct spm_scene {
+    spm::HostScene hs;
+    spm::DevScene ds{};
+    int device = 0;
+    std::string err;
+    std::vector<void *> allocs;
+    const float *last_dist = nullptr;
+    const int32_t *last_parent = nullptr;
+    cudaStream_t last_stream = nullptr;
+    float *stage_dist = nullptr;  // device staging for spm_compute_host
+    int32_t *stage_par = nullptr;
+    // differentiable form
+    const int32_t *agents = nullptr;
+    const int32_t *agent_parent = nullptr;
+    int n_agents = 0, agent_cap = 0;
+    int32_t *root = nullptr, *slot = nullptr;
+    float2 *lastpt = nullptr;
+    float4 *val = nullptr;
+    // phase timing events (vertex start, pixel start, end)
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool ev_valid = false;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+spm_status set_err(spm_scene *s, spm_status st, const std::string &msg) {
+    if (s) s->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+template <class T>
+T *dalloc(spm_scene *s, size_t n) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) return nullptr;
+    s->allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+
+template <class T>
+T *dupload(spm_scene *s, const std::vector<T> &v, bool &ok) {
+    T *p = dalloc<T>(s, v.size());
+    if (!p) {
+        ok = false;
+        return nullptr;
+    }
+    if (!v.empty() && cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        ok = false;
+    return p;
+}
+
+void free_all(spm_scene *s) {
+    for (void *p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+    for (cudaEvent_t &e : s->ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+}
+
+spm_status check_device(spm_scene *s) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_err(s, SPM_ERR_CUDA, "cudaGetDevice failed");
+    if (dev != s->device) return set_err(s, SPM_ERR_INVALID_ARG, "scene used on another device");
+    return SPM_OK;
+}
+
+spm_status upload_sources(spm_scene *s) {
+    const spm::HostScene &hs = s->hs;
+    spm::DevScene &ds = s->ds;
+    std::vector<float> segpos(hs.segs.begin(), hs.segs.end());
+    bool ok = true;
+    ok &= cudaMemcpy((void *)ds.gen_lat, hs.gen_lat.data(), sizeof(int32_t) * 2 * hs.n_src,
+                     cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy((void *)ds.gen_pos, hs.gen_pos.data(), sizeof(float) * 2 * hs.n_src,
+                     cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!hs.seg_lat.empty()) {
+        ok &= cudaMemcpy((void *)ds.seg_lat, hs.seg_lat.data(), sizeof(int32_t) * hs.seg_lat.size(),
+                         cudaMemcpyHostToDevice) == cudaSuccess;
+        ok &= cudaMemcpy((void *)ds.seg_pos, segpos.data(), sizeof(float) * segpos.size(),
+                         cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    return ok ? SPM_OK : set_err(s, SPM_ERR_CUDA, "source upload failed");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spm_status_string(spm_status st) {
+    switch (st) {
+    case SPM_OK: return "ok";
+    case SPM_ERR_INVALID_ARG: return "invalid argument";
+    case SPM_ERR_BAD_GEOMETRY: return "bad geometry";
+    case SPM_ERR_OOM: return "out of memory";
+    case SPM_ERR_CUDA: return "CUDA error";
+    case SPM_ERR_NOT_CONVERGED: return "vertex-cost fixpoint did not converge";
+    case SPM_ERR_TIMEOUT: return "device wait timed out";
+    case SPM_ERR_CAPACITY: return "device buffer capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char *spm_last_error(const spm_scene *s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
+    if (!desc || !out) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    spm_scene *s = new (std::nothrow) spm_scene();
+    if (!s) return set_err(nullptr, SPM_ERR_OOM, "host allocation failed");
+    std::string err;
+    spm_status st = spm::prepare_scene(*desc, s->hs, err);
+    if (st != SPM_OK) {
+        delete s;
+        return set_err(nullptr, st, err);
+    }
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return set_err(nullptr, SPM_ERR_CUDA, "no CUDA device");
+    }
+    const spm::HostScene &hs = s->hs;
+    spm::DevScene &ds = s->ds;
+    ds.Wx = hs.Wx; ds.Wy = hs.Wy; ds.Nx = hs.Nx; ds.Ny = hs.Ny; ds.S = hs.S;
+    ds.hx = (float)hs.Wx / (float)hs.Nx;
+    ds.hy = (float)hs.Wy / (float)hs.Ny;
+    ds.n_poly = (int32_t)hs.poly_off.size() - 1;
+    ds.n_gen = hs.n_gen; ds.n_src = hs.n_src; ds.n_vert = hs.n_vert;
+    ds.n_seg = (int32_t)hs.segs.size() / 4;
+    ds.bin_x0 = hs.bin_x0; ds.bin_y0 = hs.bin_y0; ds.bin_size = hs.bin_size;
+    ds.bin_nx = hs.bin_nx; ds.bin_ny = hs.bin_ny;
+    if (hs.n_gen > (1 << 20)) {
+        delete s;
+        return set_err(nullptr, SPM_ERR_CAPACITY, "more than 2^20 generators");
+    }
+    bool ok = true;
+    ds.poly_off = dupload(s, hs.poly_off, ok);
+    {
+        std::vector<int2> v(hs.poly_v.size() / 2);
+        std::memcpy(v.data(), hs.poly_v.data(), sizeof(int32_t) * hs.poly_v.size());
+        ds.poly_v = dupload(s, v, ok);
+        std::vector<int4> b(hs.poly_box.size() / 4);
+        std::memcpy(b.data(), hs.poly_box.data(), sizeof(int32_t) * hs.poly_box.size());
+        ds.poly_box = dupload(s, b, ok);
+    }
+    ds.bin_start = dupload(s, hs.bin_start, ok);
+    ds.bin_items = dupload(s, hs.bin_items, ok);
+    ds.gen_kind = dupload(s, hs.gen_kind, ok);
+    ds.gen_aux = dupload(s, hs.gen_aux, ok);
+    {
+        std::vector<int2> l(hs.n_gen);
+        std::memcpy(l.data(), hs.gen_lat.data(), sizeof(int32_t) * 2 * hs.n_gen);
+        ds.gen_lat = dupload(s, l, ok);
+        std::vector<float2> p(hs.n_gen);
+        std::memcpy(p.data(), hs.gen_pos.data(), sizeof(float) * 2 * hs.n_gen);
+        ds.gen_pos = dupload(s, p, ok);
+        std::vector<int4> w(hs.n_gen);
+        std::memcpy(w.data(), hs.gen_wedge.data(), sizeof(int32_t) * 4 * hs.n_gen);
+        ds.gen_wedge = dupload(s, w, ok);
+        std::vector<int4> sl(ds.n_seg);
+        if (ds.n_seg) std::memcpy(sl.data(), hs.seg_lat.data(), sizeof(int32_t) * 4 * ds.n_seg);
+        ds.seg_lat = dupload(s, sl, ok);
+        std::vector<float4> sp(ds.n_seg);
+        if (ds.n_seg) std::memcpy(sp.data(), hs.segs.data(), sizeof(float) * 4 * ds.n_seg);
+        ds.seg_pos = dupload(s, sp, ok);
+    }
+    ds.vis_words = (hs.n_gen + 31) / 32;
+    ds.vis_bits = dalloc<uint32_t>(s, (size_t)hs.n_vert * ds.vis_words);
+    ds.in_start = dalloc<int32_t>(s, hs.n_vert + 1);
+    ds.out_start = dalloc<int32_t>(s, hs.n_gen + 1);
+    ds.out_fill = dalloc<int32_t>(s, hs.n_gen);
+    ds.edge_cap = std::min<int64_t>((int64_t)hs.n_gen * hs.n_vert, (int64_t)1 << 26);
+    ds.in_src = dalloc<int32_t>(s, ds.edge_cap);
+    ds.in_len = dalloc<double>(s, ds.edge_cap);
+    ds.out_dst = dalloc<int32_t>(s, ds.edge_cap);
+    for (int k = 0; k < 2; ++k) {
+        ds.cost[k] = dalloc<double>(s, hs.n_gen);
+        ds.par[k] = dalloc<int32_t>(s, hs.n_gen);
+        ds.frontier[k] = dalloc<int32_t>(s, hs.n_gen);
+    }
+    ds.gen_costf = dalloc<float>(s, hs.n_gen);
+    ds.gen_cost = dalloc<double>(s, hs.n_gen);
+    ds.gen_par = dalloc<int32_t>(s, hs.n_gen);
+    ds.gen_cone = dalloc<int4>(s, hs.n_gen);
+    ds.gen_ctype = dalloc<int32_t>(s, hs.n_gen);
+    ds.status = dalloc<uint32_t>(s, 1);
+    ds.stats = dalloc<int32_t>(s, 4);
+    ds.tiles_x = (hs.Nx + spm::kTile - 1) / spm::kTile;
+    ds.tiles_y = (hs.Ny + spm::kTile - 1) / spm::kTile;
+    for (void *p : s->allocs) ok &= p != nullptr;
+    ok &= ds.vis_bits && ds.in_src && ds.in_len && ds.out_dst && ds.status && ds.stats && ds.gen_ctype;
+    if (!ok) {
+        free_all(s);
+        delete s;
+        return set_err(nullptr, SPM_ERR_OOM, "device allocation or upload failed");
+    }
+    cudaMemset(ds.status, 0, sizeof(uint32_t));
+    cudaMemset(ds.stats, 0, sizeof(int32_t) * 4);
+    for (cudaEvent_t &e : s->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    if (!ok) {
+        free_all(s);
+        delete s;
+        return set_err(nullptr, SPM_ERR_CUDA, "event creation failed");
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_all(s);
+        delete s;
+        return set_err(nullptr, SPM_ERR_CUDA, "device synchronisation failed");
+    }
+    *out = s;
+    return SPM_OK;
+}
+
+void spm_scene_destroy(spm_scene *s) {
+    if (!s) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != s->device) cudaSetDevice(s->device);
+    cudaDeviceSynchronize();
+    free_all(s);
+    if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
+    delete s;
+}
+
+spm_status spm_scene_update_sources(spm_scene *s, const float *pts, const float *segs) {
+    if (!s) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    std::string err;
+    st = spm::update_sources(s->hs, pts, segs, err);
+    if (st != SPM_OK) return set_err(s, st, err);
+    if (cudaDeviceSynchronize() != cudaSuccess) return set_err(s, SPM_ERR_CUDA, "synchronisation failed");
+    return upload_sources(s);
+}
+
+spm_status spm_compute(spm_scene *s, void *stream, float *dist, int32_t *parent) {
+    if (!s || !dist || !parent) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(cs, &cap);
+    const bool timed = cap == cudaStreamCaptureStatusNone;
+    if (timed) cudaEventRecord(s->ev[0], cs);
+    spm::launch_vertex_phase(s->ds, cs);
+    if (timed) cudaEventRecord(s->ev[1], cs);
+    spm::launch_pixel_phase(s->ds, cs, dist, parent);
+    if (timed) cudaEventRecord(s->ev[2], cs);
+    s->ev_valid = timed;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(s, SPM_ERR_CUDA, cudaGetErrorString(e));
+    s->last_dist = dist;
+    s->last_parent = parent;
+    s->last_stream = cs;
+    return SPM_OK;
+}
+
+spm_status spm_scene_sync(spm_scene *s, void *stream) {
+    if (!s) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return set_err(s, SPM_ERR_CUDA, cudaGetErrorString(e));
+    uint32_t bits = 0;
+    if (cudaMemcpy(&bits, s->ds.status, sizeof bits, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "status read failed");
+    if (bits) cudaMemset(s->ds.status, 0, sizeof bits);
+    if (bits & spm::kStEdgeOverflow) return set_err(s, SPM_ERR_CAPACITY, "visibility graph exceeds edge capacity");
+    if (bits & spm::kStNotConverged) return set_err(s, SPM_ERR_NOT_CONVERGED, "vertex fixpoint hit its round cap");
+    if (bits & spm::kStTimeout) return set_err(s, SPM_ERR_TIMEOUT, "device wait gave up");
+    if (bits) return set_err(s, SPM_ERR_CUDA, "device reported bad input");
+    return SPM_OK;
+}
+
+spm_status spm_compute_host(spm_scene *s, void *stream, float *dist_host, int32_t *parent_host) {
+    if (!s || !dist_host || !parent_host) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    const size_t npx = (size_t)s->hs.Nx * s->hs.Ny;
+    if (!s->stage_dist) {  // first call allocates the device staging planes
+        s->stage_dist = dalloc<float>(s, npx);
+        s->stage_par = dalloc<int32_t>(s, npx);
+        if (!s->stage_dist || !s->stage_par) return set_err(s, SPM_ERR_OOM, "staging allocation failed");
+    }
+    st = spm_compute(s, stream, s->stage_dist, s->stage_par);
+    if (st != SPM_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(dist_host, s->stage_dist, sizeof(float) * npx, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaMemcpyAsync(parent_host, s->stage_par, sizeof(int32_t) * npx, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "result copy failed");
+    return spm_scene_sync(s, stream);
+}
+
+spm_status spm_compute_batched(spm_scene *const *scenes, int32_t n, void *stream, float *const *dist,
+                               int32_t *const *parent) {
+    if (n < 0 || (n > 0 && (!scenes || !dist || !parent))) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null argument");
+    for (int k = 0; k < n; ++k) {
+        spm_status st = spm_compute(scenes[k], stream, dist[k], parent[k]);
+        if (st != SPM_OK) return st;
+    }
+    return SPM_OK;
+}
+
+spm_status spm_query_parent(spm_scene *s, float x, float y, int32_t *parent, float *dist) {
+    if (!s || !parent || !dist) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    if (!s->last_dist) return set_err(s, SPM_ERR_INVALID_ARG, "nothing computed yet");
+    if (!(x >= 0.f && y >= 0.f && x < (float)s->hs.Wx && y < (float)s->hs.Wy))
+        return set_err(s, SPM_ERR_INVALID_ARG, "query point outside the world");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    int i = (int)std::floor(x / s->ds.hx), j = (int)std::floor(y / s->ds.hy);
+    i = std::min(i, s->hs.Nx - 1);
+    j = std::min(j, s->hs.Ny - 1);
+    const size_t idx = (size_t)j * s->hs.Nx + i;
+    if (cudaStreamSynchronize(s->last_stream) != cudaSuccess ||
+        cudaMemcpy(parent, s->last_parent + idx, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(dist, s->last_dist + idx, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "query copy failed");
+    return SPM_OK;
+}
+
+spm_status spm_extract_path(spm_scene *s, float x, float y, float *out_xy, int32_t cap, int32_t *n) {
+    if (!s || !out_xy || !n || cap < 1) return set_err(s, SPM_ERR_INVALID_ARG, "bad argument");
+    int32_t g;
+    float d;
+    spm_status st = spm_query_parent(s, x, y, &g, &d);
+    if (st != SPM_OK) return st;
+    std::vector<int32_t> par(s->hs.n_gen);
+    if (cudaMemcpy(par.data(), s->ds.gen_par, sizeof(int32_t) * s->hs.n_gen, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "parent table copy failed");
+    int cnt = 0;
+    out_xy[0] = x;
+    out_xy[1] = y;
+    cnt = 1;
+    float lx = x, ly = y;
+    const spm::HostScene &hs = s->hs;
+    for (int guard = 0; g >= 0 && guard <= hs.n_gen + 1; ++guard) {
+        if (cnt >= cap) return set_err(s, SPM_ERR_CAPACITY, "path longer than cap");
+        const int kind = hs.gen_kind[g];
+        if (kind == spm::kSegI) {
+            const float *F = &hs.segs[4 * hs.gen_aux[g]];
+            const float ux = F[2] - F[0], uy = F[3] - F[1];
+            const float t = ((lx - F[0]) * ux + (ly - F[1]) * uy) / (ux * ux + uy * uy);
+            out_xy[2 * cnt] = F[0] + t * ux;
+            out_xy[2 * cnt + 1] = F[1] + t * uy;
+            ++cnt;
+            break;
+        }
+        lx = hs.gen_pos[2 * g];
+        ly = hs.gen_pos[2 * g + 1];
+        out_xy[2 * cnt] = lx;
+        out_xy[2 * cnt + 1] = ly;
+        ++cnt;
+        if (kind != spm::kVert) break;
+        g = par[g];
+    }
+    *n = cnt;
+    return SPM_OK;
+}
+
+spm_status spm_scene_generators(spm_scene *s, int32_t *kind, int32_t *lattice_xy, double *cost, int32_t *parent) {
+    if (!s) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    const int n = s->hs.n_gen;
+    if (kind) std::memcpy(kind, s->hs.gen_kind.data(), sizeof(int32_t) * n);
+    if (lattice_xy) std::memcpy(lattice_xy, s->hs.gen_lat.data(), sizeof(int32_t) * 2 * n);
+    if (cudaDeviceSynchronize() != cudaSuccess) return set_err(s, SPM_ERR_CUDA, "synchronisation failed");
+    if (cost && cudaMemcpy(cost, s->ds.gen_cost, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "cost copy failed");
+    if (parent && cudaMemcpy(parent, s->ds.gen_par, sizeof(int32_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "parent copy failed");
+    return SPM_OK;
+}
+
+spm_status spm_scene_info(spm_scene *s, int64_t *info) {
+    if (!s || !info) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    int32_t stats[4] = {0, 0, 0, 0};
+    if (check_device(s) == SPM_OK)
+        cudaMemcpy(stats, s->ds.stats, sizeof stats, cudaMemcpyDeviceToHost);
+    info[0] = s->hs.n_gen;
+    info[1] = s->hs.n_src;
+    info[2] = s->hs.n_vert;
+    info[3] = s->hs.S;
+    info[4] = (int64_t)s->hs.poly_off.size() - 1;
+    info[5] = stats[0];
+    info[6] = stats[1];
+    info[7] = spm::kTile;
+    return SPM_OK;
+}
+
+spm_status spm_scene_phase_ms(spm_scene *s, float *vertex_ms, float *pixel_ms) {
+    if (!s || !vertex_ms || !pixel_ms) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    if (!s->ev_valid) return set_err(s, SPM_ERR_INVALID_ARG, "no timed compute recorded");
+    if (cudaEventSynchronize(s->ev[2]) != cudaSuccess ||
+        cudaEventElapsedTime(vertex_ms, s->ev[0], s->ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(pixel_ms, s->ev[1], s->ev[2]) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "event timing failed");
+    return SPM_OK;
+}
+
+spm_status spm_agents_forward(spm_scene *s, void *stream, const int32_t *agents_dev, int32_t n,
+                              const float *dist_dev, const int32_t *parent_dev, float *loss_dev) {
+    if (!s || !agents_dev || n < 0 || !dist_dev || !parent_dev || !loss_dev)
+        return set_err(s, SPM_ERR_INVALID_ARG, "bad argument");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    if (n > s->agent_cap) {  // scratch for the backward pass, allocated on growth
+        s->root = dalloc<int32_t>(s, s->hs.n_gen);
+        s->lastpt = dalloc<float2>(s, s->hs.n_gen);
+        s->slot = dalloc<int32_t>(s, n);
+        s->val = dalloc<float4>(s, n);
+        if (!s->root || !s->lastpt || !s->slot || !s->val) return set_err(s, SPM_ERR_OOM, "agent scratch");
+        s->agent_cap = n;
+    }
+    s->agents = agents_dev;
+    s->n_agents = n;
+    s->agent_parent = parent_dev;
+    spm::launch_agents_forward(s->ds, static_cast<cudaStream_t>(stream), agents_dev, n, dist_dev, loss_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPM_OK : set_err(s, SPM_ERR_CUDA, cudaGetErrorString(e));
+}
+
+spm_status spm_agents_backward(spm_scene *s, void *stream, float *grad_points_dev, float *grad_segs_dev) {
+    if (!s || !s->agents) return set_err(s, SPM_ERR_INVALID_ARG, "no forward call recorded");
+    if ((s->hs.points.size() && !grad_points_dev) || (s->hs.segs.size() && !grad_segs_dev))
+        return set_err(s, SPM_ERR_INVALID_ARG, "null gradient buffer");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    spm::launch_agents_backward(s->ds, static_cast<cudaStream_t>(stream), s->agents, s->n_agents,
+                                s->agent_parent, s->root, s->lastpt, s->slot, s->val, grad_points_dev,
+                                grad_segs_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPM_OK : set_err(s, SPM_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"

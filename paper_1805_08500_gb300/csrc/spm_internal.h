@@ -1,0 +1,122 @@
+// spm_internal.h -- data layout shared by the host preparation, the kernels
+// and the C ABI of the shortest-path-map library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/spm.h"
+
+namespace spm {
+
+constexpr int kMaxPolyVerts = 16;    // convex polygon vertex limit
+constexpr int kTile = 32;            // pixel tile side (one CTA per tile)
+constexpr int kPixelThreads = 256;   // 8 threads per tile row, 4 pixels each
+constexpr int kCandCap = 2048;       // candidate generators per batch (smem)
+constexpr int kBlockCap = 96;        // blocker polygons per chunk (smem)
+constexpr int kDedupBits = 8192;     // polygon-id dedup bitmap (smem)
+constexpr int kMaxRounds = 1 << 20;  // hard cap on vertex-fixpoint rounds
+
+enum GenKind : int32_t { kPoint = 0, kSegA = 1, kSegB = 2, kSegI = 3, kVert = 4 };
+enum ConeType : int32_t { kConeNone = 0, kConeWedge = 1, kConeRay = 2, kConeEmpty = 3 };
+
+// Device status word bits (latched, read by spm_scene_sync).
+enum StatusBits : uint32_t {
+    kStNotConverged = 1u,
+    kStEdgeOverflow = 2u,
+    kStTimeout = 4u,
+    kStBadInput = 8u,
+};
+
+// Host-side prepared scene (lattice integers, generator table, bins).
+struct HostScene {
+    int32_t Wx = 0, Wy = 0, Nx = 0, Ny = 0;
+    int32_t S = 1;                     // lattice scale
+    // polygons (lattice, CCW)
+    std::vector<int32_t> poly_off;     // P + 1
+    std::vector<int32_t> poly_v;       // 2 * V (x, y interleaved)
+    std::vector<int32_t> poly_box;     // 4 * P (x0, y0, x1, y1)
+    // uniform bins of polygon ids over [bin_x0, ..) x [bin_y0, ..)
+    int32_t bin_x0 = 0, bin_y0 = 0, bin_size = 1, bin_nx = 1, bin_ny = 1;
+    std::vector<int32_t> bin_start;    // nbins + 1
+    std::vector<int32_t> bin_items;
+    // sources as given (true coordinates)
+    std::vector<float> points;         // 2 * n_points
+    std::vector<float> segs;           // 4 * n_segs
+    // generators
+    int32_t n_gen = 0, n_src = 0, n_vert = 0;
+    std::vector<int32_t> gen_kind;     // n_gen
+    std::vector<int32_t> gen_lat;      // 2 * n_gen lattice position
+    std::vector<float> gen_pos;        // 2 * n_gen true position (world units)
+    std::vector<int32_t> gen_aux;      // segment index / source index / polygon vertex index
+    std::vector<int32_t> gen_wedge;    // 4 * n_gen obstacle wedge (start xy, end xy), CCW
+    // segments on the lattice
+    std::vector<int32_t> seg_lat;      // 4 * n_segs
+};
+
+// Builds a HostScene from the C descriptor; on failure returns a status and
+// an explanatory message.
+spm_status prepare_scene(const spm_scene_desc &d, HostScene &hs, std::string &err);
+// Re-snaps and re-validates sources of an existing HostScene.
+spm_status update_sources(HostScene &hs, const float *pts, const float *segs,
+                          std::string &err);
+
+// Device pointers of one scene (all allocated at creation).
+struct DevScene {
+    int32_t Wx, Wy, Nx, Ny, S;
+    float hx, hy;                      // pixel size in world units
+    int32_t n_poly, n_gen, n_src, n_vert, n_seg;
+    // polygons
+    const int32_t *poly_off;
+    const int2 *poly_v;
+    const int4 *poly_box;
+    int32_t bin_x0, bin_y0, bin_size, bin_nx, bin_ny;
+    const int32_t *bin_start, *bin_items;
+    // generators (static part)
+    const int32_t *gen_kind;
+    const int2 *gen_lat;
+    const float2 *gen_pos;
+    const int32_t *gen_aux;
+    const int4 *gen_wedge;
+    const int4 *seg_lat;               // A.x A.y B.x B.y lattice
+    const float4 *seg_pos;             // true coordinates
+    // vertex phase
+    uint32_t *vis_bits;                // n_vert rows x vis_words
+    int32_t vis_words;
+    int32_t *in_start;                 // n_vert + 1 (by target vertex)
+    int32_t *in_src;                   // E
+    double *in_len;                    // E
+    int32_t *out_start;                // n_gen + 1 (by source generator)
+    int32_t *out_dst;                  // E
+    int32_t *out_fill;                 // n_gen cursors
+    int64_t edge_cap;
+    double *cost[2];                   // Jacobi double buffer
+    int32_t *par[2];
+    int32_t *frontier[2];              // frontier lists
+    int32_t *counters;                 // [0] frontier sizes..., see kernels
+    // finalised generator table (read by the pixel kernel)
+    float *gen_costf;                  // n_gen (inf when unreached)
+    double *gen_cost;                  // n_gen
+    int32_t *gen_par;                  // n_gen
+    int4 *gen_cone;                    // c1.x c1.y c2.x c2.y (lattice directions)
+    int32_t *gen_ctype;                // ConeType
+    uint32_t *status;                  // latched status bits
+    int32_t *stats;                    // [0] rounds, [1] edges
+    // tiles
+    int32_t tiles_x, tiles_y;
+    // differentiable form
+    float *agent_accum;                // scratch for deterministic reductions
+    const int32_t *agents;
+    int32_t n_agents;
+};
+
+// Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
+void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
+void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent);
+int count_kernel_launches_vertex();
+int count_kernel_launches_pixel();
+
+}  // namespace spm

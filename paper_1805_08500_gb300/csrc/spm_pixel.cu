@@ -1,0 +1,416 @@
+// spm_pixel.cu -- pixel phase of the shortest-path map.
+//
+// arxiv 1805.08500 Sec. 3.1, Procedure 3 ("Cone"): a pixel that sees generator
+// g takes cost(g) + |p - g| when that is smaller than what it holds; Sec. 4:
+// a segment interior reaches p through its perpendicular foot. Instead of one
+// full-screen pass per generator, one CTA owns a 32 x 32 pixel tile and
+// gathers only the generators that can win somewhere in it:
+//   * cull: finite cost, shadow cone (or perpendicular strip) meets the tile,
+//     lower bound lb = cost + dist(g, tile) below the tile's current worst;
+//   * order: candidates sorted by lb; the CTA stops once every pixel's best is
+//     <= lb (no later candidate can win);
+//   * visibility: for each candidate still useful to some pixel, the CTA
+//     builds the list of polygons that may cross the hull of (tile, g) from
+//     the polygon bins, then every pixel runs the exact integer separating-axis
+//     test against that list;
+//   * argmin: a per-pixel u64 key (FP32 distance bits << 32 | generator id),
+//     so "smaller distance, then smaller id" is one unsigned compare;
+//   * output: each thread owns 4 consecutive pixels of a row and writes them
+//     with one 16-byte store per plane (dist, parent).
+#include <cuda_runtime.h>
+
+#include "spm_device.cuh"
+#include "spm_internal.h"
+
+namespace spm {
+namespace {
+
+constexpr int T = kTile;
+constexpr int NT = kPixelThreads;
+constexpr unsigned long long kUnset = 0x7F800000FFFFFFFFull;  // (+inf, id max)
+
+struct PixSmem {
+    int cand_id[kCandCap];
+    float cand_lb[kCandCap];
+    unsigned dedup[kDedupBits / 32];
+    int2 blk_v[kBlockCap][kMaxPolyVerts];
+    int blk_oA[kBlockCap][kMaxPolyVerts];
+    int blk_oB[kBlockCap][kMaxPolyVerts];
+    unsigned blk_mask[kBlockCap];
+    int blk_m[kBlockCap];
+    int n_cand, n_block, overflow;
+    float tile_ub;
+};
+
+__device__ __forceinline__ float key_dist(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
+
+// Lower bound of cost(g) + distance from g to any pixel of the tile, or -1 if
+// g cannot be valid anywhere in the tile.
+__device__ float tile_lower_bound(const DevScene &ds, int g, int4 box, float4 fbox) {
+    const float cf = ds.gen_costf[g];
+    if (!(cf < INFINITY)) return -1.f;
+    const int kind = ds.gen_kind[g];
+    if (kind == kSegI) {
+        const int s = ds.gen_aux[g];
+        const int4 L = ds.seg_lat[s];
+        const long long ux = L.z - L.x, uy = L.w - L.y, den = ux * ux + uy * uy;
+        bool all_lo = true, all_hi = true;
+        const int cx[4] = {box.x, box.z, box.x, box.z}, cy[4] = {box.y, box.y, box.w, box.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            long long num = (cx[k] - L.x) * ux + (cy[k] - L.y) * uy;
+            all_lo &= num <= 0;
+            all_hi &= num >= den;
+        }
+        if (all_lo || all_hi) return -1.f;
+        const float4 F = ds.seg_pos[s];
+        const float fx = F.z - F.x, fy = F.w - F.y, il = rsqrtf(fx * fx + fy * fy);
+        const float qx[4] = {fbox.x, fbox.z, fbox.x, fbox.z}, qy[4] = {fbox.y, fbox.y, fbox.w, fbox.w};
+        float mn = INFINITY;
+        bool pos = false, neg = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float sd = (fx * (qy[k] - F.y) - fy * (qx[k] - F.x)) * il;
+            pos |= sd > 0.f;
+            neg |= sd < 0.f;
+            mn = fminf(mn, fabsf(sd));
+        }
+        return (pos && neg) ? 0.f : mn * 0.999999f;
+    }
+    if (kind == kVert) {
+        const int ct = ds.gen_ctype[g];
+        if (ct == kConeEmpty) return -1.f;
+        const int4 c = ds.gen_cone[g];
+        const int2 v = ds.gen_lat[g];
+        const int cx[4] = {box.x, box.z, box.x, box.z}, cy[4] = {box.y, box.y, box.w, box.w};
+        bool out1 = true, out2 = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int wx = cx[k] - v.x, wy = cy[k] - v.y;
+            out1 &= cross32(c.x, c.y, wx, wy) < 0;
+            out2 &= cross32(wx, wy, c.z, c.w) < 0;
+        }
+        if (out1 || out2) return -1.f;
+    }
+    const float2 p = ds.gen_pos[g];
+    const float dx = fmaxf(fmaxf(fbox.x - p.x, p.x - fbox.z), 0.f);
+    const float dy = fmaxf(fmaxf(fbox.y - p.y, p.y - fbox.w), 0.f);
+    return (cf + sqrtf(dx * dx + dy * dy)) * 0.999999f;
+}
+
+// Bitonic sort of (lb, id) pairs, n padded to a power of two with +inf.
+__device__ void sort_candidates(PixSmem &sm, int n) {
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = n + threadIdx.x; i < P; i += NT) {
+        sm.cand_lb[i] = INFINITY;
+        sm.cand_id[i] = 0x7fffffff;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += NT) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const float a = sm.cand_lb[i], b = sm.cand_lb[ixj];
+                    const int ia = sm.cand_id[i], ib = sm.cand_id[ixj];
+                    const bool gt = (a > b) || (a == b && ia > ib);
+                    if (gt == up) {
+                        sm.cand_lb[i] = b; sm.cand_lb[ixj] = a;
+                        sm.cand_id[i] = ib; sm.cand_id[ixj] = ia;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Column-wise conservative bin enumeration for the thick segment c->t
+// (lattice units, radius r), one column per thread; each polygon found is
+// filtered against the thick segment and appended (deduplicated) to smem.
+__device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float cy, float tx, float ty,
+                               float r, int kind, int2 tl, int4 seg) {
+    const float bs = (float)ds.bin_size, x0 = (float)ds.bin_x0, y0 = (float)ds.bin_y0;
+    const float m = r + 1.0f;
+    auto bin_of = [&](float v, float o, int n) {
+        int b = (int)floorf((v - o) / bs);
+        return b < 0 ? 0 : (b >= n ? n - 1 : b);
+    };
+    const int c0 = bin_of(fminf(cx, tx) - m, x0, ds.bin_nx), c1 = bin_of(fmaxf(cx, tx) + m, x0, ds.bin_nx);
+    const float dx = tx - cx, dy = ty - cy;
+    const bool dedup = ds.n_poly <= kDedupBits;
+    for (int col = c0 + (int)threadIdx.x; col <= c1; col += NT) {
+        float ylo, yhi;
+        if (fabsf(dx) < 0.5f) {
+            ylo = fminf(cy, ty);
+            yhi = fmaxf(cy, ty);
+        } else {
+            float a = x0 + col * bs - m, b = x0 + (col + 1) * bs + m;
+            float t0 = (a - cx) / dx, t1 = (b - cx) / dx;
+            float tlo = fmaxf(0.f, fminf(t0, t1)), thi = fminf(1.f, fmaxf(t0, t1));
+            if (tlo > thi) { tlo = 0.f; thi = 1.f; }
+            float ya = cy + tlo * dy, yb = cy + thi * dy;
+            ylo = fminf(ya, yb);
+            yhi = fmaxf(ya, yb);
+        }
+        const int r0 = bin_of(ylo - m, y0, ds.bin_ny), r1 = bin_of(yhi + m, y0, ds.bin_ny);
+        for (int row = r0; row <= r1; ++row) {
+            const int bin = row * ds.bin_nx + col;
+            for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
+                const int k = ds.bin_items[it];
+                if (dedup) {
+                    const unsigned bit = 1u << (k & 31);
+                    if (atomicOr(&sm.dedup[k >> 5], bit) & bit) continue;
+                }
+                if (!seg_near_box(cx, cy, tx, ty, r, ds.poly_box[k])) continue;
+                const int slot = atomicAdd(&sm.n_block, 1);
+                if (slot >= kBlockCap) {
+                    sm.overflow = 1;
+                    continue;
+                }
+                const int b = ds.poly_off[k], nv = ds.poly_off[k + 1] - b;
+                sm.blk_m[slot] = nv;
+                for (int i = 0; i < nv; ++i) sm.blk_v[slot][i] = ds.poly_v[b + i];
+                if (kind == kSegI) {
+                    for (int i = 0; i < nv; ++i) {
+                        const int2 a = sm.blk_v[slot][i], bb = sm.blk_v[slot][i + 1 == nv ? 0 : i + 1];
+                        sm.blk_oA[slot][i] = orient32(a.x, a.y, bb.x, bb.y, seg.x, seg.y);
+                        sm.blk_oB[slot][i] = orient32(a.x, a.y, bb.x, bb.y, seg.z, seg.w);
+                    }
+                } else {
+                    sm.blk_mask[slot] = edge_mask(sm.blk_v[slot], nv, tl.x, tl.y);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ dist,
+                                               int32_t *__restrict__ parent) {
+    __shared__ PixSmem sm;
+    const int tile = blockIdx.x;
+    const int i0 = (tile % ds.tiles_x) * T, j0 = (tile / ds.tiles_x) * T;
+    const int row = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
+    const int j = j0 + row;
+    const int pitch_x = ds.S * ds.Wx / ds.Nx, pitch_y = ds.S * ds.Wy / ds.Ny;
+    const int py = pitch_y * j + pitch_y / 2;
+    const float fy = ((float)j + 0.5f) * ds.hy;
+    int px[4];
+    float fx[4];
+    unsigned long long key[4];
+    unsigned live = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = i0 + c4 + k;
+        px[k] = pitch_x * i + pitch_x / 2;
+        fx[k] = ((float)i + 0.5f) * ds.hx;
+        key[k] = kUnset;
+        if (i < ds.Nx && j < ds.Ny) live |= 1u << k;
+    }
+    // free space: not in the open interior of any polygon
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!(live & (1u << k))) continue;
+        int bx = (px[k] - ds.bin_x0) / ds.bin_size, by = (py - ds.bin_y0) / ds.bin_size;
+        if (bx < 0 || by < 0 || bx >= ds.bin_nx || by >= ds.bin_ny) continue;
+        const int bin = by * ds.bin_nx + bx;
+        for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
+            const int q = ds.bin_items[it];
+            const int4 b4 = ds.poly_box[q];
+            if (px[k] <= b4.x || px[k] >= b4.z || py <= b4.y || py >= b4.w) continue;
+            const int b = ds.poly_off[q], m = ds.poly_off[q + 1] - b;
+            bool inside = true;
+            for (int e = 0; e < m && inside; ++e) {
+                const int2 a = ds.poly_v[b + e], c = ds.poly_v[b + (e + 1 == m ? 0 : e + 1)];
+                inside = orient32(a.x, a.y, c.x, c.y, px[k], py) > 0;
+            }
+            if (inside) {
+                live &= ~(1u << k);
+                break;
+            }
+        }
+    }
+    const int ni = min(T, ds.Nx - i0), nj = min(T, ds.Ny - j0);
+    const int4 box = make_int4(pitch_x * i0 + pitch_x / 2, pitch_y * j0 + pitch_y / 2,
+                               pitch_x * (i0 + ni - 1) + pitch_x / 2, pitch_y * (j0 + nj - 1) + pitch_y / 2);
+    const float4 fbox = make_float4(((float)i0 + 0.5f) * ds.hx, ((float)j0 + 0.5f) * ds.hy,
+                                    ((float)(i0 + ni - 1) + 0.5f) * ds.hx, ((float)(j0 + nj - 1) + 0.5f) * ds.hy);
+    const float bcx = 0.5f * ((float)box.x + (float)box.z), bcy = 0.5f * ((float)box.y + (float)box.w);
+    const float brad = 0.5f * sqrtf((float)(box.z - box.x) * (float)(box.z - box.x) +
+                                    (float)(box.w - box.y) * (float)(box.w - box.y)) + 1.0f;
+    if (threadIdx.x == 0) {
+        sm.n_cand = 0;
+        sm.tile_ub = INFINITY;
+    }
+    __syncthreads();
+    const bool any_live = __syncthreads_or(live != 0);
+    for (int g0 = 0; any_live && g0 < ds.n_gen; g0 += NT) {
+        const int g = g0 + threadIdx.x;
+        float lb = -1.f;
+        if (g < ds.n_gen) lb = tile_lower_bound(ds, g, box, fbox);
+        const bool keep = lb >= 0.f && lb <= sm.tile_ub;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(&sm.n_cand, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const int slot = base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+            sm.cand_id[slot] = g;
+            sm.cand_lb[slot] = lb;
+        }
+        __syncthreads();
+        const int nc = sm.n_cand;
+        const bool last = g0 + NT >= ds.n_gen;
+        if (nc > kCandCap - NT || (last && nc > 0)) {
+            sort_candidates(sm, nc);
+            for (int c = 0; c < nc; ++c) {
+                const float lb_c = sm.cand_lb[c];
+                const int gc = sm.cand_id[c];
+                bool act = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) act |= (live >> k & 1u) && key_dist(key[k]) > lb_c;
+                if (!__syncthreads_or(act)) break;
+                const int kind = ds.gen_kind[gc];
+                const float cf = ds.gen_costf[gc];
+                const int2 gl = ds.gen_lat[gc];
+                const float2 gp = ds.gen_pos[gc];
+                int ct = kConeNone;
+                int4 cone = make_int4(0, 0, 0, 0);
+                int4 seg = make_int4(0, 0, 0, 0);
+                float4 segf = make_float4(0.f, 0.f, 0.f, 0.f);
+                long long den = 0;
+                float seg_il = 0.f;
+                if (kind == kVert) {
+                    ct = ds.gen_ctype[gc];
+                    cone = ds.gen_cone[gc];
+                } else if (kind == kSegI) {
+                    seg = ds.seg_lat[ds.gen_aux[gc]];
+                    segf = ds.seg_pos[ds.gen_aux[gc]];
+                    const long long ux = seg.z - seg.x, uy = seg.w - seg.y;
+                    den = ux * ux + uy * uy;
+                    const float fux = segf.z - segf.x, fuy = segf.w - segf.y;
+                    seg_il = 1.0f / sqrtf(fux * fux + fuy * fuy);
+                }
+                unsigned need = 0;
+                unsigned long long nk[4];
+                long long num[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    nk[k] = kUnset;
+                    num[k] = 0;
+                    if (!((live >> k) & 1u) || !(key_dist(key[k]) > lb_c)) continue;
+                    float d;
+                    if (kind == kSegI) {
+                        const long long nm = (long long)(px[k] - seg.x) * (seg.z - seg.x) +
+                                             (long long)(py - seg.y) * (seg.w - seg.y);
+                        if (!(nm > 0 && nm < den)) continue;
+                        num[k] = nm;
+                        d = fabsf((segf.z - segf.x) * (fy - segf.y) - (segf.w - segf.y) * (fx[k] - segf.x)) * seg_il;
+                    } else {
+                        if (kind == kVert && !in_cone(ct, cone, px[k] - gl.x, py - gl.y)) continue;
+                        const float ddx = fx[k] - gp.x, ddy = fy - gp.y;
+                        d = cf + sqrtf(ddx * ddx + ddy * ddy);
+                    }
+                    const unsigned long long kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)gc;
+                    if (kk < key[k]) {
+                        nk[k] = kk;
+                        need |= 1u << k;
+                    }
+                }
+                if (!__syncthreads_or(need != 0)) continue;
+                // blockers of the hull of (tile, target)
+                float tx, ty;
+                if (kind == kSegI) {
+                    const float ux = (float)(seg.z - seg.x), uy = (float)(seg.w - seg.y);
+                    const float t = ((bcx - seg.x) * ux + (bcy - seg.y) * uy) / (ux * ux + uy * uy);
+                    tx = seg.x + t * ux;
+                    ty = seg.y + t * uy;
+                } else {
+                    tx = (float)gl.x;
+                    ty = (float)gl.y;
+                }
+                for (int w = threadIdx.x; w < kDedupBits / 32; w += NT) sm.dedup[w] = 0u;
+                if (threadIdx.x == 0) {
+                    sm.n_block = 0;
+                    sm.overflow = 0;
+                }
+                __syncthreads();
+                build_blockers(ds, sm, bcx, bcy, tx, ty, brad, kind, gl, seg);
+                __syncthreads();
+                const int nb = min(sm.n_block, kBlockCap);
+                const bool ovf = sm.overflow != 0;
+                const int nx = -(seg.w - seg.y), ny = seg.z - seg.x;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!((need >> k) & 1u)) continue;
+                    bool vis;
+                    if (ovf) {
+                        vis = kind == kSegI ? visible_foot(ds, ds.gen_aux[gc], px[k], py, num[k], den)
+                                            : visible_points(ds, px[k], py, gl.x, gl.y);
+                    } else if (kind == kSegI) {
+                        vis = true;
+                        if (cross32(seg.z - seg.x, seg.w - seg.y, px[k] - seg.x, py - seg.y) != 0)
+                            for (int b = 0; b < nb && vis; ++b)
+                                vis = !poly_blocks_foot(sm.blk_v[b], sm.blk_m[b], sm.blk_oA[b], sm.blk_oB[b],
+                                                        px[k], py, num[k], den, nx, ny);
+                    } else {
+                        vis = true;
+                        if (px[k] != gl.x || py != gl.y)
+                            for (int b = 0; b < nb && vis; ++b)
+                                vis = !poly_blocks(sm.blk_v[b], sm.blk_m[b], px[k], py, gl.x, gl.y, sm.blk_mask[b]);
+                    }
+                    if (vis) key[k] = nk[k];
+                }
+                __syncthreads();
+            }
+            // tile upper bound for candidate pruning: worst best over live pixels
+            float worst = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((live >> k) & 1u) worst = fmaxf(worst, key_dist(key[k]));
+            for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                sm.n_cand = 0;
+                sm.tile_ub = 0.f;
+            }
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) atomicMax((int *)&sm.tile_ub, __float_as_int(worst));
+            __syncthreads();
+        }
+    }
+
+    if (j < ds.Ny) {
+        float od[4];
+        int op[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = ((live >> k) & 1u) && key[k] != kUnset;
+            od[k] = ok ? key_dist(key[k]) : INFINITY;
+            op[k] = ok ? (int)(unsigned)(key[k] & 0xffffffffu) : -1;
+        }
+        const size_t base = (size_t)j * ds.Nx + i0 + c4;
+        if ((ds.Nx & 3) == 0 && i0 + c4 + 3 < ds.Nx) {
+            *reinterpret_cast<float4 *>(dist + base) = make_float4(od[0], od[1], od[2], od[3]);
+            *reinterpret_cast<int4 *>(parent + base) = make_int4(op[0], op[1], op[2], op[3]);
+        } else {
+            for (int k = 0; k < 4; ++k)
+                if (i0 + c4 + k < ds.Nx) {
+                    dist[base + k] = od[k];
+                    parent[base + k] = op[k];
+                }
+        }
+    }
+}
+
+}  // namespace
+
+void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent) {
+    const int tiles = ds.tiles_x * ds.tiles_y;
+    k_pixels<<<tiles, NT, 0, st>>>(ds, dist, parent);
+}
+
+int count_kernel_launches_pixel() { return 1; }
+
+}  // namespace spm

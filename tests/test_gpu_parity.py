@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Tolerances (stated for every comparison):
+  * finite/infinite pattern identical (free, reached pixels);
+  * FP32 distance within 1e-5 relative of the FP64 oracle, relative to
+    max(oracle value, pixel size);
+  * parent ids identical except at near ties, where the oracle's best and
+    second-best valid generators differ by <= 1e-4 * scene diameter (world
+    diagonal); such exempt mismatches must stay <= 0.1% of free pixels (on
+    grids under 256^2 pixels, where one pixel is already > 0.002%, at most 8
+    pixels: exact ties on tangent rays through lattice points are decided by
+    FP32 rounding on the GPU and FP64 rounding in the oracle);
+  * vertex-generator costs: identical FP64 values (both sides run the same
+    correctly rounded operations), parents identical.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import scenegen as sg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+TIE_FRAC = 1e-4
+MAX_TIE_SHARE = 1e-3
+
+
+@pytest.fixture(scope="module")
+def spm():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1805_08500_gb300 as m
+    m.load_library()
+    return m
+
+
+def gpu_field(spm, scene):
+    s = spm.Scene(scene)
+    d, p = s.compute()
+    s.sync()
+    return s, d.cpu().numpy(), p.cpu().numpy()
+
+
+def check_parity(scene, gd, gp, rd, rp, rd2, where=""):
+    W = math.hypot(*scene.world)
+    h = min(scene.world[0] / scene.grid[0], scene.world[1] / scene.grid[1])
+    fin = np.isfinite(rd)
+    bad = np.isfinite(gd) != fin
+    assert not bad.any(), f"{where}: {bad.sum()} pixels differ in reached/free status"
+    rel = np.abs(gd[fin].astype(np.float64) - rd[fin]) / np.maximum(rd[fin], h)
+    assert rel.size == 0 or rel.max() <= REL_TOL, f"{where}: max rel err {rel.max():.3g}"
+    with np.errstate(invalid="ignore"):
+        tie = np.where(np.isfinite(rd2), rd2 - rd, np.inf) <= TIE_FRAC * W
+    mism = fin & (gp != rp)
+    hard = mism & ~tie
+    assert not hard.any(), (f"{where}: {hard.sum()} parent mismatches outside near ties, "
+                            f"first at {np.argwhere(hard)[:3].tolist()}")
+    allowed = MAX_TIE_SHARE * fin.sum() if gd.size >= 65536 else max(8, MAX_TIE_SHARE * fin.sum())
+    assert mism.sum() <= allowed, f"{where}: {mism.sum()} near-tie mismatches"
+    return int(mism.sum())
+
+
+def full_parity(spm, oracle_mod, scene, where):
+    s, gd, gp = gpu_field(spm, scene)
+    o = oracle_mod.Oracle(scene)
+    rd, rp, rd2, _ = o.field()
+    check_parity(scene, gd, gp, rd, rp, rd2, where)
+    return s, o, gd, gp
+
+
+def sampled_parity(spm, oracle_mod, scene, n_samples, where, window=None, seed=0):
+    s, gd, gp = gpu_field(spm, scene)
+    o = oracle_mod.Oracle(scene)
+    Nx, Ny = scene.grid
+    rng = np.random.default_rng(seed)
+    ij = np.stack([rng.integers(0, Nx, n_samples), rng.integers(0, Ny, n_samples)], 1)
+    if window is not None:
+        i0, j0, w = window
+        jj, ii = np.mgrid[j0:j0 + w, i0:i0 + w]
+        ij = np.concatenate([ij, np.stack([ii.ravel(), jj.ravel()], 1)])
+    ij = ij.astype(np.int32)
+    rd, rp, rd2, _ = o.pixels(ij)
+    check_parity(scene, gd[ij[:, 1], ij[:, 0]], gp[ij[:, 1], ij[:, 0]], rd, rp, rd2, where)
+    return s, o, gd, gp
+
+
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,n_segs", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 0)])
+def test_tiny_scenes(spm, oracle_mod, seed, n_segs):
+    scene = sg.tiny(seed, W=64, N=64, n_polys=5, n_points=1 + seed % 2, n_segs=n_segs)
+    full_parity(spm, oracle_mod, scene, f"tiny{seed}")
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plain_rects_256(spm, oracle_mod, seed):
+    full_parity(spm, oracle_mod, sg.plain_rects(seed), f"rects{seed}")
+
+
+def test_plain_polys_1024_full(spm, oracle_mod):
+    full_parity(spm, oracle_mod, sg.plain_polys(0), "polys1024")
+
+
+def test_maze_small_full(spm, oracle_mod):
+    full_parity(spm, oracle_mod, sg.maze(1, cells=8, N=512), "maze8")
+
+
+def test_maze_4096_sampled(spm, oracle_mod):
+    scene = sg.maze(0)
+    sampled_parity(spm, oracle_mod, scene, 12000, "maze64", window=(2000, 1000, 64))
+
+
+def test_differentiable_scene_sampled(spm, oracle_mod):
+    scene = sg.differentiable(0, n_agents=10)
+    sampled_parity(spm, oracle_mod, scene, 30000, "diff2048", window=(700, 900, 64))
+
+
+def test_vertex_costs_bit_exact(spm, oracle_mod):
+    for scene in (sg.plain_rects(1), sg.plain_polys(2, n_polys=120, N=256), sg.maze(2, cells=10, N=640)):
+        s = spm.Scene(scene)
+        s.compute()
+        s.sync()
+        kind, lat, cost, par = s.generators()
+        o = oracle_mod.Oracle(scene)
+        assert np.array_equal(kind, o.kind)
+        assert np.array_equal(lat, o.lxy.astype(np.int32))
+        fin = np.isfinite(o.cost)
+        assert np.array_equal(np.isfinite(cost), fin)
+        assert np.array_equal(cost[fin], o.cost[fin])
+        assert np.array_equal(par, o.parent)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_no_obstacles(spm, oracle_mod):
+    scene = sg.empty_scene(W=96, N=96, points=[(10.0, 80.0), (70.0, 20.0)],
+                           segs=[(20.0, 30.0, 60.0, 55.0)])
+    full_parity(spm, oracle_mod, scene, "empty")
+
+
+def test_ragged_nonsquare_grid(spm, oracle_mod):
+    polys = [np.array([(30, 20), (50, 22), (44, 40)]), np.array([(120, 60), (140, 60), (140, 90), (120, 90)])]
+    scene = sg.Scene((200, 140), (100, 70), polys, [(5.0, 5.0), (190.0, 130.0)], [(60.0, 100.0, 100.0, 120.0)])
+    full_parity(spm, oracle_mod, scene, "ragged")
+
+
+def test_single_pixel_and_tiny_grids(spm, oracle_mod):
+    for N in (1, 2, 3, 33):
+        scene = sg.Scene((66, 66), (N, N), [np.array([(20, 20), (40, 20), (40, 40), (20, 40)])],
+                         [(5.0, 60.0)], np.zeros((0, 4)))
+        full_parity(spm, oracle_mod, scene, f"grid{N}")
+
+
+def test_enclosed_unreachable_region(spm, oracle_mod):
+    # four overlapping walls close a box the source cannot enter
+    walls = [np.array([(20, 20), (60, 20), (60, 24), (20, 24)]), np.array([(20, 56), (60, 56), (60, 60), (20, 60)]),
+             np.array([(20, 20), (24, 20), (24, 60), (20, 60)]), np.array([(56, 20), (60, 20), (60, 60), (56, 60)])]
+    scene = sg.Scene((80, 80), (80, 80), walls, [(5.0, 5.0)], np.zeros((0, 4)))
+    s, o, gd, gp = full_parity(spm, oracle_mod, scene, "enclosed")
+    assert np.isinf(gd[40, 40]) and gp[40, 40] == -1
+
+
+def test_max_polygon_vertices_and_lattice_span(spm, oracle_mod):
+    # a 16-gon and a world at the lattice limit (span 32767 -> S = 1)
+    ang = np.linspace(0, 2 * np.pi, 16, endpoint=False)
+    poly16 = np.stack([np.round(16000 + 3000 * np.cos(ang)), np.round(16000 + 3000 * np.sin(ang))], 1).astype(int)
+    scene = sg.Scene((32766, 32766), (381, 381), [poly16], [(2000.0, 30000.0)], [(28000.0, 2000.0, 30000.0, 6000.0)])
+    sampled_parity(spm, oracle_mod, scene, 20000, "span32766")
+
+
+def test_source_touching_distance_and_many_sources(spm, oracle_mod):
+    rng = np.random.default_rng(7)
+    sq = np.array([(40, 40), (80, 40), (80, 80), (40, 80)])
+    pts = [(39.0, 60.0), (81.0, 41.0)] + [tuple(map(float, rng.integers(90, 127, 2))) for _ in range(30)]
+    scene = sg.Scene((128, 128), (128, 128), [sq], pts, np.zeros((0, 4)))
+    full_parity(spm, oracle_mod, scene, "manysrc")
+
+
+def test_repeat_is_deterministic(spm):
+    s = spm.Scene(sg.plain_polys(5, n_polys=100, N=512))
+    d1, p1 = s.compute()
+    d1, p1 = d1.clone(), p1.clone()
+    d2, p2 = s.compute()
+    s.sync()
+    assert torch.equal(d1, d2) and torch.equal(p1, p2)
+
+
+def test_update_sources(spm, oracle_mod):
+    scene = sg.plain_polys(6, n_polys=60, N=256, n_points=2, n_segs=1)
+    s = spm.Scene(scene)
+    s.compute()
+    moved = sg.Scene(scene.world, scene.grid, scene.polys, scene.points.copy(), scene.segs.copy())
+    moved.points[0] += (3.0, -2.0)
+    moved.segs[0] += (1.0, 1.0, 1.0, 1.0)
+    try:
+        oracle_mod.Oracle(moved)
+    except oracle_mod.OracleError:
+        pytest.skip("moved source landed in an obstacle")
+    s.update_sources(moved.points, moved.segs)
+    d, p = s.compute()
+    s.sync()
+    rd, rp, rd2, _ = oracle_mod.Oracle(moved).field()
+    check_parity(moved, d.cpu().numpy(), p.cpu().numpy(), rd, rp, rd2, "moved")
+
+
+# ---------------------------------------------------------------------------
+# queries
+# ---------------------------------------------------------------------------
+
+def test_query_and_extract_path(spm, oracle_mod):
+    scene = sg.plain_polys(7, n_polys=80, N=256, n_segs=2)
+    s, gd, gp = gpu_field(spm, scene)
+    rng = np.random.default_rng(3)
+    h = scene.world[0] / scene.grid[0]
+    for _ in range(200):
+        x, y = rng.uniform(0, scene.world[0]), rng.uniform(0, scene.world[1])
+        i, j = int(x // h), int(y // h)
+        par, dist = s.query_parent(x, y)
+        assert par == gp[j, i]
+        if par < 0:
+            continue
+        path = s.extract_path((i + 0.5) * h, (j + 0.5) * h)
+        L = float(np.sum(np.hypot(*np.diff(path.astype(np.float64), axis=0).T)))
+        assert abs(L - gd[j, i]) <= 1e-4 * max(gd[j, i], h)
+
+
+# ---------------------------------------------------------------------------
+# differentiable form
+# ---------------------------------------------------------------------------
+
+def test_agent_gradient_matches_oracle(spm, oracle_mod):
+    scene = sg.differentiable(1, W=1024, N=256, n_polys=20, n_agents=3000)
+    o = oracle_mod.Oracle(scene)
+    d, _, _, _ = o.pixels(scene.agents)
+    agents = scene.agents[np.isfinite(d)]
+    loss_ref, gp_ref, gs_ref = o.agent_loss_and_grad(agents)
+    s = spm.Scene(scene)
+    pts = torch.tensor(scene.points, dtype=torch.float32, requires_grad=True)
+    segs = torch.tensor(scene.segs, dtype=torch.float32, requires_grad=True)
+    ag = torch.tensor(agents, dtype=torch.int32, device="cuda")
+    loss = spm.agent_loss(s, pts, segs, ag)
+    loss.backward()
+    assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+    np.testing.assert_allclose(pts.grad.cpu().numpy(), gp_ref, atol=1e-4)
+    np.testing.assert_allclose(segs.grad.cpu().numpy(), gs_ref, atol=1e-4)
