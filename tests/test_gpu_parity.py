@@ -6,10 +6,12 @@ Tolerances (stated for every comparison):
     max(oracle value, pixel size);
   * parent ids identical except at near ties, where the oracle's best and
     second-best valid generators differ by <= 1e-4 * scene diameter (world
-    diagonal); such exempt mismatches must stay <= 0.1% of free pixels (on
-    grids under 256^2 pixels, where one pixel is already > 0.002%, at most 8
-    pixels: exact ties on tangent rays through lattice points are decided by
-    FP32 rounding on the GPU and FP64 rounding in the oracle);
+    diagonal); such exempt mismatches must stay <= 0.1% of free pixels (at
+    most 8 pixels on grids under 256^2);
+  * exact ties (best and second-best within 1e-9 relative in FP64, e.g. a
+    pixel collinear with two obstacle vertices of one path) have several
+    correct labels: there the GPU label must be the oracle's tied runner-up,
+    and such pixels are checked for validity instead of being counted;
   * vertex-generator costs: identical FP64 values (both sides run the same
     correctly rounded operations), parents identical.
 """
@@ -44,7 +46,7 @@ def gpu_field(spm, scene):
     return s, d.cpu().numpy(), p.cpu().numpy()
 
 
-def check_parity(scene, gd, gp, rd, rp, rd2, where=""):
+def check_parity(scene, gd, gp, rd, rp, rd2, where="", rp2=None):
     W = math.hypot(*scene.world)
     h = min(scene.world[0] / scene.grid[0], scene.world[1] / scene.grid[1])
     fin = np.isfinite(rd)
@@ -55,6 +57,11 @@ def check_parity(scene, gd, gp, rd, rp, rd2, where=""):
     with np.errstate(invalid="ignore"):
         tie = np.where(np.isfinite(rd2), rd2 - rd, np.inf) <= TIE_FRAC * W
     mism = fin & (gp != rp)
+    if rp2 is not None:
+        with np.errstate(invalid="ignore"):
+            exact = np.where(np.isfinite(rd2), rd2 - rd, np.inf) <= 1e-9 * np.maximum(rd, 1.0)
+        alt = mism & exact & (gp == rp2)
+        mism = mism & ~alt
     hard = mism & ~tie
     assert not hard.any(), (f"{where}: {hard.sum()} parent mismatches outside near ties, "
                             f"first at {np.argwhere(hard)[:3].tolist()}")
@@ -66,8 +73,8 @@ def check_parity(scene, gd, gp, rd, rp, rd2, where=""):
 def full_parity(spm, oracle_mod, scene, where):
     s, gd, gp = gpu_field(spm, scene)
     o = oracle_mod.Oracle(scene)
-    rd, rp, rd2, _ = o.field()
-    check_parity(scene, gd, gp, rd, rp, rd2, where)
+    rd, rp, rd2, rp2 = o.field()
+    check_parity(scene, gd, gp, rd, rp, rd2, where, rp2)
     return s, o, gd, gp
 
 
@@ -82,8 +89,8 @@ def sampled_parity(spm, oracle_mod, scene, n_samples, where, window=None, seed=0
         jj, ii = np.mgrid[j0:j0 + w, i0:i0 + w]
         ij = np.concatenate([ij, np.stack([ii.ravel(), jj.ravel()], 1)])
     ij = ij.astype(np.int32)
-    rd, rp, rd2, _ = o.pixels(ij)
-    check_parity(scene, gd[ij[:, 1], ij[:, 0]], gp[ij[:, 1], ij[:, 0]], rd, rp, rd2, where)
+    rd, rp, rd2, rp2 = o.pixels(ij)
+    check_parity(scene, gd[ij[:, 1], ij[:, 0]], gp[ij[:, 1], ij[:, 0]], rd, rp, rd2, where, rp2)
     return s, o, gd, gp
 
 
@@ -204,8 +211,8 @@ def test_update_sources(spm, oracle_mod):
     s.update_sources(moved.points, moved.segs)
     d, p = s.compute()
     s.sync()
-    rd, rp, rd2, _ = oracle_mod.Oracle(moved).field()
-    check_parity(moved, d.cpu().numpy(), p.cpu().numpy(), rd, rp, rd2, "moved")
+    rd, rp, rd2, rp2 = oracle_mod.Oracle(moved).field()
+    check_parity(moved, d.cpu().numpy(), p.cpu().numpy(), rd, rp, rd2, "moved", rp2)
 
 
 # ---------------------------------------------------------------------------
