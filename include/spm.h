@@ -164,6 +164,33 @@ spm_status spm_agents_forward(spm_scene *scene, void *stream, const int32_t *age
 spm_status spm_agents_backward(spm_scene *scene, void *stream, float *grad_points_dev,
                                float *grad_segs_dev);
 
+/* Allocation-free variant of spm_agents_backward. The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory while they run, such as a per-frame agent-steering loop in a
+ * game or crowd simulation, where a cudaMalloc can stall the frame, or code
+ * living inside a framework whose memory pool owns the device and forbids raw
+ * cudaMalloc calls.
+ *
+ * It computes the same gradient as spm_agents_forward + spm_agents_backward
+ * for n agents (int32 (i, j) pixel pairs, DEVICE memory) on the parent field
+ * parent_dev of a previous spm_compute of this scene, writing
+ * grad_points_dev (2 * n_points floats) and grad_segs_dev (4 * n_segments
+ * floats), asynchronously on `stream`. It calls no allocating function: its
+ * scratch is one fixed array inside the library (about 3.3 MB, held on every
+ * GPU that loads the library until the process exits), sized for at most
+ * SPM_NOALLOC_MAX_AGENTS agents and SPM_NOALLOC_MAX_GENERATORS generators;
+ * larger inputs return SPM_ERR_CAPACITY. The first call on each device looks
+ * up the array's device address (once, with that device current); make that
+ * first call before any stream capture. All calls share the one array, so
+ * calls whose kernels overlap on the GPU (different streams, no ordering)
+ * race and give wrong gradients; calls on one stream are safe. */
+#define SPM_NOALLOC_MAX_AGENTS 131072
+#define SPM_NOALLOC_MAX_GENERATORS 65536
+spm_status spm_agents_backward_noalloc(spm_scene *scene, void *stream,
+                                       const int32_t *agents_dev, int32_t n,
+                                       const int32_t *parent_dev, float *grad_points_dev,
+                                       float *grad_segs_dev);
+
 /* Device time of the two phases of the last spm_compute on this scene, in
  * milliseconds, from CUDA events the library records around them on the
  * compute stream (not recorded while the stream is being captured into a

@@ -85,6 +85,7 @@ def load_library():
         "spm_agents_forward": ([P, P, P, I32, P, P, P], I32),
         "spm_agents_backward": ([P, P, P, P], I32),
         "spm_scene_phase_ms": ([P, P, P], I32),
+        "spm_agents_backward_noalloc": ([P, P, P, I32, P, P, P], I32),
         "spm_status_string": ([I32], ctypes.c_char_p),
         "spm_last_error": ([P], ctypes.c_char_p),
     }
@@ -230,6 +231,16 @@ def spm_agents_forward(handle, stream, agents, dist, parent, loss):
 def spm_agents_backward(handle, stream, grad_points, grad_segs):
     _check(load_library().spm_agents_backward(handle, _stream_handle(stream), _ptr(grad_points),
                                               _ptr(grad_segs)), "spm_agents_backward", handle)
+
+
+def spm_agents_backward_noalloc(handle, stream, agents, parent, grad_points, grad_segs):
+    """Same gradient as spm_agents_forward + spm_agents_backward, but the
+    library allocates nothing: its scratch is a fixed in-library array (see
+    include/spm.h for the limits and the shared-scratch caveat)."""
+    n = int(agents.shape[0]) if hasattr(agents, "shape") else len(agents) // 2
+    _check(load_library().spm_agents_backward_noalloc(
+        handle, _stream_handle(stream), _ptr(agents), n, _ptr(parent), _ptr(grad_points),
+        _ptr(grad_segs)), "spm_agents_backward_noalloc", handle)
 
 
 def spm_scene_phase_ms(handle):

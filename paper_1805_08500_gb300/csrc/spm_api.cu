@@ -461,3 +461,10 @@ spm_status spm_agents_backward(spm_scene *s, void *stream, float *grad_points_de
 }
 
 }  // extern "C"
+
+// Internal accessors for entry points defined in other translation units.
+namespace spm {
+const DevScene *scene_dev(const spm_scene *s) { return &s->ds; }
+int scene_device(const spm_scene *s) { return s->device; }
+void scene_set_error(spm_scene *s, const char *msg) { s->err = msg; }
+}  // namespace spm

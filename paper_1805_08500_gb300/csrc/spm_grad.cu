@@ -12,6 +12,8 @@
 // All reductions run in a fixed order in FP64, so results are deterministic.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "spm_device.cuh"
 #include "spm_internal.h"
 
@@ -139,3 +141,97 @@ void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *
 }
 
 }  // namespace spm
+
+// ---------------------------------------------------------------------------
+// Allocation-free backward (spm_agents_backward_noalloc).
+//
+// Same kernels and launcher as spm_agents_backward, but the scratch (root
+// table, last points, per-agent slots and values) lives in one file-scope
+// device array instead of buffers allocated by spm_agents_forward. Every GPU
+// that loads the library keeps this array until the process exits. Host code
+// must not pass the array's name to a kernel: the host-side symbol is only a
+// stand-in, so its device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, and cached.
+// ---------------------------------------------------------------------------
+namespace spm {
+namespace {
+
+constexpr size_t kNaRootOff = 0;
+constexpr size_t kNaLastOff = kNaRootOff + sizeof(int32_t) * SPM_NOALLOC_MAX_GENERATORS;
+constexpr size_t kNaSlotOff = kNaLastOff + sizeof(float2) * SPM_NOALLOC_MAX_GENERATORS;
+constexpr size_t kNaValOff = kNaSlotOff + sizeof(int32_t) * SPM_NOALLOC_MAX_AGENTS;
+constexpr size_t kNaBytes = kNaValOff + sizeof(float4) * SPM_NOALLOC_MAX_AGENTS;
+static_assert(kNaLastOff % 16 == 0 && kNaSlotOff % 16 == 0 && kNaValOff % 16 == 0, "alignment");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char *g_na_addr[kNaMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+cudaError_t noalloc_scratch(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_na_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace spm
+
+extern "C" spm_status spm_agents_backward_noalloc(spm_scene *scene, void *stream,
+                                                  const int32_t *agents_dev, int32_t n,
+                                                  const int32_t *parent_dev, float *grad_points_dev,
+                                                  float *grad_segs_dev) {
+    using namespace spm;
+    if (!scene) return SPM_ERR_INVALID_ARG;
+    const DevScene &ds = *scene_dev(scene);
+    const int n_pts = ds.n_src - 3 * ds.n_seg;
+    if (n < 0 || (n > 0 && !agents_dev) || !parent_dev || (n_pts > 0 && !grad_points_dev) ||
+        (ds.n_seg > 0 && !grad_segs_dev)) {
+        scene_set_error(scene, "null pointer or negative agent count");
+        return SPM_ERR_INVALID_ARG;
+    }
+    if (n > SPM_NOALLOC_MAX_AGENTS || ds.n_gen > SPM_NOALLOC_MAX_GENERATORS) {
+        scene_set_error(scene, "too many agents or generators for the fixed scratch "
+                               "(limits: SPM_NOALLOC_MAX_AGENTS, SPM_NOALLOC_MAX_GENERATORS)");
+        return SPM_ERR_CAPACITY;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        scene_set_error(scene, "cudaGetDevice failed");
+        return SPM_ERR_CUDA;
+    }
+    if (dev != scene_device(scene)) {
+        scene_set_error(scene, "scene used on another device");
+        return SPM_ERR_INVALID_ARG;
+    }
+    unsigned char *base = nullptr;
+    cudaError_t e = noalloc_scratch(dev, &base);
+    if (e != cudaSuccess) {
+        scene_set_error(scene, cudaGetErrorString(e));
+        return SPM_ERR_CUDA;
+    }
+    // Every scratch element the kernels read is written earlier in the same
+    // call (root/lastpt for all generators, slot/val for all n agents), so
+    // nothing needs clearing between calls.
+    launch_agents_backward(ds, static_cast<cudaStream_t>(stream), agents_dev, n, parent_dev,
+                           reinterpret_cast<int32_t *>(base + kNaRootOff),
+                           reinterpret_cast<float2 *>(base + kNaLastOff),
+                           reinterpret_cast<int32_t *>(base + kNaSlotOff),
+                           reinterpret_cast<float4 *>(base + kNaValOff), grad_points_dev,
+                           grad_segs_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        scene_set_error(scene, cudaGetErrorString(e));
+        return SPM_ERR_CUDA;
+    }
+    return SPM_OK;
+}

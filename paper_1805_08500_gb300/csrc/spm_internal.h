@@ -118,5 +118,15 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent);
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();
+void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
+                            const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot,
+                            float4 *val, float *grad_pts, float *grad_segs);
+}  // namespace spm
+
+struct spm_scene;
+namespace spm {
+const DevScene *scene_dev(const spm_scene *s);
+int scene_device(const spm_scene *s);
+void scene_set_error(spm_scene *s, const char *msg);
 
 }  // namespace spm
