@@ -42,6 +42,8 @@ FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
 def workload(name: str):
     if name == "maze4096":
         return sg.maze(0), "maze 64x64 cells, 4096^2 px, 16384^2 world, 1 segment + 4 points"
+    if name == "maze2048":
+        return sg.maze(0, cells=32, N=2048), "maze 32x32 cells, 2048^2 px, 8192^2 world, 1 segment + 4 points"
     if name == "polys1024":
         return sg.plain_polys(0), "200 convex polygons, 1024^2 px, 4096^2 world, 3 points + 2 segments"
     if name == "rects256":
@@ -171,7 +173,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maze4096",
-                    choices=["maze4096", "polys1024", "rects256", "diff2048"])
+                    choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048"])
     ap.add_argument("--cpu-pixels", type=int, default=200_000,
                     help="oracle pixel sample for the cpu_baseline leg")
     ap.add_argument("--ref-pixels", type=int, default=40_000,

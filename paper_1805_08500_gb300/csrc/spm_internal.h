@@ -15,7 +15,7 @@ namespace spm {
 constexpr int kMaxPolyVerts = 16;    // convex polygon vertex limit
 constexpr int kTile = 32;            // pixel tile side (one CTA per tile)
 constexpr int kPixelThreads = 256;   // 8 threads per tile row, 4 pixels each
-constexpr int kCandCap = 2048;       // candidate generators per batch (smem)
+constexpr int kCandCap = 1024;       // candidate generators per batch (smem)
 constexpr int kBlockCap = 96;        // blocker polygons per chunk (smem)
 constexpr int kDedupBits = 8192;     // polygon-id dedup bitmap (smem)
 constexpr int kMaxRounds = 1 << 20;  // hard cap on vertex-fixpoint rounds

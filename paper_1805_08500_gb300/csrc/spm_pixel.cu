@@ -9,10 +9,14 @@
 //     lower bound lb = cost + dist(g, tile) below the tile's current worst;
 //   * order: candidates sorted by lb; the CTA stops once every pixel's best is
 //     <= lb (no later candidate can win);
+//   * hidden tiles: in lb order, 256 candidates at a time, each thread walks
+//     the polygon bins from the tile toward one candidate and drops it when a
+//     single polygon hides all four corners of the tile (the region a convex
+//     polygon hides from a point is convex, so the whole tile is hidden);
 //   * visibility: for each candidate still useful to some pixel, the CTA
-//     builds the list of polygons that may cross the hull of (tile, g) from
-//     the polygon bins, then every pixel runs the exact integer separating-axis
-//     test against that list;
+//     builds the list of polygons whose interior meets the hull of (tile, g)
+//     (exact separating-axis filter), then every pixel runs the exact integer
+//     separating-axis test against that list (none when the list is empty);
 //   * argmin: a per-pixel u64 key (FP32 distance bits << 32 | generator id),
 //     so "smaller distance, then smaller id" is one unsigned compare;
 //   * output: each thread owns 4 consecutive pixels of a row and writes them
@@ -38,9 +42,68 @@ struct PixSmem {
     int blk_oB[kBlockCap][kMaxPolyVerts];
     unsigned blk_mask[kBlockCap];
     int blk_m[kBlockCap];
+    unsigned char hidden[kCandCap];
     int n_cand, n_block, overflow;
     float tile_ub;
 };
+
+// True when one polygon hides every pixel of the tile from the point
+// generator at lattice point g. The set of points whose open segment to g
+// meets a convex polygon's interior is convex, so it suffices that the four
+// corners of the pixel-centre box are hidden by the same polygon. Walks the
+// bins of the thick segment (tile centre -> g, radius r) from the tile side
+// and stops at the first such polygon.
+__device__ bool tile_hidden(const DevScene &ds, int2 g, int4 box, float cx, float cy, float r) {
+    return walk_bins(ds, cx, cy, (float)g.x, (float)g.y, r, [&](int bin) {
+        for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
+            const int k = ds.bin_items[it];
+            if (!seg_near_box(cx, cy, (float)g.x, (float)g.y, r, ds.poly_box[k])) continue;
+            const int b = ds.poly_off[k], m = ds.poly_off[k + 1] - b;
+            const int2 *V = ds.poly_v + b;
+            const unsigned mg = edge_mask(V, m, g.x, g.y);
+            if (poly_blocks(V, m, box.x, box.y, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.y, g.x, g.y, mg) &&
+                poly_blocks(V, m, box.x, box.w, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.w, g.x, g.y, mg))
+                return true;
+        }
+        return false;
+    });
+}
+
+// Does the interior of convex polygon V meet the convex hull of the tile box
+// and point t? Exact separating-axis test over the polygon's edges and the
+// candidate hull edges (box edges, and lines from t through each corner).
+__device__ bool poly_meets_hull(const int2 *V, int m, int4 box, int tx, int ty) {
+    const int px[5] = {box.x, box.z, box.z, box.x, tx}, py[5] = {box.y, box.y, box.w, box.w, ty};
+    for (int i = 0; i < m; ++i) {  // polygon edges (outward side is orient < 0)
+        const int2 a = V[i], b = V[i + 1 == m ? 0 : i + 1];
+        bool all_out = true;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) all_out &= orient32(a.x, a.y, b.x, b.y, px[k], py[k]) <= 0;
+        if (all_out) return false;
+    }
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {  // 4 box edges, 4 lines t -> corner
+        const int ax = l < 4 ? px[l] : tx, ay = l < 4 ? py[l] : ty;
+        const int bx = l < 4 ? px[(l + 1) & 3] : px[l - 4], by = l < 4 ? py[(l + 1) & 3] : py[l - 4];
+        if (ax == bx && ay == by) continue;
+        bool hpos = true, hneg = true;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int o = orient32(ax, ay, bx, by, px[k], py[k]);
+            hpos &= o >= 0;
+            hneg &= o <= 0;
+        }
+        if (!hpos && !hneg) continue;
+        bool ppos = true, pneg = true;
+        for (int i = 0; i < m; ++i) {
+            const int o = orient32(ax, ay, bx, by, V[i].x, V[i].y);
+            ppos &= o >= 0;
+            pneg &= o <= 0;
+        }
+        if ((hpos && pneg) || (hneg && ppos)) return false;
+    }
+    return true;
+}
 
 __device__ __forceinline__ float key_dist(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
 
@@ -130,7 +193,7 @@ __device__ void sort_candidates(PixSmem &sm, int n) {
 // (lattice units, radius r), one column per thread; each polygon found is
 // filtered against the thick segment and appended (deduplicated) to smem.
 __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float cy, float tx, float ty,
-                               float r, int kind, int2 tl, int4 seg) {
+                               float r, int kind, int2 tl, int4 seg, int4 box) {
     const float bs = (float)ds.bin_size, x0 = (float)ds.bin_x0, y0 = (float)ds.bin_y0;
     const float m = r + 1.0f;
     auto bin_of = [&](float v, float o, int n) {
@@ -164,6 +227,9 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
                     if (atomicOr(&sm.dedup[k >> 5], bit) & bit) continue;
                 }
                 if (!seg_near_box(cx, cy, tx, ty, r, ds.poly_box[k])) continue;
+                if (kind != kSegI &&
+                    !poly_meets_hull(ds.poly_v + ds.poly_off[k], ds.poly_off[k + 1] - ds.poly_off[k], box, tl.x, tl.y))
+                    continue;
                 const int slot = atomicAdd(&sm.n_block, 1);
                 if (slot >= kBlockCap) {
                     sm.overflow = 1;
@@ -239,12 +305,12 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
     const float bcx = 0.5f * ((float)box.x + (float)box.z), bcy = 0.5f * ((float)box.y + (float)box.w);
     const float brad = 0.5f * sqrtf((float)(box.z - box.x) * (float)(box.z - box.x) +
                                     (float)(box.w - box.y) * (float)(box.w - box.y)) + 1.0f;
+    const bool any_live = __syncthreads_or(live != 0);
     if (threadIdx.x == 0) {
         sm.n_cand = 0;
         sm.tile_ub = INFINITY;
     }
     __syncthreads();
-    const bool any_live = __syncthreads_or(live != 0);
     for (int g0 = 0; any_live && g0 < ds.n_gen; g0 += NT) {
         const int g = g0 + threadIdx.x;
         float lb = -1.f;
@@ -264,13 +330,27 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
         const bool last = g0 + NT >= ds.n_gen;
         if (nc > kCandCap - NT || (last && nc > 0)) {
             sort_candidates(sm, nc);
-            for (int c = 0; c < nc; ++c) {
+            bool done = false;
+            for (int c = 0; c < nc && !done; ++c) {
                 const float lb_c = sm.cand_lb[c];
-                const int gc = sm.cand_id[c];
                 bool act = false;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) act |= (live >> k & 1u) && key_dist(key[k]) > lb_c;
-                if (!__syncthreads_or(act)) break;
+                if (!__syncthreads_or(act)) {
+                    done = true;
+                    break;
+                }
+                if ((c % NT) == 0) {  // hidden-tile test for the next NT candidates, in parallel
+                    const int cc = c + threadIdx.x;
+                    if (cc < nc) {
+                        const int g2 = sm.cand_id[cc];
+                        sm.hidden[cc] = ds.gen_kind[g2] != kSegI &&
+                                        tile_hidden(ds, ds.gen_lat[g2], box, bcx, bcy, brad);
+                    }
+                    __syncthreads();
+                }
+                if (sm.hidden[c]) continue;
+                const int gc = sm.cand_id[c];
                 const int kind = ds.gen_kind[gc];
                 const float cf = ds.gen_costf[gc];
                 const int2 gl = ds.gen_lat[gc];
@@ -336,7 +416,7 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
                     sm.overflow = 0;
                 }
                 __syncthreads();
-                build_blockers(ds, sm, bcx, bcy, tx, ty, brad, kind, gl, seg);
+                build_blockers(ds, sm, bcx, bcy, tx, ty, brad, kind, gl, seg, box);
                 __syncthreads();
                 const int nb = min(sm.n_block, kBlockCap);
                 const bool ovf = sm.overflow != 0;
