@@ -201,16 +201,20 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         ds.cost[k] = dalloc<double>(s, hs.n_gen);
         ds.par[k] = dalloc<int32_t>(s, hs.n_gen);
         ds.frontier[k] = dalloc<int32_t>(s, hs.n_gen);
+        ds.dirtyl[k] = dalloc<int32_t>(s, hs.n_gen);
     }
     ds.gen_costf = dalloc<float>(s, hs.n_gen);
     ds.gen_cost = dalloc<double>(s, hs.n_gen);
     ds.gen_par = dalloc<int32_t>(s, hs.n_gen);
     ds.gen_cone = dalloc<int4>(s, hs.n_gen);
     ds.gen_ctype = dalloc<int32_t>(s, hs.n_gen);
+    ds.dirty = dalloc<uint32_t>(s, (hs.n_gen + 31) / 32);
+    ds.counters = dalloc<int32_t>(s, 4);
     ds.status = dalloc<uint32_t>(s, 1);
     ds.stats = dalloc<int32_t>(s, 4);
     ds.tiles_x = (hs.Nx + spm::kTile - 1) / spm::kTile;
     ds.tiles_y = (hs.Ny + spm::kTile - 1) / spm::kTile;
+    ds.sssp_blocks = spm::sssp_grid_blocks();
     for (void *p : s->allocs) ok &= p != nullptr;
     ok &= ds.vis_bits && ds.in_src && ds.in_len && ds.out_dst && ds.status && ds.stats && ds.gen_ctype;
     if (!ok) {

@@ -95,8 +95,11 @@ struct DevScene {
     int64_t edge_cap;
     double *cost[2];                   // Jacobi double buffer
     int32_t *par[2];
-    int32_t *frontier[2];              // frontier lists
-    int32_t *counters;                 // [0] frontier sizes..., see kernels
+    int32_t *frontier[2];              // changed-vertex lists, alternating by round
+    int32_t *dirtyl[2];                // vertices to pull, alternating by round
+    uint32_t *dirty;                   // n_gen bits: vertex already in the dirty list
+    int32_t *counters;                 // [0,1] frontier sizes, [2,3] dirty-list sizes
+    int32_t sssp_blocks;               // cooperative grid size (CTAs)
     // finalised generator table (read by the pixel kernel)
     float *gen_costf;                  // n_gen (inf when unreached)
     double *gen_cost;                  // n_gen
@@ -116,6 +119,7 @@ struct DevScene {
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent);
+int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();
 void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,

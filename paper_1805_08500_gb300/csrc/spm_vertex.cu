@@ -12,20 +12,24 @@
 //      relax v); segment interiors reach v through its perpendicular foot.
 //   2. k_edges_*: the bits become CSR in-lists (by v) with FP64 edge lengths
 //      and out-lists (by u) for frontier marking.
-//   3. k_sssp: one CTA runs Jacobi rounds restricted to the frontier until no
-//      cost or parent changes (bounded round count -> status bit).
+//   3. k_sssp: a cooperative kernel on every SM runs Jacobi rounds restricted
+//      to the vertices whose in-neighbours changed, until no cost or parent
+//      changes (bounded round count -> status bit).
 // Costs are FP64 with explicitly rounded operations, so they match a plain
 // FP64 Dijkstra over the same edges bit for bit.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "spm_device.cuh"
 #include "spm_internal.h"
 
+namespace cg = cooperative_groups;
+
 namespace spm {
 namespace {
 
 constexpr int kVisThreads = 256;
-constexpr int kSsspThreads = 1024;
+constexpr int kSsspThreads = 256;
 
 // Static filter + exact visibility for one (u, v) pair.
 __device__ bool pair_edge(const DevScene &ds, int u, int v) {
@@ -155,99 +159,134 @@ __global__ void k_edges_fill(DevScene ds) {
     }
 }
 
-// Jacobi rounds over the frontier in one CTA. cost[0]/par[0] hold the
-// committed state; cost[1]/par[1] the values computed this round.
-__global__ void __launch_bounds__(kSsspThreads) k_sssp(DevScene ds, int max_rounds) {
-    extern __shared__ uint32_t dirty[];
-    __shared__ int next_count, cur_count;
-    const int n = ds.n_gen, nwords = (n + 31) / 32;
-    if (ds.in_start[ds.n_vert] > ds.edge_cap) {
-        if (threadIdx.x == 0) ds.stats[0] = 0;
-        return;
+// Jacobi rounds of the fixpoint on the whole GPU (cooperative launch, two
+// grid barriers per round). cost[0]/par[0] and the cone cache hold the
+// committed state; a round
+//   pull:   one warp per dirty vertex v reduces its in-list to the
+//           lexicographic minimum of (cost(u) + |u - v|, u) over valid u
+//           (u a source, or v inside u's committed shadow cone) and records
+//           v when that differs from its committed state;
+//   commit: the changed vertices become committed (cost, parent, cone) and
+//           mark their out-neighbours dirty for the next round.
+// Lists and counters alternate by round parity, so a counter is zeroed only
+// in a phase where nobody reads it. Stops when no vertex changes, or at the
+// round cap (status bit). Deterministic: each pull is a min over a set.
+__device__ __forceinline__ void commit_vertex(const DevScene &ds, int v) {
+    ds.cost[0][v] = ds.cost[1][v];
+    const int p = ds.par[1][v];
+    ds.par[0][v] = p;
+    int dx, dy;
+    arrival_dir(ds, p, ds.gen_lat[v], dx, dy);
+    int4 c;
+    const int ct = make_cone(ds.gen_wedge[v], dx, dy, c);
+    ds.gen_cone[v] = c;
+    ds.gen_ctype[v] = ct;
+}
+
+// One warp marks the out-neighbours of u dirty, appending each newly dirty
+// vertex once to the dirty list (warp-aggregated counter update).
+__device__ __forceinline__ void mark_out_warp(const DevScene &ds, int u, int lane, int32_t *dl,
+                                              int32_t *dcount) {
+    const int e0 = ds.out_start[u], e1 = ds.out_start[u + 1];
+    for (int eb = e0; eb < e1; eb += 32) {
+        const int e = eb + lane;
+        bool fresh = false;
+        int v = 0;
+        if (e < e1) {
+            v = ds.out_dst[e];
+            const uint32_t bit = 1u << (v & 31);
+            fresh = !(atomicOr(&ds.dirty[v >> 5], bit) & bit);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(dcount, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fresh) dl[base + __popc(bal & ((1u << lane) - 1u))] = v;
     }
-    double *cost = ds.cost[0], *ncost = ds.cost[1];
-    int32_t *par = ds.par[0], *npar = ds.par[1];
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+}
+
+__global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
+    cg::grid_group grid = cg::this_grid();
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsize = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31, gwarp = gtid >> 5, nwarps = gsize >> 5;
+    const int n = ds.n_gen;
+    int32_t *cnt = ds.counters;  // [0,1] frontier counts, [2,3] dirty counts
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    const bool overflow = ds.in_start[ds.n_vert] > ds.edge_cap;
+    for (int g = gtid; g < n; g += gsize) {
         const bool src = g < ds.n_src;
-        cost[g] = src ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
-        par[g] = src ? g : -1;
-        if (src) ds.frontier[0][g] = g;
+        ds.cost[0][g] = src ? 0.0 : inf;
+        ds.par[0][g] = src ? g : -1;
+        ds.gen_ctype[g] = src ? kConeNone : kConeEmpty;
+        ds.gen_cone[g] = make_int4(0, 0, 0, 0);
     }
-    for (int w = threadIdx.x; w < nwords; w += blockDim.x) dirty[w] = 0u;
-    if (threadIdx.x == 0) { cur_count = ds.n_src; next_count = 0; }
-    __syncthreads();
-    int round = 0, fsel = 0;
-    while (true) {
-        const int *front = ds.frontier[fsel];
-        int *nfront = ds.frontier[fsel ^ 1];
-        const int fc = cur_count;
-        if (fc == 0) break;
-        if (round >= max_rounds) {
-            if (threadIdx.x == 0) atomicOr(ds.status, kStNotConverged);
+    for (int w = gtid; w < (n + 31) / 32; w += gsize) ds.dirty[w] = 0u;
+    if (gtid < 4) cnt[gtid] = 0;
+    grid.sync();
+    if (!overflow)
+        for (int u = gwarp; u < ds.n_src; u += nwarps) mark_out_warp(ds, u, lane, ds.dirtyl[0], &cnt[2]);
+    grid.sync();
+    int round = 0;
+    for (;; ++round) {
+        const int par_r = round & 1, par_n = par_r ^ 1;
+        // pull
+        if (gtid == 0) {
+            cnt[par_n] = 0;
+            cnt[2 + par_n] = 0;
+        }
+        const int nd = cnt[2 + par_r];
+        const int32_t *dl = ds.dirtyl[par_r];
+        for (int i = gwarp; i < nd; i += nwarps) {
+            const int v = dl[i];
+            const int vv = v - ds.n_src;
+            if (lane == 0) atomicAnd(&ds.dirty[v >> 5], ~(1u << (v & 31)));
+            const int2 vl = ds.gen_lat[v];
+            double best = inf;
+            int bpar = -1;
+            for (int e = ds.in_start[vv] + lane; e < ds.in_start[vv + 1]; e += 32) {
+                const int u = ds.in_src[e];
+                const double cu = ds.cost[0][u];
+                if (!(cu < inf)) continue;
+                const int ct = ds.gen_ctype[u];
+                if (ct != kConeNone) {
+                    const int2 ul = ds.gen_lat[u];
+                    if (!in_cone(ct, ds.gen_cone[u], vl.x - ul.x, vl.y - ul.y)) continue;
+                }
+                const double cand = __dadd_rn(cu, ds.in_len[e]);
+                if (cand < best || (cand == best && u < bpar)) {
+                    best = cand;
+                    bpar = u;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
+                if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
+                    best = ob;
+                    bpar = op;
+                }
+            }
+            if (lane == 0 && (best != ds.cost[0][v] || bpar != ds.par[0][v])) {
+                ds.cost[1][v] = best;
+                ds.par[1][v] = bpar;
+                ds.frontier[par_r][atomicAdd(&cnt[par_r], 1)] = v;
+            }
+        }
+        grid.sync();
+        const int nc = cnt[par_r];
+        if (nc == 0) break;
+        if (round + 1 >= max_rounds) {
+            if (gtid == 0) atomicOr(ds.status, kStNotConverged);
             break;
         }
-        // mark out-neighbours of the frontier
-        for (int i = threadIdx.x; i < fc; i += blockDim.x) {
-            const int u = front[i];
-            for (int e = ds.out_start[u]; e < ds.out_start[u + 1]; ++e) {
-                const int v = ds.out_dst[e];
-                atomicOr(&dirty[v >> 5], 1u << (v & 31));
-            }
-        }
-        __syncthreads();
-        // pull the dirty vertices from the committed state
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-            uint32_t b = dirty[w];
-            dirty[w] = 0u;
-            while (b) {
-                const int v = w * 32 + __ffs(b) - 1;
-                b &= b - 1;
-                const int vv = v - ds.n_src;
-                const int2 vl = ds.gen_lat[v];
-                double best = __longlong_as_double(0x7ff0000000000000ll);
-                int bpar = -1;
-                for (int e = ds.in_start[vv]; e < ds.in_start[vv + 1]; ++e) {
-                    const int u = ds.in_src[e];
-                    const double cu = cost[u];
-                    if (!(cu < best)) continue;  // cannot improve (edge lengths > 0)
-                    if (ds.gen_kind[u] == kVert) {
-                        int dx, dy;
-                        arrival_dir(ds, par[u], ds.gen_lat[u], dx, dy);
-                        int4 c;
-                        int ct = make_cone(ds.gen_wedge[u], dx, dy, c);
-                        const int2 ul = ds.gen_lat[u];
-                        if (!in_cone(ct, c, vl.x - ul.x, vl.y - ul.y)) continue;
-                    }
-                    const double cand = __dadd_rn(cu, ds.in_len[e]);
-                    if (cand < best || (cand == best && u < bpar)) {
-                        best = cand;
-                        bpar = u;
-                    }
-                }
-                if (best != cost[v] || bpar != par[v]) {
-                    ncost[v] = best;
-                    npar[v] = bpar;
-                    nfront[atomicAdd(&next_count, 1)] = v;
-                }
-            }
-        }
-        __syncthreads();
-        const int nc = next_count;
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-            const int v = nfront[i];
-            cost[v] = ncost[v];
-            par[v] = npar[v];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            cur_count = nc;
-            next_count = 0;
-        }
-        fsel ^= 1;
-        ++round;
-        __syncthreads();
+        // commit the changed vertices and mark their out-neighbours
+        const int32_t *fr = ds.frontier[par_r];
+        for (int i = gtid; i < nc; i += gsize) commit_vertex(ds, fr[i]);
+        for (int i = gwarp; i < nc; i += nwarps) mark_out_warp(ds, fr[i], lane, ds.dirtyl[par_n], &cnt[2 + par_n]);
+        grid.sync();
     }
-    if (threadIdx.x == 0) ds.stats[0] = round;
+    if (gtid == 0) ds.stats[0] = round + 1;
 }
 
 // Final generator table for the pixel phase: FP32 costs and shadow cones.
@@ -258,19 +297,6 @@ __global__ void k_finalize(DevScene ds) {
         ds.gen_cost[g] = c;
         ds.gen_par[g] = p;
         ds.gen_costf[g] = (float)c;
-        int4 cone = make_int4(0, 0, 0, 0);
-        int ct = kConeNone;
-        if (g >= ds.n_src) {
-            if (p < 0) {
-                ct = kConeEmpty;
-            } else {
-                int dx, dy;
-                arrival_dir(ds, p, ds.gen_lat[g], dx, dy);
-                ct = make_cone(ds.gen_wedge[g], dx, dy, cone);
-            }
-        }
-        ds.gen_cone[g] = cone;
-        ds.gen_ctype[g] = ct;
     }
 }
 
@@ -291,9 +317,20 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
     } else {
         cudaMemsetAsync(ds.in_start, 0, sizeof(int32_t) * (ds.n_vert + 1), st);
     }
-    const size_t smem = sizeof(uint32_t) * ((ds.n_gen + 31) / 32);
-    k_sssp<<<1, kSsspThreads, smem, st>>>(ds, 4 * ds.n_gen + 64);
+    DevScene arg = ds;
+    int max_rounds = 4 * ds.n_gen + 64;
+    void *args[] = {&arg, &max_rounds};
+    cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
     k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
+}
+
+int sssp_grid_blocks() {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp, kSsspThreads, 0);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+    return (sms > 0 ? sms : 1) * per_sm;
 }
 
 int count_kernel_launches_vertex() { return 6; }
