@@ -147,7 +147,8 @@ spm_status spm_scene_generators(spm_scene *scene, int32_t *kind, int32_t *lattic
 /* info[0] generators, [1] sources (incl. 3 per segment), [2] obstacle-vertex
  * generators, [3] lattice scale S, [4] polygons, [5] vertex-phase rounds of
  * the last compute (after sync), [6] visibility-graph edges of the last
- * compute (after sync), [7] tile size in pixels. */
+ * compute (after sync), [7] tile size in pixels, [8] 1 if the last compute
+ * used flooded per-tile candidate lists (after sync), [9] flood_mode. */
 spm_status spm_scene_info(spm_scene *scene, int64_t *info);
 
 /* Differentiable form. Forward: loss = mean over n agents (pixel indices,
@@ -197,6 +198,29 @@ spm_status spm_agents_backward_noalloc(spm_scene *scene, void *stream,
  * CUDA graph): vertex_ms = vertex-cost fixpoint (Sec. 3.1 Procedures 1, 2
  * and 4), pixel_ms = pixel pass (Procedure 3). Waits for the compute. */
 spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *pixel_ms);
+
+/* Tuning of the pixel pass's culling, per scene.
+ * flood_mode: 0 = automatic (flood the per-tile candidate lists when the
+ *   visibility graph among generators is sparse -- below 1% of all pairs,
+ *   as in mazes -- otherwise let every tile scan every generator; decided on
+ *   the device each compute), 1 = always flood, 2 = never flood.
+ * hidden_chunk: first chunk of lb-ordered candidates whose tiles are tested
+ *   for being hidden (32..256; later chunks double). */
+typedef struct {
+    int32_t flood_mode;
+    int32_t hidden_chunk;
+    int32_t reserved[6];
+} spm_tuning;
+
+spm_status spm_scene_get_tuning(const spm_scene *scene, spm_tuning *out);
+spm_status spm_scene_set_tuning(spm_scene *scene, const spm_tuning *tuning);
+
+/* Autotuner: times spm_compute on this scene (device events on `stream`,
+ * warm-up then the median of 3 runs) for every flood_mode x hidden_chunk
+ * combination in {1, 2} x {32, 256}, keeps the fastest and writes it to
+ * *chosen (may be NULL). Synchronous. Allocates the scene's output staging
+ * planes on first use; call it at set-up, not inside a captured stream. */
+spm_status spm_scene_autotune(spm_scene *scene, void *stream, spm_tuning *chosen);
 
 /* Static text for a status code. */
 const char *spm_status_string(spm_status status);

@@ -40,6 +40,11 @@ class SpmError(RuntimeError):
                          + (f" ({msg})" if msg else ""))
 
 
+class SpmTuning(ctypes.Structure):
+    _fields_ = [("flood_mode", ctypes.c_int32), ("hidden_chunk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
 class _Desc(ctypes.Structure):
     _fields_ = [("world_w", ctypes.c_int32), ("world_h", ctypes.c_int32),
                 ("grid_w", ctypes.c_int32), ("grid_h", ctypes.c_int32),
@@ -86,6 +91,9 @@ def load_library():
         "spm_agents_backward": ([P, P, P, P], I32),
         "spm_scene_phase_ms": ([P, P, P], I32),
         "spm_agents_backward_noalloc": ([P, P, P, I32, P, P, P], I32),
+        "spm_scene_get_tuning": ([P, P], I32),
+        "spm_scene_set_tuning": ([P, P], I32),
+        "spm_scene_autotune": ([P, P, P], I32),
         "spm_status_string": ([I32], ctypes.c_char_p),
         "spm_last_error": ([P], ctypes.c_char_p),
     }
@@ -202,10 +210,29 @@ def spm_extract_path(handle, x, y, cap=4096):
     return out[:2 * n.value].reshape(-1, 2)
 
 
+def spm_scene_get_tuning(handle):
+    t = SpmTuning()
+    _check(load_library().spm_scene_get_tuning(handle, ctypes.byref(t)), "spm_scene_get_tuning", handle)
+    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk}
+
+
+def spm_scene_set_tuning(handle, flood_mode, hidden_chunk):
+    t = SpmTuning(int(flood_mode), int(hidden_chunk))
+    _check(load_library().spm_scene_set_tuning(handle, ctypes.byref(t)), "spm_scene_set_tuning", handle)
+
+
+def spm_scene_autotune(handle, stream=None):
+    t = SpmTuning()
+    _check(load_library().spm_scene_autotune(handle, _stream_handle(stream), ctypes.byref(t)),
+           "spm_scene_autotune", handle)
+    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk}
+
+
 def spm_scene_info(handle):
-    info = np.zeros(8, np.int64)
+    info = np.zeros(10, np.int64)
     _check(load_library().spm_scene_info(handle, info.ctypes.data), "spm_scene_info", handle)
-    keys = ["n_gen", "n_src", "n_vert", "lattice_scale", "n_polys", "rounds", "edges", "tile"]
+    keys = ["n_gen", "n_src", "n_vert", "lattice_scale", "n_polys", "rounds", "edges", "tile",
+            "flooded", "flood_mode"]
     return dict(zip(keys, (int(v) for v in info)))
 
 
@@ -314,6 +341,15 @@ class Scene:
     def update_sources(self, points, segs):
         spm_scene_update_sources(self.handle, points, segs)
 
+    def autotune(self, stream=None, cache_key=None):
+        """Pick the culling configuration: from the tuning cache when cache_key
+        (a workload-class string) has an entry for this GPU, else by timing
+        (spm_scene_autotune) and recording the result in the cache."""
+        return autotune_cached(self, stream, cache_key)
+
+    def tuning(self):
+        return spm_scene_get_tuning(self.handle)
+
     def phase_ms(self):
         return spm_scene_phase_ms(self.handle)
 
@@ -322,6 +358,35 @@ class Scene:
 
     def extract_path(self, x, y, cap=4096):
         return spm_extract_path(self.handle, x, y, cap)
+
+
+TUNING_CACHE = os.path.join(_HERE, "tuning_cache.json")
+
+
+def _gpu_name():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def autotune_cached(scene: "Scene", stream=None, cache_key=None, path=TUNING_CACHE):
+    import json
+    cache = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            cache = json.load(f)
+    key = f"{cache_key}|{_gpu_name()}" if cache_key else None
+    if key and key in cache:
+        t = cache[key]
+        spm_scene_set_tuning(scene.handle, t["flood_mode"], t["hidden_chunk"])
+        return dict(t, source="cache")
+    t = spm_scene_autotune(scene.handle, stream)
+    if key:
+        cache[key] = t
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return dict(t, source="measured")
 
 
 def agent_loss(scene: "Scene", points, segs, agents):

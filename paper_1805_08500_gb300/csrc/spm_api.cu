@@ -214,6 +214,21 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     ds.stats = dalloc<int32_t>(s, 4);
     ds.tiles_x = (hs.Nx + spm::kTile - 1) / spm::kTile;
     ds.tiles_y = (hs.Ny + spm::kTile - 1) / spm::kTile;
+    {
+        const int64_t ntiles = (int64_t)ds.tiles_x * ds.tiles_y;
+        ds.use_flood = spm::flood_possible((int)ntiles) && spm::flood_smem_attr() ? 1 : 0;
+        ds.flood_mode = 0;
+        ds.hidden_chunk = 32;
+        ds.pair_cap = (int32_t)std::min<int64_t>(std::max<int64_t>((int64_t)hs.n_gen * ntiles / 2, 1),
+                                                 std::max<int64_t>(4 << 20, 64 * (int64_t)hs.n_gen));
+        if (!ds.use_flood) ds.pair_cap = 1;
+        ds.tile_start = dalloc<int32_t>(s, ntiles + 1);
+        ds.tile_count = dalloc<int32_t>(s, ntiles);
+        ds.tile_items = dalloc<int32_t>(s, ds.pair_cap);
+        ds.pairs = dalloc<int2>(s, ds.pair_cap);
+        ds.glob_list = dalloc<int32_t>(s, hs.n_gen);
+        ds.flood_counts = dalloc<int32_t>(s, 4);
+    }
     ds.sssp_blocks = spm::sssp_grid_blocks();
     for (void *p : s->allocs) ok &= p != nullptr;
     ok &= ds.vis_bits && ds.in_src && ds.in_len && ds.out_dst && ds.status && ds.stats && ds.gen_ctype;
@@ -273,6 +288,12 @@ spm_status spm_compute(spm_scene *s, void *stream, float *dist, int32_t *parent)
     if (timed) cudaEventRecord(s->ev[0], cs);
     spm::launch_vertex_phase(s->ds, cs);
     if (timed) cudaEventRecord(s->ev[1], cs);
+    if (s->ds.use_flood) {
+        spm::launch_flood(s->ds, cs);
+    } else {
+        static const int32_t off[4] = {0, 0, 1, 0};
+        cudaMemcpyAsync(s->ds.flood_counts, off, sizeof off, cudaMemcpyHostToDevice, cs);
+    }
     spm::launch_pixel_phase(s->ds, cs, dist, parent);
     if (timed) cudaEventRecord(s->ev[2], cs);
     s->ev_valid = timed;
@@ -405,9 +426,11 @@ spm_status spm_scene_generators(spm_scene *s, int32_t *kind, int32_t *lattice_xy
 
 spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     if (!s || !info) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
-    int32_t stats[4] = {0, 0, 0, 0};
-    if (check_device(s) == SPM_OK)
+    int32_t stats[4] = {0, 0, 0, 0}, fc[4] = {0, 0, 1, 0};
+    if (check_device(s) == SPM_OK) {
         cudaMemcpy(stats, s->ds.stats, sizeof stats, cudaMemcpyDeviceToHost);
+        cudaMemcpy(fc, s->ds.flood_counts, sizeof fc, cudaMemcpyDeviceToHost);
+    }
     info[0] = s->hs.n_gen;
     info[1] = s->hs.n_src;
     info[2] = s->hs.n_vert;
@@ -416,7 +439,77 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     info[5] = stats[0];
     info[6] = stats[1];
     info[7] = spm::kTile;
+    info[8] = (s->ds.use_flood && fc[2] == 0) ? 1 : 0;
+    info[9] = s->ds.flood_mode;
     return SPM_OK;
+}
+
+spm_status spm_scene_get_tuning(const spm_scene *s, spm_tuning *out) {
+    if (!s || !out) return SPM_ERR_INVALID_ARG;
+    *out = spm_tuning{};
+    out->flood_mode = s->ds.flood_mode;
+    out->hidden_chunk = s->ds.hidden_chunk;
+    return SPM_OK;
+}
+
+spm_status spm_scene_set_tuning(spm_scene *s, const spm_tuning *t) {
+    if (!s || !t) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    if (t->flood_mode < 0 || t->flood_mode > 2 || t->hidden_chunk < 32 || t->hidden_chunk > 256)
+        return set_err(s, SPM_ERR_INVALID_ARG, "tuning out of range");
+    s->ds.flood_mode = t->flood_mode;
+    s->ds.hidden_chunk = t->hidden_chunk;
+    return SPM_OK;
+}
+
+spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
+    if (!s) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    const size_t npx = (size_t)s->hs.Nx * s->hs.Ny;
+    if (!s->stage_dist) {
+        s->stage_dist = dalloc<float>(s, npx);
+        s->stage_par = dalloc<int32_t>(s, npx);
+        if (!s->stage_dist || !s->stage_par) return set_err(s, SPM_ERR_OOM, "staging allocation failed");
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "event creation failed");
+    const int modes[2] = {1, 2}, chunks[2] = {32, 256};
+    float best = 3.4e38f;
+    spm_tuning pick{};
+    pick.flood_mode = s->ds.flood_mode;
+    pick.hidden_chunk = s->ds.hidden_chunk;
+    for (int mi = 0; mi < 2; ++mi) {
+        if (modes[mi] == 1 && !s->ds.use_flood) continue;
+        for (int ci = 0; ci < 2; ++ci) {
+            s->ds.flood_mode = modes[mi];
+            s->ds.hidden_chunk = chunks[ci];
+            float t[3];
+            st = spm_compute(s, stream, s->stage_dist, s->stage_par);  // warm-up
+            for (int k = 0; k < 3 && st == SPM_OK; ++k) {
+                cudaEventRecord(a, cs);
+                st = spm_compute(s, stream, s->stage_dist, s->stage_par);
+                cudaEventRecord(b, cs);
+                cudaEventSynchronize(b);
+                cudaEventElapsedTime(&t[k], a, b);
+            }
+            if (st != SPM_OK) break;
+            std::sort(t, t + 3);
+            if (t[1] < best) {
+                best = t[1];
+                pick.flood_mode = modes[mi];
+                pick.hidden_chunk = chunks[ci];
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    s->ds.flood_mode = pick.flood_mode;
+    s->ds.hidden_chunk = pick.hidden_chunk;
+    if (chosen) *chosen = pick;
+    if (st != SPM_OK) return st;
+    return spm_scene_sync(s, stream);
 }
 
 spm_status spm_scene_phase_ms(spm_scene *s, float *vertex_ms, float *pixel_ms) {

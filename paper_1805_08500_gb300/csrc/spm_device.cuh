@@ -241,4 +241,34 @@ __device__ __forceinline__ bool visible_foot(const DevScene &ds, int s, int px, 
     return !blocked;
 }
 
+// Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
+#ifdef SPM_COUNT
+static __device__ unsigned long long g_count[16];  // one copy per translation unit
+#define SPM_CNT(i, v) atomicAdd(&::spm::g_count[i], (unsigned long long)(v))
+#else
+#define SPM_CNT(i, v) ((void)0)
+#endif
+
+// True when one polygon hides every point of the box from the point
+// generator at lattice point g. The set of points whose open segment to g
+// meets a convex polygon's interior is convex, so it suffices that the four
+// corners of the pixel-centre box are hidden by the same polygon. Walks the
+// bins of the thick segment (tile centre -> g, radius r) from the tile side
+// and stops at the first such polygon.
+__device__ __forceinline__ bool box_hidden(const DevScene &ds, int2 g, int4 box, float cx, float cy, float r) {
+    return walk_bins(ds, cx, cy, (float)g.x, (float)g.y, r, [&](int bin) {
+        for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
+            const int k = ds.bin_items[it];
+            if (!seg_near_box(cx, cy, (float)g.x, (float)g.y, r, ds.poly_box[k])) continue;
+            const int b = ds.poly_off[k], m = ds.poly_off[k + 1] - b;
+            const int2 *V = ds.poly_v + b;
+            const unsigned mg = edge_mask(V, m, g.x, g.y);
+            if (poly_blocks(V, m, box.x, box.y, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.y, g.x, g.y, mg) &&
+                poly_blocks(V, m, box.x, box.w, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.w, g.x, g.y, mg))
+                return true;
+        }
+        return false;
+    });
+}
+
 }  // namespace spm

@@ -108,8 +108,18 @@ struct DevScene {
     int32_t *gen_ctype;                // ConeType
     uint32_t *status;                  // latched status bits
     int32_t *stats;                    // [0] rounds, [1] edges
-    // tiles
+    // tiles and their candidate lists (flood)
     int32_t tiles_x, tiles_y;
+    int32_t use_flood;                 // 0: flood impossible (too many tiles for smem)
+    int32_t flood_mode;                // 0 auto (sparse visibility graph), 1 on, 2 off
+    int32_t hidden_chunk;              // first hidden-test chunk in the pixel pass
+    int32_t *tile_start;               // ntiles + 1 (CSR by tile)
+    int32_t *tile_count;               // ntiles (counts, then fill cursors)
+    int32_t *tile_items;               // pair_cap generator ids
+    int2 *pairs;                       // pair_cap (tile, generator)
+    int32_t pair_cap;
+    int32_t *glob_list;                // generators every tile scans
+    int32_t *flood_counts;             // [0] pairs, [1] global list size, [2] overflow
     // differentiable form
     float *agent_accum;                // scratch for deterministic reductions
     const int32_t *agents;
@@ -119,6 +129,9 @@ struct DevScene {
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent);
+void launch_flood(const DevScene &ds, cudaStream_t st);
+bool flood_possible(int tiles);
+int flood_smem_attr();
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();

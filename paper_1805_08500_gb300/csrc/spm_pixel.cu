@@ -9,7 +9,9 @@
 //     lower bound lb = cost + dist(g, tile) below the tile's current worst;
 //   * order: candidates sorted by lb; the CTA stops once every pixel's best is
 //     <= lb (no later candidate can win);
-//   * hidden tiles: in lb order, 256 candidates at a time, each thread walks
+//   * hidden tiles: in lb order, in chunks of 32, 64, 128, then 256
+//     candidates (the early exit usually comes within the first chunk), each
+//     thread walks
 //     the polygon bins from the tile toward one candidate and drops it when a
 //     single polygon hides all four corners of the tile (the region a convex
 //     polygon hides from a point is convex, so the whole tile is hidden);
@@ -33,6 +35,9 @@ constexpr int T = kTile;
 constexpr int NT = kPixelThreads;
 constexpr unsigned long long kUnset = 0x7F800000FFFFFFFFull;  // (+inf, id max)
 
+// Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
+
+
 struct PixSmem {
     int cand_id[kCandCap];
     float cand_lb[kCandCap];
@@ -46,28 +51,6 @@ struct PixSmem {
     int n_cand, n_block, overflow;
     float tile_ub;
 };
-
-// True when one polygon hides every pixel of the tile from the point
-// generator at lattice point g. The set of points whose open segment to g
-// meets a convex polygon's interior is convex, so it suffices that the four
-// corners of the pixel-centre box are hidden by the same polygon. Walks the
-// bins of the thick segment (tile centre -> g, radius r) from the tile side
-// and stops at the first such polygon.
-__device__ bool tile_hidden(const DevScene &ds, int2 g, int4 box, float cx, float cy, float r) {
-    return walk_bins(ds, cx, cy, (float)g.x, (float)g.y, r, [&](int bin) {
-        for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-            const int k = ds.bin_items[it];
-            if (!seg_near_box(cx, cy, (float)g.x, (float)g.y, r, ds.poly_box[k])) continue;
-            const int b = ds.poly_off[k], m = ds.poly_off[k + 1] - b;
-            const int2 *V = ds.poly_v + b;
-            const unsigned mg = edge_mask(V, m, g.x, g.y);
-            if (poly_blocks(V, m, box.x, box.y, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.y, g.x, g.y, mg) &&
-                poly_blocks(V, m, box.x, box.w, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.w, g.x, g.y, mg))
-                return true;
-        }
-        return false;
-    });
-}
 
 // Does the interior of convex polygon V meet the convex hull of the tile box
 // and point t? Exact separating-axis test over the polygon's edges and the
@@ -306,15 +289,25 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
     const float brad = 0.5f * sqrtf((float)(box.z - box.x) * (float)(box.z - box.x) +
                                     (float)(box.w - box.y) * (float)(box.w - box.y)) + 1.0f;
     const bool any_live = __syncthreads_or(live != 0);
+    if (threadIdx.x == 0) SPM_CNT(0, 1);
     if (threadIdx.x == 0) {
         sm.n_cand = 0;
         sm.tile_ub = INFINITY;
     }
     __syncthreads();
-    for (int g0 = 0; any_live && g0 < ds.n_gen; g0 += NT) {
-        const int g = g0 + threadIdx.x;
+    // candidate source: the tile's flooded list plus the global list, or every
+    // generator when the lists are unavailable
+    const bool lists = ds.use_flood && ds.flood_counts[2] == 0;
+    const int tix = tile;
+    const int l0 = lists ? ds.tile_start[tix] : 0;
+    const int nlist = lists ? ds.tile_start[tix + 1] - l0 : 0;
+    const int ntotal = lists ? nlist + ds.flood_counts[1] : ds.n_gen;
+    for (int g0 = 0; any_live && g0 < ntotal; g0 += NT) {
+        const int i = g0 + threadIdx.x;
+        int g = i;
+        if (lists && i < ntotal) g = i < nlist ? ds.tile_items[l0 + i] : ds.glob_list[i - nlist];
         float lb = -1.f;
-        if (g < ds.n_gen) lb = tile_lower_bound(ds, g, box, fbox);
+        if (i < ntotal) lb = tile_lower_bound(ds, g, box, fbox);
         const bool keep = lb >= 0.f && lb <= sm.tile_ub;
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         int base = 0;
@@ -327,10 +320,12 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
         }
         __syncthreads();
         const int nc = sm.n_cand;
-        const bool last = g0 + NT >= ds.n_gen;
+        const bool last = g0 + NT >= ntotal;
         if (nc > kCandCap - NT || (last && nc > 0)) {
             sort_candidates(sm, nc);
+            if (threadIdx.x == 0) SPM_CNT(1, nc);
             bool done = false;
+            int tested = 0, chunk = ds.hidden_chunk;
             for (int c = 0; c < nc && !done; ++c) {
                 const float lb_c = sm.cand_lb[c];
                 bool act = false;
@@ -340,16 +335,23 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
                     done = true;
                     break;
                 }
-                if ((c % NT) == 0) {  // hidden-tile test for the next NT candidates, in parallel
+                if (c == tested) {  // hidden-tile test for the next chunk, in parallel
                     const int cc = c + threadIdx.x;
-                    if (cc < nc) {
+                    if (threadIdx.x < chunk && cc < nc) {
+                        SPM_CNT(2, 1);
                         const int g2 = sm.cand_id[cc];
                         sm.hidden[cc] = ds.gen_kind[g2] != kSegI &&
-                                        tile_hidden(ds, ds.gen_lat[g2], box, bcx, bcy, brad);
+                                        box_hidden(ds, ds.gen_lat[g2], box, bcx, bcy, brad);
                     }
+                    tested += chunk;
+                    chunk = min(2 * chunk, NT);  // most tiles exit within the first chunk
                     __syncthreads();
                 }
-                if (sm.hidden[c]) continue;
+                if (sm.hidden[c]) {
+                    if (threadIdx.x == 0) SPM_CNT(3, 1);
+                    continue;
+                }
+                if (threadIdx.x == 0) SPM_CNT(4, 1);
                 const int gc = sm.cand_id[c];
                 const int kind = ds.gen_kind[gc];
                 const float cf = ds.gen_costf[gc];
@@ -399,6 +401,7 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
                     }
                 }
                 if (!__syncthreads_or(need != 0)) continue;
+                if (threadIdx.x == 0) SPM_CNT(5, 1);
                 // blockers of the hull of (tile, target)
                 float tx, ty;
                 if (kind == kSegI) {
@@ -420,6 +423,12 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
                 __syncthreads();
                 const int nb = min(sm.n_block, kBlockCap);
                 const bool ovf = sm.overflow != 0;
+                if (threadIdx.x == 0) {
+                    SPM_CNT(6, nb);
+                    SPM_CNT(8, ovf ? 1 : 0);
+                    if (nb == 0) SPM_CNT(9, 1);
+                }
+                SPM_CNT(7, __popc(need));
                 const int nx = -(seg.w - seg.y), ny = seg.z - seg.x;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -438,7 +447,10 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
                         vis = true;
                         if (px[k] != gl.x || py != gl.y)
                             for (int b = 0; b < nb && vis; ++b)
+                            {
                                 vis = !poly_blocks(sm.blk_v[b], sm.blk_m[b], px[k], py, gl.x, gl.y, sm.blk_mask[b]);
+                                SPM_CNT(10, 1);
+                            }
                     }
                     if (vis) key[k] = nk[k];
                 }
@@ -492,5 +504,20 @@ void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_
 }
 
 int count_kernel_launches_pixel() { return 1; }
+
+}  // namespace spm
+
+#ifdef SPM_COUNT
+// Instrumentation build only: reads and clears the work counters.
+extern "C" int spm_debug_counters(unsigned long long *out16) {
+    cudaDeviceSynchronize();
+    if (cudaMemcpyFromSymbol(out16, spm::g_count, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
+    unsigned long long z[16] = {0};
+    cudaMemcpyToSymbol(spm::g_count, z, sizeof z);
+    return 0;
+}
+#endif
+
+namespace spm {
 
 }  // namespace spm
