@@ -30,6 +30,8 @@ namespace {
 
 constexpr int kVisThreads = 256;
 constexpr int kSsspThreads = 256;
+constexpr int kSoloThreads = 512;
+constexpr int kSoloSmem = 200 * 1024;
 
 // Static filter + exact visibility for one (u, v) pair.
 __device__ bool pair_edge(const DevScene &ds, int u, int v) {
@@ -205,7 +207,17 @@ __device__ __forceinline__ void mark_out_warp(const DevScene &ds, int u, int lan
     }
 }
 
+// Shared-memory bytes the single-CTA fixpoint needs (0 if it cannot run).
+__device__ __forceinline__ int solo_bytes(const DevScene &ds) {
+    const long long n = ds.n_gen, E = ds.in_start[ds.n_vert];
+    if (n >= 32768 || E > ds.edge_cap) return 0;
+    const long long b = n * (8 + 4 + 8 + 1) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
+                        4 * ((n + 31) / 32) + 2 * 3 * n + n * (8 + 4) + 256;
+    return b <= kSoloSmem ? (int)b : 0;
+}
+
 __global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
+    if (solo_bytes(ds) > 0) return;  // the single-CTA kernel handles this graph
     cg::grid_group grid = cg::this_grid();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsize = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, gwarp = gtid >> 5, nwarps = gsize >> 5;
@@ -289,6 +301,143 @@ __global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
     if (gtid == 0) ds.stats[0] = round + 1;
 }
 
+// The same fixpoint in one CTA with the graph and the state in shared
+// memory, for graphs that fit (16-bit generator ids, cone directions packed
+// in 16-bit lanes -- lattice directions fit in 16 bits). A round costs two
+// __syncthreads instead of two grid barriers, which is what deep, sparse
+// graphs (mazes: hundreds of rounds, a few vertices each) need. Results are
+// identical to k_sssp: the same pulls over the same sets.
+__global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(DevScene ds, int max_rounds) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int bytes = solo_bytes(ds);
+    if (bytes == 0) return;
+    const int n = ds.n_gen, nv = ds.n_vert, E = ds.in_start[nv];
+    unsigned char *p = sm_raw;
+    auto take = [&](size_t sz) {
+        unsigned char *q = p;
+        p += (sz + 15) & ~(size_t)15;
+        return q;
+    };
+    double *cost = (double *)take(8 * n);
+    double *ncost = (double *)take(8 * n);
+    int *par = (int *)take(4 * n);
+    int *npar = (int *)take(4 * n);
+    short4 *cone = (short4 *)take(8 * n);
+    signed char *ctype = (signed char *)take(n);
+    int *in_start = (int *)take(4 * (nv + 1));
+    unsigned short *in_src = (unsigned short *)take(2 * E);
+    int *out_start = (int *)take(4 * (n + 1));
+    unsigned short *out_dst = (unsigned short *)take(2 * E);
+    unsigned *dirty = (unsigned *)take(4 * ((n + 31) / 32));
+    unsigned short *dl[2] = {(unsigned short *)take(2 * n), (unsigned short *)take(2 * n)};
+    unsigned short *fr = (unsigned short *)take(2 * n);
+    __shared__ int cnt[4];  // [0,1] dirty counts by parity, [2] changed count
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSoloThreads / 32;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
+    for (int i = tid; i <= n; i += kSoloThreads) out_start[i] = ds.out_start[i];
+    for (int i = tid; i < E; i += kSoloThreads) {
+        in_src[i] = (unsigned short)ds.in_src[i];
+        out_dst[i] = (unsigned short)ds.out_dst[i];
+    }
+    for (int g = tid; g < n; g += kSoloThreads) {
+        const bool src = g < ds.n_src;
+        cost[g] = src ? 0.0 : inf;
+        par[g] = src ? g : -1;
+        ctype[g] = (signed char)(src ? kConeNone : kConeEmpty);
+        cone[g] = make_short4(0, 0, 0, 0);
+    }
+    for (int w = tid; w < (n + 31) / 32; w += kSoloThreads) dirty[w] = 0u;
+    if (tid < 4) cnt[tid] = 0;
+    __syncthreads();
+    auto mark = [&](int u, unsigned short *list, int *count) {
+        for (int e = out_start[u] + lane; e < out_start[u + 1]; e += 32) {
+            const int v = out_dst[e];
+            const unsigned bit = 1u << (v & 31);
+            if (!(atomicOr(&dirty[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
+        }
+    };
+    for (int u = warp; u < ds.n_src; u += nwarps) mark(u, dl[0], &cnt[0]);
+    __syncthreads();
+    int round = 0;
+    for (;; ++round) {
+        const int par_r = round & 1, par_n = par_r ^ 1;
+        const int nd = cnt[par_r];
+        if (tid == 0) {
+            cnt[par_n] = 0;
+            cnt[2] = 0;
+        }
+        __syncthreads();
+        for (int i = warp; i < nd; i += nwarps) {
+            const int v = dl[par_r][i];
+            const int vv = v - ds.n_src;
+            if (lane == 0) atomicAnd(&dirty[v >> 5], ~(1u << (v & 31)));
+            const int2 vl = ds.gen_lat[v];
+            double best = inf;
+            int bpar = -1;
+            for (int e = in_start[vv] + lane; e < in_start[vv + 1]; e += 32) {
+                const int u = in_src[e];
+                const double cu = cost[u];
+                if (!(cu < inf)) continue;
+                const int ct = ctype[u];
+                if (ct != kConeNone) {
+                    const int2 ul = ds.gen_lat[u];
+                    const short4 c = cone[u];
+                    if (!in_cone(ct, make_int4(c.x, c.y, c.z, c.w), vl.x - ul.x, vl.y - ul.y)) continue;
+                }
+                const double cand = __dadd_rn(cu, ds.in_len[e]);
+                if (cand < best || (cand == best && u < bpar)) {
+                    best = cand;
+                    bpar = u;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
+                if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
+                    best = ob;
+                    bpar = op;
+                }
+            }
+            if (lane == 0 && (best != cost[v] || bpar != par[v])) {
+                ncost[v] = best;
+                npar[v] = bpar;
+                fr[atomicAdd(&cnt[2], 1)] = (unsigned short)v;
+            }
+        }
+        __syncthreads();
+        const int nc = cnt[2];
+        if (nc == 0) break;
+        if (round + 1 >= max_rounds) {
+            if (tid == 0) atomicOr(ds.status, kStNotConverged);
+            break;
+        }
+        for (int i = tid; i < nc; i += kSoloThreads) {
+            const int v = fr[i];
+            cost[v] = ncost[v];
+            const int pv = npar[v];
+            par[v] = pv;
+            int dx, dy;
+            arrival_dir(ds, pv, ds.gen_lat[v], dx, dy);
+            int4 c;
+            ctype[v] = (signed char)make_cone(ds.gen_wedge[v], dx, dy, c);
+            cone[v] = make_short4((short)c.x, (short)c.y, (short)c.z, (short)c.w);
+        }
+        __syncthreads();
+        for (int i = warp; i < nc; i += nwarps) mark(fr[i], dl[par_n], &cnt[par_n]);
+        __syncthreads();
+    }
+    for (int g = tid; g < n; g += kSoloThreads) {
+        ds.cost[0][g] = cost[g];
+        ds.par[0][g] = par[g];
+        const short4 c = cone[g];
+        ds.gen_cone[g] = make_int4(c.x, c.y, c.z, c.w);
+        ds.gen_ctype[g] = ctype[g];
+    }
+    if (tid == 0) ds.stats[0] = round + 1;
+}
+
 // Final generator table for the pixel phase: FP32 costs and shadow cones.
 __global__ void k_finalize(DevScene ds) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ds.n_gen; g += gridDim.x * blockDim.x) {
@@ -320,11 +469,13 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
     DevScene arg = ds;
     int max_rounds = 4 * ds.n_gen + 64;
     void *args[] = {&arg, &max_rounds};
+    k_sssp_solo<<<1, kSoloThreads, kSoloSmem, st>>>(ds, max_rounds);
     cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
     k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
 }
 
 int sssp_grid_blocks() {
+    cudaFuncSetAttribute(k_sssp_solo, cudaFuncAttributeMaxDynamicSharedMemorySize, kSoloSmem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
