@@ -179,6 +179,8 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=40_000,
                     help="oracle pixel sample per step for --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--culling", default="autotune", choices=["autotune", "flood", "scan", "auto"],
+                    help="culling mode: autotuned at set-up (default) or fixed")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -201,7 +203,11 @@ def main():
     import paper_1805_08500_gb300 as spm
 
     s = spm.Scene(scene)
-    tuning = s.autotune(cache_key=args.workload)  # set-up, not timed
+    if args.culling == "autotune":
+        tuning = s.autotune(cache_key=args.workload)  # set-up, not timed
+    else:
+        spm.spm_scene_set_tuning(s.handle, {"auto": 0, "flood": 1, "scan": 2}[args.culling], 32)
+        tuning = dict(s.tuning(), source="fixed")
     Nx, Ny = scene.grid
     npx = Nx * Ny
     d_out, p_out = s.empty_outputs()

@@ -53,6 +53,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    # a shared library links with unresolved symbols; refuse one that has any
+    # of our own (a declaration left without a definition)
+    und = subprocess.run(["nm", "-uC", tmp], capture_output=True, text=True).stdout
+    missing = [ln.strip() for ln in und.splitlines() if "spm" in ln]
+    if missing:
+        os.remove(tmp)
+        raise RuntimeError("unresolved library symbols: " + "; ".join(missing))
     os.replace(tmp, LIB)
     return LIB
 

@@ -219,9 +219,9 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         ds.use_flood = spm::flood_possible((int)ntiles) && spm::flood_smem_attr() ? 1 : 0;
         ds.flood_mode = 0;
         ds.hidden_chunk = 32;
-        ds.pair_cap = (int32_t)std::min<int64_t>(std::max<int64_t>((int64_t)hs.n_gen * ntiles / 2, 1),
-                                                 std::max<int64_t>(4 << 20, 64 * (int64_t)hs.n_gen));
-        if (!ds.use_flood) ds.pair_cap = 1;
+        const int64_t cap = std::min<int64_t>(std::max<int64_t>((int64_t)hs.n_gen * ntiles, 1),
+                                              std::max<int64_t>(4 << 20, 64 * (int64_t)hs.n_gen));
+        ds.pair_cap = ds.use_flood ? (int32_t)cap : 1;
         ds.tile_start = dalloc<int32_t>(s, ntiles + 1);
         ds.tile_count = dalloc<int32_t>(s, ntiles);
         ds.tile_items = dalloc<int32_t>(s, ds.pair_cap);

@@ -255,11 +255,20 @@ static __device__ unsigned long long g_count[16];  // one copy per translation u
 // corners of the pixel-centre box are hidden by the same polygon. Walks the
 // bins of the thick segment (tile centre -> g, radius r) from the tile side
 // and stops at the first such polygon.
-__device__ __forceinline__ bool box_hidden(const DevScene &ds, int2 g, int4 box, float cx, float cy, float r) {
-    return walk_bins(ds, cx, cy, (float)g.x, (float)g.y, r, [&](int bin) {
+__device__ __forceinline__ bool box_hidden(const DevScene &ds, int2 g, int4 box, float cx, float cy, float r,
+                                           float max_len = 3.4e38f) {
+    // walk toward g, optionally only the first max_len units (any subset of
+    // polygons keeps the test exact)
+    float tx = (float)g.x, ty = (float)g.y;
+    const float dx = tx - cx, dy = ty - cy, len = sqrtf(dx * dx + dy * dy);
+    if (len > max_len) {
+        tx = cx + dx * (max_len / len);
+        ty = cy + dy * (max_len / len);
+    }
+    return walk_bins(ds, cx, cy, tx, ty, r, [&](int bin) {
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
             const int k = ds.bin_items[it];
-            if (!seg_near_box(cx, cy, (float)g.x, (float)g.y, r, ds.poly_box[k])) continue;
+            if (!seg_near_box(cx, cy, tx, ty, r, ds.poly_box[k])) continue;
             const int b = ds.poly_off[k], m = ds.poly_off[k + 1] - b;
             const int2 *V = ds.poly_v + b;
             const unsigned mg = edge_mask(V, m, g.x, g.y);

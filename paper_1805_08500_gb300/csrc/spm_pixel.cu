@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
                     if (threadIdx.x < chunk && cc < nc) {
                         SPM_CNT(2, 1);
                         const int g2 = sm.cand_id[cc];
-                        sm.hidden[cc] = ds.gen_kind[g2] != kSegI &&
+                        // flooded lists were already tested on the whole tile area
+                        sm.hidden[cc] = !lists && ds.gen_kind[g2] != kSegI &&
                                         box_hidden(ds, ds.gen_lat[g2], box, bcx, bcy, brad);
                     }
                     tested += chunk;

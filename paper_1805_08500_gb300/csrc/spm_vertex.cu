@@ -174,8 +174,8 @@ __global__ void k_edges_fill(DevScene ds) {
 // in a phase where nobody reads it. Stops when no vertex changes, or at the
 // round cap (status bit). Deterministic: each pull is a min over a set.
 __device__ __forceinline__ void commit_vertex(const DevScene &ds, int v) {
-    ds.cost[0][v] = ds.cost[1][v];
-    const int p = ds.par[1][v];
+    ds.cost[0][v] = __ldcg(&ds.cost[1][v]);
+    const int p = __ldcg(&ds.par[1][v]);
     ds.par[0][v] = p;
     int dx, dy;
     arrival_dir(ds, p, ds.gen_lat[v], dx, dy);
@@ -246,25 +246,29 @@ __global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
             cnt[par_n] = 0;
             cnt[2 + par_n] = 0;
         }
-        const int nd = cnt[2 + par_r];
+        // data written by other CTAs since the last grid barrier is read
+        // through L2 (__ldcg): L1 is not coherent across SMs
+        const int nd = __ldcg(&cnt[2 + par_r]);
         const int32_t *dl = ds.dirtyl[par_r];
         for (int i = gwarp; i < nd; i += nwarps) {
-            const int v = dl[i];
+            const int v = __ldcg(&dl[i]);
             const int vv = v - ds.n_src;
             if (lane == 0) atomicAnd(&ds.dirty[v >> 5], ~(1u << (v & 31)));
             const int2 vl = ds.gen_lat[v];
-            double best = inf;
+            long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
             for (int e = ds.in_start[vv] + lane; e < ds.in_start[vv + 1]; e += 32) {
                 const int u = ds.in_src[e];
-                const double cu = ds.cost[0][u];
-                if (!(cu < inf)) continue;
-                const int ct = ds.gen_ctype[u];
+                const double cu = __ldcg(&ds.cost[0][u]);
+                if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;  // unreached
+                const int ct = __ldcg(&ds.gen_ctype[u]);
                 if (ct != kConeNone) {
                     const int2 ul = ds.gen_lat[u];
-                    if (!in_cone(ct, ds.gen_cone[u], vl.x - ul.x, vl.y - ul.y)) continue;
+                    if (!in_cone(ct, __ldcg(&ds.gen_cone[u]), vl.x - ul.x, vl.y - ul.y)) continue;
                 }
-                const double cand = __dadd_rn(cu, ds.in_len[e]);
+                // costs are non-negative, so their bit patterns order like
+                // their values: compare as integers, keep FP64 for the add
+                const long long cand = __double_as_longlong(__dadd_rn(cu, ds.in_len[e]));
                 if (cand < best || (cand == best && u < bpar)) {
                     best = cand;
                     bpar = u;
@@ -272,21 +276,21 @@ __global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
                 if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
                     best = ob;
                     bpar = op;
                 }
             }
-            if (lane == 0 && (best != ds.cost[0][v] || bpar != ds.par[0][v])) {
-                ds.cost[1][v] = best;
+            if (lane == 0 && (best != __double_as_longlong(__ldcg(&ds.cost[0][v])) || bpar != __ldcg(&ds.par[0][v]))) {
+                ds.cost[1][v] = __longlong_as_double(best);
                 ds.par[1][v] = bpar;
                 ds.frontier[par_r][atomicAdd(&cnt[par_r], 1)] = v;
             }
         }
         grid.sync();
-        const int nc = cnt[par_r];
+        const int nc = __ldcg(&cnt[par_r]);
         if (nc == 0) break;
         if (round + 1 >= max_rounds) {
             if (gtid == 0) atomicOr(ds.status, kStNotConverged);
@@ -294,8 +298,8 @@ __global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
         }
         // commit the changed vertices and mark their out-neighbours
         const int32_t *fr = ds.frontier[par_r];
-        for (int i = gtid; i < nc; i += gsize) commit_vertex(ds, fr[i]);
-        for (int i = gwarp; i < nc; i += nwarps) mark_out_warp(ds, fr[i], lane, ds.dirtyl[par_n], &cnt[2 + par_n]);
+        for (int i = gtid; i < nc; i += gsize) commit_vertex(ds, __ldcg(&fr[i]));
+        for (int i = gwarp; i < nc; i += nwarps) mark_out_warp(ds, __ldcg(&fr[i]), lane, ds.dirtyl[par_n], &cnt[2 + par_n]);
         grid.sync();
     }
     if (gtid == 0) ds.stats[0] = round + 1;
@@ -373,19 +377,21 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(DevScene ds, int max
             const int vv = v - ds.n_src;
             if (lane == 0) atomicAnd(&dirty[v >> 5], ~(1u << (v & 31)));
             const int2 vl = ds.gen_lat[v];
-            double best = inf;
+            long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
             for (int e = in_start[vv] + lane; e < in_start[vv + 1]; e += 32) {
                 const int u = in_src[e];
                 const double cu = cost[u];
-                if (!(cu < inf)) continue;
+                if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;  // unreached
                 const int ct = ctype[u];
                 if (ct != kConeNone) {
                     const int2 ul = ds.gen_lat[u];
                     const short4 c = cone[u];
                     if (!in_cone(ct, make_int4(c.x, c.y, c.z, c.w), vl.x - ul.x, vl.y - ul.y)) continue;
                 }
-                const double cand = __dadd_rn(cu, ds.in_len[e]);
+                // costs are non-negative, so their bit patterns order like
+                // their values: compare as integers, keep FP64 for the add
+                const long long cand = __double_as_longlong(__dadd_rn(cu, ds.in_len[e]));
                 if (cand < best || (cand == best && u < bpar)) {
                     best = cand;
                     bpar = u;
@@ -393,15 +399,15 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(DevScene ds, int max
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
                 if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
                     best = ob;
                     bpar = op;
                 }
             }
-            if (lane == 0 && (best != cost[v] || bpar != par[v])) {
-                ncost[v] = best;
+            if (lane == 0 && (best != __double_as_longlong(cost[v]) || bpar != par[v])) {
+                ncost[v] = __longlong_as_double(best);
                 npar[v] = bpar;
                 fr[atomicAdd(&cnt[2], 1)] = (unsigned short)v;
             }
