@@ -169,6 +169,19 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     }
     ds.bin_start = dupload(s, hs.bin_start, ok);
     ds.bin_items = dupload(s, hs.bin_items, ok);
+    {
+        std::vector<spm::BinRec> recs(hs.bin_items.size());
+        for (size_t i = 0; i < recs.size(); ++i) {
+            const int k = hs.bin_items[i];
+            recs[i].box = make_int4(hs.poly_box[4 * k], hs.poly_box[4 * k + 1], hs.poly_box[4 * k + 2],
+                                    hs.poly_box[4 * k + 3]);
+            recs[i].poly = k;
+            recs[i].voff = hs.poly_off[k];
+            recs[i].m = hs.poly_off[k + 1] - hs.poly_off[k];
+            recs[i].pad = 0;
+        }
+        ds.bin_recs = dupload(s, recs, ok);
+    }
     ds.gen_kind = dupload(s, hs.gen_kind, ok);
     ds.gen_aux = dupload(s, hs.gen_aux, ok);
     {

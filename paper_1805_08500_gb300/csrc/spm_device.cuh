@@ -196,12 +196,11 @@ __device__ __forceinline__ bool visible_points(const DevScene &ds, int px, int p
     int4 sb = make_int4(min(px, qx), min(py, qy), max(px, qx), max(py, qy));
     bool blocked = walk_bins(ds, (float)px, (float)py, (float)qx, (float)qy, 0.f, [&](int bin) {
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-            int k = ds.bin_items[it];
-            int4 bx = ds.poly_box[k];
+            const BinRec rec = ds.bin_recs[it];
+            const int4 bx = rec.box;
             if (bx.z < sb.x || bx.x > sb.z || bx.w < sb.y || bx.y > sb.w) continue;
-            int b = ds.poly_off[k], m = ds.poly_off[k + 1] - b;
-            const int2 *V = ds.poly_v + b;
-            if (poly_blocks(V, m, px, py, qx, qy, edge_mask(V, m, qx, qy))) return true;
+            const int2 *V = ds.poly_v + rec.voff;
+            if (poly_blocks(V, rec.m, px, py, qx, qy, edge_mask(V, rec.m, qx, qy))) return true;
         }
         return false;
     });
@@ -223,11 +222,11 @@ __device__ __forceinline__ bool visible_foot(const DevScene &ds, int s, int px, 
     const int nx = -uy, ny = ux;
     bool blocked = walk_bins(ds, (float)px, (float)py, fx, fy, 0.f, [&](int bin) {
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-            int k = ds.bin_items[it];
-            int4 bx = ds.poly_box[k];
+            const BinRec rec = ds.bin_recs[it];
+            const int4 bx = rec.box;
             if (bx.z < sb.x || bx.x > sb.z || bx.w < sb.y || bx.y > sb.w) continue;
-            int b = ds.poly_off[k], m = ds.poly_off[k + 1] - b;
-            const int2 *V = ds.poly_v + b;
+            const int m = rec.m;
+            const int2 *V = ds.poly_v + rec.voff;
             int oA[kMaxPolyVerts], oB[kMaxPolyVerts];
             for (int i = 0; i < m; ++i) {
                 int2 a = V[i], bb = V[i + 1 == m ? 0 : i + 1];
@@ -267,10 +266,10 @@ __device__ __forceinline__ bool box_hidden(const DevScene &ds, int2 g, int4 box,
     }
     return walk_bins(ds, cx, cy, tx, ty, r, [&](int bin) {
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-            const int k = ds.bin_items[it];
-            if (!seg_near_box(cx, cy, tx, ty, r, ds.poly_box[k])) continue;
-            const int b = ds.poly_off[k], m = ds.poly_off[k + 1] - b;
-            const int2 *V = ds.poly_v + b;
+            const BinRec rec = ds.bin_recs[it];
+            if (!seg_near_box(cx, cy, tx, ty, r, rec.box)) continue;
+            const int m = rec.m;
+            const int2 *V = ds.poly_v + rec.voff;
             const unsigned mg = edge_mask(V, m, g.x, g.y);
             if (poly_blocks(V, m, box.x, box.y, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.y, g.x, g.y, mg) &&
                 poly_blocks(V, m, box.x, box.w, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.w, g.x, g.y, mg))
@@ -278,6 +277,67 @@ __device__ __forceinline__ bool box_hidden(const DevScene &ds, int2 g, int4 box,
         }
         return false;
     });
+}
+
+// Warp-cooperative form of box_hidden (every lane must call it with the same
+// arguments): the thick segment from the box centre to g is cut into strips
+// one bin wide along its major axis; lane l takes strips l, l + 32, ...
+// (nearest the box first) and the warp stops at the first round in which
+// some lane found a polygon hiding all four corners.
+__device__ __forceinline__ bool box_hidden_warp(const DevScene &ds, int2 g, int4 box, float cx, float cy,
+                                                float r) {
+    const int lane = threadIdx.x & 31;
+    const float tx = (float)g.x, ty = (float)g.y;
+    const float bs = (float)ds.bin_size, m = r + 1.0f;
+    const bool xmaj = fabsf(tx - cx) >= fabsf(ty - cy);
+    // major axis: u (bins along it), minor: w
+    const float pu = xmaj ? cx : cy, pw = xmaj ? cy : cx, qu = xmaj ? tx : ty, qw = xmaj ? ty : tx;
+    const float ou = xmaj ? (float)ds.bin_x0 : (float)ds.bin_y0, ow = xmaj ? (float)ds.bin_y0 : (float)ds.bin_x0;
+    const int nu = xmaj ? ds.bin_nx : ds.bin_ny, nw = xmaj ? ds.bin_ny : ds.bin_nx;
+    auto bin_of = [&](float v, float o, int n) {
+        int b = (int)floorf((v - o) / bs);
+        return b < 0 ? 0 : (b >= n ? n - 1 : b);
+    };
+    const int u0 = bin_of(fminf(pu, qu) - m, ou, nu), u1 = bin_of(fmaxf(pu, qu) + m, ou, nu);
+    const int ustep = qu >= pu ? 1 : -1, us = ustep > 0 ? u0 : u1;
+    const int nstrips = u1 - u0 + 1;
+    const float du = qu - pu, dw = qw - pw;
+    for (int base = 0; base < nstrips; base += 32) {
+        bool found = false;
+        const int sidx = base + lane;
+        if (sidx < nstrips) {
+            const int u = us + ustep * sidx;
+            float wlo, whi;
+            if (fabsf(du) < 0.5f) {
+                wlo = fminf(pw, qw);
+                whi = fmaxf(pw, qw);
+            } else {
+                const float a = ou + u * bs - m, b = ou + (u + 1) * bs + m;
+                const float t0 = (a - pu) / du, t1 = (b - pu) / du;
+                float tl = fmaxf(0.f, fminf(t0, t1)), th = fminf(1.f, fmaxf(t0, t1));
+                if (tl > th) { tl = 0.f; th = 1.f; }
+                const float wa = pw + tl * dw, wb = pw + th * dw;
+                wlo = fminf(wa, wb);
+                whi = fmaxf(wa, wb);
+            }
+            const int w0 = bin_of(wlo - m, ow, nw), w1 = bin_of(whi + m, ow, nw);
+            for (int w = w0; w <= w1 && !found; ++w) {
+                const int bin = xmaj ? w * ds.bin_nx + u : u * ds.bin_nx + w;
+                for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1] && !found; ++it) {
+                    const BinRec rec = ds.bin_recs[it];
+                    if (!seg_near_box(cx, cy, tx, ty, r, rec.box)) continue;
+                    const int2 *V = ds.poly_v + rec.voff;
+                    const unsigned mg = edge_mask(V, rec.m, g.x, g.y);
+                    found = poly_blocks(V, rec.m, box.x, box.y, g.x, g.y, mg) &&
+                            poly_blocks(V, rec.m, box.z, box.y, g.x, g.y, mg) &&
+                            poly_blocks(V, rec.m, box.x, box.w, g.x, g.y, mg) &&
+                            poly_blocks(V, rec.m, box.z, box.w, g.x, g.y, mg);
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, found)) return true;
+    }
+    return false;
 }
 
 }  // namespace spm

@@ -103,31 +103,25 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
         }
         bool overflow = false;
         while (head < tail && !overflow) {
-            const int take = min(32, tail - head);
-            int t = -1;
-            if (lane < take) t = queue[(head + lane) % kQueue];
-            head += take;
-            bool ok = false;
-            const int cx = t >= 0 ? t % ds.tiles_x : 0, cy = t >= 0 ? t / ds.tiles_x : 0;
-            if (t >= 0) {
-                const int4 area = tile_area(ds, cx, cy);
-                ok = cone_meets_box(ct, cone, gl, area);
-                if (ok) {
-                    const float acx = 0.5f * ((float)area.x + (float)area.z), acy = 0.5f * ((float)area.y + (float)area.w);
-                    const float ar = 0.5f * sqrtf((float)(area.z - area.x) * (float)(area.z - area.x) +
-                                                  (float)(area.w - area.y) * (float)(area.w - area.y)) + 1.0f;
-                    ok = !box_hidden(ds, gl, area, acx, acy, ar);
+            // the whole warp tests one frontier tile (uniform control flow)
+            const int t = queue[head % kQueue];
+            ++head;
+            const int cx = t % ds.tiles_x, cy = t / ds.tiles_x;
+            const int4 area = tile_area(ds, cx, cy);
+            bool ok = cone_meets_box(ct, cone, gl, area);
+            if (ok) {
+                const float acx = 0.5f * ((float)area.x + (float)area.z), acy = 0.5f * ((float)area.y + (float)area.w);
+                const float ar = 0.5f * sqrtf((float)(area.z - area.x) * (float)(area.z - area.x) +
+                                              (float)(area.w - area.y) * (float)(area.w - area.y)) + 1.0f;
+                ok = !box_hidden_warp(ds, gl, area, acx, acy, ar);
+                if (lane == 0) {
                     SPM_CNT(11, 1);
                     SPM_CNT(12, ok ? 1 : 0);
                 }
             }
-            // emit (tile, g)
-            const unsigned em = __ballot_sync(0xffffffffu, ok);
-            int base = 0;
-            if (lane == 0 && em) base = atomicAdd(&ds.flood_counts[0], __popc(em));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (ok) {
-                const int slot = base + __popc(em & ((1u << lane) - 1u));
+            if (!ok) continue;
+            if (lane == 0) {  // emit (tile, g)
+                const int slot = atomicAdd(&ds.flood_counts[0], 1);
                 if (slot < ds.pair_cap) {
                     ds.pairs[slot] = make_int2(t, g);
                     atomicAdd(&ds.tile_count[t], 1);
@@ -135,20 +129,19 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
                     atomicOr(&ds.flood_counts[2], 1);
                 }
             }
-            // push the unvisited 8-neighbours of accepted tiles
-            for (int d = 0; d < 9; ++d) {
-                if (d == 4) continue;
-                const int nx = cx + d % 3 - 1, ny = cy + d / 3 - 1;
-                bool nfresh = false;
-                int nt = 0;
-                if (ok && nx >= 0 && ny >= 0 && nx < ds.tiles_x && ny < ds.tiles_y) {
+            // lanes 0..8 look at the 8-neighbours, fresh ones join the queue
+            bool nfresh = false;
+            int nt = 0;
+            if (lane < 9 && lane != 4) {
+                const int nx = cx + lane % 3 - 1, ny = cy + lane / 3 - 1;
+                if (nx >= 0 && ny >= 0 && nx < ds.tiles_x && ny < ds.tiles_y) {
                     nt = ny * ds.tiles_x + nx;
                     nfresh = !(atomicOr(&visited[nt >> 5], 1u << (nt & 31)) & (1u << (nt & 31)));
                 }
-                const unsigned pb = __ballot_sync(0xffffffffu, nfresh);
-                if (nfresh) queue[(tail + __popc(pb & ((1u << lane) - 1u))) % kQueue] = nt;
-                tail += __popc(pb);
             }
+            const unsigned pb = __ballot_sync(0xffffffffu, nfresh);
+            if (nfresh) queue[(tail + __popc(pb & ((1u << lane) - 1u))) % kQueue] = nt;
+            tail += __popc(pb);
             if (tail - head > kQueue) overflow = true;
         }
         if (overflow && lane == 0) {

@@ -64,6 +64,13 @@ spm_status prepare_scene(const spm_scene_desc &d, HostScene &hs, std::string &er
 spm_status update_sources(HostScene &hs, const float *pts, const float *segs,
                           std::string &err);
 
+// One polygon entry of a bin, packed so a walk needs a single 32-byte load
+// per polygon instead of a chain (id -> box -> offset -> vertices).
+struct __align__(16) BinRec {
+    int4 box;
+    int32_t poly, voff, m, pad;
+};
+
 // Device pointers of one scene (all allocated at creation).
 struct DevScene {
     int32_t Wx, Wy, Nx, Ny, S;
@@ -75,6 +82,7 @@ struct DevScene {
     const int4 *poly_box;
     int32_t bin_x0, bin_y0, bin_size, bin_nx, bin_ny;
     const int32_t *bin_start, *bin_items;
+    const BinRec *bin_recs;            // parallel to bin_items
     // generators (static part)
     const int32_t *gen_kind;
     const int2 *gen_lat;

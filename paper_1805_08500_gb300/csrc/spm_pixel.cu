@@ -204,21 +204,20 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
         for (int row = r0; row <= r1; ++row) {
             const int bin = row * ds.bin_nx + col;
             for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-                const int k = ds.bin_items[it];
+                const BinRec rec = ds.bin_recs[it];
+                const int k = rec.poly;
                 if (dedup) {
                     const unsigned bit = 1u << (k & 31);
                     if (atomicOr(&sm.dedup[k >> 5], bit) & bit) continue;
                 }
-                if (!seg_near_box(cx, cy, tx, ty, r, ds.poly_box[k])) continue;
-                if (kind != kSegI &&
-                    !poly_meets_hull(ds.poly_v + ds.poly_off[k], ds.poly_off[k + 1] - ds.poly_off[k], box, tl.x, tl.y))
-                    continue;
+                if (!seg_near_box(cx, cy, tx, ty, r, rec.box)) continue;
+                if (kind != kSegI && !poly_meets_hull(ds.poly_v + rec.voff, rec.m, box, tl.x, tl.y)) continue;
                 const int slot = atomicAdd(&sm.n_block, 1);
                 if (slot >= kBlockCap) {
                     sm.overflow = 1;
                     continue;
                 }
-                const int b = ds.poly_off[k], nv = ds.poly_off[k + 1] - b;
+                const int b = rec.voff, nv = rec.m;
                 sm.blk_m[slot] = nv;
                 for (int i = 0; i < nv; ++i) sm.blk_v[slot][i] = ds.poly_v[b + i];
                 if (kind == kSegI) {
@@ -265,10 +264,10 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
         if (bx < 0 || by < 0 || bx >= ds.bin_nx || by >= ds.bin_ny) continue;
         const int bin = by * ds.bin_nx + bx;
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-            const int q = ds.bin_items[it];
-            const int4 b4 = ds.poly_box[q];
+            const BinRec rec = ds.bin_recs[it];
+            const int4 b4 = rec.box;
             if (px[k] <= b4.x || px[k] >= b4.z || py <= b4.y || py >= b4.w) continue;
-            const int b = ds.poly_off[q], m = ds.poly_off[q + 1] - b;
+            const int b = rec.voff, m = rec.m;
             bool inside = true;
             for (int e = 0; e < m && inside; ++e) {
                 const int2 a = ds.poly_v[b + e], c = ds.poly_v[b + (e + 1 == m ? 0 : e + 1)];
