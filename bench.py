@@ -44,6 +44,8 @@ def workload(name: str):
         return sg.maze(0), "maze 64x64 cells, 4096^2 px, 16384^2 world, 1 segment + 4 points"
     if name == "maze2048":
         return sg.maze(0, cells=32, N=2048), "maze 32x32 cells, 2048^2 px, 8192^2 world, 1 segment + 4 points"
+    if name == "batched256":
+        return sg.batched(0), "256 scenes, side uniform in {128,256,512,1024} over 4096^2, 10-500 convex polygons, 1-6 point/segment sources"
     if name == "polys1024":
         return sg.plain_polys(0), "200 convex polygons, 1024^2 px, 4096^2 world, 3 points + 2 segments"
     if name == "rects256":
@@ -166,6 +168,47 @@ def run_reference(args, cfg_desc, scene):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, cfg_desc, scenes):
+    """Batched form: all scenes in one batch (batched vertex phase, one
+    persistent pixel kernel, replayed from a CUDA graph); value = scenes/s."""
+    import torch
+    import paper_1805_08500_gb300 as spm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    objs = [spm.Scene(sc) for sc in scenes]
+    for o in objs:
+        spm.spm_scene_set_tuning(o.handle, 2, 32)
+    batch = spm.Batch(objs)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    npx = sum(sc.grid[0] * sc.grid[1] for sc in scenes)
+    for _ in range(args.warmup):
+        batch.compute(stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            batch.compute(stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    for o in objs:
+        o.sync()
+    total_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+    ms = total_ms / args.steps
+    line = {"metric": "SPM batched scenes/s", "value": len(scenes) / (ms * 1e-3), "unit": "scenes/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
+            "config": {"workload": "batched256", "scene": cfg_desc, "scenes": len(scenes),
+                       "pixels": npx, "l2": "flushed between timed steps (256 MiB write)",
+                       "launch": "one CUDA graph per step"},
+            "mpixel_per_s": npx / (ms * 1e-3) / 1e6, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,7 +216,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maze4096",
-                    choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048"])
+                    choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048", "batched256"])
     ap.add_argument("--cpu-pixels", type=int, default=200_000,
                     help="oracle pixel sample for the cpu_baseline leg")
     ap.add_argument("--ref-pixels", type=int, default=40_000,
@@ -187,6 +230,9 @@ def main():
     scene, cfg_desc = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg_desc, scene)
+        return
+    if args.workload == "batched256":
+        run_batched(args, cfg_desc, scene)
         return
 
     import torch

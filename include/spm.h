@@ -113,9 +113,25 @@ spm_status spm_compute_host(spm_scene *scene, void *stream, float *dist_host,
 /* Computes n independent scenes in one batched, persistent launch sequence
  * (all scenes' vertex phases, then one persistent pixel kernel over every
  * scene's tiles, largest first). dist[k] / parent[k] are caller-owned device
- * buffers of scene k's grid. All scenes must live on the current device. */
+ * buffers of scene k's grid. All scenes must live on the current device.
+ * Convenience form of spm_batch_create + spm_batch_compute +
+ * spm_batch_destroy: it allocates the batch descriptors and waits for the
+ * stream before returning; keep an spm_batch for repeated calls. */
 spm_status spm_compute_batched(spm_scene *const *scenes, int32_t n, void *stream,
                                float *const *dist, int32_t *const *parent);
+
+/* A batch: n scenes computed together by one launch sequence (vertex phase of
+ * every scene in batched kernels, then one persistent pixel kernel over all
+ * scenes' tiles, largest scenes first), captured once into a CUDA graph and
+ * replayed by spm_batch_compute. dist[k] / parent[k] are caller-owned device
+ * buffers of scene k's grid, fixed for the batch's lifetime. Creation
+ * allocates the batch's device descriptors; compute allocates nothing. The
+ * scenes must outlive the batch; culling settings are read at creation. */
+typedef struct spm_batch spm_batch;
+spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *dist,
+                            int32_t *const *parent, spm_batch **out);
+spm_status spm_batch_compute(spm_batch *batch, void *stream);
+void spm_batch_destroy(spm_batch *batch);
 
 /* Waits for the scene's last work on `stream` and returns the first latched
  * device-side or CUDA error (SPM_OK if none), clearing it. */

@@ -82,6 +82,9 @@ def load_library():
         "spm_compute": ([P, P, P, P], I32),
         "spm_compute_host": ([P, P, P, P], I32),
         "spm_compute_batched": ([P, I32, P, P, P], I32),
+        "spm_batch_create": ([P, I32, P, P, P], I32),
+        "spm_batch_compute": ([P, P], I32),
+        "spm_batch_destroy": ([P], None),
         "spm_scene_sync": ([P, P], I32),
         "spm_query_parent": ([P, F, F, P, P], I32),
         "spm_extract_path": ([P, F, F, P, I32, P], I32),
@@ -188,6 +191,50 @@ def spm_compute_batched(handles, stream, dists, parents):
     Pp = (ctypes.c_void_p * n)(*[_ptr(p) for p in parents])
     _check(load_library().spm_compute_batched(H, n, _stream_handle(stream), D, Pp),
            "spm_compute_batched")
+
+
+def spm_batch_create(handles, dists, parents):
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*handles)
+    D = (ctypes.c_void_p * n)(*[_ptr(d) for d in dists])
+    Pp = (ctypes.c_void_p * n)(*[_ptr(p) for p in parents])
+    out = ctypes.c_void_p()
+    _check(load_library().spm_batch_create(H, n, D, Pp, ctypes.byref(out)), "spm_batch_create")
+    return out.value
+
+
+def spm_batch_compute(batch, stream=None):
+    _check(load_library().spm_batch_compute(batch, _stream_handle(stream)), "spm_batch_compute")
+
+
+def spm_batch_destroy(batch):
+    if batch:
+        load_library().spm_batch_destroy(batch)
+
+
+class Batch:
+    """Scenes computed together; outputs are torch tensors, one pair per scene."""
+
+    def __init__(self, scenes):
+        self.scenes = list(scenes)
+        self.outputs = [s.empty_outputs() for s in self.scenes]
+        self.handle = spm_batch_create([s.handle for s in self.scenes],
+                                       [o[0] for o in self.outputs], [o[1] for o in self.outputs])
+
+    def compute(self, stream=None):
+        spm_batch_compute(self.handle, stream)
+        return self.outputs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def spm_scene_sync(handle, stream=None):

@@ -206,7 +206,8 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     ds.in_start = dalloc<int32_t>(s, hs.n_vert + 1);
     ds.out_start = dalloc<int32_t>(s, hs.n_gen + 1);
     ds.out_fill = dalloc<int32_t>(s, hs.n_gen);
-    ds.edge_cap = std::min<int64_t>((int64_t)hs.n_gen * hs.n_vert, (int64_t)1 << 26);
+    ds.edge_cap = std::min<int64_t>(std::min<int64_t>((int64_t)hs.n_gen * hs.n_vert, (int64_t)1 << 26),
+                                    std::max<int64_t>(1 << 20, 128 * (int64_t)hs.n_gen));
     ds.in_src = dalloc<int32_t>(s, ds.edge_cap);
     ds.in_len = dalloc<double>(s, ds.edge_cap);
     ds.out_dst = dalloc<int32_t>(s, ds.edge_cap);
@@ -355,14 +356,168 @@ spm_status spm_compute_host(spm_scene *s, void *stream, float *dist_host, int32_
     return spm_scene_sync(s, stream);
 }
 
-spm_status spm_compute_batched(spm_scene *const *scenes, int32_t n, void *stream, float *const *dist,
-                               int32_t *const *parent) {
-    if (n < 0 || (n > 0 && (!scenes || !dist || !parent))) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null argument");
+}  // extern "C"
+
+struct spm_batch {
+    std::vector<spm_scene *> scenes;
+    int device = 0;
+    std::vector<void *> allocs;
+    spm::BatchDev dev{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    bool capture_failed = false;
+};
+
+namespace {
+template <class T>
+T *balloc(spm_batch *b, size_t n) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) return nullptr;
+    b->allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+template <class T>
+T *bupload(spm_batch *b, const std::vector<T> &v, bool &ok) {
+    T *p = balloc<T>(b, v.size());
+    if (!p) {
+        ok = false;
+        return nullptr;
+    }
+    if (!v.empty() && cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+    return p;
+}
+void batch_free(spm_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (void *p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+}
+void batch_launch(spm_batch *b, cudaStream_t st) {
+    spm::launch_vertex_phase_batched(b->dev, st);
+    spm::launch_pixel_phase_batched(b->dev, st);
+}
+}  // namespace
+
+extern "C" {
+
+spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *dist, int32_t *const *parent,
+                            spm_batch **out) {
+    if (!out || n <= 0 || !scenes || !dist || !parent) return set_err(nullptr, SPM_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_err(nullptr, SPM_ERR_CUDA, "no CUDA device");
+    for (int k = 0; k < n; ++k)
+        if (!scenes[k] || !dist[k] || !parent[k] || scenes[k]->device != dev)
+            return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene/buffer or scene on another device");
+    spm_batch *b = new (std::nothrow) spm_batch();
+    if (!b) return set_err(nullptr, SPM_ERR_OOM, "host allocation failed");
+    b->scenes.assign(scenes, scenes + n);
+    b->device = dev;
+    std::vector<spm::DevScene> descs(n);
+    std::vector<long long> pair_off(n + 1, 0);
+    std::vector<int32_t> vert_off(n + 1, 0), gen_off(n + 1, 0), order(n), tile_off(n + 1, 0);
+    std::vector<float *> dv(dist, dist + n);
+    std::vector<int32_t *> pv(parent, parent + n);
+    int max_gen = 0;
     for (int k = 0; k < n; ++k) {
-        spm_status st = spm_compute(scenes[k], stream, dist[k], parent[k]);
-        if (st != SPM_OK) return st;
+        descs[k] = scenes[k]->ds;
+        pair_off[k + 1] = pair_off[k] + (long long)descs[k].n_vert * descs[k].vis_words;
+        vert_off[k + 1] = vert_off[k] + descs[k].n_vert;
+        gen_off[k + 1] = gen_off[k] + descs[k].n_gen;
+        max_gen = std::max(max_gen, descs[k].n_gen);
+        order[k] = k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (long long)descs[a].tiles_x * descs[a].tiles_y > (long long)descs[c].tiles_x * descs[c].tiles_y;
+    });
+    for (int k = 0; k < n; ++k)
+        tile_off[k + 1] = tile_off[k] + descs[order[k]].tiles_x * descs[order[k]].tiles_y;
+    bool ok = true;
+    spm::BatchDev &bd = b->dev;
+    bd.n = n;
+    bd.scenes = bupload(b, descs, ok);
+    bd.pair_off = bupload(b, pair_off, ok);
+    bd.vert_off = bupload(b, vert_off, ok);
+    bd.gen_off = bupload(b, gen_off, ok);
+    bd.order = bupload(b, order, ok);
+    bd.tile_off = bupload(b, tile_off, ok);
+    bd.total_tiles = tile_off[n];
+    bd.tile_counter = balloc<int32_t>(b, 1);
+    bd.dist = bupload(b, dv, ok);
+    bd.parent = bupload(b, pv, ok);
+    for (int k = 0; k < 2; ++k) {
+        bd.dirtyl[k] = balloc<int2>(b, gen_off[n]);
+        bd.frontier[k] = balloc<int2>(b, gen_off[n]);
+    }
+    bd.counters = balloc<int32_t>(b, 8);
+    bd.max_rounds = 4 * max_gen + 64;
+    bd.sssp_blocks = spm::sssp_batched_grid_blocks();
+    for (void *p : b->allocs) ok &= p != nullptr;
+    if (!ok) {
+        batch_free(b);
+        delete b;
+        return set_err(nullptr, SPM_ERR_OOM, "batch allocation failed");
+    }
+    *out = b;
+    return SPM_OK;
+}
+
+spm_status spm_batch_compute(spm_batch *b, void *stream) {
+    if (!b) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null batch");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return set_err(nullptr, SPM_ERR_INVALID_ARG, "batch used on another device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!b->exec && !b->capture_failed && st != nullptr) {  // capture once into a CUDA graph
+        cudaGraph_t g = nullptr;
+        bool okc = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (okc) {
+            batch_launch(b, st);
+            okc = cudaStreamEndCapture(st, &g) == cudaSuccess && g != nullptr;
+        }
+        if (okc && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+            b->graph = g;
+        } else {
+            if (g) cudaGraphDestroy(g);
+            b->exec = nullptr;
+            b->capture_failed = true;
+            cudaGetLastError();  // clear a capture error; fall back to direct launches
+        }
+    }
+    if (b->exec) {
+        if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return set_err(nullptr, SPM_ERR_CUDA, "graph launch failed");
+    } else {
+        batch_launch(b, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(nullptr, SPM_ERR_CUDA, cudaGetErrorString(e));
+    for (size_t k = 0; k < b->scenes.size(); ++k) {
+        spm_scene *s = b->scenes[k];
+        s->last_dist = nullptr;  // queries need a single-scene compute
+        s->ev_valid = false;
     }
     return SPM_OK;
+}
+
+void spm_batch_destroy(spm_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+}
+
+spm_status spm_compute_batched(spm_scene *const *scenes, int32_t n, void *stream, float *const *dist,
+                               int32_t *const *parent) {
+    if (n == 0) return SPM_OK;
+    spm_batch *b = nullptr;
+    spm_status st = spm_batch_create(scenes, n, dist, parent, &b);
+    if (st != SPM_OK) return st;
+    st = spm_batch_compute(b, stream);
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && st == SPM_OK)
+        st = set_err(nullptr, SPM_ERR_CUDA, "synchronisation failed");
+    spm_batch_destroy(b);
+    return st;
 }
 
 spm_status spm_query_parent(spm_scene *s, float x, float y, int32_t *parent, float *dist) {

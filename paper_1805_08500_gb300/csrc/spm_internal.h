@@ -134,10 +134,36 @@ struct DevScene {
     int32_t n_agents;
 };
 
+// A batch of scenes computed together (device-side descriptor).
+struct BatchDev {
+    int32_t n;                         // scenes
+    const DevScene *scenes;            // n descriptors (device memory)
+    // prefix offsets over scenes (n + 1 entries each)
+    const long long *pair_off;         // warp tasks of the visibility pairs: n_vert * vis_words
+    const int32_t *vert_off;           // obstacle-vertex generators
+    const int32_t *gen_off;            // generators
+    // pixel pass: scenes in processing order (most tiles first)
+    const int32_t *order;              // n scene indices
+    const int32_t *tile_off;           // n + 1 prefix of tiles in that order
+    int32_t total_tiles;
+    int32_t *tile_counter;             // persistent-kernel work counter
+    float *const *dist;                // n output planes (device pointers)
+    int32_t *const *parent;
+    // fixpoint over all scenes: (scene, vertex) lists and counters
+    int2 *dirtyl[2];
+    int2 *frontier[2];
+    int32_t *counters;                 // [0,1] frontier sizes, [2,3] dirty sizes, [4] rounds
+    int32_t max_rounds;
+    int32_t sssp_blocks;
+};
+
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent);
 void launch_flood(const DevScene &ds, cudaStream_t st);
+void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);
+void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);
+int sssp_batched_grid_blocks();
 bool flood_possible(int tiles);
 int flood_smem_attr();
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel

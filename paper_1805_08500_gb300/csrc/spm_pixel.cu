@@ -234,10 +234,10 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
     }
 }
 
-__global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ dist,
-                                               int32_t *__restrict__ parent) {
-    __shared__ PixSmem sm;
-    const int tile = blockIdx.x;
+// One 32 x 32 tile of one scene, by one CTA. allow_lists = false ignores
+// flooded candidate lists (the batched form scans every generator).
+__device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, float *__restrict__ dist,
+                                           int32_t *__restrict__ parent, PixSmem &sm, const bool allow_lists) {
     const int i0 = (tile % ds.tiles_x) * T, j0 = (tile / ds.tiles_x) * T;
     const int row = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
     const int j = j0 + row;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
     __syncthreads();
     // candidate source: the tile's flooded list plus the global list, or every
     // generator when the lists are unavailable
-    const bool lists = ds.use_flood && ds.flood_counts[2] == 0;
+    const bool lists = allow_lists && ds.use_flood && ds.flood_counts[2] == 0;
     const int tix = tile;
     const int l0 = lists ? ds.tile_start[tix] : 0;
     const int nlist = lists ? ds.tile_start[tix + 1] - l0 : 0;
@@ -496,11 +496,60 @@ __global__ void __launch_bounds__(NT) k_pixels(DevScene ds, float *__restrict__ 
     }
 }
 
+__global__ void __launch_bounds__(NT) k_pixels(const __grid_constant__ DevScene ds, float *__restrict__ dist,
+                                               int32_t *__restrict__ parent) {
+    __shared__ PixSmem sm;
+    pixel_tile(ds, blockIdx.x, dist, parent, sm, true);
+}
+
+// Persistent form over a batch of scenes: each CTA takes the next
+// (scene, tile) from a global counter (scenes ordered largest first), copies
+// that scene's descriptor into shared memory and runs the same tile code.
+__global__ void __launch_bounds__(NT) k_pixels_batched(const __grid_constant__ BatchDev b) {
+    __shared__ PixSmem sm;
+    __shared__ DevScene sds;
+    __shared__ int cur, cur_scene;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(b.tile_counter, 1);
+            cur = t;
+            if (t < b.total_tiles) {
+                int lo = 0, hi = b.n;  // last order index with tile_off <= t
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (b.tile_off[mid] <= t) lo = mid;
+                    else hi = mid;
+                }
+                cur_scene = lo;
+            }
+        }
+        __syncthreads();
+        const int t = cur;
+        if (t >= b.total_tiles) break;
+        const int oi = cur_scene, sc = b.order[oi];
+        for (int w = threadIdx.x; w < (int)(sizeof(DevScene) / 4); w += NT)
+            reinterpret_cast<int *>(&sds)[w] = reinterpret_cast<const int *>(&b.scenes[sc])[w];
+        __syncthreads();
+        pixel_tile(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, false);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent) {
     const int tiles = ds.tiles_x * ds.tiles_y;
     k_pixels<<<tiles, NT, 0, st>>>(ds, dist, parent);
+}
+
+void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st) {
+    cudaMemsetAsync(b.tile_counter, 0, sizeof(int32_t), st);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pixels_batched, NT, 0);
+    const int grid = max(1, min(b.total_tiles, sms * max(per_sm, 1)));
+    k_pixels_batched<<<grid, NT, 0, st>>>(b);
 }
 
 int count_kernel_launches_pixel() { return 1; }

@@ -57,24 +57,27 @@ __device__ bool pair_edge(const DevScene &ds, int u, int v) {
     return visible_points(ds, vl.x, vl.y, ul.x, ul.y);
 }
 
-// Row v (vertex index) of the bit matrix, word w covers generators 32w..32w+31.
-__global__ void __launch_bounds__(kVisThreads) k_vis_pairs(DevScene ds) {
+// One warp task: row vv (vertex index) of the bit matrix, word w covering
+// generators 32w..32w+31.
+__device__ __forceinline__ void vis_pairs_task(const DevScene &ds, long long t, int lane) {
+    const int vv = (int)(t / ds.vis_words), w = (int)(t % ds.vis_words);
+    const int u = w * 32 + lane, v = ds.n_src + vv;
+    const bool e = (u < ds.n_gen) && pair_edge(ds, u, v);
+    const unsigned bits = __ballot_sync(0xffffffffu, e);
+    if (lane == 0) ds.vis_bits[(size_t)vv * ds.vis_words + w] = bits;
+}
+
+__global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds) {
     const int lane = threadIdx.x & 31;
     const long long tasks = (long long)ds.n_vert * ds.vis_words;
     const long long warps = (long long)gridDim.x * (kVisThreads / 32);
-    for (long long t = (long long)blockIdx.x * (kVisThreads / 32) + (threadIdx.x >> 5); t < tasks;
-         t += warps) {
-        const int vv = (int)(t / ds.vis_words), w = (int)(t % ds.vis_words);
-        const int u = w * 32 + lane, v = ds.n_src + vv;
-        bool e = (u < ds.n_gen) && pair_edge(ds, u, v);
-        unsigned bits = __ballot_sync(0xffffffffu, e);
-        if (lane == 0) ds.vis_bits[(size_t)vv * ds.vis_words + w] = bits;
-    }
+    for (long long t = (long long)blockIdx.x * (kVisThreads / 32) + (threadIdx.x >> 5); t < tasks; t += warps)
+        vis_pairs_task(ds, t, lane);
 }
 
 // In-degree per vertex row and out-degree per generator.
-__global__ void k_edges_count(DevScene ds) {
-    for (int vv = blockIdx.x * blockDim.x + threadIdx.x; vv < ds.n_vert; vv += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void edges_count_row(const DevScene &ds, int vv) {
+    {
         const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
         int cnt = 0;
         for (int w = 0; w < ds.vis_words; ++w) {
@@ -90,9 +93,13 @@ __global__ void k_edges_count(DevScene ds) {
     }
 }
 
+__global__ void k_edges_count(const __grid_constant__ DevScene ds) {
+    for (int vv = blockIdx.x * blockDim.x + threadIdx.x; vv < ds.n_vert; vv += gridDim.x * blockDim.x)
+        edges_count_row(ds, vv);
+}
+
 // Exclusive scans of in_start (n_vert + 1) and out_start (n_gen + 1), one CTA.
-__global__ void __launch_bounds__(1024) k_edges_scan(DevScene ds) {
-    __shared__ long long part[1024];
+__device__ __forceinline__ void edges_scan_block(const DevScene &ds, long long *part) {
     for (int which = 0; which < 2; ++which) {
         int32_t *a = which == 0 ? ds.in_start : ds.out_start;
         const int n = which == 0 ? ds.n_vert : ds.n_gen;  // entries 1..n hold counts
@@ -126,6 +133,11 @@ __global__ void __launch_bounds__(1024) k_edges_scan(DevScene ds) {
     }
 }
 
+__global__ void __launch_bounds__(1024) k_edges_scan(const __grid_constant__ DevScene ds) {
+    __shared__ long long part[1024];
+    edges_scan_block(ds, part);
+}
+
 __device__ __forceinline__ double edge_len(const DevScene &ds, int u, int v) {
     const float2 vp = ds.gen_pos[v];
     if (ds.gen_kind[u] == kSegI) {
@@ -140,9 +152,8 @@ __device__ __forceinline__ double edge_len(const DevScene &ds, int u, int v) {
     return __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
 }
 
-__global__ void k_edges_fill(DevScene ds) {
-    if (ds.in_start[ds.n_vert] > ds.edge_cap) return;
-    for (int vv = blockIdx.x * blockDim.x + threadIdx.x; vv < ds.n_vert; vv += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void edges_fill_row(const DevScene &ds, int vv) {
+    {
         const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
         int e = ds.in_start[vv];
         const int v = ds.n_src + vv;
@@ -159,6 +170,12 @@ __global__ void k_edges_fill(DevScene ds) {
             }
         }
     }
+}
+
+__global__ void k_edges_fill(const __grid_constant__ DevScene ds) {
+    if (ds.in_start[ds.n_vert] > ds.edge_cap) return;
+    for (int vv = blockIdx.x * blockDim.x + threadIdx.x; vv < ds.n_vert; vv += gridDim.x * blockDim.x)
+        edges_fill_row(ds, vv);
 }
 
 // Jacobi rounds of the fixpoint on the whole GPU (cooperative launch, two
@@ -216,7 +233,7 @@ __device__ __forceinline__ int solo_bytes(const DevScene &ds) {
     return b <= kSoloSmem ? (int)b : 0;
 }
 
-__global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
+__global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene ds, int max_rounds) {
     if (solo_bytes(ds) > 0) return;  // the single-CTA kernel handles this graph
     cg::grid_group grid = cg::this_grid();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsize = gridDim.x * blockDim.x;
@@ -311,7 +328,7 @@ __global__ void __launch_bounds__(256) k_sssp(DevScene ds, int max_rounds) {
 // __syncthreads instead of two grid barriers, which is what deep, sparse
 // graphs (mazes: hundreds of rounds, a few vertices each) need. Results are
 // identical to k_sssp: the same pulls over the same sets.
-__global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(DevScene ds, int max_rounds) {
+__global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int bytes = solo_bytes(ds);
     if (bytes == 0) return;
@@ -445,13 +462,212 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(DevScene ds, int max
 }
 
 // Final generator table for the pixel phase: FP32 costs and shadow cones.
-__global__ void k_finalize(DevScene ds) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ds.n_gen; g += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void finalize_gen(const DevScene &ds, int g) {
+    {
         const double c = ds.cost[0][g];
         const int p = ds.par[0][g];
         ds.gen_cost[g] = c;
         ds.gen_par[g] = p;
         ds.gen_costf[g] = (float)c;
+    }
+}
+
+__global__ void k_finalize(const __grid_constant__ DevScene ds) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ds.n_gen; g += gridDim.x * blockDim.x)
+        finalize_gen(ds, g);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: the same per-scene work for every scene of a batch in one
+// launch per step. Global task indices map to (scene, local index) through
+// prefix offsets (binary search over scenes).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ int scene_of(const T *off, int n, T x) {
+    int lo = 0, hi = n;  // last scene with off[s] <= x
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
+    const int total = b.gen_off[b.n];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total + b.n; i += gridDim.x * blockDim.x) {
+        // entries 0..total-1: one per generator; total..total+n-1: one per scene
+        if (i < total) {
+            const int s = scene_of(b.gen_off, b.n, i);
+            const DevScene &ds = b.scenes[s];
+            const int g = i - b.gen_off[s];
+            ds.out_start[g + 1] = 0;
+            ds.out_fill[g] = 0;
+        } else {
+            const DevScene &ds = b.scenes[i - total];
+            ds.out_start[0] = 0;
+            if (ds.n_vert == 0) ds.in_start[0] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kVisThreads) k_vis_pairs_b(const __grid_constant__ BatchDev b) {
+    const int lane = threadIdx.x & 31;
+    const long long tasks = b.pair_off[b.n];
+    const long long warps = (long long)gridDim.x * (kVisThreads / 32);
+    for (long long t = (long long)blockIdx.x * (kVisThreads / 32) + (threadIdx.x >> 5); t < tasks; t += warps) {
+        const int s = scene_of(b.pair_off, b.n, t);
+        vis_pairs_task(b.scenes[s], t - b.pair_off[s], lane);
+    }
+}
+
+__global__ void k_edges_count_b(const __grid_constant__ BatchDev b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.vert_off[b.n]; i += gridDim.x * blockDim.x) {
+        const int s = scene_of(b.vert_off, b.n, i);
+        edges_count_row(b.scenes[s], i - b.vert_off[s]);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_edges_scan_b(const __grid_constant__ BatchDev b) {
+    __shared__ long long part[1024];
+    const DevScene &ds = b.scenes[blockIdx.x];
+    if (ds.n_vert > 0) edges_scan_block(ds, part);
+}
+
+__global__ void k_edges_fill_b(const __grid_constant__ BatchDev b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.vert_off[b.n]; i += gridDim.x * blockDim.x) {
+        const int s = scene_of(b.vert_off, b.n, i);
+        const DevScene &ds = b.scenes[s];
+        if (ds.in_start[ds.n_vert] > ds.edge_cap) continue;
+        edges_fill_row(ds, i - b.vert_off[s]);
+    }
+}
+
+__device__ __forceinline__ void mark_out_warp_b(const DevScene &ds, int s, int u, int lane, int2 *dl,
+                                                int32_t *dcount) {
+    const int e0 = ds.out_start[u], e1 = ds.out_start[u + 1];
+    for (int eb = e0; eb < e1; eb += 32) {
+        const int e = eb + lane;
+        bool fresh = false;
+        int v = 0;
+        if (e < e1) {
+            v = ds.out_dst[e];
+            const uint32_t bit = 1u << (v & 31);
+            fresh = !(atomicOr(&ds.dirty[v >> 5], bit) & bit);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(dcount, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fresh) dl[base + __popc(bal & ((1u << lane) - 1u))] = make_int2(s, v);
+    }
+}
+
+// The cooperative fixpoint of k_sssp over every scene at once: dirty and
+// changed lists hold (scene, vertex) entries, rounds run until no scene
+// changes (the deepest scene sets the round count).
+__global__ void __launch_bounds__(256) k_sssp_b(const __grid_constant__ BatchDev b) {
+    cg::grid_group grid = cg::this_grid();
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsize = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31, gwarp = gtid >> 5, nwarps = gsize >> 5;
+    int32_t *cnt = b.counters;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    const int total = b.gen_off[b.n];
+    for (int i = gtid; i < total; i += gsize) {
+        const int s = scene_of(b.gen_off, b.n, i);
+        const DevScene &ds = b.scenes[s];
+        const int g = i - b.gen_off[s];
+        const bool src = g < ds.n_src;
+        ds.cost[0][g] = src ? 0.0 : inf;
+        ds.par[0][g] = src ? g : -1;
+        ds.gen_ctype[g] = src ? kConeNone : kConeEmpty;
+        ds.gen_cone[g] = make_int4(0, 0, 0, 0);
+        if ((g & 31) == 0) ds.dirty[g >> 5] = 0u;
+    }
+    if (gtid < 5) cnt[gtid] = 0;
+    grid.sync();
+    for (int i = gwarp; i < total; i += nwarps) {  // sources mark their out-neighbours
+        const int s = scene_of(b.gen_off, b.n, i);
+        const DevScene &ds = b.scenes[s];
+        const int g = i - b.gen_off[s];
+        if (g < ds.n_src && ds.in_start[ds.n_vert] <= ds.edge_cap) mark_out_warp_b(ds, s, g, lane, b.dirtyl[0], &cnt[2]);
+    }
+    grid.sync();
+    int round = 0;
+    for (;; ++round) {
+        const int par_r = round & 1, par_n = par_r ^ 1;
+        if (gtid == 0) {
+            cnt[par_n] = 0;
+            cnt[2 + par_n] = 0;
+        }
+        const int nd = __ldcg(&cnt[2 + par_r]);
+        for (int i = gwarp; i < nd; i += nwarps) {
+            const int2 ent = __ldcg(&b.dirtyl[par_r][i]);
+            const int s = ent.x, v = ent.y;
+            const DevScene &ds = b.scenes[s];
+            const int vv = v - ds.n_src;
+            if (lane == 0) atomicAnd(&ds.dirty[v >> 5], ~(1u << (v & 31)));
+            const int2 vl = ds.gen_lat[v];
+            long long best = 0x7ff0000000000000ll;
+            int bpar = -1;
+            for (int e = ds.in_start[vv] + lane; e < ds.in_start[vv + 1]; e += 32) {
+                const int u = ds.in_src[e];
+                const double cu = __ldcg(&ds.cost[0][u]);
+                if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;
+                const int ct = __ldcg(&ds.gen_ctype[u]);
+                if (ct != kConeNone) {
+                    const int2 ul = ds.gen_lat[u];
+                    if (!in_cone(ct, __ldcg(&ds.gen_cone[u]), vl.x - ul.x, vl.y - ul.y)) continue;
+                }
+                const long long cand = __double_as_longlong(__dadd_rn(cu, ds.in_len[e]));
+                if (cand < best || (cand == best && u < bpar)) {
+                    best = cand;
+                    bpar = u;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
+                if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
+                    best = ob;
+                    bpar = op;
+                }
+            }
+            if (lane == 0 && (best != __double_as_longlong(__ldcg(&ds.cost[0][v])) || bpar != __ldcg(&ds.par[0][v]))) {
+                ds.cost[1][v] = __longlong_as_double(best);
+                ds.par[1][v] = bpar;
+                b.frontier[par_r][atomicAdd(&cnt[par_r], 1)] = make_int2(s, v);
+            }
+        }
+        grid.sync();
+        const int nc = __ldcg(&cnt[par_r]);
+        if (nc == 0) break;
+        if (round + 1 >= b.max_rounds) {
+            if (gtid == 0) cnt[4] = -1;
+            break;
+        }
+        for (int i = gtid; i < nc; i += gsize) {
+            const int2 ent = __ldcg(&b.frontier[par_r][i]);
+            commit_vertex(b.scenes[ent.x], ent.y);
+        }
+        for (int i = gwarp; i < nc; i += nwarps) {
+            const int2 ent = __ldcg(&b.frontier[par_r][i]);
+            mark_out_warp_b(b.scenes[ent.x], ent.x, ent.y, lane, b.dirtyl[par_n], &cnt[2 + par_n]);
+        }
+        grid.sync();
+    }
+    for (int s = gtid; s < b.n; s += gsize) {
+        const DevScene &ds = b.scenes[s];
+        ds.stats[0] = round + 1;
+        if (cnt[4] < 0) atomicOr(ds.status, kStNotConverged);
+    }
+}
+
+__global__ void k_finalize_b(const __grid_constant__ BatchDev b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.gen_off[b.n]; i += gridDim.x * blockDim.x) {
+        const int s = scene_of(b.gen_off, b.n, i);
+        finalize_gen(b.scenes[s], i - b.gen_off[s]);
     }
 }
 
@@ -491,5 +707,26 @@ int sssp_grid_blocks() {
 }
 
 int count_kernel_launches_vertex() { return 6; }
+
+int sssp_batched_grid_blocks() {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp_b, kSsspThreads, 0);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+    return (sms > 0 ? sms : 1) * per_sm;
+}
+
+void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st) {
+    k_prepare_b<<<152 * 4, 256, 0, st>>>(b);
+    k_vis_pairs_b<<<152 * 16, kVisThreads, 0, st>>>(b);
+    k_edges_count_b<<<152 * 4, 256, 0, st>>>(b);
+    k_edges_scan_b<<<b.n, 1024, 0, st>>>(b);
+    k_edges_fill_b<<<152 * 4, 256, 0, st>>>(b);
+    BatchDev arg = b;
+    void *args[] = {&arg};
+    cudaLaunchCooperativeKernel((const void *)k_sssp_b, dim3(b.sssp_blocks), dim3(kSsspThreads), args, 0, st);
+    k_finalize_b<<<152 * 4, 256, 0, st>>>(b);
+}
 
 }  // namespace spm
