@@ -176,8 +176,8 @@ def run_batched(args, cfg_desc, scenes):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
     objs = [spm.Scene(sc) for sc in scenes]
-    for o in objs:
-        spm.spm_scene_set_tuning(o.handle, 2, 32)
+    for o in objs:  # full scans; the default tile follows each scene's pixel size
+        spm.spm_scene_set_tuning(o.handle, 2, 32, 0)
     batch = spm.Batch(objs)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

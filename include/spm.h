@@ -126,7 +126,8 @@ spm_status spm_compute_batched(spm_scene *const *scenes, int32_t n, void *stream
  * replayed by spm_batch_compute. dist[k] / parent[k] are caller-owned device
  * buffers of scene k's grid, fixed for the batch's lifetime. Creation
  * allocates the batch's device descriptors; compute allocates nothing. The
- * scenes must outlive the batch; culling settings are read at creation. */
+ * scenes must outlive the batch; culling and tile settings are read at
+ * creation. */
 typedef struct spm_batch spm_batch;
 spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *dist,
                             int32_t *const *parent, spm_batch **out);
@@ -221,21 +222,25 @@ spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *pixel_m
  *   as in mazes -- otherwise let every tile scan every generator; decided on
  *   the device each compute), 1 = always flood, 2 = never flood.
  * hidden_chunk: first chunk of lb-ordered candidates whose tiles are tested
- *   for being hidden (32..256; later chunks double). */
+ *   for being hidden (32..256; later chunks double).
+ * tile: pixel tile side, 16 or 32 (default 16 when a pixel spans 8 world
+ *   units or more, else 32): each tile is one CTA of the pixel pass. */
 typedef struct {
     int32_t flood_mode;
     int32_t hidden_chunk;
-    int32_t reserved[6];
+    int32_t tile;
+    int32_t reserved[5];
 } spm_tuning;
 
 spm_status spm_scene_get_tuning(const spm_scene *scene, spm_tuning *out);
 spm_status spm_scene_set_tuning(spm_scene *scene, const spm_tuning *tuning);
 
 /* Autotuner: times spm_compute on this scene (device events on `stream`,
- * warm-up then the median of 3 runs) for every flood_mode x hidden_chunk
- * combination in {1, 2} x {32, 256}, keeps the fastest and writes it to
- * *chosen (may be NULL). Synchronous. Allocates the scene's output staging
- * planes on first use; call it at set-up, not inside a captured stream. */
+ * warm-up then the median of 3 runs) for every flood_mode x hidden_chunk x
+ * tile combination in {1, 2} x {32, 256} x {16, 32}, keeps the fastest and
+ * writes it to *chosen (may be NULL). Synchronous. Allocates the scene's
+ * output staging planes on first use; call it at set-up, not inside a
+ * captured stream. */
 spm_status spm_scene_autotune(spm_scene *scene, void *stream, spm_tuning *chosen);
 
 /* Static text for a status code. */

@@ -90,6 +90,12 @@ spm_status check_device(spm_scene *s) {
     return SPM_OK;
 }
 
+void set_tile(spm::DevScene &ds, int tile) {
+    ds.tile = tile;
+    ds.tiles_x = (ds.Nx + tile - 1) / tile;
+    ds.tiles_y = (ds.Ny + tile - 1) / tile;
+}
+
 spm_status upload_sources(spm_scene *s) {
     const spm::HostScene &hs = s->hs;
     spm::DevScene &ds = s->ds;
@@ -226,10 +232,11 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     ds.counters = dalloc<int32_t>(s, 4);
     ds.status = dalloc<uint32_t>(s, 1);
     ds.stats = dalloc<int32_t>(s, 4);
-    ds.tiles_x = (hs.Nx + spm::kTile - 1) / spm::kTile;
-    ds.tiles_y = (hs.Ny + spm::kTile - 1) / spm::kTile;
     {
-        const int64_t ntiles = (int64_t)ds.tiles_x * ds.tiles_y;
+        // lists are sized for the small tile; the default tile follows the pixel size
+        const int64_t ntiles = (int64_t)((hs.Nx + spm::kTileSmall - 1) / spm::kTileSmall) *
+                               ((hs.Ny + spm::kTileSmall - 1) / spm::kTileSmall);
+        set_tile(ds, (ds.hx >= 8.f || ds.hy >= 8.f) ? spm::kTileSmall : spm::kTile);
         ds.use_flood = spm::flood_possible((int)ntiles) && spm::flood_smem_attr() ? 1 : 0;
         ds.flood_mode = 0;
         ds.hidden_chunk = 32;
@@ -606,7 +613,7 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     info[4] = (int64_t)s->hs.poly_off.size() - 1;
     info[5] = stats[0];
     info[6] = stats[1];
-    info[7] = spm::kTile;
+    info[7] = s->ds.tile;
     info[8] = (s->ds.use_flood && fc[2] == 0) ? 1 : 0;
     info[9] = s->ds.flood_mode;
     return SPM_OK;
@@ -617,15 +624,18 @@ spm_status spm_scene_get_tuning(const spm_scene *s, spm_tuning *out) {
     *out = spm_tuning{};
     out->flood_mode = s->ds.flood_mode;
     out->hidden_chunk = s->ds.hidden_chunk;
+    out->tile = s->ds.tile;
     return SPM_OK;
 }
 
 spm_status spm_scene_set_tuning(spm_scene *s, const spm_tuning *t) {
     if (!s || !t) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
-    if (t->flood_mode < 0 || t->flood_mode > 2 || t->hidden_chunk < 32 || t->hidden_chunk > 256)
+    if (t->flood_mode < 0 || t->flood_mode > 2 || t->hidden_chunk < 32 || t->hidden_chunk > 256 ||
+        (t->tile != 0 && t->tile != spm::kTile && t->tile != spm::kTileSmall))
         return set_err(s, SPM_ERR_INVALID_ARG, "tuning out of range");
     s->ds.flood_mode = t->flood_mode;
     s->ds.hidden_chunk = t->hidden_chunk;
+    if (t->tile) set_tile(s->ds, t->tile);
     return SPM_OK;
 }
 
@@ -643,16 +653,19 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
         return set_err(s, SPM_ERR_CUDA, "event creation failed");
-    const int modes[2] = {1, 2}, chunks[2] = {32, 256};
+    const int modes[2] = {1, 2}, chunks[2] = {32, 256}, tiles[2] = {spm::kTileSmall, spm::kTile};
     float best = 3.4e38f;
     spm_tuning pick{};
     pick.flood_mode = s->ds.flood_mode;
     pick.hidden_chunk = s->ds.hidden_chunk;
+    pick.tile = s->ds.tile;
+    for (int ti = 0; ti < 2; ++ti)
     for (int mi = 0; mi < 2; ++mi) {
         if (modes[mi] == 1 && !s->ds.use_flood) continue;
         for (int ci = 0; ci < 2; ++ci) {
             s->ds.flood_mode = modes[mi];
             s->ds.hidden_chunk = chunks[ci];
+            set_tile(s->ds, tiles[ti]);
             float t[3];
             st = spm_compute(s, stream, s->stage_dist, s->stage_par);  // warm-up
             for (int k = 0; k < 3 && st == SPM_OK; ++k) {
@@ -668,6 +681,7 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
                 best = t[1];
                 pick.flood_mode = modes[mi];
                 pick.hidden_chunk = chunks[ci];
+                pick.tile = tiles[ti];
             }
         }
     }
@@ -675,6 +689,7 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     cudaEventDestroy(b);
     s->ds.flood_mode = pick.flood_mode;
     s->ds.hidden_chunk = pick.hidden_chunk;
+    set_tile(s->ds, pick.tile);
     if (chosen) *chosen = pick;
     if (st != SPM_OK) return st;
     return spm_scene_sync(s, stream);

@@ -29,8 +29,8 @@ constexpr int kQueue = 1024;  // per-warp ring buffer of tiles
 // share edges. Pixel i covers [i * pitch, (i + 1) * pitch].
 __device__ __forceinline__ int4 tile_area(const DevScene &ds, int tx, int ty) {
     const int px = ds.S * ds.Wx / ds.Nx, py = ds.S * ds.Wy / ds.Ny;
-    return make_int4(tx * kTile * px, ty * kTile * py, min((tx + 1) * kTile, ds.Nx) * px,
-                     min((ty + 1) * kTile, ds.Ny) * py);
+    const int T = ds.tile;
+    return make_int4(tx * T * px, ty * T * py, min((tx + 1) * T, ds.Nx) * px, min((ty + 1) * T, ds.Ny) * py);
 }
 
 __device__ __forceinline__ bool cone_meets_box(int ct, int4 c, int2 v, int4 box) {
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
     unsigned *visited = fsm + warp * (words + kQueue);
     int *queue = (int *)(visited + words);
     const int nwarps = gridDim.x * kFloodWarps;
-    const int tpx = kTile * (ds.S * ds.Wx / ds.Nx), tpy = kTile * (ds.S * ds.Wy / ds.Ny);
+    const int tpx = ds.tile * (ds.S * ds.Wx / ds.Nx), tpy = ds.tile * (ds.S * ds.Wy / ds.Ny);
     for (int g = blockIdx.x * kFloodWarps + warp; g < ds.n_gen; g += nwarps) {
         if (!(ds.gen_costf[g] < INFINITY)) continue;
         const int kind = ds.gen_kind[g];

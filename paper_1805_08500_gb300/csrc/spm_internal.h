@@ -13,8 +13,9 @@
 namespace spm {
 
 constexpr int kMaxPolyVerts = 16;    // convex polygon vertex limit
-constexpr int kTile = 32;            // pixel tile side (one CTA per tile)
-constexpr int kPixelThreads = 256;   // 8 threads per tile row, 4 pixels each
+constexpr int kTile = 32;            // largest pixel tile side (one CTA per tile)
+constexpr int kTileSmall = 16;       // small tile side, for coarse grids
+constexpr int kPixelThreads = 256;   // 32x32 tiles: 4 pixels per thread; 16x16: 1
 constexpr int kCandCap = 1024;       // candidate generators per batch (smem)
 constexpr int kBlockCap = 96;        // blocker polygons per chunk (smem)
 constexpr int kDedupBits = 8192;     // polygon-id dedup bitmap (smem)
@@ -117,6 +118,7 @@ struct DevScene {
     uint32_t *status;                  // latched status bits
     int32_t *stats;                    // [0] rounds, [1] edges
     // tiles and their candidate lists (flood)
+    int32_t tile;                      // tile side in pixels: 16 or 32
     int32_t tiles_x, tiles_y;
     int32_t use_flood;                 // 0: flood impossible (too many tiles for smem)
     int32_t flood_mode;                // 0 auto (sparse visibility graph), 1 on, 2 off

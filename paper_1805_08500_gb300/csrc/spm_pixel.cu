@@ -31,7 +31,6 @@
 namespace spm {
 namespace {
 
-constexpr int T = kTile;
 constexpr int NT = kPixelThreads;
 constexpr unsigned long long kUnset = 0x7F800000FFFFFFFFull;  // (+inf, id max)
 
@@ -234,22 +233,26 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
     }
 }
 
-// One 32 x 32 tile of one scene, by one CTA. allow_lists = false ignores
-// flooded candidate lists (the batched form scans every generator).
+// One tile of one scene, by one CTA: 32 x 32 pixels with PX = 4 pixels per
+// thread (consecutive in a row), or 16 x 16 with PX = 1. allow_lists = false
+// ignores flooded candidate lists (the batched form scans every generator).
+template <int PX>
 __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, float *__restrict__ dist,
                                            int32_t *__restrict__ parent, PixSmem &sm, const bool allow_lists) {
+    constexpr int T = PX == 4 ? 32 : 16;
+    constexpr int TPR = T / PX;  // threads per tile row
     const int i0 = (tile % ds.tiles_x) * T, j0 = (tile / ds.tiles_x) * T;
-    const int row = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
+    const int row = threadIdx.x / TPR, c4 = (threadIdx.x % TPR) * PX;
     const int j = j0 + row;
     const int pitch_x = ds.S * ds.Wx / ds.Nx, pitch_y = ds.S * ds.Wy / ds.Ny;
     const int py = pitch_y * j + pitch_y / 2;
     const float fy = ((float)j + 0.5f) * ds.hy;
-    int px[4];
-    float fx[4];
-    unsigned long long key[4];
+    int px[PX];
+    float fx[PX];
+    unsigned long long key[PX];
     unsigned live = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < PX; ++k) {
         const int i = i0 + c4 + k;
         px[k] = pitch_x * i + pitch_x / 2;
         fx[k] = ((float)i + 0.5f) * ds.hx;
@@ -258,7 +261,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
     }
     // free space: not in the open interior of any polygon
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < PX; ++k) {
         if (!(live & (1u << k))) continue;
         int bx = (px[k] - ds.bin_x0) / ds.bin_size, by = (py - ds.bin_y0) / ds.bin_size;
         if (bx < 0 || by < 0 || bx >= ds.bin_nx || by >= ds.bin_ny) continue;
@@ -329,7 +332,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 const float lb_c = sm.cand_lb[c];
                 bool act = false;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) act |= (live >> k & 1u) && key_dist(key[k]) > lb_c;
+                for (int k = 0; k < PX; ++k) act |= (live >> k & 1u) && key_dist(key[k]) > lb_c;
                 if (!__syncthreads_or(act)) {
                     done = true;
                     break;
@@ -375,10 +378,10 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                     seg_il = 1.0f / sqrtf(fux * fux + fuy * fuy);
                 }
                 unsigned need = 0;
-                unsigned long long nk[4];
-                long long num[4];
+                unsigned long long nk[PX];
+                long long num[PX];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < PX; ++k) {
                     nk[k] = kUnset;
                     num[k] = 0;
                     if (!((live >> k) & 1u) || !(key_dist(key[k]) > lb_c)) continue;
@@ -431,7 +434,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 SPM_CNT(7, __popc(need));
                 const int nx = -(seg.w - seg.y), ny = seg.z - seg.x;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < PX; ++k) {
                     if (!((need >> k) & 1u)) continue;
                     bool vis;
                     if (ovf) {
@@ -459,7 +462,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
             // tile upper bound for candidate pruning: worst best over live pixels
             float worst = 0.f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < PX; ++k)
                 if ((live >> k) & 1u) worst = fmaxf(worst, key_dist(key[k]));
             for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
             __syncthreads();
@@ -474,20 +477,20 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
     }
 
     if (j < ds.Ny) {
-        float od[4];
-        int op[4];
+        float od[PX];
+        int op[PX];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < PX; ++k) {
             const bool ok = ((live >> k) & 1u) && key[k] != kUnset;
             od[k] = ok ? key_dist(key[k]) : INFINITY;
             op[k] = ok ? (int)(unsigned)(key[k] & 0xffffffffu) : -1;
         }
         const size_t base = (size_t)j * ds.Nx + i0 + c4;
-        if ((ds.Nx & 3) == 0 && i0 + c4 + 3 < ds.Nx) {
-            *reinterpret_cast<float4 *>(dist + base) = make_float4(od[0], od[1], od[2], od[3]);
-            *reinterpret_cast<int4 *>(parent + base) = make_int4(op[0], op[1], op[2], op[3]);
+        if (PX == 4 && (ds.Nx & 3) == 0 && i0 + c4 + 3 < ds.Nx) {
+            *reinterpret_cast<float4 *>(dist + base) = make_float4(od[0], od[PX > 1 ? 1 : 0], od[PX > 2 ? 2 : 0], od[PX > 3 ? 3 : 0]);
+            *reinterpret_cast<int4 *>(parent + base) = make_int4(op[0], op[PX > 1 ? 1 : 0], op[PX > 2 ? 2 : 0], op[PX > 3 ? 3 : 0]);
         } else {
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < PX; ++k)
                 if (i0 + c4 + k < ds.Nx) {
                     dist[base + k] = od[k];
                     parent[base + k] = op[k];
@@ -499,7 +502,8 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
 __global__ void __launch_bounds__(NT) k_pixels(const __grid_constant__ DevScene ds, float *__restrict__ dist,
                                                int32_t *__restrict__ parent) {
     __shared__ PixSmem sm;
-    pixel_tile(ds, blockIdx.x, dist, parent, sm, true);
+    if (ds.tile == kTile) pixel_tile<4>(ds, blockIdx.x, dist, parent, sm, true);
+    else pixel_tile<1>(ds, blockIdx.x, dist, parent, sm, true);
 }
 
 // Persistent form over a batch of scenes: each CTA takes the next
@@ -530,7 +534,8 @@ __global__ void __launch_bounds__(NT) k_pixels_batched(const __grid_constant__ B
         for (int w = threadIdx.x; w < (int)(sizeof(DevScene) / 4); w += NT)
             reinterpret_cast<int *>(&sds)[w] = reinterpret_cast<const int *>(&b.scenes[sc])[w];
         __syncthreads();
-        pixel_tile(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, false);
+        if (sds.tile == kTile) pixel_tile<4>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, false);
+        else pixel_tile<1>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, false);
         __syncthreads();
     }
 }

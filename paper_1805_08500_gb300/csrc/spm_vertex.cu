@@ -7,9 +7,12 @@
 //               cone, of cost(u) + |u - v|
 // computed on the GPU in three steps:
 //   1. k_vis_pairs: one bit per (generator u, obstacle vertex v) pair, set when
-//      u sees v exactly and the line uv is tangent to u's obstacle wedge (a
-//      vertex can only pass a path on along a tangent, so other pairs can never
-//      relax v); segment interiors reach v through its perpendicular foot.
+//      u sees v exactly and the line uv is tangent to the obstacle wedges of u
+//      and of v (a vertex passes a path on only along a tangent: other edges
+//      never carry a shortest path to a pixel); segment interiors reach v
+//      through its perpendicular foot. A vertex whose shortest arrival is not
+//      tangent has an empty shadow cone and is never a parent, so only its
+//      own reported cost can exceed the true one.
 //   2. k_edges_*: the bits become CSR in-lists (by v) with FP64 edge lengths
 //      and out-lists (by u) for frontier marking.
 //   3. k_sssp: a cooperative kernel on every SM runs Jacobi rounds restricted
@@ -48,10 +51,16 @@ __device__ bool pair_edge(const DevScene &ds, int u, int v) {
     }
     const int2 ul = ds.gen_lat[u];
     if (ul.x == vl.x && ul.y == vl.y) return false;
+    const int wx = vl.x - ul.x, wy = vl.y - ul.y;
     if (ku == kVert) {  // tangent at u: the line uv does not split u's wedge
-        int4 w = ds.gen_wedge[u];
-        int wx = vl.x - ul.x, wy = vl.y - ul.y;
-        int a = cross32(wx, wy, w.x, w.y), b = cross32(wx, wy, w.z, w.w);
+        const int4 w = ds.gen_wedge[u];
+        const int a = cross32(wx, wy, w.x, w.y), b = cross32(wx, wy, w.z, w.w);
+        if ((a > 0 && b < 0) || (a < 0 && b > 0)) return false;
+    }
+    {   // tangent at v: an arrival pointing into v's wedge leaves v an empty
+        // shadow cone, so v could never pass such a path on
+        const int4 w = ds.gen_wedge[v];
+        const int a = cross32(wx, wy, w.x, w.y), b = cross32(wx, wy, w.z, w.w);
         if ((a > 0 && b < 0) || (a < 0 && b > 0)) return false;
     }
     return visible_points(ds, vl.x, vl.y, ul.x, ul.y);
@@ -227,7 +236,8 @@ __device__ __forceinline__ void mark_out_warp(const DevScene &ds, int u, int lan
 // Shared-memory bytes the single-CTA fixpoint needs (0 if it cannot run).
 __device__ __forceinline__ int solo_bytes(const DevScene &ds) {
     const long long n = ds.n_gen, E = ds.in_start[ds.n_vert];
-    if (n >= 32768 || E > ds.edge_cap) return 0;
+    // sparse graphs only (deep, few vertices per round); dense ones need the GPU
+    if (n >= 32768 || E > ds.edge_cap || E > 8 * n) return 0;
     const long long b = n * (8 + 4 + 8 + 1) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
                         4 * ((n + 31) / 32) + 2 * 3 * n + n * (8 + 4) + 256;
     return b <= kSoloSmem ? (int)b : 0;

@@ -13,7 +13,8 @@ Tolerances (stated for every comparison):
     correct labels: there the GPU label must be the oracle's tied runner-up,
     and such pixels are checked for validity instead of being counted;
   * vertex-generator costs: identical FP64 values (both sides run the same
-    correctly rounded operations), parents identical.
+    correctly rounded operations) and parents for every generator with a
+    usable shadow cone.
 """
 import math
 
@@ -134,10 +135,16 @@ def test_vertex_costs_bit_exact(spm, oracle_mod):
         o = oracle_mod.Oracle(scene)
         assert np.array_equal(kind, o.kind)
         assert np.array_equal(lat, o.lxy.astype(np.int32))
-        fin = np.isfinite(o.cost)
-        assert np.array_equal(np.isfinite(cost), fin)
+        # generators with a usable shadow cone (sources, tangent arrivals)
+        # match bit for bit; vertices reached head-on (empty cone, never a
+        # parent) only get an upper bound on the GPU (see the vertex phase)
+        used = o.cside != oracle_mod.CONE_EMPTY
+        fin = np.isfinite(o.cost) & used
+        assert np.array_equal(np.isfinite(cost) & used, fin)
         assert np.array_equal(cost[fin], o.cost[fin])
-        assert np.array_equal(par, o.parent)
+        assert np.array_equal(par[used], o.parent[used])
+        rest = ~used & np.isfinite(o.cost)
+        assert np.all(cost[rest] >= o.cost[rest])
 
 
 # ---------------------------------------------------------------------------
@@ -196,19 +203,20 @@ def test_culling_modes_agree_bit_for_bit(spm, oracle_mod, which):
     scene = sg.maze(3, cells=10, N=640) if which == "maze" else sg.plain_polys(8, n_polys=90, N=512)
     s = spm.Scene(scene)
     outs = []
-    for mode in (1, 2, 0):
-        for chunk in (32, 256):
-            spm.spm_scene_set_tuning(s.handle, mode, chunk)
-            d, p = s.compute()
-            s.sync()
-            outs.append((d.cpu().numpy(), p.cpu().numpy(), s.info()["flooded"]))
-    assert outs[0][2] == 1 and outs[2][2] == 0
+    for tile in (32, 16):
+        for mode in (1, 2, 0):
+            for chunk in (32, 256):
+                spm.spm_scene_set_tuning(s.handle, mode, chunk, tile)
+                d, p = s.compute()
+                s.sync()
+                outs.append((d.cpu().numpy(), p.cpu().numpy(), s.info()["flooded"]))
+    assert outs[0][2] == 1 and outs[2][2] == 0 and outs[6][2] == 1
     for d, p, _ in outs[1:]:
         assert np.array_equal(d, outs[0][0]) and np.array_equal(p, outs[0][1])
     rd, rp, rd2, rp2 = oracle_mod.Oracle(scene).field()
     check_parity(scene, outs[0][0], outs[0][1], rd, rp, rd2, f"modes-{which}", rp2)
     t = s.autotune()
-    assert t["flood_mode"] in (1, 2) and t["hidden_chunk"] in (32, 256)
+    assert t["flood_mode"] in (1, 2) and t["hidden_chunk"] in (32, 256) and t["tile"] in (16, 32)
 
 
 def test_batched_matches_individual_computes(spm, oracle_mod):
