@@ -204,7 +204,8 @@ def run_batched(args, cfg_desc, scenes):
             "config": {"workload": "batched256", "scene": cfg_desc, "scenes": len(scenes),
                        "pixels": npx, "l2": "flushed between timed steps (256 MiB write)",
                        "launch": "one CUDA graph per step"},
-            "mpixel_per_s": npx / (ms * 1e-3) / 1e6, "clocks": clk.summary()}
+            "mpixel_per_s": npx / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
+            "gpu_launches": 8 * args.steps}  # 7 vertex-phase kernels + 1 persistent pixel kernel
     print(json.dumps(line), flush=True)
     batch.close()
 
@@ -217,7 +218,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maze4096",
                     choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048", "batched256"])
-    ap.add_argument("--cpu-pixels", type=int, default=200_000,
+    ap.add_argument("--cpu-pixels", type=int, default=3_000_000,
                     help="oracle pixel sample for the cpu_baseline leg")
     ap.add_argument("--ref-pixels", type=int, default=40_000,
                     help="oracle pixel sample per step for --impl reference")
@@ -260,7 +261,7 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     info = s.info()
-    launches_per_step = (6 if info["n_vert"] > 0 else 2) + 1
+    launches_per_step = info["kernels_per_compute"]
 
     for _ in range(args.warmup):
         s.compute(d_out, p_out, stream)
@@ -312,8 +313,9 @@ def main():
     e2e_value = world * npx / float(e2e_t.item()) / 1e6
 
     peaks, peak_src = load_peaks()
-    pix_ms = float(np.mean([p[1] for p in phases]))
     vert_ms = float(np.mean([p[0] for p in phases]))
+    cull_ms = float(np.mean([p[1] for p in phases]))
+    pix_ms = float(np.mean([p[2] for p in phases]))  # k_pixels, one launch per step
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = FP32_LANES * N_SMS * 2 * clock_mhz * 1e6 / 1e12
     achieved = FLOPS_PER_PIXEL * npx / (pix_ms * 1e-3) / 1e12
@@ -330,7 +332,7 @@ def main():
                    "l2": "flushed between timed steps (256 MiB write)",
                    "tuning": tuning,
                    "parallelism": f"replicas x{world}"},
-        "phases_ms": {"vertex": vert_ms, "pixel": pix_ms},
+        "phases_ms": {"vertex": vert_ms, "cull": cull_ms, "pixel": pix_ms},
         "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": None,

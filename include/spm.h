@@ -161,11 +161,13 @@ spm_status spm_extract_path(spm_scene *scene, float x, float y, float *out_xy,
 spm_status spm_scene_generators(spm_scene *scene, int32_t *kind, int32_t *lattice_xy,
                                 double *cost, int32_t *parent);
 
-/* info[0] generators, [1] sources (incl. 3 per segment), [2] obstacle-vertex
- * generators, [3] lattice scale S, [4] polygons, [5] vertex-phase rounds of
- * the last compute (after sync), [6] visibility-graph edges of the last
- * compute (after sync), [7] tile size in pixels, [8] 1 if the last compute
- * used flooded per-tile candidate lists (after sync), [9] flood_mode. */
+/* info must hold 11 entries: [0] generators, [1] sources (incl. 3 per
+ * segment), [2] obstacle-vertex generators, [3] lattice scale S, [4]
+ * polygons, [5] vertex-phase rounds of the last compute (after sync), [6]
+ * visibility-graph edges of the last compute (after sync), [7] tile size in
+ * pixels, [8] 1 if the last compute used flooded per-tile candidate lists
+ * (after sync), [9] flood_mode, [10] kernels one spm_compute launches with
+ * the current settings. */
 spm_status spm_scene_info(spm_scene *scene, int64_t *info);
 
 /* Differentiable form. Forward: loss = mean over n agents (pixel indices,
@@ -209,12 +211,15 @@ spm_status spm_agents_backward_noalloc(spm_scene *scene, void *stream,
                                        const int32_t *parent_dev, float *grad_points_dev,
                                        float *grad_segs_dev);
 
-/* Device time of the two phases of the last spm_compute on this scene, in
- * milliseconds, from CUDA events the library records around them on the
+/* Device time of the three phases of the last spm_compute on this scene, in
+ * milliseconds, from CUDA events the library records between them on the
  * compute stream (not recorded while the stream is being captured into a
  * CUDA graph): vertex_ms = vertex-cost fixpoint (Sec. 3.1 Procedures 1, 2
- * and 4), pixel_ms = pixel pass (Procedure 3). Waits for the compute. */
-spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *pixel_ms);
+ * and 4), cull_ms = per-tile candidate lists (the flood, 0 when the scene
+ * scans every generator), pixel_ms = the pixel kernel (Procedure 3).
+ * Waits for the compute. */
+spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *cull_ms,
+                              float *pixel_ms);
 
 /* Tuning of the pixel pass's culling, per scene.
  * flood_mode: 0 = automatic (flood the per-tile candidate lists when the

@@ -92,7 +92,7 @@ def load_library():
         "spm_scene_info": ([P, P], I32),
         "spm_agents_forward": ([P, P, P, I32, P, P, P], I32),
         "spm_agents_backward": ([P, P, P, P], I32),
-        "spm_scene_phase_ms": ([P, P, P], I32),
+        "spm_scene_phase_ms": ([P, P, P, P], I32),
         "spm_agents_backward_noalloc": ([P, P, P, I32, P, P, P], I32),
         "spm_scene_get_tuning": ([P, P], I32),
         "spm_scene_set_tuning": ([P, P], I32),
@@ -276,10 +276,10 @@ def spm_scene_autotune(handle, stream=None):
 
 
 def spm_scene_info(handle):
-    info = np.zeros(10, np.int64)
+    info = np.zeros(11, np.int64)
     _check(load_library().spm_scene_info(handle, info.ctypes.data), "spm_scene_info", handle)
     keys = ["n_gen", "n_src", "n_vert", "lattice_scale", "n_polys", "rounds", "edges", "tile",
-            "flooded", "flood_mode"]
+            "flooded", "flood_mode", "kernels_per_compute"]
     return dict(zip(keys, (int(v) for v in info)))
 
 
@@ -318,12 +318,13 @@ def spm_agents_backward_noalloc(handle, stream, agents, parent, grad_points, gra
 
 
 def spm_scene_phase_ms(handle):
-    """(vertex_ms, pixel_ms) of the last compute, from the library's events."""
+    """(vertex_ms, cull_ms, pixel_ms) of the last compute, from the library's events."""
     v = ctypes.c_float()
+    c = ctypes.c_float()
     p = ctypes.c_float()
-    _check(load_library().spm_scene_phase_ms(handle, ctypes.byref(v), ctypes.byref(p)),
+    _check(load_library().spm_scene_phase_ms(handle, ctypes.byref(v), ctypes.byref(c), ctypes.byref(p)),
            "spm_scene_phase_ms", handle)
-    return v.value, p.value
+    return v.value, c.value, p.value
 
 
 def spm_status_string(status: int) -> str:

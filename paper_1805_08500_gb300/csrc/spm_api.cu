@@ -39,7 +39,7 @@ struct spm_scene {
     float2 *lastpt = nullptr;
     float4 *val = nullptr;
     // phase timing events (vertex start, pixel start, end)
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_valid = false;
 };
 
@@ -315,6 +315,7 @@ spm_status spm_compute(spm_scene *s, void *stream, float *dist, int32_t *parent)
         static const int32_t off[4] = {0, 0, 1, 0};
         cudaMemcpyAsync(s->ds.flood_counts, off, sizeof off, cudaMemcpyHostToDevice, cs);
     }
+    if (timed) cudaEventRecord(s->ev[3], cs);
     spm::launch_pixel_phase(s->ds, cs, dist, parent);
     if (timed) cudaEventRecord(s->ev[2], cs);
     s->ev_valid = timed;
@@ -616,6 +617,7 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     info[7] = s->ds.tile;
     info[8] = (s->ds.use_flood && fc[2] == 0) ? 1 : 0;
     info[9] = s->ds.flood_mode;
+    info[10] = (s->hs.n_vert > 0 ? 7 : 3) + (s->ds.use_flood && s->ds.flood_mode != 2 ? 3 : 0) + 1;
     return SPM_OK;
 }
 
@@ -695,12 +697,13 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     return spm_scene_sync(s, stream);
 }
 
-spm_status spm_scene_phase_ms(spm_scene *s, float *vertex_ms, float *pixel_ms) {
-    if (!s || !vertex_ms || !pixel_ms) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+spm_status spm_scene_phase_ms(spm_scene *s, float *vertex_ms, float *cull_ms, float *pixel_ms) {
+    if (!s || !vertex_ms || !cull_ms || !pixel_ms) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
     if (!s->ev_valid) return set_err(s, SPM_ERR_INVALID_ARG, "no timed compute recorded");
     if (cudaEventSynchronize(s->ev[2]) != cudaSuccess ||
         cudaEventElapsedTime(vertex_ms, s->ev[0], s->ev[1]) != cudaSuccess ||
-        cudaEventElapsedTime(pixel_ms, s->ev[1], s->ev[2]) != cudaSuccess)
+        cudaEventElapsedTime(cull_ms, s->ev[1], s->ev[3]) != cudaSuccess ||
+        cudaEventElapsedTime(pixel_ms, s->ev[3], s->ev[2]) != cudaSuccess)
         return set_err(s, SPM_ERR_CUDA, "event timing failed");
     return SPM_OK;
 }
