@@ -244,8 +244,10 @@ __device__ __forceinline__ bool visible_foot(const DevScene &ds, int s, int px, 
 #ifdef SPM_COUNT
 static __device__ unsigned long long g_count[16];  // one copy per translation unit
 #define SPM_CNT(i, v) atomicAdd(&::spm::g_count[i], (unsigned long long)(v))
+#define SPM_CNT_MAX(i, v) atomicMax(&::spm::g_count[i], (unsigned long long)(v))
 #else
 #define SPM_CNT(i, v) ((void)0)
+#define SPM_CNT_MAX(i, v) ((void)0)
 #endif
 
 // True when one polygon hides every point of the box from the point

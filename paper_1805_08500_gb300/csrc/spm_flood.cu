@@ -21,9 +21,8 @@
 namespace spm {
 namespace {
 
-constexpr int kFloodWarps = 4;
-constexpr int kFloodThreads = 32 * kFloodWarps;
-constexpr int kQueue = 1024;  // per-warp ring buffer of tiles
+constexpr int kFloodThreads = 256;  // one CTA floods one generator at a time
+constexpr int kFront = 1024;        // frontier tiles per breadth-first level
 
 // Full area of tile (tx, ty) in lattice units: closed rectangle, neighbours
 // share edges. Pixel i covers [i * pitch, (i + 1) * pitch].
@@ -51,8 +50,133 @@ __device__ __forceinline__ void push_global(const DevScene &ds, int g) {
     ds.glob_list[atomicAdd(&ds.flood_counts[1], 1)] = g;
 }
 
+// The bins that can hold a polygon hiding a tile from g: the thick segment
+// from the tile centre c to g (radius r, the tile's half diagonal + 1), cut
+// into strips of bins along its major axis. Each strip is one work item.
+struct StripWalk {
+    float pu, pw, du, dw, ou, ow, m;
+    int us, ustep, nstrips, nw;
+    bool xmaj;
+};
+
+__device__ __forceinline__ int bin_clamp(float v, float o, float bs, int n) {
+    const int b = (int)floorf((v - o) / bs);
+    return b < 0 ? 0 : (b >= n ? n - 1 : b);
+}
+
+__device__ __forceinline__ StripWalk strip_walk(const DevScene &ds, int2 g, float cx, float cy, float r) {
+    StripWalk w;
+    const float tx = (float)g.x, ty = (float)g.y, bs = (float)ds.bin_size;
+    w.m = r + 1.0f;
+    w.xmaj = fabsf(tx - cx) >= fabsf(ty - cy);
+    w.pu = w.xmaj ? cx : cy;
+    w.pw = w.xmaj ? cy : cx;
+    const float qu = w.xmaj ? tx : ty, qw = w.xmaj ? ty : tx;
+    w.ou = w.xmaj ? (float)ds.bin_x0 : (float)ds.bin_y0;
+    w.ow = w.xmaj ? (float)ds.bin_y0 : (float)ds.bin_x0;
+    const int nu = w.xmaj ? ds.bin_nx : ds.bin_ny;
+    w.nw = w.xmaj ? ds.bin_ny : ds.bin_nx;
+    const int u0 = bin_clamp(fminf(w.pu, qu) - w.m, w.ou, bs, nu), u1 = bin_clamp(fmaxf(w.pu, qu) + w.m, w.ou, bs, nu);
+    w.ustep = qu >= w.pu ? 1 : -1;
+    w.us = w.ustep > 0 ? u0 : u1;
+    w.nstrips = u1 - u0 + 1;
+    w.du = qu - w.pu;
+    w.dw = qw - w.pw;
+    return w;
+}
+
+// Upper bound on the bins one strip spans across the minor axis: the strip's
+// major-axis extent is bs + 2m, the segment moves |dw/du| per unit along it,
+// and the span grows by m on both sides.
+__device__ __forceinline__ int strip_bins_max(const DevScene &ds, const StripWalk &w) {
+    const float bs = (float)ds.bin_size;
+    const float slope = fabsf(w.du) < 0.5f ? 0.f : fabsf(w.dw / w.du);
+    const float span = fabsf(w.du) < 0.5f ? fabsf(w.dw) + 2.f * w.m : slope * (bs + 2.f * w.m) + 2.f * w.m;
+    return min((int)(span / bs) + 2, w.nw);
+}
+
+// Does one polygon in bin k of strip sidx hide every point of box from g?
+// Stops early once another item has found a hiding polygon for the same tile.
+__device__ __forceinline__ bool bin_hides(const DevScene &ds, const StripWalk &w, int sidx, int k, int2 g, int4 box, float cx,
+                          float cy, float r, const volatile int *stop) {
+    const float bs = (float)ds.bin_size;
+    const int u = w.us + w.ustep * sidx;
+    float wlo, whi;
+    if (fabsf(w.du) < 0.5f) {
+        wlo = fminf(w.pw, w.pw + w.dw);
+        whi = fmaxf(w.pw, w.pw + w.dw);
+    } else {
+        const float a = w.ou + u * bs - w.m, b = w.ou + (u + 1) * bs + w.m;
+        const float t0 = (a - w.pu) / w.du, t1 = (b - w.pu) / w.du;
+        float tl = fmaxf(0.f, fminf(t0, t1)), th = fminf(1.f, fmaxf(t0, t1));
+        if (tl > th) { tl = 0.f; th = 1.f; }
+        const float wa = w.pw + tl * w.dw, wb = w.pw + th * w.dw;
+        wlo = fminf(wa, wb);
+        whi = fmaxf(wa, wb);
+    }
+    const int v = bin_clamp(wlo - w.m, w.ow, bs, w.nw) + k;
+    if (v > bin_clamp(whi + w.m, w.ow, bs, w.nw)) return false;
+    const float tx = (float)g.x, ty = (float)g.y;
+    const int bin = w.xmaj ? v * ds.bin_nx + u : u * ds.bin_nx + v;
+    const int e = __ldg(ds.bin_start + bin + 1);
+    for (int it = __ldg(ds.bin_start + bin); it < e; ++it) {
+        if (*stop) return false;
+        const int4 *rp = reinterpret_cast<const int4 *>(ds.bin_recs + it);
+        const int4 rbox = __ldg(rp), rmeta = __ldg(rp + 1);  // box; poly, voff, m
+        if (!seg_near_box(cx, cy, tx, ty, r, rbox)) continue;
+        const int2 *V = ds.poly_v + rmeta.y;
+        const int m = rmeta.z;
+        const unsigned mg = edge_mask(V, m, g.x, g.y);
+        if (poly_blocks(V, m, box.x, box.y, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.y, g.x, g.y, mg) &&
+            poly_blocks(V, m, box.x, box.w, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.w, g.x, g.y, mg))
+            return true;
+    }
+    return false;
+}
+
+struct FloodSmem {
+    int front[2][kFront];  // current / next breadth-first level
+    int pre[kFront + 1];   // exclusive prefix of (strip, bin) items per frontier tile
+    int flag[kFront];      // 0 visible, 1 hidden, 2 outside the cone
+    int cnt[2];
+    int overflow;
+    int wsum[kFloodThreads / 32];
+};
+
+// Exclusive scan of v[0..n) in place (n <= kFront), v[n] = total. All threads.
+__device__ void cta_scan(int *v, int n, int *wsum) {
+    constexpr int per = (kFront + kFloodThreads - 1) / kFloodThreads;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int loc[per];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        const int i = threadIdx.x * per + k;
+        loc[k] = i < n ? v[i] : 0;
+        s += loc[k];
+    }
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int run = inc - s;
+    for (int w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        const int i = threadIdx.x * per + k;
+        if (i < n) v[i] = run;
+        run += loc[k];
+    }
+    if (threadIdx.x == kFloodThreads - 1) v[n] = run;
+}
+
 __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
-    extern __shared__ unsigned fsm[];
+    extern __shared__ unsigned visited[];
+    __shared__ FloodSmem sm;
     if (ds.flood_mode == 0) {  // automatic: flood only sparse visibility graphs
         const double pairs = (double)ds.n_gen * (double)max(ds.n_vert, 1);
         if ((double)ds.in_start[ds.n_vert] > 0.01 * pairs) {
@@ -60,95 +184,145 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
             return;
         }
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x;
     const int ntiles = ds.tiles_x * ds.tiles_y, words = (ntiles + 31) / 32;
-    unsigned *visited = fsm + warp * (words + kQueue);
-    int *queue = (int *)(visited + words);
-    const int nwarps = gridDim.x * kFloodWarps;
     const int tpx = ds.tile * (ds.S * ds.Wx / ds.Nx), tpy = ds.tile * (ds.S * ds.Wy / ds.Ny);
-    for (int g = blockIdx.x * kFloodWarps + warp; g < ds.n_gen; g += nwarps) {
+    for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) {
         if (!(ds.gen_costf[g] < INFINITY)) continue;
         const int kind = ds.gen_kind[g];
         const int ct = kind == kVert ? ds.gen_ctype[g] : kConeNone;
         if (ct == kConeEmpty) continue;
-        const int2 gl = ds.gen_lat[g];
-        const int tx = gl.x >= 0 ? gl.x / tpx : -1, ty = gl.y >= 0 ? gl.y / tpy : -1;
         if (kind == kSegI) {
-            if (lane == 0) push_global(ds, g);
+            if (tid == 0) push_global(ds, g);
             continue;
         }
+        const int2 gl = ds.gen_lat[g];
         const int4 cone = kind == kVert ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
-        for (int w = lane; w < words; w += 32) visited[w] = 0u;
-        __syncwarp();
-        // seeds: every tile whose closed area contains g (up to 4 when g lies
-        // on tile edges)
-        bool fresh = false;
-        int t0 = 0;
-        if (lane < 4) {
-            const int sx = tx - (lane & 1), sy = ty - ((lane >> 1) & 1);
+        const int tx = gl.x >= 0 ? gl.x / tpx : -1, ty = gl.y >= 0 ? gl.y / tpy : -1;
+        __syncthreads();  // the previous generator's last level is done with smem
+        for (int w = tid; w < words; w += kFloodThreads) visited[w] = 0u;
+        if (tid == 0) {
+            sm.cnt[0] = 0;
+            sm.overflow = 0;
+        }
+        __syncthreads();
+        // seeds: every tile whose closed area contains g (up to 4 when g lies on tile edges)
+        if (tid < 4) {
+            const int sx = tx - (tid & 1), sy = ty - ((tid >> 1) & 1);
             if (tx >= 0 && ty >= 0 && sx >= 0 && sy >= 0 && sx < ds.tiles_x && sy < ds.tiles_y) {
                 const int4 a4 = tile_area(ds, sx, sy);
                 if (gl.x >= a4.x && gl.x <= a4.z && gl.y >= a4.y && gl.y <= a4.w) {
-                    t0 = sy * ds.tiles_x + sx;
-                    fresh = !(atomicOr(&visited[t0 >> 5], 1u << (t0 & 31)) & (1u << (t0 & 31)));
+                    const int t0 = sy * ds.tiles_x + sx;
+                    if (!(atomicOr(&visited[t0 >> 5], 1u << (t0 & 31)) & (1u << (t0 & 31))))
+                        sm.front[0][atomicAdd(&sm.cnt[0], 1)] = t0;
                 }
             }
         }
-        const unsigned sb = __ballot_sync(0xffffffffu, fresh);
-        if (fresh) queue[__popc(sb & ((1u << lane) - 1u))] = t0;
-        int head = 0, tail = __popc(sb);
-        if (tail == 0) {  // g outside every tile: scanned by all tiles instead
-            if (lane == 0) push_global(ds, g);
+        __syncthreads();
+        if (sm.cnt[0] == 0) {  // g outside every tile: scanned by all tiles instead
+            if (tid == 0) push_global(ds, g);
             continue;
         }
-        bool overflow = false;
-        while (head < tail && !overflow) {
-            // the whole warp tests one frontier tile (uniform control flow)
-            const int t = queue[head % kQueue];
-            ++head;
-            const int cx = t % ds.tiles_x, cy = t / ds.tiles_x;
-            const int4 area = tile_area(ds, cx, cy);
-            bool ok = cone_meets_box(ct, cone, gl, area);
-            if (ok) {
+#ifdef SPM_COUNT
+        int n_tests = 0;
+#endif
+        int p = 0;
+        for (;;) {
+            if (sm.overflow) {  // a level outgrew the frontier: every tile scans g instead
+                if (tid == 0) {
+                    push_global(ds, g);
+                    SPM_CNT(13, 1);
+                }
+                break;
+            }
+            const int nc = min(sm.cnt[p], kFront);
+            if (nc == 0) break;
+            const int *cur = sm.front[p];
+            // A: cone test and strip count per frontier tile
+            for (int i = tid; i < nc; i += kFloodThreads) {
+                const int t = cur[i];
+                const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
+                const bool ok = cone_meets_box(ct, cone, gl, area);
+                int ns = 0;
+                if (ok) {
+                    const float acx = 0.5f * ((float)area.x + (float)area.z), acy = 0.5f * ((float)area.y + (float)area.w);
+                    const float ar = 0.5f * sqrtf((float)(area.z - area.x) * (float)(area.z - area.x) +
+                                                  (float)(area.w - area.y) * (float)(area.w - area.y)) + 1.0f;
+                    const StripWalk w = strip_walk(ds, gl, acx, acy, ar);
+                    ns = w.nstrips * strip_bins_max(ds, w);
+                }
+                sm.flag[i] = ok ? 0 : 2;
+                sm.pre[i] = ns;
+            }
+            if (tid == 0) sm.cnt[p ^ 1] = 0;
+            __syncthreads();
+            cta_scan(sm.pre, nc, sm.wsum);
+            __syncthreads();
+            // B: every (tile, strip, bin) item in parallel; a hiding polygon sets the tile's flag
+            const int total = sm.pre[nc];
+            for (int j = tid; j < total; j += kFloodThreads) {
+                int lo = 0, hi = nc;  // pre[lo] <= j < pre[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.pre[mid] <= j) lo = mid;
+                    else hi = mid;
+                }
+                volatile int *fl = &sm.flag[lo];
+                if (*fl) continue;
+                const int t = cur[lo];
+                const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
                 const float acx = 0.5f * ((float)area.x + (float)area.z), acy = 0.5f * ((float)area.y + (float)area.w);
                 const float ar = 0.5f * sqrtf((float)(area.z - area.x) * (float)(area.z - area.x) +
                                               (float)(area.w - area.y) * (float)(area.w - area.y)) + 1.0f;
-                ok = !box_hidden_warp(ds, gl, area, acx, acy, ar);
-                if (lane == 0) {
+                const StripWalk w = strip_walk(ds, gl, acx, acy, ar);
+                const int kb = strip_bins_max(ds, w), q = j - sm.pre[lo];
+                if (bin_hides(ds, w, q / kb, q - (q / kb) * kb, gl, area, acx, acy, ar, fl)) *fl = 1;
+            }
+            __syncthreads();
+            // C: emit visible tiles, queue their fresh 8-neighbours
+            int *nxt = sm.front[p ^ 1];
+            for (int q = tid; q < nc * 9; q += kFloodThreads) {
+                const int i = q / 9, k = q - 9 * i;
+                const int f = sm.flag[i];
+#ifdef SPM_COUNT
+                if (k == 4 && f != 2) {
                     SPM_CNT(11, 1);
-                    SPM_CNT(12, ok ? 1 : 0);
+                    SPM_CNT(12, f == 0 ? 1 : 0);
                 }
-            }
-            if (!ok) continue;
-            if (lane == 0) {  // emit (tile, g)
-                const int slot = atomicAdd(&ds.flood_counts[0], 1);
-                if (slot < ds.pair_cap) {
-                    ds.pairs[slot] = make_int2(t, g);
-                    atomicAdd(&ds.tile_count[t], 1);
-                } else {
-                    atomicOr(&ds.flood_counts[2], 1);
+#endif
+                if (f) continue;
+                const int t = cur[i];
+                if (k == 4) {
+                    const int slot = atomicAdd(&ds.flood_counts[0], 1);
+                    if (slot < ds.pair_cap) {
+                        ds.pairs[slot] = make_int2(t, g);
+                        atomicAdd(&ds.tile_count[t], 1);
+                    } else {
+                        atomicOr(&ds.flood_counts[2], 1);
+                    }
+                    continue;
                 }
+                const int nx = t % ds.tiles_x + k % 3 - 1, ny = t / ds.tiles_x + k / 3 - 1;
+                if (nx < 0 || ny < 0 || nx >= ds.tiles_x || ny >= ds.tiles_y) continue;
+                const int nt = ny * ds.tiles_x + nx;
+                if (atomicOr(&visited[nt >> 5], 1u << (nt & 31)) & (1u << (nt & 31))) continue;
+                const int slot = atomicAdd(&sm.cnt[p ^ 1], 1);
+                if (slot < kFront) nxt[slot] = nt;
+                else sm.overflow = 1;
             }
-            // lanes 0..8 look at the 8-neighbours, fresh ones join the queue
-            bool nfresh = false;
-            int nt = 0;
-            if (lane < 9 && lane != 4) {
-                const int nx = cx + lane % 3 - 1, ny = cy + lane / 3 - 1;
-                if (nx >= 0 && ny >= 0 && nx < ds.tiles_x && ny < ds.tiles_y) {
-                    nt = ny * ds.tiles_x + nx;
-                    nfresh = !(atomicOr(&visited[nt >> 5], 1u << (nt & 31)) & (1u << (nt & 31)));
-                }
-            }
-            const unsigned pb = __ballot_sync(0xffffffffu, nfresh);
-            if (nfresh) queue[(tail + __popc(pb & ((1u << lane) - 1u))) % kQueue] = nt;
-            tail += __popc(pb);
-            if (tail - head > kQueue) overflow = true;
+#ifdef SPM_COUNT
+            if (tid == 0)
+                for (int i = 0; i < nc; ++i) n_tests += sm.flag[i] != 2;
+#endif
+            __syncthreads();
+            p ^= 1;
         }
-        if (overflow && lane == 0) {
-            push_global(ds, g);
-            SPM_CNT(13, 1);
+#ifdef SPM_COUNT
+        if (tid == 0) {
+            SPM_CNT_MAX(14, n_tests);
+            SPM_CNT(15, n_tests > 256 ? 1 : 0);
         }
-        __syncwarp();
+#endif
     }
 }
 
@@ -192,12 +366,11 @@ __global__ void k_tiles_fill(DevScene ds) {
 
 }  // namespace
 
-size_t flood_smem_bytes(int tiles) {
-    const int words = (tiles + 31) / 32;
-    return sizeof(unsigned) * (size_t)kFloodWarps * (words + kQueue);
+size_t flood_smem_bytes(int tiles) {  // dynamic part: the visited bitmap
+    return sizeof(unsigned) * (size_t)((tiles + 31) / 32);
 }
 
-bool flood_possible(int tiles) { return flood_smem_bytes(tiles) <= 200 * 1024; }
+bool flood_possible(int tiles) { return flood_smem_bytes(tiles) + sizeof(FloodSmem) <= 200 * 1024; }
 
 void launch_flood(const DevScene &ds, cudaStream_t st) {
     const int ntiles = ds.tiles_x * ds.tiles_y;
@@ -209,14 +382,15 @@ void launch_flood(const DevScene &ds, cudaStream_t st) {
     cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
     cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
     const size_t smem = flood_smem_bytes(ntiles);
-    const int blocks = min(152 * 8, (ds.n_gen + kFloodWarps - 1) / kFloodWarps);
+    const int blocks = min(152 * 4, ds.n_gen);
     k_flood<<<max(blocks, 1), kFloodThreads, smem, st>>>(ds);
     k_tiles_scan<<<1, 1024, 0, st>>>(ds);
     k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds);
 }
 
 int flood_smem_attr() {
-    return cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) == cudaSuccess;
+    return cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024 - (int)sizeof(FloodSmem)) == cudaSuccess;
 }
 
 }  // namespace spm
