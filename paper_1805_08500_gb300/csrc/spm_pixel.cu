@@ -171,9 +171,10 @@ __device__ void sort_candidates(PixSmem &sm, int n) {
         }
 }
 
-// Column-wise conservative bin enumeration for the thick segment c->t
-// (lattice units, radius r), one column per thread; each polygon found is
-// filtered against the thick segment and appended (deduplicated) to smem.
+// Conservative bin enumeration for the thick segment c->t (lattice units,
+// radius r): column-wise, one (column, bin) item per thread, so that every
+// thread scans one bin's records. Each polygon found is filtered against the
+// thick segment and appended (deduplicated) to smem.
 __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float cy, float tx, float ty,
                                float r, int kind, int2 tl, int4 seg, int4 box) {
     const float bs = (float)ds.bin_size, x0 = (float)ds.bin_x0, y0 = (float)ds.bin_y0;
@@ -185,7 +186,14 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
     const int c0 = bin_of(fminf(cx, tx) - m, x0, ds.bin_nx), c1 = bin_of(fmaxf(cx, tx) + m, x0, ds.bin_nx);
     const float dx = tx - cx, dy = ty - cy;
     const bool dedup = ds.n_poly <= kDedupBits;
-    for (int col = c0 + (int)threadIdx.x; col <= c1; col += NT) {
+    // items per column: about the rows one column spans (its x extent is
+    // bs + 2m, the segment rises |dy/dx| per unit along it, plus m on both
+    // sides); each item strides by K, so any K covers every row
+    const float span = fabsf(dx) < 0.5f ? fabsf(dy) + 2.f * m : fabsf(dy / dx) * (bs + 2.f * m) + 2.f * m;
+    const int K = min((int)(span / bs) + 2, ds.bin_ny);
+    const int items = (c1 - c0 + 1) * K;
+    for (int j = threadIdx.x; j < items; j += NT) {
+        const int col = c0 + j / K, kr = j - (j / K) * K;
         float ylo, yhi;
         if (fabsf(dx) < 0.5f) {
             ylo = fminf(cy, ty);
@@ -200,10 +208,12 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
             yhi = fmaxf(ya, yb);
         }
         const int r0 = bin_of(ylo - m, y0, ds.bin_ny), r1 = bin_of(yhi + m, y0, ds.bin_ny);
-        for (int row = r0; row <= r1; ++row) {
+        for (int row = r0 + kr; row <= r1; row += K) {  // rows kr, kr + K, ...: every row once
             const int bin = row * ds.bin_nx + col;
-            for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-                const BinRec rec = ds.bin_recs[it];
+            const int e = __ldg(ds.bin_start + bin + 1);
+            for (int it = __ldg(ds.bin_start + bin); it < e; ++it) {
+                const int4 *rp = reinterpret_cast<const int4 *>(ds.bin_recs + it);
+                const BinRec rec = {__ldg(rp), __ldg(rp + 1).x, __ldg(rp + 1).y, __ldg(rp + 1).z, 0};
                 const int k = rec.poly;
                 if (dedup) {
                     const unsigned bit = 1u << (k & 31);
@@ -499,7 +509,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
     }
 }
 
-__global__ void __launch_bounds__(NT) k_pixels(const __grid_constant__ DevScene ds, float *__restrict__ dist,
+__global__ void __launch_bounds__(NT, 3) k_pixels(const __grid_constant__ DevScene ds, float *__restrict__ dist,
                                                int32_t *__restrict__ parent) {
     __shared__ PixSmem sm;
     if (ds.tile == kTile) pixel_tile<4>(ds, blockIdx.x, dist, parent, sm, true);
@@ -509,7 +519,7 @@ __global__ void __launch_bounds__(NT) k_pixels(const __grid_constant__ DevScene 
 // Persistent form over a batch of scenes: each CTA takes the next
 // (scene, tile) from a global counter (scenes ordered largest first), copies
 // that scene's descriptor into shared memory and runs the same tile code.
-__global__ void __launch_bounds__(NT) k_pixels_batched(const __grid_constant__ BatchDev b) {
+__global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant__ BatchDev b) {
     __shared__ PixSmem sm;
     __shared__ DevScene sds;
     __shared__ int cur, cur_scene;
