@@ -67,13 +67,19 @@ __device__ bool pair_edge(const DevScene &ds, int u, int v) {
 }
 
 // One warp task: row vv (vertex index) of the bit matrix, word w covering
-// generators 32w..32w+31.
+// generators 32w..32w+31. The matrix starts zeroed. A pair of obstacle
+// vertices passes the filter and sees each other symmetrically (both
+// tangency tests and the blocking predicate are symmetric in the two
+// points), so only generators u < v are tested here and an edge between two
+// vertices also sets its mirror bit in u's row.
 __device__ __forceinline__ void vis_pairs_task(const DevScene &ds, long long t, int lane) {
     const int vv = (int)(t / ds.vis_words), w = (int)(t % ds.vis_words);
     const int u = w * 32 + lane, v = ds.n_src + vv;
-    const bool e = (u < ds.n_gen) && pair_edge(ds, u, v);
+    if (w * 32 >= v) return;  // the whole word lies at or above the diagonal (warp-uniform)
+    const bool e = u < v && pair_edge(ds, u, v);
     const unsigned bits = __ballot_sync(0xffffffffu, e);
-    if (lane == 0) ds.vis_bits[(size_t)vv * ds.vis_words + w] = bits;
+    if (lane == 0 && bits) atomicOr(&ds.vis_bits[(size_t)vv * ds.vis_words + w], bits);
+    if (e && u >= ds.n_src) atomicOr(&ds.vis_bits[(size_t)(u - ds.n_src) * ds.vis_words + (v >> 5)], 1u << (v & 31));
 }
 
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds) {
@@ -504,6 +510,11 @@ __device__ __forceinline__ int scene_of(const T *off, int n, T x) {
 }
 
 __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.pair_off[b.n];
+         i += (long long)gridDim.x * blockDim.x) {  // zero every scene's visibility bit matrix
+        const int s = scene_of(b.pair_off, b.n, i);
+        b.scenes[s].vis_bits[i - b.pair_off[s]] = 0u;
+    }
     const int total = b.gen_off[b.n];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total + b.n; i += gridDim.x * blockDim.x) {
         // entries 0..total-1: one per generator; total..total+n-1: one per scene
@@ -687,6 +698,7 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
     cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
     cudaMemsetAsync(ds.out_fill, 0, sizeof(int32_t) * ds.n_gen, st);
     if (ds.n_vert > 0) {
+        cudaMemsetAsync(ds.vis_bits, 0, sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words, st);
         const long long tasks = (long long)ds.n_vert * ds.vis_words;
         long long blocks = (tasks + (kVisThreads / 32) - 1) / (kVisThreads / 32);
         blocks = blocks > 152 * 16 ? 152 * 16 : blocks;
