@@ -251,6 +251,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         ds.flood_counts = dalloc<int32_t>(s, 4);
     }
     ds.sssp_blocks = spm::sssp_grid_blocks();
+    ds.solo_smem = spm::solo_smem_bytes();
     for (void *p : s->allocs) ok &= p != nullptr;
     ok &= ds.vis_bits && ds.in_src && ds.in_len && ds.out_dst && ds.status && ds.stats && ds.gen_ctype;
     if (!ok) {
@@ -617,7 +618,8 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     info[7] = s->ds.tile;
     info[8] = (s->ds.use_flood && fc[2] == 0) ? 1 : 0;
     info[9] = s->ds.flood_mode;
-    info[10] = (s->hs.n_vert > 0 ? 7 : 3) + (s->ds.use_flood && s->ds.flood_mode != 2 ? 3 : 0) + 1;
+    info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.solo_smem > 0 ? 1 : 0) + 2 +  // vertex phase
+               (s->ds.use_flood && s->ds.flood_mode != 2 ? 3 : 0) + 1;          // flood, pixels
     return SPM_OK;
 }
 

@@ -109,6 +109,7 @@ struct DevScene {
     uint32_t *dirty;                   // n_gen bits: vertex already in the dirty list
     int32_t *counters;                 // [0,1] frontier sizes, [2,3] dirty-list sizes
     int32_t sssp_blocks;               // cooperative grid size (CTAs)
+    int32_t solo_smem;                 // shared memory the single-CTA fixpoint may use (0: not available)
     // finalised generator table (read by the pixel kernel)
     float *gen_costf;                  // n_gen (inf when unreached)
     double *gen_cost;                  // n_gen
@@ -169,6 +170,7 @@ int sssp_batched_grid_blocks();
 bool flood_possible(int tiles);
 int flood_smem_attr();
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
+int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();
 void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,

@@ -34,7 +34,7 @@ namespace {
 constexpr int kVisThreads = 256;
 constexpr int kSsspThreads = 256;
 constexpr int kSoloThreads = 512;
-constexpr int kSoloSmem = 200 * 1024;
+constexpr int kSoloSmem = 226 * 1024;  // within the 227 KB opt-in maximum, with the static part
 
 // Static filter + exact visibility for one (u, v) pair.
 __device__ bool pair_edge(const DevScene &ds, int u, int v) {
@@ -209,10 +209,13 @@ __device__ __forceinline__ void commit_vertex(const DevScene &ds, int v) {
     ds.cost[0][v] = __ldcg(&ds.cost[1][v]);
     const int p = __ldcg(&ds.par[1][v]);
     ds.par[0][v] = p;
-    int dx, dy;
-    arrival_dir(ds, p, ds.gen_lat[v], dx, dy);
-    int4 c;
-    const int ct = make_cone(ds.gen_wedge[v], dx, dy, c);
+    int4 c = make_int4(0, 0, 0, 0);
+    int ct = kConeEmpty;  // unreachable again: no arrival direction
+    if (p >= 0) {
+        int dx, dy;
+        arrival_dir(ds, p, ds.gen_lat[v], dx, dy);
+        ct = make_cone(ds.gen_wedge[v], dx, dy, c);
+    }
     ds.gen_cone[v] = c;
     ds.gen_ctype[v] = ct;
 }
@@ -244,9 +247,9 @@ __device__ __forceinline__ int solo_bytes(const DevScene &ds) {
     const long long n = ds.n_gen, E = ds.in_start[ds.n_vert];
     // sparse graphs only (deep, few vertices per round); dense ones need the GPU
     if (n >= 32768 || E > ds.edge_cap || E > 8 * n) return 0;
-    const long long b = n * (8 + 4 + 8 + 1) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
-                        4 * ((n + 31) / 32) + 2 * 3 * n + n * (8 + 4) + 256;
-    return b <= kSoloSmem ? (int)b : 0;
+    const long long b = n * (8 + 4 + 8 + 8 + 1) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
+                        4 * ((n + 31) / 32) + 2 * 3 * n + n * (8 + 4) + 16 * 16;
+    return b <= ds.solo_smem ? (int)b : 0;
 }
 
 __global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene ds, int max_rounds) {
@@ -343,7 +346,8 @@ __global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene d
 // in 16-bit lanes -- lattice directions fit in 16 bits). A round costs two
 // __syncthreads instead of two grid barriers, which is what deep, sparse
 // graphs (mazes: hundreds of rounds, a few vertices each) need. Results are
-// identical to k_sssp: the same pulls over the same sets.
+// identical to k_sssp: the same pulls over the same sets, committed between
+// the same two barriers.
 __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int bytes = solo_bytes(ds);
@@ -360,6 +364,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     int *par = (int *)take(4 * n);
     int *npar = (int *)take(4 * n);
     short4 *cone = (short4 *)take(8 * n);
+    int2 *lat = (int2 *)take(8 * n);
     signed char *ctype = (signed char *)take(n);
     int *in_start = (int *)take(4 * (nv + 1));
     unsigned short *in_src = (unsigned short *)take(2 * E);
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     unsigned *dirty = (unsigned *)take(4 * ((n + 31) / 32));
     unsigned short *dl[2] = {(unsigned short *)take(2 * n), (unsigned short *)take(2 * n)};
     unsigned short *fr = (unsigned short *)take(2 * n);
-    __shared__ int cnt[4];  // [0,1] dirty counts by parity, [2] changed count
+    __shared__ int cnt_d[2], cnt_c[2];  // dirty-list and changed-list counts, by round parity
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSoloThreads / 32;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
@@ -383,9 +388,13 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         par[g] = src ? g : -1;
         ctype[g] = (signed char)(src ? kConeNone : kConeEmpty);
         cone[g] = make_short4(0, 0, 0, 0);
+        lat[g] = ds.gen_lat[g];
     }
     for (int w = tid; w < (n + 31) / 32; w += kSoloThreads) dirty[w] = 0u;
-    if (tid < 4) cnt[tid] = 0;
+    if (tid < 2) {
+        cnt_d[tid] = 0;
+        cnt_c[tid] = 0;
+    }
     __syncthreads();
     auto mark = [&](int u, unsigned short *list, int *count) {
         for (int e = out_start[u] + lane; e < out_start[u + 1]; e += 32) {
@@ -394,37 +403,42 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             if (!(atomicOr(&dirty[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
         }
     };
-    for (int u = warp; u < ds.n_src; u += nwarps) mark(u, dl[0], &cnt[0]);
+    for (int u = warp; u < ds.n_src; u += nwarps) mark(u, dl[0], &cnt_d[0]);
     __syncthreads();
+    // Two barriers a round: (pull) every dirty vertex recomputes its best
+    // in-edge into ncost/npar | (commit + mark) changed vertices take the new
+    // value and cone, and dirty their out-neighbours for the next round. The
+    // counters of the other parity are reset during the pull, when nothing
+    // reads or writes them.
     int round = 0;
     for (;; ++round) {
         const int par_r = round & 1, par_n = par_r ^ 1;
-        const int nd = cnt[par_r];
+        const int nd = cnt_d[par_r];
         if (tid == 0) {
-            cnt[par_n] = 0;
-            cnt[2] = 0;
+            cnt_d[par_n] = 0;
+            cnt_c[par_n] = 0;
         }
-        __syncthreads();
         for (int i = warp; i < nd; i += nwarps) {
             const int v = dl[par_r][i];
             const int vv = v - ds.n_src;
             if (lane == 0) atomicAnd(&dirty[v >> 5], ~(1u << (v & 31)));
-            const int2 vl = ds.gen_lat[v];
+            const int2 vl = lat[v];
             long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
             for (int e = in_start[vv] + lane; e < in_start[vv + 1]; e += 32) {
+                const double len = __ldg(ds.in_len + e);  // issued before the dependent smem reads
                 const int u = in_src[e];
                 const double cu = cost[u];
                 if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;  // unreached
                 const int ct = ctype[u];
                 if (ct != kConeNone) {
-                    const int2 ul = ds.gen_lat[u];
+                    const int2 ul = lat[u];
                     const short4 c = cone[u];
                     if (!in_cone(ct, make_int4(c.x, c.y, c.z, c.w), vl.x - ul.x, vl.y - ul.y)) continue;
                 }
                 // costs are non-negative, so their bit patterns order like
                 // their values: compare as integers, keep FP64 for the add
-                const long long cand = __double_as_longlong(__dadd_rn(cu, ds.in_len[e]));
+                const long long cand = __double_as_longlong(__dadd_rn(cu, len));
                 if (cand < best || (cand == best && u < bpar)) {
                     best = cand;
                     bpar = u;
@@ -442,29 +456,40 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             if (lane == 0 && (best != __double_as_longlong(cost[v]) || bpar != par[v])) {
                 ncost[v] = __longlong_as_double(best);
                 npar[v] = bpar;
-                fr[atomicAdd(&cnt[2], 1)] = (unsigned short)v;
+                fr[atomicAdd(&cnt_c[par_r], 1)] = (unsigned short)v;
             }
         }
         __syncthreads();
-        const int nc = cnt[2];
+        const int nc = cnt_c[par_r];
         if (nc == 0) break;
         if (round + 1 >= max_rounds) {
             if (tid == 0) atomicOr(ds.status, kStNotConverged);
             break;
         }
-        for (int i = tid; i < nc; i += kSoloThreads) {
+        for (int i = warp; i < nc; i += nwarps) {
             const int v = fr[i];
-            cost[v] = ncost[v];
-            const int pv = npar[v];
-            par[v] = pv;
-            int dx, dy;
-            arrival_dir(ds, pv, ds.gen_lat[v], dx, dy);
-            int4 c;
-            ctype[v] = (signed char)make_cone(ds.gen_wedge[v], dx, dy, c);
-            cone[v] = make_short4((short)c.x, (short)c.y, (short)c.z, (short)c.w);
+            if (lane == 0) {
+                cost[v] = ncost[v];
+                const int pv = npar[v];
+                par[v] = pv;
+                const int2 vl = lat[v];
+                int dx = 0, dy = 0;
+                int4 c = make_int4(0, 0, 0, 0);
+                int ct = kConeEmpty;  // unreachable again: no arrival direction
+                if (pv >= 0) {
+                    if (ds.gen_kind[pv] == kSegI) {
+                        arrival_dir(ds, pv, vl, dx, dy);
+                    } else {
+                        dx = vl.x - lat[pv].x;
+                        dy = vl.y - lat[pv].y;
+                    }
+                    ct = make_cone(ds.gen_wedge[v], dx, dy, c);
+                }
+                ctype[v] = (signed char)ct;
+                cone[v] = make_short4((short)c.x, (short)c.y, (short)c.z, (short)c.w);
+            }
+            mark(v, dl[par_n], &cnt_d[par_n]);
         }
-        __syncthreads();
-        for (int i = warp; i < nc; i += nwarps) mark(fr[i], dl[par_n], &cnt[par_n]);
         __syncthreads();
     }
     for (int g = tid; g < n; g += kSoloThreads) {
@@ -713,13 +738,18 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
     DevScene arg = ds;
     int max_rounds = 4 * ds.n_gen + 64;
     void *args[] = {&arg, &max_rounds};
-    k_sssp_solo<<<1, kSoloThreads, kSoloSmem, st>>>(ds, max_rounds);
+    if (ds.solo_smem > 0) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(ds, max_rounds);
     cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
     k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
 }
 
+int solo_smem_bytes() {
+    return cudaFuncSetAttribute(k_sssp_solo, cudaFuncAttributeMaxDynamicSharedMemorySize, kSoloSmem) == cudaSuccess
+               ? kSoloSmem
+               : (cudaGetLastError(), 0);
+}
+
 int sssp_grid_blocks() {
-    cudaFuncSetAttribute(k_sssp_solo, cudaFuncAttributeMaxDynamicSharedMemorySize, kSoloSmem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
