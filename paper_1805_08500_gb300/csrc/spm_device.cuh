@@ -240,6 +240,35 @@ __device__ __forceinline__ bool visible_foot(const DevScene &ds, int s, int px, 
     return !blocked;
 }
 
+// Exclusive prefix sum of one value per thread over a CTA of blockDim.x
+// threads (a multiple of 32, at most 1024); every thread must call it.
+// wsum: 32 shared slots. Returns the sum of the values of lower threads.
+__device__ __forceinline__ long long cta_exclusive_scan(long long x, long long *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const long long w = lane < nwarp ? wsum[lane] : 0;
+        long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nwarp) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const long long r = wsum[warp] + inc - x;
+    __syncthreads();  // wsum may be reused right after
+    return r;
+}
+
 // Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
 #ifdef SPM_COUNT
 static __device__ unsigned long long g_count[16];  // one copy per translation unit

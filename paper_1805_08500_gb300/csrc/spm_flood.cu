@@ -328,24 +328,13 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
 
 // Exclusive scan of tile_count into tile_start (one CTA), then fill.
 __global__ void __launch_bounds__(1024) k_tiles_scan(DevScene ds) {
-    __shared__ long long part[1024];
+    __shared__ long long wsum[32];
     const int n = ds.tiles_x * ds.tiles_y;
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int lo = threadIdx.x * per, hi = min(n, lo + per);
     long long s = 0;
     for (int i = lo; i < hi; ++i) s += ds.tile_count[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long run = 0;
-        for (int t = 0; t < (int)blockDim.x; ++t) {
-            long long x = part[t];
-            part[t] = run;
-            run += x;
-        }
-    }
-    __syncthreads();
-    long long run = part[threadIdx.x];
+    long long run = cta_exclusive_scan(s, wsum);
     for (int i = lo; i < hi; ++i) {
         ds.tile_start[i] = (int32_t)run;
         run += ds.tile_count[i];

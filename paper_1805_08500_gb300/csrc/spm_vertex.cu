@@ -90,27 +90,29 @@ __global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant
         vis_pairs_task(ds, t, lane);
 }
 
-// In-degree per vertex row and out-degree per generator.
-__device__ __forceinline__ void edges_count_row(const DevScene &ds, int vv) {
-    {
-        const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
-        int cnt = 0;
-        for (int w = 0; w < ds.vis_words; ++w) {
-            uint32_t b = row[w];
-            cnt += __popc(b);
-            while (b) {
-                int bit = __ffs(b) - 1;
-                b &= b - 1;
-                atomicAdd(&ds.out_start[w * 32 + bit + 1], 1);
-            }
+// In-degree per vertex row and out-degree per generator: one warp per row,
+// lanes over the row's words.
+__device__ __forceinline__ void edges_count_row(const DevScene &ds, int vv, int lane) {
+    const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
+    int cnt = 0;
+    for (int w = lane; w < ds.vis_words; w += 32) {
+        uint32_t b = row[w];
+        cnt += __popc(b);
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            atomicAdd(&ds.out_start[w * 32 + bit + 1], 1);
         }
-        ds.in_start[vv + 1] = cnt;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) ds.in_start[vv + 1] = cnt;
 }
 
 __global__ void k_edges_count(const __grid_constant__ DevScene ds) {
-    for (int vv = blockIdx.x * blockDim.x + threadIdx.x; vv < ds.n_vert; vv += gridDim.x * blockDim.x)
-        edges_count_row(ds, vv);
+    const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+    for (int vv = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vv < ds.n_vert; vv += nw)
+        edges_count_row(ds, vv, lane);
 }
 
 // Exclusive scans of in_start (n_vert + 1) and out_start (n_gen + 1), one CTA.
@@ -122,18 +124,7 @@ __device__ __forceinline__ void edges_scan_block(const DevScene &ds, long long *
         const int lo = 1 + threadIdx.x * per, hi = min(n + 1, lo + per);
         long long s = 0;
         for (int i = lo; i < hi; ++i) s += a[i];
-        part[threadIdx.x] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long run = 0;
-            for (int t = 0; t < (int)blockDim.x; ++t) {
-                long long x = part[t];
-                part[t] = run;
-                run += x;
-            }
-        }
-        __syncthreads();
-        long long run = part[threadIdx.x];
+        long long run = cta_exclusive_scan(s, part);
         for (int i = lo; i < hi; ++i) {
             run += a[i];
             a[i] = (int32_t)min(run, (long long)INT32_MAX);
@@ -149,7 +140,7 @@ __device__ __forceinline__ void edges_scan_block(const DevScene &ds, long long *
 }
 
 __global__ void __launch_bounds__(1024) k_edges_scan(const __grid_constant__ DevScene ds) {
-    __shared__ long long part[1024];
+    __shared__ long long part[32];
     edges_scan_block(ds, part);
 }
 
@@ -167,30 +158,41 @@ __device__ __forceinline__ double edge_len(const DevScene &ds, int u, int v) {
     return __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
 }
 
-__device__ __forceinline__ void edges_fill_row(const DevScene &ds, int vv) {
-    {
-        const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
-        int e = ds.in_start[vv];
-        const int v = ds.n_src + vv;
-        for (int w = 0; w < ds.vis_words; ++w) {
-            uint32_t b = row[w];
-            while (b) {
-                int u = w * 32 + __ffs(b) - 1;
-                b &= b - 1;
-                ds.in_src[e] = u;
-                ds.in_len[e] = edge_len(ds, u, v);
-                ++e;
-                int slot = atomicAdd(&ds.out_fill[u], 1);
-                ds.out_dst[ds.out_start[u] + slot] = v;
-            }
+// In-list of row vv in generator order (the same order as a serial scan of
+// the row): one warp, lanes over words, a warp prefix places each word.
+__device__ __forceinline__ void edges_fill_row(const DevScene &ds, int vv, int lane) {
+    const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
+    int e0 = ds.in_start[vv];
+    const int v = ds.n_src + vv;
+    for (int w0 = 0; w0 < ds.vis_words; w0 += 32) {
+        const int w = w0 + lane;
+        uint32_t b = w < ds.vis_words ? row[w] : 0u;
+        const int c = __popc(b);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
+        int e = e0 + inc - c;
+        while (b) {
+            const int u = w * 32 + __ffs(b) - 1;
+            b &= b - 1;
+            ds.in_src[e] = u;
+            ds.in_len[e] = edge_len(ds, u, v);
+            ++e;
+            const int slot = atomicAdd(&ds.out_fill[u], 1);
+            ds.out_dst[ds.out_start[u] + slot] = v;
+        }
+        e0 += __shfl_sync(0xffffffffu, inc, 31);
     }
 }
 
 __global__ void k_edges_fill(const __grid_constant__ DevScene ds) {
     if (ds.in_start[ds.n_vert] > ds.edge_cap) return;
-    for (int vv = blockIdx.x * blockDim.x + threadIdx.x; vv < ds.n_vert; vv += gridDim.x * blockDim.x)
-        edges_fill_row(ds, vv);
+    const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+    for (int vv = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vv < ds.n_vert; vv += nw)
+        edges_fill_row(ds, vv, lane);
 }
 
 // Jacobi rounds of the fixpoint on the whole GPU (cooperative launch, two
@@ -396,14 +398,16 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         cnt_c[tid] = 0;
     }
     __syncthreads();
+    // work unit: a group of 8 lanes per vertex (in-degrees here are small), 4 per warp
+    const int grp = lane >> 3, gl = lane & 7, ngroups = nwarps * 4, gid = warp * 4 + grp;
     auto mark = [&](int u, unsigned short *list, int *count) {
-        for (int e = out_start[u] + lane; e < out_start[u + 1]; e += 32) {
+        for (int e = out_start[u] + gl; e < out_start[u + 1]; e += 8) {
             const int v = out_dst[e];
             const unsigned bit = 1u << (v & 31);
             if (!(atomicOr(&dirty[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
         }
     };
-    for (int u = warp; u < ds.n_src; u += nwarps) mark(u, dl[0], &cnt_d[0]);
+    for (int u = gid; u < ds.n_src; u += ngroups) mark(u, dl[0], &cnt_d[0]);
     __syncthreads();
     // Two barriers a round: (pull) every dirty vertex recomputes its best
     // in-edge into ncost/npar | (commit + mark) changed vertices take the new
@@ -418,14 +422,17 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             cnt_d[par_n] = 0;
             cnt_c[par_n] = 0;
         }
-        for (int i = warp; i < nd; i += nwarps) {
-            const int v = dl[par_r][i];
+        for (int i0 = warp * 4; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
+            const int i = i0 + grp;
+            const bool act = i < nd;
+            const int v = act ? dl[par_r][i] : ds.n_src;
             const int vv = v - ds.n_src;
-            if (lane == 0) atomicAnd(&dirty[v >> 5], ~(1u << (v & 31)));
+            if (act && gl == 0) atomicAnd(&dirty[v >> 5], ~(1u << (v & 31)));
             const int2 vl = lat[v];
             long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
-            for (int e = in_start[vv] + lane; e < in_start[vv + 1]; e += 32) {
+            const int e1 = act ? in_start[vv + 1] : 0;
+            for (int e = in_start[vv] + gl; e < e1; e += 8) {
                 const double len = __ldg(ds.in_len + e);  // issued before the dependent smem reads
                 const int u = in_src[e];
                 const double cu = cost[u];
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 4; o > 0; o >>= 1) {  // within the 8-lane group
                 const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
                 if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
@@ -453,7 +460,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                     bpar = op;
                 }
             }
-            if (lane == 0 && (best != __double_as_longlong(cost[v]) || bpar != par[v])) {
+            if (act && gl == 0 && (best != __double_as_longlong(cost[v]) || bpar != par[v])) {
                 ncost[v] = __longlong_as_double(best);
                 npar[v] = bpar;
                 fr[atomicAdd(&cnt_c[par_r], 1)] = (unsigned short)v;
@@ -466,9 +473,9 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             if (tid == 0) atomicOr(ds.status, kStNotConverged);
             break;
         }
-        for (int i = warp; i < nc; i += nwarps) {
+        for (int i = gid; i < nc; i += ngroups) {
             const int v = fr[i];
-            if (lane == 0) {
+            if (gl == 0) {
                 cost[v] = ncost[v];
                 const int pv = npar[v];
                 par[v] = pv;
@@ -568,24 +575,26 @@ __global__ void __launch_bounds__(kVisThreads) k_vis_pairs_b(const __grid_consta
 }
 
 __global__ void k_edges_count_b(const __grid_constant__ BatchDev b) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.vert_off[b.n]; i += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < b.vert_off[b.n]; i += nw) {
         const int s = scene_of(b.vert_off, b.n, i);
-        edges_count_row(b.scenes[s], i - b.vert_off[s]);
+        edges_count_row(b.scenes[s], i - b.vert_off[s], lane);
     }
 }
 
 __global__ void __launch_bounds__(1024) k_edges_scan_b(const __grid_constant__ BatchDev b) {
-    __shared__ long long part[1024];
+    __shared__ long long part[32];
     const DevScene &ds = b.scenes[blockIdx.x];
     if (ds.n_vert > 0) edges_scan_block(ds, part);
 }
 
 __global__ void k_edges_fill_b(const __grid_constant__ BatchDev b) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.vert_off[b.n]; i += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < b.vert_off[b.n]; i += nw) {
         const int s = scene_of(b.vert_off, b.n, i);
         const DevScene &ds = b.scenes[s];
         if (ds.in_start[ds.n_vert] > ds.edge_cap) continue;
-        edges_fill_row(ds, i - b.vert_off[s]);
+        edges_fill_row(ds, i - b.vert_off[s], lane);
     }
 }
 
@@ -728,7 +737,7 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
         long long blocks = (tasks + (kVisThreads / 32) - 1) / (kVisThreads / 32);
         blocks = blocks > 152 * 16 ? 152 * 16 : blocks;
         k_vis_pairs<<<(int)blocks, kVisThreads, 0, st>>>(ds);
-        int eb = (ds.n_vert + 255) / 256;
+        const int eb = (ds.n_vert + 7) / 8;  // one warp per row
         k_edges_count<<<eb, 256, 0, st>>>(ds);
         k_edges_scan<<<1, 1024, 0, st>>>(ds);
         k_edges_fill<<<eb, 256, 0, st>>>(ds);
