@@ -52,6 +52,9 @@ def workload(name: str):
         return sg.plain_rects(0), "8 rectangles, 256^2 px, 256^2 world, 1 point"
     if name == "diff2048":
         return sg.differentiable(0, n_agents=10), "150 convex polygons, 2048^2 px, 8192^2 world"
+    if name == "diff2048_grad":
+        return sg.differentiable(0), ("150 convex polygons, 2048^2 px, 8192^2 world, 4 FP32 points + "
+                                      "1 FP32 segment, 100k agents")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -210,6 +213,89 @@ def run_batched(args, cfg_desc, scenes):
     batch.close()
 
 
+def run_differentiable(args, cfg_desc, scene):
+    """Differentiable form: one step = spm_compute + agent loss (forward) +
+    its adjoint w.r.t. the sources (backward), 100k agents; value = forward +
+    backward ms per step (lower is better)."""
+    import torch
+    import paper_1805_08500_gb300 as spm
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = spm.Scene(scene)
+    tuning = s.autotune(cache_key="diff2048_grad")  # set-up, not timed
+    agents = torch.tensor(np.asarray(scene.agents, np.int32), device=dev)
+    n_p, n_s = len(scene.points), len(scene.segs)
+    d_out, p_out = s.empty_outputs()
+    loss = torch.empty((), dtype=torch.float32, device=dev)
+    gp = torch.empty(2 * n_p, dtype=torch.float32, device=dev)
+    gs = torch.empty(4 * max(n_s, 1), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        s.compute(d_out, p_out, stream)
+        spm.spm_agents_forward(s.handle, stream, agents, d_out, p_out, loss)
+
+    for _ in range(args.warmup):
+        step()
+        spm.spm_agents_backward(s.handle, stream, gp, gs)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            spm.spm_agents_backward(s.handle, stream, gp, gs)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+    s.sync(stream)
+    fwd = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
+    bwd = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
+    # end to end: FP32 sources up from the host, the step, loss and gradients back
+    pts = np.asarray(scene.points, np.float32)
+    segs = np.asarray(scene.segs, np.float32)
+    h_out = torch.empty(1 + 2 * n_p + 4 * max(n_s, 1), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        spm.spm_scene_update_sources(s.handle, pts, segs)
+        step()
+        spm.spm_agents_backward(s.handle, stream, gp, gs)
+        h_out[:1].copy_(loss.reshape(1), non_blocking=True)
+        h_out[1:1 + 2 * n_p].copy_(gp, non_blocking=True)
+        h_out[1 + 2 * n_p:].copy_(gs, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+    info = s.info()
+    line = {"metric": "SPM differentiable step ms (forward + backward), 2048^2, 100k agents",
+            "value": fwd + bwd, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": fwd + bwd, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+i32 (f64 vertex costs, f64 gradient sums)", "data": "synthetic",
+            "config": {"workload": "diff2048_grad", "scene": cfg_desc, "agents": int(agents.shape[0]),
+                       "l2": "flushed between timed steps (256 MiB write)", "tuning": tuning},
+            "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(pts.nbytes + segs.nbytes),
+                    "d2h_bytes_per_step": int(h_out.numel() * 4)},
+            "gpu_launches": (info["kernels_per_compute"] + 4) * args.steps}  # + k_loss, 3 backward kernels
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build_oracle()
+        nthreads = oracle.default_threads()
+        t0 = time.perf_counter()
+        o = oracle.Oracle(scene, nthreads=nthreads)
+        o.agent_loss_and_grad(scene.agents)
+        used = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": used * 1e3, "unit": "ms", "cores": nthreads, "kind": "oracle",
+                                "sample": f"the full step: oracle vertex phase + all {len(scene.agents)} agents "
+                                          f"+ root-link gradients ({used:.1f} s wall)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,7 +303,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maze4096",
-                    choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048", "batched256"])
+                    choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048", "diff2048_grad",
+                             "batched256"])
     ap.add_argument("--cpu-pixels", type=int, default=3_000_000,
                     help="oracle pixel sample for the cpu_baseline leg")
     ap.add_argument("--ref-pixels", type=int, default=40_000,
@@ -234,6 +321,9 @@ def main():
         return
     if args.workload == "batched256":
         run_batched(args, cfg_desc, scene)
+        return
+    if args.workload == "diff2048_grad":
+        run_differentiable(args, cfg_desc, scene)
         return
 
     import torch
