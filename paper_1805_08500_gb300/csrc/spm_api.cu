@@ -237,7 +237,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         const int64_t ntiles = (int64_t)((hs.Nx + spm::kTileSmall - 1) / spm::kTileSmall) *
                                ((hs.Ny + spm::kTileSmall - 1) / spm::kTileSmall);
         set_tile(ds, (ds.hx >= 8.f || ds.hy >= 8.f) ? spm::kTileSmall : spm::kTile);
-        ds.use_flood = spm::flood_possible((int)ntiles) && spm::flood_smem_attr() ? 1 : 0;
+        ds.use_flood = spm::flood_possible((int)ntiles, ds.n_poly) && spm::flood_smem_attr() ? 1 : 0;
         ds.flood_mode = 0;
         ds.hidden_chunk = 32;
         const int64_t cap = std::min<int64_t>(std::max<int64_t>((int64_t)hs.n_gen * ntiles, 1),

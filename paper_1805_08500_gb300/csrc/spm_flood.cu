@@ -6,13 +6,14 @@
 // star-shaped from g: the segment from g to any such pixel stays inside the
 // cone and sees g all along. Every tile that segment crosses therefore holds
 // visible points. A breadth-first flood over tiles from g's tile, expanding a
-// tile only when it meets the cone and is not hidden from g by a single
-// polygon between it and g, thus reaches every tile where g can win (tiles are closed
-// rectangles that tile the plane; 8-neighbour steps follow any segment).
-// Each reached tile gets g in its candidate list. Segment interiors, points
-// outside the tile grid and floods that outgrow their queue go to a global
-// list that every tile scans. Any failure of the lists (pair capacity) sets a
-// flag and the pixel pass falls back to scanning every generator.
+// tile only when it meets the cone and is not provably hidden from g (by the
+// angular depth map below), thus reaches every tile where g can win (tiles
+// are closed rectangles that tile the plane; 8-neighbour steps follow any
+// segment). Each reached tile gets g in its candidate list. One CTA floods one
+// generator, a breadth-first level at a time. Segment interiors, points
+// outside the tile grid and floods whose level outgrows the frontier go to a
+// global list that every tile scans. Any failure of the lists (pair capacity)
+// sets a flag and the pixel pass falls back to scanning every generator.
 #include <cuda_runtime.h>
 
 #include "spm_device.cuh"
@@ -23,6 +24,7 @@ namespace {
 
 constexpr int kFloodThreads = 256;  // one CTA floods one generator at a time
 constexpr int kFront = 1024;        // frontier tiles per breadth-first level
+constexpr int kFloodPolyBits = 65536;  // polygons tracked for insertion (beyond: inserted again, harmless)
 
 // Full area of tile (tx, ty) in lattice units: closed rectangle, neighbours
 // share edges. Pixel i covers [i * pitch, (i + 1) * pitch].
@@ -50,132 +52,122 @@ __device__ __forceinline__ void push_global(const DevScene &ds, int g) {
     ds.glob_list[atomicAdd(&ds.flood_counts[1], 1)] = g;
 }
 
-// The bins that can hold a polygon hiding a tile from g: the thick segment
-// from the tile centre c to g (radius r, the tile's half diagonal + 1), cut
-// into strips of bins along its major axis. Each strip is one work item.
-struct StripWalk {
-    float pu, pw, du, dw, ou, ow, m;
-    int us, ustep, nstrips, nw;
-    bool xmaj;
-};
+// Angular depth map of one generator g (shadow volumes, in the spirit of the
+// shadow construction of Sec. 3.1): directions around g are cut into kAng
+// bins of a pseudo-angle; depth2[b] is an upper bound on the squared distance
+// from g at which every ray of bin b has crossed a front-facing obstacle edge
+// (g strictly on its outer side), i.e. entered an obstacle interior. A tile is
+// hidden from g when every bin its corners span has depth2 at most the tile's
+// squared nearest distance: each of its points lies beyond an obstacle
+// interior on its ray. Along an edge's line the crossing distance is convex in
+// the ray angle, so over a bin it peaks at one of the two boundary rays; the
+// boundary directions are exact multiples of 1/512, which makes the dot
+// products exact in integers and leaves a few float roundings (covered by a
+// 1e-5 relative margin). Polygons enter the map as the flood reaches their
+// tiles, so every test is conservative; unions of polygons (walls that
+// overlap at posts) hide tiles that no single polygon hides.
+constexpr int kAng = 2048;          // pseudo-angle bins over [0, 4)
+constexpr int kAngQ = kAng / 4;     // bins per quadrant (boundary m is pseudo-angle m / kAngQ)
+constexpr float kAngW = 4.0f / kAng;
+constexpr float kAngEps = 1e-4f;    // pseudo-angle margin (float error of pang is ~1e-6)
+constexpr int kInsCap = 1024;       // polygons inserted per level
 
-__device__ __forceinline__ int bin_clamp(float v, float o, float bs, int n) {
-    const int b = (int)floorf((v - o) / bs);
-    return b < 0 ? 0 : (b >= n ? n - 1 : b);
+// Pseudo-angle of direction (x, y) != 0: monotone in the true angle, [0, 4),
+// opposite directions differ by exactly 2.
+__device__ __forceinline__ float pang(float x, float y) {
+    const float r = __fdividef(fabsf(y), fabsf(x) + fabsf(y));
+    if (y >= 0.f) return x >= 0.f ? r : 2.f - r;
+    return x < 0.f ? 2.f + r : 4.f - r;
 }
 
-__device__ __forceinline__ StripWalk strip_walk(const DevScene &ds, int2 g, float cx, float cy, float r) {
-    StripWalk w;
-    const float tx = (float)g.x, ty = (float)g.y, bs = (float)ds.bin_size;
-    w.m = r + 1.0f;
-    w.xmaj = fabsf(tx - cx) >= fabsf(ty - cy);
-    w.pu = w.xmaj ? cx : cy;
-    w.pw = w.xmaj ? cy : cx;
-    const float qu = w.xmaj ? tx : ty, qw = w.xmaj ? ty : tx;
-    w.ou = w.xmaj ? (float)ds.bin_x0 : (float)ds.bin_y0;
-    w.ow = w.xmaj ? (float)ds.bin_y0 : (float)ds.bin_x0;
-    const int nu = w.xmaj ? ds.bin_nx : ds.bin_ny;
-    w.nw = w.xmaj ? ds.bin_ny : ds.bin_nx;
-    const int u0 = bin_clamp(fminf(w.pu, qu) - w.m, w.ou, bs, nu), u1 = bin_clamp(fmaxf(w.pu, qu) + w.m, w.ou, bs, nu);
-    w.ustep = qu >= w.pu ? 1 : -1;
-    w.us = w.ustep > 0 ? u0 : u1;
-    w.nstrips = u1 - u0 + 1;
-    w.du = qu - w.pu;
-    w.dw = qw - w.pw;
-    return w;
+// Pseudo-angle difference b - a wrapped into (-2, 2].
+__device__ __forceinline__ float pang_diff(float a, float b) {
+    float d = b - a;
+    if (d > 2.f) d -= 4.f;
+    if (d <= -2.f) d += 4.f;
+    return d;
 }
 
-// Upper bound on the bins one strip spans across the minor axis: the strip's
-// major-axis extent is bs + 2m, the segment moves |dw/du| per unit along it,
-// and the span grows by m on both sides.
-__device__ __forceinline__ int strip_bins_max(const DevScene &ds, const StripWalk &w) {
-    const float bs = (float)ds.bin_size;
-    const float slope = fabsf(w.du) < 0.5f ? 0.f : fabsf(w.dw / w.du);
-    const float span = fabsf(w.du) < 0.5f ? fabsf(w.dw) + 2.f * w.m : slope * (bs + 2.f * w.m) + 2.f * w.m;
-    return min((int)(span / bs) + 2, w.nw);
-}
-
-// Does one polygon in bin k of strip sidx hide every point of box from g?
-// Stops early once another item has found a hiding polygon for the same tile.
-__device__ __forceinline__ bool bin_hides(const DevScene &ds, const StripWalk &w, int sidx, int k, int2 g, int4 box, float cx,
-                          float cy, float r, const volatile int *stop) {
-    const float bs = (float)ds.bin_size;
-    const int u = w.us + w.ustep * sidx;
-    float wlo, whi;
-    if (fabsf(w.du) < 0.5f) {
-        wlo = fminf(w.pw, w.pw + w.dw);
-        whi = fmaxf(w.pw, w.pw + w.dw);
-    } else {
-        const float a = w.ou + u * bs - w.m, b = w.ou + (u + 1) * bs + w.m;
-        const float t0 = (a - w.pu) / w.du, t1 = (b - w.pu) / w.du;
-        float tl = fmaxf(0.f, fminf(t0, t1)), th = fminf(1.f, fmaxf(t0, t1));
-        if (tl > th) { tl = 0.f; th = 1.f; }
-        const float wa = w.pw + tl * w.dw, wb = w.pw + th * w.dw;
-        wlo = fminf(wa, wb);
-        whi = fmaxf(wa, wb);
+// Direction of bin boundary m, scaled by kAngQ: integer components.
+__device__ __forceinline__ int2 boundary_dir(int m) {
+    const int mm = m & (kAng - 1), f = mm & (kAngQ - 1);
+    switch (mm / kAngQ) {
+        case 0: return make_int2(kAngQ - f, f);
+        case 1: return make_int2(-f, kAngQ - f);
+        case 2: return make_int2(-(kAngQ - f), -f);
+        default: return make_int2(f, -(kAngQ - f));
     }
-    const int v = bin_clamp(wlo - w.m, w.ow, bs, w.nw) + k;
-    if (v > bin_clamp(whi + w.m, w.ow, bs, w.nw)) return false;
-    const float tx = (float)g.x, ty = (float)g.y;
-    const int bin = w.xmaj ? v * ds.bin_nx + u : u * ds.bin_nx + v;
-    const int e = __ldg(ds.bin_start + bin + 1);
-    for (int it = __ldg(ds.bin_start + bin); it < e; ++it) {
-        if (*stop) return false;
-        const int4 *rp = reinterpret_cast<const int4 *>(ds.bin_recs + it);
-        const int4 rbox = __ldg(rp), rmeta = __ldg(rp + 1);  // box; poly, voff, m
-        if (!seg_near_box(cx, cy, tx, ty, r, rbox)) continue;
-        const int2 *V = ds.poly_v + rmeta.y;
-        const int m = rmeta.z;
-        const unsigned mg = edge_mask(V, m, g.x, g.y);
-        if (poly_blocks(V, m, box.x, box.y, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.y, g.x, g.y, mg) &&
-            poly_blocks(V, m, box.x, box.w, g.x, g.y, mg) && poly_blocks(V, m, box.z, box.w, g.x, g.y, mg))
-            return true;
-    }
-    return false;
 }
 
 struct FloodSmem {
+    float depth2[kAng];
     int front[2][kFront];  // current / next breadth-first level
-    int pre[kFront + 1];   // exclusive prefix of (strip, bin) items per frontier tile
     int flag[kFront];      // 0 visible, 1 hidden, 2 outside the cone
+    int ins[kInsCap];      // polygons to insert before this level's tests
     int cnt[2];
+    int n_ins;
     int overflow;
-    int wsum[kFloodThreads / 32];
 };
 
-// Exclusive scan of v[0..n) in place (n <= kFront), v[n] = total. All threads.
-__device__ void cta_scan(int *v, int n, int *wsum) {
-    constexpr int per = (kFront + kFloodThreads - 1) / kFloodThreads;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int loc[per];
-    int s = 0;
+// Is the closed box hidden from g (lattice point, not inside the box) by the
+// depth map?
+__device__ bool box_hidden_ang(const float *depth2, int2 g, int4 box) {
+    const long long dx = max(max(box.x - g.x, g.x - box.z), 0), dy = max(max(box.y - g.y, g.y - box.w), 0);
+    const float mind2 = (float)(dx * dx + dy * dy) * (1.f - 1e-6f);
+    const float c0 = pang(0.5f * (float)(box.x + box.z) - (float)g.x, 0.5f * (float)(box.y + box.w) - (float)g.y);
+    float lo = 0.f, hi = 0.f;
+    const int cx[4] = {box.x, box.z, box.x, box.z}, cy[4] = {box.y, box.y, box.w, box.w};
 #pragma unroll
-    for (int k = 0; k < per; ++k) {
-        const int i = threadIdx.x * per + k;
-        loc[k] = i < n ? v[i] : 0;
-        s += loc[k];
+    for (int k = 0; k < 4; ++k) {
+        const float d = pang_diff(c0, pang((float)(cx[k] - g.x), (float)(cy[k] - g.y)));
+        lo = fminf(lo, d);
+        hi = fmaxf(hi, d);
     }
-    int inc = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
+    const int k0 = (int)floorf((c0 + lo - kAngEps) / kAngW), k1 = (int)floorf((c0 + hi + kAngEps) / kAngW);
+    for (int k = k0; k <= k1; ++k)
+        if (!(depth2[(k + 2 * kAng) & (kAng - 1)] <= mind2)) return false;
+    return true;
+}
+
+// Inserts edge i of polygon q into the depth map if it is front-facing.
+__device__ void insert_edge(const DevScene &ds, float *depth2, int2 g, int q, int i) {
+    const int b = ds.poly_off[q], m = ds.poly_off[q + 1] - b;
+    if (i >= m) return;
+    const int2 a = ds.poly_v[b + i], c = ds.poly_v[b + (i + 1 == m ? 0 : i + 1)];
+    if (orient32(a.x, a.y, c.x, c.y, g.x, g.y) >= 0) return;  // not front-facing
+    // line normal n (left of a -> c); g is on its negative side, so
+    // n . (a - g) > 0 and n . u > 0 for every ray u that meets the edge
+    const int nx = -(c.y - a.y), ny = c.x - a.x;
+    const long long N = (long long)nx * (a.x - g.x) + (long long)ny * (a.y - g.y);
+    const float fN2 = (float)N * (float)N;
+    // no ray crosses the line closer than its distance from g
+    const float h2 = __fdividef(fN2, (float)nx * (float)nx + (float)ny * (float)ny) * (1.f - 1e-5f);
+    // the edge runs clockwise seen from g: its angle range goes
+    // counter-clockwise from c to a
+    const float lo = pang((float)(c.x - g.x), (float)(c.y - g.y));
+    const float hi = lo + fmodf(pang((float)(a.x - g.x), (float)(a.y - g.y)) - lo + 4.f, 4.f);
+    const int k0 = (int)ceilf((lo + kAngEps) / kAngW), k1 = (int)floorf((hi - kAngEps) / kAngW) - 1;
+    auto bdist2 = [&](int mb) {  // squared crossing distance along boundary ray mb, rounded up
+        const int2 u = boundary_dir(mb);
+        const float fD = (float)(nx * u.x + ny * u.y);  // exact: |n| < 2^16, |u| <= 512
+        return __fdividef(fN2 * (float)(u.x * u.x + u.y * u.y), fD * fD) * (1.f + 1e-5f);
+    };
+    float prev = -1.f;  // boundary k's value when known
+    for (int k = k0; k <= k1; ++k) {
+        int *slot = (int *)&depth2[k & (kAng - 1)];
+        if (__int_as_float(*slot) <= h2) {  // this edge cannot lower the bin
+            prev = -1.f;
+            continue;
+        }
+        if (prev < 0.f) prev = bdist2(k);
+        const float next = bdist2(k + 1);
+        atomicMin(slot, __float_as_int(fmaxf(prev, next)));  // non-negative floats order as ints
+        prev = next;
     }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    int run = inc - s;
-    for (int w = 0; w < warp; ++w) run += wsum[w];
-#pragma unroll
-    for (int k = 0; k < per; ++k) {
-        const int i = threadIdx.x * per + k;
-        if (i < n) v[i] = run;
-        run += loc[k];
-    }
-    if (threadIdx.x == kFloodThreads - 1) v[n] = run;
 }
 
 __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
-    extern __shared__ unsigned visited[];
+    extern __shared__ unsigned fdyn[];
     __shared__ FloodSmem sm;
     if (ds.flood_mode == 0) {  // automatic: flood only sparse visibility graphs
         const double pairs = (double)ds.n_gen * (double)max(ds.n_vert, 1);
@@ -186,6 +178,8 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
     }
     const int tid = threadIdx.x;
     const int ntiles = ds.tiles_x * ds.tiles_y, words = (ntiles + 31) / 32;
+    const int pwords = ds.n_poly <= kFloodPolyBits ? (ds.n_poly + 31) / 32 : 0;
+    unsigned *visited = fdyn, *seen = fdyn + words;  // tiles reached; polygons inserted
     const int tpx = ds.tile * (ds.S * ds.Wx / ds.Nx), tpy = ds.tile * (ds.S * ds.Wy / ds.Ny);
     for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) {
         if (!(ds.gen_costf[g] < INFINITY)) continue;
@@ -199,11 +193,13 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
         const int2 gl = ds.gen_lat[g];
         const int4 cone = kind == kVert ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
         const int tx = gl.x >= 0 ? gl.x / tpx : -1, ty = gl.y >= 0 ? gl.y / tpy : -1;
-        __syncthreads();  // the previous generator's last level is done with smem
-        for (int w = tid; w < words; w += kFloodThreads) visited[w] = 0u;
+        __syncthreads();  // the previous generator is done with smem
+        for (int w = tid; w < words + pwords; w += kFloodThreads) fdyn[w] = 0u;
+        for (int k = tid; k < kAng; k += kFloodThreads) sm.depth2[k] = INFINITY;
         if (tid == 0) {
             sm.cnt[0] = 0;
             sm.overflow = 0;
+            sm.n_ins = 0;
         }
         __syncthreads();
         // seeds: every tile whose closed area contains g (up to 4 when g lies on tile edges)
@@ -224,7 +220,7 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
             continue;
         }
 #ifdef SPM_COUNT
-        int n_tests = 0;
+        int n_tests = 0, n_levels = 0;
 #endif
         int p = 0;
         for (;;) {
@@ -238,45 +234,48 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
             const int nc = min(sm.cnt[p], kFront);
             if (nc == 0) break;
             const int *cur = sm.front[p];
-            // A: cone test and strip count per frontier tile
+            // A: the polygons in the frontier tiles' bins enter the depth map
+            for (int q = tid; q < nc * 16; q += kFloodThreads) {  // (tile, one of its first 16 bins)
+                const int i = q >> 4, j = q & 15;
+                const int t = cur[i];
+                const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
+                const int bx0 = max(0, (area.x - ds.bin_x0) / ds.bin_size), by0 = max(0, (area.y - ds.bin_y0) / ds.bin_size);
+                const int bx1 = min(ds.bin_nx - 1, (area.z - ds.bin_x0) / ds.bin_size);
+                const int by1 = min(ds.bin_ny - 1, (area.w - ds.bin_y0) / ds.bin_size);
+                const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
+                for (int jj = j; jj < nbx * nby; jj += 16) {
+                    const int bin = (by0 + jj / nbx) * ds.bin_nx + bx0 + jj % nbx;
+                    const int e = __ldg(ds.bin_start + bin + 1);
+                    for (int it = __ldg(ds.bin_start + bin); it < e; ++it) {
+                        const int poly = __ldg(reinterpret_cast<const int *>(ds.bin_recs + it) + 4);
+                        if (pwords) {
+                            const unsigned bit = 1u << (poly & 31);
+                            if (atomicOr(&seen[poly >> 5], bit) & bit) continue;
+                        }
+                        const int slot = atomicAdd(&sm.n_ins, 1);
+                        if (slot < kInsCap) sm.ins[slot] = poly;  // beyond the cap: left out (conservative)
+                    }
+                }
+            }
+            __syncthreads();
+            const int ni = min(sm.n_ins, kInsCap);
+            for (int q = tid; q < ni * kMaxPolyVerts; q += kFloodThreads)  // (polygon, edge) items
+                insert_edge(ds, sm.depth2, gl, sm.ins[q / kMaxPolyVerts], q % kMaxPolyVerts);
+            __syncthreads();
+            // B: cone and depth-map test per frontier tile
             for (int i = tid; i < nc; i += kFloodThreads) {
                 const int t = cur[i];
                 const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
-                const bool ok = cone_meets_box(ct, cone, gl, area);
-                int ns = 0;
-                if (ok) {
-                    const float acx = 0.5f * ((float)area.x + (float)area.z), acy = 0.5f * ((float)area.y + (float)area.w);
-                    const float ar = 0.5f * sqrtf((float)(area.z - area.x) * (float)(area.z - area.x) +
-                                                  (float)(area.w - area.y) * (float)(area.w - area.y)) + 1.0f;
-                    const StripWalk w = strip_walk(ds, gl, acx, acy, ar);
-                    ns = w.nstrips * strip_bins_max(ds, w);
+                int f = 2;
+                if (cone_meets_box(ct, cone, gl, area)) {
+                    const bool inside = gl.x >= area.x && gl.x <= area.z && gl.y >= area.y && gl.y <= area.w;
+                    f = !inside && box_hidden_ang(sm.depth2, gl, area) ? 1 : 0;
                 }
-                sm.flag[i] = ok ? 0 : 2;
-                sm.pre[i] = ns;
+                sm.flag[i] = f;
             }
-            if (tid == 0) sm.cnt[p ^ 1] = 0;
-            __syncthreads();
-            cta_scan(sm.pre, nc, sm.wsum);
-            __syncthreads();
-            // B: every (tile, strip, bin) item in parallel; a hiding polygon sets the tile's flag
-            const int total = sm.pre[nc];
-            for (int j = tid; j < total; j += kFloodThreads) {
-                int lo = 0, hi = nc;  // pre[lo] <= j < pre[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (sm.pre[mid] <= j) lo = mid;
-                    else hi = mid;
-                }
-                volatile int *fl = &sm.flag[lo];
-                if (*fl) continue;
-                const int t = cur[lo];
-                const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
-                const float acx = 0.5f * ((float)area.x + (float)area.z), acy = 0.5f * ((float)area.y + (float)area.w);
-                const float ar = 0.5f * sqrtf((float)(area.z - area.x) * (float)(area.z - area.x) +
-                                              (float)(area.w - area.y) * (float)(area.w - area.y)) + 1.0f;
-                const StripWalk w = strip_walk(ds, gl, acx, acy, ar);
-                const int kb = strip_bins_max(ds, w), q = j - sm.pre[lo];
-                if (bin_hides(ds, w, q / kb, q - (q / kb) * kb, gl, area, acx, acy, ar, fl)) *fl = 1;
+            if (tid == 0) {
+                sm.cnt[p ^ 1] = 0;
+                sm.n_ins = 0;
             }
             __syncthreads();
             // C: emit visible tiles, queue their fresh 8-neighbours
@@ -311,8 +310,10 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
                 else sm.overflow = 1;
             }
 #ifdef SPM_COUNT
-            if (tid == 0)
+            if (tid == 0) {
+                ++n_levels;
                 for (int i = 0; i < nc; ++i) n_tests += sm.flag[i] != 2;
+            }
 #endif
             __syncthreads();
             p ^= 1;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
 #ifdef SPM_COUNT
         if (tid == 0) {
             SPM_CNT_MAX(14, n_tests);
-            SPM_CNT(15, n_tests > 256 ? 1 : 0);
+            SPM_CNT_MAX(15, n_levels);
         }
 #endif
     }
@@ -355,11 +356,11 @@ __global__ void k_tiles_fill(DevScene ds) {
 
 }  // namespace
 
-size_t flood_smem_bytes(int tiles) {  // dynamic part: the visited bitmap
-    return sizeof(unsigned) * (size_t)((tiles + 31) / 32);
+size_t flood_smem_bytes(int tiles, int polys) {  // dynamic part: visited tiles, inserted polygons
+    return sizeof(unsigned) * (size_t)((tiles + 31) / 32 + (polys <= kFloodPolyBits ? (polys + 31) / 32 : 0));
 }
 
-bool flood_possible(int tiles) { return flood_smem_bytes(tiles) + sizeof(FloodSmem) <= 200 * 1024; }
+bool flood_possible(int tiles, int polys) { return flood_smem_bytes(tiles, polys) + sizeof(FloodSmem) <= 200 * 1024; }
 
 void launch_flood(const DevScene &ds, cudaStream_t st) {
     const int ntiles = ds.tiles_x * ds.tiles_y;
@@ -370,8 +371,8 @@ void launch_flood(const DevScene &ds, cudaStream_t st) {
     }
     cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
     cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
-    const size_t smem = flood_smem_bytes(ntiles);
-    const int blocks = min(152 * 4, ds.n_gen);
+    const size_t smem = flood_smem_bytes(ntiles, ds.n_poly);
+    const int blocks = min(152 * 8, ds.n_gen);
     k_flood<<<max(blocks, 1), kFloodThreads, smem, st>>>(ds);
     k_tiles_scan<<<1, 1024, 0, st>>>(ds);
     k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds);

@@ -167,7 +167,7 @@ void launch_flood(const DevScene &ds, cudaStream_t st);
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);
 int sssp_batched_grid_blocks();
-bool flood_possible(int tiles);
+bool flood_possible(int tiles, int polys);
 int flood_smem_attr();
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)
