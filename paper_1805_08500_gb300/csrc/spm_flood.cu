@@ -129,40 +129,35 @@ __device__ bool box_hidden_ang(const float *depth2, int2 g, int4 box) {
     return true;
 }
 
-// Inserts edge i of polygon q into the depth map if it is front-facing.
-__device__ void insert_edge(const DevScene &ds, float *depth2, int2 g, int q, int i) {
+// One warp inserts polygon q's front-facing edges into the depth map, the
+// lanes spread over each edge's bins.
+__device__ void insert_polygon_warp(const DevScene &ds, float *depth2, int2 g, int q, int lane) {
     const int b = ds.poly_off[q], m = ds.poly_off[q + 1] - b;
-    if (i >= m) return;
-    const int2 a = ds.poly_v[b + i], c = ds.poly_v[b + (i + 1 == m ? 0 : i + 1)];
-    if (orient32(a.x, a.y, c.x, c.y, g.x, g.y) >= 0) return;  // not front-facing
-    // line normal n (left of a -> c); g is on its negative side, so
-    // n . (a - g) > 0 and n . u > 0 for every ray u that meets the edge
-    const int nx = -(c.y - a.y), ny = c.x - a.x;
-    const long long N = (long long)nx * (a.x - g.x) + (long long)ny * (a.y - g.y);
-    const float fN2 = (float)N * (float)N;
-    // no ray crosses the line closer than its distance from g
-    const float h2 = __fdividef(fN2, (float)nx * (float)nx + (float)ny * (float)ny) * (1.f - 1e-5f);
-    // the edge runs clockwise seen from g: its angle range goes
-    // counter-clockwise from c to a
-    const float lo = pang((float)(c.x - g.x), (float)(c.y - g.y));
-    const float hi = lo + fmodf(pang((float)(a.x - g.x), (float)(a.y - g.y)) - lo + 4.f, 4.f);
-    const int k0 = (int)ceilf((lo + kAngEps) / kAngW), k1 = (int)floorf((hi - kAngEps) / kAngW) - 1;
-    auto bdist2 = [&](int mb) {  // squared crossing distance along boundary ray mb, rounded up
-        const int2 u = boundary_dir(mb);
-        const float fD = (float)(nx * u.x + ny * u.y);  // exact: |n| < 2^16, |u| <= 512
-        return __fdividef(fN2 * (float)(u.x * u.x + u.y * u.y), fD * fD) * (1.f + 1e-5f);
-    };
-    float prev = -1.f;  // boundary k's value when known
-    for (int k = k0; k <= k1; ++k) {
-        int *slot = (int *)&depth2[k & (kAng - 1)];
-        if (__int_as_float(*slot) <= h2) {  // this edge cannot lower the bin
-            prev = -1.f;
-            continue;
+    for (int i = 0; i < m; ++i) {
+        const int2 a = ds.poly_v[b + i], c = ds.poly_v[b + (i + 1 == m ? 0 : i + 1)];
+        if (orient32(a.x, a.y, c.x, c.y, g.x, g.y) >= 0) continue;  // not front-facing
+        // line normal n (left of a -> c); g is on its negative side, so
+        // n . (a - g) > 0 and n . u > 0 for every ray u that meets the edge
+        const int nx = -(c.y - a.y), ny = c.x - a.x;
+        const long long N = (long long)nx * (a.x - g.x) + (long long)ny * (a.y - g.y);
+        const float fN2 = (float)N * (float)N;
+        // no ray crosses the line closer than its distance from g
+        const float h2 = __fdividef(fN2, (float)nx * (float)nx + (float)ny * (float)ny) * (1.f - 1e-5f);
+        // the edge runs clockwise seen from g: its angle range goes
+        // counter-clockwise from c to a
+        const float lo = pang((float)(c.x - g.x), (float)(c.y - g.y));
+        const float hi = lo + fmodf(pang((float)(a.x - g.x), (float)(a.y - g.y)) - lo + 4.f, 4.f);
+        const int k0 = (int)ceilf((lo + kAngEps) / kAngW), k1 = (int)floorf((hi - kAngEps) / kAngW) - 1;
+        auto bdist2 = [&](int mb) {  // squared crossing distance along boundary ray mb, rounded up
+            const int2 u = boundary_dir(mb);
+            const float fD = (float)(nx * u.x + ny * u.y);  // exact: |n| < 2^16, |u| <= 512
+            return __fdividef(fN2 * (float)(u.x * u.x + u.y * u.y), fD * fD) * (1.f + 1e-5f);
+        };
+        for (int k = k0 + lane; k <= k1; k += 32) {
+            int *slot = (int *)&depth2[k & (kAng - 1)];
+            if (__int_as_float(*slot) <= h2) continue;  // this edge cannot lower the bin
+            atomicMin(slot, __float_as_int(fmaxf(bdist2(k), bdist2(k + 1))));  // non-negative floats order as ints
         }
-        if (prev < 0.f) prev = bdist2(k);
-        const float next = bdist2(k + 1);
-        atomicMin(slot, __float_as_int(fmaxf(prev, next)));  // non-negative floats order as ints
-        prev = next;
     }
 }
 
@@ -259,8 +254,8 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
             }
             __syncthreads();
             const int ni = min(sm.n_ins, kInsCap);
-            for (int q = tid; q < ni * kMaxPolyVerts; q += kFloodThreads)  // (polygon, edge) items
-                insert_edge(ds, sm.depth2, gl, sm.ins[q / kMaxPolyVerts], q % kMaxPolyVerts);
+            for (int q = tid >> 5; q < ni; q += kFloodThreads / 32)
+                insert_polygon_warp(ds, sm.depth2, gl, sm.ins[q], tid & 31);
             __syncthreads();
             // B: cone and depth-map test per frontier tile
             for (int i = tid; i < nc; i += kFloodThreads) {
