@@ -36,18 +36,17 @@ constexpr int kSsspThreads = 256;
 constexpr int kSoloThreads = 512;
 constexpr int kSoloSmem = 226 * 1024;  // within the 227 KB opt-in maximum, with the static part
 
-// Static filter + exact visibility for one (u, v) pair.
-__device__ bool pair_edge(const DevScene &ds, int u, int v) {
+// Static filter for one (u, v) pair: tangency at both ends, or for a
+// segment interior u a perpendicular foot strictly inside the segment.
+__device__ bool pair_filter(const DevScene &ds, int u, int v) {
     if (u == v) return false;
     const int ku = ds.gen_kind[u];
     const int2 vl = ds.gen_lat[v];
     if (ku == kSegI) {
-        int4 L = ds.seg_lat[ds.gen_aux[u]];
-        long long ux = L.z - L.x, uy = L.w - L.y;
-        long long num = (vl.x - L.x) * ux + (vl.y - L.y) * uy;
-        long long den = ux * ux + uy * uy;
-        if (!(num > 0 && num < den)) return false;
-        return visible_foot(ds, ds.gen_aux[u], vl.x, vl.y, num, den);
+        const int4 L = ds.seg_lat[ds.gen_aux[u]];
+        const long long ux = L.z - L.x, uy = L.w - L.y;
+        const long long num = (vl.x - L.x) * ux + (vl.y - L.y) * uy;
+        return num > 0 && num < ux * ux + uy * uy;
     }
     const int2 ul = ds.gen_lat[u];
     if (ul.x == vl.x && ul.y == vl.y) return false;
@@ -57,37 +56,86 @@ __device__ bool pair_edge(const DevScene &ds, int u, int v) {
         const int a = cross32(wx, wy, w.x, w.y), b = cross32(wx, wy, w.z, w.w);
         if ((a > 0 && b < 0) || (a < 0 && b > 0)) return false;
     }
-    {   // tangent at v: an arrival pointing into v's wedge leaves v an empty
-        // shadow cone, so v could never pass such a path on
-        const int4 w = ds.gen_wedge[v];
-        const int a = cross32(wx, wy, w.x, w.y), b = cross32(wx, wy, w.z, w.w);
-        if ((a > 0 && b < 0) || (a < 0 && b > 0)) return false;
+    // tangent at v: an arrival pointing into v's wedge leaves v an empty
+    // shadow cone, so v could never pass such a path on
+    const int4 w = ds.gen_wedge[v];
+    const int a = cross32(wx, wy, w.x, w.y), b = cross32(wx, wy, w.z, w.w);
+    return !((a > 0 && b < 0) || (a < 0 && b > 0));
+}
+
+// Exact visibility of a pair that passed the filter.
+__device__ bool pair_visible(const DevScene &ds, int u, int v) {
+    const int2 vl = ds.gen_lat[v];
+    if (ds.gen_kind[u] == kSegI) {
+        const int s = ds.gen_aux[u];
+        const int4 L = ds.seg_lat[s];
+        const long long ux = L.z - L.x, uy = L.w - L.y;
+        return visible_foot(ds, s, vl.x, vl.y, (vl.x - L.x) * ux + (vl.y - L.y) * uy, ux * ux + uy * uy);
     }
+    const int2 ul = ds.gen_lat[u];
     return visible_points(ds, vl.x, vl.y, ul.x, ul.y);
 }
 
-// One warp task: row vv (vertex index) of the bit matrix, word w covering
-// generators 32w..32w+31. The matrix starts zeroed. A pair of obstacle
-// vertices passes the filter and sees each other symmetrically (both
-// tangency tests and the blocking predicate are symmetric in the two
-// points), so only generators u < v are tested here and an edge between two
-// vertices also sets its mirror bit in u's row.
-__device__ __forceinline__ void vis_pairs_task(const DevScene &ds, long long t, int lane) {
-    const int vv = (int)(t / ds.vis_words), w = (int)(t % ds.vis_words);
-    const int u = w * 32 + lane, v = ds.n_src + vv;
-    if (w * 32 >= v) return;  // the whole word lies at or above the diagonal (warp-uniform)
-    const bool e = u < v && pair_edge(ds, u, v);
-    const unsigned bits = __ballot_sync(0xffffffffu, e);
-    if (lane == 0 && bits) atomicOr(&ds.vis_bits[(size_t)vv * ds.vis_words + w], bits);
-    if (e && u >= ds.n_src) atomicOr(&ds.vis_bits[(size_t)(u - ds.n_src) * ds.vis_words + (v >> 5)], 1u << (v & 31));
+// Sets the bit of edge u -> v (row v) and, between two obstacle vertices,
+// its mirror v -> u (row u). The matrix starts zeroed.
+__device__ __forceinline__ void set_edge_bits(const DevScene &ds, int u, int v) {
+    atomicOr(&ds.vis_bits[(size_t)(v - ds.n_src) * ds.vis_words + (u >> 5)], 1u << (u & 31));
+    if (u >= ds.n_src) atomicOr(&ds.vis_bits[(size_t)(u - ds.n_src) * ds.vis_words + (v >> 5)], 1u << (v & 31));
+}
+
+// Visibility pairs of one or many scenes. A warp task is row vv (vertex
+// index) of a scene's bit matrix and word w covering generators
+// 32w..32w+31. A pair of obstacle vertices passes the filter and sees each
+// other symmetrically (both tangency tests and the blocking predicate are
+// symmetric in the two points), so only generators u < v are tested and an
+// edge between two vertices also sets its mirror bit. Pairs that pass the
+// filter queue up per warp in shared memory and are walked 32 at a time, so
+// every lane walks (the filter passes a few lanes of each word).
+constexpr int kPairQ = 64;
+struct PairQ {
+    int3 e[kVisThreads / 32][kPairQ];  // (scene, u, v)
+};
+
+template <class Scene, class Task>
+__device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, Scene scene_of_task, Task task_of) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long warps = (long long)gridDim.x * (kVisThreads / 32);
+    int qn = 0;  // warp-uniform queue length
+    auto walk = [&](int n) {  // lanes < n walk the last n queued pairs
+        if (lane < n) {
+            const int3 pr = q.e[warp][qn - n + lane];
+            const DevScene &ds = *scene_of_task(pr.x);
+            if (pair_visible(ds, pr.y, pr.z)) set_edge_bits(ds, pr.y, pr.z);
+        }
+        qn -= n;
+        __syncwarp();
+    };
+    for (long long t = (long long)blockIdx.x * (kVisThreads / 32) + warp; t < tasks; t += warps) {
+        int sc;
+        long long lt;
+        task_of(t, sc, lt);
+        const DevScene &ds = *scene_of_task(sc);
+        const int vv = (int)(lt / ds.vis_words), w = (int)(lt % ds.vis_words);
+        const int u = w * 32 + lane, v = ds.n_src + vv;
+        if (w * 32 >= v) continue;  // the whole word lies at or above the diagonal (warp-uniform)
+        const bool c = u < v && pair_filter(ds, u, v);
+        const unsigned bal = __ballot_sync(0xffffffffu, c);
+        if (c) q.e[warp][qn + __popc(bal & ((1u << lane) - 1u))] = make_int3(sc, u, v);
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) walk(32);
+    }
+    if (qn > 0) walk(qn);
 }
 
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds) {
-    const int lane = threadIdx.x & 31;
-    const long long tasks = (long long)ds.n_vert * ds.vis_words;
-    const long long warps = (long long)gridDim.x * (kVisThreads / 32);
-    for (long long t = (long long)blockIdx.x * (kVisThreads / 32) + (threadIdx.x >> 5); t < tasks; t += warps)
-        vis_pairs_task(ds, t, lane);
+    __shared__ PairQ q;
+    vis_pairs_run(
+        q, (long long)ds.n_vert * ds.vis_words, [&](int) { return &ds; },
+        [&](long long t, int &sc, long long &lt) {
+            sc = 0;
+            lt = t;
+        });
 }
 
 // In-degree per vertex row and out-degree per generator: one warp per row,
@@ -565,13 +613,13 @@ __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
 }
 
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs_b(const __grid_constant__ BatchDev b) {
-    const int lane = threadIdx.x & 31;
-    const long long tasks = b.pair_off[b.n];
-    const long long warps = (long long)gridDim.x * (kVisThreads / 32);
-    for (long long t = (long long)blockIdx.x * (kVisThreads / 32) + (threadIdx.x >> 5); t < tasks; t += warps) {
-        const int s = scene_of(b.pair_off, b.n, t);
-        vis_pairs_task(b.scenes[s], t - b.pair_off[s], lane);
-    }
+    __shared__ PairQ q;
+    vis_pairs_run(
+        q, b.pair_off[b.n], [&](int s) { return b.scenes + s; },
+        [&](long long t, int &sc, long long &lt) {
+            sc = scene_of(b.pair_off, b.n, t);
+            lt = t - b.pair_off[sc];
+        });
 }
 
 __global__ void k_edges_count_b(const __grid_constant__ BatchDev b) {
