@@ -279,6 +279,31 @@ static __device__ unsigned long long g_count[16];  // one copy per translation u
 #define SPM_CNT_MAX(i, v) ((void)0)
 #endif
 
+// Phase clocks of an instrumentation build (-DSPM_TIME); compiled out otherwise.
+#ifdef SPM_TIME
+// phase clocks of thread 0 (CTA wall time, barriers included), kept in
+// registers and added to the global totals once at the end
+static __device__ unsigned long long g_time[8];
+#define SPM_T0()                                 \
+    long long spm_t_ = clock64();                \
+    unsigned long long spm_acc_[8] = {0, 0, 0, 0, 0, 0, 0, 0}
+#define SPM_LAP(i)                                              \
+    do {                                                        \
+        const long long n_ = clock64();                         \
+        spm_acc_[i] += (unsigned long long)(n_ - spm_t_);       \
+        spm_t_ = n_;                                            \
+    } while (0)
+#define SPM_TFLUSH()                                                          \
+    do {                                                                      \
+        if (threadIdx.x == 0)                                                 \
+            for (int i_ = 0; i_ < 8; ++i_) atomicAdd(&::spm::g_time[i_], spm_acc_[i_]); \
+    } while (0)
+#else
+#define SPM_T0() ((void)0)
+#define SPM_LAP(i) ((void)0)
+#define SPM_TFLUSH() ((void)0)
+#endif
+
 // True when one polygon hides every point of the box from the point
 // generator at lattice point g. The set of points whose open segment to g
 // meets a convex polygon's interior is convex, so it suffices that the four

@@ -51,38 +51,64 @@ struct PixSmem {
     float tile_ub;
 };
 
-// Does the interior of convex polygon V meet the convex hull of the tile box
-// and point t? Exact separating-axis test over the polygon's edges and the
-// candidate hull edges (box edges, and lines from t through each corner).
-__device__ bool poly_meets_hull(const int2 *V, int m, int4 box, int tx, int ty) {
-    const int px[5] = {box.x, box.z, box.z, box.x, tx}, py[5] = {box.y, box.y, box.w, box.w, ty};
+// Convex hull (counter-clockwise, no repeated or collinear vertices) of the
+// tile's pixel-centre box and the lattice point t, by Andrew's monotone chain
+// over the 5 points. The box may be degenerate (a one-pixel row or column),
+// so the hull may be a segment (2 vertices) or a point (1).
+struct Hull {
+    int2 v[5];
+    int n;
+};
+
+__device__ __forceinline__ Hull hull_box_point(int4 box, int tx, int ty) {
+    int2 p[5] = {make_int2(box.x, box.y), make_int2(box.z, box.y), make_int2(box.z, box.w), make_int2(box.x, box.w),
+                 make_int2(tx, ty)};
+#pragma unroll
+    for (int i = 1; i < 5; ++i)  // sort by (x, y)
+#pragma unroll
+        for (int j = i; j > 0; --j)
+            if (p[j].x < p[j - 1].x || (p[j].x == p[j - 1].x && p[j].y < p[j - 1].y)) {
+                const int2 t = p[j];
+                p[j] = p[j - 1];
+                p[j - 1] = t;
+            }
+    int2 st[10];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {  // lower chain
+        while (k >= 2 && orient32(st[k - 2].x, st[k - 2].y, st[k - 1].x, st[k - 1].y, p[i].x, p[i].y) <= 0) --k;
+        st[k++] = p[i];
+    }
+    const int lower = k + 1;
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {  // upper chain
+        while (k >= lower && orient32(st[k - 2].x, st[k - 2].y, st[k - 1].x, st[k - 1].y, p[i].x, p[i].y) <= 0) --k;
+        st[k++] = p[i];
+    }
+    Hull h;
+    h.n = k > 1 ? k - 1 : 1;  // the last point repeats the first
+    if (h.n == 2 && st[0].x == st[1].x && st[0].y == st[1].y) h.n = 1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) h.v[i] = st[i < h.n ? i : 0];
+    return h;
+}
+
+// Does the interior of convex polygon V meet the closed convex hull H?
+// Separating-axis test over the edges of both (an edge separates when the
+// other body lies on its closed outer side).
+__device__ bool poly_meets_hull(const int2 *V, int m, const Hull &H) {
     for (int i = 0; i < m; ++i) {  // polygon edges (outward side is orient < 0)
         const int2 a = V[i], b = V[i + 1 == m ? 0 : i + 1];
         bool all_out = true;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) all_out &= orient32(a.x, a.y, b.x, b.y, px[k], py[k]) <= 0;
+        for (int k = 0; k < H.n && all_out; ++k) all_out = orient32(a.x, a.y, b.x, b.y, H.v[k].x, H.v[k].y) <= 0;
         if (all_out) return false;
     }
-#pragma unroll
-    for (int l = 0; l < 8; ++l) {  // 4 box edges, 4 lines t -> corner
-        const int ax = l < 4 ? px[l] : tx, ay = l < 4 ? py[l] : ty;
-        const int bx = l < 4 ? px[(l + 1) & 3] : px[l - 4], by = l < 4 ? py[(l + 1) & 3] : py[l - 4];
-        if (ax == bx && ay == by) continue;
-        bool hpos = true, hneg = true;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const int o = orient32(ax, ay, bx, by, px[k], py[k]);
-            hpos &= o >= 0;
-            hneg &= o <= 0;
-        }
-        if (!hpos && !hneg) continue;
-        bool ppos = true, pneg = true;
-        for (int i = 0; i < m; ++i) {
-            const int o = orient32(ax, ay, bx, by, V[i].x, V[i].y);
-            ppos &= o >= 0;
-            pneg &= o <= 0;
-        }
-        if ((hpos && pneg) || (hneg && ppos)) return false;
+    for (int j = 0; j < H.n; ++j) {  // hull edges
+        const int2 a = H.v[j], b = H.v[j + 1 == H.n ? 0 : j + 1];
+        if (a.x == b.x && a.y == b.y) continue;  // a one-point hull has no edge
+        bool all_out = true;
+        for (int i = 0; i < m && all_out; ++i) all_out = orient32(a.x, a.y, b.x, b.y, V[i].x, V[i].y) <= 0;
+        if (all_out) return false;
     }
     return true;
 }
@@ -186,6 +212,7 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
     const int c0 = bin_of(fminf(cx, tx) - m, x0, ds.bin_nx), c1 = bin_of(fmaxf(cx, tx) + m, x0, ds.bin_nx);
     const float dx = tx - cx, dy = ty - cy;
     const bool dedup = ds.n_poly <= kDedupBits;
+    const Hull hull = hull_box_point(box, tl.x, tl.y);  // used for point targets only
     // items per column: about the rows one column spans (its x extent is
     // bs + 2m, the segment rises |dy/dx| per unit along it, plus m on both
     // sides); each item strides by K, so any K covers every row
@@ -220,7 +247,7 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
                     if (atomicOr(&sm.dedup[k >> 5], bit) & bit) continue;
                 }
                 if (!seg_near_box(cx, cy, tx, ty, r, rec.box)) continue;
-                if (kind != kSegI && !poly_meets_hull(ds.poly_v + rec.voff, rec.m, box, tl.x, tl.y)) continue;
+                if (kind != kSegI && !poly_meets_hull(ds.poly_v + rec.voff, rec.m, hull)) continue;
                 const int slot = atomicAdd(&sm.n_block, 1);
                 if (slot >= kBlockCap) {
                     sm.overflow = 1;
@@ -251,6 +278,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                                            int32_t *__restrict__ parent, PixSmem &sm, const bool allow_lists) {
     constexpr int T = PX == 4 ? 32 : 16;
     constexpr int TPR = T / PX;  // threads per tile row
+    SPM_T0();
     const int i0 = (tile % ds.tiles_x) * T, j0 = (tile / ds.tiles_x) * T;
     const int row = threadIdx.x / TPR, c4 = (threadIdx.x % TPR) * PX;
     const int j = j0 + row;
@@ -307,6 +335,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
         sm.tile_ub = INFINITY;
     }
     __syncthreads();
+    SPM_LAP(0);
     // candidate source: the tile's flooded list plus the global list, or every
     // generator when the lists are unavailable
     const bool lists = allow_lists && ds.use_flood && ds.flood_counts[2] == 0;
@@ -331,10 +360,12 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
             sm.cand_lb[slot] = lb;
         }
         __syncthreads();
+        SPM_LAP(1);
         const int nc = sm.n_cand;
         const bool last = g0 + NT >= ntotal;
         if (nc > kCandCap - NT || (last && nc > 0)) {
             sort_candidates(sm, nc);
+            SPM_LAP(2);
             if (threadIdx.x == 0) SPM_CNT(1, nc);
             bool done = false;
             int tested = 0, chunk = ds.hidden_chunk;
@@ -345,8 +376,10 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 for (int k = 0; k < PX; ++k) act |= (live >> k & 1u) && key_dist(key[k]) > lb_c;
                 if (!__syncthreads_or(act)) {
                     done = true;
+                    SPM_LAP(3);
                     break;
                 }
+                SPM_LAP(3);
                 if (c == tested) {  // hidden-tile test for the next chunk, in parallel
                     const int cc = c + threadIdx.x;
                     if (threadIdx.x < chunk && cc < nc) {
@@ -413,7 +446,11 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                         need |= 1u << k;
                     }
                 }
-                if (!__syncthreads_or(need != 0)) continue;
+                if (!__syncthreads_or(need != 0)) {
+                    SPM_LAP(4);
+                    continue;
+                }
+                SPM_LAP(4);
                 if (threadIdx.x == 0) SPM_CNT(5, 1);
                 // blockers of the hull of (tile, target)
                 float tx, ty;
@@ -434,6 +471,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 __syncthreads();
                 build_blockers(ds, sm, bcx, bcy, tx, ty, brad, kind, gl, seg, box);
                 __syncthreads();
+                SPM_LAP(5);
                 const int nb = min(sm.n_block, kBlockCap);
                 const bool ovf = sm.overflow != 0;
                 if (threadIdx.x == 0) {
@@ -468,6 +506,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                     if (vis) key[k] = nk[k];
                 }
                 __syncthreads();
+                SPM_LAP(6);
             }
             // tile upper bound for candidate pruning: worst best over live pixels
             float worst = 0.f;
@@ -507,6 +546,8 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 }
         }
     }
+    SPM_LAP(7);
+    SPM_TFLUSH();
 }
 
 __global__ void __launch_bounds__(NT, 3) k_pixels(const __grid_constant__ DevScene ds, float *__restrict__ dist,
@@ -582,6 +623,13 @@ extern "C" int spm_debug_counters(unsigned long long *out16) {
 }
 #endif
 
-namespace spm {
-
-}  // namespace spm
+#ifdef SPM_TIME
+// Instrumentation build only: reads and clears the pixel kernel's phase clocks.
+extern "C" int spm_debug_times(unsigned long long *out8) {
+    cudaDeviceSynchronize();
+    if (cudaMemcpyFromSymbol(out8, spm::g_time, sizeof(unsigned long long) * 8) != cudaSuccess) return 1;
+    unsigned long long z[8] = {0};
+    cudaMemcpyToSymbol(spm::g_time, z, sizeof z);
+    return 0;
+}
+#endif
