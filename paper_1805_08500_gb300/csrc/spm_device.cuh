@@ -170,7 +170,8 @@ __device__ __forceinline__ bool walk_bins(const DevScene &ds, float px, float py
 }
 
 // Does the (float, lattice units) segment p->q come within r of box [x0,x1]x[y0,y1]?
-// Slab test on the box grown by r + 1: conservative.
+// Slab test on the box grown by r + 1: conservative (the 1e-4 slack on the
+// segment parameter is far above the error of the fast divisions).
 __device__ __forceinline__ bool seg_near_box(float px, float py, float qx, float qy, float r, int4 box) {
     const float m = r + 1.0f;
     float lo = 0.f, hi = 1.f;
@@ -181,7 +182,8 @@ __device__ __forceinline__ bool seg_near_box(float px, float py, float qx, float
         if (fabsf(d[k]) < 1e-6f) {
             if (p[k] < bl[k] || p[k] > bh[k]) return false;
         } else {
-            float t0 = (bl[k] - p[k]) / d[k], t1 = (bh[k] - p[k]) / d[k];
+            const float id = __fdividef(1.0f, d[k]);
+            float t0 = (bl[k] - p[k]) * id, t1 = (bh[k] - p[k]) * id;
             lo = fmaxf(lo, fminf(t0, t1));
             hi = fminf(hi, fmaxf(t0, t1));
         }

@@ -203,10 +203,12 @@ __device__ void sort_candidates(PixSmem &sm, int n) {
 // thick segment and appended (deduplicated) to smem.
 __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float cy, float tx, float ty,
                                float r, int kind, int2 tl, int4 seg, int4 box) {
-    const float bs = (float)ds.bin_size, x0 = (float)ds.bin_x0, y0 = (float)ds.bin_y0;
+    // Float steps here only choose bins; their errors (~1e-3 lattice units)
+    // stay far inside the margin m, so fast reciprocals are safe.
+    const float bs = (float)ds.bin_size, ibs = 1.0f / bs, x0 = (float)ds.bin_x0, y0 = (float)ds.bin_y0;
     const float m = r + 1.0f;
     auto bin_of = [&](float v, float o, int n) {
-        int b = (int)floorf((v - o) / bs);
+        int b = (int)floorf((v - o) * ibs);
         return b < 0 ? 0 : (b >= n ? n - 1 : b);
     };
     const int c0 = bin_of(fminf(cx, tx) - m, x0, ds.bin_nx), c1 = bin_of(fmaxf(cx, tx) + m, x0, ds.bin_nx);
@@ -216,8 +218,9 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
     // items per column: about the rows one column spans (its x extent is
     // bs + 2m, the segment rises |dy/dx| per unit along it, plus m on both
     // sides); each item strides by K, so any K covers every row
-    const float span = fabsf(dx) < 0.5f ? fabsf(dy) + 2.f * m : fabsf(dy / dx) * (bs + 2.f * m) + 2.f * m;
-    const int K = min((int)(span / bs) + 2, ds.bin_ny);
+    const float idx = fabsf(dx) < 0.5f ? 0.f : __fdividef(1.0f, dx);
+    const float span = fabsf(dx) < 0.5f ? fabsf(dy) + 2.f * m : fabsf(dy * idx) * (bs + 2.f * m) + 2.f * m;
+    const int K = min((int)(span * ibs) + 2, ds.bin_ny);
     const int items = (c1 - c0 + 1) * K;
     for (int j = threadIdx.x; j < items; j += NT) {
         const int col = c0 + j / K, kr = j - (j / K) * K;
@@ -227,7 +230,7 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
             yhi = fmaxf(cy, ty);
         } else {
             float a = x0 + col * bs - m, b = x0 + (col + 1) * bs + m;
-            float t0 = (a - cx) / dx, t1 = (b - cx) / dx;
+            float t0 = (a - cx) * idx, t1 = (b - cx) * idx;
             float tlo = fmaxf(0.f, fminf(t0, t1)), thi = fminf(1.f, fmaxf(t0, t1));
             if (tlo > thi) { tlo = 0.f; thi = 1.f; }
             float ya = cy + tlo * dy, yb = cy + thi * dy;
