@@ -37,20 +37,6 @@ constexpr unsigned long long kUnset = 0x7F800000FFFFFFFFull;  // (+inf, id max)
 // Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
 
 
-struct PixSmem {
-    int cand_id[kCandCap];
-    float cand_lb[kCandCap];
-    unsigned dedup[kDedupBits / 32];
-    int2 blk_v[kBlockCap][kMaxPolyVerts];
-    int blk_oA[kBlockCap][kMaxPolyVerts];
-    int blk_oB[kBlockCap][kMaxPolyVerts];
-    unsigned blk_mask[kBlockCap];
-    int blk_m[kBlockCap];
-    unsigned char hidden[kCandCap];
-    int n_cand, n_block, overflow;
-    float tile_ub;
-};
-
 // Convex hull (counter-clockwise, no repeated or collinear vertices) of the
 // tile's pixel-centre box and the lattice point t, by Andrew's monotone chain
 // over the 5 points. The box may be degenerate (a one-pixel row or column),
@@ -92,6 +78,21 @@ __device__ __forceinline__ Hull hull_box_point(int4 box, int tx, int ty) {
     for (int i = 0; i < 5; ++i) h.v[i] = st[i < h.n ? i : 0];
     return h;
 }
+
+struct PixSmem {
+    int cand_id[kCandCap];
+    float cand_lb[kCandCap];
+    unsigned dedup[kDedupBits / 32];
+    int2 blk_v[kBlockCap][kMaxPolyVerts];
+    int blk_oA[kBlockCap][kMaxPolyVerts];
+    int blk_oB[kBlockCap][kMaxPolyVerts];
+    unsigned blk_mask[kBlockCap];
+    int blk_m[kBlockCap];
+    unsigned char hidden[kCandCap];
+    int n_cand, n_block, overflow;
+    float tile_ub;
+    Hull hull;  // of the tile box and the current point target
+};
 
 // Does the interior of convex polygon V meet the closed convex hull H?
 // Separating-axis test over the edges of both (an edge separates when the
@@ -214,7 +215,6 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
     const int c0 = bin_of(fminf(cx, tx) - m, x0, ds.bin_nx), c1 = bin_of(fmaxf(cx, tx) + m, x0, ds.bin_nx);
     const float dx = tx - cx, dy = ty - cy;
     const bool dedup = ds.n_poly <= kDedupBits;
-    const Hull hull = hull_box_point(box, tl.x, tl.y);  // used for point targets only
     // items per column: about the rows one column spans (its x extent is
     // bs + 2m, the segment rises |dy/dx| per unit along it, plus m on both
     // sides); each item strides by K, so any K covers every row
@@ -250,7 +250,7 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
                     if (atomicOr(&sm.dedup[k >> 5], bit) & bit) continue;
                 }
                 if (!seg_near_box(cx, cy, tx, ty, r, rec.box)) continue;
-                if (kind != kSegI && !poly_meets_hull(ds.poly_v + rec.voff, rec.m, hull)) continue;
+                if (kind != kSegI && !poly_meets_hull(ds.poly_v + rec.voff, rec.m, sm.hull)) continue;
                 const int slot = atomicAdd(&sm.n_block, 1);
                 if (slot >= kBlockCap) {
                     sm.overflow = 1;
@@ -470,6 +470,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 if (threadIdx.x == 0) {
                     sm.n_block = 0;
                     sm.overflow = 0;
+                    if (kind != kSegI) sm.hull = hull_box_point(box, gl.x, gl.y);
                 }
                 __syncthreads();
                 build_blockers(ds, sm, bcx, bcy, tx, ty, brad, kind, gl, seg, box);
