@@ -37,6 +37,10 @@ FALLBACK_HBM_GBS = 6800.0
 # FP32 lanes per SM x SMs x 2 flops per FMA; clock from the measured peaks file
 FP32_LANES, N_SMS = 128, 152
 FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
+# DRAM bytes (read + write) of one k_pixels launch, from the ncu capture
+# summarised in profiles/k_pixels_dram_maze4096.md; only for that workload and
+# that kernel version (re-capture after changing the kernel).
+KPIXELS_TRAFFIC = {"maze4096": 82_898_176}
 
 
 def workload(name: str):
@@ -425,7 +429,7 @@ def main():
         "phases_ms": {"vertex": vert_ms, "cull": cull_ms, "pixel": pix_ms},
         "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": None,
+                     "traffic": KPIXELS_TRAFFIC.get(args.workload),
                      "note": f"algorithmic = {FLOPS_PER_PIXEL} FP32 flops/pixel (winning distance); "
                              f"peak = FP32 lanes x SMs x 2 x max SM clock ({peak_src})"},
         "hbm_write": {"achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
