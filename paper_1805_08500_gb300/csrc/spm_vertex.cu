@@ -297,8 +297,10 @@ __device__ __forceinline__ int solo_bytes(const DevScene &ds) {
     const long long n = ds.n_gen, E = ds.in_start[ds.n_vert];
     // sparse graphs only (deep, few vertices per round); dense ones need the GPU
     if (n >= 32768 || E > ds.edge_cap || E > 8 * n) return 0;
-    const long long b = n * (8 + 4 + 8 + 8 + 1) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
-                        4 * ((n + 31) / 32) + 2 * 3 * n + n * (8 + 4) + 16 * 16;
+    // two state copies (cost 8, parent 2, cone 8, cone type 1), stamp 4,
+    // lattice 4, CSR in/out, two dirty bitmaps and lists, 16-byte alignment
+    const long long b = n * 2 * (8 + 2 + 8 + 1) + n * (4 + 4) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
+                        2 * 4 * ((n + 31) / 32) + 2 * 2 * n + 16 * 16;
     return b <= ds.solo_smem ? (int)b : 0;
 }
 
@@ -392,12 +394,15 @@ __global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene d
 }
 
 // The same fixpoint in one CTA with the graph and the state in shared
-// memory, for graphs that fit (16-bit generator ids, cone directions packed
-// in 16-bit lanes -- lattice directions fit in 16 bits). A round costs two
-// __syncthreads instead of two grid barriers, which is what deep, sparse
-// graphs (mazes: hundreds of rounds, a few vertices each) need. Results are
-// identical to k_sssp: the same pulls over the same sets, committed between
-// the same two barriers.
+// memory, for graphs that fit (16-bit generator ids and lattice coordinates,
+// cone directions in 16-bit lanes -- lattice directions fit in 16 bits). One
+// barrier per round: each vertex keeps two copies of its state (cost,
+// parent, cone) and a stamp (round that wrote it, which copy is current).
+// A dirty vertex pulls its in-neighbours' state as of the previous round --
+// the other copy when a neighbour was already updated in this round -- and,
+// when its own value changes, writes its spare copy and marks its
+// out-neighbours in the next round's dirty bitmap and list. Every pull sees
+// the same state as in k_sssp's rounds, so the results are identical.
 __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int bytes = solo_bytes(ds);
@@ -409,22 +414,24 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         p += (sz + 15) & ~(size_t)15;
         return q;
     };
-    double *cost = (double *)take(8 * n);
-    double *ncost = (double *)take(8 * n);
-    int *par = (int *)take(4 * n);
-    int *npar = (int *)take(4 * n);
-    short4 *cone = (short4 *)take(8 * n);
-    int2 *lat = (int2 *)take(8 * n);
-    signed char *ctype = (signed char *)take(n);
+    // two copies of each state array, copy c of vertex u at index c * n + u
+    double *cost = (double *)take(8 * 2 * n);
+    short4 *cone = (short4 *)take(8 * 2 * n);
+    short *par = (short *)take(2 * 2 * n);
+    signed char *ctype = (signed char *)take(2 * n);
+    int *stamp = (int *)take(4 * n);  // (round that wrote the current copy + 1) << 1 | current copy
+    short2 *lat = (short2 *)take(4 * n);
     int *in_start = (int *)take(4 * (nv + 1));
     unsigned short *in_src = (unsigned short *)take(2 * E);
     int *out_start = (int *)take(4 * (n + 1));
     unsigned short *out_dst = (unsigned short *)take(2 * E);
-    unsigned *dirty = (unsigned *)take(4 * ((n + 31) / 32));
-    unsigned short *dl[2] = {(unsigned short *)take(2 * n), (unsigned short *)take(2 * n)};
-    unsigned short *fr = (unsigned short *)take(2 * n);
-    __shared__ int cnt_d[2], cnt_c[2];  // dirty-list and changed-list counts, by round parity
+    const int dw = (n + 31) / 32;
+    unsigned *dirty = (unsigned *)take(4 * 2 * dw);         // round parity p at p * dw
+    unsigned short *dl = (unsigned short *)take(2 * 2 * n);  // round parity p at p * n
+    __shared__ int cnt[3];  // dirty-list counts, by round modulo 3
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSoloThreads / 32;
+    // work unit: a group of 8 lanes per vertex (in-degrees here are small), 4 per warp
+    const int grp = lane >> 3, gl = lane & 7, ngroups = nwarps * 4, gid = warp * 4 + grp;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
     for (int i = tid; i <= n; i += kSoloThreads) out_start[i] = ds.out_start[i];
@@ -435,60 +442,57 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     for (int g = tid; g < n; g += kSoloThreads) {
         const bool src = g < ds.n_src;
         cost[g] = src ? 0.0 : inf;
-        par[g] = src ? g : -1;
+        par[g] = (short)(src ? g : -1);
         ctype[g] = (signed char)(src ? kConeNone : kConeEmpty);
         cone[g] = make_short4(0, 0, 0, 0);
-        lat[g] = ds.gen_lat[g];
+        stamp[g] = 0;
+        const int2 l = ds.gen_lat[g];
+        lat[g] = make_short2((short)l.x, (short)l.y);
     }
-    for (int w = tid; w < (n + 31) / 32; w += kSoloThreads) dirty[w] = 0u;
-    if (tid < 2) {
-        cnt_d[tid] = 0;
-        cnt_c[tid] = 0;
-    }
+    for (int w = tid; w < 2 * dw; w += kSoloThreads) dirty[w] = 0u;
+    if (tid < 3) cnt[tid] = 0;
     __syncthreads();
-    // work unit: a group of 8 lanes per vertex (in-degrees here are small), 4 per warp
-    const int grp = lane >> 3, gl = lane & 7, ngroups = nwarps * 4, gid = warp * 4 + grp;
-    auto mark = [&](int u, unsigned short *list, int *count) {
+    auto mark = [&](int u, unsigned *bits, unsigned short *list, int *count) {
         for (int e = out_start[u] + gl; e < out_start[u + 1]; e += 8) {
             const int v = out_dst[e];
             const unsigned bit = 1u << (v & 31);
-            if (!(atomicOr(&dirty[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
+            if (!(atomicOr(&bits[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
         }
     };
-    for (int u = gid; u < ds.n_src; u += ngroups) mark(u, dl[0], &cnt_d[0]);
+    for (int u = gid; u < ds.n_src; u += ngroups) mark(u, dirty, dl, &cnt[0]);
     __syncthreads();
-    // Two barriers a round: (pull) every dirty vertex recomputes its best
-    // in-edge into ncost/npar | (commit + mark) changed vertices take the new
-    // value and cone, and dirty their out-neighbours for the next round. The
-    // counters of the other parity are reset during the pull, when nothing
-    // reads or writes them.
     int round = 0;
     for (;; ++round) {
-        const int par_r = round & 1, par_n = par_r ^ 1;
-        const int nd = cnt_d[par_r];
-        if (tid == 0) {
-            cnt_d[par_n] = 0;
-            cnt_c[par_n] = 0;
+        const int cur = round & 1, nxt = cur ^ 1;
+        const int nd = cnt[round % 3];
+        if (nd == 0) break;
+        if (round >= max_rounds) {
+            if (tid == 0) atomicOr(ds.status, kStNotConverged);
+            break;
         }
+        if (tid == 0) cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
+        const int written = (round + 1) << 1;     // stamp of a copy written in this round, without the copy bit
         for (int i0 = warp * 4; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
-            const int v = act ? dl[par_r][i] : ds.n_src;
+            const int v = act ? dl[cur * n + i] : ds.n_src;
             const int vv = v - ds.n_src;
-            if (act && gl == 0) atomicAnd(&dirty[v >> 5], ~(1u << (v & 31)));
-            const int2 vl = lat[v];
+            if (act && gl == 0) atomicAnd(&dirty[cur * dw + (v >> 5)], ~(1u << (v & 31)));
+            const short2 vl = lat[v];
             long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
             const int e1 = act ? in_start[vv + 1] : 0;
             for (int e = in_start[vv] + gl; e < e1; e += 8) {
                 const double len = __ldg(ds.in_len + e);  // issued before the dependent smem reads
                 const int u = in_src[e];
-                const double cu = cost[u];
+                const int su = stamp[u];
+                const int cu_i = ((su & ~1) == written ? (su & 1) ^ 1 : (su & 1)) * n + u;  // u as of last round
+                const double cu = cost[cu_i];
                 if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;  // unreached
-                const int ct = ctype[u];
+                const int ct = ctype[cu_i];
                 if (ct != kConeNone) {
-                    const int2 ul = lat[u];
-                    const short4 c = cone[u];
+                    const short2 ul = lat[u];
+                    const short4 c = cone[cu_i];
                     if (!in_cone(ct, make_int4(c.x, c.y, c.z, c.w), vl.x - ul.x, vl.y - ul.y)) continue;
                 }
                 // costs are non-negative, so their bit patterns order like
@@ -508,53 +512,45 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                     bpar = op;
                 }
             }
-            if (act && gl == 0 && (best != __double_as_longlong(cost[v]) || bpar != par[v])) {
-                ncost[v] = __longlong_as_double(best);
-                npar[v] = bpar;
-                fr[atomicAdd(&cnt_c[par_r], 1)] = (unsigned short)v;
-            }
-        }
-        __syncthreads();
-        const int nc = cnt_c[par_r];
-        if (nc == 0) break;
-        if (round + 1 >= max_rounds) {
-            if (tid == 0) atomicOr(ds.status, kStNotConverged);
-            break;
-        }
-        for (int i = gid; i < nc; i += ngroups) {
-            const int v = fr[i];
-            if (gl == 0) {
-                cost[v] = ncost[v];
-                const int pv = npar[v];
-                par[v] = pv;
-                const int2 vl = lat[v];
-                int dx = 0, dy = 0;
-                int4 c = make_int4(0, 0, 0, 0);
-                int ct = kConeEmpty;  // unreachable again: no arrival direction
-                if (pv >= 0) {
-                    if (ds.gen_kind[pv] == kSegI) {
-                        arrival_dir(ds, pv, vl, dx, dy);
-                    } else {
-                        dx = vl.x - lat[pv].x;
-                        dy = vl.y - lat[pv].y;
+            bool changed = false;
+            if (act && gl == 0) {
+                const int sv = stamp[v], ci = sv & 1;  // only this group writes v
+                if (best != __double_as_longlong(cost[ci * n + v]) || bpar != par[ci * n + v]) {
+                    const int ni = ci ^ 1;
+                    cost[ni * n + v] = __longlong_as_double(best);
+                    par[ni * n + v] = (short)bpar;
+                    int4 c = make_int4(0, 0, 0, 0);
+                    int ctv = kConeEmpty;  // unreachable again: no arrival direction
+                    if (bpar >= 0) {
+                        int dx, dy;
+                        if (ds.gen_kind[bpar] == kSegI) {
+                            arrival_dir(ds, bpar, make_int2(vl.x, vl.y), dx, dy);
+                        } else {
+                            dx = vl.x - lat[bpar].x;
+                            dy = vl.y - lat[bpar].y;
+                        }
+                        ctv = make_cone(ds.gen_wedge[v], dx, dy, c);
                     }
-                    ct = make_cone(ds.gen_wedge[v], dx, dy, c);
+                    ctype[ni * n + v] = (signed char)ctv;
+                    cone[ni * n + v] = make_short4((short)c.x, (short)c.y, (short)c.z, (short)c.w);
+                    stamp[v] = written | ni;
+                    changed = true;
                 }
-                ctype[v] = (signed char)ct;
-                cone[v] = make_short4((short)c.x, (short)c.y, (short)c.z, (short)c.w);
             }
-            mark(v, dl[par_n], &cnt_d[par_n]);
+            changed = __shfl_sync(0xffffffffu, changed, grp * 8) && act;
+            if (changed) mark(v, dirty + nxt * dw, dl + nxt * n, &cnt[(round + 1) % 3]);
         }
         __syncthreads();
     }
     for (int g = tid; g < n; g += kSoloThreads) {
-        ds.cost[0][g] = cost[g];
-        ds.par[0][g] = par[g];
-        const short4 c = cone[g];
+        const int ci = (stamp[g] & 1) * n + g;
+        ds.cost[0][g] = cost[ci];
+        ds.par[0][g] = par[ci];
+        const short4 c = cone[ci];
         ds.gen_cone[g] = make_int4(c.x, c.y, c.z, c.w);
-        ds.gen_ctype[g] = ctype[g];
+        ds.gen_ctype[g] = ctype[ci];
     }
-    if (tid == 0) ds.stats[0] = round + 1;
+    if (tid == 0) ds.stats[0] = round;
 }
 
 // Final generator table for the pixel phase: FP32 costs and shadow cones.
