@@ -62,6 +62,42 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def rank_env():
+    """(world size, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (x itself on one rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, slowest_seconds: float) -> float:
+    """Units all ranks processed (each rank the same amount) over the slowest rank's time."""
+    return world * units_per_rank / slowest_seconds
+
+
+def shard_lpt(weights, world: int, rank: int):
+    """Longest-processing-time-first assignment of items to ranks (heaviest
+    item to the least loaded rank, ties to the lower index); the indices of
+    this rank's items, in input order."""
+    order = sorted(range(len(weights)), key=lambda i: (-weights[i], i))
+    load = [0.0] * world
+    owner = [0] * len(weights)
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += weights[i]
+    return [i for i in range(len(weights)) if owner[i] == rank]
+
+
 def load_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -177,10 +213,21 @@ def run_reference(args, cfg_desc, scene):
 
 def run_batched(args, cfg_desc, scenes):
     """Batched form: all scenes in one batch (batched vertex phase, one
-    persistent pixel kernel, replayed from a CUDA graph); value = scenes/s."""
+    persistent pixel kernel, replayed from a CUDA graph); value = scenes/s.
+    Under torchrun the job is 256 scenes per rank (seeded set of
+    256 x world scenes), dealt to ranks longest-first by pixel count; ranks
+    share no data."""
     import torch
+    import torch.distributed as dist
     import paper_1805_08500_gb300 as spm
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    world, rank, local = rank_env()
+    all_scenes = scenes
+    if world > 1:
+        dist.init_process_group("nccl")
+        all_scenes = sg.batched(0, n_scenes=len(scenes) * world)
+        mine = shard_lpt([sc.grid[0] * sc.grid[1] for sc in all_scenes], world, rank)
+        scenes = [all_scenes[i] for i in mine]
+    torch.cuda.set_device(local)
     dev = torch.device("cuda", torch.cuda.current_device())
     objs = [spm.Scene(sc) for sc in scenes]
     for o in objs:  # full scans; the default tile follows each scene's pixel size
@@ -193,28 +240,39 @@ def run_batched(args, cfg_desc, scenes):
         batch.compute(stream)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
             batch.compute(stream)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     for o in objs:
         o.sync()
-    total_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+    total_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev])), world, dev)
     ms = total_ms / args.steps
-    line = {"metric": "SPM batched scenes/s", "value": len(scenes) / (ms * 1e-3), "unit": "scenes/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+    npx_all = sum(sc.grid[0] * sc.grid[1] for sc in all_scenes)
+    line = {"metric": "SPM batched scenes/s", "value": len(all_scenes) / (ms * 1e-3), "unit": "scenes/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
-            "config": {"workload": "batched256", "scene": cfg_desc, "scenes": len(scenes),
-                       "pixels": npx, "l2": "flushed between timed steps (256 MiB write)",
+            "config": {"workload": "batched256", "scene": cfg_desc, "scenes": len(all_scenes),
+                       "pixels": npx_all, "l2": "flushed between timed steps (256 MiB write)",
                        "launch": "one CUDA graph per step"},
-            "mpixel_per_s": npx / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
+            "mpixel_per_s": npx_all / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
             "gpu_launches": 8 * args.steps}  # 7 vertex-phase kernels + 1 persistent pixel kernel
-    print(json.dumps(line), flush=True)
+    if world > 1:
+        line["config"]["parallelism"] = f"scenes sharded longest-first over {world} ranks"
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     batch.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_differentiable(args, cfg_desc, scene):
@@ -333,9 +391,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -379,13 +435,9 @@ def main():
         dist.barrier()
     s.sync(stream)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(np.sum(step_ms))
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * npx * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_rate(npx * args.steps, world, total_ms * 1e-3) / 1e6
 
     # end to end through the C ABI with host buffers: source upload + compute +
     # copy of both output planes into pinned host memory
@@ -401,10 +453,7 @@ def main():
         spm.spm_scene_update_sources(s.handle, pts, segs)
         spm.spm_compute_host(s.handle, stream, hd, hp)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * npx / float(e2e_t.item()) / 1e6
+    e2e_value = whole_job_rate(npx, world, max_over_ranks(e2e_s, world, dev)) / 1e6
 
     peaks, peak_src = load_peaks()
     vert_ms = float(np.mean([p[0] for p in phases]))
