@@ -105,6 +105,18 @@ spm_status spm_scene_update_sources(spm_scene *scene, const float *point_xy,
 spm_status spm_compute(spm_scene *scene, void *stream, float *dist_dev,
                        int32_t *parent_dev);
 
+/* Row slab of the same map, for splitting one scene over several GPUs (no
+ * counterpart in the paper; each GPU computes its own slab, and no data is
+ * exchanged). Runs the whole vertex phase and culling, then the pixel pass
+ * for grid rows [row0, row1) only: row0 and row1 must be multiples of the
+ * scene's tile size (spm_scene_info()[7]) or row1 == grid_h, else
+ * SPM_ERR_INVALID_ARG. dist_dev / parent_dev are the full-grid buffers of
+ * spm_compute; only the slab's rows are written, with the values
+ * spm_compute writes there. Queries (spm_query_parent, spm_extract_path)
+ * need a whole-grid spm_compute. Asynchronous; allocates nothing. */
+spm_status spm_compute_rows(spm_scene *scene, void *stream, int32_t row0, int32_t row1,
+                            float *dist_dev, int32_t *parent_dev);
+
 /* spm_compute on HOST buffers: copies the outputs back before returning
  * (synchronous on `stream`). For callers that keep the field on the host. */
 spm_status spm_compute_host(spm_scene *scene, void *stream, float *dist_host,

@@ -80,6 +80,7 @@ def load_library():
         "spm_scene_destroy": ([P], None),
         "spm_scene_update_sources": ([P, P, P], I32),
         "spm_compute": ([P, P, P, P], I32),
+        "spm_compute_rows": ([P, P, I32, I32, P, P], I32),
         "spm_compute_host": ([P, P, P, P], I32),
         "spm_compute_batched": ([P, I32, P, P, P], I32),
         "spm_batch_create": ([P, I32, P, P, P], I32),
@@ -177,6 +178,22 @@ def spm_scene_update_sources(handle, points, segs):
 def spm_compute(handle, stream, dist, parent):
     _check(load_library().spm_compute(handle, _stream_handle(stream), _ptr(dist), _ptr(parent)),
            "spm_compute", handle)
+
+
+def spm_compute_rows(handle, stream, row0, row1, dist, parent):
+    _check(load_library().spm_compute_rows(handle, _stream_handle(stream), int(row0), int(row1), _ptr(dist),
+                                           _ptr(parent)), "spm_compute_rows", handle)
+
+
+def row_slabs(grid_h: int, tile: int, world: int):
+    """Tile-aligned row slabs [row0, row1) of a grid, one per rank: whole
+    tile rows dealt as evenly as possible, the last slab ending at grid_h."""
+    tiles = (grid_h + tile - 1) // tile
+    out = []
+    for r in range(world):
+        t0, t1 = tiles * r // world, tiles * (r + 1) // world
+        out.append((min(t0 * tile, grid_h), min(t1 * tile, grid_h)))
+    return out
 
 
 def spm_compute_host(handle, stream, dist_host, parent_host):
@@ -370,6 +387,11 @@ class Scene:
         Nx, Ny = self.grid
         return (torch.empty((Ny, Nx), dtype=torch.float32, device=self.device),
                 torch.empty((Ny, Nx), dtype=torch.int32, device=self.device))
+
+    def compute_rows(self, row0, row1, dist, parent, stream=None):
+        """Rows [row0, row1) of the map into the full-grid buffers (tile-aligned)."""
+        spm_compute_rows(self.handle, stream, row0, row1, dist, parent)
+        return dist, parent
 
     def compute(self, dist=None, parent=None, stream=None):
         if dist is None or parent is None:

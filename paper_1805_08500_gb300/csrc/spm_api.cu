@@ -299,10 +299,7 @@ spm_status spm_scene_update_sources(spm_scene *s, const float *pts, const float 
     return upload_sources(s);
 }
 
-spm_status spm_compute(spm_scene *s, void *stream, float *dist, int32_t *parent) {
-    if (!s || !dist || !parent) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
-    spm_status st = check_device(s);
-    if (st != SPM_OK) return st;
+spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent, int tile_row0, int tile_row1) {
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(cs, &cap);
@@ -317,15 +314,33 @@ spm_status spm_compute(spm_scene *s, void *stream, float *dist, int32_t *parent)
         cudaMemcpyAsync(s->ds.flood_counts, off, sizeof off, cudaMemcpyHostToDevice, cs);
     }
     if (timed) cudaEventRecord(s->ev[3], cs);
-    spm::launch_pixel_phase(s->ds, cs, dist, parent);
+    spm::launch_pixel_phase(s->ds, cs, dist, parent, tile_row0, tile_row1);
     if (timed) cudaEventRecord(s->ev[2], cs);
     s->ev_valid = timed;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(s, SPM_ERR_CUDA, cudaGetErrorString(e));
-    s->last_dist = dist;
-    s->last_parent = parent;
+    const bool whole = tile_row0 == 0 && tile_row1 == s->ds.tiles_y;
+    s->last_dist = whole ? dist : nullptr;  // queries need the whole field
+    s->last_parent = whole ? parent : nullptr;
     s->last_stream = cs;
     return SPM_OK;
+}
+
+spm_status spm_compute(spm_scene *s, void *stream, float *dist, int32_t *parent) {
+    if (!s || !dist || !parent) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    return compute_impl(s, stream, dist, parent, 0, s->ds.tiles_y);
+}
+
+spm_status spm_compute_rows(spm_scene *s, void *stream, int32_t row0, int32_t row1, float *dist, int32_t *parent) {
+    if (!s || !dist || !parent) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    const int T = s->ds.tile, Ny = s->ds.Ny;
+    if (row0 < 0 || row1 > Ny || row0 > row1 || row0 % T != 0 || (row1 % T != 0 && row1 != Ny))
+        return set_err(s, SPM_ERR_INVALID_ARG, "rows must be tile-aligned within the grid");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    return compute_impl(s, stream, dist, parent, row0 / T, (row1 + T - 1) / T);
 }
 
 spm_status spm_scene_sync(spm_scene *s, void *stream) {

@@ -162,7 +162,9 @@ struct BatchDev {
 
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
-void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent);
+// pixel kernel over the tiles of tile rows [tile_row0, tile_row1)
+void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
+                        int tile_row1);
 void launch_flood(const DevScene &ds, cudaStream_t st);
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);

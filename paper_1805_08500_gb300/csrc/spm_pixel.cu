@@ -555,10 +555,10 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
 }
 
 __global__ void __launch_bounds__(NT, 3) k_pixels(const __grid_constant__ DevScene ds, float *__restrict__ dist,
-                                               int32_t *__restrict__ parent) {
+                                               int32_t *__restrict__ parent, int tile0) {
     __shared__ PixSmem sm;
-    if (ds.tile == kTile) pixel_tile<4>(ds, blockIdx.x, dist, parent, sm, true);
-    else pixel_tile<1>(ds, blockIdx.x, dist, parent, sm, true);
+    if (ds.tile == kTile) pixel_tile<4>(ds, tile0 + blockIdx.x, dist, parent, sm, true);
+    else pixel_tile<1>(ds, tile0 + blockIdx.x, dist, parent, sm, true);
 }
 
 // Persistent form over a batch of scenes: each CTA takes the next
@@ -597,9 +597,10 @@ __global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant_
 
 }  // namespace
 
-void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent) {
-    const int tiles = ds.tiles_x * ds.tiles_y;
-    k_pixels<<<tiles, NT, 0, st>>>(ds, dist, parent);
+void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
+                        int tile_row1) {
+    const int tiles = ds.tiles_x * (tile_row1 - tile_row0);
+    if (tiles > 0) k_pixels<<<tiles, NT, 0, st>>>(ds, dist, parent, tile_row0 * ds.tiles_x);
 }
 
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st) {

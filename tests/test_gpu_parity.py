@@ -311,3 +311,25 @@ def test_agent_gradient_matches_oracle(spm, oracle_mod):
     assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
     np.testing.assert_allclose(pts.grad.cpu().numpy(), gp_ref, atol=1e-4)
     np.testing.assert_allclose(segs.grad.cpu().numpy(), gs_ref, atol=1e-4)
+
+
+@pytest.mark.gpu
+def test_row_slabs_concatenate_to_the_full_map(spm):
+    """Two and three tile-aligned row slabs, computed separately into their
+    own buffers, reproduce the whole-grid map bit for bit (the per-GPU split
+    of one scene)."""
+    scene = sg.plain_polys(2, W=2048, N=512, n_polys=60)
+    s = spm.Scene(scene)
+    d_full, p_full = s.compute()
+    s.sync()
+    tile = s.info()["tile"]
+    for world in (2, 3):
+        d = torch.full_like(d_full, float("nan"))
+        p = torch.full_like(p_full, -7)
+        for r0, r1 in spm.row_slabs(scene.grid[1], tile, world):
+            s.compute_rows(r0, r1, d, p)
+        s.sync()
+        assert torch.equal(p, p_full)
+        assert torch.equal(d.view(torch.int32), d_full.view(torch.int32))
+    with pytest.raises(spm.SpmError):
+        s.compute_rows(1, tile, d_full, p_full)  # not tile-aligned

@@ -77,3 +77,15 @@ def test_single_rank_is_identity():
     assert bench.max_over_ranks(3.5, 1, None) == 3.5
     assert bench.shard_lpt([3.0, 1.0, 2.0], 1, 0) == [0, 1, 2]
     assert bench.whole_job_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_row_slabs_partition_the_grid():
+    import paper_1805_08500_gb300 as spm
+    for grid_h, tile, world in [(4096, 32, 2), (4096, 32, 3), (1000, 16, 4), (17, 16, 2), (8, 16, 3)]:
+        slabs = spm.row_slabs(grid_h, tile, world)
+        assert len(slabs) == world
+        assert slabs[0][0] == 0 and slabs[-1][1] == grid_h
+        for (a0, a1), (b0, b1) in zip(slabs, slabs[1:]):
+            assert a1 == b0 and a0 <= a1
+        for r0, r1 in slabs:
+            assert r0 % tile == 0 and (r1 % tile == 0 or r1 == grid_h)
