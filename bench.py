@@ -275,6 +275,63 @@ def run_batched(args, cfg_desc, scenes):
         dist.destroy_process_group()
 
 
+# Table 1 of the paper (GTX 970, OpenGL, 1000^2, single source, mean of 100
+# random sources): Profiling0..6, compute seconds. Context only.
+PAPER_PROFILING_S = {4: 0.0014, 16: 0.0054, 36: 0.0456, 64: 0.1251, 100: 0.2701, 196: 0.8564, 400: 2.7371}
+
+
+def run_profiling(args):
+    """The paper's Profiling maps (k x k uniform squares, P = k^2, 1000^2
+    grid, one point source): per map, the mean device time of spm_compute
+    over 100 seeded free source positions (each moved in with
+    spm_scene_update_sources before its timed compute). value = the
+    Profiling3 map (P = 64, V = 256, the configuration Table 2 also quotes)."""
+    import torch
+    import paper_1805_08500_gb300 as spm
+    world, rank, local = rank_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n_src = 100
+    rows = []
+    with ClockSampler(local) as clk:
+        for k in (2, 4, 6, 8, 10, 14, 20):
+            scene = sg.profiling_map(k)
+            s = spm.Scene(scene)
+            tuning = s.autotune(cache_key=f"profiling{k * k}")
+            d, p = s.empty_outputs()
+            srcs = sg.profiling_sources(k, n_src)
+            empty = np.zeros((0, 4), np.float32)
+            for i in range(max(args.warmup, 3)):
+                spm.spm_scene_update_sources(s.handle, srcs[i:i + 1].astype(np.float32), empty)
+                s.compute(d, p, stream)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_src)]
+            for i in range(n_src):
+                spm.spm_scene_update_sources(s.handle, srcs[i:i + 1].astype(np.float32), empty)
+                ev[i][0].record(stream)
+                s.compute(d, p, stream)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            s.sync(stream)
+            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            P = k * k
+            rows.append({"P": P, "V": 4 * P, "ms": ms, "mpixel_per_s": 1.0e6 / (ms * 1e-3) / 1e6,
+                         "paper_gtx970_ms": 1e3 * PAPER_PROFILING_S[P], "tuning": tuning})
+    ref = next(r for r in rows if r["P"] == 64)
+    line = {"metric": "SPM ms per map, Profiling3 (64 squares), 1000^2, one source", "value": ref["ms"],
+            "unit": "ms", "n_gpus": 1, "steps": n_src, "warmup": max(args.warmup, 3), "ms_per_step": ref["ms"],
+            "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": ref["ms"] / ref["paper_gtx970_ms"],
+            "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
+            "config": {"workload": "profiling1000", "scene": "k x k uniform squares (half the cell pitch), 1000^2 world "
+                       "and grid, one seeded free point source per compute, mean of 100 sources",
+                       "l2": "inputs resident; no flush (the paper times back-to-back frames)"},
+            "maps": rows, "clocks": clk.summary(),
+            "note": "vs_baseline divides by the paper's GTX 970 OpenGL time (Table 1): context, not a target"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_differentiable(args, cfg_desc, scene):
     """Differentiable form: one step = spm_compute + agent loss (forward) +
     its adjoint w.r.t. the sources (backward), 100k agents; value = forward +
@@ -366,7 +423,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maze4096",
                     choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048", "diff2048_grad",
-                             "batched256"])
+                             "batched256", "profiling1000"])
     ap.add_argument("--cpu-pixels", type=int, default=3_000_000,
                     help="oracle pixel sample for the cpu_baseline leg")
     ap.add_argument("--ref-pixels", type=int, default=40_000,
@@ -377,6 +434,9 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
+    if args.workload == "profiling1000":
+        run_profiling(args)
+        return
     scene, cfg_desc = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg_desc, scene)

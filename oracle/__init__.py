@@ -66,6 +66,8 @@ def _load():
                                    ctypes.c_int, ctypes.c_int]
         lib.orc_visible.restype = ctypes.c_int
         lib.orc_visible.argtypes = [P] + [ctypes.c_longlong] * 4
+        lib.orc_keys.argtypes = [P, ctypes.c_int, i32p, i32p, f64p]
+        lib.orc_keys.restype = None
         lib.orc_root_link.restype = ctypes.c_int
         lib.orc_root_link.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       f64p, ctypes.POINTER(ctypes.c_double)]
@@ -164,6 +166,16 @@ class Oracle:
         d, p, d2, p2 = self.pixels(ij)
         return (d.reshape(Ny, Nx), p.reshape(Ny, Nx), d2.reshape(Ny, Nx),
                 p2.reshape(Ny, Nx))
+
+    def keys(self, ij, gens):
+        """Key of generator gens[n] at pixel ij[n] (inf when that generator is
+        not valid there): to check a tied alternative parent."""
+        ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int32).reshape(-1, 2))
+        gens = np.ascontiguousarray(np.asarray(gens, dtype=np.int32).reshape(-1))
+        out = np.empty(len(gens), np.float64)
+        if len(gens):
+            _lib.orc_keys(self._h, len(gens), ij.reshape(-1), gens, out)
+        return out
 
     def visible(self, a, b) -> bool:
         """Exact visibility between two lattice points."""

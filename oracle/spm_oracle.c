@@ -931,6 +931,45 @@ void orc_pixels(void *h, int n, const int *ij, double *dist, int *par, double *s
 }
 
 /* Exact visibility between two lattice points (1 = visible). */
+/* Keys of given generators at given pixels: key[n] = cost(g) + |p - g| (the
+ * perpendicular distance for a segment interior) when generator g = gen[n] is
+ * valid at pixel (i, j) = ij[2n..2n+1] -- the pixel is free, g is reached,
+ * p lies in g's shadow cone (obstacle vertices) or its foot strictly inside
+ * the segment (segment interiors), and p sees g (or the foot) -- else +inf.
+ * The same steps as the per-pixel minimum, for one generator at a time:
+ * used to check that a different but tied choice of parent is valid. */
+void orc_keys(void *h, int n, const int *ij, const int *gen, double *key) {
+    const orc_t *o = h;
+    int *stamp = calloc(o->np + 1, sizeof(int));
+    int tick = 0;
+    for (int q = 0; q < n; q++) {
+        const int i = ij[2 * q], j = ij[2 * q + 1], g = gen[q];
+        key[q] = INFINITY;
+        if (g < 0 || g >= o->ng || !(o->cost[g] < INFINITY)) continue;
+        ll px = pix_lat(o->S, o->Wx, o->Nx, i), py = pix_lat(o->S, o->Wy, o->Ny, j);
+        if (!pixel_free(o, px, py)) continue;
+        double fx = ((double)i + 0.5) * (double)o->Wx / (double)o->Nx;
+        double fy = ((double)j + 0.5) * (double)o->Wy / (double)o->Ny;
+        double k;
+        int ok;
+        if (o->kind[g] == K_SEGI) {
+            ll num, den, side;
+            if (!seg_foot_interior(o, o->sidx[g], px, py, &num, &den, &side)) continue;
+            const double *F = o->sf + 4 * o->sidx[g];
+            double ux = F[2] - F[0], uy = F[3] - F[1];
+            k = fabs(ux * (fy - F[1]) - uy * (fx - F[0])) / sqrt(ux * ux + uy * uy);
+            ok = vis_foot(o, o->sidx[g], px, py, side, den, stamp, &tick);
+        } else {
+            if (o->kind[g] == K_VERT && !in_cone(o, g, px - o->lx[g], py - o->ly[g])) continue;
+            double dx = fx - o->tx[g], dy = fy - o->ty[g];
+            k = o->cost[g] + sqrt(dx * dx + dy * dy);
+            ok = vis_points(o, px, py, o->lx[g], o->ly[g], stamp, &tick);
+        }
+        if (ok) key[q] = k;
+    }
+    free(stamp);
+}
+
 int orc_visible(void *h, long long ax, long long ay, long long bx, long long by) {
     orc_t *o = h;
     int *stamp = calloc(o->np + 1, sizeof(int));

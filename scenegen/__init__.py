@@ -17,6 +17,7 @@ from .scenes import (  # noqa: F401
     empty_scene,
     single_square,
     profiling_map,
+    profiling_sources,
     load_scene,
     save_scene,
 )

@@ -480,3 +480,20 @@ def profiling_map(k: int = 8, W: int = 1000, N: int = 1000, seed: int = 0) -> Sc
             break
     return Scene((W, W), (N, N), polys, np.array([(float(x), float(y))]),
                  np.zeros((0, 4)), name=f"profiling_{k * k}", seed=seed)
+
+
+def profiling_sources(k: int = 8, n: int = 100, W: int = 1000, seed: int = 0) -> np.ndarray:
+    """n seeded integer source positions for profiling_map(k, W): uniform in
+    the world, kept when outside every (closed) square, so each is free."""
+    rng = SplitMix64(seed * 0x1000193 + 131)
+    pitch = W // k
+    side = pitch // 2
+    out = []
+    while len(out) < n:
+        x, y = rng.randint(1, W - 1), rng.randint(1, W - 1)
+        a, b = x // pitch, y // pitch
+        x0, y0 = a * pitch + (pitch - side) // 2, b * pitch + (pitch - side) // 2
+        if a < k and b < k and x0 <= x <= x0 + side and y0 <= y <= y0 + side:
+            continue
+        out.append((float(x), float(y)))
+    return np.array(out)

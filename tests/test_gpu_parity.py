@@ -47,7 +47,7 @@ def gpu_field(spm, scene):
     return s, d.cpu().numpy(), p.cpu().numpy()
 
 
-def check_parity(scene, gd, gp, rd, rp, rd2, where="", rp2=None):
+def check_parity(scene, gd, gp, rd, rp, rd2, where="", rp2=None, oracle=None):
     W = math.hypot(*scene.world)
     h = min(scene.world[0] / scene.grid[0], scene.world[1] / scene.grid[1])
     fin = np.isfinite(rd)
@@ -63,6 +63,14 @@ def check_parity(scene, gd, gp, rd, rp, rd2, where="", rp2=None):
             exact = np.where(np.isfinite(rd2), rd2 - rd, np.inf) <= 1e-9 * np.maximum(rd, 1.0)
         alt = mism & exact & (gp == rp2)
         mism = mism & ~alt
+    if oracle is not None and mism.any():
+        # a different parent is still correct when the oracle finds it valid
+        # at that pixel (free, reached, in its cone, visible) with a key the
+        # FP32 evaluation cannot tell from the minimum (several tied generators)
+        jj, ii = np.nonzero(mism)
+        k = oracle.keys(np.stack([ii, jj], 1), gp[jj, ii])
+        ok = k <= rd[jj, ii] + 1e-6 * np.maximum(rd[jj, ii], h)
+        mism[jj[ok], ii[ok]] = False
     hard = mism & ~tie
     assert not hard.any(), (f"{where}: {hard.sum()} parent mismatches outside near ties, "
                             f"first at {np.argwhere(hard)[:3].tolist()}")
@@ -75,7 +83,7 @@ def full_parity(spm, oracle_mod, scene, where):
     s, gd, gp = gpu_field(spm, scene)
     o = oracle_mod.Oracle(scene)
     rd, rp, rd2, rp2 = o.field()
-    check_parity(scene, gd, gp, rd, rp, rd2, where, rp2)
+    check_parity(scene, gd, gp, rd, rp, rd2, where, rp2, oracle=o)
     return s, o, gd, gp
 
 
@@ -110,6 +118,13 @@ def test_plain_rects_256(spm, oracle_mod, seed):
 
 def test_plain_polys_1024_full(spm, oracle_mod):
     full_parity(spm, oracle_mod, sg.plain_polys(0), "polys1024")
+
+
+@pytest.mark.parametrize("k", [2, 8, 20])
+def test_profiling_map_full(spm, oracle_mod, k):
+    """The paper's Profiling maps (k x k uniform squares, 1000^2, one source,
+    Table 1), whole grid, against the oracle."""
+    full_parity(spm, oracle_mod, sg.profiling_map(k), f"profiling{k * k}")
 
 
 def test_maze_small_full(spm, oracle_mod):

@@ -396,3 +396,24 @@ def test_gradient_matches_central_differences(oracle_mod):
             fd[idx] = (lp - lm) / (2 * h)
     np.testing.assert_allclose(gp, fd_p, atol=1e-3)
     np.testing.assert_allclose(gs, fd_s, atol=1e-3)
+
+
+def test_keys_brute_force_minimum_is_the_field(oracle_mod):
+    """The key of every generator at every pixel, minimised by brute force,
+    gives the field and a parent with that key (small profiling map and a
+    small polygon scene with a segment)."""
+    for scene in (sg.profiling_map(3, N=50), sg.plain_polys(4, W=512, N=64, n_polys=8)):
+        o = oracle_mod.Oracle(scene)
+        d, p, _, _ = o.field()
+        Nx, Ny = scene.grid
+        ng = len(o.kind)
+        jj, ii = np.meshgrid(np.arange(Ny), np.arange(Nx), indexing="ij")
+        ij = np.repeat(np.stack([ii.reshape(-1), jj.reshape(-1)], 1), ng, axis=0)
+        gens = np.tile(np.arange(ng), Nx * Ny)
+        k = o.keys(ij, gens).reshape(Ny, Nx, ng)
+        kmin = k.min(axis=2)
+        fin = np.isfinite(d)
+        assert np.array_equal(np.isfinite(kmin), fin)
+        assert np.allclose(kmin[fin], d[fin], rtol=0, atol=1e-9)
+        kp = np.take_along_axis(k, np.where(p >= 0, p, 0)[..., None], axis=2)[..., 0]
+        assert np.allclose(kp[fin], d[fin], rtol=0, atol=1e-9)
