@@ -237,7 +237,10 @@ spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *cull_ms
  * flood_mode: 0 = automatic (flood the per-tile candidate lists when the
  *   visibility graph among generators is sparse -- below 1% of all pairs,
  *   as in mazes -- otherwise let every tile scan every generator; decided on
- *   the device each compute), 1 = always flood, 2 = never flood.
+ *   the device each compute), 1 = always flood, 2 = never flood, 3 = flood
+ *   from geometry alone (every generator's visible tiles, no shadow cone) on
+ *   the scene's own side stream, concurrently with the vertex phase; the
+ *   pixel pass then applies costs and cones.
  * hidden_chunk: first chunk of lb-ordered candidates whose tiles are tested
  *   for being hidden (32..256; later chunks double).
  * tile: pixel tile side, 16 or 32 (default 16 when a pixel spans 8 world
@@ -254,7 +257,7 @@ spm_status spm_scene_set_tuning(spm_scene *scene, const spm_tuning *tuning);
 
 /* Autotuner: times spm_compute on this scene (device events on `stream`,
  * warm-up then the median of 3 runs) for every flood_mode x hidden_chunk x
- * tile combination in {1, 2} x {32, 256} x {16, 32}, keeps the fastest and
+ * tile combination in {1, 2, 3} x {32, 256} x {16, 32}, keeps the fastest and
  * writes it to *chosen (may be NULL). Synchronous. Allocates the scene's
  * output staging planes on first use; call it at set-up, not inside a
  * captured stream. */

@@ -41,6 +41,9 @@ struct spm_scene {
     // phase timing events (vertex start, pixel start, end)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_valid = false;
+    // side stream of the geometric flood (flood mode 3), with fork/join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -81,6 +84,15 @@ void free_all(spm_scene *s) {
             cudaEventDestroy(e);
             e = nullptr;
         }
+    for (cudaEvent_t *e : {&s->fork, &s->join})
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    if (s->side) {
+        cudaStreamDestroy(s->side);
+        s->side = nullptr;
+    }
 }
 
 spm_status check_device(spm_scene *s) {
@@ -263,6 +275,10 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     cudaMemset(ds.stats, 0, sizeof(int32_t) * 4);
     for (cudaEvent_t &e : s->ev)
         if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming) != cudaSuccess)
+        ok = false;
     if (!ok) {
         free_all(s);
         delete s;
@@ -304,10 +320,19 @@ spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(cs, &cap);
     const bool timed = cap == cudaStreamCaptureStatusNone;
+    const bool side = s->ds.use_flood && s->ds.flood_mode == 3;  // geometric flood beside the vertex phase
     if (timed) cudaEventRecord(s->ev[0], cs);
+    if (side) {
+        cudaEventRecord(s->fork, cs);
+        cudaStreamWaitEvent(s->side, s->fork, 0);
+        spm::launch_flood(s->ds, s->side);
+        cudaEventRecord(s->join, s->side);
+    }
     spm::launch_vertex_phase(s->ds, cs);
     if (timed) cudaEventRecord(s->ev[1], cs);
-    if (s->ds.use_flood) {
+    if (side) {
+        cudaStreamWaitEvent(cs, s->join, 0);
+    } else if (s->ds.use_flood) {
         spm::launch_flood(s->ds, cs);
     } else {
         static const int32_t off[4] = {0, 0, 1, 0};
@@ -649,7 +674,7 @@ spm_status spm_scene_get_tuning(const spm_scene *s, spm_tuning *out) {
 
 spm_status spm_scene_set_tuning(spm_scene *s, const spm_tuning *t) {
     if (!s || !t) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
-    if (t->flood_mode < 0 || t->flood_mode > 2 || t->hidden_chunk < 32 || t->hidden_chunk > 256 ||
+    if (t->flood_mode < 0 || t->flood_mode > 3 || t->hidden_chunk < 32 || t->hidden_chunk > 256 ||
         (t->tile != 0 && t->tile != spm::kTile && t->tile != spm::kTileSmall))
         return set_err(s, SPM_ERR_INVALID_ARG, "tuning out of range");
     s->ds.flood_mode = t->flood_mode;
@@ -672,15 +697,15 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
         return set_err(s, SPM_ERR_CUDA, "event creation failed");
-    const int modes[2] = {1, 2}, chunks[2] = {32, 256}, tiles[2] = {spm::kTileSmall, spm::kTile};
+    const int modes[3] = {1, 2, 3}, chunks[2] = {32, 256}, tiles[2] = {spm::kTileSmall, spm::kTile};
     float best = 3.4e38f;
     spm_tuning pick{};
     pick.flood_mode = s->ds.flood_mode;
     pick.hidden_chunk = s->ds.hidden_chunk;
     pick.tile = s->ds.tile;
     for (int ti = 0; ti < 2; ++ti)
-    for (int mi = 0; mi < 2; ++mi) {
-        if (modes[mi] == 1 && !s->ds.use_flood) continue;
+    for (int mi = 0; mi < 3; ++mi) {
+        if (modes[mi] != 2 && !s->ds.use_flood) continue;
         for (int ci = 0; ci < 2; ++ci) {
             s->ds.flood_mode = modes[mi];
             s->ds.hidden_chunk = chunks[ci];

@@ -176,17 +176,20 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
     const int pwords = ds.n_poly <= kFloodPolyBits ? (ds.n_poly + 31) / 32 : 0;
     unsigned *visited = fdyn, *seen = fdyn + words;  // tiles reached; polygons inserted
     const int tpx = ds.tile * (ds.S * ds.Wx / ds.Nx), tpy = ds.tile * (ds.S * ds.Wy / ds.Ny);
+    // mode 3 floods from geometry alone (every generator, no cone): it runs
+    // before the vertex costs exist, and the pixel pass applies cost and cone
+    const bool geometric = ds.flood_mode == 3;
     for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) {
-        if (!(ds.gen_costf[g] < INFINITY)) continue;
+        if (!geometric && !(ds.gen_costf[g] < INFINITY)) continue;
         const int kind = ds.gen_kind[g];
-        const int ct = kind == kVert ? ds.gen_ctype[g] : kConeNone;
+        const int ct = kind == kVert && !geometric ? ds.gen_ctype[g] : kConeNone;
         if (ct == kConeEmpty) continue;
         if (kind == kSegI) {
             if (tid == 0) push_global(ds, g);
             continue;
         }
         const int2 gl = ds.gen_lat[g];
-        const int4 cone = kind == kVert ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
+        const int4 cone = ct != kConeNone ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
         const int tx = gl.x >= 0 ? gl.x / tpx : -1, ty = gl.y >= 0 ? gl.y / tpy : -1;
         __syncthreads();  // the previous generator is done with smem
         for (int w = tid; w < words + pwords; w += kFloodThreads) fdyn[w] = 0u;

@@ -122,7 +122,7 @@ struct DevScene {
     int32_t tile;                      // tile side in pixels: 16 or 32
     int32_t tiles_x, tiles_y;
     int32_t use_flood;                 // 0: flood impossible (too many tiles for smem)
-    int32_t flood_mode;                // 0 auto (sparse visibility graph), 1 on, 2 off
+    int32_t flood_mode;                // 0 auto (sparse visibility graph), 1 on, 2 off, 3 geometric (concurrent)
     int32_t hidden_chunk;              // first hidden-test chunk in the pixel pass
     int32_t *tile_start;               // ntiles + 1 (CSR by tile)
     int32_t *tile_count;               // ntiles (counts, then fill cursors)

@@ -212,26 +212,27 @@ def test_source_touching_distance_and_many_sources(spm, oracle_mod):
 
 @pytest.mark.parametrize("which", ["maze", "polys"])
 def test_culling_modes_agree_bit_for_bit(spm, oracle_mod, which):
-    """Flooded per-tile lists, full scans, and both hidden-test chunk sizes
-    only drop candidates that cannot win, so every mode gives identical
-    outputs (and matches the oracle)."""
+    """Flooded per-tile lists (cone-pruned, or geometric on the side stream),
+    full scans, and both hidden-test chunk sizes only drop candidates that
+    cannot win, so every mode gives identical outputs (and matches the
+    oracle)."""
     scene = sg.maze(3, cells=10, N=640) if which == "maze" else sg.plain_polys(8, n_polys=90, N=512)
     s = spm.Scene(scene)
     outs = []
     for tile in (32, 16):
-        for mode in (1, 2, 0):
+        for mode in (1, 2, 0, 3):
             for chunk in (32, 256):
                 spm.spm_scene_set_tuning(s.handle, mode, chunk, tile)
                 d, p = s.compute()
                 s.sync()
                 outs.append((d.cpu().numpy(), p.cpu().numpy(), s.info()["flooded"]))
-    assert outs[0][2] == 1 and outs[2][2] == 0 and outs[6][2] == 1
+    assert outs[0][2] == 1 and outs[2][2] == 0 and outs[6][2] == 1 and outs[8][2] == 1
     for d, p, _ in outs[1:]:
         assert np.array_equal(d, outs[0][0]) and np.array_equal(p, outs[0][1])
     rd, rp, rd2, rp2 = oracle_mod.Oracle(scene).field()
     check_parity(scene, outs[0][0], outs[0][1], rd, rp, rd2, f"modes-{which}", rp2)
     t = s.autotune()
-    assert t["flood_mode"] in (1, 2) and t["hidden_chunk"] in (32, 256) and t["tile"] in (16, 32)
+    assert t["flood_mode"] in (1, 2, 3) and t["hidden_chunk"] in (32, 256) and t["tile"] in (16, 32)
 
 
 def test_batched_matches_individual_computes(spm, oracle_mod):
