@@ -32,6 +32,9 @@ namespace spm {
 namespace {
 
 constexpr int NT = kPixelThreads;
+#ifndef SPM_PIX16_MINB
+#define SPM_PIX16_MINB 4  // resident CTAs per SM the 16 x 16 kernel is compiled for
+#endif
 constexpr unsigned long long kUnset = 0x7F800000FFFFFFFFull;  // (+inf, id max)
 
 // Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
@@ -554,11 +557,14 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
     SPM_TFLUSH();
 }
 
-__global__ void __launch_bounds__(NT, 3) k_pixels(const __grid_constant__ DevScene ds, float *__restrict__ dist,
-                                               int32_t *__restrict__ parent, int tile0) {
+// One CTA per tile; one kernel per tile size, so each gets its own register
+// allocation (32 x 32 tiles: 4 pixels a thread, 16 x 16: 1).
+template <int PX>
+__global__ void __launch_bounds__(NT, PX == 4 ? 3 : SPM_PIX16_MINB) k_pixels(const __grid_constant__ DevScene ds,
+                                                                         float *__restrict__ dist,
+                                                                         int32_t *__restrict__ parent, int tile0) {
     __shared__ PixSmem sm;
-    if (ds.tile == kTile) pixel_tile<4>(ds, tile0 + blockIdx.x, dist, parent, sm, true);
-    else pixel_tile<1>(ds, tile0 + blockIdx.x, dist, parent, sm, true);
+    pixel_tile<PX>(ds, tile0 + blockIdx.x, dist, parent, sm, true);
 }
 
 // Persistent form over a batch of scenes: each CTA takes the next
@@ -600,7 +606,9 @@ __global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant_
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1) {
     const int tiles = ds.tiles_x * (tile_row1 - tile_row0);
-    if (tiles > 0) k_pixels<<<tiles, NT, 0, st>>>(ds, dist, parent, tile_row0 * ds.tiles_x);
+    if (tiles <= 0) return;
+    if (ds.tile == kTile) k_pixels<4><<<tiles, NT, 0, st>>>(ds, dist, parent, tile_row0 * ds.tiles_x);
+    else k_pixels<1><<<tiles, NT, 0, st>>>(ds, dist, parent, tile_row0 * ds.tiles_x);
 }
 
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st) {
