@@ -235,8 +235,9 @@ def run_batched(args, cfg_desc, scenes):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", torch.cuda.current_device())
     objs = [spm.Scene(sc) for sc in scenes]
-    for o in objs:  # full scans; the default tile follows each scene's pixel size
-        spm.spm_scene_set_tuning(o.handle, 2, 32, 0)
+    mode = 2 if args.culling == "scan" else 1  # flooded lists unless full scans are asked for
+    for o in objs:  # the default tile follows each scene's pixel size
+        spm.spm_scene_set_tuning(o.handle, mode, 32, 0)
     batch = spm.Batch(objs)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -268,9 +269,11 @@ def run_batched(args, cfg_desc, scenes):
             "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
             "config": {"workload": "batched256", "scene": cfg_desc, "scenes": len(all_scenes),
                        "pixels": npx_all, "l2": "flushed between timed steps (256 MiB write)",
-                       "launch": "one CUDA graph per step"},
+                       "launch": "one CUDA graph per step",
+                       "culling": "flooded per-tile lists" if mode != 2 else "every tile scans every generator"},
             "mpixel_per_s": npx_all / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
-            "gpu_launches": 8 * args.steps}  # 7 vertex-phase kernels + 1 persistent pixel kernel
+            # 7 vertex-phase kernels, the list reset, [flood, scan, fill], 1 persistent pixel kernel
+            "gpu_launches": (9 + (3 if mode != 2 else 0)) * args.steps}
     if world > 1:
         line["config"]["parallelism"] = f"scenes sharded longest-first over {world} ranks"
     if rank == 0:

@@ -444,6 +444,7 @@ void batch_free(spm_batch *b) {
 }
 void batch_launch(spm_batch *b, cudaStream_t st) {
     spm::launch_vertex_phase_batched(b->dev, st);
+    spm::launch_flood_batched(b->dev, st);
     spm::launch_pixel_phase_batched(b->dev, st);
 }
 }  // namespace
@@ -502,6 +503,11 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     bd.counters = balloc<int32_t>(b, 8);
     bd.max_rounds = 4 * max_gen + 64;
     bd.sssp_blocks = spm::sssp_batched_grid_blocks();
+    bd.flood_smem = 0;
+    for (int k = 0; k < n; ++k)
+        if (descs[k].use_flood && descs[k].flood_mode != 2)
+            bd.flood_smem = std::max<int32_t>(
+                bd.flood_smem, (int32_t)spm::flood_smem_bytes(descs[k].tiles_x * descs[k].tiles_y, descs[k].n_poly));
     for (void *p : b->allocs) ok &= p != nullptr;
     if (!ok) {
         batch_free(b);

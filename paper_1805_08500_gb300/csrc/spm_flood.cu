@@ -161,16 +161,8 @@ __device__ void insert_polygon_warp(const DevScene &ds, float *depth2, int2 g, i
     }
 }
 
-__global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
-    extern __shared__ unsigned fdyn[];
-    __shared__ FloodSmem sm;
-    if (ds.flood_mode == 0) {  // automatic: flood only sparse visibility graphs
-        const double pairs = (double)ds.n_gen * (double)max(ds.n_vert, 1);
-        if ((double)ds.in_start[ds.n_vert] > 0.01 * pairs) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) ds.flood_counts[2] = 1;
-            return;
-        }
-    }
+// Floods generator g of scene ds: one CTA, a breadth-first level at a time.
+__device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int g) {
     const int tid = threadIdx.x;
     const int ntiles = ds.tiles_x * ds.tiles_y, words = (ntiles + 31) / 32;
     const int pwords = ds.n_poly <= kFloodPolyBits ? (ds.n_poly + 31) / 32 : 0;
@@ -179,154 +171,218 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
     // mode 3 floods from geometry alone (every generator, no cone): it runs
     // before the vertex costs exist, and the pixel pass applies cost and cone
     const bool geometric = ds.flood_mode == 3;
-    for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) {
-        if (!geometric && !(ds.gen_costf[g] < INFINITY)) continue;
-        const int kind = ds.gen_kind[g];
-        const int ct = kind == kVert && !geometric ? ds.gen_ctype[g] : kConeNone;
-        if (ct == kConeEmpty) continue;
-        if (kind == kSegI) {
-            if (tid == 0) push_global(ds, g);
-            continue;
+    if (!geometric && !(ds.gen_costf[g] < INFINITY)) return;
+    const int kind = ds.gen_kind[g];
+    const int ct = kind == kVert && !geometric ? ds.gen_ctype[g] : kConeNone;
+    if (ct == kConeEmpty) return;
+    if (kind == kSegI) {
+        if (tid == 0) push_global(ds, g);
+        return;
+    }
+    const int2 gl = ds.gen_lat[g];
+    const int4 cone = ct != kConeNone ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
+    const int tx = gl.x >= 0 ? gl.x / tpx : -1, ty = gl.y >= 0 ? gl.y / tpy : -1;
+    __syncthreads();  // the previous generator is done with smem
+    for (int w = tid; w < words + pwords; w += kFloodThreads) fdyn[w] = 0u;
+    for (int k = tid; k < kAng; k += kFloodThreads) sm.depth2[k] = INFINITY;
+    if (tid == 0) {
+        sm.cnt[0] = 0;
+        sm.overflow = 0;
+        sm.n_ins = 0;
+    }
+    __syncthreads();
+    // seeds: every tile whose closed area contains g (up to 4 when g lies on tile edges)
+    if (tid < 4) {
+        const int sx = tx - (tid & 1), sy = ty - ((tid >> 1) & 1);
+        if (tx >= 0 && ty >= 0 && sx >= 0 && sy >= 0 && sx < ds.tiles_x && sy < ds.tiles_y) {
+            const int4 a4 = tile_area(ds, sx, sy);
+            if (gl.x >= a4.x && gl.x <= a4.z && gl.y >= a4.y && gl.y <= a4.w) {
+                const int t0 = sy * ds.tiles_x + sx;
+                if (!(atomicOr(&visited[t0 >> 5], 1u << (t0 & 31)) & (1u << (t0 & 31))))
+                    sm.front[0][atomicAdd(&sm.cnt[0], 1)] = t0;
+            }
         }
-        const int2 gl = ds.gen_lat[g];
-        const int4 cone = ct != kConeNone ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
-        const int tx = gl.x >= 0 ? gl.x / tpx : -1, ty = gl.y >= 0 ? gl.y / tpy : -1;
-        __syncthreads();  // the previous generator is done with smem
-        for (int w = tid; w < words + pwords; w += kFloodThreads) fdyn[w] = 0u;
-        for (int k = tid; k < kAng; k += kFloodThreads) sm.depth2[k] = INFINITY;
+    }
+    __syncthreads();
+    if (sm.cnt[0] == 0) {  // g outside every tile: scanned by all tiles instead
+        if (tid == 0) push_global(ds, g);
+        return;
+    }
+#ifdef SPM_COUNT
+    int n_tests = 0, n_levels = 0;
+#endif
+    int p = 0;
+    for (;;) {
+        if (sm.overflow) {  // a level outgrew the frontier: every tile scans g instead
+            if (tid == 0) {
+                push_global(ds, g);
+                SPM_CNT(13, 1);
+            }
+            break;
+        }
+        const int nc = min(sm.cnt[p], kFront);
+        if (nc == 0) break;
+        const int *cur = sm.front[p];
+        // A: the polygons in the frontier tiles' bins enter the depth map
+        for (int q = tid; q < nc * 16; q += kFloodThreads) {  // (tile, one of its first 16 bins)
+            const int i = q >> 4, j = q & 15;
+            const int t = cur[i];
+            const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
+            const int bx0 = max(0, (area.x - ds.bin_x0) / ds.bin_size), by0 = max(0, (area.y - ds.bin_y0) / ds.bin_size);
+            const int bx1 = min(ds.bin_nx - 1, (area.z - ds.bin_x0) / ds.bin_size);
+            const int by1 = min(ds.bin_ny - 1, (area.w - ds.bin_y0) / ds.bin_size);
+            const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
+            for (int jj = j; jj < nbx * nby; jj += 16) {
+                const int bin = (by0 + jj / nbx) * ds.bin_nx + bx0 + jj % nbx;
+                const int e = __ldg(ds.bin_start + bin + 1);
+                for (int it = __ldg(ds.bin_start + bin); it < e; ++it) {
+                    const int poly = __ldg(reinterpret_cast<const int *>(ds.bin_recs + it) + 4);
+                    if (pwords) {
+                        const unsigned bit = 1u << (poly & 31);
+                        if (atomicOr(&seen[poly >> 5], bit) & bit) continue;
+                    }
+                    const int slot = atomicAdd(&sm.n_ins, 1);
+                    if (slot < kInsCap) sm.ins[slot] = poly;  // beyond the cap: left out (conservative)
+                }
+            }
+        }
+        __syncthreads();
+        const int ni = min(sm.n_ins, kInsCap);
+        for (int q = tid >> 5; q < ni; q += kFloodThreads / 32)
+            insert_polygon_warp(ds, sm.depth2, gl, sm.ins[q], tid & 31);
+        __syncthreads();
+        // B: cone and depth-map test per frontier tile
+        for (int i = tid; i < nc; i += kFloodThreads) {
+            const int t = cur[i];
+            const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
+            int f = 2;
+            if (cone_meets_box(ct, cone, gl, area)) {
+                const bool inside = gl.x >= area.x && gl.x <= area.z && gl.y >= area.y && gl.y <= area.w;
+                f = !inside && box_hidden_ang(sm.depth2, gl, area) ? 1 : 0;
+            }
+            sm.flag[i] = f;
+        }
         if (tid == 0) {
-            sm.cnt[0] = 0;
-            sm.overflow = 0;
+            sm.cnt[p ^ 1] = 0;
             sm.n_ins = 0;
         }
         __syncthreads();
-        // seeds: every tile whose closed area contains g (up to 4 when g lies on tile edges)
-        if (tid < 4) {
-            const int sx = tx - (tid & 1), sy = ty - ((tid >> 1) & 1);
-            if (tx >= 0 && ty >= 0 && sx >= 0 && sy >= 0 && sx < ds.tiles_x && sy < ds.tiles_y) {
-                const int4 a4 = tile_area(ds, sx, sy);
-                if (gl.x >= a4.x && gl.x <= a4.z && gl.y >= a4.y && gl.y <= a4.w) {
-                    const int t0 = sy * ds.tiles_x + sx;
-                    if (!(atomicOr(&visited[t0 >> 5], 1u << (t0 & 31)) & (1u << (t0 & 31))))
-                        sm.front[0][atomicAdd(&sm.cnt[0], 1)] = t0;
-                }
-            }
-        }
-        __syncthreads();
-        if (sm.cnt[0] == 0) {  // g outside every tile: scanned by all tiles instead
-            if (tid == 0) push_global(ds, g);
-            continue;
-        }
+        // C: emit visible tiles, queue their fresh 8-neighbours
+        int *nxt = sm.front[p ^ 1];
+        for (int q = tid; q < nc * 9; q += kFloodThreads) {
+            const int i = q / 9, k = q - 9 * i;
+            const int f = sm.flag[i];
 #ifdef SPM_COUNT
-        int n_tests = 0, n_levels = 0;
-#endif
-        int p = 0;
-        for (;;) {
-            if (sm.overflow) {  // a level outgrew the frontier: every tile scans g instead
-                if (tid == 0) {
-                    push_global(ds, g);
-                    SPM_CNT(13, 1);
-                }
-                break;
-            }
-            const int nc = min(sm.cnt[p], kFront);
-            if (nc == 0) break;
-            const int *cur = sm.front[p];
-            // A: the polygons in the frontier tiles' bins enter the depth map
-            for (int q = tid; q < nc * 16; q += kFloodThreads) {  // (tile, one of its first 16 bins)
-                const int i = q >> 4, j = q & 15;
-                const int t = cur[i];
-                const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
-                const int bx0 = max(0, (area.x - ds.bin_x0) / ds.bin_size), by0 = max(0, (area.y - ds.bin_y0) / ds.bin_size);
-                const int bx1 = min(ds.bin_nx - 1, (area.z - ds.bin_x0) / ds.bin_size);
-                const int by1 = min(ds.bin_ny - 1, (area.w - ds.bin_y0) / ds.bin_size);
-                const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
-                for (int jj = j; jj < nbx * nby; jj += 16) {
-                    const int bin = (by0 + jj / nbx) * ds.bin_nx + bx0 + jj % nbx;
-                    const int e = __ldg(ds.bin_start + bin + 1);
-                    for (int it = __ldg(ds.bin_start + bin); it < e; ++it) {
-                        const int poly = __ldg(reinterpret_cast<const int *>(ds.bin_recs + it) + 4);
-                        if (pwords) {
-                            const unsigned bit = 1u << (poly & 31);
-                            if (atomicOr(&seen[poly >> 5], bit) & bit) continue;
-                        }
-                        const int slot = atomicAdd(&sm.n_ins, 1);
-                        if (slot < kInsCap) sm.ins[slot] = poly;  // beyond the cap: left out (conservative)
-                    }
-                }
-            }
-            __syncthreads();
-            const int ni = min(sm.n_ins, kInsCap);
-            for (int q = tid >> 5; q < ni; q += kFloodThreads / 32)
-                insert_polygon_warp(ds, sm.depth2, gl, sm.ins[q], tid & 31);
-            __syncthreads();
-            // B: cone and depth-map test per frontier tile
-            for (int i = tid; i < nc; i += kFloodThreads) {
-                const int t = cur[i];
-                const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
-                int f = 2;
-                if (cone_meets_box(ct, cone, gl, area)) {
-                    const bool inside = gl.x >= area.x && gl.x <= area.z && gl.y >= area.y && gl.y <= area.w;
-                    f = !inside && box_hidden_ang(sm.depth2, gl, area) ? 1 : 0;
-                }
-                sm.flag[i] = f;
-            }
-            if (tid == 0) {
-                sm.cnt[p ^ 1] = 0;
-                sm.n_ins = 0;
-            }
-            __syncthreads();
-            // C: emit visible tiles, queue their fresh 8-neighbours
-            int *nxt = sm.front[p ^ 1];
-            for (int q = tid; q < nc * 9; q += kFloodThreads) {
-                const int i = q / 9, k = q - 9 * i;
-                const int f = sm.flag[i];
-#ifdef SPM_COUNT
-                if (k == 4 && f != 2) {
-                    SPM_CNT(11, 1);
-                    SPM_CNT(12, f == 0 ? 1 : 0);
-                }
-#endif
-                if (f) continue;
-                const int t = cur[i];
-                if (k == 4) {
-                    const int slot = atomicAdd(&ds.flood_counts[0], 1);
-                    if (slot < ds.pair_cap) {
-                        ds.pairs[slot] = make_int2(t, g);
-                        atomicAdd(&ds.tile_count[t], 1);
-                    } else {
-                        atomicOr(&ds.flood_counts[2], 1);
-                    }
-                    continue;
-                }
-                const int nx = t % ds.tiles_x + k % 3 - 1, ny = t / ds.tiles_x + k / 3 - 1;
-                if (nx < 0 || ny < 0 || nx >= ds.tiles_x || ny >= ds.tiles_y) continue;
-                const int nt = ny * ds.tiles_x + nx;
-                if (atomicOr(&visited[nt >> 5], 1u << (nt & 31)) & (1u << (nt & 31))) continue;
-                const int slot = atomicAdd(&sm.cnt[p ^ 1], 1);
-                if (slot < kFront) nxt[slot] = nt;
-                else sm.overflow = 1;
-            }
-#ifdef SPM_COUNT
-            if (tid == 0) {
-                ++n_levels;
-                for (int i = 0; i < nc; ++i) n_tests += sm.flag[i] != 2;
+            if (k == 4 && f != 2) {
+                SPM_CNT(11, 1);
+                SPM_CNT(12, f == 0 ? 1 : 0);
             }
 #endif
-            __syncthreads();
-            p ^= 1;
+            if (f) continue;
+            const int t = cur[i];
+            if (k == 4) {
+                const int slot = atomicAdd(&ds.flood_counts[0], 1);
+                if (slot < ds.pair_cap) {
+                    ds.pairs[slot] = make_int2(t, g);
+                    atomicAdd(&ds.tile_count[t], 1);
+                } else {
+                    atomicOr(&ds.flood_counts[2], 1);
+                }
+                continue;
+            }
+            const int nx = t % ds.tiles_x + k % 3 - 1, ny = t / ds.tiles_x + k / 3 - 1;
+            if (nx < 0 || ny < 0 || nx >= ds.tiles_x || ny >= ds.tiles_y) continue;
+            const int nt = ny * ds.tiles_x + nx;
+            if (atomicOr(&visited[nt >> 5], 1u << (nt & 31)) & (1u << (nt & 31))) continue;
+            const int slot = atomicAdd(&sm.cnt[p ^ 1], 1);
+            if (slot < kFront) nxt[slot] = nt;
+            else sm.overflow = 1;
         }
 #ifdef SPM_COUNT
         if (tid == 0) {
-            SPM_CNT_MAX(14, n_tests);
-            SPM_CNT_MAX(15, n_levels);
+            ++n_levels;
+            for (int i = 0; i < nc; ++i) n_tests += sm.flag[i] != 2;
         }
 #endif
+        __syncthreads();
+        p ^= 1;
+    }
+#ifdef SPM_COUNT
+    if (tid == 0) {
+        SPM_CNT_MAX(14, n_tests);
+        SPM_CNT_MAX(15, n_levels);
+    }
+#endif
+
+}
+
+// Automatic mode: flood only sparse visibility graphs (mazes); a dense one
+// marks the lists unavailable and every tile scans every generator.
+__device__ __forceinline__ bool flood_declined(const DevScene &ds) {
+    if (ds.flood_mode != 0) return false;
+    const double pairs = (double)ds.n_gen * (double)max(ds.n_vert, 1);
+    return (double)ds.in_start[ds.n_vert] > 0.01 * pairs;
+}
+
+__global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
+    extern __shared__ unsigned fdyn[];
+    __shared__ FloodSmem sm;
+    if (flood_declined(ds)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ds.flood_counts[2] = 1;
+        return;
+    }
+    for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) flood_one(ds, sm, fdyn, g);
+}
+
+// Batched form: every (scene, generator) of the batch, one CTA each.
+template <class T>
+__device__ __forceinline__ int scene_of_b(const T *off, int n, T x) {
+    int lo = 0, hi = n;  // last scene with off[s] <= x
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kFloodThreads) k_flood_b(const __grid_constant__ BatchDev b) {
+    extern __shared__ unsigned fdyn[];
+    __shared__ FloodSmem sm;
+    const int total = b.gen_off[b.n];
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        const int sc = scene_of_b(b.gen_off, b.n, i);
+        const DevScene &ds = b.scenes[sc];
+        if (!ds.use_flood || ds.flood_mode == 2) continue;
+        if (flood_declined(ds)) {
+            if (threadIdx.x == 0) ds.flood_counts[2] = 1;
+            continue;
+        }
+        flood_one(ds, sm, fdyn, i - b.gen_off[sc]);
+    }
+}
+
+// Per-scene list state before a batched flood: counts zeroed, or the lists
+// marked unavailable for scenes that scan.
+__global__ void k_flood_reset_b(const __grid_constant__ BatchDev b) {
+    const int total = b.tile_off[b.n];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total + b.n; i += gridDim.x * blockDim.x) {
+        if (i < total) {
+            const int oi = scene_of_b(b.tile_off, b.n, i), sc = b.order[oi];
+            b.scenes[sc].tile_count[i - b.tile_off[oi]] = 0;
+        } else {
+            const DevScene &ds = b.scenes[i - total];
+            const bool on = ds.use_flood && ds.flood_mode != 2;
+            ds.flood_counts[0] = 0;
+            ds.flood_counts[1] = 0;
+            ds.flood_counts[2] = on ? 0 : 1;
+            ds.flood_counts[3] = 0;
+        }
     }
 }
 
 // Exclusive scan of tile_count into tile_start (one CTA), then fill.
-__global__ void __launch_bounds__(1024) k_tiles_scan(DevScene ds) {
+__device__ void tiles_scan_block(const DevScene &ds) {
     __shared__ long long wsum[32];
     const int n = ds.tiles_x * ds.tiles_y;
     const int per = (n + blockDim.x - 1) / blockDim.x;
@@ -343,13 +399,30 @@ __global__ void __launch_bounds__(1024) k_tiles_scan(DevScene ds) {
     if (threadIdx.x == 0 && n == 0) ds.tile_start[0] = 0;
 }
 
-__global__ void k_tiles_fill(DevScene ds) {
+__device__ __forceinline__ void tiles_fill(const DevScene &ds, int i0, int stride) {
     const int np = min(ds.flood_counts[0], ds.pair_cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    for (int i = i0; i < np; i += stride) {
         const int2 pr = ds.pairs[i];
         const int slot = atomicAdd(&ds.tile_count[pr.x], 1);
         ds.tile_items[ds.tile_start[pr.x] + slot] = pr.y;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_tiles_scan(DevScene ds) { tiles_scan_block(ds); }
+
+__global__ void k_tiles_fill(DevScene ds) {
+    tiles_fill(ds, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// batched: one CTA per scene for the scan, a row of CTAs per scene for the fill
+__global__ void __launch_bounds__(1024) k_tiles_scan_b(const __grid_constant__ BatchDev b) {
+    const DevScene &ds = b.scenes[blockIdx.x];
+    if (ds.use_flood && ds.flood_mode != 2) tiles_scan_block(ds);
+}
+
+__global__ void k_tiles_fill_b(const __grid_constant__ BatchDev b) {
+    const DevScene &ds = b.scenes[blockIdx.y];
+    if (ds.use_flood && ds.flood_mode != 2) tiles_fill(ds, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 }  // namespace
@@ -377,8 +450,17 @@ void launch_flood(const DevScene &ds, cudaStream_t st) {
 }
 
 int flood_smem_attr() {
-    return cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024 - (int)sizeof(FloodSmem)) == cudaSuccess;
+    const int dyn = 200 * 1024 - (int)sizeof(FloodSmem);
+    return cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess &&
+           cudaFuncSetAttribute(k_flood_b, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
+}
+
+void launch_flood_batched(const BatchDev &b, cudaStream_t st) {
+    k_flood_reset_b<<<152 * 4, 256, 0, st>>>(b);
+    if (b.flood_smem <= 0) return;  // every scene scans
+    k_flood_b<<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
+    k_tiles_scan_b<<<b.n, 1024, 0, st>>>(b);
+    k_tiles_fill_b<<<dim3(16, b.n), 256, 0, st>>>(b);
 }
 
 }  // namespace spm

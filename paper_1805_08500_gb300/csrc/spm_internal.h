@@ -158,6 +158,7 @@ struct BatchDev {
     int32_t *counters;                 // [0,1] frontier sizes, [2,3] dirty sizes, [4] rounds
     int32_t max_rounds;
     int32_t sssp_blocks;
+    int32_t flood_smem;                // dynamic shared memory of the batched flood (0: no scene floods)
 };
 
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
@@ -168,8 +169,10 @@ void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_
 void launch_flood(const DevScene &ds, cudaStream_t st);
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);
+void launch_flood_batched(const BatchDev &b, cudaStream_t st);
 int sssp_batched_grid_blocks();
 bool flood_possible(int tiles, int polys);
+size_t flood_smem_bytes(int tiles, int polys);  // dynamic shared memory of one flood CTA
 int flood_smem_attr();
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)

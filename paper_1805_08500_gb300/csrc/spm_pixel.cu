@@ -595,8 +595,8 @@ __global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant_
         for (int w = threadIdx.x; w < (int)(sizeof(DevScene) / 4); w += NT)
             reinterpret_cast<int *>(&sds)[w] = reinterpret_cast<const int *>(&b.scenes[sc])[w];
         __syncthreads();
-        if (sds.tile == kTile) pixel_tile<4>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, false);
-        else pixel_tile<1>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, false);
+        if (sds.tile == kTile) pixel_tile<4>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, true);
+        else pixel_tile<1>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, true);
         __syncthreads();
     }
 }
