@@ -429,6 +429,8 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     unsigned *dirty = (unsigned *)take(4 * 2 * dw);         // round parity p at p * dw
     unsigned short *dl = (unsigned short *)take(2 * 2 * n);  // round parity p at p * n
     __shared__ int cnt[3];  // dirty-list counts, by round modulo 3
+    constexpr int kSrcKinds = 64;
+    __shared__ signed char src_kind[kSrcKinds];  // kinds of the first sources (ids >= n_src are vertices)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSoloThreads / 32;
     // work unit: a group of 8 lanes per vertex (in-degrees here are small), 4 per warp
     const int grp = lane >> 3, gl = lane & 7, ngroups = nwarps * 4, gid = warp * 4 + grp;
@@ -450,6 +452,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         lat[g] = make_short2((short)l.x, (short)l.y);
     }
     for (int w = tid; w < 2 * dw; w += kSoloThreads) dirty[w] = 0u;
+    for (int g = tid; g < min(ds.n_src, kSrcKinds); g += kSoloThreads) src_kind[g] = (signed char)ds.gen_kind[g];
     if (tid < 3) cnt[tid] = 0;
     __syncthreads();
     auto mark = [&](int u, unsigned *bits, unsigned short *list, int *count) {
@@ -479,6 +482,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             const int vv = v - ds.n_src;
             if (act && gl == 0) atomicAnd(&dirty[cur * dw + (v >> 5)], ~(1u << (v & 31)));
             const short2 vl = lat[v];
+            const int4 wedge_v = act && gl == 0 ? __ldg(ds.gen_wedge + v) : make_int4(0, 0, 0, 0);  // needed at commit
             long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
             const int e1 = act ? in_start[vv + 1] : 0;
@@ -523,13 +527,14 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                     int ctv = kConeEmpty;  // unreachable again: no arrival direction
                     if (bpar >= 0) {
                         int dx, dy;
-                        if (ds.gen_kind[bpar] == kSegI) {
+                        const int kp = bpar >= ds.n_src ? kVert : (bpar < kSrcKinds ? src_kind[bpar] : ds.gen_kind[bpar]);
+                        if (kp == kSegI) {
                             arrival_dir(ds, bpar, make_int2(vl.x, vl.y), dx, dy);
                         } else {
                             dx = vl.x - lat[bpar].x;
                             dy = vl.y - lat[bpar].y;
                         }
-                        ctv = make_cone(ds.gen_wedge[v], dx, dy, c);
+                        ctv = make_cone(wedge_v, dx, dy, c);
                     }
                     ctype[ni * n + v] = (signed char)ctv;
                     cone[ni * n + v] = make_short4((short)c.x, (short)c.y, (short)c.z, (short)c.w);
