@@ -322,13 +322,15 @@ spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent
     const bool timed = cap == cudaStreamCaptureStatusNone;
     const bool side = s->ds.use_flood && s->ds.flood_mode == 3;  // geometric flood beside the vertex phase
     if (timed) cudaEventRecord(s->ev[0], cs);
+    // the side flood forks once the visibility graph is built and is
+    // submitted after the fixpoint kernel, so that the single-CTA fixpoint
+    // gets its SM first and the flood fills the others while it runs
+    spm::launch_vertex_phase(s->ds, cs, side ? s->fork : nullptr);
     if (side) {
-        cudaEventRecord(s->fork, cs);
         cudaStreamWaitEvent(s->side, s->fork, 0);
         spm::launch_flood(s->ds, s->side);
         cudaEventRecord(s->join, s->side);
     }
-    spm::launch_vertex_phase(s->ds, cs);
     if (timed) cudaEventRecord(s->ev[1], cs);
     if (side) {
         cudaStreamWaitEvent(cs, s->join, 0);

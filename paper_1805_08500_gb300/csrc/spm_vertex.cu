@@ -777,7 +777,7 @@ __global__ void k_finalize_b(const __grid_constant__ BatchDev b) {
 
 }  // namespace
 
-void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
+void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
     cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
     cudaMemsetAsync(ds.out_fill, 0, sizeof(int32_t) * ds.n_gen, st);
     if (ds.n_vert > 0) {
@@ -793,6 +793,7 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
     } else {
         cudaMemsetAsync(ds.in_start, 0, sizeof(int32_t) * (ds.n_vert + 1), st);
     }
+    if (graph_done) cudaEventRecord(graph_done, st);  // the visibility graph is built
     DevScene arg = ds;
     int max_rounds = 4 * ds.n_gen + 64;
     void *args[] = {&arg, &max_rounds};
