@@ -244,12 +244,18 @@ spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *cull_ms
  * hidden_chunk: first chunk of lb-ordered candidates whose tiles are tested
  *   for being hidden (32..256; later chunks double).
  * tile: pixel tile side, 16 or 32 (default 16 when a pixel spans 8 world
- *   units or more, else 32): each tile is one CTA of the pixel pass. */
+ *   units or more, else 32): each tile is one CTA of the pixel pass.
+ * maps: 1 = the flood keeps each point generator's angular depth map and the
+ *   pixel pass decides most pixels' visibility from it (exact bounds; only
+ *   the undecided pixels take the exact polygon test), 0 = every pixel takes
+ *   the exact test (default). Only with a flood (flood_mode != 2) and when
+ *   the maps fit (n_gen x 16 KB <= 256 MB). */
 typedef struct {
     int32_t flood_mode;
     int32_t hidden_chunk;
     int32_t tile;
-    int32_t reserved[5];
+    int32_t maps;
+    int32_t reserved[4];
 } spm_tuning;
 
 spm_status spm_scene_get_tuning(const spm_scene *scene, spm_tuning *out);
@@ -257,7 +263,8 @@ spm_status spm_scene_set_tuning(spm_scene *scene, const spm_tuning *tuning);
 
 /* Autotuner: times spm_compute on this scene (device events on `stream`,
  * warm-up then the median of 3 runs) for every flood_mode x hidden_chunk x
- * tile combination in {1, 2, 3} x {32, 256} x {16, 32}, keeps the fastest and
+ * tile x maps combination in {1, 2, 3} x {32, 256} x {16, 32} x {0, 1} (maps
+ * only with a flood), keeps the fastest and
  * writes it to *chosen (may be NULL). Synchronous. Allocates the scene's
  * output staging planes on first use; call it at set-up, not inside a
  * captured stream. */

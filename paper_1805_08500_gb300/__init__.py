@@ -42,7 +42,7 @@ class SpmError(RuntimeError):
 
 class SpmTuning(ctypes.Structure):
     _fields_ = [("flood_mode", ctypes.c_int32), ("hidden_chunk", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("tile", ctypes.c_int32), ("maps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class _Desc(ctypes.Structure):
@@ -277,11 +277,11 @@ def spm_extract_path(handle, x, y, cap=4096):
 def spm_scene_get_tuning(handle):
     t = SpmTuning()
     _check(load_library().spm_scene_get_tuning(handle, ctypes.byref(t)), "spm_scene_get_tuning", handle)
-    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk, "tile": t.tile}
+    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk, "tile": t.tile, "maps": t.maps}
 
 
-def spm_scene_set_tuning(handle, flood_mode, hidden_chunk, tile=0):
-    t = SpmTuning(int(flood_mode), int(hidden_chunk), int(tile))
+def spm_scene_set_tuning(handle, flood_mode, hidden_chunk, tile=0, maps=0):
+    t = SpmTuning(int(flood_mode), int(hidden_chunk), int(tile), int(maps))
     _check(load_library().spm_scene_set_tuning(handle, ctypes.byref(t)), "spm_scene_set_tuning", handle)
 
 
@@ -289,7 +289,7 @@ def spm_scene_autotune(handle, stream=None):
     t = SpmTuning()
     _check(load_library().spm_scene_autotune(handle, _stream_handle(stream), ctypes.byref(t)),
            "spm_scene_autotune", handle)
-    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk, "tile": t.tile}
+    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk, "tile": t.tile, "maps": t.maps}
 
 
 def spm_scene_info(handle):
@@ -447,7 +447,7 @@ def autotune_cached(scene: "Scene", stream=None, cache_key=None, path=TUNING_CAC
     key = f"{cache_key}|{_gpu_name()}" if cache_key else None
     if key and key in cache:
         t = cache[key]
-        spm_scene_set_tuning(scene.handle, t["flood_mode"], t["hidden_chunk"], t.get("tile", 0))
+        spm_scene_set_tuning(scene.handle, t["flood_mode"], t["hidden_chunk"], t.get("tile", 0), t.get("maps", 0))
         return dict(t, source="cache")
     t = spm_scene_autotune(scene.handle, stream)
     if key:

@@ -252,6 +252,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         ds.use_flood = spm::flood_possible((int)ntiles, ds.n_poly) && spm::flood_smem_attr() ? 1 : 0;
         ds.flood_mode = 0;
         ds.hidden_chunk = 32;
+        ds.use_maps = 0;
         const int64_t cap = std::min<int64_t>(std::max<int64_t>((int64_t)hs.n_gen * ntiles, 1),
                                               std::max<int64_t>(4 << 20, 64 * (int64_t)hs.n_gen));
         ds.pair_cap = ds.use_flood ? (int32_t)cap : 1;
@@ -260,6 +261,15 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         ds.tile_items = dalloc<int32_t>(s, ds.pair_cap);
         ds.pairs = dalloc<int2>(s, ds.pair_cap);
         ds.glob_list = dalloc<int32_t>(s, hs.n_gen);
+        // depth maps for the pixel pass, when they fit in 256 MB
+        const size_t map_bytes = (size_t)hs.n_gen * spm::kAngBins * sizeof(float2);
+        ds.gen_maps = nullptr;
+        ds.gen_map_ok = nullptr;
+        if (ds.use_flood && map_bytes <= ((size_t)256 << 20)) {
+            ds.gen_maps = dalloc<float2>(s, (size_t)hs.n_gen * spm::kAngBins);
+            ds.gen_map_ok = dalloc<uint8_t>(s, hs.n_gen);
+            if (ds.gen_map_ok) cudaMemset(ds.gen_map_ok, 0, hs.n_gen);
+        }
         ds.flood_counts = dalloc<int32_t>(s, 4);
     }
     ds.sssp_blocks = spm::sssp_grid_blocks();
@@ -506,10 +516,13 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     bd.max_rounds = 4 * max_gen + 64;
     bd.sssp_blocks = spm::sssp_batched_grid_blocks();
     bd.flood_smem = 0;
+    bd.any_maps = 0;
+    for (int k = 0; k < n; ++k) bd.any_maps |= descs[k].use_flood && descs[k].flood_mode != 2 && descs[k].use_maps;
     for (int k = 0; k < n; ++k)
         if (descs[k].use_flood && descs[k].flood_mode != 2)
             bd.flood_smem = std::max<int32_t>(
-                bd.flood_smem, (int32_t)spm::flood_smem_bytes(descs[k].tiles_x * descs[k].tiles_y, descs[k].n_poly));
+                bd.flood_smem, (int32_t)spm::flood_smem_bytes(descs[k].tiles_x * descs[k].tiles_y, descs[k].n_poly,
+                                                              descs[k].use_maps && descs[k].gen_maps));
     for (void *p : b->allocs) ok &= p != nullptr;
     if (!ok) {
         batch_free(b);
@@ -677,16 +690,18 @@ spm_status spm_scene_get_tuning(const spm_scene *s, spm_tuning *out) {
     out->flood_mode = s->ds.flood_mode;
     out->hidden_chunk = s->ds.hidden_chunk;
     out->tile = s->ds.tile;
+    out->maps = s->ds.use_maps;
     return SPM_OK;
 }
 
 spm_status spm_scene_set_tuning(spm_scene *s, const spm_tuning *t) {
     if (!s || !t) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
     if (t->flood_mode < 0 || t->flood_mode > 3 || t->hidden_chunk < 32 || t->hidden_chunk > 256 ||
-        (t->tile != 0 && t->tile != spm::kTile && t->tile != spm::kTileSmall))
+        (t->tile != 0 && t->tile != spm::kTile && t->tile != spm::kTileSmall) || t->maps < 0 || t->maps > 1)
         return set_err(s, SPM_ERR_INVALID_ARG, "tuning out of range");
     s->ds.flood_mode = t->flood_mode;
     s->ds.hidden_chunk = t->hidden_chunk;
+    s->ds.use_maps = t->maps && s->ds.gen_maps ? 1 : 0;
     if (t->tile) set_tile(s->ds, t->tile);
     return SPM_OK;
 }
@@ -711,12 +726,16 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     pick.flood_mode = s->ds.flood_mode;
     pick.hidden_chunk = s->ds.hidden_chunk;
     pick.tile = s->ds.tile;
+    pick.maps = s->ds.use_maps;
+    for (int ui = 0; ui < 2; ++ui)
     for (int ti = 0; ti < 2; ++ti)
     for (int mi = 0; mi < 3; ++mi) {
         if (modes[mi] != 2 && !s->ds.use_flood) continue;
+        if (ui == 1 && (modes[mi] == 2 || !s->ds.gen_maps)) continue;  // maps need a flood
         for (int ci = 0; ci < 2; ++ci) {
             s->ds.flood_mode = modes[mi];
             s->ds.hidden_chunk = chunks[ci];
+            s->ds.use_maps = ui;
             set_tile(s->ds, tiles[ti]);
             float t[3];
             st = spm_compute(s, stream, s->stage_dist, s->stage_par);  // warm-up
@@ -734,6 +753,7 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
                 pick.flood_mode = modes[mi];
                 pick.hidden_chunk = chunks[ci];
                 pick.tile = tiles[ti];
+                pick.maps = ui;
             }
         }
     }
@@ -741,6 +761,7 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     cudaEventDestroy(b);
     s->ds.flood_mode = pick.flood_mode;
     s->ds.hidden_chunk = pick.hidden_chunk;
+    s->ds.use_maps = pick.maps;
     set_tile(s->ds, pick.tile);
     if (chosen) *chosen = pick;
     if (st != SPM_OK) return st;

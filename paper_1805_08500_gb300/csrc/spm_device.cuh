@@ -242,6 +242,18 @@ __device__ __forceinline__ bool visible_foot(const DevScene &ds, int s, int px, 
     return !blocked;
 }
 
+// Pseudo-angle of direction (x, y) != 0: monotone in the true angle, [0, 4),
+// opposite directions differ by exactly 2. The angular depth maps of the
+// flood and the pixel pass bin directions by it (kAngBins bins of width
+// kAngW; kAngEps covers its float error, about 1e-6).
+constexpr float kAngW = 4.0f / kAngBins;
+constexpr float kAngEps = 1e-4f;
+__device__ __forceinline__ float pang(float x, float y) {
+    const float r = __fdividef(fabsf(y), fabsf(x) + fabsf(y));
+    if (y >= 0.f) return x >= 0.f ? r : 2.f - r;
+    return x < 0.f ? 2.f + r : 4.f - r;
+}
+
 // Exclusive prefix sum of one value per thread over a CTA of blockDim.x
 // threads (a multiple of 32, at most 1024); every thread must call it.
 // wsum: 32 shared slots. Returns the sum of the values of lower threads.

@@ -66,19 +66,9 @@ __device__ __forceinline__ void push_global(const DevScene &ds, int g) {
 // 1e-5 relative margin). Polygons enter the map as the flood reaches their
 // tiles, so every test is conservative; unions of polygons (walls that
 // overlap at posts) hide tiles that no single polygon hides.
-constexpr int kAng = 2048;          // pseudo-angle bins over [0, 4)
+constexpr int kAng = kAngBins;      // pseudo-angle bins over [0, 4)
 constexpr int kAngQ = kAng / 4;     // bins per quadrant (boundary m is pseudo-angle m / kAngQ)
-constexpr float kAngW = 4.0f / kAng;
-constexpr float kAngEps = 1e-4f;    // pseudo-angle margin (float error of pang is ~1e-6)
 constexpr int kInsCap = 1024;       // polygons inserted per level
-
-// Pseudo-angle of direction (x, y) != 0: monotone in the true angle, [0, 4),
-// opposite directions differ by exactly 2.
-__device__ __forceinline__ float pang(float x, float y) {
-    const float r = __fdividef(fabsf(y), fabsf(x) + fabsf(y));
-    if (y >= 0.f) return x >= 0.f ? r : 2.f - r;
-    return x < 0.f ? 2.f + r : 4.f - r;
-}
 
 // Pseudo-angle difference b - a wrapped into (-2, 2].
 __device__ __forceinline__ float pang_diff(float a, float b) {
@@ -107,6 +97,7 @@ struct FloodSmem {
     int cnt[2];
     int n_ins;
     int overflow;
+    int ins_dropped;       // a polygon was left out of the map (insertion list full)
 };
 
 // Is the closed box hidden from g (lattice point, not inside the box) by the
@@ -131,7 +122,9 @@ __device__ bool box_hidden_ang(const float *depth2, int2 g, int4 box) {
 
 // One warp inserts polygon q's front-facing edges into the depth map, the
 // lanes spread over each edge's bins.
-__device__ void insert_polygon_warp(const DevScene &ds, float *depth2, int2 g, int q, int lane) {
+template <bool MAPS>
+__device__ void insert_polygon_warp(const DevScene &ds, float *depth2, float *lo2, int2 g, int q, int lane,
+                                    float plen) {
     const int b = ds.poly_off[q], m = ds.poly_off[q + 1] - b;
     for (int i = 0; i < m; ++i) {
         const int2 a = ds.poly_v[b + i], c = ds.poly_v[b + (i + 1 == m ? 0 : i + 1)];
@@ -158,19 +151,46 @@ __device__ void insert_polygon_warp(const DevScene &ds, float *depth2, int2 g, i
             if (__int_as_float(*slot) <= h2) continue;  // this edge cannot lower the bin
             atomicMin(slot, __float_as_int(fmaxf(bdist2(k), bdist2(k + 1))));  // non-negative floats order as ints
         }
+        // Lower bound: a ray entering an obstacle crosses a front-facing edge
+        // (or passes a vertex of one) at a point of some piece of it, no
+        // nearer than that piece's distance from g. Pieces of at most plen
+        // lattice units; every bin touching a piece's closed angle range.
+        if (!MAPS) continue;
+        const float ax = (float)(a.x - g.x), ay = (float)(a.y - g.y), ex = (float)(c.x - a.x), ey = (float)(c.y - a.y);
+        const float el = sqrtf(ex * ex + ey * ey);
+        const int np = max(1, (int)ceilf(el / plen));
+        for (int j = lane; j < np; j += 32) {
+            const float t0 = (float)j / (float)np, t1 = j + 1 == np ? 1.f : (float)(j + 1) / (float)np;
+            const float px0 = ax + t0 * ex, py0 = ay + t0 * ey, px1 = ax + t1 * ex, py1 = ay + t1 * ey;
+            const float dx = px1 - px0, dy = py1 - py0, dd = dx * dx + dy * dy;
+            const float tt = dd > 0.f ? fminf(fmaxf(-(px0 * dx + py0 * dy) / dd, 0.f), 1.f) : 0.f;
+            const float cx = px0 + tt * dx, cy = py0 + tt * dy;
+            const float d2 = fmaxf((cx * cx + cy * cy) * (1.f - 2e-5f) - 0.05f, 0.f);
+            const float plo = pang(px1, py1), phi = plo + fmodf(pang(px0, py0) - plo + 4.f, 4.f);
+            const int b0 = (int)floorf((plo - kAngEps) / kAngW), b1 = (int)floorf((phi + kAngEps) / kAngW);
+            for (int k = b0; k <= b1; ++k) atomicMin((int *)&lo2[(k + 2 * kAng) & (kAng - 1)], __float_as_int(d2));
+        }
     }
 }
 
 // Floods generator g of scene ds: one CTA, a breadth-first level at a time.
+// MAPS: also keep g's depth map (with the lower-bound bins) for the pixel pass.
+template <bool MAPS>
 __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int g) {
     const int tid = threadIdx.x;
     const int ntiles = ds.tiles_x * ds.tiles_y, words = (ntiles + 31) / 32;
     const int pwords = ds.n_poly <= kFloodPolyBits ? (ds.n_poly + 31) / 32 : 0;
     unsigned *visited = fdyn, *seen = fdyn + words;  // tiles reached; polygons inserted
+    // with maps: lower bound of the squared distance at which a ray of each
+    // bin can first meet an obstacle (after the bitmaps in dynamic smem)
+    float *lo2 = reinterpret_cast<float *>(fdyn + words + pwords);
     const int tpx = ds.tile * (ds.S * ds.Wx / ds.Nx), tpy = ds.tile * (ds.S * ds.Wy / ds.Ny);
     // mode 3 floods from geometry alone (every generator, no cone): it runs
     // before the vertex costs exist, and the pixel pass applies cost and cone
     const bool geometric = ds.flood_mode == 3;
+    const float plen = fmaxf(1.f, 0.125f * (float)min(tpx, tpy));  // lower-bound piece length
+    constexpr bool maps = MAPS;
+    if (ds.gen_map_ok && tid == 0) ds.gen_map_ok[g] = 0;  // set again when the map is complete
     if (!geometric && !(ds.gen_costf[g] < INFINITY)) return;
     const int kind = ds.gen_kind[g];
     const int ct = kind == kVert && !geometric ? ds.gen_ctype[g] : kConeNone;
@@ -185,10 +205,13 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
     __syncthreads();  // the previous generator is done with smem
     for (int w = tid; w < words + pwords; w += kFloodThreads) fdyn[w] = 0u;
     for (int k = tid; k < kAng; k += kFloodThreads) sm.depth2[k] = INFINITY;
+    if (maps)
+        for (int k = tid; k < kAng; k += kFloodThreads) lo2[k] = INFINITY;
     if (tid == 0) {
         sm.cnt[0] = 0;
         sm.overflow = 0;
         sm.n_ins = 0;
+        sm.ins_dropped = 0;
     }
     __syncthreads();
     // seeds: every tile whose closed area contains g (up to 4 when g lies on tile edges)
@@ -242,14 +265,15 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
                         if (atomicOr(&seen[poly >> 5], bit) & bit) continue;
                     }
                     const int slot = atomicAdd(&sm.n_ins, 1);
-                    if (slot < kInsCap) sm.ins[slot] = poly;  // beyond the cap: left out (conservative)
+                    if (slot < kInsCap) sm.ins[slot] = poly;  // beyond the cap: left out of the map
+                    else sm.ins_dropped = 1;
                 }
             }
         }
         __syncthreads();
         const int ni = min(sm.n_ins, kInsCap);
         for (int q = tid >> 5; q < ni; q += kFloodThreads / 32)
-            insert_polygon_warp(ds, sm.depth2, gl, sm.ins[q], tid & 31);
+            insert_polygon_warp<MAPS>(ds, sm.depth2, lo2, gl, sm.ins[q], tid & 31, plen);
         __syncthreads();
         // B: cone and depth-map test per frontier tile
         for (int i = tid; i < nc; i += kFloodThreads) {
@@ -313,7 +337,13 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
         SPM_CNT_MAX(15, n_levels);
     }
 #endif
-
+    // keep the depth map for the pixel pass when it holds every polygon of
+    // the reached tiles (no frontier overflow, nothing left out)
+    if (maps && !sm.overflow && !sm.ins_dropped) {
+        float2 *mp = ds.gen_maps + (size_t)g * kAng;
+        for (int k = tid; k < kAng; k += kFloodThreads) mp[k] = make_float2(sm.depth2[k], lo2[k]);
+        if (tid == 0) ds.gen_map_ok[g] = 1;
+    }
 }
 
 // Automatic mode: flood only sparse visibility graphs (mazes); a dense one
@@ -324,14 +354,15 @@ __device__ __forceinline__ bool flood_declined(const DevScene &ds) {
     return (double)ds.in_start[ds.n_vert] > 0.01 * pairs;
 }
 
-__global__ void __launch_bounds__(kFloodThreads) k_flood(DevScene ds) {
+template <bool MAPS>
+__global__ void __launch_bounds__(kFloodThreads, MAPS ? 6 : 8) k_flood(DevScene ds) {
     extern __shared__ unsigned fdyn[];
     __shared__ FloodSmem sm;
     if (flood_declined(ds)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) ds.flood_counts[2] = 1;
         return;
     }
-    for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) flood_one(ds, sm, fdyn, g);
+    for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) flood_one<MAPS>(ds, sm, fdyn, g);
 }
 
 // Batched form: every (scene, generator) of the batch, one CTA each.
@@ -346,7 +377,8 @@ __device__ __forceinline__ int scene_of_b(const T *off, int n, T x) {
     return lo;
 }
 
-__global__ void __launch_bounds__(kFloodThreads) k_flood_b(const __grid_constant__ BatchDev b) {
+template <bool ANY_MAPS>  // some scene of the batch keeps depth maps
+__global__ void __launch_bounds__(kFloodThreads, ANY_MAPS ? 6 : 8) k_flood_b(const __grid_constant__ BatchDev b) {
     extern __shared__ unsigned fdyn[];
     __shared__ FloodSmem sm;
     const int total = b.gen_off[b.n];
@@ -358,7 +390,8 @@ __global__ void __launch_bounds__(kFloodThreads) k_flood_b(const __grid_constant
             if (threadIdx.x == 0) ds.flood_counts[2] = 1;
             continue;
         }
-        flood_one(ds, sm, fdyn, i - b.gen_off[sc]);
+        if (ANY_MAPS && ds.use_maps && ds.gen_maps) flood_one<true>(ds, sm, fdyn, i - b.gen_off[sc]);
+        else flood_one<false>(ds, sm, fdyn, i - b.gen_off[sc]);
     }
 }
 
@@ -427,11 +460,15 @@ __global__ void k_tiles_fill_b(const __grid_constant__ BatchDev b) {
 
 }  // namespace
 
-size_t flood_smem_bytes(int tiles, int polys) {  // dynamic part: visited tiles, inserted polygons
-    return sizeof(unsigned) * (size_t)((tiles + 31) / 32 + (polys <= kFloodPolyBits ? (polys + 31) / 32 : 0));
+// dynamic part: visited tiles, inserted polygons, and with maps the lower-bound bins
+size_t flood_smem_bytes(int tiles, int polys, bool maps) {
+    return sizeof(unsigned) * (size_t)((tiles + 31) / 32 + (polys <= kFloodPolyBits ? (polys + 31) / 32 : 0) +
+                                       (maps ? kAng : 0));
 }
 
-bool flood_possible(int tiles, int polys) { return flood_smem_bytes(tiles, polys) + sizeof(FloodSmem) <= 200 * 1024; }
+bool flood_possible(int tiles, int polys) {
+    return flood_smem_bytes(tiles, polys, true) + sizeof(FloodSmem) <= 200 * 1024;
+}
 
 void launch_flood(const DevScene &ds, cudaStream_t st) {
     const int ntiles = ds.tiles_x * ds.tiles_y;
@@ -442,23 +479,27 @@ void launch_flood(const DevScene &ds, cudaStream_t st) {
     }
     cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
     cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
-    const size_t smem = flood_smem_bytes(ntiles, ds.n_poly);
+    const size_t smem = flood_smem_bytes(ntiles, ds.n_poly, ds.use_maps && ds.gen_maps);
     const int blocks = min(152 * 8, ds.n_gen);
-    k_flood<<<max(blocks, 1), kFloodThreads, smem, st>>>(ds);
+    if (ds.use_maps && ds.gen_maps) k_flood<true><<<max(blocks, 1), kFloodThreads, smem, st>>>(ds);
+    else k_flood<false><<<max(blocks, 1), kFloodThreads, smem, st>>>(ds);
     k_tiles_scan<<<1, 1024, 0, st>>>(ds);
     k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds);
 }
 
 int flood_smem_attr() {
     const int dyn = 200 * 1024 - (int)sizeof(FloodSmem);
-    return cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess &&
-           cudaFuncSetAttribute(k_flood_b, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
+    return cudaFuncSetAttribute(k_flood<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess &&
+           cudaFuncSetAttribute(k_flood<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess &&
+           cudaFuncSetAttribute(k_flood_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess &&
+           cudaFuncSetAttribute(k_flood_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
 }
 
 void launch_flood_batched(const BatchDev &b, cudaStream_t st) {
     k_flood_reset_b<<<152 * 4, 256, 0, st>>>(b);
     if (b.flood_smem <= 0) return;  // every scene scans
-    k_flood_b<<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
+    if (b.any_maps) k_flood_b<true><<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
+    else k_flood_b<false><<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
     k_tiles_scan_b<<<b.n, 1024, 0, st>>>(b);
     k_tiles_fill_b<<<dim3(16, b.n), 256, 0, st>>>(b);
 }

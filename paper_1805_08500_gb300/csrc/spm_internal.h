@@ -13,6 +13,7 @@
 namespace spm {
 
 constexpr int kMaxPolyVerts = 16;    // convex polygon vertex limit
+constexpr int kAngBins = 2048;       // pseudo-angle bins of a generator's depth map
 constexpr int kTile = 32;            // largest pixel tile side (one CTA per tile)
 constexpr int kTileSmall = 16;       // small tile side, for coarse grids
 constexpr int kPixelThreads = 256;   // 32x32 tiles: 4 pixels per thread; 16x16: 1
@@ -124,10 +125,19 @@ struct DevScene {
     int32_t use_flood;                 // 0: flood impossible (too many tiles for smem)
     int32_t flood_mode;                // 0 auto (sparse visibility graph), 1 on, 2 off, 3 geometric (concurrent)
     int32_t hidden_chunk;              // first hidden-test chunk in the pixel pass
+    int32_t use_maps;                  // keep and use the flood's depth maps (needs gen_maps)
     int32_t *tile_start;               // ntiles + 1 (CSR by tile)
     int32_t *tile_count;               // ntiles (counts, then fill cursors)
     int32_t *tile_items;               // pair_cap generator ids
     int2 *pairs;                       // pair_cap (tile, generator)
+    // per-generator angular depth maps kept by the flood for the pixel pass
+    // (null when the scene has too many generators for them): kAngBins
+    // float2 (upper bound of the squared distance at which every ray of the
+    // bin is inside an obstacle, lower bound of the squared distance at which
+    // any ray of the bin can first meet one) per generator, and a flag per
+    // generator set when its map is complete for this compute
+    float2 *gen_maps;
+    uint8_t *gen_map_ok;
     int32_t pair_cap;
     int32_t *glob_list;                // generators every tile scans
     int32_t *flood_counts;             // [0] pairs, [1] global list size, [2] overflow
@@ -159,6 +169,7 @@ struct BatchDev {
     int32_t max_rounds;
     int32_t sssp_blocks;
     int32_t flood_smem;                // dynamic shared memory of the batched flood (0: no scene floods)
+    int32_t any_maps;                  // some scene keeps depth maps
 };
 
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
@@ -173,7 +184,7 @@ void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_flood_batched(const BatchDev &b, cudaStream_t st);
 int sssp_batched_grid_blocks();
 bool flood_possible(int tiles, int polys);
-size_t flood_smem_bytes(int tiles, int polys);  // dynamic shared memory of one flood CTA
+size_t flood_smem_bytes(int tiles, int polys, bool maps);  // dynamic shared memory of one flood CTA
 int flood_smem_attr();
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)

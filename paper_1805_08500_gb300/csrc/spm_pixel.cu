@@ -279,7 +279,7 @@ __device__ void build_blockers(const DevScene &ds, PixSmem &sm, float cx, float 
 // One tile of one scene, by one CTA: 32 x 32 pixels with PX = 4 pixels per
 // thread (consecutive in a row), or 16 x 16 with PX = 1. allow_lists = false
 // ignores flooded candidate lists (the batched form scans every generator).
-template <int PX>
+template <int PX, bool MAPS>
 __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, float *__restrict__ dist,
                                            int32_t *__restrict__ parent, PixSmem &sm, const bool allow_lists) {
     constexpr int T = PX == 4 ? 32 : 16;
@@ -429,6 +429,12 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 unsigned need = 0;
                 unsigned long long nk[PX];
                 long long num[PX];
+                // the flood's depth map of a point generator decides most pixels:
+                // nearer than any obstacle on their ray -> visible; beyond a full
+                // blocking -> hidden; only the rest need the exact test below
+                const float2 *gmap = MAPS && lists && ds.use_maps && ds.gen_maps && kind != kSegI && ds.gen_map_ok[gc]
+                                         ? ds.gen_maps + (size_t)gc * kAngBins
+                                         : nullptr;
 #pragma unroll
                 for (int k = 0; k < PX; ++k) {
                     nk[k] = kUnset;
@@ -448,6 +454,23 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                     }
                     const unsigned long long kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)gc;
                     if (kk < key[k]) {
+                        if (MAPS && gmap) {
+                            const int rx = px[k] - gl.x, ry = py - gl.y;
+                            if (rx == 0 && ry == 0) {  // the generator's own pixel
+                                key[k] = kk;
+                                continue;
+                            }
+                            const float r2 = (float)((long long)rx * rx + (long long)ry * ry);
+                            const float a = pang((float)rx, (float)ry);
+                            const int b0 = (int)floorf((a - kAngEps) / kAngW), b1 = (int)floorf((a + kAngEps) / kAngW);
+                            const float2 m0 = __ldg(gmap + ((b0 + kAngBins) & (kAngBins - 1)));
+                            const float2 m1 = __ldg(gmap + (b1 & (kAngBins - 1)));
+                            if (r2 * (1.f - 1e-5f) >= fmaxf(m0.x, m1.x)) continue;  // hidden
+                            if (r2 * (1.f + 1e-5f) < fminf(m0.y, m1.y)) {           // visible
+                                key[k] = kk;
+                                continue;
+                            }
+                        }
                         nk[k] = kk;
                         need |= 1u << k;
                     }
@@ -559,17 +582,18 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
 
 // One CTA per tile; one kernel per tile size, so each gets its own register
 // allocation (32 x 32 tiles: 4 pixels a thread, 16 x 16: 1).
-template <int PX>
+template <int PX, bool MAPS>
 __global__ void __launch_bounds__(NT, PX == 4 ? 3 : SPM_PIX16_MINB) k_pixels(const __grid_constant__ DevScene ds,
                                                                          float *__restrict__ dist,
                                                                          int32_t *__restrict__ parent, int tile0) {
     __shared__ PixSmem sm;
-    pixel_tile<PX>(ds, tile0 + blockIdx.x, dist, parent, sm, true);
+    pixel_tile<PX, MAPS>(ds, tile0 + blockIdx.x, dist, parent, sm, true);
 }
 
 // Persistent form over a batch of scenes: each CTA takes the next
 // (scene, tile) from a global counter (scenes ordered largest first), copies
 // that scene's descriptor into shared memory and runs the same tile code.
+template <bool ANY_MAPS>  // some scene of the batch uses depth maps
 __global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant__ BatchDev b) {
     __shared__ PixSmem sm;
     __shared__ DevScene sds;
@@ -595,8 +619,8 @@ __global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant_
         for (int w = threadIdx.x; w < (int)(sizeof(DevScene) / 4); w += NT)
             reinterpret_cast<int *>(&sds)[w] = reinterpret_cast<const int *>(&b.scenes[sc])[w];
         __syncthreads();
-        if (sds.tile == kTile) pixel_tile<4>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, true);
-        else pixel_tile<1>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, true);
+        if (sds.tile == kTile) pixel_tile<4, ANY_MAPS>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, true);
+        else pixel_tile<1, ANY_MAPS>(sds, t - b.tile_off[oi], b.dist[sc], b.parent[sc], sm, true);
         __syncthreads();
     }
 }
@@ -607,8 +631,14 @@ void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_
                         int tile_row1) {
     const int tiles = ds.tiles_x * (tile_row1 - tile_row0);
     if (tiles <= 0) return;
-    if (ds.tile == kTile) k_pixels<4><<<tiles, NT, 0, st>>>(ds, dist, parent, tile_row0 * ds.tiles_x);
-    else k_pixels<1><<<tiles, NT, 0, st>>>(ds, dist, parent, tile_row0 * ds.tiles_x);
+    const int t0 = tile_row0 * ds.tiles_x;
+    if (ds.use_maps && ds.gen_maps) {
+        if (ds.tile == kTile) k_pixels<4, true><<<tiles, NT, 0, st>>>(ds, dist, parent, t0);
+        else k_pixels<1, true><<<tiles, NT, 0, st>>>(ds, dist, parent, t0);
+    } else {
+        if (ds.tile == kTile) k_pixels<4, false><<<tiles, NT, 0, st>>>(ds, dist, parent, t0);
+        else k_pixels<1, false><<<tiles, NT, 0, st>>>(ds, dist, parent, t0);
+    }
 }
 
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st) {
@@ -616,9 +646,11 @@ void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st) {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pixels_batched, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.any_maps ? k_pixels_batched<true> : k_pixels_batched<false>,
+                                                  NT, 0);
     const int grid = max(1, min(b.total_tiles, sms * max(per_sm, 1)));
-    k_pixels_batched<<<grid, NT, 0, st>>>(b);
+    if (b.any_maps) k_pixels_batched<true><<<grid, NT, 0, st>>>(b);
+    else k_pixels_batched<false><<<grid, NT, 0, st>>>(b);
 }
 
 int count_kernel_launches_pixel() { return 1; }

@@ -227,12 +227,20 @@ def test_culling_modes_agree_bit_for_bit(spm, oracle_mod, which):
                 s.sync()
                 outs.append((d.cpu().numpy(), p.cpu().numpy(), s.info()["flooded"]))
     assert outs[0][2] == 1 and outs[2][2] == 0 and outs[6][2] == 1 and outs[8][2] == 1
+    for tile in (32, 16):  # depth maps decide most pixels: same outputs
+        for mode in (1, 3):
+            spm.spm_scene_set_tuning(s.handle, mode, 32, tile, 1)
+            assert s.tuning()["maps"] == 1
+            d, p = s.compute()
+            s.sync()
+            outs.append((d.cpu().numpy(), p.cpu().numpy(), s.info()["flooded"]))
     for d, p, _ in outs[1:]:
         assert np.array_equal(d, outs[0][0]) and np.array_equal(p, outs[0][1])
     rd, rp, rd2, rp2 = oracle_mod.Oracle(scene).field()
     check_parity(scene, outs[0][0], outs[0][1], rd, rp, rd2, f"modes-{which}", rp2)
     t = s.autotune()
     assert t["flood_mode"] in (1, 2, 3) and t["hidden_chunk"] in (32, 256) and t["tile"] in (16, 32)
+    assert t["maps"] in (0, 1)
 
 
 def test_batched_matches_individual_computes(spm, oracle_mod):
