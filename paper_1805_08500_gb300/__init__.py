@@ -26,6 +26,8 @@ SPM_OK = 0
 STATUS_NAMES = {0: "SPM_OK", 1: "SPM_ERR_INVALID_ARG", 2: "SPM_ERR_BAD_GEOMETRY",
                 3: "SPM_ERR_OOM", 4: "SPM_ERR_CUDA", 5: "SPM_ERR_NOT_CONVERGED",
                 6: "SPM_ERR_TIMEOUT", 7: "SPM_ERR_CAPACITY"}
+(SPM_ERR_INVALID_ARG, SPM_ERR_BAD_GEOMETRY, SPM_ERR_OOM, SPM_ERR_CUDA, SPM_ERR_NOT_CONVERGED,
+ SPM_ERR_TIMEOUT, SPM_ERR_CAPACITY) = range(1, 8)
 KIND_POINT, KIND_SEG_A, KIND_SEG_B, KIND_SEG_INTERIOR, KIND_VERTEX = range(5)
 
 

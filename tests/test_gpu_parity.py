@@ -357,3 +357,46 @@ def test_row_slabs_concatenate_to_the_full_map(spm):
         assert torch.equal(d.view(torch.int32), d_full.view(torch.int32))
     with pytest.raises(spm.SpmError):
         s.compute_rows(1, tile, d_full, p_full)  # not tile-aligned
+
+
+def test_edge_capacity_overflow_is_reported(spm):
+    """A visibility graph larger than the edge capacity (max(2^20, 128 per
+    generator)) is reported as SPM_ERR_CAPACITY by spm_scene_sync, not
+    silently truncated: 784 small squares in open space give ~3100 mutually
+    visible corners."""
+    polys = []
+    for i in range(28):
+        for j in range(28):
+            x0, y0 = 64 + 140 * i, 64 + 140 * j
+            polys.append(np.array([(x0, y0), (x0 + 8, y0), (x0 + 8, y0 + 8), (x0, y0 + 8)], np.int32))
+    scene = sg.Scene((4096, 4096), (256, 256), polys, np.array([[30.0, 30.0]]), np.zeros((0, 4)), name="dense")
+    s = spm.Scene(scene)
+    d, p = s.empty_outputs()
+    s.compute(d, p)
+    with pytest.raises(spm.SpmError) as err:
+        s.sync()
+    assert err.value.status == spm.SPM_ERR_CAPACITY
+    s.compute(d, p)  # the scene stays usable and keeps reporting it
+    with pytest.raises(spm.SpmError):
+        s.sync()
+
+
+def test_compute_captured_in_a_cuda_graph(spm, oracle_mod):
+    """spm_compute records into a user's CUDA graph -- including the
+    geometric flood on the scene's side stream and the depth maps -- and the
+    replay reproduces a direct compute bit for bit."""
+    scene = sg.maze(4, cells=12, N=768)
+    s = spm.Scene(scene)
+    spm.spm_scene_set_tuning(s.handle, 3, 32, 32, 1)
+    d_ref, p_ref = s.compute()
+    s.sync()
+    d, p = s.empty_outputs()
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        spm.spm_compute(s.handle, st, d, p)
+    d.fill_(0.0)
+    p.fill_(-5)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(p, p_ref) and torch.equal(d.view(torch.int32), d_ref.view(torch.int32))
