@@ -158,6 +158,18 @@ spm_status spm_scene_sync(spm_scene *scene, void *stream);
 spm_status spm_query_parent(spm_scene *scene, float x, float y, int32_t *parent,
                             float *dist);
 
+/* Exact point query (Sec. 6, Discussion: a point on a region border may take
+ * a parent up to half a pixel's diagonal off, and comparing the neighbouring
+ * parents at the point itself removes the error). The parents of the 3 x 3
+ * pixels around (x, y) in the last whole-grid compute are evaluated at the
+ * lattice point nearest (x, y) with the exact visibility and cone tests and
+ * FP64 distances at (x, y) itself; writes the closest (ties: smaller id) and
+ * its distance, -1 / +inf when none is valid there. Synchronous (one small
+ * kernel on the compute's stream). SPM_ERR_INVALID_ARG when (x, y) is outside
+ * the world or nothing was computed yet. */
+spm_status spm_query_exact(spm_scene *scene, float x, float y, int32_t *parent,
+                           float *dist);
+
 /* Shortest path from world point (x, y) back to its source (Sec. 1: the path
  * is retrieved by following parents, linear in its number of vertices).
  * Writes the polyline to out_xy (2 floats per point, starting at (x, y),

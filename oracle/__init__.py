@@ -68,6 +68,8 @@ def _load():
         lib.orc_visible.argtypes = [P] + [ctypes.c_longlong] * 4
         lib.orc_keys.argtypes = [P, ctypes.c_int, i32p, i32p, f64p]
         lib.orc_keys.restype = None
+        lib.orc_points.argtypes = [P, ctypes.c_int, i64p, f64p, i32p]
+        lib.orc_points.restype = None
         lib.orc_root_link.restype = ctypes.c_int
         lib.orc_root_link.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       f64p, ctypes.POINTER(ctypes.c_double)]
@@ -176,6 +178,17 @@ class Oracle:
         if len(gens):
             _lib.orc_keys(self._h, len(gens), ij.reshape(-1), gens, out)
         return out
+
+    def points(self, lxy):
+        """Field (dist, parent) at arbitrary lattice points lxy (n, 2), world
+        coordinates lxy / S (Sec. 6: exact point queries)."""
+        lxy = np.ascontiguousarray(np.asarray(lxy, dtype=np.int64).reshape(-1, 2))
+        n = lxy.shape[0]
+        dist = np.zeros(n, np.float64)
+        par = np.zeros(n, np.int32)
+        if n:
+            _lib.orc_points(self._h, n, lxy.reshape(-1), dist, par)
+        return dist, par
 
     def visible(self, a, b) -> bool:
         """Exact visibility between two lattice points."""

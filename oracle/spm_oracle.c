@@ -775,11 +775,11 @@ static int pixel_free(const orc_t *o, ll px, ll py) {
     return 1;
 }
 
-static void eval_pixel(const orc_t *o, int i, int j, hitem *heap, int *stamp, int *tick,
+/* The field at one point: lattice position (px, py) for the exact predicates,
+ * world coordinates (fx, fy) for the distances. Best and second-best valid
+ * generator (different ids), by key then id. */
+static void eval_point(const orc_t *o, ll px, ll py, double fx, double fy, hitem *heap, int *stamp, int *tick,
                        int use_cone, double *d1, int *p1, double *d2, int *p2) {
-    ll px = pix_lat(o->S, o->Wx, o->Nx, i), py = pix_lat(o->S, o->Wy, o->Ny, j);
-    double fx = ((double)i + 0.5) * (double)o->Wx / (double)o->Nx;
-    double fy = ((double)j + 0.5) * (double)o->Wy / (double)o->Ny;
     *d1 = *d2 = INFINITY;
     *p1 = *p2 = -1;
     if (!pixel_free(o, px, py)) return;
@@ -828,6 +828,14 @@ static void eval_pixel(const orc_t *o, int i, int j, hitem *heap, int *stamp, in
         else { *d2 = it.c; *p2 = g; }
         found++;
     }
+}
+
+static void eval_pixel(const orc_t *o, int i, int j, hitem *heap, int *stamp, int *tick,
+                       int use_cone, double *d1, int *p1, double *d2, int *p2) {
+    ll px = pix_lat(o->S, o->Wx, o->Nx, i), py = pix_lat(o->S, o->Wy, o->Ny, j);
+    double fx = ((double)i + 0.5) * (double)o->Wx / (double)o->Nx;
+    double fy = ((double)j + 0.5) * (double)o->Wy / (double)o->Ny;
+    eval_point(o, px, py, fx, fy, heap, stamp, tick, use_cone, d1, p1, d2, p2);
 }
 
 static void *pix_worker(void *arg) {
@@ -967,6 +975,23 @@ void orc_keys(void *h, int n, const int *ij, const int *gen, double *key) {
         }
         if (ok) key[q] = k;
     }
+    free(stamp);
+}
+
+/* The field at arbitrary lattice points lxy (2 per point), world coordinates
+ * lxy / S: best key and generator (the point queries of Sec. 6). */
+void orc_points(void *h, int n, const long long *lxy, double *dist, int *par) {
+    const orc_t *o = h;
+    hitem *heap = malloc(sizeof(hitem) * (o->ng + 1));
+    int *stamp = calloc(o->np + 1, sizeof(int));
+    int tick = 0;
+    for (int q = 0; q < n; q++) {
+        double d2;
+        int p2;
+        eval_point(o, lxy[2 * q], lxy[2 * q + 1], (double)lxy[2 * q] / (double)o->S, (double)lxy[2 * q + 1] / (double)o->S,
+                   heap, stamp, &tick, 1, &dist[q], &par[q], &d2, &p2);
+    }
+    free(heap);
     free(stamp);
 }
 

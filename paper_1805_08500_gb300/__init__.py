@@ -90,6 +90,7 @@ def load_library():
         "spm_batch_destroy": ([P], None),
         "spm_scene_sync": ([P, P], I32),
         "spm_query_parent": ([P, F, F, P, P], I32),
+        "spm_query_exact": ([P, F, F, P, P], I32),
         "spm_extract_path": ([P, F, F, P, I32, P], I32),
         "spm_scene_generators": ([P, P, P, P, P], I32),
         "spm_scene_info": ([P, P], I32),
@@ -268,6 +269,15 @@ def spm_query_parent(handle, x, y):
     return p.value, d.value
 
 
+def spm_query_exact(handle, x, y):
+    """(parent, distance) at (x, y) itself, from the neighbouring pixels' parents."""
+    p = ctypes.c_int32()
+    d = ctypes.c_float()
+    _check(load_library().spm_query_exact(handle, float(x), float(y), ctypes.byref(p),
+                                          ctypes.byref(d)), "spm_query_exact", handle)
+    return p.value, d.value
+
+
 def spm_extract_path(handle, x, y, cap=4096):
     out = np.zeros(2 * cap, np.float32)
     n = ctypes.c_int32()
@@ -427,6 +437,9 @@ class Scene:
 
     def query_parent(self, x, y):
         return spm_query_parent(self.handle, x, y)
+
+    def query_exact(self, x, y):
+        return spm_query_exact(self.handle, x, y)
 
     def extract_path(self, x, y, cap=4096):
         return spm_extract_path(self.handle, x, y, cap)

@@ -41,6 +41,7 @@ struct spm_scene {
     // phase timing events (vertex start, pixel start, end)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_valid = false;
+    double *query_out = nullptr;  // exact query result: distance, then parent (device)
     // side stream of the geometric flood (flood mode 3), with fork/join events
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -605,6 +606,35 @@ spm_status spm_query_parent(spm_scene *s, float x, float y, int32_t *parent, flo
         cudaMemcpy(parent, s->last_parent + idx, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(dist, s->last_dist + idx, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
         return set_err(s, SPM_ERR_CUDA, "query copy failed");
+    return SPM_OK;
+}
+
+spm_status spm_query_exact(spm_scene *s, float x, float y, int32_t *parent, float *dist) {
+    if (!s || !parent || !dist) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    if (!s->last_parent) return set_err(s, SPM_ERR_INVALID_ARG, "nothing computed yet");
+    if (!(x >= 0.f && y >= 0.f && x < (float)s->hs.Wx && y < (float)s->hs.Wy))
+        return set_err(s, SPM_ERR_INVALID_ARG, "query point outside the world");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    int i = (int)std::floor(x / s->ds.hx), j = (int)std::floor(y / s->ds.hy);
+    i = std::min(i, s->hs.Nx - 1);
+    j = std::min(j, s->hs.Ny - 1);
+    // the predicates run on the lattice point nearest to (x, y)
+    const double S = (double)s->hs.S;
+    const int qx = (int)std::lrint((double)x * S), qy = (int)std::lrint((double)y * S);
+    if (!s->query_out) {
+        s->query_out = dalloc<double>(s, 2);
+        if (!s->query_out) return set_err(s, SPM_ERR_OOM, "query buffer allocation failed");
+    }
+    int32_t *out_par = reinterpret_cast<int32_t *>(s->query_out + 1);
+    spm::launch_query_exact(s->ds, s->last_stream, s->last_parent, i, j, qx, qy, (double)x, (double)y, out_par,
+                            s->query_out);
+    double res[2];
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s->last_stream) != cudaSuccess ||
+        cudaMemcpy(res, s->query_out, sizeof res, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "exact query failed");
+    std::memcpy(parent, &res[1], sizeof(int32_t));
+    *dist = (float)res[0];
     return SPM_OK;
 }
 

@@ -182,6 +182,9 @@ void launch_flood(const DevScene &ds, cudaStream_t st);
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_flood_batched(const BatchDev &b, cudaStream_t st);
+// exact query at lattice point (qx, qy), world (fx, fy), pixel (i, j) of the last field
+void launch_query_exact(const DevScene &ds, cudaStream_t st, const int32_t *field_parent, int i, int j, int qx,
+                        int qy, double fx, double fy, int32_t *out_par, double *out_dist);
 int sssp_batched_grid_blocks();
 bool flood_possible(int tiles, int polys);
 size_t flood_smem_bytes(int tiles, int polys, bool maps);  // dynamic shared memory of one flood CTA

@@ -627,6 +627,67 @@ __global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant_
 
 }  // namespace
 
+// Exact point query (Sec. 6, Discussion: a point on a region border may take
+// a parent up to half a pixel's diagonal off; comparing the parents of the
+// neighbouring pixels at the point itself removes the error). One warp: lane
+// k < 9 evaluates the parent of pixel (i + k % 3 - 1, j + k / 3 - 1) at the
+// lattice point q (world coordinates qf) with the exact predicates, FP64 keys
+// in the same operation order as the distance definition; the smallest key
+// (then id) wins.
+__global__ void k_query_exact(const __grid_constant__ DevScene ds, const int32_t *__restrict__ field_parent, int i,
+                              int j, int2 q, double2 qf, int32_t *out_par, double *out_dist) {
+    const int lane = threadIdx.x;
+    int g = -1;
+    if (lane < 9) {
+        const int ii = i + lane % 3 - 1, jj = j + lane / 3 - 1;
+        if (ii >= 0 && jj >= 0 && ii < ds.Nx && jj < ds.Ny) g = field_parent[(size_t)jj * ds.Nx + ii];
+    }
+    double key = INFINITY;
+    if (g >= 0 && ds.gen_cost[g] < INFINITY) {
+        const int kind = ds.gen_kind[g];
+        if (kind == kSegI) {
+            const int s = ds.gen_aux[g];
+            const int4 L = ds.seg_lat[s];
+            const long long ux = L.z - L.x, uy = L.w - L.y;
+            const long long num = (q.x - L.x) * ux + (q.y - L.y) * uy, den = ux * ux + uy * uy;
+            if (num > 0 && num < den && visible_foot(ds, s, q.x, q.y, num, den)) {
+                const float4 F = ds.seg_pos[s];
+                const double fx = __dsub_rn((double)F.z, (double)F.x), fy = __dsub_rn((double)F.w, (double)F.y);
+                const double c = __dsub_rn(__dmul_rn(fx, __dsub_rn(qf.y, (double)F.y)), __dmul_rn(fy, __dsub_rn(qf.x, (double)F.x)));
+                key = __ddiv_rn(fabs(c), __dsqrt_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy))));
+            }
+        } else {
+            const int2 gl = ds.gen_lat[g];
+            const bool cone_ok = kind != kVert || in_cone(ds.gen_ctype[g], ds.gen_cone[g], q.x - gl.x, q.y - gl.y);
+            if (cone_ok && visible_points(ds, q.x, q.y, gl.x, gl.y)) {
+                const float2 gp = ds.gen_pos[g];
+                const double dx = __dsub_rn(qf.x, (double)gp.x), dy = __dsub_rn(qf.y, (double)gp.y);
+                key = __dadd_rn(ds.gen_cost[g], __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))));
+            }
+        }
+    }
+    int best = key < INFINITY ? g : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const int og = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ok < key || (ok == key && og >= 0 && (best < 0 || og < best))) {
+            key = ok;
+            best = og;
+        }
+    }
+    if (lane == 0) {
+        *out_par = best;
+        *out_dist = key;
+    }
+}
+
+void launch_query_exact(const DevScene &ds, cudaStream_t st, const int32_t *field_parent, int i, int j, int qx,
+                        int qy, double fx, double fy, int32_t *out_par, double *out_dist) {
+    k_query_exact<<<1, 32, 0, st>>>(ds, field_parent, i, j, make_int2(qx, qy), make_double2(fx, fy), out_par,
+                                    out_dist);
+}
+
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1) {
     const int tiles = ds.tiles_x * (tile_row1 - tile_row0);

@@ -400,3 +400,33 @@ def test_compute_captured_in_a_cuda_graph(spm, oracle_mod):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(p, p_ref) and torch.equal(d.view(torch.int32), d_ref.view(torch.int32))
+
+
+@pytest.mark.parametrize("which", ["maze", "polys"])
+def test_exact_point_query(spm, oracle_mod, which):
+    """spm_query_exact at arbitrary points: the neighbouring pixels' parents
+    evaluated at the point itself (Sec. 6) give the oracle's field there --
+    distance to FP32 rounding of the same FP64 key -- whenever the oracle's
+    parent is among them, and never a shorter distance than the oracle."""
+    scene = sg.maze(5, cells=8, N=512) if which == "maze" else sg.plain_polys(6, W=2048, N=512, n_polys=40)
+    s = spm.Scene(scene)
+    s.compute()
+    s.sync()
+    o = oracle_mod.Oracle(scene)
+    S = s.info()["lattice_scale"]
+    rng = np.random.default_rng(11)
+    W = scene.world[0]
+    lxy = rng.integers(1, W * S - 1, (400, 2))
+    od, op = o.points(lxy)
+    agree = 0
+    for (lx, ly), d_ref, p_ref in zip(lxy, od, op):
+        g, d = s.query_exact(lx / S, ly / S)
+        if not np.isfinite(d_ref):
+            continue
+        assert np.isfinite(d) or g == -1
+        if g == p_ref:
+            agree += 1
+            assert abs(d - d_ref) <= 1e-6 * max(d_ref, 1.0)
+        elif g >= 0:
+            assert d >= np.float32(d_ref) * (1 - 1e-6)  # another valid parent is never shorter
+    assert agree >= 0.97 * np.isfinite(od).sum()

@@ -417,3 +417,19 @@ def test_keys_brute_force_minimum_is_the_field(oracle_mod):
         assert np.allclose(kmin[fin], d[fin], rtol=0, atol=1e-9)
         kp = np.take_along_axis(k, np.where(p >= 0, p, 0)[..., None], axis=2)[..., 0]
         assert np.allclose(kp[fin], d[fin], rtol=0, atol=1e-9)
+
+
+def test_point_queries_at_pixel_centres_are_the_field(oracle_mod):
+    """The field at arbitrary lattice points (the exact point queries) agrees
+    with the per-pixel field where the point is a pixel centre."""
+    scene = sg.plain_polys(4, W=512, N=64, n_polys=8)
+    o = oracle_mod.Oracle(scene)
+    d, p, _, _ = o.field()
+    rng = np.random.default_rng(3)
+    ij = rng.integers(0, 64, (200, 2))
+    lxy = np.stack([o.pixel_lattice(i, j) for i, j in ij])
+    pd, pp = o.points(lxy)
+    fin = np.isfinite(d[ij[:, 1], ij[:, 0]])
+    assert np.array_equal(np.isfinite(pd), fin)
+    assert np.array_equal(pd[fin], d[ij[:, 1], ij[:, 0]][fin])
+    assert np.array_equal(pp[fin], p[ij[:, 1], ij[:, 0]][fin])
