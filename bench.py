@@ -46,6 +46,9 @@ KPIXELS_TRAFFIC = {"maze4096": 89_675_008}
 def workload(name: str):
     if name == "maze4096":
         return sg.maze(0), "maze 64x64 cells, 4096^2 px, 16384^2 world, 1 segment + 4 points"
+    if name == "dynamic4096":
+        return sg.maze(0), ("maze 64x64 cells, 4096^2 px, 16384^2 world, 1 segment + 4 points moving "
+                            "every frame, 100k agents")
     if name == "maze2048":
         return sg.maze(0, cells=32, N=2048), "maze 32x32 cells, 2048^2 px, 8192^2 world, 1 segment + 4 points"
     if name == "batched256":
@@ -203,15 +206,19 @@ def run_reference(args, cfg_desc, scene):
     Nx, Ny = scene.grid
     sample = (f"per step: oracle vertex phase + {args.ref_pixels} seeded pixels of the "
               f"{Nx}x{Ny} grid, extrapolated to the full grid")
+    metric, unit, ms_step = metric_for(Nx, Ny), UNIT, 1e3 * Nx * Ny / (value * 1e6)
+    if args.workload == "dynamic4096":  # one frame = one full map
+        metric, unit = "SPM frames/s with sources moving every frame, maze 4096^2", "frames/s"
+        value = value * 1e6 / (Nx * Ny)
     line = {
-        "impl": "reference", "metric": metric_for(Nx, Ny), "value": value, "unit": UNIT,
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * Nx * Ny / (value * 1e6), "higher_is_better": True,
+        "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "scene": cfg_desc, "grid": [Nx, Ny]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": unit, "cores": nthreads, "kind": "oracle",
                          "sample": sample},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -385,11 +392,15 @@ def run_differentiable(args, cfg_desc, scene):
     pts = np.asarray(scene.points, np.float32)
     segs = np.asarray(scene.segs, np.float32)
     h_out = torch.empty(1 + 2 * n_p + 4 * max(n_s, 1), dtype=torch.float32).pin_memory()
+    h_src = torch.tensor(np.concatenate([pts.reshape(-1), segs.reshape(-1)])).pin_memory()
+    d_src = torch.empty_like(h_src, device=dev)
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        spm.spm_scene_update_sources(s.handle, pts, segs)
+        d_src.copy_(h_src, non_blocking=True)
+        spm.spm_scene_update_sources_device(s.handle, stream, d_src[:2 * n_p] if n_p else None,
+                                            d_src[2 * n_p:] if n_s else None)
         step()
         spm.spm_agents_backward(s.handle, stream, gp, gs)
         h_out[:1].copy_(loss.reshape(1), non_blocking=True)
@@ -423,6 +434,138 @@ def run_differentiable(args, cfg_desc, scene):
     print(json.dumps(line), flush=True)
 
 
+def run_dynamic(args, cfg_desc, scene):
+    """Maps of moving sources (Sec. 6): every frame the maze's point sources
+    take a step of their seeded random walk and the exit segment slides, the
+    new coordinates are validated and committed on the device
+    (spm_scene_update_sources_device) and the map is recomputed. value =
+    frames/s from the CUDA-event time of (source update + compute) per frame,
+    L2 flushed between frames. e2e = frames/s of the wall-clock frame loop a
+    user runs: the frame's sources copied up from pinned host memory, update,
+    compute, 100k agents read their distance (spm_agents_forward) and the mean
+    comes back to the host; the same loop with host-side source updates and
+    one CUDA graph of all frames are reported beside it."""
+    import torch
+    import paper_1805_08500_gb300 as spm
+    world, rank, local = rank_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = spm.Scene(scene)
+    if args.culling == "autotune":
+        tuning = s.autotune(cache_key="maze4096")  # the same scene class as the static map
+    else:
+        spm.spm_scene_set_tuning(s.handle, {"auto": 0, "flood": 1, "scan": 2}[args.culling], 32)
+        tuning = dict(s.tuning(), source="fixed")
+    Nx, Ny = scene.grid
+    npx = Nx * Ny
+    F = args.warmup + args.steps
+    pts, segs = sg.maze_source_frames(scene, F, seed=1)
+    n_p, n_s = pts.shape[1], segs.shape[1]
+    P = torch.tensor(pts.reshape(F, -1), device=dev)
+    Q = torch.tensor(segs.reshape(F, -1), device=dev)
+    agents = torch.tensor(sg.maze_agents(scene, 100_000, seed=2), device=dev)
+    d_out, p_out = s.empty_outputs()
+    loss = torch.empty((), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    info = s.info()
+
+    for f in range(args.warmup):
+        spm.spm_scene_update_sources_device(s.handle, stream, P[f], Q[f])
+        s.compute(d_out, p_out, stream)
+    s.sync(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            f = args.warmup + k
+            flush.zero_()
+            ev[k][0].record(stream)
+            spm.spm_scene_update_sources_device(s.handle, stream, P[f], Q[f])
+            s.compute(d_out, p_out, stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    s.sync(stream)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    # wall-clock frame loops (no flush: frames follow each other as in an application)
+    h_pts = torch.tensor(pts.reshape(F, -1)).pin_memory()
+    h_segs = torch.tensor(segs.reshape(F, -1)).pin_memory()
+    h_loss = torch.zeros(F, dtype=torch.float32).pin_memory()
+    p_dev = torch.empty(2 * n_p, dtype=torch.float32, device=dev)
+    s_dev = torch.empty(4 * n_s, dtype=torch.float32, device=dev)
+
+    def frame(f, st):
+        p_dev.copy_(h_pts[f], non_blocking=True)
+        s_dev.copy_(h_segs[f], non_blocking=True)
+        spm.spm_scene_update_sources_device(s.handle, st, p_dev, s_dev)
+        spm.spm_compute(s.handle, st, d_out, p_out)
+        spm.spm_agents_forward(s.handle, st, agents, d_out, p_out, loss)
+        h_loss[f:f + 1].copy_(loss.reshape(1), non_blocking=True)
+
+    def loop(body):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        body()
+        torch.cuda.synchronize()
+        return F / (time.perf_counter() - t0)
+
+    frame(0, stream)
+    e2e_fps = loop(lambda: [frame(f, stream) for f in range(F)])
+    s.sync(stream)
+    device_losses = h_loss.clone()
+
+    def host_frames():
+        for f in range(F):
+            spm.spm_scene_update_sources(s.handle, pts[f], segs[f])
+            spm.spm_compute(s.handle, stream, d_out, p_out)
+            spm.spm_agents_forward(s.handle, stream, agents, d_out, p_out, loss)
+            h_loss[f:f + 1].copy_(loss.reshape(1), non_blocking=True)
+    host_fps = loop(host_frames)
+    s.sync(stream)
+    host_losses = h_loss.clone()
+
+    gst = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=gst):
+        for f in range(F):
+            frame(f, gst)
+    graph_fps = loop(g.replay)
+    s.sync(stream)
+    same = bool(torch.equal(device_losses, host_losses) and torch.equal(h_loss, host_losses))
+
+    line = {"metric": "SPM frames/s with sources moving every frame, maze 4096^2", "value": 1e3 / ms,
+            "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
+            "config": {"workload": "dynamic4096", "scene": cfg_desc, "grid": [Nx, Ny],
+                       "motion": "point sources: integer random walk (<= 6 units per axis per frame) in their "
+                                 "cells; exit segment: sideways walk within 3 units",
+                       "agents": int(agents.shape[0]), "frames": F,
+                       "l2": "flushed between timed frames (256 MiB write)", "tuning": tuning},
+            "mpixel_per_s": npx * 1e3 / ms / 1e6,
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_fps, "unit": "frames/s",
+                    "h2d_bytes_per_step": int(4 * (2 * n_p + 4 * n_s)), "d2h_bytes_per_step": 4},
+            "e2e_host_update_fps": host_fps, "e2e_cuda_graph_fps": graph_fps,
+            "losses_identical_across_loops": same,
+            "gpu_launches": (info["kernels_per_compute"] + 1) * args.steps}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build_oracle()
+        nthreads = oracle.default_threads()
+        moved = sg.Scene(scene.world, scene.grid, scene.polys, pts[-1].astype(np.float64),
+                         segs[-1].astype(np.float64))
+        rate, used = cpu_oracle_rate(moved, args.cpu_pixels, 4321, nthreads)
+        line["cpu_baseline"] = {
+            "value": rate * 1e6 / npx, "unit": "frames/s", "cores": nthreads, "kind": "oracle",
+            "sample": (f"one frame's sources: oracle vertex phase + {args.cpu_pixels} seeded pixels, "
+                       f"extrapolated to {Nx}x{Ny} ({used:.1f} s wall on {nthreads} threads)")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,7 +574,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maze4096",
                     choices=["maze4096", "maze2048", "polys1024", "rects256", "diff2048", "diff2048_grad",
-                             "batched256", "profiling1000"])
+                             "batched256", "profiling1000", "dynamic4096"])
     ap.add_argument("--cpu-pixels", type=int, default=3_000_000,
                     help="oracle pixel sample for the cpu_baseline leg")
     ap.add_argument("--ref-pixels", type=int, default=40_000,
@@ -454,6 +597,9 @@ def main():
         return
     if args.workload == "diff2048_grad":
         run_differentiable(args, cfg_desc, scene)
+        return
+    if args.workload == "dynamic4096":
+        run_dynamic(args, cfg_desc, scene)
         return
 
     import torch

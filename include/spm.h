@@ -95,6 +95,25 @@ void spm_scene_destroy(spm_scene *scene);
 spm_status spm_scene_update_sources(spm_scene *scene, const float *point_xy,
                                     const float *seg_xyxy);
 
+/* Moves the sources from DEVICE arrays, stream-ordered on `stream` (a
+ * cudaStream_t, NULL = legacy default stream): the dynamically changing maps
+ * of Sec. 6, where sources move every frame and the map is recomputed with no
+ * host round trip. point_xy_dev: 2 * n_points floats (x, y); seg_xyxy_dev:
+ * 4 * n_segments floats (ax, ay, bx, by), both world units, caller-owned,
+ * read by the kernel when it runs (keep them alive and unchanged until then);
+ * either may be NULL when its count is 0. A kernel snaps and validates them
+ * exactly as spm_scene_update_sources does and then commits all of them, or,
+ * when any source is invalid (non-finite, outside the world, not strictly
+ * outside every obstacle, a zero-length segment, a segment touching an
+ * obstacle), none: the scene keeps its previous sources and the next
+ * spm_scene_sync returns SPM_ERR_BAD_GEOMETRY. The next spm_compute on the
+ * same stream uses the new sources. Allocates nothing and may be captured in
+ * a CUDA graph. Returns SPM_ERR_INVALID_ARG for a null scene or a null array
+ * with a non-zero count, SPM_ERR_CUDA when the launch fails. */
+spm_status spm_scene_update_sources_device(spm_scene *scene, void *stream,
+                                           const float *point_xy_dev,
+                                           const float *seg_xyxy_dev);
+
 /* Computes the shortest-path map (Sec. 3: vertex costs relaxed to a fixpoint,
  * then every pixel takes the minimum over visible generators of
  * cost(g) + |p - g|, Procedures 1-4; segment interiors use the perpendicular

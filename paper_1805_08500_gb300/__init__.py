@@ -81,6 +81,7 @@ def load_library():
         "spm_scene_create": ([ctypes.POINTER(_Desc), ctypes.POINTER(P)], I32),
         "spm_scene_destroy": ([P], None),
         "spm_scene_update_sources": ([P, P, P], I32),
+        "spm_scene_update_sources_device": ([P, P, P, P], I32),
         "spm_compute": ([P, P, P, P], I32),
         "spm_compute_rows": ([P, P, I32, I32, P, P], I32),
         "spm_compute_host": ([P, P, P, P], I32),
@@ -176,6 +177,23 @@ def spm_scene_update_sources(handle, points, segs):
     _check(load_library().spm_scene_update_sources(
         handle, pts.ctypes.data if pts.size else None, sg.ctypes.data if sg.size else None),
         "spm_scene_update_sources", handle)
+
+
+def spm_scene_update_sources_device(handle, stream, points_dev, segs_dev):
+    """Move the sources from device buffers (float32, contiguous, on the
+    scene's device; None when the count is 0), stream-ordered."""
+    for t in (points_dev, segs_dev):
+        if t is not None and hasattr(t, "is_cuda"):
+            if not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous() or not t.is_floating_point():
+                raise ValueError("device sources must be contiguous float32 CUDA tensors")
+    pp = _ptr(points_dev) if points_dev is not None and _numel(points_dev) else None
+    sp = _ptr(segs_dev) if segs_dev is not None and _numel(segs_dev) else None
+    _check(load_library().spm_scene_update_sources_device(handle, _stream_handle(stream), pp, sp),
+           "spm_scene_update_sources_device", handle)
+
+
+def _numel(x):
+    return x.numel() if hasattr(x, "numel") else int(np.size(x))
 
 
 def spm_compute(handle, stream, dist, parent):
@@ -423,6 +441,11 @@ class Scene:
     def update_sources(self, points, segs):
         spm_scene_update_sources(self.handle, points, segs)
 
+    def update_sources_device(self, points, segs, stream=None):
+        """Move the sources from float32 CUDA tensors (n_points, 2) and
+        (n_segs, 4), stream-ordered; a rejected move surfaces at sync()."""
+        spm_scene_update_sources_device(self.handle, stream, points, segs)
+
     def autotune(self, stream=None, cache_key=None):
         """Pick the culling configuration: from the tuning cache when cache_key
         (a workload-class string) has an entry for this GPU, else by timing
@@ -477,7 +500,9 @@ def autotune_cached(scene: "Scene", stream=None, cache_key=None, path=TUNING_CAC
 def agent_loss(scene: "Scene", points, segs, agents):
     """Differentiable mean geodesic distance of agents (pixel indices, int32
     (n, 2) device tensor) w.r.t. the point sources (n_p, 2) and segment
-    endpoints (n_s, 4): forward and backward run in the library's kernels."""
+    endpoints (n_s, 4): forward and backward run in the library's kernels.
+    The sources move on the device (no host round trip); a move the library
+    rejects keeps the previous sources and is reported by scene.sync()."""
     return _AgentLoss.apply(points, segs, scene, agents)
 
 
@@ -487,13 +512,16 @@ def _make_autograd():
     class AgentLoss(torch.autograd.Function):
         @staticmethod
         def forward(ctx, points, segs, scene, agents):
-            spm_scene_update_sources(scene.handle, points.detach().float().cpu().numpy(),
-                                     segs.detach().float().cpu().numpy())
+            # the sources move on the device: no host round trip in the step
+            pts = points.detach().to(scene.device, torch.float32).contiguous()
+            sgs = segs.detach().to(scene.device, torch.float32).contiguous()
+            spm_scene_update_sources_device(scene.handle, None, pts.reshape(-1) if pts.numel() else None,
+                                            sgs.reshape(-1) if sgs.numel() else None)
             dist, parent = scene.compute()
             loss = torch.empty((), dtype=torch.float32, device=scene.device)
             spm_agents_forward(scene.handle, None, agents, dist, parent, loss)
             ctx.scene = scene
-            ctx.keep = (dist, parent, agents)
+            ctx.keep = (dist, parent, agents, pts, sgs)
             ctx.shapes = (points.shape, segs.shape)
             ctx.devices = (points.device, segs.device)
             return loss

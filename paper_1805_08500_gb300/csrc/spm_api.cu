@@ -45,6 +45,9 @@ struct spm_scene {
     // side stream of the geometric flood (flood mode 3), with fork/join events
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // the device holds sources moved by spm_scene_update_sources_device that
+    // the host copy in hs has not seen yet
+    bool host_src_stale = false;
 };
 
 namespace {
@@ -125,6 +128,30 @@ spm_status upload_sources(spm_scene *s) {
                          cudaMemcpyHostToDevice) == cudaSuccess;
     }
     return ok ? SPM_OK : set_err(s, SPM_ERR_CUDA, "source upload failed");
+}
+
+// Brings the host copy of the Source entries up to date after device-side
+// updates (synchronises the device).
+spm_status refresh_host_sources(spm_scene *s) {
+    if (!s->host_src_stale) return SPM_OK;
+    spm::HostScene &hs = s->hs;
+    const spm::DevScene &ds = s->ds;
+    const int np = (int)hs.points.size() / 2, ns = (int)hs.segs.size() / 4;
+    if (cudaDeviceSynchronize() != cudaSuccess) return set_err(s, SPM_ERR_CUDA, "synchronisation failed");
+    bool ok = true;
+    ok &= cudaMemcpy(hs.gen_lat.data(), ds.gen_lat, sizeof(int32_t) * 2 * hs.n_src, cudaMemcpyDeviceToHost) ==
+          cudaSuccess;
+    ok &= cudaMemcpy(hs.gen_pos.data(), ds.gen_pos, sizeof(float) * 2 * hs.n_src, cudaMemcpyDeviceToHost) ==
+          cudaSuccess;
+    if (ns) {
+        ok &= cudaMemcpy(hs.seg_lat.data(), ds.seg_lat, sizeof(int32_t) * 4 * ns, cudaMemcpyDeviceToHost) ==
+              cudaSuccess;
+        ok &= cudaMemcpy(hs.segs.data(), ds.seg_pos, sizeof(float) * 4 * ns, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    if (!ok) return set_err(s, SPM_ERR_CUDA, "source table copy failed");
+    for (int i = 0; i < 2 * np; ++i) hs.points[i] = hs.gen_pos[i];
+    s->host_src_stale = false;
+    return SPM_OK;
 }
 
 }  // namespace
@@ -323,7 +350,21 @@ spm_status spm_scene_update_sources(spm_scene *s, const float *pts, const float 
     st = spm::update_sources(s->hs, pts, segs, err);
     if (st != SPM_OK) return set_err(s, st, err);
     if (cudaDeviceSynchronize() != cudaSuccess) return set_err(s, SPM_ERR_CUDA, "synchronisation failed");
+    s->host_src_stale = false;
     return upload_sources(s);
+}
+
+spm_status spm_scene_update_sources_device(spm_scene *s, void *stream, const float *pts_dev,
+                                           const float *segs_dev) {
+    if (!s) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    const int np = (int)s->hs.points.size() / 2, ns = (int)s->hs.segs.size() / 4;
+    if ((np > 0 && !pts_dev) || (ns > 0 && !segs_dev)) return set_err(s, SPM_ERR_INVALID_ARG, "null source array");
+    spm::launch_update_sources(s->ds, static_cast<cudaStream_t>(stream), pts_dev, segs_dev);
+    if (cudaPeekAtLastError() != cudaSuccess) return set_err(s, SPM_ERR_CUDA, "source update launch failed");
+    s->host_src_stale = true;
+    return SPM_OK;
 }
 
 spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent, int tile_row0, int tile_row1) {
@@ -395,6 +436,9 @@ spm_status spm_scene_sync(spm_scene *s, void *stream) {
     if (bits & spm::kStEdgeOverflow) return set_err(s, SPM_ERR_CAPACITY, "visibility graph exceeds edge capacity");
     if (bits & spm::kStNotConverged) return set_err(s, SPM_ERR_NOT_CONVERGED, "vertex fixpoint hit its round cap");
     if (bits & spm::kStTimeout) return set_err(s, SPM_ERR_TIMEOUT, "device wait gave up");
+    if (bits & spm::kStBadSource)
+        return set_err(s, SPM_ERR_BAD_GEOMETRY, "device source update rejected: a source is outside the world, "
+                                                "not strictly outside every obstacle, or a zero-length segment");
     if (bits) return set_err(s, SPM_ERR_CUDA, "device reported bad input");
     return SPM_OK;
 }
@@ -644,6 +688,8 @@ spm_status spm_extract_path(spm_scene *s, float x, float y, float *out_xy, int32
     float d;
     spm_status st = spm_query_parent(s, x, y, &g, &d);
     if (st != SPM_OK) return st;
+    st = refresh_host_sources(s);
+    if (st != SPM_OK) return st;
     std::vector<int32_t> par(s->hs.n_gen);
     if (cudaMemcpy(par.data(), s->ds.gen_par, sizeof(int32_t) * s->hs.n_gen, cudaMemcpyDeviceToHost) != cudaSuccess)
         return set_err(s, SPM_ERR_CUDA, "parent table copy failed");
@@ -680,6 +726,8 @@ spm_status spm_extract_path(spm_scene *s, float x, float y, float *out_xy, int32
 spm_status spm_scene_generators(spm_scene *s, int32_t *kind, int32_t *lattice_xy, double *cost, int32_t *parent) {
     if (!s) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene");
     spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    st = refresh_host_sources(s);
     if (st != SPM_OK) return st;
     const int n = s->hs.n_gen;
     if (kind) std::memcpy(kind, s->hs.gen_kind.data(), sizeof(int32_t) * n);

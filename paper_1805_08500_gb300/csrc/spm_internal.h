@@ -31,6 +31,7 @@ enum StatusBits : uint32_t {
     kStEdgeOverflow = 2u,
     kStTimeout = 4u,
     kStBadInput = 8u,
+    kStBadSource = 16u,  // a device-side source update was rejected (table unchanged)
 };
 
 // Host-side prepared scene (lattice integers, generator table, bins).
@@ -179,6 +180,8 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1);
 void launch_flood(const DevScene &ds, cudaStream_t st);
+// validates and commits new source coordinates (device arrays) on `st`
+void launch_update_sources(const DevScene &ds, cudaStream_t st, const float *pts, const float *segs);
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_flood_batched(const BatchDev &b, cudaStream_t st);

@@ -172,6 +172,12 @@ spm_status snap_sources(HostScene &hs, const float *pts, const float *segs, std:
         if (!std::isfinite(v)) return fail(err, SPM_ERR_BAD_GEOMETRY, "non-finite point source");
     for (float v : hs.segs)
         if (!std::isfinite(v)) return fail(err, SPM_ERR_BAD_GEOMETRY, "non-finite segment source");
+    for (float v : hs.points)
+        if (std::fabs(std::nearbyint((double)v * (double)hs.S)) > 1073741824.0)
+            return fail(err, SPM_ERR_BAD_GEOMETRY, "point source outside the world");
+    for (float v : hs.segs)
+        if (std::fabs(std::nearbyint((double)v * (double)hs.S)) > 1073741824.0)
+            return fail(err, SPM_ERR_BAD_GEOMETRY, "segment endpoint outside the world");
     auto snap = [&](float v) { return (int32_t)std::nearbyint((double)v * (double)hs.S); };
     int g = 0;
     for (int i = 0; i < np; ++i, ++g) {

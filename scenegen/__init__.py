@@ -18,6 +18,8 @@ from .scenes import (  # noqa: F401
     single_square,
     profiling_map,
     profiling_sources,
+    maze_source_frames,
+    maze_agents,
     load_scene,
     save_scene,
 )

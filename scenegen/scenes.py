@@ -497,3 +497,55 @@ def profiling_sources(k: int = 8, n: int = 100, W: int = 1000, seed: int = 0) ->
             continue
         out.append((float(x), float(y)))
     return np.array(out)
+
+
+def maze_source_frames(scene: Scene, frames: int, seed: int = 0, step: int = 6):
+    """Seeded per-frame sources for a maze() scene (maps of moving sources):
+    frame 0 is the scene's own sources; after it every point source takes an
+    integer random walk (each axis moves by a seeded step in [-step, step])
+    clamped to its cell's free interior, 8 units clear of the walls, and the
+    exit segment slides sideways by a clamped walk of at most 3 units (its
+    ends stay 9 units clear of the side walls). Integer arithmetic only, so
+    both machines draw the same frames. Returns float32 arrays points
+    (frames, n_points, 2) and segs (frames, n_segs, 4)."""
+    cell, thick = int(scene.meta["cell"]), int(scene.meta["thick"])
+    ht = thick // 2
+    rng = SplitMix64(seed * 0x1000193 + 977)
+    p0 = np.asarray(scene.points, np.float64).reshape(-1, 2)
+    s0 = np.asarray(scene.segs, np.float64).reshape(-1, 4)
+    pts = np.zeros((frames, len(p0), 2), np.float32)
+    segs = np.zeros((frames, len(s0), 4), np.float32)
+    cur = [[int(x), int(y)] for x, y in p0]
+    lo_hi = []
+    for x, y in cur:
+        cx, cy = x // cell, y // cell
+        lo_hi.append((cx * cell + ht + 8, (cx + 1) * cell - ht - 8, cy * cell + ht + 8, (cy + 1) * cell - ht - 8))
+    shift = 0
+    for f in range(frames):
+        if f > 0:
+            for i, (x0, x1, y0, y1) in enumerate(lo_hi):
+                cur[i][0] = min(x1, max(x0, cur[i][0] + rng.randint(-step, step)))
+                cur[i][1] = min(y1, max(y0, cur[i][1] + rng.randint(-step, step)))
+            shift = min(3, max(-3, shift + rng.randint(-1, 1)))
+        for i in range(len(cur)):
+            pts[f, i] = cur[i]
+        for i in range(len(s0)):
+            segs[f, i] = (s0[i, 0] + shift, s0[i, 1], s0[i, 2] + shift, s0[i, 3])
+    return pts, segs
+
+
+def maze_agents(scene: Scene, n: int, seed: int = 0) -> np.ndarray:
+    """n seeded agent pixels (column, row) for a maze() scene: uniform in the
+    free interior of uniformly drawn cells, 16 units clear of the wall centre
+    lines, so every agent pixel is free and reached."""
+    cells, cell, thick = (int(scene.meta[k]) for k in ("cells", "cell", "thick"))
+    ht = thick // 2
+    rng = SplitMix64(seed * 0x1000193 + 1301)
+    W, N = scene.world[0], scene.grid[0]
+    out = np.zeros((n, 2), np.int32)
+    for k in range(n):
+        cx, cy = rng.randint(0, cells - 1), rng.randint(0, cells - 1)
+        x = rng.randint(cx * cell + ht + 16, (cx + 1) * cell - ht - 16)
+        y = rng.randint(cy * cell + ht + 16, (cy + 1) * cell - ht - 16)
+        out[k] = (x * N // W, y * N // W)
+    return out

@@ -295,6 +295,130 @@ def test_update_sources(spm, oracle_mod):
     check_parity(moved, d.cpu().numpy(), p.cpu().numpy(), rd, rp, rd2, "moved", rp2)
 
 
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a, np.float32), device="cuda").contiguous()
+
+
+def test_device_source_update_frames(spm, oracle_mod):
+    """Moving sources (Sec. 6, dynamic maps): frames moved in from device
+    buffers give bit for bit the map of the same sources moved in from the
+    host, and the oracle's map of a scene built with them; the host-side
+    generator table follows the device."""
+    scene = sg.maze(7, cells=16, N=512)
+    pts, segs = sg.maze_source_frames(scene, 6, seed=3)
+    s_dev, s_host = spm.Scene(scene), spm.Scene(scene)
+    for f in range(len(pts)):
+        s_dev.update_sources_device(_dev(pts[f]), _dev(segs[f].reshape(-1)))
+        d1, p1 = s_dev.compute()
+        s_host.update_sources(pts[f], segs[f])
+        d2, p2 = s_host.compute()
+        s_dev.sync()
+        s_host.sync()
+        assert torch.equal(p1, p2) and torch.equal(d1.view(torch.int32), d2.view(torch.int32)), f"frame {f}"
+        if f in (1, len(pts) - 1):
+            moved = sg.Scene(scene.world, scene.grid, scene.polys, pts[f].astype(np.float64),
+                             segs[f].astype(np.float64))
+            o = oracle_mod.Oracle(moved)
+            rd, rp, rd2, rp2 = o.field()
+            check_parity(moved, d1.cpu().numpy(), p1.cpu().numpy(), rd, rp, rd2, f"frame {f}", rp2, oracle=o)
+    kind, lat, _, _ = s_dev.generators()
+    S = s_dev.info()["lattice_scale"]
+    n_p = len(pts[-1])
+    assert np.array_equal(lat[:n_p], np.rint(pts[-1].astype(np.float64) * S).astype(np.int32))
+    assert np.array_equal(lat[n_p], np.rint(segs[-1][0, :2].astype(np.float64) * S).astype(np.int32))
+
+
+def _crossing_wall_segment(scene):
+    """A segment between two free cell interiors that crosses an inner wall."""
+    cell = scene.meta["cell"]
+    W = scene.world[0]
+    for P in scene.polys:
+        x0, y0 = P.min(0)
+        x1, y1 = P.max(0)
+        if x1 - x0 == scene.meta["thick"] and x0 > 0 and x1 < W:
+            xm, ym = (x0 + x1) / 2, y0 + 8 + cell / 2
+            return (xm - 50.0, ym, xm + 50.0, ym)
+    raise AssertionError("maze without an inner vertical wall")
+
+
+def test_device_source_update_rejects_bad_sources(spm):
+    """A device-side move is all or nothing: any invalid source (inside or on
+    an obstacle, outside the world, non-finite, a zero-length segment, a
+    segment crossing a wall) leaves every source where it was, the next sync
+    reports SPM_ERR_BAD_GEOMETRY, and the host-side update rejects the same
+    input."""
+    scene = sg.maze(8, cells=8, N=256)
+    s = spm.Scene(scene)
+    d_ref, p_ref = s.compute()
+    s.sync()
+    wall = scene.polys[len(scene.polys) // 2]
+    pts0 = np.asarray(scene.points, np.float32)
+    seg0 = np.asarray(scene.segs, np.float32)
+    bad_points = [wall.mean(0), wall[0], (-1.0, 5.0), (np.nan, 30.0), (1e30, 1e30)]
+    cases = []
+    for q in bad_points:
+        p = pts0.copy()
+        p[-1] = q
+        cases.append((p, seg0))
+    for sgm in [(140.0, 140.0, 140.0, 140.0), _crossing_wall_segment(scene)]:
+        sg2 = seg0.copy()
+        sg2[0] = sgm
+        cases.append((pts0, sg2))
+    for k, (p, sgs) in enumerate(cases):
+        moved_ok = pts0.copy()
+        moved_ok[0] += (2.0, 2.0)  # a valid move in the same call must not be applied either
+        if k < len(bad_points):
+            p = p.copy()
+            p[0] = moved_ok[0]
+        s.update_sources_device(_dev(p), _dev(sgs.reshape(-1)))
+        d, pp = s.compute()
+        with pytest.raises(spm.SpmError) as e:
+            s.sync()
+        assert e.value.status == spm.SPM_ERR_BAD_GEOMETRY, f"case {k}"
+        assert torch.equal(pp, p_ref) and torch.equal(d.view(torch.int32), d_ref.view(torch.int32)), f"case {k}"
+        with pytest.raises(spm.SpmError) as e:
+            s.update_sources(p, sgs)
+        assert e.value.status == spm.SPM_ERR_BAD_GEOMETRY, f"host case {k}"
+    s.sync()
+
+
+def test_moving_source_frames_in_one_cuda_graph(spm):
+    """A frame loop -- move the sources from a device buffer, recompute --
+    captured once in a CUDA graph: the replay reproduces every frame of the
+    eager loop bit for bit (the geometric flood on its side stream and the
+    depth maps included)."""
+    scene = sg.maze(9, cells=12, N=768)
+    F = 4
+    pts, segs = sg.maze_source_frames(scene, F, seed=5)
+    s = spm.Scene(scene)
+    spm.spm_scene_set_tuning(s.handle, 3, 32, 32, 1)
+    P = _dev(pts.reshape(F, -1))
+    Q = _dev(segs.reshape(F, -1))
+    ref = []
+    for f in range(F):
+        s.update_sources_device(P[f], Q[f])
+        d, p = s.compute()
+        s.sync()
+        ref.append((d, p))
+    outs = [s.empty_outputs() for _ in range(F)]
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        for f in range(F):
+            spm.spm_scene_update_sources_device(s.handle, st, P[f], Q[f])
+            spm.spm_compute(s.handle, st, outs[f][0], outs[f][1])
+    s.update_sources(pts[0], segs[0])
+    for d, p in outs:
+        d.fill_(0.0)
+        p.fill_(-5)
+    g.replay()
+    torch.cuda.synchronize()
+    s.sync()
+    for f in range(F):
+        assert torch.equal(outs[f][1], ref[f][1]), f"frame {f}"
+        assert torch.equal(outs[f][0].view(torch.int32), ref[f][0].view(torch.int32)), f"frame {f}"
+
+
 # ---------------------------------------------------------------------------
 # queries
 # ---------------------------------------------------------------------------
@@ -320,18 +444,21 @@ def test_query_and_extract_path(spm, oracle_mod):
 # differentiable form
 # ---------------------------------------------------------------------------
 
-def test_agent_gradient_matches_oracle(spm, oracle_mod):
+@pytest.mark.parametrize("src_device", ["cpu", "cuda"])
+def test_agent_gradient_matches_oracle(spm, oracle_mod, src_device):
     scene = sg.differentiable(1, W=1024, N=256, n_polys=20, n_agents=3000)
     o = oracle_mod.Oracle(scene)
     d, _, _, _ = o.pixels(scene.agents)
     agents = scene.agents[np.isfinite(d)]
     loss_ref, gp_ref, gs_ref = o.agent_loss_and_grad(agents)
     s = spm.Scene(scene)
-    pts = torch.tensor(scene.points, dtype=torch.float32, requires_grad=True)
-    segs = torch.tensor(scene.segs, dtype=torch.float32, requires_grad=True)
+    pts = torch.tensor(scene.points, dtype=torch.float32, device=src_device, requires_grad=True)
+    segs = torch.tensor(scene.segs, dtype=torch.float32, device=src_device, requires_grad=True)
     ag = torch.tensor(agents, dtype=torch.int32, device="cuda")
     loss = spm.agent_loss(s, pts, segs, ag)
     loss.backward()
+    s.sync()
+    assert pts.grad.device.type == src_device and segs.grad.device.type == src_device
     assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
     np.testing.assert_allclose(pts.grad.cpu().numpy(), gp_ref, atol=1e-4)
     np.testing.assert_allclose(segs.grad.cpu().numpy(), gs_ref, atol=1e-4)
