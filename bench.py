@@ -329,8 +329,24 @@ def run_profiling(args):
             torch.cuda.synchronize()
             s.sync(stream)
             ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            # A/B: the paper's generator-sequential schedule on the same maps
+            # and sources (first n_seq sources), same outputs
+            n_seq = 10
+            ev_seq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(n_seq)]
+            spm.spm_scene_update_sources(s.handle, srcs[0:1].astype(np.float32), empty)
+            s.compute_sequential(d, p, stream)  # warm-up
+            for i in range(n_seq):
+                spm.spm_scene_update_sources(s.handle, srcs[i:i + 1].astype(np.float32), empty)
+                ev_seq[i][0].record(stream)
+                s.compute_sequential(d, p, stream)
+                ev_seq[i][1].record(stream)
+            torch.cuda.synchronize()
+            s.sync(stream)
+            seq_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_seq]))
             P = k * k
             rows.append({"P": P, "V": 4 * P, "ms": ms, "mpixel_per_s": 1.0e6 / (ms * 1e-3) / 1e6,
+                         "sequential_ms": seq_ms, "culled_speedup_over_sequential": seq_ms / ms,
                          "paper_gtx970_ms": 1e3 * PAPER_PROFILING_S[P], "tuning": tuning})
     ref = next(r for r in rows if r["P"] == 64)
     line = {"metric": "SPM ms per map, Profiling3 (64 squares), 1000^2, one source", "value": ref["ms"],
@@ -342,7 +358,9 @@ def run_profiling(args):
                        "and grid, one seeded free point source per compute, mean of 100 sources",
                        "l2": "inputs resident; no flush (the paper times back-to-back frames)"},
             "maps": rows, "clocks": clk.summary(),
-            "note": "vs_baseline divides by the paper's GTX 970 OpenGL time (Table 1): context, not a target"}
+            "note": "vs_baseline divides by the paper's GTX 970 OpenGL time (Table 1): context, not a target; "
+                    "sequential_ms = the paper's generator-sequential schedule (spm_compute_sequential) on "
+                    "this GPU, mean of the first 10 sources"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -702,6 +720,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pts.nbytes + segs.nbytes),
                 "d2h_bytes_per_step": int(8 * npx)},
         "gpu_launches": launches_per_step * args.steps,
+        "step_ms_stats": {"median": float(np.median(step_ms)), "p10": float(np.percentile(step_ms, 10)),
+                          "p90": float(np.percentile(step_ms, 90)), "rank": rank},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -712,6 +732,11 @@ def main():
             "value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": (f"oracle vertex phase + {args.cpu_pixels} seeded pixels, extrapolated "
                        f"to {Nx}x{Ny} ({used:.1f} s wall on {nthreads} threads)")}
+        if npx <= 65536:  # a small grid: the whole map on one host thread as well
+            t0 = time.perf_counter()
+            oracle.Oracle(scene, nthreads=1).field()
+            line["cpu_baseline"]["single_thread_full_map"] = {
+                "value": npx / (time.perf_counter() - t0) / 1e6, "unit": UNIT, "cores": 1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

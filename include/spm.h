@@ -136,6 +136,24 @@ spm_status spm_compute(spm_scene *scene, void *stream, float *dist_dev,
 spm_status spm_compute_rows(spm_scene *scene, void *stream, int32_t row0, int32_t row1,
                             float *dist_dev, int32_t *parent_dev);
 
+/* The same map by the paper's own schedule (Sec. 3.1, Procedures 1-4): one
+ * generator at a time, in order of cost, over every pixel -- the search for
+ * the least-cost unexpanded generator (Procedure 1), the update of the
+ * obstacle vertices it sees (Procedure 4) and a depth-tested pass over all
+ * pixels with exact visibility in place of the shadow stencil (Procedures
+ * 2-3), in one cooperative kernel with a grid barrier per generator. An A/B
+ * baseline for spm_compute: like the paper it has no shadow cones and no
+ * visibility-graph tangency filter, so distances agree with spm_compute to
+ * FP32 rounding and parents agree except at (near-)ties. dist_dev /
+ * parent_dev: caller-owned device buffers as for spm_compute (they also
+ * serve as the depth buffer). Uses the scene's vertex-phase scratch, so do
+ * not run it concurrently with another compute of the same scene; leaves
+ * the generator table of the last spm_compute (and so the queries)
+ * untouched. Asynchronous; allocates nothing. SPM_ERR_CAPACITY above 65536
+ * generators, SPM_ERR_CUDA when the cooperative launch fails. */
+spm_status spm_compute_sequential(spm_scene *scene, void *stream, float *dist_dev,
+                                  int32_t *parent_dev);
+
 /* spm_compute on HOST buffers: copies the outputs back before returning
  * (synchronous on `stream`). For callers that keep the field on the host. */
 spm_status spm_compute_host(spm_scene *scene, void *stream, float *dist_host,

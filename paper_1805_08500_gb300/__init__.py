@@ -84,6 +84,7 @@ def load_library():
         "spm_scene_update_sources_device": ([P, P, P, P], I32),
         "spm_compute": ([P, P, P, P], I32),
         "spm_compute_rows": ([P, P, I32, I32, P, P], I32),
+        "spm_compute_sequential": ([P, P, P, P], I32),
         "spm_compute_host": ([P, P, P, P], I32),
         "spm_compute_batched": ([P, I32, P, P, P], I32),
         "spm_batch_create": ([P, I32, P, P, P], I32),
@@ -199,6 +200,11 @@ def _numel(x):
 def spm_compute(handle, stream, dist, parent):
     _check(load_library().spm_compute(handle, _stream_handle(stream), _ptr(dist), _ptr(parent)),
            "spm_compute", handle)
+
+
+def spm_compute_sequential(handle, stream, dist, parent):
+    _check(load_library().spm_compute_sequential(handle, _stream_handle(stream), _ptr(dist), _ptr(parent)),
+           "spm_compute_sequential", handle)
 
 
 def spm_compute_rows(handle, stream, row0, row1, dist, parent):
@@ -427,6 +433,13 @@ class Scene:
         if dist is None or parent is None:
             dist, parent = self.empty_outputs()
         spm_compute(self.handle, stream, dist, parent)
+        return dist, parent
+
+    def compute_sequential(self, dist=None, parent=None, stream=None):
+        """The map by the paper's generator-sequential schedule (A/B baseline)."""
+        if dist is None or parent is None:
+            dist, parent = self.empty_outputs()
+        spm_compute_sequential(self.handle, stream, dist, parent)
         return dist, parent
 
     def sync(self, stream=None):

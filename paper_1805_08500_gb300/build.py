@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspm_gb300.so")
-SOURCES = ["spm_prep.cpp", "spm_vertex.cu", "spm_flood.cu", "spm_pixel.cu", "spm_grad.cu", "spm_sources.cu", "spm_api.cu"]
+SOURCES = ["spm_prep.cpp", "spm_vertex.cu", "spm_flood.cu", "spm_pixel.cu", "spm_grad.cu", "spm_sources.cu", "spm_sequential.cu", "spm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -48,6 +48,7 @@ struct spm_scene {
     // the device holds sources moved by spm_scene_update_sources_device that
     // the host copy in hs has not seen yet
     bool host_src_stale = false;
+    int seq_blocks = 0;  // co-resident CTAs of the sequential kernel
 };
 
 namespace {
@@ -440,6 +441,17 @@ spm_status spm_scene_sync(spm_scene *s, void *stream) {
         return set_err(s, SPM_ERR_BAD_GEOMETRY, "device source update rejected: a source is outside the world, "
                                                 "not strictly outside every obstacle, or a zero-length segment");
     if (bits) return set_err(s, SPM_ERR_CUDA, "device reported bad input");
+    return SPM_OK;
+}
+
+spm_status spm_compute_sequential(spm_scene *s, void *stream, float *dist, int32_t *parent) {
+    if (!s || !dist || !parent) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
+    spm_status st = check_device(s);
+    if (st != SPM_OK) return st;
+    if (s->hs.n_gen > spm::kSeqMaxGen) return set_err(s, SPM_ERR_CAPACITY, "more generators than the sequential kernel takes");
+    if (!s->seq_blocks) s->seq_blocks = spm::sequential_grid_blocks();
+    if (spm::launch_sequential(s->ds, static_cast<cudaStream_t>(stream), dist, parent, s->seq_blocks) != cudaSuccess)
+        return set_err(s, SPM_ERR_CUDA, "sequential kernel launch failed");
     return SPM_OK;
 }
 

@@ -21,6 +21,7 @@ constexpr int kCandCap = 1024;       // candidate generators per batch (smem)
 constexpr int kBlockCap = 96;        // blocker polygons per chunk (smem)
 constexpr int kDedupBits = 8192;     // polygon-id dedup bitmap (smem)
 constexpr int kMaxRounds = 1 << 20;  // hard cap on vertex-fixpoint rounds
+constexpr int kSeqMaxGen = 1 << 16;  // generators the sequential (paper-schedule) kernel takes
 
 enum GenKind : int32_t { kPoint = 0, kSegA = 1, kSegB = 2, kSegI = 3, kVert = 4 };
 enum ConeType : int32_t { kConeNone = 0, kConeWedge = 1, kConeRay = 2, kConeEmpty = 3 };
@@ -180,6 +181,9 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1);
 void launch_flood(const DevScene &ds, cudaStream_t st);
+// the paper's generator-sequential schedule over the whole map (cooperative launch of `blocks` CTAs)
+cudaError_t launch_sequential(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int blocks);
+int sequential_grid_blocks();
 // validates and commits new source coordinates (device arrays) on `st`
 void launch_update_sources(const DevScene &ds, cudaStream_t st, const float *pts, const float *segs);
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);

@@ -419,6 +419,32 @@ def test_moving_source_frames_in_one_cuda_graph(spm):
         assert torch.equal(outs[f][0].view(torch.int32), ref[f][0].view(torch.int32)), f"frame {f}"
 
 
+@pytest.mark.parametrize("which", ["tiny", "rects", "profiling", "maze", "polys"])
+def test_sequential_schedule(spm, oracle_mod, which):
+    """The paper's own schedule (Procedures 1-4: one generator at a time in
+    order of cost, every pixel depth-tested) on the GPU: the oracle's
+    unrestricted minimum (no shadow cones, as in the paper) pixel for pixel,
+    and the distances of spm_compute to FP32 rounding."""
+    scene = {"tiny": lambda: sg.tiny(2, n_segs=1),
+             "rects": lambda: sg.plain_rects(1),
+             "profiling": lambda: sg.profiling_map(8, W=400, N=400),
+             "maze": lambda: sg.maze(3, cells=8, N=256),
+             "polys": lambda: sg.plain_polys(4, W=2048, N=256, n_polys=40)}[which]()
+    s = spm.Scene(scene)
+    d, p = s.compute_sequential()
+    d_ref, _ = s.compute()
+    s.sync()
+    gd, gp = d.cpu().numpy(), p.cpu().numpy()
+    o = oracle_mod.Oracle(scene, use_cone=False)
+    rd, rp, rd2, rp2 = o.field()
+    check_parity(scene, gd, gp, rd, rp, rd2, f"sequential {which}", rp2, oracle=o)
+    cd = d_ref.cpu().numpy()
+    fin = np.isfinite(cd)
+    assert np.array_equal(np.isfinite(gd), fin)
+    h = scene.world[0] / scene.grid[0]
+    assert np.all(np.abs(gd[fin].astype(np.float64) - cd[fin]) <= 1e-5 * np.maximum(cd[fin], h))
+
+
 # ---------------------------------------------------------------------------
 # queries
 # ---------------------------------------------------------------------------
