@@ -301,6 +301,9 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         }
         ds.flood_counts = dalloc<int32_t>(s, 4);
     }
+    ds.free_words = (hs.Nx + 31) / 32;
+    uint32_t *free_bits = dalloc<uint32_t>(s, (size_t)hs.Ny * ds.free_words);
+    ds.free_bits = free_bits;
     ds.sssp_blocks = spm::sssp_grid_blocks();
     ds.solo_smem = spm::solo_smem_bytes();
     for (void *p : s->allocs) ok &= p != nullptr;
@@ -312,6 +315,8 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     }
     cudaMemset(ds.status, 0, sizeof(uint32_t));
     cudaMemset(ds.stats, 0, sizeof(int32_t) * 4);
+    spm::launch_free_mask(ds, nullptr, free_bits);
+    if (cudaPeekAtLastError() != cudaSuccess) ok = false;
     for (cudaEvent_t &e : s->ev)
         if (cudaEventCreate(&e) != cudaSuccess) ok = false;
     if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||

@@ -87,6 +87,8 @@ struct DevScene {
     int32_t bin_x0, bin_y0, bin_size, bin_nx, bin_ny;
     const int32_t *bin_start, *bin_items;
     const BinRec *bin_recs;            // parallel to bin_items
+    const uint32_t *free_bits;         // free-space mask of pixel centres, free_words words per grid row
+    int32_t free_words;
     // generators (static part)
     const int32_t *gen_kind;
     const int2 *gen_lat;
@@ -181,6 +183,8 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1);
 void launch_flood(const DevScene &ds, cudaStream_t st);
+// free-space mask of the pixel centres (once per scene)
+void launch_free_mask(const DevScene &ds, cudaStream_t st, uint32_t *bits);
 // the paper's generator-sequential schedule over the whole map (cooperative launch of `blocks` CTAs)
 cudaError_t launch_sequential(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int blocks);
 int sequential_grid_blocks();

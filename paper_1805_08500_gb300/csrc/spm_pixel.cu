@@ -303,28 +303,13 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
         key[k] = kUnset;
         if (i < ds.Nx && j < ds.Ny) live |= 1u << k;
     }
-    // free space: not in the open interior of any polygon
+    // free space: not in the open interior of any polygon (the scene's
+    // free-space mask; the PX pixels of a thread share one word)
+    if (j < ds.Ny) {
+        const uint32_t fw = __ldg(ds.free_bits + (size_t)j * ds.free_words + ((i0 + c4) >> 5));
 #pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        if (!(live & (1u << k))) continue;
-        int bx = (px[k] - ds.bin_x0) / ds.bin_size, by = (py - ds.bin_y0) / ds.bin_size;
-        if (bx < 0 || by < 0 || bx >= ds.bin_nx || by >= ds.bin_ny) continue;
-        const int bin = by * ds.bin_nx + bx;
-        for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
-            const BinRec rec = ds.bin_recs[it];
-            const int4 b4 = rec.box;
-            if (px[k] <= b4.x || px[k] >= b4.z || py <= b4.y || py >= b4.w) continue;
-            const int b = rec.voff, m = rec.m;
-            bool inside = true;
-            for (int e = 0; e < m && inside; ++e) {
-                const int2 a = ds.poly_v[b + e], c = ds.poly_v[b + (e + 1 == m ? 0 : e + 1)];
-                inside = orient32(a.x, a.y, c.x, c.y, px[k], py) > 0;
-            }
-            if (inside) {
-                live &= ~(1u << k);
-                break;
-            }
-        }
+        for (int k = 0; k < PX; ++k)
+            if (!((fw >> ((i0 + c4 + k) & 31)) & 1u)) live &= ~(1u << k);
     }
     const int ni = min(T, ds.Nx - i0), nj = min(T, ds.Ny - j0);
     const int4 box = make_int4(pitch_x * i0 + pitch_x / 2, pitch_y * j0 + pitch_y / 2,
@@ -686,6 +671,50 @@ void launch_query_exact(const DevScene &ds, cudaStream_t st, const int32_t *fiel
                         int qy, double fx, double fy, int32_t *out_par, double *out_dist) {
     k_query_exact<<<1, 32, 0, st>>>(ds, field_parent, i, j, make_int2(qx, qy), make_double2(fx, fy), out_par,
                                     out_dist);
+}
+
+namespace {
+
+// Lattice point inside the open interior of an obstacle?
+__device__ bool centre_in_obstacle(const DevScene &ds, int px, int py) {
+    const int bx = (px - ds.bin_x0) / ds.bin_size, by = (py - ds.bin_y0) / ds.bin_size;
+    if (bx < 0 || by < 0 || bx >= ds.bin_nx || by >= ds.bin_ny) return false;
+    const int bin = by * ds.bin_nx + bx;
+    for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
+        const BinRec rec = ds.bin_recs[it];
+        const int4 b4 = rec.box;
+        if (px <= b4.x || px >= b4.z || py <= b4.y || py >= b4.w) continue;
+        bool inside = true;
+        for (int e = 0; e < rec.m && inside; ++e) {
+            const int2 a = ds.poly_v[rec.voff + e], c = ds.poly_v[rec.voff + (e + 1 == rec.m ? 0 : e + 1)];
+            inside = orient32(a.x, a.y, c.x, c.y, px, py) > 0;
+        }
+        if (inside) return true;
+    }
+    return false;
+}
+
+// Free-space mask of the pixel centres: bit (i % 32) of word j * free_words +
+// i / 32 is set when pixel (i, j)'s centre lies outside the open interior of
+// every obstacle. The obstacles are fixed for the scene's lifetime, so it is
+// built once, one warp per word.
+__global__ void k_free_mask(const __grid_constant__ DevScene ds, uint32_t *bits) {
+    const long long w = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (w >= (long long)ds.Ny * ds.free_words) return;  // whole warps
+    const int lane = threadIdx.x & 31;
+    const int j = (int)(w / ds.free_words), i = (int)(w % ds.free_words) * 32 + lane;
+    const int pitch_x = ds.S * ds.Wx / ds.Nx, pitch_y = ds.S * ds.Wy / ds.Ny;
+    const bool is_free = i < ds.Nx && !centre_in_obstacle(ds, pitch_x * i + pitch_x / 2, pitch_y * j + pitch_y / 2);
+    const unsigned m = __ballot_sync(0xffffffffu, is_free);
+    if (lane == 0) bits[w] = m;
+}
+
+}  // namespace
+
+void launch_free_mask(const DevScene &ds, cudaStream_t st, uint32_t *bits) {
+    const long long words = (long long)ds.Ny * ds.free_words;
+    const int per_block = NT / 32;
+    k_free_mask<<<(unsigned)((words + per_block - 1) / per_block), NT, 0, st>>>(ds, bits);
 }
 
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,

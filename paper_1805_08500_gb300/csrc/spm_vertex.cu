@@ -475,6 +475,14 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         }
         if (tid == 0) cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
         const int written = (round + 1) << 1;     // stamp of a copy written in this round, without the copy bit
+#ifdef SPM_COUNT
+        const long long t_round = clock64();
+        if (tid == 0) {
+            SPM_CNT(0, nd);
+            SPM_CNT_MAX(1, nd);
+            SPM_CNT(2, (nd + ngroups - 1) / ngroups);
+        }
+#endif
         for (int i0 = warp * 4; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
@@ -544,8 +552,19 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             }
             changed = __shfl_sync(0xffffffffu, changed, grp * 8) && act;
             if (changed) mark(v, dirty + nxt * dw, dl + nxt * n, &cnt[(round + 1) % 3]);
+#ifdef SPM_COUNT
+            if (gl == 0 && act) SPM_CNT(3, in_start[vv + 1] - in_start[vv]);
+            if (gl == 0 && changed) SPM_CNT(4, 1);
+#endif
         }
+#ifdef SPM_COUNT
+        if (lane == 0) SPM_CNT_MAX(6, (unsigned long long)(clock64() - t_round));  // slowest warp, any round
+        if (tid == 0) SPM_CNT(7, (unsigned long long)(clock64() - t_round));  // warp 0 (always has work)
+#endif
         __syncthreads();
+#ifdef SPM_COUNT
+        if (tid == 0) SPM_CNT(5, (unsigned long long)(clock64() - t_round));
+#endif
     }
     for (int g = tid; g < n; g += kSoloThreads) {
         const int ci = (stamp[g] & 1) * n + g;
@@ -841,3 +860,14 @@ void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st) {
 }
 
 }  // namespace spm
+
+#ifdef SPM_COUNT
+// Instrumentation build only: reads and clears this unit's work counters.
+extern "C" int spm_debug_counters_vertex(unsigned long long *out16) {
+    cudaDeviceSynchronize();
+    if (cudaMemcpyFromSymbol(out16, spm::g_count, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
+    unsigned long long z[16] = {0};
+    cudaMemcpyToSymbol(spm::g_count, z, sizeof z);
+    return 0;
+}
+#endif
