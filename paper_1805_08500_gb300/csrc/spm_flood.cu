@@ -101,8 +101,9 @@ struct FloodSmem {
 };
 
 // Is the closed box hidden from g (lattice point, not inside the box) by the
-// depth map?
-__device__ bool box_hidden_ang(const float *depth2, int2 g, int4 box) {
+// depth map? One warp: the lanes test 32 of the spanned bins at a time (a
+// tile near g spans hundreds of bins).
+__device__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int lane) {
     const long long dx = max(max(box.x - g.x, g.x - box.z), 0), dy = max(max(box.y - g.y, g.y - box.w), 0);
     const float mind2 = (float)(dx * dx + dy * dy) * (1.f - 1e-6f);
     const float c0 = pang(0.5f * (float)(box.x + box.z) - (float)g.x, 0.5f * (float)(box.y + box.w) - (float)g.y);
@@ -115,8 +116,11 @@ __device__ bool box_hidden_ang(const float *depth2, int2 g, int4 box) {
         hi = fmaxf(hi, d);
     }
     const int k0 = (int)floorf((c0 + lo - kAngEps) / kAngW), k1 = (int)floorf((c0 + hi + kAngEps) / kAngW);
-    for (int k = k0; k <= k1; ++k)
-        if (!(depth2[(k + 2 * kAng) & (kAng - 1)] <= mind2)) return false;
+    for (int k = k0; k <= k1; k += 32) {
+        const int kk = k + lane;
+        const bool h = kk > k1 || depth2[(kk + 2 * kAng) & (kAng - 1)] <= mind2;
+        if (!__all_sync(0xffffffffu, h)) return false;
+    }
     return true;
 }
 
@@ -126,8 +130,11 @@ template <bool MAPS>
 __device__ void insert_polygon_warp(const DevScene &ds, float *depth2, float *lo2, int2 g, int q, int lane,
                                     float plen) {
     const int b = ds.poly_off[q], m = ds.poly_off[q + 1] - b;
+    const int2 mine = lane < m ? ds.poly_v[b + lane] : make_int2(0, 0);  // vertex `lane`, one load per lane
     for (int i = 0; i < m; ++i) {
-        const int2 a = ds.poly_v[b + i], c = ds.poly_v[b + (i + 1 == m ? 0 : i + 1)];
+        const int in = i + 1 == m ? 0 : i + 1;
+        const int2 a = make_int2(__shfl_sync(0xffffffffu, mine.x, i), __shfl_sync(0xffffffffu, mine.y, i));
+        const int2 c = make_int2(__shfl_sync(0xffffffffu, mine.x, in), __shfl_sync(0xffffffffu, mine.y, in));
         if (orient32(a.x, a.y, c.x, c.y, g.x, g.y) >= 0) continue;  // not front-facing
         // line normal n (left of a -> c); g is on its negative side, so
         // n . (a - g) > 0 and n . u > 0 for every ray u that meets the edge
@@ -191,6 +198,7 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
     const float plen = fmaxf(1.f, 0.125f * (float)min(tpx, tpy));  // lower-bound piece length
     constexpr bool maps = MAPS;
     if (ds.gen_map_ok && tid == 0) ds.gen_map_ok[g] = 0;  // set again when the map is complete
+    SPM_T0();
     if (!geometric && !(ds.gen_costf[g] < INFINITY)) return;
     const int kind = ds.gen_kind[g];
     const int ct = kind == kVert && !geometric ? ds.gen_ctype[g] : kConeNone;
@@ -227,6 +235,7 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
         }
     }
     __syncthreads();
+    SPM_LAP(0);
     if (sm.cnt[0] == 0) {  // g outside every tile: scanned by all tiles instead
         if (tid == 0) push_global(ds, g);
         return;
@@ -271,26 +280,33 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
             }
         }
         __syncthreads();
+        SPM_LAP(1);
         const int ni = min(sm.n_ins, kInsCap);
         for (int q = tid >> 5; q < ni; q += kFloodThreads / 32)
             insert_polygon_warp<MAPS>(ds, sm.depth2, lo2, gl, sm.ins[q], tid & 31, plen);
         __syncthreads();
-        // B: cone and depth-map test per frontier tile
-        for (int i = tid; i < nc; i += kFloodThreads) {
+        SPM_LAP(2);
+#ifdef SPM_TIME
+        spm_acc_[6] += 1;   // levels
+        spm_acc_[7] += ni;  // polygons inserted
+#endif
+        // B: cone and depth-map test per frontier tile, a warp per tile
+        for (int i = tid >> 5; i < nc; i += kFloodThreads / 32) {
             const int t = cur[i];
             const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
             int f = 2;
             if (cone_meets_box(ct, cone, gl, area)) {
                 const bool inside = gl.x >= area.x && gl.x <= area.z && gl.y >= area.y && gl.y <= area.w;
-                f = !inside && box_hidden_ang(sm.depth2, gl, area) ? 1 : 0;
+                f = !inside && box_hidden_ang_warp(sm.depth2, gl, area, tid & 31) ? 1 : 0;
             }
-            sm.flag[i] = f;
+            if ((tid & 31) == 0) sm.flag[i] = f;
         }
         if (tid == 0) {
             sm.cnt[p ^ 1] = 0;
             sm.n_ins = 0;
         }
         __syncthreads();
+        SPM_LAP(3);
         // C: emit visible tiles, queue their fresh 8-neighbours
         int *nxt = sm.front[p ^ 1];
         for (int q = tid; q < nc * 9; q += kFloodThreads) {
@@ -329,6 +345,7 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
         }
 #endif
         __syncthreads();
+        SPM_LAP(4);
         p ^= 1;
     }
 #ifdef SPM_COUNT
@@ -344,6 +361,8 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
         for (int k = tid; k < kAng; k += kFloodThreads) mp[k] = make_float2(sm.depth2[k], lo2[k]);
         if (tid == 0) ds.gen_map_ok[g] = 1;
     }
+    SPM_LAP(5);
+    SPM_TFLUSH();
 }
 
 // Automatic mode: flood only sparse visibility graphs (mazes); a dense one
@@ -354,15 +373,26 @@ __device__ __forceinline__ bool flood_declined(const DevScene &ds) {
     return (double)ds.in_start[ds.n_vert] > 0.01 * pairs;
 }
 
+// Resident CTAs take generators from a work counter (flood_counts[3]) as
+// they finish: flood depths vary widely, so a fixed stride would leave the
+// kernel waiting for the CTAs that drew several deep generators.
 template <bool MAPS>
 __global__ void __launch_bounds__(kFloodThreads, MAPS ? 6 : 8) k_flood(DevScene ds) {
     extern __shared__ unsigned fdyn[];
     __shared__ FloodSmem sm;
+    __shared__ int next_g;
     if (flood_declined(ds)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) ds.flood_counts[2] = 1;
         return;
     }
-    for (int g = blockIdx.x; g < ds.n_gen; g += gridDim.x) flood_one<MAPS>(ds, sm, fdyn, g);
+    for (;;) {
+        if (threadIdx.x == 0) next_g = atomicAdd(&ds.flood_counts[3], 1);
+        __syncthreads();
+        const int g = next_g;
+        __syncthreads();  // next_g is rewritten for the next generator
+        if (g >= ds.n_gen) break;
+        flood_one<MAPS>(ds, sm, fdyn, g);
+    }
 }
 
 // Batched form: every (scene, generator) of the batch, one CTA each.
@@ -479,10 +509,15 @@ void launch_flood(const DevScene &ds, cudaStream_t st) {
     }
     cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
     cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
-    const size_t smem = flood_smem_bytes(ntiles, ds.n_poly, ds.use_maps && ds.gen_maps);
-    const int blocks = min(152 * 8, ds.n_gen);
-    if (ds.use_maps && ds.gen_maps) k_flood<true><<<max(blocks, 1), kFloodThreads, smem, st>>>(ds);
-    else k_flood<false><<<max(blocks, 1), kFloodThreads, smem, st>>>(ds);
+    const bool maps = ds.use_maps && ds.gen_maps;
+    const size_t smem = flood_smem_bytes(ntiles, ds.n_poly, maps);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, maps ? k_flood<true> : k_flood<false>, kFloodThreads, smem);
+    const int blocks = max(1, min(max(sms, 1) * max(per_sm, 1), ds.n_gen));  // resident CTAs only
+    if (maps) k_flood<true><<<blocks, kFloodThreads, smem, st>>>(ds);
+    else k_flood<false><<<blocks, kFloodThreads, smem, st>>>(ds);
     k_tiles_scan<<<1, 1024, 0, st>>>(ds);
     k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds);
 }
@@ -505,6 +540,17 @@ void launch_flood_batched(const BatchDev &b, cudaStream_t st) {
 }
 
 }  // namespace spm
+
+#ifdef SPM_TIME
+// Instrumentation build only: reads and clears the flood's phase clocks.
+extern "C" int spm_debug_times_flood(unsigned long long *out8) {
+    cudaDeviceSynchronize();
+    if (cudaMemcpyFromSymbol(out8, spm::g_time, sizeof(unsigned long long) * 8) != cudaSuccess) return 1;
+    unsigned long long z[8] = {0};
+    cudaMemcpyToSymbol(spm::g_time, z, sizeof z);
+    return 0;
+}
+#endif
 
 #ifdef SPM_COUNT
 // Instrumentation build only: reads and clears this unit's work counters.

@@ -82,7 +82,20 @@ __device__ __forceinline__ Hull hull_box_point(int4 box, int tx, int ty) {
     return h;
 }
 
+// Per-candidate generator data staged in shared memory for the first
+// kStage candidates of a sorted batch: one parallel load replaces a dependent
+// global load per candidate in the lb-ordered loop.
+constexpr int kStage = 64;
+struct CandRec {
+    int4 cone;
+    int2 lat;
+    float2 pos;
+    float cf;
+    int kind, ctype, map_ok;
+};
+
 struct PixSmem {
+    CandRec rec[kStage];
     int cand_id[kCandCap];
     float cand_lb[kCandCap];
     unsigned dedup[kDedupBits / 32];
@@ -356,6 +369,19 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
         const bool last = g0 + NT >= ntotal;
         if (nc > kCandCap - NT || (last && nc > 0)) {
             sort_candidates(sm, nc);
+            for (int t = threadIdx.x; t < min(nc, kStage); t += NT) {
+                const int g = sm.cand_id[t];
+                CandRec r;
+                r.kind = ds.gen_kind[g];
+                r.cf = ds.gen_costf[g];
+                r.lat = ds.gen_lat[g];
+                r.pos = ds.gen_pos[g];
+                r.ctype = r.kind == kVert ? ds.gen_ctype[g] : kConeNone;
+                r.cone = r.kind == kVert ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
+                r.map_ok = MAPS && ds.gen_map_ok ? ds.gen_map_ok[g] : 0;
+                sm.rec[t] = r;
+            }
+            __syncthreads();
             SPM_LAP(2);
             if (threadIdx.x == 0) SPM_CNT(1, nc);
             bool done = false;
@@ -390,10 +416,11 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 }
                 if (threadIdx.x == 0) SPM_CNT(4, 1);
                 const int gc = sm.cand_id[c];
-                const int kind = ds.gen_kind[gc];
-                const float cf = ds.gen_costf[gc];
-                const int2 gl = ds.gen_lat[gc];
-                const float2 gp = ds.gen_pos[gc];
+                const bool staged = c < kStage;
+                const int kind = staged ? sm.rec[c].kind : ds.gen_kind[gc];
+                const float cf = staged ? sm.rec[c].cf : ds.gen_costf[gc];
+                const int2 gl = staged ? sm.rec[c].lat : ds.gen_lat[gc];
+                const float2 gp = staged ? sm.rec[c].pos : ds.gen_pos[gc];
                 int ct = kConeNone;
                 int4 cone = make_int4(0, 0, 0, 0);
                 int4 seg = make_int4(0, 0, 0, 0);
@@ -401,8 +428,8 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 long long den = 0;
                 float seg_il = 0.f;
                 if (kind == kVert) {
-                    ct = ds.gen_ctype[gc];
-                    cone = ds.gen_cone[gc];
+                    ct = staged ? sm.rec[c].ctype : ds.gen_ctype[gc];
+                    cone = staged ? sm.rec[c].cone : ds.gen_cone[gc];
                 } else if (kind == kSegI) {
                     seg = ds.seg_lat[ds.gen_aux[gc]];
                     segf = ds.seg_pos[ds.gen_aux[gc]];
@@ -417,7 +444,8 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 // the flood's depth map of a point generator decides most pixels:
                 // nearer than any obstacle on their ray -> visible; beyond a full
                 // blocking -> hidden; only the rest need the exact test below
-                const float2 *gmap = MAPS && lists && ds.use_maps && ds.gen_maps && kind != kSegI && ds.gen_map_ok[gc]
+                const float2 *gmap = MAPS && lists && ds.use_maps && ds.gen_maps && kind != kSegI &&
+                                             (staged ? sm.rec[c].map_ok : ds.gen_map_ok[gc])
                                          ? ds.gen_maps + (size_t)gc * kAngBins
                                          : nullptr;
 #pragma unroll

@@ -293,19 +293,25 @@ __device__ __forceinline__ void mark_out_warp(const DevScene &ds, int u, int lan
 }
 
 // Shared-memory bytes the single-CTA fixpoint needs (0 if it cannot run).
-__device__ __forceinline__ int solo_bytes(const DevScene &ds) {
+// Shared memory of the single-CTA fixpoint, 0 when the graph does not fit or
+// is not sparse. with_len: the FP64 edge lengths fit as well.
+__device__ __forceinline__ int solo_bytes(const DevScene &ds, bool &with_len) {
     const long long n = ds.n_gen, E = ds.in_start[ds.n_vert];
+    with_len = false;
     // sparse graphs only (deep, few vertices per round); dense ones need the GPU
     if (n >= 32768 || E > ds.edge_cap || E > 8 * n) return 0;
-    // two state copies (cost 8, parent 2, cone 8, cone type 1), stamp 4,
-    // lattice 4, CSR in/out, two dirty bitmaps and lists, 16-byte alignment
-    const long long b = n * 2 * (8 + 2 + 8 + 1) + n * (4 + 4) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
+    // cost 8, parent 2, lattice 4, wedge 8 per generator; CSR in / out with
+    // 16-bit ids; two dirty bitmaps and lists; 16-byte alignment slack
+    const long long b = n * (8 + 2 + 4 + 8) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
                         2 * 4 * ((n + 31) / 32) + 2 * 2 * n + 16 * 16;
-    return b <= ds.solo_smem ? (int)b : 0;
+    if (b > ds.solo_smem) return 0;
+    with_len = b + 8 * E <= ds.solo_smem;
+    return (int)(with_len ? b + 8 * E : b);
 }
 
 __global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene ds, int max_rounds) {
-    if (solo_bytes(ds) > 0) return;  // the single-CTA kernel handles this graph
+    bool solo_len;
+    if (solo_bytes(ds, solo_len) > 0) return;  // the single-CTA kernel handles this graph
     cg::grid_group grid = cg::this_grid();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsize = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, gwarp = gtid >> 5, nwarps = gsize >> 5;
@@ -394,19 +400,35 @@ __global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene d
 }
 
 // The same fixpoint in one CTA with the graph and the state in shared
-// memory, for graphs that fit (16-bit generator ids and lattice coordinates,
-// cone directions in 16-bit lanes -- lattice directions fit in 16 bits). One
-// barrier per round: each vertex keeps two copies of its state (cost,
-// parent, cone) and a stamp (round that wrote it, which copy is current).
-// A dirty vertex pulls its in-neighbours' state as of the previous round --
-// the other copy when a neighbour was already updated in this round -- and,
-// when its own value changes, writes its spare copy and marks its
-// out-neighbours in the next round's dirty bitmap and list. Every pull sees
-// the same state as in k_sssp's rounds, so the results are identical.
+// memory, for graphs that fit (16-bit generator ids and lattice coordinates;
+// wedge directions are lattice differences and fit in 16 bits as well). One
+// barrier per round. A dirty vertex pulls its in-neighbours' current state --
+// including values written earlier in the same round, so a change can travel
+// several edges in one round -- and, when its own value changes, writes it and
+// marks its out-neighbours in the next round's dirty bitmap and list. A
+// neighbour's shadow cone is derived from its current parent when it is
+// pulled. A pull may see a neighbour half-way through an update in the same
+// round; that neighbour's change marks the puller dirty again, so the last
+// round reads only settled values and the loop stops at the fixpoint of the
+// vertex equations. With positive link lengths that fixpoint is unique
+// (costs and then parents are fixed in order of increasing cost), so the
+// result is the one k_sssp's synchronous rounds reach. The FP64 link
+// lengths are staged in shared memory when they fit, else read from global.
+__device__ __forceinline__ void arrival_from(const DevScene &ds, const signed char *src_kind, const short2 *lat,
+                                             int p, short2 vl, int &dx, int &dy) {
+    const int kp = p >= ds.n_src ? kVert : (p < 64 ? src_kind[p] : ds.gen_kind[p]);
+    if (kp == kSegI) {
+        arrival_dir(ds, p, make_int2(vl.x, vl.y), dx, dy);
+    } else {
+        dx = vl.x - lat[p].x;
+        dy = vl.y - lat[p].y;
+    }
+}
+
 __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    const int bytes = solo_bytes(ds);
-    if (bytes == 0) return;
+    bool with_len;
+    if (solo_bytes(ds, with_len) == 0) return;
     const int n = ds.n_gen, nv = ds.n_vert, E = ds.in_start[nv];
     unsigned char *p = sm_raw;
     auto take = [&](size_t sz) {
@@ -414,42 +436,40 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         p += (sz + 15) & ~(size_t)15;
         return q;
     };
-    // two copies of each state array, copy c of vertex u at index c * n + u
-    double *cost = (double *)take(8 * 2 * n);
-    short4 *cone = (short4 *)take(8 * 2 * n);
-    short *par = (short *)take(2 * 2 * n);
-    signed char *ctype = (signed char *)take(2 * n);
-    int *stamp = (int *)take(4 * n);  // (round that wrote the current copy + 1) << 1 | current copy
-    short2 *lat = (short2 *)take(4 * n);
-    int *in_start = (int *)take(4 * (nv + 1));
-    unsigned short *in_src = (unsigned short *)take(2 * E);
-    int *out_start = (int *)take(4 * (n + 1));
-    unsigned short *out_dst = (unsigned short *)take(2 * E);
+    double *cost = (double *)take(8 * (size_t)n);
+    short4 *wedge = (short4 *)take(8 * (size_t)n);
+    short *par = (short *)take(2 * (size_t)n);
+    short2 *lat = (short2 *)take(4 * (size_t)n);
+    int *in_start = (int *)take(4 * (size_t)(nv + 1));
+    unsigned short *in_src = (unsigned short *)take(2 * (size_t)E);
+    int *out_start = (int *)take(4 * (size_t)(n + 1));
+    unsigned short *out_dst = (unsigned short *)take(2 * (size_t)E);
     const int dw = (n + 31) / 32;
-    unsigned *dirty = (unsigned *)take(4 * 2 * dw);         // round parity p at p * dw
-    unsigned short *dl = (unsigned short *)take(2 * 2 * n);  // round parity p at p * n
+    unsigned *dirty = (unsigned *)take(4 * 2 * (size_t)dw);         // round parity p at p * dw
+    unsigned short *dl = (unsigned short *)take(2 * 2 * (size_t)n);  // round parity p at p * n
+    double *slen = with_len ? (double *)take(8 * (size_t)E) : nullptr;
     __shared__ int cnt[3];  // dirty-list counts, by round modulo 3
     constexpr int kSrcKinds = 64;
     __shared__ signed char src_kind[kSrcKinds];  // kinds of the first sources (ids >= n_src are vertices)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSoloThreads / 32;
     // work unit: a group of 8 lanes per vertex (in-degrees here are small), 4 per warp
-    const int grp = lane >> 3, gl = lane & 7, ngroups = nwarps * 4, gid = warp * 4 + grp;
+    const int grp = lane >> 3, gl = lane & 7, ngroups = nwarps * 4;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
     for (int i = tid; i <= n; i += kSoloThreads) out_start[i] = ds.out_start[i];
     for (int i = tid; i < E; i += kSoloThreads) {
         in_src[i] = (unsigned short)ds.in_src[i];
         out_dst[i] = (unsigned short)ds.out_dst[i];
+        if (with_len) slen[i] = ds.in_len[i];
     }
     for (int g = tid; g < n; g += kSoloThreads) {
         const bool src = g < ds.n_src;
         cost[g] = src ? 0.0 : inf;
         par[g] = (short)(src ? g : -1);
-        ctype[g] = (signed char)(src ? kConeNone : kConeEmpty);
-        cone[g] = make_short4(0, 0, 0, 0);
-        stamp[g] = 0;
         const int2 l = ds.gen_lat[g];
         lat[g] = make_short2((short)l.x, (short)l.y);
+        const int4 w = ds.gen_wedge[g];
+        wedge[g] = make_short4((short)w.x, (short)w.y, (short)w.z, (short)w.w);
     }
     for (int w = tid; w < 2 * dw; w += kSoloThreads) dirty[w] = 0u;
     for (int g = tid; g < min(ds.n_src, kSrcKinds); g += kSoloThreads) src_kind[g] = (signed char)ds.gen_kind[g];
@@ -462,7 +482,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             if (!(atomicOr(&bits[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
         }
     };
-    for (int u = gid; u < ds.n_src; u += ngroups) mark(u, dirty, dl, &cnt[0]);
+    for (int u = warp * 4 + grp; u < ds.n_src; u += ngroups) mark(u, dirty, dl, &cnt[0]);
     __syncthreads();
     int round = 0;
     for (;; ++round) {
@@ -474,7 +494,6 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             break;
         }
         if (tid == 0) cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
-        const int written = (round + 1) << 1;     // stamp of a copy written in this round, without the copy bit
 #ifdef SPM_COUNT
         const long long t_round = clock64();
         if (tid == 0) {
@@ -490,22 +509,27 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             const int vv = v - ds.n_src;
             if (act && gl == 0) atomicAnd(&dirty[cur * dw + (v >> 5)], ~(1u << (v & 31)));
             const short2 vl = lat[v];
-            const int4 wedge_v = act && gl == 0 ? __ldg(ds.gen_wedge + v) : make_int4(0, 0, 0, 0);  // needed at commit
             long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
             const int e1 = act ? in_start[vv + 1] : 0;
+#ifdef SPM_COUNT
+            long long tc0 = clock64();
+#endif
             for (int e = in_start[vv] + gl; e < e1; e += 8) {
-                const double len = __ldg(ds.in_len + e);  // issued before the dependent smem reads
+                const double len = with_len ? slen[e] : __ldg(ds.in_len + e);
                 const int u = in_src[e];
-                const int su = stamp[u];
-                const int cu_i = ((su & ~1) == written ? (su & 1) ^ 1 : (su & 1)) * n + u;  // u as of last round
-                const double cu = cost[cu_i];
+                const double cu = cost[u];
                 if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;  // unreached
-                const int ct = ctype[cu_i];
-                if (ct != kConeNone) {
+                if (u >= ds.n_src) {  // an obstacle vertex passes paths on only inside its shadow cone
+                    const int pu = par[u];
+                    if (pu < 0) continue;
                     const short2 ul = lat[u];
-                    const short4 c = cone[cu_i];
-                    if (!in_cone(ct, make_int4(c.x, c.y, c.z, c.w), vl.x - ul.x, vl.y - ul.y)) continue;
+                    int dx, dy;
+                    arrival_from(ds, src_kind, lat, pu, ul, dx, dy);
+                    const short4 w = wedge[u];
+                    int4 c;
+                    const int ct = make_cone(make_int4(w.x, w.y, w.z, w.w), dx, dy, c);
+                    if (!in_cone(ct, c, vl.x - ul.x, vl.y - ul.y)) continue;
                 }
                 // costs are non-negative, so their bit patterns order like
                 // their values: compare as integers, keep FP64 for the add
@@ -515,6 +539,9 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                     bpar = u;
                 }
             }
+#ifdef SPM_COUNT
+            long long tc1 = clock64();
+#endif
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) {  // within the 8-lane group
                 const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -524,35 +551,29 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                     bpar = op;
                 }
             }
+#ifdef SPM_COUNT
+            long long tc2 = clock64();
+#endif
             bool changed = false;
-            if (act && gl == 0) {
-                const int sv = stamp[v], ci = sv & 1;  // only this group writes v
-                if (best != __double_as_longlong(cost[ci * n + v]) || bpar != par[ci * n + v]) {
-                    const int ni = ci ^ 1;
-                    cost[ni * n + v] = __longlong_as_double(best);
-                    par[ni * n + v] = (short)bpar;
-                    int4 c = make_int4(0, 0, 0, 0);
-                    int ctv = kConeEmpty;  // unreachable again: no arrival direction
-                    if (bpar >= 0) {
-                        int dx, dy;
-                        const int kp = bpar >= ds.n_src ? kVert : (bpar < kSrcKinds ? src_kind[bpar] : ds.gen_kind[bpar]);
-                        if (kp == kSegI) {
-                            arrival_dir(ds, bpar, make_int2(vl.x, vl.y), dx, dy);
-                        } else {
-                            dx = vl.x - lat[bpar].x;
-                            dy = vl.y - lat[bpar].y;
-                        }
-                        ctv = make_cone(wedge_v, dx, dy, c);
-                    }
-                    ctype[ni * n + v] = (signed char)ctv;
-                    cone[ni * n + v] = make_short4((short)c.x, (short)c.y, (short)c.z, (short)c.w);
-                    stamp[v] = written | ni;
-                    changed = true;
-                }
+            if (act && gl == 0 && (best != __double_as_longlong(cost[v]) || bpar != par[v])) {
+                cost[v] = __longlong_as_double(best);  // only this group writes v in this round
+                par[v] = (short)bpar;
+                changed = true;
             }
             changed = __shfl_sync(0xffffffffu, changed, grp * 8) && act;
+#ifdef SPM_COUNT
+            long long tc3 = clock64();
+#endif
             if (changed) mark(v, dirty + nxt * dw, dl + nxt * n, &cnt[(round + 1) % 3]);
 #ifdef SPM_COUNT
+            long long tc4 = clock64();
+            if (tid == 0) {
+                SPM_CNT(8, tc0 - t_round);
+                SPM_CNT(9, tc1 - tc0);
+                SPM_CNT(10, tc2 - tc1);
+                SPM_CNT(11, tc3 - tc2);
+                SPM_CNT(12, tc4 - tc3);
+            }
             if (gl == 0 && act) SPM_CNT(3, in_start[vv + 1] - in_start[vv]);
             if (gl == 0 && changed) SPM_CNT(4, 1);
 #endif
@@ -566,13 +587,24 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         if (tid == 0) SPM_CNT(5, (unsigned long long)(clock64() - t_round));
 #endif
     }
+    // the settled state, with each vertex's shadow cone from its parent
     for (int g = tid; g < n; g += kSoloThreads) {
-        const int ci = (stamp[g] & 1) * n + g;
-        ds.cost[0][g] = cost[ci];
-        ds.par[0][g] = par[ci];
-        const short4 c = cone[ci];
-        ds.gen_cone[g] = make_int4(c.x, c.y, c.z, c.w);
-        ds.gen_ctype[g] = ctype[ci];
+        const int pg = par[g];
+        int4 c = make_int4(0, 0, 0, 0);
+        int ct = kConeNone;
+        if (g >= ds.n_src) {
+            ct = kConeEmpty;  // unreached: no arrival direction
+            if (pg >= 0) {
+                int dx, dy;
+                arrival_from(ds, src_kind, lat, pg, lat[g], dx, dy);
+                const short4 w = wedge[g];
+                ct = make_cone(make_int4(w.x, w.y, w.z, w.w), dx, dy, c);
+            }
+        }
+        ds.cost[0][g] = cost[g];
+        ds.par[0][g] = pg;
+        ds.gen_cone[g] = c;
+        ds.gen_ctype[g] = ct;
     }
     if (tid == 0) ds.stats[0] = round;
 }
