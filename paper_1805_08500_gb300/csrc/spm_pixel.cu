@@ -596,7 +596,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
 // One CTA per tile; one kernel per tile size, so each gets its own register
 // allocation (32 x 32 tiles: 4 pixels a thread, 16 x 16: 1).
 template <int PX, bool MAPS>
-__global__ void __launch_bounds__(NT, PX == 4 ? 3 : SPM_PIX16_MINB) k_pixels(const __grid_constant__ DevScene ds,
+__global__ void __launch_bounds__(NT, PX == 4 ? 4 : SPM_PIX16_MINB) k_pixels(const __grid_constant__ DevScene ds,
                                                                          float *__restrict__ dist,
                                                                          int32_t *__restrict__ parent, int tile0) {
     __shared__ PixSmem sm;
