@@ -304,6 +304,11 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     ds.free_words = (hs.Nx + 31) / 32;
     uint32_t *free_bits = dalloc<uint32_t>(s, (size_t)hs.Ny * ds.free_words);
     ds.free_bits = free_bits;
+    // local depth maps of the obstacle vertices, when they fit in 256 MB
+    float *vert_maps = nullptr;
+    if ((size_t)hs.n_vert * spm::kLocBins * sizeof(float) <= ((size_t)256 << 20))
+        vert_maps = dalloc<float>(s, (size_t)hs.n_vert * spm::kLocBins);
+    ds.vert_maps = vert_maps;
     ds.sssp_blocks = spm::sssp_grid_blocks();
     ds.solo_smem = spm::solo_smem_bytes();
     for (void *p : s->allocs) ok &= p != nullptr;
@@ -316,6 +321,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     cudaMemset(ds.status, 0, sizeof(uint32_t));
     cudaMemset(ds.stats, 0, sizeof(int32_t) * 4);
     spm::launch_free_mask(ds, nullptr, free_bits);
+    if (vert_maps) spm::launch_vert_maps(ds, nullptr, vert_maps);
     if (cudaPeekAtLastError() != cudaSuccess) ok = false;
     for (cudaEvent_t &e : s->ev)
         if (cudaEventCreate(&e) != cudaSuccess) ok = false;

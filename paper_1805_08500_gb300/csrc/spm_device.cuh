@@ -15,6 +15,16 @@
 
 namespace spm {
 
+// Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
+#ifdef SPM_COUNT
+static __device__ unsigned long long g_count[16];  // one copy per translation unit
+#define SPM_CNT(i, v) atomicAdd(&::spm::g_count[i], (unsigned long long)(v))
+#define SPM_CNT_MAX(i, v) atomicMax(&::spm::g_count[i], (unsigned long long)(v))
+#else
+#define SPM_CNT(i, v) ((void)0)
+#define SPM_CNT_MAX(i, v) ((void)0)
+#endif
+
 __device__ __forceinline__ int orient32(int ax, int ay, int bx, int by, int cx, int cy) {
     return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
 }
@@ -197,10 +207,12 @@ __device__ __forceinline__ bool visible_points(const DevScene &ds, int px, int p
     if (px == qx && py == qy) return true;
     int4 sb = make_int4(min(px, qx), min(py, qy), max(px, qx), max(py, qy));
     bool blocked = walk_bins(ds, (float)px, (float)py, (float)qx, (float)qy, 0.f, [&](int bin) {
+        SPM_CNT(15, 1);
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
             const BinRec rec = ds.bin_recs[it];
             const int4 bx = rec.box;
             if (bx.z < sb.x || bx.x > sb.z || bx.w < sb.y || bx.y > sb.w) continue;
+            SPM_CNT(12, 1);
             const int2 *V = ds.poly_v + rec.voff;
             if (poly_blocks(V, rec.m, px, py, qx, qy, edge_mask(V, rec.m, qx, qy))) return true;
         }
@@ -283,15 +295,6 @@ __device__ __forceinline__ long long cta_exclusive_scan(long long x, long long *
     return r;
 }
 
-// Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
-#ifdef SPM_COUNT
-static __device__ unsigned long long g_count[16];  // one copy per translation unit
-#define SPM_CNT(i, v) atomicAdd(&::spm::g_count[i], (unsigned long long)(v))
-#define SPM_CNT_MAX(i, v) atomicMax(&::spm::g_count[i], (unsigned long long)(v))
-#else
-#define SPM_CNT(i, v) ((void)0)
-#define SPM_CNT_MAX(i, v) ((void)0)
-#endif
 
 // Phase clocks of an instrumentation build (-DSPM_TIME); compiled out otherwise.
 #ifdef SPM_TIME

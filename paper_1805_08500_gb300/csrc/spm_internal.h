@@ -22,6 +22,7 @@ constexpr int kBlockCap = 96;        // blocker polygons per chunk (smem)
 constexpr int kDedupBits = 8192;     // polygon-id dedup bitmap (smem)
 constexpr int kMaxRounds = 1 << 20;  // hard cap on vertex-fixpoint rounds
 constexpr int kSeqMaxGen = 1 << 16;  // generators the sequential (paper-schedule) kernel takes
+constexpr int kLocBins = 256;        // pseudo-angle bins of an obstacle vertex's local depth map
 
 enum GenKind : int32_t { kPoint = 0, kSegA = 1, kSegB = 2, kSegI = 3, kVert = 4 };
 enum ConeType : int32_t { kConeNone = 0, kConeWedge = 1, kConeRay = 2, kConeEmpty = 3 };
@@ -89,6 +90,12 @@ struct DevScene {
     const BinRec *bin_recs;            // parallel to bin_items
     const uint32_t *free_bits;         // free-space mask of pixel centres, free_words words per grid row
     int32_t free_words;
+    // local depth map of each obstacle vertex (kLocBins floats, n_vert rows;
+    // null when too large): per pseudo-angle bin an upper bound of the
+    // squared distance beyond which every ray of the bin has entered an
+    // obstacle, from the polygons near the vertex -- a conservative filter
+    // of hidden vertex pairs before the exact test
+    const float *vert_maps;
     // generators (static part)
     const int32_t *gen_kind;
     const int2 *gen_lat;
@@ -185,6 +192,8 @@ void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_
 void launch_flood(const DevScene &ds, cudaStream_t st);
 // free-space mask of the pixel centres (once per scene)
 void launch_free_mask(const DevScene &ds, cudaStream_t st, uint32_t *bits);
+// local depth maps of the obstacle vertices (once per scene)
+void launch_vert_maps(const DevScene &ds, cudaStream_t st, float *maps);
 // the paper's generator-sequential schedule over the whole map (cooperative launch of `blocks` CTAs)
 cudaError_t launch_sequential(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int blocks);
 int sequential_grid_blocks();

@@ -63,6 +63,84 @@ __device__ bool pair_filter(const DevScene &ds, int u, int v) {
     return !((a > 0 && b < 0) || (a < 0 && b > 0));
 }
 
+// Local depth maps (obstacles are fixed, so they are built once per scene).
+// Directions around a vertex are cut into kLocBins bins of the pseudo-angle;
+// map[b] bounds from above the squared distance at which every ray of bin b
+// has crossed a front-facing edge of a nearby polygon (the vertex strictly
+// on the edge's outer side), i.e. entered that polygon's interior. Along an
+// edge's line the crossing distance is convex in the ray angle, so over a
+// bin it peaks at a boundary ray; boundary directions are integer vectors
+// (multiples of 1 / kLocQ per quadrant), so the products are exact in
+// integers up to a few float roundings, covered by a 1e-5 relative margin.
+// Only polygons of the bins within two bins of the vertex enter; leaving
+// others out only raises the bounds.
+constexpr int kLocQ = kLocBins / 4;
+constexpr float kLocW = 4.0f / kLocBins;
+
+__device__ __forceinline__ int2 loc_boundary_dir(int m) {
+    const int mm = m & (kLocBins - 1), f = mm & (kLocQ - 1);
+    switch (mm / kLocQ) {
+        case 0: return make_int2(kLocQ - f, f);
+        case 1: return make_int2(-f, kLocQ - f);
+        case 2: return make_int2(-(kLocQ - f), -f);
+        default: return make_int2(f, -(kLocQ - f));
+    }
+}
+
+// One warp per obstacle vertex; the lanes over the bins an edge spans.
+__global__ void __launch_bounds__(256) k_vert_maps(const __grid_constant__ DevScene ds, float *maps) {
+    __shared__ float sm[8][kLocBins];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int vv = blockIdx.x * 8 + warp;
+    if (vv >= ds.n_vert) return;  // whole warps
+    float *map = sm[warp];
+    for (int k = lane; k < kLocBins; k += 32) map[k] = INFINITY;
+    __syncwarp();
+    const int2 g = ds.gen_lat[ds.n_src + vv];
+    const int cx = (g.x - ds.bin_x0) / ds.bin_size, cy = (g.y - ds.bin_y0) / ds.bin_size;
+    for (int by = max(0, cy - 2); by <= min(ds.bin_ny - 1, cy + 2); ++by)
+        for (int bx = max(0, cx - 2); bx <= min(ds.bin_nx - 1, cx + 2); ++bx) {
+            const int bin = by * ds.bin_nx + bx;
+            for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
+                const BinRec rec = ds.bin_recs[it];
+                const int2 *V = ds.poly_v + rec.voff;
+                for (int i = 0; i < rec.m; ++i) {
+                    const int2 a = V[i], c = V[i + 1 == rec.m ? 0 : i + 1];
+                    if (orient32(a.x, a.y, c.x, c.y, g.x, g.y) >= 0) continue;  // not front-facing
+                    const int nx = -(c.y - a.y), ny = c.x - a.x;
+                    const long long N = (long long)nx * (a.x - g.x) + (long long)ny * (a.y - g.y);
+                    const float fN2 = (float)N * (float)N;
+                    // the edge runs clockwise seen from g: counter-clockwise from c to a
+                    const float lo = pang((float)(c.x - g.x), (float)(c.y - g.y));
+                    const float hi = lo + fmodf(pang((float)(a.x - g.x), (float)(a.y - g.y)) - lo + 4.f, 4.f);
+                    const int k0 = (int)ceilf((lo + kAngEps) / kLocW), k1 = (int)floorf((hi - kAngEps) / kLocW) - 1;
+                    auto bdist2 = [&](int mb) {
+                        const int2 u = loc_boundary_dir(mb);
+                        const float fD = (float)(nx * u.x + ny * u.y);  // exact: |n| < 2^16, |u| <= kLocQ
+                        return __fdividef(fN2 * (float)(u.x * u.x + u.y * u.y), fD * fD) * (1.f + 1e-5f);
+                    };
+                    for (int k = k0 + lane; k <= k1; k += 32) {
+                        int *slot = (int *)&map[k & (kLocBins - 1)];
+                        atomicMin(slot, __float_as_int(fmaxf(bdist2(k), bdist2(k + 1))));
+                    }
+                }
+            }
+        }
+    __syncwarp();
+    for (int k = lane; k < kLocBins; k += 32) maps[(size_t)vv * kLocBins + k] = map[k];
+}
+
+// Is lattice point q hidden from obstacle vertex v by v's local depth map?
+__device__ __forceinline__ bool loc_hidden(const DevScene &ds, int v, int2 vl, int2 q) {
+    const int rx = q.x - vl.x, ry = q.y - vl.y;
+    const float r2 = (float)((long long)rx * rx + (long long)ry * ry);
+    const float a = pang((float)rx, (float)ry);
+    const int b0 = (int)floorf((a - kAngEps) / kLocW), b1 = (int)floorf((a + kAngEps) / kLocW);
+    const float *map = ds.vert_maps + (size_t)(v - ds.n_src) * kLocBins;
+    return r2 * (1.f - 1e-5f) >= fmaxf(__ldg(map + ((b0 + kLocBins) & (kLocBins - 1))),
+                                       __ldg(map + (b1 & (kLocBins - 1))));
+}
+
 // Exact visibility of a pair that passed the filter.
 __device__ bool pair_visible(const DevScene &ds, int u, int v) {
     const int2 vl = ds.gen_lat[v];
@@ -105,7 +183,10 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, Scene s
         if (lane < n) {
             const int3 pr = q.e[warp][qn - n + lane];
             const DevScene &ds = *scene_of_task(pr.x);
-            if (pair_visible(ds, pr.y, pr.z)) set_edge_bits(ds, pr.y, pr.z);
+            const bool vis = pair_visible(ds, pr.y, pr.z);
+            if (vis) set_edge_bits(ds, pr.y, pr.z);
+            SPM_CNT(13, 1);
+            SPM_CNT(14, vis ? 1 : 0);
         }
         qn -= n;
         __syncwarp();
@@ -118,7 +199,11 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, Scene s
         const int vv = (int)(lt / ds.vis_words), w = (int)(lt % ds.vis_words);
         const int u = w * 32 + lane, v = ds.n_src + vv;
         if (w * 32 >= v) continue;  // the whole word lies at or above the diagonal (warp-uniform)
-        const bool c = u < v && pair_filter(ds, u, v);
+        bool c = u < v && pair_filter(ds, u, v);
+        if (c && ds.vert_maps && ds.gen_kind[u] != kSegI) {  // hidden by an obstacle near either end
+            const int2 ul = ds.gen_lat[u], vl = ds.gen_lat[v];
+            c = !loc_hidden(ds, v, vl, ul) && !(u >= ds.n_src && loc_hidden(ds, u, ul, vl));
+        }
         const unsigned bal = __ballot_sync(0xffffffffu, c);
         if (c) q.e[warp][qn + __popc(bal & ((1u << lane) - 1u))] = make_int3(sc, u, v);
         qn += __popc(bal);
@@ -566,13 +651,11 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
 #endif
             if (changed) mark(v, dirty + nxt * dw, dl + nxt * n, &cnt[(round + 1) % 3]);
 #ifdef SPM_COUNT
-            long long tc4 = clock64();
             if (tid == 0) {
                 SPM_CNT(8, tc0 - t_round);
                 SPM_CNT(9, tc1 - tc0);
                 SPM_CNT(10, tc2 - tc1);
                 SPM_CNT(11, tc3 - tc2);
-                SPM_CNT(12, tc4 - tc3);
             }
             if (gl == 0 && act) SPM_CNT(3, in_start[vv + 1] - in_start[vv]);
             if (gl == 0 && changed) SPM_CNT(4, 1);
@@ -869,6 +952,10 @@ int sssp_grid_blocks() {
 }
 
 int count_kernel_launches_vertex() { return 6; }
+
+void launch_vert_maps(const DevScene &ds, cudaStream_t st, float *maps) {
+    if (ds.n_vert > 0) k_vert_maps<<<(ds.n_vert + 7) / 8, 256, 0, st>>>(ds, maps);
+}
 
 int sssp_batched_grid_blocks() {
     int dev = 0, sms = 0, per_sm = 0;
