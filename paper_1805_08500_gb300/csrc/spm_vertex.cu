@@ -34,6 +34,7 @@ namespace {
 constexpr int kVisThreads = 256;
 constexpr int kSsspThreads = 256;
 constexpr int kSoloThreads = 512;
+constexpr int kSoloGrp = 8;  // lanes per dirty vertex in the single-CTA fixpoint (in-degrees are small)
 constexpr int kSoloSmem = 226 * 1024;  // within the 227 KB opt-in maximum, with the static part
 
 // Static filter for one (u, v) pair: tangency at both ends, or for a
@@ -537,8 +538,9 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     constexpr int kSrcKinds = 64;
     __shared__ signed char src_kind[kSrcKinds];  // kinds of the first sources (ids >= n_src are vertices)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSoloThreads / 32;
-    // work unit: a group of 8 lanes per vertex (in-degrees here are small), 4 per warp
-    const int grp = lane >> 3, gl = lane & 7, ngroups = nwarps * 4;
+    // work unit: a group of kSoloGrp lanes per dirty vertex
+    constexpr int kGpw = 32 / kSoloGrp;  // groups per warp
+    const int grp = lane / kSoloGrp, gl = lane % kSoloGrp, ngroups = nwarps * kGpw;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
     for (int i = tid; i <= n; i += kSoloThreads) out_start[i] = ds.out_start[i];
@@ -561,13 +563,13 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     if (tid < 3) cnt[tid] = 0;
     __syncthreads();
     auto mark = [&](int u, unsigned *bits, unsigned short *list, int *count) {
-        for (int e = out_start[u] + gl; e < out_start[u + 1]; e += 8) {
+        for (int e = out_start[u] + gl; e < out_start[u + 1]; e += kSoloGrp) {
             const int v = out_dst[e];
             const unsigned bit = 1u << (v & 31);
             if (!(atomicOr(&bits[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
         }
     };
-    for (int u = warp * 4 + grp; u < ds.n_src; u += ngroups) mark(u, dirty, dl, &cnt[0]);
+    for (int u = warp * kGpw + grp; u < ds.n_src; u += ngroups) mark(u, dirty, dl, &cnt[0]);
     __syncthreads();
     int round = 0;
     for (;; ++round) {
@@ -587,7 +589,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             SPM_CNT(2, (nd + ngroups - 1) / ngroups);
         }
 #endif
-        for (int i0 = warp * 4; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
+        for (int i0 = warp * kGpw; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
             const int v = act ? dl[cur * n + i] : ds.n_src;
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
 #ifdef SPM_COUNT
             long long tc0 = clock64();
 #endif
-            for (int e = in_start[vv] + gl; e < e1; e += 8) {
+            for (int e = in_start[vv] + gl; e < e1; e += kSoloGrp) {
                 const double len = with_len ? slen[e] : __ldg(ds.in_len + e);
                 const int u = in_src[e];
                 const double cu = cost[u];
@@ -628,7 +630,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             long long tc1 = clock64();
 #endif
 #pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {  // within the 8-lane group
+            for (int o = kSoloGrp / 2; o > 0; o >>= 1) {  // within the group
                 const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
                 if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
@@ -645,7 +647,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 par[v] = (short)bpar;
                 changed = true;
             }
-            changed = __shfl_sync(0xffffffffu, changed, grp * 8) && act;
+            changed = __shfl_sync(0xffffffffu, changed, grp * kSoloGrp) && act;
 #ifdef SPM_COUNT
             long long tc3 = clock64();
 #endif
