@@ -175,10 +175,15 @@ struct PairQ {
     int3 e[kVisThreads / 32][kPairQ];  // (scene, u, v)
 };
 
+// Warps take tasks kVisChunk at a time from a work counter: the walks left
+// after the filters are few and uneven, and a fixed share per warp leaves
+// SMs idle behind a few long ones.
+constexpr int kVisChunk = 32;
+
 template <class Scene, class Task>
-__device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, Scene scene_of_task, Task task_of) {
+__device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, unsigned long long *work, Scene scene_of_task,
+                                              Task task_of) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long warps = (long long)gridDim.x * (kVisThreads / 32);
     int qn = 0;  // warp-uniform queue length
     auto walk = [&](int n) {  // lanes < n walk the last n queued pairs
         if (lane < n) {
@@ -192,10 +197,19 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, Scene s
         qn -= n;
         __syncwarp();
     };
-    for (long long t = (long long)blockIdx.x * (kVisThreads / 32) + warp; t < tasks; t += warps) {
+    long long t = 0, t_end = 0;
+    for (;;) {
+        if (t == t_end) {
+            unsigned long long c = 0;
+            if (lane == 0) c = atomicAdd(work, (unsigned long long)kVisChunk);
+            t = (long long)__shfl_sync(0xffffffffu, c, 0);
+            if (t >= tasks) break;
+            t_end = min(t + kVisChunk, tasks);
+        }
+        const long long tt = t++;
         int sc;
         long long lt;
-        task_of(t, sc, lt);
+        task_of(tt, sc, lt);
         const DevScene &ds = *scene_of_task(sc);
         const int vv = (int)(lt / ds.vis_words), w = (int)(lt % ds.vis_words);
         const int u = w * 32 + lane, v = ds.n_src + vv;
@@ -217,7 +231,8 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, Scene s
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds) {
     __shared__ PairQ q;
     vis_pairs_run(
-        q, (long long)ds.n_vert * ds.vis_words, [&](int) { return &ds; },
+        q, (long long)ds.n_vert * ds.vis_words, reinterpret_cast<unsigned long long *>(ds.stats + 2),
+        [&](int) { return &ds; },
         [&](long long t, int &sc, long long &lt) {
             sc = 0;
             lt = t;
@@ -732,6 +747,8 @@ __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
         const int s = scene_of(b.pair_off, b.n, i);
         b.scenes[s].vis_bits[i - b.pair_off[s]] = 0u;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *reinterpret_cast<unsigned long long *>(b.counters + 6) = 0ull;  // visibility-pair work counter
     const int total = b.gen_off[b.n];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total + b.n; i += gridDim.x * blockDim.x) {
         // entries 0..total-1: one per generator; total..total+n-1: one per scene
@@ -752,7 +769,7 @@ __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs_b(const __grid_constant__ BatchDev b) {
     __shared__ PairQ q;
     vis_pairs_run(
-        q, b.pair_off[b.n], [&](int s) { return b.scenes + s; },
+        q, b.pair_off[b.n], reinterpret_cast<unsigned long long *>(b.counters + 6), [&](int s) { return b.scenes + s; },
         [&](long long t, int &sc, long long &lt) {
             sc = scene_of(b.pair_off, b.n, t);
             lt = t - b.pair_off[sc];
@@ -913,14 +930,18 @@ __global__ void k_finalize_b(const __grid_constant__ BatchDev b) {
 
 }  // namespace
 
+int vis_resident_blocks();  // co-resident CTAs of the visibility-pair kernel
+
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
     cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
     cudaMemsetAsync(ds.out_fill, 0, sizeof(int32_t) * ds.n_gen, st);
     if (ds.n_vert > 0) {
         cudaMemsetAsync(ds.vis_bits, 0, sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words, st);
         const long long tasks = (long long)ds.n_vert * ds.vis_words;
-        long long blocks = (tasks + (kVisThreads / 32) - 1) / (kVisThreads / 32);
-        blocks = blocks > 152 * 16 ? 152 * 16 : blocks;
+        cudaMemsetAsync(ds.stats + 2, 0, sizeof(unsigned long long), st);  // the pair kernel's work counter
+        long long blocks = (tasks + (kVisThreads / 32) * kVisChunk - 1) / ((kVisThreads / 32) * kVisChunk);
+        const int resident = vis_resident_blocks();
+        blocks = blocks > resident ? resident : blocks;
         k_vis_pairs<<<(int)blocks, kVisThreads, 0, st>>>(ds);
         const int eb = (ds.n_vert + 7) / 8;  // one warp per row
         k_edges_count<<<eb, 256, 0, st>>>(ds);
@@ -955,6 +976,18 @@ int sssp_grid_blocks() {
 
 int count_kernel_launches_vertex() { return 6; }
 
+int vis_resident_blocks() {
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vis_pairs, kVisThreads, 0);
+        blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+    return blocks;
+}
+
 void launch_vert_maps(const DevScene &ds, cudaStream_t st, float *maps) {
     if (ds.n_vert > 0) k_vert_maps<<<(ds.n_vert + 7) / 8, 256, 0, st>>>(ds, maps);
 }
@@ -970,7 +1003,7 @@ int sssp_batched_grid_blocks() {
 
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st) {
     k_prepare_b<<<152 * 4, 256, 0, st>>>(b);
-    k_vis_pairs_b<<<152 * 16, kVisThreads, 0, st>>>(b);
+    k_vis_pairs_b<<<vis_resident_blocks(), kVisThreads, 0, st>>>(b);
     k_edges_count_b<<<152 * 4, 256, 0, st>>>(b);
     k_edges_scan_b<<<b.n, 1024, 0, st>>>(b);
     k_edges_fill_b<<<152 * 4, 256, 0, st>>>(b);
