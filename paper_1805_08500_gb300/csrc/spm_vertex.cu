@@ -175,14 +175,14 @@ struct PairQ {
     int3 e[kVisThreads / 32][kPairQ];  // (scene, u, v)
 };
 
-// Warps take tasks kVisChunk at a time from a work counter: the walks left
+// Warps take tasks `chunk` at a time from a work counter: the walks left
 // after the filters are few and uneven, and a fixed share per warp leaves
-// SMs idle behind a few long ones.
-constexpr int kVisChunk = 32;
-
+// SMs idle behind a few long ones. A chunk is a run of consecutive words of
+// one row, so the row vertex's data and local map stay in L1; the host sizes
+// it so that every resident warp takes about two chunks.
 template <class Scene, class Task>
-__device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, unsigned long long *work, Scene scene_of_task,
-                                              Task task_of) {
+__device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, int chunk, unsigned long long *work,
+                                              Scene scene_of_task, Task task_of) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int qn = 0;  // warp-uniform queue length
     auto walk = [&](int n) {  // lanes < n walk the last n queued pairs
@@ -201,10 +201,10 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, unsigne
     for (;;) {
         if (t == t_end) {
             unsigned long long c = 0;
-            if (lane == 0) c = atomicAdd(work, (unsigned long long)kVisChunk);
+            if (lane == 0) c = atomicAdd(work, (unsigned long long)chunk);
             t = (long long)__shfl_sync(0xffffffffu, c, 0);
             if (t >= tasks) break;
-            t_end = min(t + kVisChunk, tasks);
+            t_end = min(t + chunk, tasks);
         }
         const long long tt = t++;
         int sc;
@@ -228,10 +228,10 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, unsigne
     if (qn > 0) walk(qn);
 }
 
-__global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds) {
+__global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds, int chunk) {
     __shared__ PairQ q;
     vis_pairs_run(
-        q, (long long)ds.n_vert * ds.vis_words, reinterpret_cast<unsigned long long *>(ds.stats + 2),
+        q, (long long)ds.n_vert * ds.vis_words, chunk, reinterpret_cast<unsigned long long *>(ds.stats + 2),
         [&](int) { return &ds; },
         [&](long long t, int &sc, long long &lt) {
             sc = 0;
@@ -769,7 +769,7 @@ __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs_b(const __grid_constant__ BatchDev b) {
     __shared__ PairQ q;
     vis_pairs_run(
-        q, b.pair_off[b.n], reinterpret_cast<unsigned long long *>(b.counters + 6), [&](int s) { return b.scenes + s; },
+        q, b.pair_off[b.n], 4, reinterpret_cast<unsigned long long *>(b.counters + 6), [&](int s) { return b.scenes + s; },
         [&](long long t, int &sc, long long &lt) {
             sc = scene_of(b.pair_off, b.n, t);
             lt = t - b.pair_off[sc];
@@ -939,10 +939,12 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
         cudaMemsetAsync(ds.vis_bits, 0, sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words, st);
         const long long tasks = (long long)ds.n_vert * ds.vis_words;
         cudaMemsetAsync(ds.stats + 2, 0, sizeof(unsigned long long), st);  // the pair kernel's work counter
-        long long blocks = (tasks + (kVisThreads / 32) * kVisChunk - 1) / ((kVisThreads / 32) * kVisChunk);
         const int resident = vis_resident_blocks();
+        long long blocks = (tasks + (kVisThreads / 32) - 1) / (kVisThreads / 32);  // a task per warp at least
         blocks = blocks > resident ? resident : blocks;
-        k_vis_pairs<<<(int)blocks, kVisThreads, 0, st>>>(ds);
+        const long long per_chunk = tasks / (blocks * (kVisThreads / 32) * 2);
+        const int chunk = (int)(per_chunk < 1 ? 1 : (per_chunk > 32 ? 32 : per_chunk));
+        k_vis_pairs<<<(int)blocks, kVisThreads, 0, st>>>(ds, chunk);
         const int eb = (ds.n_vert + 7) / 8;  // one warp per row
         k_edges_count<<<eb, 256, 0, st>>>(ds);
         k_edges_scan<<<1, 1024, 0, st>>>(ds);
