@@ -136,6 +136,33 @@ def test_maze_4096_sampled(spm, oracle_mod):
     sampled_parity(spm, oracle_mod, scene, 12000, "maze64", window=(2000, 1000, 64))
 
 
+def test_maze_4096_bench_configurations_agree(spm, oracle_mod):
+    """The full-size maze in the launch configurations the benchmark times
+    (the autotuner's pick, and the geometric flood beside the fixpoint with
+    depth maps on 32 x 32 tiles) gives bit for bit the map of the default
+    configuration, which test_maze_4096_sampled checks against the oracle;
+    here a further sample is checked against the oracle directly."""
+    scene = sg.maze(0)
+    s = spm.Scene(scene)
+    d0, p0 = s.compute()
+    s.sync()
+    for tuning in [(3, 256, 32, 1), (3, 32, 32, 1), (1, 256, 32, 1), (2, 32, 32, 0)]:
+        spm.spm_scene_set_tuning(s.handle, *tuning)
+        d, p = s.compute()
+        s.sync()
+        assert torch.equal(p, p0) and torch.equal(d.view(torch.int32), d0.view(torch.int32)), tuning
+    s.autotune()
+    d, p = s.compute()
+    s.sync()
+    assert torch.equal(p, p0) and torch.equal(d.view(torch.int32), d0.view(torch.int32)), s.tuning()
+    o = oracle_mod.Oracle(scene)
+    rng = np.random.default_rng(7)
+    ij = np.stack([rng.integers(0, 4096, 4000), rng.integers(0, 4096, 4000)], 1).astype(np.int32)
+    rd, rp, rd2, rp2 = o.pixels(ij)
+    gd, gp = d.cpu().numpy(), p.cpu().numpy()
+    check_parity(scene, gd[ij[:, 1], ij[:, 0]], gp[ij[:, 1], ij[:, 0]], rd, rp, rd2, "maze4096 bench config", rp2)
+
+
 def test_differentiable_scene_sampled(spm, oracle_mod):
     scene = sg.differentiable(0, n_agents=10)
     sampled_parity(spm, oracle_mod, scene, 30000, "diff2048", window=(700, 900, 64))
