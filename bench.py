@@ -40,7 +40,7 @@ FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
 # DRAM bytes (read + write) of one k_pixels launch, from the ncu capture
 # summarised in profiles/k_pixels_dram_maze4096.md; only for that workload and
 # that kernel version (re-capture after changing the kernel).
-KPIXELS_TRAFFIC = {"maze4096": 107_553_792}
+KPIXELS_TRAFFIC = {"maze4096": 107_700_480}
 
 
 def workload(name: str):
