@@ -322,7 +322,11 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     cudaMemset(ds.stats, 0, sizeof(int32_t) * 4);
     spm::launch_free_mask(ds, nullptr, free_bits);
     if (vert_maps) spm::launch_vert_maps(ds, nullptr, vert_maps);
-    if (cudaPeekAtLastError() != cudaSuccess) ok = false;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        free_all(s);
+        delete s;
+        return set_err(nullptr, SPM_ERR_CUDA, "scene preparation kernels failed to launch");
+    }
     for (cudaEvent_t &e : s->ev)
         if (cudaEventCreate(&e) != cudaSuccess) ok = false;
     if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||

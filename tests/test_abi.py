@@ -79,3 +79,23 @@ def test_missing_library_is_loud(tmp_path, monkeypatch):
     monkeypatch.setattr(m, "LIB_PATH", os.path.join(str(tmp_path), "nope.so"))
     with pytest.raises(m.SpmLibraryMissing):
         m.load_library()
+
+
+def test_null_scene_and_arguments_are_rejected(spm):
+    """Entry points validate their arguments on the host before any CUDA
+    call: a null scene or a null buffer is SPM_ERR_INVALID_ARG."""
+    lib = spm.load_library()
+    host = np.zeros(16, np.float32)
+    buf = host.ctypes.data
+    assert lib.spm_compute_sequential(None, None, buf, buf) == spm.SPM_ERR_INVALID_ARG
+    assert lib.spm_scene_update_sources_device(None, None, buf, buf) == spm.SPM_ERR_INVALID_ARG
+    assert lib.spm_compute(None, None, buf, buf) == spm.SPM_ERR_INVALID_ARG
+    assert lib.spm_query_exact(None, 1.0, 1.0, None, None) == spm.SPM_ERR_INVALID_ARG
+
+
+def test_device_source_update_wants_cuda_float32(spm):
+    """The binding refuses host or non-float32 tensors for the device-side
+    source update before calling the library."""
+    for bad in (torch.zeros(4, dtype=torch.float32), torch.zeros(4, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            spm.spm_scene_update_sources_device(None, None, bad, None)
