@@ -368,6 +368,22 @@ def _crossing_wall_segment(scene):
     raise AssertionError("maze without an inner vertical wall")
 
 
+def test_device_source_update_points_only(spm):
+    """A scene without segment sources moves its points from a device buffer
+    (no segment array) exactly as from the host (the moved point is free:
+    the oracle accepts it)."""
+    scene = sg.plain_rects(2)
+    s_dev, s_host = spm.Scene(scene), spm.Scene(scene)
+    moved = np.asarray(scene.points, np.float32) + np.float32(1.0)
+    s_dev.update_sources_device(_dev(moved.reshape(-1)), None)
+    s_host.update_sources(moved, np.zeros((0, 4), np.float32))
+    d1, p1 = s_dev.compute()
+    d2, p2 = s_host.compute()
+    s_dev.sync()
+    s_host.sync()
+    assert torch.equal(p1, p2) and torch.equal(d1.view(torch.int32), d2.view(torch.int32))
+
+
 def test_device_source_update_rejects_bad_sources(spm):
     """A device-side move is all or nothing: any invalid source (inside or on
     an obstacle, outside the world, non-finite, a zero-length segment, a
@@ -446,7 +462,13 @@ def test_moving_source_frames_in_one_cuda_graph(spm):
         assert torch.equal(outs[f][0].view(torch.int32), ref[f][0].view(torch.int32)), f"frame {f}"
 
 
-@pytest.mark.parametrize("which", ["tiny", "rects", "profiling", "maze", "polys"])
+def _enclosed_scene():
+    walls = [np.array([(20, 20), (60, 20), (60, 24), (20, 24)]), np.array([(20, 56), (60, 56), (60, 60), (20, 60)]),
+             np.array([(20, 20), (24, 20), (24, 60), (20, 60)]), np.array([(56, 20), (60, 20), (60, 60), (56, 60)])]
+    return sg.Scene((80, 80), (80, 80), walls, [(5.0, 5.0)], np.zeros((0, 4)))
+
+
+@pytest.mark.parametrize("which", ["tiny", "rects", "profiling", "maze", "polys", "empty", "enclosed"])
 def test_sequential_schedule(spm, oracle_mod, which):
     """The paper's own schedule (Procedures 1-4: one generator at a time in
     order of cost, every pixel depth-tested) on the GPU: the oracle's
@@ -456,7 +478,9 @@ def test_sequential_schedule(spm, oracle_mod, which):
              "rects": lambda: sg.plain_rects(1),
              "profiling": lambda: sg.profiling_map(8, W=400, N=400),
              "maze": lambda: sg.maze(3, cells=8, N=256),
-             "polys": lambda: sg.plain_polys(4, W=2048, N=256, n_polys=40)}[which]()
+             "polys": lambda: sg.plain_polys(4, W=2048, N=256, n_polys=40),
+             "empty": lambda: sg.empty_scene(W=96, N=96, points=[(10.0, 80.0)], segs=[(20.0, 30.0, 60.0, 55.0)]),
+             "enclosed": _enclosed_scene}[which]()
     s = spm.Scene(scene)
     d, p = s.compute_sequential()
     d_ref, _ = s.compute()
