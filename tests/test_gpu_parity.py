@@ -270,13 +270,19 @@ def test_culling_modes_agree_bit_for_bit(spm, oracle_mod, which):
     assert t["maps"] in (0, 1)
 
 
-def test_batched_matches_individual_computes(spm, oracle_mod):
+@pytest.mark.parametrize("tuning", [None, (3, 256, 0, 1), (1, 32, 0, 1), (2, 32, 0, 0)])
+def test_batched_matches_individual_computes(spm, oracle_mod, tuning):
     """One batch (batched vertex-phase kernels + persistent pixel kernel,
     replayed from a CUDA graph) gives exactly the per-scene results; scenes
-    of uneven size, including a deep maze."""
+    of uneven size, including a deep maze; default culling, and every scene
+    set to the geometric flood with depth maps, to the cone-pruned flood with
+    maps, or to scanning."""
     scenes = sg.batched(4, n_scenes=10, sides=(128, 256), poly_range=(10, 60))
     scenes.append(sg.maze(5, cells=6, N=192))
     objs = [spm.Scene(sc) for sc in scenes]
+    if tuning is not None:
+        for o in objs:
+            spm.spm_scene_set_tuning(o.handle, *tuning)
     single = []
     for o in objs:
         d, p = o.compute()
@@ -542,12 +548,18 @@ def test_agent_gradient_matches_oracle(spm, oracle_mod, src_device):
 
 
 @pytest.mark.gpu
-def test_row_slabs_concatenate_to_the_full_map(spm):
+@pytest.mark.parametrize("which", ["polys", "maze_maps"])
+def test_row_slabs_concatenate_to_the_full_map(spm, which):
     """Two and three tile-aligned row slabs, computed separately into their
     own buffers, reproduce the whole-grid map bit for bit (the per-GPU split
-    of one scene)."""
-    scene = sg.plain_polys(2, W=2048, N=512, n_polys=60)
-    s = spm.Scene(scene)
+    of one scene); also for a maze with the geometric flood and depth maps."""
+    if which == "polys":
+        scene = sg.plain_polys(2, W=2048, N=512, n_polys=60)
+        s = spm.Scene(scene)
+    else:
+        scene = sg.maze(6, cells=12, N=768)
+        s = spm.Scene(scene)
+        spm.spm_scene_set_tuning(s.handle, 3, 256, 32, 1)
     d_full, p_full = s.compute()
     s.sync()
     tile = s.info()["tile"]
