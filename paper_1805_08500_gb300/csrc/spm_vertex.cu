@@ -12,12 +12,16 @@
 //      never carry a shortest path to a pixel); segment interiors reach v
 //      through its perpendicular foot. A vertex whose shortest arrival is not
 //      tangent has an empty shadow cone and is never a parent, so only its
-//      own reported cost can exceed the true one.
+//      own reported cost can exceed the true one. The local depth maps of
+//      the obstacle vertices (k_vert_maps, once per scene) reject most hidden
+//      pairs before the exact test.
 //   2. k_edges_*: the bits become CSR in-lists (by v) with FP64 edge lengths
 //      and out-lists (by u) for frontier marking.
-//   3. k_sssp: a cooperative kernel on every SM runs Jacobi rounds restricted
-//      to the vertices whose in-neighbours changed, until no cost or parent
-//      changes (bounded round count -> status bit).
+//   3. k_sssp_solo: for sparse graphs, one CTA with the graph in shared
+//      memory runs rounds over the vertices whose in-neighbours changed, each
+//      pulling its in-neighbours' current state; k_sssp: otherwise, the same
+//      rounds (synchronous) on every SM with a cooperative launch. Both stop
+//      at the fixpoint (bounded round count -> status bit).
 // Costs are FP64 with explicitly rounded operations, so they match a plain
 // FP64 Dijkstra over the same edges bit for bit.
 #include <cooperative_groups.h>
