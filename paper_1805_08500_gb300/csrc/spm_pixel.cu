@@ -3,8 +3,11 @@
 // arxiv 1805.08500 Sec. 3.1, Procedure 3 ("Cone"): a pixel that sees generator
 // g takes cost(g) + |p - g| when that is smaller than what it holds; Sec. 4:
 // a segment interior reaches p through its perpendicular foot. Instead of one
-// full-screen pass per generator, one CTA owns a 32 x 32 pixel tile and
-// gathers only the generators that can win somewhere in it:
+// full-screen pass per generator, one CTA owns a 32 x 32 (or 16 x 16) pixel
+// tile and gathers only the generators that can win somewhere in it:
+//   * free space: the pixels inside obstacles come from the scene's
+//     free-space mask (built once, one bit per pixel);
+//   * candidates: the tile's list from the flood, or every generator;
 //   * cull: finite cost, shadow cone (or perpendicular strip) meets the tile,
 //     lower bound lb = cost + dist(g, tile) below the tile's current worst;
 //   * order: candidates sorted by lb; the CTA stops once every pixel's best is
@@ -15,6 +18,9 @@
 //     the polygon bins from the tile toward one candidate and drops it when a
 //     single polygon hides all four corners of the tile (the region a convex
 //     polygon hides from a point is convex, so the whole tile is hidden);
+//   * depth maps (when the flood kept them): a pixel nearer than the lower
+//     bound of its bin sees the candidate, one beyond the full-blocking upper
+//     bound does not; only the pixels in between take the exact test below;
 //   * visibility: for each candidate still useful to some pixel, the CTA
 //     builds the list of polygons whose interior meets the hull of (tile, g)
 //     (exact separating-axis filter), then every pixel runs the exact integer
