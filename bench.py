@@ -188,6 +188,77 @@ def cpu_oracle_rate(scene, n_pixels: int, seed: int, nthreads: int):
     return (Nx * Ny) / full / 1e6, t_build + t_pix
 
 
+def _reference_line(args, metric, value, unit, higher, ms_step, config, nthreads, sample):
+    return {
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": higher,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": nthreads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def _oracle_scene_seconds(scene, n_pixels, seed, nthreads):
+    """Oracle time for one whole map: vertex phase + a seeded pixel sample,
+    extrapolated to the grid."""
+    rate, _ = cpu_oracle_rate(scene, n_pixels, seed, nthreads)
+    return scene.grid[0] * scene.grid[1] / (rate * 1e6)
+
+
+def run_reference_other(args, nthreads):
+    """The oracle on the workloads that are not a single map per step."""
+    import oracle
+    steps = range(args.warmup + args.steps)
+    if args.workload == "batched256":
+        scenes, cfg_desc = workload("batched256")
+        k = 8  # scenes sampled per step, extrapolated to the batch
+        per_step = []
+        for st in steps:
+            pick = [scenes[(st * k + i) % len(scenes)] for i in range(k)]
+            t = sum(_oracle_scene_seconds(sc, max(1000, args.ref_pixels // k), st, nthreads) for sc in pick)
+            per_step.append(t * len(scenes) / k)
+        batch_s = float(np.mean(per_step[args.warmup:]))
+        value = len(scenes) / batch_s
+        return _reference_line(args, "SPM batched scenes/s", value, "scenes/s", True, 1e3 * batch_s,
+                               {"workload": args.workload, "scene": cfg_desc}, nthreads,
+                               f"per step: {k} of the {len(scenes)} scenes (oracle vertex phase + "
+                               f"{max(1000, args.ref_pixels // k)} seeded pixels each, extrapolated to their "
+                               f"grids), scaled to the batch")
+    if args.workload == "diff2048_grad":
+        scene, cfg_desc = workload("diff2048_grad")
+        n_ag = 2000  # agents sampled per step, extrapolated to all
+        per_step = []
+        for st in steps:
+            t0 = time.perf_counter()
+            o = oracle.Oracle(scene, nthreads=nthreads)
+            t_build = time.perf_counter() - t0
+            rng = np.random.default_rng(st)
+            sub = np.asarray(scene.agents)[rng.integers(0, len(scene.agents), n_ag)]
+            t1 = time.perf_counter()
+            o.agent_loss_and_grad(sub)
+            per_step.append(t_build + (time.perf_counter() - t1) * len(scene.agents) / n_ag)
+        ms = 1e3 * float(np.mean(per_step[args.warmup:]))
+        return _reference_line(args, "SPM differentiable step ms (forward + backward), 2048^2, 100k agents", ms,
+                               "ms", False, ms, {"workload": args.workload, "scene": cfg_desc}, nthreads,
+                               f"per step: oracle vertex phase + loss and root-link gradients of {n_ag} seeded "
+                               f"agents, extrapolated to all {len(scene.agents)}")
+    # profiling1000: the paper's Profiling3 map, one seeded source per step
+    k = 8
+    srcs = sg.profiling_sources(k, max(1, args.warmup + args.steps))
+    per_step = []
+    for st in steps:
+        sc = sg.profiling_map(k)
+        sc = sg.Scene(sc.world, sc.grid, sc.polys, srcs[st:st + 1], sc.segs)
+        per_step.append(_oracle_scene_seconds(sc, args.ref_pixels, st, nthreads))
+    ms = 1e3 * float(np.mean(per_step[args.warmup:]))
+    return _reference_line(args, "SPM ms per map, Profiling3 (64 squares), 1000^2, one source", ms, "ms", False,
+                           ms, {"workload": args.workload, "scene": "k x k uniform squares (k = 8), 1000^2"},
+                           nthreads, f"per step: one seeded source, oracle vertex phase + {args.ref_pixels} "
+                                     f"seeded pixels extrapolated to the 1000x1000 grid")
+
+
 def run_reference(args, cfg_desc, scene):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -195,6 +266,9 @@ def run_reference(args, cfg_desc, scene):
     import oracle
     oracle.build_oracle()
     nthreads = oracle.default_threads()
+    if args.workload in ("batched256", "diff2048_grad", "profiling1000"):
+        print(json.dumps(run_reference_other(args, nthreads)), flush=True)
+        return
     for w in range(args.warmup):
         cpu_oracle_rate(scene, args.ref_pixels, 1000 + w, nthreads)
     rates, used = [], 0.0
@@ -603,13 +677,14 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
+    if args.impl == "reference":
+        scene, cfg_desc = (None, None) if args.workload == "profiling1000" else workload(args.workload)
+        run_reference(args, cfg_desc, scene)
+        return
     if args.workload == "profiling1000":
         run_profiling(args)
         return
     scene, cfg_desc = workload(args.workload)
-    if args.impl == "reference":
-        run_reference(args, cfg_desc, scene)
-        return
     if args.workload == "batched256":
         run_batched(args, cfg_desc, scene)
         return
