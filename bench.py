@@ -444,8 +444,11 @@ def run_differentiable(args, cfg_desc, scene):
     its adjoint w.r.t. the sources (backward), 100k agents; value = forward +
     backward ms per step (lower is better)."""
     import torch
+    import torch.distributed as dist
     import paper_1805_08500_gb300 as spm
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
+    if world > 1:  # replicas: every rank runs its own step; the time is the slowest rank's
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     s = spm.Scene(scene)
@@ -466,8 +469,10 @@ def run_differentiable(args, cfg_desc, scene):
     for _ in range(args.warmup):
         step()
         spm.spm_agents_backward(s.handle, stream, gp, gs)
-    torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.zero_()
@@ -477,9 +482,11 @@ def run_differentiable(args, cfg_desc, scene):
             spm.spm_agents_backward(s.handle, stream, gp, gs)
             ev[k][2].record(stream)
         torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     s.sync(stream)
-    fwd = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
-    bwd = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
+    fwd = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b, _ in ev])), world, dev)
+    bwd = max_over_ranks(float(np.mean([b.elapsed_time(c) for _, b, c in ev])), world, dev)
     # end to end: FP32 sources up from the host, the step, loss and gradients back
     pts = np.asarray(scene.points, np.float32)
     segs = np.asarray(scene.segs, np.float32)
@@ -499,20 +506,21 @@ def run_differentiable(args, cfg_desc, scene):
         h_out[1:1 + 2 * n_p].copy_(gp, non_blocking=True)
         h_out[1 + 2 * n_p:].copy_(gs, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, world, dev)
     info = s.info()
     line = {"metric": "SPM differentiable step ms (forward + backward), 2048^2, 100k agents",
-            "value": fwd + bwd, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "value": fwd + bwd, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": fwd + bwd, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+i32 (f64 vertex costs, f64 gradient sums)", "data": "synthetic",
             "config": {"workload": "diff2048_grad", "scene": cfg_desc, "agents": int(agents.shape[0]),
-                       "l2": "flushed between timed steps (256 MiB write)", "tuning": tuning},
+                       "l2": "flushed between timed steps (256 MiB write)", "tuning": tuning,
+                       "parallelism": f"replicas x{world} (the slowest rank's step)"},
             "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
             "clocks": clk.summary(),
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(pts.nbytes + segs.nbytes),
                     "d2h_bytes_per_step": int(h_out.numel() * 4)},
             "gpu_launches": (info["kernels_per_compute"] + 4) * args.steps}  # + k_loss, 3 backward kernels
-    if not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build_oracle()
         nthreads = oracle.default_threads()
@@ -523,7 +531,10 @@ def run_differentiable(args, cfg_desc, scene):
         line["cpu_baseline"] = {"value": used * 1e3, "unit": "ms", "cores": nthreads, "kind": "oracle",
                                 "sample": f"the full step: oracle vertex phase + all {len(scene.agents)} agents "
                                           f"+ root-link gradients ({used:.1f} s wall)"}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_dynamic(args, cfg_desc, scene):
@@ -538,8 +549,11 @@ def run_dynamic(args, cfg_desc, scene):
     comes back to the host; the same loop with host-side source updates and
     one CUDA graph of all frames are reported beside it."""
     import torch
+    import torch.distributed as dist
     import paper_1805_08500_gb300 as spm
     world, rank, local = rank_env()
+    if world > 1:  # replicas: every rank runs its own frame stream
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     s = spm.Scene(scene)
@@ -567,6 +581,8 @@ def run_dynamic(args, cfg_desc, scene):
         s.compute(d_out, p_out, stream)
     s.sync(stream)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
@@ -577,8 +593,11 @@ def run_dynamic(args, cfg_desc, scene):
             s.compute(d_out, p_out, stream)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     s.sync(stream)
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    total_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev])), world, dev)
+    ms = total_ms / args.steps  # per frame on the slowest rank
 
     # wall-clock frame loops (no flush: frames follow each other as in an application)
     h_pts = torch.tensor(pts.reshape(F, -1)).pin_memory()
@@ -595,12 +614,14 @@ def run_dynamic(args, cfg_desc, scene):
         spm.spm_agents_forward(s.handle, st, agents, d_out, p_out, loss)
         h_loss[f:f + 1].copy_(loss.reshape(1), non_blocking=True)
 
-    def loop(body):
+    def loop(body):  # whole-job frames/s: every rank's frames over the slowest rank's wall time
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         body()
         torch.cuda.synchronize()
-        return F / (time.perf_counter() - t0)
+        return whole_job_rate(F, world, max_over_ranks(time.perf_counter() - t0, world, dev))
 
     frame(0, stream)
     e2e_fps = loop(lambda: [frame(f, stream) for f in range(F)])
@@ -627,23 +648,25 @@ def run_dynamic(args, cfg_desc, scene):
     s.sync(stream)
     same = bool(torch.equal(device_losses, host_losses) and torch.equal(h_loss, host_losses))
 
-    line = {"metric": "SPM frames/s with sources moving every frame, maze 4096^2", "value": 1e3 / ms,
-            "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+    line = {"metric": "SPM frames/s with sources moving every frame, maze 4096^2",
+            "value": whole_job_rate(args.steps, world, total_ms * 1e-3),
+            "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
             "config": {"workload": "dynamic4096", "scene": cfg_desc, "grid": [Nx, Ny],
                        "motion": "point sources: integer random walk (<= 6 units per axis per frame) in their "
                                  "cells; exit segment: sideways walk within 3 units",
                        "agents": int(agents.shape[0]), "frames": F,
-                       "l2": "flushed between timed frames (256 MiB write)", "tuning": tuning},
-            "mpixel_per_s": npx * 1e3 / ms / 1e6,
+                       "l2": "flushed between timed frames (256 MiB write)", "tuning": tuning,
+                       "parallelism": f"replicas x{world}"},
+            "mpixel_per_s": world * npx * 1e3 / ms / 1e6,
             "clocks": clk.summary(),
             "e2e": {"value": e2e_fps, "unit": "frames/s",
                     "h2d_bytes_per_step": int(4 * (2 * n_p + 4 * n_s)), "d2h_bytes_per_step": 4},
             "e2e_host_update_fps": host_fps, "e2e_cuda_graph_fps": graph_fps,
             "losses_identical_across_loops": same,
             "gpu_launches": (info["kernels_per_compute"] + 1) * args.steps}
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build_oracle()
         nthreads = oracle.default_threads()
@@ -656,6 +679,8 @@ def run_dynamic(args, cfg_desc, scene):
                        f"extrapolated to {Nx}x{Ny} ({used:.1f} s wall on {nthreads} threads)")}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
