@@ -326,6 +326,13 @@ const char *spm_status_string(spm_status status);
  * scene is NULL); valid until the next call on the same thread. */
 const char *spm_last_error(const spm_scene *scene);
 
+/* Test hook for the failure paths (no counterpart in the paper): the n-th
+ * next device allocation of the library fails (n = 0: the next one), as if
+ * the device were out of memory; n < 0 switches it off (the default). The
+ * call that meets the failure returns SPM_ERR_OOM and frees what it had
+ * allocated. Process-wide; has no effect unless called. */
+void spm_debug_fail_alloc_after(int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

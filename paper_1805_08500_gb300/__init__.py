@@ -105,6 +105,7 @@ def load_library():
         "spm_scene_autotune": ([P, P, P], I32),
         "spm_status_string": ([I32], ctypes.c_char_p),
         "spm_last_error": ([P], ctypes.c_char_p),
+        "spm_debug_fail_alloc_after": ([I32], None),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

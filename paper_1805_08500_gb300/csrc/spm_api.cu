@@ -1,8 +1,10 @@
 // spm_api.cu -- the C ABI (include/spm.h): scene lifetime, device buffers,
 // compute entry points and host-side queries.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +50,7 @@ struct spm_scene {
     // the device holds sources moved by spm_scene_update_sources_device that
     // the host copy in hs has not seen yet
     bool host_src_stale = false;
+    bool alloc_failed = false;  // some device allocation of this scene failed
     int seq_blocks = 0;  // co-resident CTAs of the sequential kernel
 };
 
@@ -61,10 +64,33 @@ spm_status set_err(spm_scene *s, spm_status st, const std::string &msg) {
     return st;
 }
 
+// Test hook (spm_debug_fail_alloc_after): the n-th next device allocation
+// fails, so that the failure paths can be exercised; -1 = never.
+std::atomic<int> g_fail_alloc_after{-1};
+
+// Host-side NVTX range over a scope: the phases of a compute show up by name
+// in a profiler's timeline.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <class T>
 T *dalloc(spm_scene *s, size_t n) {
+    for (int k = g_fail_alloc_after.load(); k >= 0; k = g_fail_alloc_after.load())
+        if (g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+            if (k == 0) {
+                s->alloc_failed = true;
+                return nullptr;
+            }
+            break;
+        }
     void *p = nullptr;
-    if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) return nullptr;
+    if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) {
+        cudaGetLastError();  // not sticky: clear it, the caller reports SPM_ERR_OOM
+        s->alloc_failed = true;
+        return nullptr;
+    }
     s->allocs.push_back(p);
     return static_cast<T *>(p);
 }
@@ -174,6 +200,8 @@ const char *spm_status_string(spm_status st) {
 }
 
 const char *spm_last_error(const spm_scene *s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+void spm_debug_fail_alloc_after(int32_t n) { g_fail_alloc_after.store(n < 0 ? -1 : n); }
 
 spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     if (!desc || !out) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null argument");
@@ -311,8 +339,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     ds.vert_maps = vert_maps;
     ds.sssp_blocks = spm::sssp_grid_blocks();
     ds.solo_smem = spm::solo_smem_bytes();
-    for (void *p : s->allocs) ok &= p != nullptr;
-    ok &= ds.vis_bits && ds.in_src && ds.in_len && ds.out_dst && ds.status && ds.stats && ds.gen_ctype;
+    ok &= !s->alloc_failed;  // no kernel below may run on a buffer that failed to allocate
     if (!ok) {
         free_all(s);
         delete s;
@@ -389,12 +416,17 @@ spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent
     cudaStreamIsCapturing(cs, &cap);
     const bool timed = cap == cudaStreamCaptureStatusNone;
     const bool side = s->ds.use_flood && s->ds.flood_mode == 3;  // geometric flood beside the vertex phase
+    NvtxRange range_all("spm_compute");
     if (timed) cudaEventRecord(s->ev[0], cs);
     // the side flood forks once the visibility graph is built and is
     // submitted after the fixpoint kernel, so that the single-CTA fixpoint
     // gets its SM first and the flood fills the others while it runs
-    spm::launch_vertex_phase(s->ds, cs, side ? s->fork : nullptr);
+    {
+        NvtxRange r("spm vertex phase");
+        spm::launch_vertex_phase(s->ds, cs, side ? s->fork : nullptr);
+    }
     if (side) {
+        NvtxRange r("spm flood (side stream)");
         cudaStreamWaitEvent(s->side, s->fork, 0);
         spm::launch_flood(s->ds, s->side);
         cudaEventRecord(s->join, s->side);
@@ -409,7 +441,10 @@ spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent
         cudaMemcpyAsync(s->ds.flood_counts, off, sizeof off, cudaMemcpyHostToDevice, cs);
     }
     if (timed) cudaEventRecord(s->ev[3], cs);
-    spm::launch_pixel_phase(s->ds, cs, dist, parent, tile_row0, tile_row1);
+    {
+        NvtxRange r("spm pixel phase");
+        spm::launch_pixel_phase(s->ds, cs, dist, parent, tile_row0, tile_row1);
+    }
     if (timed) cudaEventRecord(s->ev[2], cs);
     s->ev_valid = timed;
     cudaError_t e = cudaGetLastError();

@@ -597,6 +597,35 @@ def test_edge_capacity_overflow_is_reported(spm):
         s.sync()
 
 
+def test_allocation_failure_is_reported_and_cleaned_up(spm):
+    """An allocation that fails during scene creation (the library's test
+    hook) returns SPM_ERR_OOM, frees what was allocated, and leaves the
+    library usable; so does one in the first host-buffer compute."""
+    scene = sg.plain_rects(0)
+    lib = spm.load_library()
+    try:
+        for k in (0, 1, 7, 25):
+            lib.spm_debug_fail_alloc_after(k)
+            with pytest.raises(spm.SpmError) as e:
+                spm.Scene(scene)
+            assert e.value.status == spm.SPM_ERR_OOM, (k, str(e.value))
+        lib.spm_debug_fail_alloc_after(-1)
+        s = spm.Scene(scene)
+        d_ref, p_ref = s.compute()
+        s.sync()
+        hd = np.zeros(scene.grid[::-1], np.float32)
+        hp = np.zeros(scene.grid[::-1], np.int32)
+        lib.spm_debug_fail_alloc_after(0)  # the staging planes of the first host-buffer compute
+        with pytest.raises(spm.SpmError) as e:
+            spm.spm_compute_host(s.handle, None, hd, hp)
+        assert e.value.status == spm.SPM_ERR_OOM
+        lib.spm_debug_fail_alloc_after(-1)
+        spm.spm_compute_host(s.handle, None, hd, hp)
+        assert np.array_equal(hp, p_ref.cpu().numpy()) and np.array_equal(hd, d_ref.cpu().numpy())
+    finally:
+        lib.spm_debug_fail_alloc_after(-1)
+
+
 def test_compute_captured_in_a_cuda_graph(spm, oracle_mod):
     """spm_compute records into a user's CUDA graph -- including the
     geometric flood on the scene's side stream and the depth maps -- and the
