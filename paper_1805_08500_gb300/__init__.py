@@ -19,7 +19,9 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libspm_gb300.so")
+# the product library; SPM_GB300_LIB may name an instrumentation build of it
+# (build.py --counters / --clocks) for a profiling session
+LIB_PATH = os.environ.get("SPM_GB300_LIB") or os.path.join(_HERE, "libspm_gb300.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "spm.h")
 
 SPM_OK = 0
@@ -563,3 +565,22 @@ class _Lazy:
 
 
 _AgentLoss = _Lazy()
+
+
+def debug_read(kind: str):
+    """Read and clear an instrumentation build's device counters: kind
+    "pixels", "flood" or "vertex" (16 work counters each, SPM_COUNT build) or
+    "pixel_clocks" / "flood_clocks" (8 phase clocks, SPM_TIME build). Raises
+    AttributeError on the product library, which has none."""
+    names = {"pixels": ("spm_debug_counters", 16), "flood": ("spm_debug_counters_flood", 16),
+             "vertex": ("spm_debug_counters_vertex", 16), "pixel_clocks": ("spm_debug_times", 8),
+             "flood_clocks": ("spm_debug_times_flood", 8)}
+    name, n = names[kind]
+    fn = getattr(load_library(), name)
+    buf = (ctypes.c_ulonglong * n)()
+    fn.argtypes = [ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    if fn(ctypes.addressof(buf)) != 0:
+        raise SpmError(SPM_ERR_CUDA, name)
+    return list(buf)
+

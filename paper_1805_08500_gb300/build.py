@@ -2,6 +2,12 @@
 
 Compiles every translation unit of ``csrc/`` with nvcc in parallel and links
 one shared library next to this file. Used by ``__graft_entry__.build()``.
+
+Instrumentation builds (``--counters``: work counters, ``--clocks``: per-phase
+SM clocks) go to separate libraries, libspm_gb300_counters.so and
+libspm_gb300_clocks.so, that add the ``spm_debug_*`` readers; select one for a
+process with the SPM_GB300_LIB environment variable. The product library
+compiles the instrumentation out.
 """
 from __future__ import annotations
 
@@ -32,13 +38,20 @@ def _newest_input() -> float:
     return max(os.path.getmtime(p) for p in paths if os.path.exists(p))
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+VARIANTS = {None: ("", ()), "counters": ("_counters", ("-DSPM_COUNT",)), "clocks": ("_clocks", ("-DSPM_TIME",))}
+
+
+def build(force: bool = False, verbose: bool = False, extra=(), variant=None) -> str:
+    suffix, defs = VARIANTS[variant]
+    lib = os.path.join(HERE, f"libspm_gb300{suffix}.so")
+    bdir = os.path.join(BUILD, variant) if variant else BUILD
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(bdir, exist_ok=True)
+    extra = (*defs, *extra)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -49,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
@@ -60,10 +73,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if missing:
         os.remove(tmp)
         raise RuntimeError("unresolved library symbols: " + "; ".join(missing))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
+    variant = "counters" if "--counters" in sys.argv else ("clocks" if "--clocks" in sys.argv else None)
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=("-Xptxas", "-v") if "--ptxas" in sys.argv else ()))
+                extra=("-Xptxas", "-v") if "--ptxas" in sys.argv else (), variant=variant))

@@ -99,3 +99,16 @@ def test_device_source_update_wants_cuda_float32(spm):
     for bad in (torch.zeros(4, dtype=torch.float32), torch.zeros(4, dtype=torch.float64)):
         with pytest.raises(ValueError):
             spm.spm_scene_update_sources_device(None, None, bad, None)
+
+
+def test_instrumentation_build_exports_its_readers(spm):
+    """The work-counter build (a separate library; the product library
+    compiles the instrumentation out) exports the device counter readers."""
+    from paper_1805_08500_gb300 import build
+    lib = build.build(variant="counters")
+    assert lib != spm.LIB_PATH and os.path.exists(lib)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True).stdout
+    for name in ("spm_debug_counters", "spm_debug_counters_flood", "spm_debug_counters_vertex"):
+        assert f" T {name}\n" in out + "\n", name
+    prod = subprocess.run(["nm", "-D", "--defined-only", spm.LIB_PATH], capture_output=True, text=True).stdout
+    assert " T spm_debug_counters\n" not in prod + "\n"
