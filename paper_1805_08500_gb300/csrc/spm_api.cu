@@ -47,6 +47,11 @@ struct spm_scene {
     // side stream of the geometric flood (flood mode 3), with fork/join events
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // host-buffer computes: copy stream, one event per pixel-pass slab, and
+    // one for the end of the copies
+    cudaStream_t copy = nullptr;
+    cudaEvent_t slab_ev[8] = {};
+    cudaEvent_t copy_done = nullptr;
     // the device holds sources moved by spm_scene_update_sources_device that
     // the host copy in hs has not seen yet
     bool host_src_stale = false;
@@ -115,11 +120,20 @@ void free_all(spm_scene *s) {
             cudaEventDestroy(e);
             e = nullptr;
         }
-    for (cudaEvent_t *e : {&s->fork, &s->join})
+    for (cudaEvent_t *e : {&s->fork, &s->join, &s->copy_done})
         if (*e) {
             cudaEventDestroy(*e);
             *e = nullptr;
         }
+    for (cudaEvent_t &e : s->slab_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (s->copy) {
+        cudaStreamDestroy(s->copy);
+        s->copy = nullptr;
+    }
     if (s->side) {
         cudaStreamDestroy(s->side);
         s->side = nullptr;
@@ -358,8 +372,12 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         if (cudaEventCreate(&e) != cudaSuccess) ok = false;
     if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming) != cudaSuccess)
         ok = false;
+    for (cudaEvent_t &e : s->slab_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) ok = false;
     if (!ok) {
         free_all(s);
         delete s;
@@ -410,7 +428,12 @@ spm_status spm_scene_update_sources_device(spm_scene *s, void *stream, const flo
     return SPM_OK;
 }
 
-spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent, int tile_row0, int tile_row1) {
+// dist / parent: device planes; when dist_host / parent_host are given (a
+// host-buffer compute of the whole grid), the pixel pass runs as row slabs
+// and each slab's rows are copied to the host on the copy stream while the
+// next slab computes; the caller's stream then waits for the copies.
+spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent, int tile_row0, int tile_row1,
+                        float *dist_host = nullptr, int32_t *parent_host = nullptr) {
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(cs, &cap);
@@ -441,9 +464,24 @@ spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent
         cudaMemcpyAsync(s->ds.flood_counts, off, sizeof off, cudaMemcpyHostToDevice, cs);
     }
     if (timed) cudaEventRecord(s->ev[3], cs);
-    {
+    if (!dist_host) {
         NvtxRange r("spm pixel phase");
         spm::launch_pixel_phase(s->ds, cs, dist, parent, tile_row0, tile_row1);
+    } else {
+        NvtxRange r("spm pixel phase with host copies");
+        const int rows = tile_row1 - tile_row0, nslab = std::min(rows, (int)(sizeof s->slab_ev / sizeof s->slab_ev[0]));
+        for (int k = 0; k < nslab; ++k) {
+            const int t0 = tile_row0 + rows * k / nslab, t1 = tile_row0 + rows * (k + 1) / nslab;
+            spm::launch_pixel_phase(s->ds, cs, dist, parent, t0, t1);
+            cudaEventRecord(s->slab_ev[k], cs);
+            cudaStreamWaitEvent(s->copy, s->slab_ev[k], 0);
+            const size_t r0 = (size_t)t0 * s->ds.tile, r1 = std::min((size_t)t1 * s->ds.tile, (size_t)s->hs.Ny);
+            const size_t off = r0 * s->hs.Nx, cnt = (r1 - r0) * s->hs.Nx;
+            cudaMemcpyAsync(dist_host + off, dist + off, sizeof(float) * cnt, cudaMemcpyDeviceToHost, s->copy);
+            cudaMemcpyAsync(parent_host + off, parent + off, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, s->copy);
+        }
+        cudaEventRecord(s->copy_done, s->copy);
+        cudaStreamWaitEvent(cs, s->copy_done, 0);
     }
     if (timed) cudaEventRecord(s->ev[2], cs);
     s->ev_valid = timed;
@@ -515,12 +553,8 @@ spm_status spm_compute_host(spm_scene *s, void *stream, float *dist_host, int32_
         s->stage_par = dalloc<int32_t>(s, npx);
         if (!s->stage_dist || !s->stage_par) return set_err(s, SPM_ERR_OOM, "staging allocation failed");
     }
-    st = spm_compute(s, stream, s->stage_dist, s->stage_par);
+    st = compute_impl(s, stream, s->stage_dist, s->stage_par, 0, s->ds.tiles_y, dist_host, parent_host);
     if (st != SPM_OK) return st;
-    cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(dist_host, s->stage_dist, sizeof(float) * npx, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
-        cudaMemcpyAsync(parent_host, s->stage_par, sizeof(int32_t) * npx, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
-        return set_err(s, SPM_ERR_CUDA, "result copy failed");
     return spm_scene_sync(s, stream);
 }
 

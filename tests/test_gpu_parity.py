@@ -626,6 +626,31 @@ def test_allocation_failure_is_reported_and_cleaned_up(spm):
         lib.spm_debug_fail_alloc_after(-1)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_compute_matches_device_compute(spm, pinned):
+    """spm_compute_host (the pixel pass in row slabs, each copied to the host
+    while the next one computes) writes the device compute's map bit for
+    bit, into pinned or pageable host memory."""
+    scene = sg.maze(6, cells=12, N=768)
+    s = spm.Scene(scene)
+    spm.spm_scene_set_tuning(s.handle, 3, 256, 32, 1)
+    d_ref, p_ref = s.compute()
+    s.sync()
+    Ny, Nx = scene.grid[1], scene.grid[0]
+    if pinned:
+        hd = torch.full((Ny, Nx), -1.0).pin_memory()
+        hp = torch.full((Ny, Nx), -9, dtype=torch.int32).pin_memory()
+    else:
+        hd = np.full((Ny, Nx), -1.0, np.float32)
+        hp = np.full((Ny, Nx), -9, np.int32)
+    for _ in range(2):
+        spm.spm_compute_host(s.handle, None, hd, hp)
+        gd = hd.numpy() if pinned else hd
+        gp = hp.numpy() if pinned else hp
+        assert np.array_equal(gp, p_ref.cpu().numpy())
+        assert np.array_equal(gd.view(np.int32), d_ref.cpu().numpy().view(np.int32))
+
+
 def test_compute_captured_in_a_cuda_graph(spm, oracle_mod):
     """spm_compute records into a user's CUDA graph -- including the
     geometric flood on the scene's side stream and the depth maps -- and the
