@@ -553,7 +553,18 @@ spm_status spm_compute_host(spm_scene *s, void *stream, float *dist_host, int32_
         s->stage_par = dalloc<int32_t>(s, npx);
         if (!s->stage_dist || !s->stage_par) return set_err(s, SPM_ERR_OOM, "staging allocation failed");
     }
-    st = compute_impl(s, stream, s->stage_dist, s->stage_par, 0, s->ds.tiles_y, dist_host, parent_host);
+    // page-locked host buffers are device-addressable: the pixel pass then
+    // writes the map straight into them (no staging planes, no copies)
+    cudaPointerAttributes ad{}, ap{};
+    const bool direct = cudaPointerGetAttributes(&ad, dist_host) == cudaSuccess &&
+                        cudaPointerGetAttributes(&ap, parent_host) == cudaSuccess && ad.type == cudaMemoryTypeHost &&
+                        ap.type == cudaMemoryTypeHost && ad.devicePointer && ap.devicePointer;
+    cudaGetLastError();  // a pageable pointer is not an error here
+    if (direct)
+        st = compute_impl(s, stream, static_cast<float *>(ad.devicePointer), static_cast<int32_t *>(ap.devicePointer),
+                          0, s->ds.tiles_y);
+    else
+        st = compute_impl(s, stream, s->stage_dist, s->stage_par, 0, s->ds.tiles_y, dist_host, parent_host);
     if (st != SPM_OK) return st;
     return spm_scene_sync(s, stream);
 }
@@ -743,8 +754,8 @@ spm_status spm_query_parent(spm_scene *s, float x, float y, int32_t *parent, flo
     j = std::min(j, s->hs.Ny - 1);
     const size_t idx = (size_t)j * s->hs.Nx + i;
     if (cudaStreamSynchronize(s->last_stream) != cudaSuccess ||
-        cudaMemcpy(parent, s->last_parent + idx, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(dist, s->last_dist + idx, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(parent, s->last_parent + idx, sizeof(int32_t), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(dist, s->last_dist + idx, sizeof(float), cudaMemcpyDefault) != cudaSuccess)
         return set_err(s, SPM_ERR_CUDA, "query copy failed");
     return SPM_OK;
 }
