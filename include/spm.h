@@ -154,8 +154,12 @@ spm_status spm_compute_rows(spm_scene *scene, void *stream, int32_t row0, int32_
 spm_status spm_compute_sequential(spm_scene *scene, void *stream, float *dist_dev,
                                   int32_t *parent_dev);
 
-/* spm_compute on HOST buffers: copies the outputs back before returning
- * (synchronous on `stream`). For callers that keep the field on the host. */
+/* spm_compute on HOST buffers, complete when it returns (synchronous on
+ * `stream`). For callers that keep the field on the host. Page-locked
+ * buffers (cudaHostAlloc, torch pin_memory) receive the map directly from the
+ * pixel pass. Pageable ones receive it through device staging planes,
+ * allocated on the first call, in row slabs copied while the next slab
+ * computes. */
 spm_status spm_compute_host(spm_scene *scene, void *stream, float *dist_host,
                             int32_t *parent_host);
 
