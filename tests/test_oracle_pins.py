@@ -14,7 +14,10 @@ x/y, a wrong cone or segment-foot rule) fails at least one of them:
   vertex costs >= straight-line distance to the nearest source;
 * the cone restriction changes no distance;
 * agreement with a second independent algorithm (Procedures 1-4 restated
-  sequentially with another exact visibility method) and with Floyd-Warshall.
+  sequentially with another exact visibility method) and with Floyd-Warshall;
+* the runner-up key (which decides the near-tie exemptions of the GPU parity
+  tests) and point queries off the pixel centres, against a brute force over
+  every generator with that independent visibility and a restated cone.
 """
 import json
 import math
@@ -433,3 +436,173 @@ def test_point_queries_at_pixel_centres_are_the_field(oracle_mod):
     assert np.array_equal(np.isfinite(pd), fin)
     assert np.array_equal(pd[fin], d[ij[:, 1], ij[:, 0]][fin])
     assert np.array_equal(pp[fin], p[ij[:, 1], ij[:, 0]][fin])
+
+
+# ---------------------------------------------------------------------------
+# runner-up keys and off-centre point queries, against a brute force built on
+# the sequential restatement's exact visibility and an independent statement
+# of the shadow cone
+# ---------------------------------------------------------------------------
+
+def _angle_key(d, e):
+    """Counter-clockwise angle of e measured from d, as an exactly comparable
+    key: (half, tie-breaker) with half 0 for [0, pi), 1 for [pi, 2 pi)."""
+    c = d[0] * e[1] - d[1] * e[0]
+    dot = d[0] * e[0] + d[1] * e[1]
+    half = 0 if (c > 0 or (c == 0 and dot > 0)) else 1
+    return half, e
+
+
+def _ccw_less(d, a, b):
+    """Is the counter-clockwise angle from d to a smaller than to b?"""
+    ha, _ = _angle_key(d, a)
+    hb, _ = _angle_key(d, b)
+    if ha != hb:
+        return ha < hb
+    return a[0] * b[1] - a[1] * b[0] > 0
+
+
+class _BruteField:
+    """Best and runner-up valid generator at arbitrary lattice points, by
+    enumerating every generator. Validity follows the definition of the map
+    (Sec. 3): the generator is reached, the point is free, the point sees it
+    (Sequential's exact visibility, a different method from the C oracle's),
+    and for an obstacle vertex the point lies in the vertex's shadow cone.
+    The cone is restated here from its definition: with arrival direction d
+    (from the parent, or perpendicular to a segment source) and the two
+    obstacle edges at the vertex, the cone is empty when the edges lie on
+    both sides of d; otherwise it is the closed sector swept from d, turning
+    toward the edges, up to the first edge met (a ray when that edge runs
+    along d). Vertex costs and parents come from the oracle's Dijkstra, which
+    Floyd-Warshall and the sequential procedures pin."""
+
+    def __init__(self, scene, o):
+        from oracle.sequential import Sequential
+        self.q = Sequential(scene)
+        self.o = o
+        self.scene = scene
+        assert o.S % self.q.S == 0
+        self.f = o.S // self.q.S  # oracle lattice units per sequential lattice unit
+        n = len(self.q.ent)
+        assert n == o.n_gen
+        # obstacle edges at each vertex (pairwise disjoint convex polygons)
+        self.edges = {}
+        g = self.q.n_src
+        for P in self.q.polys:
+            m = len(P)
+            for i in range(m):
+                v, nx, pv = P[i], P[(i + 1) % m], P[(i - 1) % m]
+                self.edges[g] = ((nx[0] - v[0], nx[1] - v[1]), (pv[0] - v[0], pv[1] - v[1]))
+                g += 1
+
+    def _arrival(self, g):
+        u = int(self.o.parent[g])
+        v = self.q.ent[g][1]
+        kind, ulat, _, k = self.q.ent[u]
+        if kind == "segment":
+            A, B = self.q.seg_lat[k]
+            ux, uy = B[0] - A[0], B[1] - A[1]
+            side = ux * (v[1] - A[1]) - uy * (v[0] - A[0])
+            return (-uy, ux) if side > 0 else (uy, -ux)
+        return (v[0] - ulat[0], v[1] - ulat[1])
+
+    def in_cone(self, g, w):
+        d = self._arrival(g)
+        ea, eb = self.edges[g]
+        sa = np.sign(d[0] * ea[1] - d[1] * ea[0])
+        sb = np.sign(d[0] * eb[1] - d[1] * eb[0])
+        if sa * sb < 0 or (sa == 0 and sb == 0):
+            return False
+        s = sa if sa != 0 else sb
+        if s > 0:  # turning counter-clockwise: the edge of smaller ccw angle from d
+            e1 = ea if _ccw_less(d, ea, eb) else eb
+        else:  # turning clockwise: mirror both to reuse the ccw comparison
+            m = lambda x: (x[0], -x[1])  # noqa: E731
+            e1 = ea if _ccw_less(m(d), m(ea), m(eb)) else eb
+        c1 = d[0] * e1[1] - d[1] * e1[0]
+        if c1 == 0 and d[0] * e1[0] + d[1] * e1[1] > 0:  # the edge runs straight on: a ray
+            return d[0] * w[1] - d[1] * w[0] == 0 and d[0] * w[0] + d[1] * w[1] >= 0
+        return (s * (d[0] * w[1] - d[1] * w[0]) >= 0 and s * (w[0] * e1[1] - w[1] * e1[0]) >= 0)
+
+    def keys(self, q_lat, q_true, use_cone=True):
+        """Sorted (key, id) of every valid generator at the point."""
+        if not self.q._free(q_lat):
+            return []
+        out = []
+        for g, (kind, glat, _, _) in enumerate(self.q.ent):
+            c = self.o.cost[g]
+            if not np.isfinite(c):
+                continue
+            if use_cone and kind == "vertex":
+                w = (q_lat[0] - glat[0], q_lat[1] - glat[1])
+                if not self.in_cone(g, w):
+                    continue
+            r = self.q._reach(g, q_lat, q_true)
+            if r is None:
+                continue
+            out.append((c + r, g))
+        out.sort()
+        return out
+
+
+def _best_two(keys):
+    if not keys:
+        return math.inf, -1, math.inf, -1
+    d1, p1 = keys[0]
+    rest = [k for k in keys[1:] if k[1] != p1]
+    return (d1, p1) + (rest[0] if rest else (math.inf, -1))
+
+
+@pytest.mark.parametrize("seed,n_segs,use_cone", [(0, 0, True), (1, 1, True), (3, 2, True), (2, 1, False)])
+def test_runner_up_matches_brute_force(oracle_mod, seed, n_segs, use_cone):
+    """orc_pixels' second-best key and generator (which decide every near-tie
+    exemption of the parity tests) at every pixel centre of tiny scenes equal
+    the brute-force runner-up: best valid key among generators with an id
+    other than the best one's."""
+    s = sg.tiny(seed, W=32, N=32, n_polys=3, n_points=1 + (seed % 2), n_segs=n_segs)
+    o = oracle_mod.Oracle(s, use_cone=use_cone)
+    bf = _BruteField(s, o)
+    d, p, d2, p2 = o.field()
+    (Wx, Wy), (Nx, Ny) = s.world, s.grid
+    S = bf.q.S
+    n_seconds = 0
+    for j in range(Ny):
+        for i in range(Nx):
+            q = ((2 * i + 1) * S * Wx // (2 * Nx), (2 * j + 1) * S * Wy // (2 * Ny))
+            qt = ((i + 0.5) * Wx / Nx, (j + 0.5) * Wy / Ny)
+            b1, g1, b2, g2 = _best_two(bf.keys(q, qt, use_cone))
+            for got, want in ((d[j, i], b1), (d2[j, i], b2)):
+                assert (math.isinf(got) and math.isinf(want)) or abs(got - want) <= 1e-12 * max(want, 1.0), \
+                    (i, j, got, want)
+            if math.isfinite(b2):
+                n_seconds += 1
+                assert b2 >= b1
+            if math.isfinite(b1) and (not math.isfinite(b2) or b2 - b1 > 1e-9):
+                assert p[j, i] == g1, (i, j)
+            # a unique runner-up (no third key within rounding) fixes the id too
+            ks = [k for k in bf.keys(q, qt, use_cone) if k[1] not in (g1,)]
+            if len(ks) >= 1 and (len(ks) == 1 or ks[1][0] - ks[0][0] > 1e-9) and b2 - b1 > 1e-9:
+                assert p2[j, i] == g2, (i, j, p2[j, i], g2)
+    assert n_seconds >= 300
+
+
+@pytest.mark.parametrize("seed,n_segs", [(0, 0), (1, 1), (3, 2)])
+def test_point_queries_off_centre_match_brute_force(oracle_mod, seed, n_segs):
+    """orc_points at lattice points that are not pixel centres (the exact
+    point queries of Sec. 6) gives the brute-force best key and generator."""
+    s = sg.tiny(seed, W=32, N=32, n_polys=3, n_points=1 + (seed % 2), n_segs=n_segs)
+    o = oracle_mod.Oracle(s)
+    bf = _BruteField(s, o)
+    S = bf.q.S
+    rng = np.random.default_rng(17 + seed)
+    pts = rng.integers(0, s.world[0] * S, (400, 2))
+    pts = pts[(pts % (S // 2 if S > 1 else 1)).any(axis=1) | (S == 1)]  # off the pixel centres
+    od, op = o.points(pts * bf.f)
+    checked = 0
+    for (x, y), dd, pp in zip(pts.tolist(), od, op):
+        b1, g1, b2, _ = _best_two(bf.keys((x, y), (x / S, y / S)))
+        assert (math.isinf(dd) and math.isinf(b1)) or abs(dd - b1) <= 1e-12 * max(b1, 1.0), (x, y, dd, b1)
+        if math.isfinite(b1) and (not math.isfinite(b2) or b2 - b1 > 1e-9):
+            assert pp == g1, (x, y)
+            checked += 1
+    assert checked > 200
