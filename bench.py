@@ -731,12 +731,27 @@ def main():
 
     import paper_1805_08500_gb300 as spm
 
-    s = spm.Scene(scene)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = spm.Scene(scene)  # returns once the scene's device structures are built
+    create_ms = (time.perf_counter() - t0) * 1e3
     if args.culling == "autotune":
         tuning = s.autotune(cache_key=args.workload)  # set-up, not timed
     else:
         spm.spm_scene_set_tuning(s.handle, {"auto": 0, "flood": 1, "scan": 2}[args.culling], 32)
         tuning = dict(s.tuning(), source="fixed")
+    # cold start: a fresh scene with the chosen tuning, created and computed once
+    # (scene creation, the obstacles' static structures and the first map)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s_cold = spm.Scene(scene)
+    spm.spm_scene_set_tuning(s_cold.handle, tuning["flood_mode"], tuning["hidden_chunk"], tuning["tile"],
+                             tuning["maps"])
+    s_cold.compute()
+    s_cold.sync()
+    cold_ms = (time.perf_counter() - t0) * 1e3
+    s_cold.close()
+    del s_cold
     Nx, Ny = scene.grid
     npx = Nx * Ny
     d_out, p_out = s.empty_outputs()
@@ -808,6 +823,11 @@ def main():
                    "tuning": tuning,
                    "parallelism": f"replicas x{world}"},
         "phases_ms": {"vertex": vert_ms, "cull": cull_ms, "pixel": pix_ms},
+        "setup_ms": {"scene_create": create_ms, "cold_create_and_first_compute": cold_ms,
+                     "note": "host wall clock, outside the timed steps: validation, lattice, device "
+                             "upload and the obstacles' static structures (free-space mask, vertex depth "
+                             "maps, obstacle-vertex visibility; the obstacle vertices' flood at the first "
+                             "compute)"},
         "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": KPIXELS_TRAFFIC.get(args.workload),

@@ -57,6 +57,10 @@ struct spm_scene {
     bool host_src_stale = false;
     bool alloc_failed = false;  // some device allocation of this scene failed
     int seq_blocks = 0;  // co-resident CTAs of the sequential kernel
+    // the static part of the geometric flood (obstacle vertices) is on the
+    // device for this tile size and depth-map setting
+    bool flood_static_ok = false;
+    int flood_static_tile = 0, flood_static_maps = 0;
 };
 
 namespace {
@@ -292,6 +296,13 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     }
     ds.vis_words = (hs.n_gen + 31) / 32;
     ds.vis_bits = dalloc<uint32_t>(s, (size_t)hs.n_vert * ds.vis_words);
+    // obstacle-vertex pairs are tested once, here; a compute tests the
+    // source columns only
+    uint32_t *vis_static = dalloc<uint32_t>(s, (size_t)hs.n_vert * ds.vis_words);
+    ds.vis_static = vis_static;
+    ds.pair_words = (hs.n_src + 31) / 32;
+    ds.pair_u0 = 0;
+    ds.pair_u1 = hs.n_src;
     ds.in_start = dalloc<int32_t>(s, hs.n_vert + 1);
     ds.out_start = dalloc<int32_t>(s, hs.n_gen + 1);
     ds.out_fill = dalloc<int32_t>(s, hs.n_gen);
@@ -342,6 +353,8 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
             if (ds.gen_map_ok) cudaMemset(ds.gen_map_ok, 0, hs.n_gen);
         }
         ds.flood_counts = dalloc<int32_t>(s, 4);
+        ds.static_tile_count = ds.use_flood ? dalloc<int32_t>(s, ntiles) : nullptr;
+        ds.static_counts = ds.use_flood ? dalloc<int32_t>(s, 4) : nullptr;
     }
     ds.free_words = (hs.Nx + 31) / 32;
     uint32_t *free_bits = dalloc<uint32_t>(s, (size_t)hs.Ny * ds.free_words);
@@ -363,6 +376,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     cudaMemset(ds.stats, 0, sizeof(int32_t) * 4);
     spm::launch_free_mask(ds, nullptr, free_bits);
     if (vert_maps) spm::launch_vert_maps(ds, nullptr, vert_maps);
+    spm::launch_vis_static(ds, nullptr, vis_static);  // after the local depth maps it filters with
     if (cudaPeekAtLastError() != cudaSuccess) {
         free_all(s);
         delete s;
@@ -450,15 +464,27 @@ spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent
     }
     if (side) {
         NvtxRange r("spm flood (side stream)");
+        // the obstacle vertices' flood depends on the obstacles alone: built
+        // once for this tile size and map setting, then only the sources flood
+        const bool maps = s->ds.use_maps && s->ds.gen_maps;
+        const bool reuse = s->flood_static_ok && s->flood_static_tile == s->ds.tile &&
+                           s->flood_static_maps == (int)maps && s->ds.static_tile_count;
         cudaStreamWaitEvent(s->side, s->fork, 0);
-        spm::launch_flood(s->ds, s->side);
+        spm::launch_flood(s->ds, s->side,
+                          !s->ds.static_tile_count ? spm::FloodStatic::kNone
+                          : reuse                  ? spm::FloodStatic::kReuse
+                                                   : spm::FloodStatic::kBuild);
         cudaEventRecord(s->join, s->side);
+        s->flood_static_ok = s->ds.static_tile_count != nullptr;
+        s->flood_static_tile = s->ds.tile;
+        s->flood_static_maps = (int)maps;
     }
     if (timed) cudaEventRecord(s->ev[1], cs);
     if (side) {
         cudaStreamWaitEvent(cs, s->join, 0);
     } else if (s->ds.use_flood) {
         spm::launch_flood(s->ds, cs);
+        s->flood_static_ok = false;  // the lists and maps now hold this flood's
     } else {
         static const int32_t off[4] = {0, 0, 1, 0};
         cudaMemcpyAsync(s->ds.flood_counts, off, sizeof off, cudaMemcpyHostToDevice, cs);
@@ -629,14 +655,15 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     b->scenes.assign(scenes, scenes + n);
     b->device = dev;
     std::vector<spm::DevScene> descs(n);
-    std::vector<long long> pair_off(n + 1, 0);
+    std::vector<long long> pair_off(n + 1, 0), bits_off(n + 1, 0);
     std::vector<int32_t> vert_off(n + 1, 0), gen_off(n + 1, 0), order(n), tile_off(n + 1, 0);
     std::vector<float *> dv(dist, dist + n);
     std::vector<int32_t *> pv(parent, parent + n);
     int max_gen = 0;
     for (int k = 0; k < n; ++k) {
         descs[k] = scenes[k]->ds;
-        pair_off[k + 1] = pair_off[k] + (long long)descs[k].n_vert * descs[k].vis_words;
+        pair_off[k + 1] = pair_off[k] + (long long)descs[k].n_vert * descs[k].pair_words;
+        bits_off[k + 1] = bits_off[k] + (long long)descs[k].n_vert * descs[k].vis_words;
         vert_off[k + 1] = vert_off[k] + descs[k].n_vert;
         gen_off[k + 1] = gen_off[k] + descs[k].n_gen;
         max_gen = std::max(max_gen, descs[k].n_gen);
@@ -652,6 +679,7 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     bd.n = n;
     bd.scenes = bupload(b, descs, ok);
     bd.pair_off = bupload(b, pair_off, ok);
+    bd.bits_off = bupload(b, bits_off, ok);
     bd.vert_off = bupload(b, vert_off, ok);
     bd.gen_off = bupload(b, gen_off, ok);
     bd.order = bupload(b, order, ok);
@@ -717,7 +745,9 @@ spm_status spm_batch_compute(spm_batch *b, void *stream) {
     for (size_t k = 0; k < b->scenes.size(); ++k) {
         spm_scene *s = b->scenes[k];
         s->last_dist = nullptr;  // queries need a single-scene compute
+        s->last_parent = nullptr;
         s->ev_valid = false;
+        s->flood_static_ok = false;  // the batched flood rewrote the scene's lists
     }
     return SPM_OK;
 }

@@ -376,8 +376,9 @@ __device__ __forceinline__ bool flood_declined(const DevScene &ds) {
 // Resident CTAs take generators from a work counter (flood_counts[3]) as
 // they finish: flood depths vary widely, so a fixed stride would leave the
 // kernel waiting for the CTAs that drew several deep generators.
+// Generators [g0, g1) are flooded.
 template <bool MAPS>
-__global__ void __launch_bounds__(kFloodThreads, MAPS ? 6 : 8) k_flood(DevScene ds) {
+__global__ void __launch_bounds__(kFloodThreads, MAPS ? 6 : 8) k_flood(DevScene ds, int g0, int g1) {
     extern __shared__ unsigned fdyn[];
     __shared__ FloodSmem sm;
     __shared__ int next_g;
@@ -386,13 +387,36 @@ __global__ void __launch_bounds__(kFloodThreads, MAPS ? 6 : 8) k_flood(DevScene 
         return;
     }
     for (;;) {
-        if (threadIdx.x == 0) next_g = atomicAdd(&ds.flood_counts[3], 1);
+        if (threadIdx.x == 0) next_g = g0 + atomicAdd(&ds.flood_counts[3], 1);
         __syncthreads();
         const int g = next_g;
         __syncthreads();  // next_g is rewritten for the next generator
-        if (g >= ds.n_gen) break;
+        if (g >= g1) break;
         flood_one<MAPS>(ds, sm, fdyn, g);
     }
+}
+
+// The static part of the lists (the obstacle vertices' flood) is kept after
+// that flood, or restored before the sources' flood; either way the work
+// counter starts again from zero.
+__global__ void k_flood_static(DevScene ds, int keep) {
+    const int ntiles = ds.tiles_x * ds.tiles_y;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        if (keep) ds.static_tile_count[t] = ds.tile_count[t];
+        else ds.tile_count[t] = ds.static_tile_count[t];
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 4) {
+        const int k = threadIdx.x;
+        if (keep) {
+            if (k < 3) ds.static_counts[k] = ds.flood_counts[k];
+        } else {
+            ds.flood_counts[k] = k < 3 ? ds.static_counts[k] : 0;
+        }
+    }
+}
+
+__global__ void k_flood_counter_reset(DevScene ds) {
+    if (threadIdx.x == 0) ds.flood_counts[3] = 0;
 }
 
 // Batched form: every (scene, generator) of the batch, one CTA each.
@@ -500,24 +524,41 @@ bool flood_possible(int tiles, int polys) {
     return flood_smem_bytes(tiles, polys, true) + sizeof(FloodSmem) <= 200 * 1024;
 }
 
-void launch_flood(const DevScene &ds, cudaStream_t st) {
+void launch_flood(const DevScene &ds, cudaStream_t st, FloodStatic how) {
     const int ntiles = ds.tiles_x * ds.tiles_y;
     if (ds.flood_mode == 2) {  // never: the pixel pass scans every generator
         static const int32_t off[4] = {0, 0, 1, 0};
         cudaMemcpyAsync(ds.flood_counts, off, sizeof off, cudaMemcpyHostToDevice, st);
         return;
     }
-    cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
-    cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
     const bool maps = ds.use_maps && ds.gen_maps;
     const size_t smem = flood_smem_bytes(ntiles, ds.n_poly, maps);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, maps ? k_flood<true> : k_flood<false>, kFloodThreads, smem);
-    const int blocks = max(1, min(max(sms, 1) * max(per_sm, 1), ds.n_gen));  // resident CTAs only
-    if (maps) k_flood<true><<<blocks, kFloodThreads, smem, st>>>(ds);
-    else k_flood<false><<<blocks, kFloodThreads, smem, st>>>(ds);
+    auto flood = [&](int g0, int g1) {
+        if (g1 <= g0) return;
+        const int blocks = max(1, min(max(sms, 1) * max(per_sm, 1), g1 - g0));  // resident CTAs only
+        if (maps) k_flood<true><<<blocks, kFloodThreads, smem, st>>>(ds, g0, g1);
+        else k_flood<false><<<blocks, kFloodThreads, smem, st>>>(ds, g0, g1);
+    };
+    const int sblocks = max(1, min((ntiles + 255) / 256, 152));
+    if (how == FloodStatic::kReuse) {
+        k_flood_static<<<sblocks, 256, 0, st>>>(ds, 0);
+        flood(0, ds.n_src);
+    } else {
+        cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
+        cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
+        if (how == FloodStatic::kBuild) {
+            flood(ds.n_src, ds.n_gen);  // the obstacle vertices first: their pairs lead the buffer
+            k_flood_static<<<sblocks, 256, 0, st>>>(ds, 1);
+            k_flood_counter_reset<<<1, 32, 0, st>>>(ds);
+            flood(0, ds.n_src);
+        } else {
+            flood(0, ds.n_gen);
+        }
+    }
     k_tiles_scan<<<1, 1024, 0, st>>>(ds);
     k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds);
 }

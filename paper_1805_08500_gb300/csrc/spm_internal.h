@@ -107,6 +107,12 @@ struct DevScene {
     // vertex phase
     uint32_t *vis_bits;                // n_vert rows x vis_words
     int32_t vis_words;
+    // bits of the obstacle-vertex pairs alone, same layout (built once per
+    // scene: obstacles never move; null when every compute tests every pair)
+    const uint32_t *vis_static;
+    // the pair kernel's range: words 0..pair_words-1 of every row, generators
+    // u in [pair_u0, pair_u1) (with vis_static: the source columns only)
+    int32_t pair_words, pair_u0, pair_u1;
     int32_t *in_start;                 // n_vert + 1 (by target vertex)
     int32_t *in_src;                   // E
     double *in_len;                    // E
@@ -151,7 +157,14 @@ struct DevScene {
     uint8_t *gen_map_ok;
     int32_t pair_cap;
     int32_t *glob_list;                // generators every tile scans
-    int32_t *flood_counts;             // [0] pairs, [1] global list size, [2] overflow
+    int32_t *flood_counts;             // [0] pairs, [1] global list size, [2] overflow, [3] work counter
+    // the geometric flood (mode 3) of the obstacle-vertex generators depends
+    // on the obstacles alone: its per-tile counts and flood_counts[0..2] are
+    // kept here, with its pairs at the front of `pairs`, its global entries
+    // at the front of `glob_list` and its depth maps in gen_maps, so that a
+    // compute floods only the sources
+    int32_t *static_tile_count;        // ntiles (small-tile sizing)
+    int32_t *static_counts;            // 4
     // differentiable form
     float *agent_accum;                // scratch for deterministic reductions
     const int32_t *agents;
@@ -163,7 +176,8 @@ struct BatchDev {
     int32_t n;                         // scenes
     const DevScene *scenes;            // n descriptors (device memory)
     // prefix offsets over scenes (n + 1 entries each)
-    const long long *pair_off;         // warp tasks of the visibility pairs: n_vert * vis_words
+    const long long *pair_off;         // warp tasks of the visibility pairs: n_vert * pair_words
+    const long long *bits_off;         // words of the visibility bit matrices: n_vert * vis_words
     const int32_t *vert_off;           // obstacle-vertex generators
     const int32_t *gen_off;            // generators
     // pixel pass: scenes in processing order (most tiles first)
@@ -189,7 +203,14 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
 // pixel kernel over the tiles of tile rows [tile_row0, tile_row1)
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1);
-void launch_flood(const DevScene &ds, cudaStream_t st);
+// flood of the per-tile candidate lists. FloodStatic::kNone floods every
+// generator; kBuild (geometric mode) floods the obstacle vertices, keeps
+// their lists as the static part, then floods the sources; kReuse restores
+// the static part and floods the sources only.
+enum class FloodStatic { kNone, kBuild, kReuse };
+void launch_flood(const DevScene &ds, cudaStream_t st, FloodStatic how = FloodStatic::kNone);
+// visibility bits of the obstacle-vertex pairs into ds.vis_static (once per scene)
+void launch_vis_static(const DevScene &ds, cudaStream_t st, uint32_t *vis_static);
 // free-space mask of the pixel centres (once per scene)
 void launch_free_mask(const DevScene &ds, cudaStream_t st, uint32_t *bits);
 // local depth maps of the obstacle vertices (once per scene)

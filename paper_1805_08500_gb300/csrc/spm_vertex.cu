@@ -38,7 +38,10 @@ namespace {
 constexpr int kVisThreads = 256;
 constexpr int kSsspThreads = 256;
 constexpr int kSoloThreads = 512;
-constexpr int kSoloGrp = 8;  // lanes per dirty vertex in the single-CTA fixpoint (in-degrees are small)
+#ifndef SPM_SOLO_GRP
+#define SPM_SOLO_GRP 8
+#endif
+constexpr int kSoloGrp = SPM_SOLO_GRP;  // lanes per dirty vertex in the single-CTA fixpoint (in-degrees are small)
 constexpr int kSoloSmem = 226 * 1024;  // within the 227 KB opt-in maximum, with the static part
 
 // Static filter for one (u, v) pair: tangency at both ends, or for a
@@ -215,10 +218,10 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, int chu
         long long lt;
         task_of(tt, sc, lt);
         const DevScene &ds = *scene_of_task(sc);
-        const int vv = (int)(lt / ds.vis_words), w = (int)(lt % ds.vis_words);
+        const int vv = (int)(lt / ds.pair_words), w = (int)(lt % ds.pair_words);
         const int u = w * 32 + lane, v = ds.n_src + vv;
         if (w * 32 >= v) continue;  // the whole word lies at or above the diagonal (warp-uniform)
-        bool c = u < v && pair_filter(ds, u, v);
+        bool c = u < v && u >= ds.pair_u0 && u < ds.pair_u1 && pair_filter(ds, u, v);
         if (c && ds.vert_maps && ds.gen_kind[u] != kSegI) {  // hidden by an obstacle near either end
             const int2 ul = ds.gen_lat[u], vl = ds.gen_lat[v];
             c = !loc_hidden(ds, v, vl, ul) && !(u >= ds.n_src && loc_hidden(ds, u, ul, vl));
@@ -235,7 +238,7 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, int chu
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds, int chunk) {
     __shared__ PairQ q;
     vis_pairs_run(
-        q, (long long)ds.n_vert * ds.vis_words, chunk, reinterpret_cast<unsigned long long *>(ds.stats + 2),
+        q, (long long)ds.n_vert * ds.pair_words, chunk, reinterpret_cast<unsigned long long *>(ds.stats + 2),
         [&](int) { return &ds; },
         [&](long long t, int &sc, long long &lt) {
             sc = 0;
@@ -519,15 +522,37 @@ __global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene d
 // (costs and then parents are fixed in order of increasing cost), so the
 // result is the one k_sssp's synchronous rounds reach. The FP64 link
 // lengths are staged in shared memory when they fit, else read from global.
-__device__ __forceinline__ void arrival_from(const DevScene &ds, const signed char *src_kind, const short2 *lat,
-                                             int p, short2 vl, int &dx, int &dy) {
-    const int kp = p >= ds.n_src ? kVert : (p < 64 ? src_kind[p] : ds.gen_kind[p]);
-    if (kp == kSegI) {
-        arrival_dir(ds, p, make_int2(vl.x, vl.y), dx, dy);
-    } else {
+//
+// A round is one dependent chain per dirty vertex, so it is laid out for
+// latency: everything a group needs about its vertex is loaded in one level,
+// the kinds and lattice endpoints of the first sources sit in shared memory
+// (a segment-interior parent needs no global load), the out-neighbours are
+// marked with one counter atomic per warp, and the finished round's dirty
+// bitmap is cleared in bulk.
+constexpr int kSoloSrc = 32;  // sources whose kind and segment endpoints are staged
+
+#ifdef SPM_COUNT
+// clock read ordered after the value x has been computed (instrumentation)
+template <class T>
+__device__ __forceinline__ long long clock_after(T x) {
+    asm volatile("" ::"l"((long long)x) : "memory");
+    return clock64();
+}
+#endif
+
+__device__ __forceinline__ void arrival_from(const DevScene &ds, const signed char *src_kind, const int4 *src_seg,
+                                             const short2 *lat, int p, short2 vl, int &dx, int &dy) {
+    if (p >= ds.n_src || (p < kSoloSrc ? src_kind[p] : ds.gen_kind[p]) != kSegI) {
         dx = vl.x - lat[p].x;
         dy = vl.y - lat[p].y;
+        return;
     }
+    // segment interior: perpendicular to the segment, toward v
+    const int4 L = p < kSoloSrc ? src_seg[p] : ds.seg_lat[ds.gen_aux[p]];
+    const int ux = L.z - L.x, uy = L.w - L.y;
+    const int side = cross32(ux, uy, vl.x - L.x, vl.y - L.y);
+    dx = side > 0 ? -uy : uy;
+    dy = side > 0 ? ux : -ux;
 }
 
 __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
@@ -554,12 +579,13 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     unsigned short *dl = (unsigned short *)take(2 * 2 * (size_t)n);  // round parity p at p * n
     double *slen = with_len ? (double *)take(8 * (size_t)E) : nullptr;
     __shared__ int cnt[3];  // dirty-list counts, by round modulo 3
-    constexpr int kSrcKinds = 64;
-    __shared__ signed char src_kind[kSrcKinds];  // kinds of the first sources (ids >= n_src are vertices)
+    __shared__ signed char src_kind[kSoloSrc];  // kinds of the first sources (ids >= n_src are vertices)
+    __shared__ int4 src_seg[kSoloSrc];          // their segment's lattice endpoints (segment sources)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSoloThreads / 32;
     // work unit: a group of kSoloGrp lanes per dirty vertex
     constexpr int kGpw = 32 / kSoloGrp;  // groups per warp
     const int grp = lane / kSoloGrp, gl = lane % kSoloGrp, ngroups = nwarps * kGpw;
+    const unsigned kFull = 0xffffffffu;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
     for (int i = tid; i <= n; i += kSoloThreads) out_start[i] = ds.out_start[i];
@@ -578,17 +604,20 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         wedge[g] = make_short4((short)w.x, (short)w.y, (short)w.z, (short)w.w);
     }
     for (int w = tid; w < 2 * dw; w += kSoloThreads) dirty[w] = 0u;
-    for (int g = tid; g < min(ds.n_src, kSrcKinds); g += kSoloThreads) src_kind[g] = (signed char)ds.gen_kind[g];
+    for (int g = tid; g < min(ds.n_src, kSoloSrc); g += kSoloThreads) {
+        const int k = ds.gen_kind[g];
+        src_kind[g] = (signed char)k;
+        src_seg[g] = k == kSegI ? ds.seg_lat[ds.gen_aux[g]] : make_int4(0, 0, 0, 0);
+    }
     if (tid < 3) cnt[tid] = 0;
     __syncthreads();
-    auto mark = [&](int u, unsigned *bits, unsigned short *list, int *count) {
+    // the sources mark their out-neighbours for round 0
+    for (int u = warp * kGpw + grp; u < ds.n_src; u += ngroups)
         for (int e = out_start[u] + gl; e < out_start[u + 1]; e += kSoloGrp) {
             const int v = out_dst[e];
             const unsigned bit = 1u << (v & 31);
-            if (!(atomicOr(&bits[v >> 5], bit) & bit)) list[atomicAdd(count, 1)] = (unsigned short)v;
+            if (!(atomicOr(&dirty[v >> 5], bit) & bit)) dl[atomicAdd(&cnt[0], 1)] = (unsigned short)v;
         }
-    };
-    for (int u = warp * kGpw + grp; u < ds.n_src; u += ngroups) mark(u, dirty, dl, &cnt[0]);
     __syncthreads();
     int round = 0;
     for (;; ++round) {
@@ -600,39 +629,43 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             break;
         }
         if (tid == 0) cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
+        int *next_cnt = &cnt[(round + 1) % 3];
 #ifdef SPM_COUNT
         const long long t_round = clock64();
         if (tid == 0) {
             SPM_CNT(0, nd);
             SPM_CNT_MAX(1, nd);
-            SPM_CNT(2, (nd + ngroups - 1) / ngroups);
         }
+        long long lap[6] = {0, 0, 0, 0, 0, 0};
 #endif
         for (int i0 = warp * kGpw; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
             const int v = act ? dl[cur * n + i] : ds.n_src;
             const int vv = v - ds.n_src;
-            if (act && gl == 0) atomicAnd(&dirty[cur * dw + (v >> 5)], ~(1u << (v & 31)));
+            // one level of loads: the vertex's lists, position and state
+            const int e0 = in_start[vv] + gl, e1 = act ? in_start[vv + 1] : 0;
+            const int o0 = out_start[v] + gl, o1 = act ? out_start[v + 1] : 0;
             const short2 vl = lat[v];
+            const long long cv = __double_as_longlong(cost[v]);
+            const int pv = par[v];
             long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
-            const int e1 = act ? in_start[vv + 1] : 0;
 #ifdef SPM_COUNT
-            long long tc0 = clock64();
+            lap[0] = clock_after((long long)e1 + o1 + vl.x + cv + pv);  // the vertex's own loads
 #endif
-            for (int e = in_start[vv] + gl; e < e1; e += kSoloGrp) {
+            for (int e = e0; e < e1; e += kSoloGrp) {
                 const double len = with_len ? slen[e] : __ldg(ds.in_len + e);
                 const int u = in_src[e];
                 const double cu = cost[u];
+                const int pu = par[u];
+                const short2 ul = lat[u];
+                const short4 w = wedge[u];
                 if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;  // unreached
                 if (u >= ds.n_src) {  // an obstacle vertex passes paths on only inside its shadow cone
-                    const int pu = par[u];
                     if (pu < 0) continue;
-                    const short2 ul = lat[u];
                     int dx, dy;
-                    arrival_from(ds, src_kind, lat, pu, ul, dx, dy);
-                    const short4 w = wedge[u];
+                    arrival_from(ds, src_kind, src_seg, lat, pu, ul, dx, dy);
                     int4 c;
                     const int ct = make_cone(make_int4(w.x, w.y, w.z, w.w), dx, dy, c);
                     if (!in_cone(ct, c, vl.x - ul.x, vl.y - ul.y)) continue;
@@ -646,49 +679,60 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 }
             }
 #ifdef SPM_COUNT
-            long long tc1 = clock64();
+            lap[1] = clock_after(best + bpar);  // the pull
 #endif
 #pragma unroll
             for (int o = kSoloGrp / 2; o > 0; o >>= 1) {  // within the group
-                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
+                const long long ob = __shfl_xor_sync(kFull, best, o);
+                const int op = __shfl_xor_sync(kFull, bpar, o);
                 if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
                     best = ob;
                     bpar = op;
                 }
             }
+            // every lane of the group holds the group's result and the old state
+            const bool changed = act && (best != cv || bpar != pv);
 #ifdef SPM_COUNT
-            long long tc2 = clock64();
+            lap[2] = clock_after(best + bpar);  // the reduction
 #endif
-            bool changed = false;
-            if (act && gl == 0 && (best != __double_as_longlong(cost[v]) || bpar != par[v])) {
+            if (changed && gl == 0) {
                 cost[v] = __longlong_as_double(best);  // only this group writes v in this round
                 par[v] = (short)bpar;
-                changed = true;
             }
-            changed = __shfl_sync(0xffffffffu, changed, grp * kSoloGrp) && act;
-#ifdef SPM_COUNT
-            long long tc3 = clock64();
-#endif
-            if (changed) mark(v, dirty + nxt * dw, dl + nxt * n, &cnt[(round + 1) % 3]);
-#ifdef SPM_COUNT
-            if (tid == 0) {
-                SPM_CNT(8, tc0 - t_round);
-                SPM_CNT(9, tc1 - tc0);
-                SPM_CNT(10, tc2 - tc1);
-                SPM_CNT(11, tc3 - tc2);
+            // mark the out-neighbours: one counter atomic per warp and step
+            for (int e = o0; __any_sync(kFull, changed && e < o1); e += kSoloGrp) {
+                bool fresh = false;
+                int w = 0;
+                if (changed && e < o1) {
+                    w = out_dst[e];
+                    const unsigned bit = 1u << (w & 31);
+                    fresh = !(atomicOr(&dirty[nxt * dw + (w >> 5)], bit) & bit);
+                }
+                const unsigned bal = __ballot_sync(kFull, fresh);
+                int base = 0;
+                if (lane == 0 && bal) base = atomicAdd(next_cnt, __popc(bal));
+                base = __shfl_sync(kFull, base, 0);
+                if (fresh) dl[nxt * n + base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)w;
             }
-            if (gl == 0 && act) SPM_CNT(3, in_start[vv + 1] - in_start[vv]);
-            if (gl == 0 && changed) SPM_CNT(4, 1);
+#ifdef SPM_COUNT
+            lap[3] = clock_after(changed);  // the marks
 #endif
         }
+        // this round's bitmap is free again (marks went to the other one)
+        for (int w = tid; w < dw; w += kSoloThreads) dirty[cur * dw + w] = 0u;
 #ifdef SPM_COUNT
         if (lane == 0) SPM_CNT_MAX(6, (unsigned long long)(clock64() - t_round));  // slowest warp, any round
-        if (tid == 0) SPM_CNT(7, (unsigned long long)(clock64() - t_round));  // warp 0 (always has work)
+        if (tid == 0) {
+            SPM_CNT(7, (unsigned long long)(clock64() - t_round));  // warp 0 (always has work)
+            SPM_CNT(8, (unsigned long long)(lap[0] - t_round));     // list entry and the vertex's loads
+            SPM_CNT(9, (unsigned long long)(lap[1] - lap[0]));      // pull over the in-edges
+            SPM_CNT(10, (unsigned long long)(lap[2] - lap[1]));     // group reduction
+            SPM_CNT(11, (unsigned long long)(lap[3] - lap[2]));     // commit and marks
+        }
 #endif
         __syncthreads();
 #ifdef SPM_COUNT
-        if (tid == 0) SPM_CNT(5, (unsigned long long)(clock64() - t_round));
+        if (tid == 0) SPM_CNT(5, (unsigned long long)(clock64() - t_round));  // whole round, barrier included
 #endif
     }
     // the settled state, with each vertex's shadow cone from its parent
@@ -700,7 +744,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
             ct = kConeEmpty;  // unreached: no arrival direction
             if (pg >= 0) {
                 int dx, dy;
-                arrival_from(ds, src_kind, lat, pg, lat[g], dx, dy);
+                arrival_from(ds, src_kind, src_seg, lat, pg, lat[g], dx, dy);
                 const short4 w = wedge[g];
                 ct = make_cone(make_int4(w.x, w.y, w.z, w.w), dx, dy, c);
             }
@@ -746,10 +790,12 @@ __device__ __forceinline__ int scene_of(const T *off, int n, T x) {
 }
 
 __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.pair_off[b.n];
-         i += (long long)gridDim.x * blockDim.x) {  // zero every scene's visibility bit matrix
-        const int s = scene_of(b.pair_off, b.n, i);
-        b.scenes[s].vis_bits[i - b.pair_off[s]] = 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.bits_off[b.n];
+         i += (long long)gridDim.x * blockDim.x) {  // every scene's bit matrix: its static part, or zero
+        const int s = scene_of(b.bits_off, b.n, i);
+        const DevScene &ds = b.scenes[s];
+        const long long k = i - b.bits_off[s];
+        ds.vis_bits[k] = ds.vis_static ? ds.vis_static[k] : 0u;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         *reinterpret_cast<unsigned long long *>(b.counters + 6) = 0ull;  // visibility-pair work counter
@@ -936,19 +982,42 @@ __global__ void k_finalize_b(const __grid_constant__ BatchDev b) {
 
 int vis_resident_blocks();  // co-resident CTAs of the visibility-pair kernel
 
+// Visibility-pair kernel over ds's pair range (resident CTAs, runs sized so
+// that every resident warp takes about two).
+void launch_pairs(const DevScene &ds, cudaStream_t st) {
+    const long long tasks = (long long)ds.n_vert * ds.pair_words;
+    cudaMemsetAsync(ds.stats + 2, 0, sizeof(unsigned long long), st);  // the pair kernel's work counter
+    if (tasks == 0) return;
+    const int resident = vis_resident_blocks();
+    long long blocks = (tasks + (kVisThreads / 32) - 1) / (kVisThreads / 32);  // a task per warp at least
+    blocks = blocks > resident ? resident : blocks;
+    const long long per_chunk = tasks / (blocks * (kVisThreads / 32) * 2);
+    const int chunk = (int)(per_chunk < 1 ? 1 : (per_chunk > 32 ? 32 : per_chunk));
+    k_vis_pairs<<<(int)blocks, kVisThreads, 0, st>>>(ds, chunk);
+}
+
+void launch_vis_static(const DevScene &ds, cudaStream_t st, uint32_t *vis_static) {
+    if (ds.n_vert == 0) return;
+    cudaMemsetAsync(vis_static, 0, sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words, st);
+    DevScene d = ds;  // every word of every row, obstacle-vertex columns only
+    d.vis_bits = vis_static;
+    d.vis_static = nullptr;
+    d.pair_words = ds.vis_words;
+    d.pair_u0 = ds.n_src;
+    d.pair_u1 = ds.n_gen;
+    launch_pairs(d, st);
+}
+
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
     cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
     cudaMemsetAsync(ds.out_fill, 0, sizeof(int32_t) * ds.n_gen, st);
     if (ds.n_vert > 0) {
-        cudaMemsetAsync(ds.vis_bits, 0, sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words, st);
-        const long long tasks = (long long)ds.n_vert * ds.vis_words;
-        cudaMemsetAsync(ds.stats + 2, 0, sizeof(unsigned long long), st);  // the pair kernel's work counter
-        const int resident = vis_resident_blocks();
-        long long blocks = (tasks + (kVisThreads / 32) - 1) / (kVisThreads / 32);  // a task per warp at least
-        blocks = blocks > resident ? resident : blocks;
-        const long long per_chunk = tasks / (blocks * (kVisThreads / 32) * 2);
-        const int chunk = (int)(per_chunk < 1 ? 1 : (per_chunk > 32 ? 32 : per_chunk));
-        k_vis_pairs<<<(int)blocks, kVisThreads, 0, st>>>(ds, chunk);
+        const size_t bytes = sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words;
+        // the obstacle-vertex pairs come from the scene's static bits; the
+        // pair kernel then tests the source columns only
+        if (ds.vis_static) cudaMemcpyAsync(ds.vis_bits, ds.vis_static, bytes, cudaMemcpyDeviceToDevice, st);
+        else cudaMemsetAsync(ds.vis_bits, 0, bytes, st);
+        launch_pairs(ds, st);
         const int eb = (ds.n_vert + 7) / 8;  // one warp per row
         k_edges_count<<<eb, 256, 0, st>>>(ds);
         k_edges_scan<<<1, 1024, 0, st>>>(ds);

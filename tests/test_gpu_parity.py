@@ -132,9 +132,27 @@ def test_maze_small_full(spm, oracle_mod):
     full_parity(spm, oracle_mod, sg.maze(1, cells=8, N=512), "maze8")
 
 
-def test_maze_4096_sampled(spm, oracle_mod):
+def test_maze_4096_full_size_sample(spm, oracle_mod):
+    """The headline maze (64 x 64 cells, 4096^2 pixels) in the benchmark's
+    launch configuration (geometric flood beside the fixpoint, depth maps,
+    32 x 32 tiles), against the oracle on one million seeded pixels plus
+    sixteen seeded 256 x 256 windows (about 2 M pixels)."""
     scene = sg.maze(0)
-    sampled_parity(spm, oracle_mod, scene, 12000, "maze64", window=(2000, 1000, 64))
+    s = spm.Scene(scene)
+    spm.spm_scene_set_tuning(s.handle, 3, 32, 32, 1)
+    d, p = s.compute()
+    s.sync()
+    gd, gp = d.cpu().numpy(), p.cpu().numpy()
+    rng = np.random.default_rng(2024)
+    ij = [np.stack([rng.integers(0, 4096, 1_000_000), rng.integers(0, 4096, 1_000_000)], 1)]
+    for _ in range(16):
+        i0, j0 = rng.integers(0, 4096 - 256, 2)
+        jj, ii = np.mgrid[j0:j0 + 256, i0:i0 + 256]
+        ij.append(np.stack([ii.ravel(), jj.ravel()], 1))
+    ij = np.concatenate(ij).astype(np.int32)
+    o = oracle_mod.Oracle(scene)
+    rd, rp, rd2, rp2 = o.pixels(ij)
+    check_parity(scene, gd[ij[:, 1], ij[:, 0]], gp[ij[:, 1], ij[:, 0]], rd, rp, rd2, "maze4096 2M px", rp2)
 
 
 def test_maze_4096_bench_configurations_agree(spm, oracle_mod):
@@ -546,6 +564,58 @@ def test_agent_gradient_matches_oracle(spm, oracle_mod, src_device):
     assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
     np.testing.assert_allclose(pts.grad.cpu().numpy(), gp_ref, atol=1e-4)
     np.testing.assert_allclose(segs.grad.cpu().numpy(), gs_ref, atol=1e-4)
+
+
+def test_agent_gradient_at_config_size(spm, oracle_mod):
+    """The differentiable workload at full size (2048^2 pixels over
+    [0, 8192)^2, 150 polygons, 4 FP32 points + 1 FP32 segment, 100k agents):
+    loss and gradient against the FP64 oracle's."""
+    scene = sg.differentiable(0)
+    o = oracle_mod.Oracle(scene)
+    d, _, _, _ = o.pixels(scene.agents)
+    agents = scene.agents[np.isfinite(d)]
+    assert len(agents) > 0.99 * len(scene.agents)
+    loss_ref, gp_ref, gs_ref = o.agent_loss_and_grad(agents)
+    s = spm.Scene(scene)
+    pts = torch.tensor(scene.points, dtype=torch.float32, device="cuda", requires_grad=True)
+    segs = torch.tensor(scene.segs, dtype=torch.float32, device="cuda", requires_grad=True)
+    ag = torch.tensor(agents, dtype=torch.int32, device="cuda")
+    loss = spm.agent_loss(s, pts, segs, ag)
+    loss.backward()
+    s.sync()
+    assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+    np.testing.assert_allclose(pts.grad.cpu().numpy(), gp_ref, atol=1e-4)
+    np.testing.assert_allclose(segs.grad.cpu().numpy(), gs_ref, atol=1e-4)
+
+
+def test_batched_parity_at_config_sizes(spm, oracle_mod):
+    """A batch of 24 scenes of the batched workload -- its first 16 and 8 of
+    its 1024^2 scenes with more than 300 polygons -- computed in one launch
+    sequence, each scene against the oracle (whole grid up to 256^2, 20k
+    seeded pixels above)."""
+    allsc = sg.batched(0)
+    big = [k for k, sc in enumerate(allsc) if sc.grid[0] == 1024 and len(sc.polys) > 300]
+    picks = list(range(16)) + [k for k in big if k >= 16][:8]
+    scenes = [allsc[k] for k in picks]
+    assert sum(sc.grid[0] == 1024 and len(sc.polys) > 300 for sc in scenes) >= 8
+    objs = [spm.Scene(sc) for sc in scenes]
+    batch = spm.Batch(objs)
+    outs = batch.compute()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(99)
+    for k, sc in enumerate(scenes):
+        gd, gp = outs[k][0].cpu().numpy(), outs[k][1].cpu().numpy()
+        o = oracle_mod.Oracle(sc)
+        N = sc.grid[0]
+        if N <= 256:
+            rd, rp, rd2, rp2 = o.field()
+            check_parity(sc, gd, gp, rd, rp, rd2, f"batched[{picks[k]}]", rp2, oracle=o)
+        else:
+            ij = rng.integers(0, N, (20000, 2)).astype(np.int32)
+            rd, rp, rd2, rp2 = o.pixels(ij)
+            check_parity(sc, gd[ij[:, 1], ij[:, 0]], gp[ij[:, 1], ij[:, 0]], rd, rp, rd2,
+                         f"batched[{picks[k]}]", rp2)
+    batch.close()
 
 
 @pytest.mark.gpu
