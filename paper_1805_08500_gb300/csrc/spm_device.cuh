@@ -122,6 +122,20 @@ __device__ __forceinline__ int make_cone(int4 wedge, int dx, int dy, int4 &c) {
     return kConeEmpty;
 }
 
+// in_cone(make_cone(wedge, d), w) written without branches (selects only):
+// the same closed sector, ray or empty set. For tight loops where divergent
+// branches cost more than the arithmetic.
+__device__ __forceinline__ bool in_shadow_cone(int dx, int dy, short4 wedge, int wx, int wy) {
+    const int a = cross32(dx, dy, wedge.x, wedge.y), b = cross32(dx, dy, wedge.z, wedge.w);
+    const bool nz = (a | b) != 0;
+    const bool left = (a >= 0) & (b >= 0) & nz, right = (a <= 0) & (b <= 0) & nz;
+    const int cdw = cross32(dx, dy, wx, wy), dot = dx * wx + dy * wy;
+    const bool ray_in = (cdw == 0) & (dot >= 0);
+    const bool left_in = (cdw >= 0) & (cross32(wx, wy, wedge.x, wedge.y) >= 0);   // from d to the wedge start
+    const bool right_in = (cdw <= 0) & (cross32(wedge.z, wedge.w, wx, wy) >= 0);  // from the wedge end to d
+    return (left & ((a == 0) ? ray_in : left_in)) | (right & ((b == 0) ? ray_in : right_in));
+}
+
 // Arrival direction at generator v whose parent is u (lattice).
 __device__ __forceinline__ void arrival_dir(const DevScene &ds, int u, int2 vl, int &dx, int &dy) {
     if (ds.gen_kind[u] == kSegI) {

@@ -641,7 +641,8 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         for (int i0 = warp * kGpw; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
-            const int v = act ? dl[cur * n + i] : ds.n_src;
+            const int v_list = dl[cur * n + min(i, n - 1)];  // loaded before nd is known
+            const int v = act ? v_list : ds.n_src;
             const int vv = v - ds.n_src;
             // one level of loads: the vertex's lists, position and state
             const int e0 = in_start[vv] + gl, e1 = act ? in_start[vv + 1] : 0;
@@ -654,6 +655,11 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
 #ifdef SPM_COUNT
             lap[0] = clock_after((long long)e1 + o1 + vl.x + cv + pv);  // the vertex's own loads
 #endif
+            const int o_first = out_dst[min(o0, E > 0 ? E - 1 : 0)];  // first out-neighbour, loaded early
+            // The in-list runs in increasing generator order, so within a lane
+            // the first of equal keys has the smaller id: a strict compare
+            // keeps it. The pull is branch-free: divergent branches here cost
+            // more than computing every test.
             for (int e = e0; e < e1; e += kSoloGrp) {
                 const double len = with_len ? slen[e] : __ldg(ds.in_len + e);
                 const int u = in_src[e];
@@ -661,22 +667,29 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 const int pu = par[u];
                 const short2 ul = lat[u];
                 const short4 w = wedge[u];
-                if (__double_as_longlong(cu) >= 0x7ff0000000000000ll) continue;  // unreached
-                if (u >= ds.n_src) {  // an obstacle vertex passes paths on only inside its shadow cone
-                    if (pu < 0) continue;
-                    int dx, dy;
+                // u's arrival direction: from its parent, or perpendicular to a
+                // segment source whose interior is the parent
+                const int pc = pu < 0 ? 0 : pu, ps = pc < kSoloSrc ? pc : 0;
+                const short2 pl = lat[pc];
+                const int4 L = src_seg[ps];
+                int dx = ul.x - pl.x, dy = ul.y - pl.y;
+                if (pu < ds.n_src && pu >= kSoloSrc) {  // beyond the staged sources (rare)
                     arrival_from(ds, src_kind, src_seg, lat, pu, ul, dx, dy);
-                    int4 c;
-                    const int ct = make_cone(make_int4(w.x, w.y, w.z, w.w), dx, dy, c);
-                    if (!in_cone(ct, c, vl.x - ul.x, vl.y - ul.y)) continue;
+                } else if (pu >= 0 && pu < ds.n_src && src_kind[ps] == kSegI) {
+                    const int sx = L.z - L.x, sy = L.w - L.y;
+                    const int side = cross32(sx, sy, ul.x - L.x, ul.y - L.y);
+                    dx = side > 0 ? -sy : sy;
+                    dy = side > 0 ? sx : -sx;
                 }
+                // an obstacle vertex passes paths on only inside its shadow cone
+                const bool valid = (__double_as_longlong(cu) < 0x7ff0000000000000ll) &
+                                   ((u < ds.n_src) | ((pu >= 0) & in_shadow_cone(dx, dy, w, vl.x - ul.x, vl.y - ul.y)));
                 // costs are non-negative, so their bit patterns order like
                 // their values: compare as integers, keep FP64 for the add
                 const long long cand = __double_as_longlong(__dadd_rn(cu, len));
-                if (cand < best || (cand == best && u < bpar)) {
-                    best = cand;
-                    bpar = u;
-                }
+                const bool better = valid & (cand < best);
+                best = better ? cand : best;
+                bpar = better ? u : bpar;
             }
 #ifdef SPM_COUNT
             lap[1] = clock_after(best + bpar);  // the pull
@@ -704,7 +717,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 bool fresh = false;
                 int w = 0;
                 if (changed && e < o1) {
-                    w = out_dst[e];
+                    w = e == o0 ? o_first : out_dst[e];
                     const unsigned bit = 1u << (w & 31);
                     fresh = !(atomicOr(&dirty[nxt * dw + (w >> 5)], bit) & bit);
                 }
