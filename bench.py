@@ -37,9 +37,9 @@ FALLBACK_HBM_GBS = 6800.0
 # FP32 lanes per SM x SMs x 2 flops per FMA; clock from the measured peaks file
 FP32_LANES, N_SMS = 128, 152
 FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
-# DRAM bytes (read + write) of one k_pixels launch, from the ncu capture
-# summarised in profiles/k_pixels_dram_maze4096.md; only for that workload and
-# that kernel version (re-capture after changing the kernel).
+# DRAM bytes (read + write) of one k_pixels launch on the 4096^2 maze, from a
+# single-pass ncu capture of dram__bytes_read.sum + dram__bytes_write.sum; valid
+# for that workload and that kernel version only (re-captured after a change).
 KPIXELS_TRAFFIC = {"maze4096": 107_700_480}
 
 
@@ -461,15 +461,21 @@ def run_differentiable(args, cfg_desc, scene):
     gs = torch.empty(4 * max(n_s, 1), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    n_ag = int(agents.shape[0])
+    tape = spm.empty_tape(n_ag, dev)  # the forward's record for the backward
 
     def step():
         s.compute(d_out, p_out, stream)
-        spm.spm_agents_forward(s.handle, stream, agents, d_out, p_out, loss)
+        spm.spm_agents_forward(s.handle, stream, agents, d_out, p_out, loss, tape)
+
+    def backward():
+        spm.spm_agents_backward(s.handle, stream, tape, n_ag, gp, gs)
 
     for _ in range(args.warmup):
         step()
-        spm.spm_agents_backward(s.handle, stream, gp, gs)
+        backward()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    phases = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -479,8 +485,9 @@ def run_differentiable(args, cfg_desc, scene):
             ev[k][0].record(stream)
             step()
             ev[k][1].record(stream)
-            spm.spm_agents_backward(s.handle, stream, gp, gs)
+            backward()
             ev[k][2].record(stream)
+            phases.append(s.phase_ms())  # this step's map: vertex phase, culling, pixel pass
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -501,7 +508,7 @@ def run_differentiable(args, cfg_desc, scene):
         spm.spm_scene_update_sources_device(s.handle, stream, d_src[:2 * n_p] if n_p else None,
                                             d_src[2 * n_p:] if n_s else None)
         step()
-        spm.spm_agents_backward(s.handle, stream, gp, gs)
+        backward()
         h_out[:1].copy_(loss.reshape(1), non_blocking=True)
         h_out[1:1 + 2 * n_p].copy_(gp, non_blocking=True)
         h_out[1 + 2 * n_p:].copy_(gs, non_blocking=True)
@@ -519,7 +526,7 @@ def run_differentiable(args, cfg_desc, scene):
             "clocks": clk.summary(),
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(pts.nbytes + segs.nbytes),
                     "d2h_bytes_per_step": int(h_out.numel() * 4)},
-            "gpu_launches": (info["kernels_per_compute"] + 4) * args.steps}  # + k_loss, 3 backward kernels
+            "gpu_launches": (info["kernels_per_compute"] + 5) * args.steps}  # + 3 forward, 2 backward kernels
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build_oracle()
@@ -801,6 +808,18 @@ def main():
         spm.spm_compute_host(s.handle, stream, hd, hp)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = whole_job_rate(npx, world, max_over_ranks(e2e_s, world, dev)) / 1e6
+    # the same into pageable host memory (numpy arrays): row slabs through the
+    # scene's page-locked bounce buffers
+    nd = np.empty((Ny, Nx), np.float32)
+    npar = np.empty((Ny, Nx), np.int32)
+    spm.spm_compute_host(s.handle, stream, nd, npar)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        spm.spm_scene_update_sources(s.handle, pts, segs)
+        spm.spm_compute_host(s.handle, stream, nd, npar)
+    e2e_pageable = whole_job_rate(npx, world, max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)) / 1e6
+    del nd, npar
 
     peaks, peak_src = load_peaks()
     vert_ms = float(np.mean([p[0] for p in phases]))
@@ -838,7 +857,8 @@ def main():
                       "peak_source": peak_src},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pts.nbytes + segs.nbytes),
-                "d2h_bytes_per_step": int(8 * npx)},
+                "d2h_bytes_per_step": int(8 * npx), "host_buffers": "page-locked (torch pin_memory)",
+                "pageable_value": e2e_pageable},
         "gpu_launches": launches_per_step * args.steps,
         "step_ms_stats": {"median": float(np.median(step_ms)), "p10": float(np.percentile(step_ms, 10)),
                           "p90": float(np.percentile(step_ms, 90)), "rank": rank},

@@ -56,7 +56,8 @@ typedef enum {
     SPM_ERR_OOM = 3,           /* device or host allocation failed           */
     SPM_ERR_CUDA = 4,          /* a CUDA runtime call failed                 */
     SPM_ERR_NOT_CONVERGED = 5, /* vertex-cost fixpoint hit its round cap     */
-    SPM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up         */
+    SPM_ERR_TIMEOUT = 6,       /* reserved: no kernel of this library waits on
+                                  another, so no call returns it              */
     SPM_ERR_CAPACITY = 7       /* a fixed-size device buffer overflowed      */
 } spm_status;
 
@@ -222,7 +223,13 @@ spm_status spm_extract_path(spm_scene *scene, float x, float y, float *out_xy,
 /* Generator table after the last spm_compute (synchronous copy to the host
  * arrays, each of length spm_scene_info()[0]; any pointer may be NULL):
  * kind (0 point, 1 segment A, 2 segment B, 3 segment interior, 4 obstacle
- * vertex), lattice position (2 per generator), FP64 cost and parent id. */
+ * vertex), lattice position (2 per generator), FP64 cost and parent id.
+ * The visibility graph keeps only links tangent to the obstacles at both
+ * ends (a shortest path bends around a vertex, Sec. 3.1), so an obstacle
+ * vertex that no tangent link reaches at its geodesic distance -- one reached
+ * only head-on, whose shadow cone is empty and which is never a parent --
+ * reports a cost above that distance (or +inf). Every vertex that can be a
+ * parent reports its exact geodesic distance; the map is unaffected. */
 spm_status spm_scene_generators(spm_scene *scene, int32_t *kind, int32_t *lattice_xy,
                                 double *cost, int32_t *parent);
 
@@ -236,18 +243,32 @@ spm_status spm_scene_generators(spm_scene *scene, int32_t *kind, int32_t *lattic
 spm_status spm_scene_info(spm_scene *scene, int64_t *info);
 
 /* Differentiable form. Forward: loss = mean over n agents (pixel indices,
- * int32 (i, j) pairs in DEVICE memory) of the field value of the last
- * spm_compute; writes the scalar to loss_dev (device float) and keeps the
- * agents for the backward call. Backward: d loss / d point sources
- * (grad_points_dev, 2 * n_points floats) and d loss / d segment endpoints
- * (grad_segs_dev, 4 * n_segments floats), from each agent's root link:
- * the last leg of its parent chain (Sec. 3.1 ParentId chain). Agents on
- * unreached pixels contribute nothing. Both asynchronous on `stream`. */
+ * int32 (i, j) pairs in DEVICE memory) of the field value in dist_dev (an
+ * spm_compute result of this scene); writes the scalar to loss_dev (device
+ * float). Agents on unreached pixels count as 0. When tape_dev is not NULL,
+ * the forward also records on it what the backward needs: each agent's
+ * contribution to d loss / d sources, from its root link -- the last leg of
+ * its parent chain in parent_dev (Sec. 3.1 ParentId chain) and the current
+ * source positions. Call it on the compute's stream, before the next compute
+ * of this scene, so that the chain is the one of that compute's generator
+ * table. tape_dev: caller-owned DEVICE memory of spm_agents_tape_bytes(n)
+ * bytes, 16-byte aligned. Asynchronous on `stream`; allocates nothing. */
 spm_status spm_agents_forward(spm_scene *scene, void *stream, const int32_t *agents_dev,
                               int32_t n, const float *dist_dev, const int32_t *parent_dev,
-                              float *loss_dev);
-spm_status spm_agents_backward(spm_scene *scene, void *stream, float *grad_points_dev,
-                               float *grad_segs_dev);
+                              float *loss_dev, void *tape_dev);
+
+/* Bytes of the tape spm_agents_forward records for n agents (0 for n < 0). */
+int64_t spm_agents_tape_bytes(int32_t n);
+
+/* Backward: d loss / d point sources (grad_points_dev, 2 * n_points floats)
+ * and d loss / d segment endpoints (grad_segs_dev, 4 * n_segments floats)
+ * from a tape recorded by spm_agents_forward for the same n agents: the mean
+ * of the agents' root-link gradients, summed in a fixed order (the result is
+ * deterministic). Reads the tape and the scene's source counts only, so a
+ * later compute or source move of the scene does not change it, and several
+ * tapes of one scene may be held at once. Asynchronous on `stream`. */
+spm_status spm_agents_backward(spm_scene *scene, void *stream, const void *tape_dev,
+                               int32_t n, float *grad_points_dev, float *grad_segs_dev);
 
 /* Allocation-free variant of spm_agents_backward. The paper has no
  * counterpart: this entry point exists for callers that must not allocate
@@ -256,9 +277,10 @@ spm_status spm_agents_backward(spm_scene *scene, void *stream, float *grad_point
  * living inside a framework whose memory pool owns the device and forbids raw
  * cudaMalloc calls.
  *
- * It computes the same gradient as spm_agents_forward + spm_agents_backward
- * for n agents (int32 (i, j) pixel pairs, DEVICE memory) on the parent field
- * parent_dev of a previous spm_compute of this scene, writing
+ * It computes the same gradient as spm_agents_forward (with a tape) followed
+ * by spm_agents_backward, for n agents (int32 (i, j) pixel pairs, DEVICE
+ * memory) on the parent field parent_dev of the last spm_compute of this
+ * scene (call it before the next compute or source move), writing
  * grad_points_dev (2 * n_points floats) and grad_segs_dev (4 * n_segments
  * floats), asynchronously on `stream`. It calls no allocating function: its
  * scratch is one fixed array inside the library (about 3.3 MB, held on every
@@ -336,6 +358,15 @@ const char *spm_last_error(const spm_scene *scene);
  * call that meets the failure returns SPM_ERR_OOM and frees what it had
  * allocated. Process-wide; has no effect unless called. */
 void spm_debug_fail_alloc_after(int32_t n);
+
+/* Test hook for the fixpoint's failure path (no counterpart in the paper):
+ * n > 0 caps the vertex fixpoint at n rounds in every later compute (and
+ * batch created later), so that a scene needing more rounds reports
+ * SPM_ERR_NOT_CONVERGED through spm_scene_sync; n <= 0 restores the default
+ * cap of 4 rounds per generator plus 64. The kernel stops at the cap and
+ * returns normally; the scene stays usable. Process-wide; no effect unless
+ * called. */
+void spm_debug_set_round_cap(int32_t n);
 
 #ifdef __cplusplus
 }

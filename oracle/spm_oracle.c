@@ -26,7 +26,7 @@
  * open interior of some convex obstacle, decided by Cyrus-Beck parametric
  * clipping with rational comparisons in __int128.
  *
- * Readings of points the paper leaves open (see the design notes): pixel
+ * Readings of points the paper leaves open: pixel
  * sample = pixel centre (Sec. 6 discussion); touching or grazing obstacle
  * boundaries is allowed; vertex generators are restricted to their shadow
  * cone behind their parent; ties go to the smaller generator id.

@@ -98,8 +98,9 @@ def load_library():
         "spm_extract_path": ([P, F, F, P, I32, P], I32),
         "spm_scene_generators": ([P, P, P, P, P], I32),
         "spm_scene_info": ([P, P], I32),
-        "spm_agents_forward": ([P, P, P, I32, P, P, P], I32),
-        "spm_agents_backward": ([P, P, P, P], I32),
+        "spm_agents_forward": ([P, P, P, I32, P, P, P, P], I32),
+        "spm_agents_tape_bytes": ([I32], I64),
+        "spm_agents_backward": ([P, P, P, I32, P, P], I32),
         "spm_scene_phase_ms": ([P, P, P, P], I32),
         "spm_agents_backward_noalloc": ([P, P, P, I32, P, P, P], I32),
         "spm_scene_get_tuning": ([P, P], I32),
@@ -108,12 +109,12 @@ def load_library():
         "spm_status_string": ([I32], ctypes.c_char_p),
         "spm_last_error": ([P], ctypes.c_char_p),
         "spm_debug_fail_alloc_after": ([I32], None),
+        "spm_debug_set_round_cap": ([I32], None),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = res
-    del I64
     _lib = lib
     return lib
 
@@ -351,16 +352,28 @@ def spm_scene_generators(handle):
     return kind, lat.reshape(-1, 2), cost, par
 
 
-def spm_agents_forward(handle, stream, agents, dist, parent, loss):
+def spm_agents_forward(handle, stream, agents, dist, parent, loss, tape=None):
+    """Mean agent distance into loss; with tape (device buffer of
+    spm_agents_tape_bytes(n) bytes) also records the backward's inputs."""
     n = int(agents.shape[0]) if hasattr(agents, "shape") else len(agents) // 2
     _check(load_library().spm_agents_forward(handle, _stream_handle(stream), _ptr(agents), n,
-                                             _ptr(dist), _ptr(parent), _ptr(loss)),
+                                             _ptr(dist), _ptr(parent), _ptr(loss), _ptr(tape)),
            "spm_agents_forward", handle)
 
 
-def spm_agents_backward(handle, stream, grad_points, grad_segs):
-    _check(load_library().spm_agents_backward(handle, _stream_handle(stream), _ptr(grad_points),
-                                              _ptr(grad_segs)), "spm_agents_backward", handle)
+def spm_agents_tape_bytes(n: int) -> int:
+    return int(load_library().spm_agents_tape_bytes(int(n)))
+
+
+def empty_tape(n: int, device):
+    """A device tape for n agents (16-byte aligned)."""
+    import torch
+    return torch.empty(max(spm_agents_tape_bytes(n), 16), dtype=torch.uint8, device=device)
+
+
+def spm_agents_backward(handle, stream, tape, n, grad_points, grad_segs):
+    _check(load_library().spm_agents_backward(handle, _stream_handle(stream), _ptr(tape), int(n),
+                                              _ptr(grad_points), _ptr(grad_segs)), "spm_agents_backward", handle)
 
 
 def spm_agents_backward_noalloc(handle, stream, agents, parent, grad_points, grad_segs):
@@ -535,9 +548,11 @@ def _make_autograd():
                                             sgs.reshape(-1) if sgs.numel() else None)
             dist, parent = scene.compute()
             loss = torch.empty((), dtype=torch.float32, device=scene.device)
-            spm_agents_forward(scene.handle, None, agents, dist, parent, loss)
+            n = int(agents.shape[0])
+            tape = empty_tape(n, scene.device)  # what the backward needs, from this forward
+            spm_agents_forward(scene.handle, None, agents, dist, parent, loss, tape)
             ctx.scene = scene
-            ctx.keep = (dist, parent, agents, pts, sgs)
+            ctx.tape, ctx.n = tape, n
             ctx.shapes = (points.shape, segs.shape)
             ctx.devices = (points.device, segs.device)
             return loss
@@ -547,7 +562,7 @@ def _make_autograd():
             scene = ctx.scene
             gp = torch.zeros(ctx.shapes[0], dtype=torch.float32, device=scene.device)
             gs = torch.zeros(ctx.shapes[1], dtype=torch.float32, device=scene.device)
-            spm_agents_backward(scene.handle, None, gp if gp.numel() else None,
+            spm_agents_backward(scene.handle, None, ctx.tape, ctx.n, gp if gp.numel() else None,
                                 gs if gs.numel() else None)
             g = grad_out.to(scene.device)
             return (gp * g).to(ctx.devices[0]), (gs * g).to(ctx.devices[1]), None, None

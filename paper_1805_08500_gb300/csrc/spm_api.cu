@@ -14,13 +14,6 @@
 
 #include "spm_internal.h"
 
-namespace spm {
-void launch_agents_forward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
-                           const float *dist, float *loss);
-void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
-                            const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot,
-                            float4 *val, float *grad_pts, float *grad_segs);
-}  // namespace spm
 
 struct spm_scene {
     spm::HostScene hs;
@@ -33,13 +26,11 @@ struct spm_scene {
     cudaStream_t last_stream = nullptr;
     float *stage_dist = nullptr;  // device staging for spm_compute_host
     int32_t *stage_par = nullptr;
-    // differentiable form
-    const int32_t *agents = nullptr;
-    const int32_t *agent_parent = nullptr;
-    int n_agents = 0, agent_cap = 0;
-    int32_t *root = nullptr, *slot = nullptr;
+    // differentiable form: root table (built by each forward that records a
+    // tape) and the partial sums of the gradient reduction
+    int32_t *root = nullptr;
     float2 *lastpt = nullptr;
-    float4 *val = nullptr;
+    double *grad_partial = nullptr;
     // phase timing events (vertex start, pixel start, end)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_valid = false;
@@ -52,6 +43,12 @@ struct spm_scene {
     cudaStream_t copy = nullptr;
     cudaEvent_t slab_ev[8] = {};
     cudaEvent_t copy_done = nullptr;
+    // pageable host destinations: two page-locked bounce buffers (dist rows,
+    // then parent rows, of the largest slab), filled by the copy stream and
+    // emptied by the host while the next slab computes
+    unsigned char *bounce[2] = {nullptr, nullptr};
+    size_t bounce_bytes = 0;
+    cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
     // the device holds sources moved by spm_scene_update_sources_device that
     // the host copy in hs has not seen yet
     bool host_src_stale = false;
@@ -134,6 +131,16 @@ void free_all(spm_scene *s) {
             cudaEventDestroy(e);
             e = nullptr;
         }
+    for (int k = 0; k < 2; ++k) {
+        if (s->bounce_ev[k]) {
+            cudaEventDestroy(s->bounce_ev[k]);
+            s->bounce_ev[k] = nullptr;
+        }
+        if (s->bounce[k]) {
+            cudaFreeHost(s->bounce[k]);
+            s->bounce[k] = nullptr;
+        }
+    }
     if (s->copy) {
         cudaStreamDestroy(s->copy);
         s->copy = nullptr;
@@ -364,6 +371,12 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     if ((size_t)hs.n_vert * spm::kLocBins * sizeof(float) <= ((size_t)256 << 20))
         vert_maps = dalloc<float>(s, (size_t)hs.n_vert * spm::kLocBins);
     ds.vert_maps = vert_maps;
+    {
+        const int n_out = 2 * (hs.n_src - 3 * ds.n_seg) + 4 * ds.n_seg;
+        s->root = dalloc<int32_t>(s, hs.n_gen);
+        s->lastpt = dalloc<float2>(s, hs.n_gen);
+        s->grad_partial = dalloc<double>(s, (size_t)std::max(n_out, 1) * spm::grad_chunks(n_out));
+    }
     ds.sssp_blocks = spm::sssp_grid_blocks();
     ds.solo_smem = spm::solo_smem_bytes();
     ok &= !s->alloc_failed;  // no kernel below may run on a buffer that failed to allocate
@@ -443,10 +456,12 @@ spm_status spm_scene_update_sources_device(spm_scene *s, void *stream, const flo
 }
 
 // dist / parent: device planes; when dist_host / parent_host are given (a
-// host-buffer compute of the whole grid), the pixel pass runs as row slabs
-// and each slab's rows are copied to the host on the copy stream while the
-// next slab computes; the caller's stream then waits for the copies.
-spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent, int tile_row0, int tile_row1,
+// host-buffer compute of the whole grid into pageable memory), the pixel pass
+// runs as row slabs: each slab's rows go to a page-locked bounce buffer on the
+// copy stream while the next slab computes, and the host moves the previous
+// slab from its bounce buffer into the caller's memory meanwhile. Returns
+// once every row is in place.
+static spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent, int tile_row0, int tile_row1,
                         float *dist_host = nullptr, int32_t *parent_host = nullptr) {
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -496,18 +511,36 @@ spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t *parent
     } else {
         NvtxRange r("spm pixel phase with host copies");
         const int rows = tile_row1 - tile_row0, nslab = std::min(rows, (int)(sizeof s->slab_ev / sizeof s->slab_ev[0]));
+        const size_t Nx = (size_t)s->hs.Nx, Ny = (size_t)s->hs.Ny;
+        auto slab_rows = [&](int k, size_t &r0, size_t &r1) {
+            const int t0 = tile_row0 + rows * k / nslab, t1 = tile_row0 + rows * (k + 1) / nslab;
+            r0 = (size_t)t0 * s->ds.tile;
+            r1 = std::min((size_t)t1 * s->ds.tile, Ny);
+        };
+        auto drain = [&](int k) {  // host: slab k from its bounce buffer into the caller's planes
+            size_t r0, r1;
+            slab_rows(k, r0, r1);
+            const size_t cnt = (r1 - r0) * Nx;
+            cudaEventSynchronize(s->bounce_ev[k & 1]);
+            std::memcpy(dist_host + r0 * Nx, s->bounce[k & 1], sizeof(float) * cnt);
+            std::memcpy(parent_host + r0 * Nx, s->bounce[k & 1] + sizeof(float) * cnt, sizeof(int32_t) * cnt);
+        };
         for (int k = 0; k < nslab; ++k) {
             const int t0 = tile_row0 + rows * k / nslab, t1 = tile_row0 + rows * (k + 1) / nslab;
             spm::launch_pixel_phase(s->ds, cs, dist, parent, t0, t1);
             cudaEventRecord(s->slab_ev[k], cs);
             cudaStreamWaitEvent(s->copy, s->slab_ev[k], 0);
-            const size_t r0 = (size_t)t0 * s->ds.tile, r1 = std::min((size_t)t1 * s->ds.tile, (size_t)s->hs.Ny);
-            const size_t off = r0 * s->hs.Nx, cnt = (r1 - r0) * s->hs.Nx;
-            cudaMemcpyAsync(dist_host + off, dist + off, sizeof(float) * cnt, cudaMemcpyDeviceToHost, s->copy);
-            cudaMemcpyAsync(parent_host + off, parent + off, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, s->copy);
+            size_t r0, r1;
+            slab_rows(k, r0, r1);
+            const size_t off = r0 * Nx, cnt = (r1 - r0) * Nx;
+            // bounce buffer k & 1 was emptied by the host when slab k - 2 drained
+            cudaMemcpyAsync(s->bounce[k & 1], dist + off, sizeof(float) * cnt, cudaMemcpyDeviceToHost, s->copy);
+            cudaMemcpyAsync(s->bounce[k & 1] + sizeof(float) * cnt, parent + off, sizeof(int32_t) * cnt,
+                            cudaMemcpyDeviceToHost, s->copy);
+            cudaEventRecord(s->bounce_ev[k & 1], s->copy);
+            if (k > 0) drain(k - 1);
         }
-        cudaEventRecord(s->copy_done, s->copy);
-        cudaStreamWaitEvent(cs, s->copy_done, 0);
+        if (nslab > 0) drain(nslab - 1);
     }
     if (timed) cudaEventRecord(s->ev[2], cs);
     s->ev_valid = timed;
@@ -569,16 +602,25 @@ spm_status spm_compute_sequential(spm_scene *s, void *stream, float *dist, int32
     return SPM_OK;
 }
 
+// Device staging planes for host-buffer computes and the autotuner
+// (allocated on first use).
+static spm_status ensure_stage(spm_scene *s) {
+    if (s->stage_dist) return SPM_OK;
+    const size_t npx = (size_t)s->hs.Nx * s->hs.Ny;
+    s->stage_dist = dalloc<float>(s, npx);
+    s->stage_par = dalloc<int32_t>(s, npx);
+    if (!s->stage_dist || !s->stage_par) {
+        s->stage_dist = nullptr;
+        s->stage_par = nullptr;
+        return set_err(s, SPM_ERR_OOM, "staging allocation failed");
+    }
+    return SPM_OK;
+}
+
 spm_status spm_compute_host(spm_scene *s, void *stream, float *dist_host, int32_t *parent_host) {
     if (!s || !dist_host || !parent_host) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
     spm_status st = check_device(s);
     if (st != SPM_OK) return st;
-    const size_t npx = (size_t)s->hs.Nx * s->hs.Ny;
-    if (!s->stage_dist) {  // first call allocates the device staging planes
-        s->stage_dist = dalloc<float>(s, npx);
-        s->stage_par = dalloc<int32_t>(s, npx);
-        if (!s->stage_dist || !s->stage_par) return set_err(s, SPM_ERR_OOM, "staging allocation failed");
-    }
     // page-locked host buffers are device-addressable: the pixel pass then
     // writes the map straight into them (no staging planes, no copies)
     cudaPointerAttributes ad{}, ap{};
@@ -586,11 +628,37 @@ spm_status spm_compute_host(spm_scene *s, void *stream, float *dist_host, int32_
                         cudaPointerGetAttributes(&ap, parent_host) == cudaSuccess && ad.type == cudaMemoryTypeHost &&
                         ap.type == cudaMemoryTypeHost && ad.devicePointer && ap.devicePointer;
     cudaGetLastError();  // a pageable pointer is not an error here
-    if (direct)
+    if (direct) {
         st = compute_impl(s, stream, static_cast<float *>(ad.devicePointer), static_cast<int32_t *>(ap.devicePointer),
                           0, s->ds.tiles_y);
-    else
+        // the caller may unpin or free these buffers at any time after the
+        // call: queries must not read them (they need a device compute)
+        s->last_dist = nullptr;
+        s->last_parent = nullptr;
+    } else {
+        st = ensure_stage(s);
+        if (st != SPM_OK) return st;
+        const size_t slab_rows = (size_t)((s->ds.tiles_y + 7) / 8 + 1) * s->ds.tile;
+        const size_t need = slab_rows * (size_t)s->hs.Nx * (sizeof(float) + sizeof(int32_t));
+        if (s->bounce_bytes < need) {  // page-locked bounce buffers, on first use or growth
+            for (int k = 0; k < 2; ++k)
+                if (s->bounce[k]) {
+                    cudaFreeHost(s->bounce[k]);
+                    s->bounce[k] = nullptr;
+                }
+            s->bounce_bytes = 0;
+            for (int k = 0; k < 2; ++k) {
+                if (cudaHostAlloc((void **)&s->bounce[k], need, cudaHostAllocDefault) != cudaSuccess) {
+                    cudaGetLastError();
+                    return set_err(s, SPM_ERR_OOM, "page-locked bounce buffer allocation failed");
+                }
+                if (!s->bounce_ev[k] && cudaEventCreateWithFlags(&s->bounce_ev[k], cudaEventDisableTiming) != cudaSuccess)
+                    return set_err(s, SPM_ERR_CUDA, "event creation failed");
+            }
+            s->bounce_bytes = need;
+        }
         st = compute_impl(s, stream, s->stage_dist, s->stage_par, 0, s->ds.tiles_y, dist_host, parent_host);
+    }
     if (st != SPM_OK) return st;
     return spm_scene_sync(s, stream);
 }
@@ -693,7 +761,7 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
         bd.frontier[k] = balloc<int2>(b, gen_off[n]);
     }
     bd.counters = balloc<int32_t>(b, 8);
-    bd.max_rounds = 4 * max_gen + 64;
+    bd.max_rounds = spm::fixpoint_round_cap(max_gen);
     bd.sssp_blocks = spm::sssp_batched_grid_blocks();
     bd.flood_smem = 0;
     bd.any_maps = 0;
@@ -925,12 +993,8 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     if (!s) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null scene");
     spm_status st = check_device(s);
     if (st != SPM_OK) return st;
-    const size_t npx = (size_t)s->hs.Nx * s->hs.Ny;
-    if (!s->stage_dist) {
-        s->stage_dist = dalloc<float>(s, npx);
-        s->stage_par = dalloc<int32_t>(s, npx);
-        if (!s->stage_dist || !s->stage_par) return set_err(s, SPM_ERR_OOM, "staging allocation failed");
-    }
+    st = ensure_stage(s);
+    if (st != SPM_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
@@ -994,37 +1058,45 @@ spm_status spm_scene_phase_ms(spm_scene *s, float *vertex_ms, float *cull_ms, fl
     return SPM_OK;
 }
 
+// Tape of the differentiable form: per agent its first gradient component
+// (int32) and up to four values (float4), as two arrays.
+static size_t tape_slot_bytes(int32_t n) { return ((size_t)n * sizeof(int32_t) + 15) & ~(size_t)15; }
+
+int64_t spm_agents_tape_bytes(int32_t n) {
+    return n < 0 ? 0 : (int64_t)(tape_slot_bytes(n) + (size_t)n * sizeof(float4));
+}
+
 spm_status spm_agents_forward(spm_scene *s, void *stream, const int32_t *agents_dev, int32_t n,
-                              const float *dist_dev, const int32_t *parent_dev, float *loss_dev) {
-    if (!s || !agents_dev || n < 0 || !dist_dev || !parent_dev || !loss_dev)
+                              const float *dist_dev, const int32_t *parent_dev, float *loss_dev, void *tape_dev) {
+    if (!s || (n > 0 && !agents_dev) || n < 0 || !dist_dev || !loss_dev || (tape_dev && !parent_dev))
         return set_err(s, SPM_ERR_INVALID_ARG, "bad argument");
+    if (tape_dev && (reinterpret_cast<uintptr_t>(tape_dev) & 15))
+        return set_err(s, SPM_ERR_INVALID_ARG, "tape must be 16-byte aligned");
     spm_status st = check_device(s);
     if (st != SPM_OK) return st;
-    if (n > s->agent_cap) {  // scratch for the backward pass, allocated on growth
-        s->root = dalloc<int32_t>(s, s->hs.n_gen);
-        s->lastpt = dalloc<float2>(s, s->hs.n_gen);
-        s->slot = dalloc<int32_t>(s, n);
-        s->val = dalloc<float4>(s, n);
-        if (!s->root || !s->lastpt || !s->slot || !s->val) return set_err(s, SPM_ERR_OOM, "agent scratch");
-        s->agent_cap = n;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    spm::launch_agents_forward(s->ds, cs, agents_dev, n, dist_dev, loss_dev);
+    if (tape_dev) {
+        unsigned char *t = static_cast<unsigned char *>(tape_dev);
+        spm::launch_agents_contrib(s->ds, cs, agents_dev, n, parent_dev, s->root, s->lastpt,
+                                   reinterpret_cast<int32_t *>(t), reinterpret_cast<float4 *>(t + tape_slot_bytes(n)));
     }
-    s->agents = agents_dev;
-    s->n_agents = n;
-    s->agent_parent = parent_dev;
-    spm::launch_agents_forward(s->ds, static_cast<cudaStream_t>(stream), agents_dev, n, dist_dev, loss_dev);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPM_OK : set_err(s, SPM_ERR_CUDA, cudaGetErrorString(e));
 }
 
-spm_status spm_agents_backward(spm_scene *s, void *stream, float *grad_points_dev, float *grad_segs_dev) {
-    if (!s || !s->agents) return set_err(s, SPM_ERR_INVALID_ARG, "no forward call recorded");
+spm_status spm_agents_backward(spm_scene *s, void *stream, const void *tape_dev, int32_t n, float *grad_points_dev,
+                               float *grad_segs_dev) {
+    if (!s || n < 0 || (n > 0 && !tape_dev)) return set_err(s, SPM_ERR_INVALID_ARG, "bad argument");
     if ((s->hs.points.size() && !grad_points_dev) || (s->hs.segs.size() && !grad_segs_dev))
         return set_err(s, SPM_ERR_INVALID_ARG, "null gradient buffer");
     spm_status st = check_device(s);
     if (st != SPM_OK) return st;
-    spm::launch_agents_backward(s->ds, static_cast<cudaStream_t>(stream), s->agents, s->n_agents,
-                                s->agent_parent, s->root, s->lastpt, s->slot, s->val, grad_points_dev,
-                                grad_segs_dev);
+    const unsigned char *t = static_cast<const unsigned char *>(tape_dev);
+    spm::launch_agents_reduce((int)s->hs.points.size() / 2, (int)s->hs.segs.size() / 4,
+                              static_cast<cudaStream_t>(stream), reinterpret_cast<const int32_t *>(t),
+                              reinterpret_cast<const float4 *>(t + tape_slot_bytes(n)), n, s->grad_partial,
+                              grad_points_dev, grad_segs_dev);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPM_OK : set_err(s, SPM_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -97,15 +97,20 @@ __global__ void k_agent_contrib(DevScene ds, const int32_t *agents, int n, const
     }
 }
 
-// One CTA per output component, fixed summation order.
-__global__ void __launch_bounds__(256) k_agent_reduce(const int32_t *slot, const float4 *val, int n,
-                                                      int n_pt2, float *grad_pts, float *grad_segs) {
+// Gradient of the loss from the agents' contributions, reduced in a fixed
+// order so that results are deterministic: agents are cut into `chunks`
+// fixed ranges; CTA (o, b) sums component o over range b (a fixed per-thread
+// stride, then a fixed tree) into partial[o * chunks + b] (FP64); then one
+// thread per component sums its partials in range order.
+__global__ void __launch_bounds__(256) k_agent_partial(const int32_t *slot, const float4 *val, int n, int chunks,
+                                                       double *partial) {
     __shared__ double part[256];
-    const int o = blockIdx.x;
+    const int o = blockIdx.x, b = blockIdx.y;
+    const int a0 = (int)((long long)n * b / chunks), a1 = (int)((long long)n * (b + 1) / chunks);
     double s = 0.0;
-    for (int a = threadIdx.x; a < n; a += blockDim.x) {
-        const int d = o - slot[a];
-        if (slot[a] < 0 || d < 0 || d > 3) continue;
+    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+        const int sl = slot[a], d = o - sl;
+        if (sl < 0 || d < 0 || d > 3) continue;
         const float4 v = val[a];
         s += (double)(d == 0 ? v.x : d == 1 ? v.y : d == 2 ? v.z : v.w);
     }
@@ -115,29 +120,52 @@ __global__ void __launch_bounds__(256) k_agent_reduce(const int32_t *slot, const
         if ((int)threadIdx.x < k) part[threadIdx.x] += part[threadIdx.x + k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const float g = (float)(part[0] / (double)max(n, 1));
-        if (o < n_pt2) grad_pts[o] = g;
-        else grad_segs[o - n_pt2] = g;
-    }
+    if (threadIdx.x == 0) partial[(size_t)o * chunks + b] = part[0];
+}
+
+__global__ void k_agent_final(const double *partial, int chunks, int n, int n_out, int n_pt2, float *grad_pts,
+                              float *grad_segs) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_out) return;
+    double s = 0.0;
+    for (int b = 0; b < chunks; ++b) s += partial[(size_t)o * chunks + b];
+    const float g = (float)(s / (double)max(n, 1));
+    if (o < n_pt2) grad_pts[o] = g;
+    else grad_segs[o - n_pt2] = g;
 }
 
 }  // namespace
+
+// Agent chunks of the two-level reduction for n_out gradient components:
+// at most 64, and at most kGradPartials partial sums in all.
+int grad_chunks(int n_out) { return n_out <= 0 ? 1 : max(1, min(64, kGradPartials / n_out)); }
 
 void launch_agents_forward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
                            const float *dist, float *loss) {
     k_loss<<<1, 1024, 0, st>>>(agents, n, ds.Nx, ds.Ny, dist, loss);
 }
 
-void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
-                            const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot,
-                            float4 *val, float *grad_pts, float *grad_segs) {
+void launch_agents_contrib(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
+                           const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot, float4 *val) {
     k_root_table<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds, root, lastpt);
     const int blocks = n > 0 ? min((n + 255) / 256, 152 * 8) : 1;
     k_agent_contrib<<<blocks, 256, 0, st>>>(ds, agents, n, parent, root, lastpt, slot, val);
-    const int n_pt2 = 2 * (ds.n_src - 3 * ds.n_seg);
-    const int n_out = n_pt2 + 4 * ds.n_seg;
-    if (n_out > 0) k_agent_reduce<<<n_out, 256, 0, st>>>(slot, val, n, n_pt2, grad_pts, grad_segs);
+}
+
+void launch_agents_reduce(int n_pts, int n_seg, cudaStream_t st, const int32_t *slot, const float4 *val, int n,
+                          double *partial, float *grad_pts, float *grad_segs) {
+    const int n_pt2 = 2 * n_pts, n_out = n_pt2 + 4 * n_seg;
+    if (n_out <= 0) return;
+    const int chunks = grad_chunks(n_out);
+    k_agent_partial<<<dim3(n_out, chunks), 256, 0, st>>>(slot, val, n, chunks, partial);
+    k_agent_final<<<(n_out + 255) / 256, 256, 0, st>>>(partial, chunks, n, n_out, n_pt2, grad_pts, grad_segs);
+}
+
+void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
+                            const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot,
+                            float4 *val, double *partial, float *grad_pts, float *grad_segs) {
+    launch_agents_contrib(ds, st, agents, n, parent, root, lastpt, slot, val);
+    launch_agents_reduce(ds.n_src - 3 * ds.n_seg, ds.n_seg, st, slot, val, n, partial, grad_pts, grad_segs);
 }
 
 }  // namespace spm
@@ -160,8 +188,10 @@ constexpr size_t kNaRootOff = 0;
 constexpr size_t kNaLastOff = kNaRootOff + sizeof(int32_t) * SPM_NOALLOC_MAX_GENERATORS;
 constexpr size_t kNaSlotOff = kNaLastOff + sizeof(float2) * SPM_NOALLOC_MAX_GENERATORS;
 constexpr size_t kNaValOff = kNaSlotOff + sizeof(int32_t) * SPM_NOALLOC_MAX_AGENTS;
-constexpr size_t kNaBytes = kNaValOff + sizeof(float4) * SPM_NOALLOC_MAX_AGENTS;
-static_assert(kNaLastOff % 16 == 0 && kNaSlotOff % 16 == 0 && kNaValOff % 16 == 0, "alignment");
+constexpr size_t kNaPartOff = kNaValOff + sizeof(float4) * SPM_NOALLOC_MAX_AGENTS;
+constexpr size_t kNaBytes = kNaPartOff + sizeof(double) * kGradPartials;
+static_assert(kNaLastOff % 16 == 0 && kNaSlotOff % 16 == 0 && kNaValOff % 16 == 0 && kNaPartOff % 16 == 0,
+              "alignment");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -220,14 +250,15 @@ extern "C" spm_status spm_agents_backward_noalloc(spm_scene *scene, void *stream
         return SPM_ERR_CUDA;
     }
     // Every scratch element the kernels read is written earlier in the same
-    // call (root/lastpt for all generators, slot/val for all n agents), so
-    // nothing needs clearing between calls.
+    // call (root/lastpt for all generators, slot/val for all n agents, one
+    // partial sum per chunk and component), so nothing needs clearing
+    // between calls.
     launch_agents_backward(ds, static_cast<cudaStream_t>(stream), agents_dev, n, parent_dev,
                            reinterpret_cast<int32_t *>(base + kNaRootOff),
                            reinterpret_cast<float2 *>(base + kNaLastOff),
                            reinterpret_cast<int32_t *>(base + kNaSlotOff),
-                           reinterpret_cast<float4 *>(base + kNaValOff), grad_points_dev,
-                           grad_segs_dev);
+                           reinterpret_cast<float4 *>(base + kNaValOff),
+                           reinterpret_cast<double *>(base + kNaPartOff), grad_points_dev, grad_segs_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         scene_set_error(scene, cudaGetErrorString(e));

@@ -165,10 +165,6 @@ struct DevScene {
     // compute floods only the sources
     int32_t *static_tile_count;        // ntiles (small-tile sizing)
     int32_t *static_counts;            // 4
-    // differentiable form
-    float *agent_accum;                // scratch for deterministic reductions
-    const int32_t *agents;
-    int32_t n_agents;
 };
 
 // A batch of scenes computed together (device-side descriptor).
@@ -227,6 +223,7 @@ void launch_flood_batched(const BatchDev &b, cudaStream_t st);
 void launch_query_exact(const DevScene &ds, cudaStream_t st, const int32_t *field_parent, int i, int j, int qx,
                         int qy, double fx, double fy, int32_t *out_par, double *out_dist);
 int sssp_batched_grid_blocks();
+int fixpoint_round_cap(int n_gen);  // rounds the vertex fixpoint may take (test hook aside: 4 n_gen + 64)
 bool flood_possible(int tiles, int polys);
 size_t flood_smem_bytes(int tiles, int polys, bool maps);  // dynamic shared memory of one flood CTA
 int flood_smem_attr();
@@ -234,9 +231,20 @@ int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();
+// differentiable form (spm_grad.cu): the per-agent contributions of the
+// root links (slot = first gradient component, val = up to four values), and
+// their deterministic two-level reduction into the gradient
+constexpr int kGradPartials = 65536;  // partial sums of the reduction (chunks x components)
+int grad_chunks(int n_out);
+void launch_agents_forward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n, const float *dist,
+                           float *loss);
+void launch_agents_contrib(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
+                           const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot, float4 *val);
+void launch_agents_reduce(int n_pts, int n_seg, cudaStream_t st, const int32_t *slot, const float4 *val, int n,
+                          double *partial, float *grad_pts, float *grad_segs);
 void launch_agents_backward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
                             const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot,
-                            float4 *val, float *grad_pts, float *grad_segs);
+                            float4 *val, double *partial, float *grad_pts, float *grad_segs);
 }  // namespace spm
 
 struct spm_scene;

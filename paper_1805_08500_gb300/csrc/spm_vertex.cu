@@ -25,6 +25,7 @@
 // Costs are FP64 with explicitly rounded operations, so they match a plain
 // FP64 Dijkstra over the same edges bit for bit.
 #include <cooperative_groups.h>
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include "spm_device.cuh"
@@ -995,6 +996,14 @@ __global__ void k_finalize_b(const __grid_constant__ BatchDev b) {
 
 int vis_resident_blocks();  // co-resident CTAs of the visibility-pair kernel
 
+// Round cap of the vertex fixpoint: 4 rounds per generator and 64 more (far
+// above the longest shortest path in links), or the test hook's override.
+std::atomic<int> g_round_cap_override{0};
+int fixpoint_round_cap(int n_gen) {
+    const int o = g_round_cap_override.load();
+    return o > 0 ? o : 4 * n_gen + 64;
+}
+
 // Visibility-pair kernel over ds's pair range (resident CTAs, runs sized so
 // that every resident warp takes about two).
 void launch_pairs(const DevScene &ds, cudaStream_t st) {
@@ -1040,7 +1049,7 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
     }
     if (graph_done) cudaEventRecord(graph_done, st);  // the visibility graph is built
     DevScene arg = ds;
-    int max_rounds = 4 * ds.n_gen + 64;
+    int max_rounds = fixpoint_round_cap(ds.n_gen);
     void *args[] = {&arg, &max_rounds};
     if (ds.solo_smem > 0) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(ds, max_rounds);
     cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
@@ -1102,6 +1111,8 @@ void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st) {
 }
 
 }  // namespace spm
+
+extern "C" void spm_debug_set_round_cap(int32_t n) { spm::g_round_cap_override.store(n > 0 ? n : 0); }
 
 #ifdef SPM_COUNT
 // Instrumentation build only: reads and clears this unit's work counters.

@@ -699,9 +699,10 @@ def test_allocation_failure_is_reported_and_cleaned_up(spm):
 
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_buffer_compute_matches_device_compute(spm, pinned):
-    """spm_compute_host (the pixel pass in row slabs, each copied to the host
-    while the next one computes) writes the device compute's map bit for
-    bit, into pinned or pageable host memory."""
+    """spm_compute_host writes the device compute's map bit for bit: into
+    page-locked memory directly from the pixel pass (pinned), or through row
+    slabs copied to page-locked bounce buffers while the next slab computes
+    and moved on by the host (pageable)."""
     scene = sg.maze(6, cells=12, N=768)
     s = spm.Scene(scene)
     spm.spm_scene_set_tuning(s.handle, 3, 256, 32, 1)
@@ -771,3 +772,101 @@ def test_exact_point_query(spm, oracle_mod, which):
         elif g >= 0:
             assert d >= np.float32(d_ref) * (1 - 1e-6)  # another valid parent is never shorter
     assert agree >= 0.97 * np.isfinite(od).sum()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_queries_after_host_buffer_compute(spm, pinned):
+    """After a host-buffer compute, queries never read the caller's host
+    buffers (which may be unpinned or freed at any time): after a direct write
+    into page-locked memory they report that no device field exists; after a
+    pageable compute they read the library's own device copy."""
+    scene = sg.plain_polys(7, n_polys=80, N=256, n_segs=1)
+    s = spm.Scene(scene)
+    d_ref, p_ref = s.compute()
+    s.sync()
+    Ny, Nx = scene.grid[1], scene.grid[0]
+    if pinned:
+        hd = torch.empty((Ny, Nx), dtype=torch.float32).pin_memory()
+        hp = torch.empty((Ny, Nx), dtype=torch.int32).pin_memory()
+    else:
+        hd = np.empty((Ny, Nx), np.float32)
+        hp = np.empty((Ny, Nx), np.int32)
+    spm.spm_compute_host(s.handle, None, hd, hp)
+    del hd, hp  # the caller lets its buffers go
+    h = scene.world[0] / Nx
+    rng = np.random.default_rng(4)
+    pref = p_ref.cpu().numpy()
+    for x, y in rng.uniform(0, scene.world[0], (20, 2)):
+        if pinned:
+            with pytest.raises(spm.SpmError) as e:
+                s.query_parent(x, y)
+            assert e.value.status == spm.SPM_ERR_INVALID_ARG
+            with pytest.raises(spm.SpmError) as e:
+                s.query_exact(x, y)
+            assert e.value.status == spm.SPM_ERR_INVALID_ARG
+        else:
+            par, _ = s.query_parent(x, y)
+            assert par == pref[int(y // h), int(x // h)]
+            s.query_exact(x, y)
+    s.compute()  # a device compute makes the queries available again
+    s.sync()
+    s.query_parent(1.0, 1.0)
+
+
+def test_round_cap_reports_not_converged(spm):
+    """The fixpoint's failure path: with its round cap forced to 1 (the
+    library's test hook), a maze that needs hundreds of rounds reports
+    SPM_ERR_NOT_CONVERGED at the next sync -- the kernel stops and returns,
+    nothing waits -- and the next compute with the default cap gives bit for
+    bit the map of a fresh scene. Also for a dense graph (the multi-SM
+    fixpoint)."""
+    lib = spm.load_library()
+    for scene in (sg.maze(6, cells=12, N=768), sg.plain_polys(3, W=4096, N=256, n_polys=150)):
+        s = spm.Scene(scene)
+        try:
+            lib.spm_debug_set_round_cap(1)
+            s.compute()
+            with pytest.raises(spm.SpmError) as e:
+                s.sync()
+            assert e.value.status == spm.SPM_ERR_NOT_CONVERGED, scene.name
+        finally:
+            lib.spm_debug_set_round_cap(0)
+        d, p = s.compute()
+        s.sync()
+        fresh = spm.Scene(scene)
+        d0, p0 = fresh.compute()
+        fresh.sync()
+        assert torch.equal(p, p0) and torch.equal(d.view(torch.int32), d0.view(torch.int32)), scene.name
+        assert s.info()["rounds"] > 1
+
+
+def test_backward_is_the_gradient_of_its_own_forward(spm, oracle_mod):
+    """Each agent_loss keeps what its backward needs: two forwards on one
+    scene with the sources moved in between, then both backwards, give each
+    forward's own oracle gradient; and moving the sources again (and
+    recomputing) after a forward does not change that forward's gradient."""
+    base = sg.differentiable(4, W=1024, N=256, n_polys=20, n_agents=3000)
+    moved = sg.Scene(base.world, base.grid, base.polys, base.points.copy(), base.segs.copy())
+    moved.points[0] += (7.0, -5.0)
+    moved.segs[0] += (3.0, 2.0, 3.0, 2.0)
+    d, _, _, _ = oracle_mod.Oracle(base).pixels(base.agents)
+    agents = base.agents[np.isfinite(d)]
+    refs = [oracle_mod.Oracle(sc).agent_loss_and_grad(agents) for sc in (base, moved)]
+    s = spm.Scene(base)
+    ag = torch.tensor(agents, dtype=torch.int32, device="cuda")
+    leaves, losses = [], []
+    for sc in (base, moved):
+        pts = torch.tensor(sc.points, dtype=torch.float32, device="cuda", requires_grad=True)
+        segs = torch.tensor(sc.segs, dtype=torch.float32, device="cuda", requires_grad=True)
+        losses.append(spm.agent_loss(s, pts, segs, ag))
+        leaves.append((pts, segs))
+    # another move and compute before any backward
+    s.update_sources(base.points, base.segs)
+    s.compute()
+    losses[1].backward()
+    losses[0].backward()
+    s.sync()
+    for (loss_ref, gp_ref, gs_ref), loss, (pts, segs) in zip(refs, losses, leaves):
+        assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+        np.testing.assert_allclose(pts.grad.cpu().numpy(), gp_ref, atol=1e-4)
+        np.testing.assert_allclose(segs.grad.cpu().numpy(), gs_ref, atol=1e-4)
