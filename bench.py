@@ -297,12 +297,33 @@ def run_reference(args, cfg_desc, scene):
     print(json.dumps(line), flush=True)
 
 
+def tune_by_size_class(spm, objs, scenes, prefix, culling):
+    """Culling per size class (grid side) of a batch: the autotuner on the
+    class's scene of median polygon count (cached per class and GPU), then
+    applied to every scene of the class. Fixed modes when culling is not
+    'autotune'."""
+    tunings = {}
+    for side in sorted({sc.grid[0] for sc in scenes}):
+        idx = sorted((k for k, sc in enumerate(scenes) if sc.grid[0] == side), key=lambda k: len(scenes[k].polys))
+        rep = idx[len(idx) // 2]
+        if culling == "autotune":
+            t = objs[rep].autotune(cache_key=f"{prefix}-side{side}")
+        else:
+            t = {"flood_mode": {"auto": 0, "flood": 1, "scan": 2}[culling], "hidden_chunk": 32, "tile": 0, "maps": 0,
+                 "source": "fixed"}
+        tunings[side] = t
+    for k, o in enumerate(objs):
+        t = tunings[scenes[k].grid[0]]
+        spm.spm_scene_set_tuning(o.handle, t["flood_mode"], t["hidden_chunk"], t["tile"], t["maps"])
+    return {str(side): t for side, t in tunings.items()}
+
+
 def run_batched(args, cfg_desc, scenes):
     """Batched form: all scenes in one batch (batched vertex phase, one
     persistent pixel kernel, replayed from a CUDA graph); value = scenes/s.
-    Under torchrun the job is 256 scenes per rank (seeded set of
-    256 x world scenes), dealt to ranks longest-first by pixel count; ranks
-    share no data."""
+    Culling is tuned per size class. Under torchrun the job is 256 scenes per
+    rank (seeded set of 256 x world scenes), dealt to ranks longest-first by
+    pixel count; ranks share no data."""
     import torch
     import torch.distributed as dist
     import paper_1805_08500_gb300 as spm
@@ -316,9 +337,7 @@ def run_batched(args, cfg_desc, scenes):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", torch.cuda.current_device())
     objs = [spm.Scene(sc) for sc in scenes]
-    mode = 2 if args.culling == "scan" else 1  # flooded lists unless full scans are asked for
-    for o in objs:  # the default tile follows each scene's pixel size
-        spm.spm_scene_set_tuning(o.handle, mode, 32, 0)
+    tunings = tune_by_size_class(spm, objs, scenes, "batched256", args.culling)  # set-up, not timed
     batch = spm.Batch(objs)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -327,6 +346,7 @@ def run_batched(args, cfg_desc, scenes):
         batch.compute(stream)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -336,6 +356,7 @@ def run_batched(args, cfg_desc, scenes):
             ev[k][0].record(stream)
             batch.compute(stream)
             ev[k][1].record(stream)
+            phases.append(batch.phase_ms())  # events inside the batch's graph
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -344,19 +365,76 @@ def run_batched(args, cfg_desc, scenes):
     total_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev])), world, dev)
     ms = total_ms / args.steps
     npx_all = sum(sc.grid[0] * sc.grid[1] for sc in all_scenes)
+    vert_ms = float(np.mean([p[0] for p in phases]))
+    pix_ms = float(np.mean([p[1] for p in phases]))
+    # end to end through the public API: every scene's sources up from
+    # page-locked host memory (one copy, then a device-side move per scene),
+    # the batch, and every output plane down into page-locked host memory
+    src = [np.concatenate([np.asarray(sc.points, np.float32).reshape(-1), np.asarray(sc.segs, np.float32).reshape(-1)])
+           for sc in scenes]
+    offs = np.cumsum([0] + [len(a) for a in src])
+    h_src = torch.tensor(np.concatenate(src) if offs[-1] else np.zeros(1, np.float32)).pin_memory()
+    d_src = torch.empty_like(h_src, device=dev)
+    outs = batch.outputs
+    h_out = [(torch.empty(d.shape, dtype=d.dtype).pin_memory(), torch.empty(p.shape, dtype=p.dtype).pin_memory())
+             for d, p in outs]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d_src.copy_(h_src, non_blocking=True)
+        for k, (sc, o) in enumerate(zip(scenes, objs)):
+            npt = 2 * len(sc.points)
+            a, b2 = int(offs[k]), int(offs[k + 1])
+            spm.spm_scene_update_sources_device(o.handle, stream, d_src[a:a + npt] if npt else None,
+                                                d_src[a + npt:b2] if b2 > a + npt else None)
+        batch.compute(stream)
+        for (d, p), (hd, hp) in zip(outs, h_out):
+            hd.copy_(d, non_blocking=True)
+            hp.copy_(p, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    peaks, peak_src = load_peaks()
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = FP32_LANES * N_SMS * 2 * clock_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_PIXEL * npx / (pix_ms * 1e-3) / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    write_gbs = 8.0 * npx / (pix_ms * 1e-3) / 1e9
     line = {"metric": "SPM batched scenes/s", "value": len(all_scenes) / (ms * 1e-3), "unit": "scenes/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+i32 (f64 vertex costs)", "data": "synthetic",
             "config": {"workload": "batched256", "scene": cfg_desc, "scenes": len(all_scenes),
                        "pixels": npx_all, "l2": "flushed between timed steps (256 MiB write)",
-                       "launch": "one CUDA graph per step",
-                       "culling": "flooded per-tile lists" if mode != 2 else "every tile scans every generator"},
+                       "launch": "one CUDA graph per step", "tuning_by_grid_side": tunings},
             "mpixel_per_s": npx_all / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
-            # 7 vertex-phase kernels, the list reset, [flood, scan, fill], 1 persistent pixel kernel
-            "gpu_launches": (9 + (3 if mode != 2 else 0)) * args.steps}
+            "phases_ms": {"vertex_and_lists": vert_ms, "pixel": pix_ms},
+            "roofline": {"bound": "alu", "kernel": "k_pixels_batched", "achieved": achieved, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                         "note": f"algorithmic = {FLOPS_PER_PIXEL} FP32 flops/pixel (winning distance) over the "
+                                 f"persistent pixel kernel's event-timed duration; peak = FP32 lanes x SMs x 2 x max "
+                                 f"SM clock ({peak_src})"},
+            "hbm_write": {"achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": write_gbs / hbm_peak,
+                          "bytes_per_pixel": 8, "peak_source": peak_src},
+            "e2e": {"value": len(all_scenes) / e2e_s, "unit": "scenes/s",
+                    "h2d_bytes_per_step": int(4 * offs[-1]), "d2h_bytes_per_step": int(8 * npx),
+                    "host_buffers": "page-locked"},
+            # vertex phase (7), list reset, flood, scan, fill, the persistent pixel kernel
+            "gpu_launches": 12 * args.steps}
     if world > 1:
         line["config"]["parallelism"] = f"scenes sharded longest-first over {world} ranks"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build_oracle()
+        nthreads = oracle.default_threads()
+        k = 8  # scenes sampled, extrapolated to the batch
+        t0 = time.perf_counter()
+        t = sum(_oracle_scene_seconds(scenes[(i * 31) % len(scenes)], 20000, i, nthreads) for i in range(k))
+        used = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k / t, "unit": "scenes/s", "cores": nthreads, "kind": "oracle",
+                                "sample": f"{k} of the {len(scenes)} scenes (oracle vertex phase + 20000 seeded "
+                                          f"pixels each, extrapolated to their grids; {used:.1f} s wall on "
+                                          f"{nthreads} threads)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
@@ -515,6 +593,14 @@ def run_differentiable(args, cfg_desc, scene):
         torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, world, dev)
     info = s.info()
+    Nx, Ny = scene.grid
+    npx = Nx * Ny
+    peaks, peak_src = load_peaks()
+    pix_ms = float(np.mean([p[2] for p in phases]))  # the map's pixel pass, the step's dominant kernel
+    peak_tflops = FP32_LANES * N_SMS * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = FLOPS_PER_PIXEL * npx / (pix_ms * 1e-3) / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    write_gbs = 8.0 * npx / (pix_ms * 1e-3) / 1e9
     line = {"metric": "SPM differentiable step ms (forward + backward), 2048^2, 100k agents",
             "value": fwd + bwd, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": fwd + bwd, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -523,6 +609,15 @@ def run_differentiable(args, cfg_desc, scene):
                        "l2": "flushed between timed steps (256 MiB write)", "tuning": tuning,
                        "parallelism": f"replicas x{world} (the slowest rank's step)"},
             "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "phases_ms": {"vertex": float(np.mean([p[0] for p in phases])),
+                          "cull": float(np.mean([p[1] for p in phases])), "pixel": pix_ms},
+            "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                         "note": f"the forward's map: algorithmic = {FLOPS_PER_PIXEL} FP32 flops/pixel (winning "
+                                 f"distance) over the pixel pass's event-timed duration; peak = FP32 lanes x SMs "
+                                 f"x 2 x max SM clock ({peak_src})"},
+            "hbm_write": {"achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": write_gbs / hbm_peak,
+                          "bytes_per_pixel": 8, "peak_source": peak_src},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(pts.nbytes + segs.nbytes),
                     "d2h_bytes_per_step": int(h_out.numel() * 4)},

@@ -181,12 +181,20 @@ spm_status spm_compute_batched(spm_scene *const *scenes, int32_t n, void *stream
  * buffers of scene k's grid, fixed for the batch's lifetime. Creation
  * allocates the batch's device descriptors; compute allocates nothing. The
  * scenes must outlive the batch; culling and tile settings are read at
- * creation. */
+ * creation. A scene in the geometric flood mode (flood_mode 3) floods only
+ * its sources in the batch, over the lists of its obstacle vertices built
+ * once (at creation, or again by a compute whose tuning replaced them). */
 typedef struct spm_batch spm_batch;
 spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *dist,
                             int32_t *const *parent, spm_batch **out);
 spm_status spm_batch_compute(spm_batch *batch, void *stream);
 void spm_batch_destroy(spm_batch *batch);
+
+/* Device time of the last spm_batch_compute, in milliseconds, from events
+ * recorded inside its launch sequence (event nodes of its CUDA graph):
+ * vertex_ms = every scene's vertex phase and candidate lists, pixel_ms = the
+ * persistent pixel kernel. Waits for that compute. */
+spm_status spm_batch_phase_ms(spm_batch *batch, float *vertex_ms, float *pixel_ms);
 
 /* Waits for the scene's last work on `stream` and returns the first latched
  * device-side or CUDA error (SPM_OK if none), clearing it. */

@@ -92,6 +92,7 @@ def load_library():
         "spm_batch_create": ([P, I32, P, P, P], I32),
         "spm_batch_compute": ([P, P], I32),
         "spm_batch_destroy": ([P], None),
+        "spm_batch_phase_ms": ([P, P, P], I32),
         "spm_scene_sync": ([P, P], I32),
         "spm_query_parent": ([P, F, F, P, P], I32),
         "spm_query_exact": ([P, F, F, P, P], I32),
@@ -255,6 +256,14 @@ def spm_batch_compute(batch, stream=None):
     _check(load_library().spm_batch_compute(batch, _stream_handle(stream)), "spm_batch_compute")
 
 
+def spm_batch_phase_ms(batch):
+    """(vertex_ms, pixel_ms) of the last batch compute, from events inside its launch sequence."""
+    v = ctypes.c_float()
+    p = ctypes.c_float()
+    _check(load_library().spm_batch_phase_ms(batch, ctypes.byref(v), ctypes.byref(p)), "spm_batch_phase_ms")
+    return v.value, p.value
+
+
 def spm_batch_destroy(batch):
     if batch:
         load_library().spm_batch_destroy(batch)
@@ -272,6 +281,9 @@ class Batch:
     def compute(self, stream=None):
         spm_batch_compute(self.handle, stream)
         return self.outputs
+
+    def phase_ms(self):
+        return spm_batch_phase_ms(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -667,13 +667,19 @@ spm_status spm_compute_host(spm_scene *s, void *stream, float *dist_host, int32_
 
 struct spm_batch {
     std::vector<spm_scene *> scenes;
+    std::vector<spm::DevScene> descs;  // the scenes' descriptors as the batch runs them
     int device = 0;
     std::vector<void *> allocs;
     spm::BatchDev dev{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t graph_stream = nullptr;
+    cudaStream_t graph_stream = nullptr;  // the graph runs here, ordered with the caller's stream by events
+    cudaEvent_t fork = nullptr, join = nullptr;
     bool capture_failed = false;
+    // phase events (start, vertex phase and flood done, end), recorded as
+    // event nodes of the batch's graph
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool ev_valid = false;
 };
 
 namespace {
@@ -697,13 +703,46 @@ T *bupload(spm_batch *b, const std::vector<T> &v, bool &ok) {
 void batch_free(spm_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t *e : {&b->ev[0], &b->ev[1], &b->ev[2], &b->fork, &b->join})
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    if (b->graph_stream) {
+        cudaStreamDestroy(b->graph_stream);
+        b->graph_stream = nullptr;
+    }
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
 }
-void batch_launch(spm_batch *b, cudaStream_t st) {
+// Builds the static part of the geometric flood (obstacle vertices) that
+// descriptor d -- the scene's own or a batch's copy -- reads, and waits.
+bool build_flood_static(spm_scene *s, const spm::DevScene &d) {
+    spm::launch_flood(d, nullptr, spm::FloodStatic::kBuild);
+    if (cudaStreamSynchronize(nullptr) != cudaSuccess) return false;
+    s->flood_static_ok = true;
+    s->flood_static_tile = d.tile;
+    s->flood_static_maps = d.use_maps && d.gen_maps ? 1 : 0;
+    return true;
+}
+
+bool flood_static_matches(const spm_scene *s, const spm::DevScene &d) {
+    return s->flood_static_ok && s->flood_static_tile == d.tile &&
+           s->flood_static_maps == (d.use_maps && d.gen_maps ? 1 : 0);
+}
+
+void batch_launch(spm_batch *b, cudaStream_t st, bool capturing) {
+    // while capturing, external records become event nodes of the graph
+    auto rec = [&](cudaEvent_t e) {
+        if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else cudaEventRecord(e, st);
+    };
+    rec(b->ev[0]);
     spm::launch_vertex_phase_batched(b->dev, st);
     spm::launch_flood_batched(b->dev, st);
+    rec(b->ev[1]);
     spm::launch_pixel_phase_batched(b->dev, st);
+    rec(b->ev[2]);
 }
 }  // namespace
 
@@ -724,12 +763,24 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     b->device = dev;
     std::vector<spm::DevScene> descs(n);
     std::vector<long long> pair_off(n + 1, 0), bits_off(n + 1, 0);
-    std::vector<int32_t> vert_off(n + 1, 0), gen_off(n + 1, 0), order(n), tile_off(n + 1, 0);
+    std::vector<int32_t> vert_off(n + 1, 0), gen_off(n + 1, 0), order(n), tile_off(n + 1, 0), flood_off(n + 1, 0);
     std::vector<float *> dv(dist, dist + n);
     std::vector<int32_t *> pv(parent, parent + n);
     int max_gen = 0;
     for (int k = 0; k < n; ++k) {
         descs[k] = scenes[k]->ds;
+        // geometric floods reuse the obstacle vertices' static lists: built
+        // here if the scene has none for this tile size and map setting
+        descs[k].flood_reuse = 0;
+        if (descs[k].use_flood && descs[k].flood_mode == 3 && descs[k].static_tile_count) {
+            if (!flood_static_matches(scenes[k], descs[k]) && !build_flood_static(scenes[k], descs[k])) {
+                delete b;
+                return set_err(nullptr, SPM_ERR_CUDA, "static flood build failed");
+            }
+            descs[k].flood_reuse = 1;
+        }
+        const bool floods = descs[k].use_flood && descs[k].flood_mode != 2;
+        flood_off[k + 1] = flood_off[k] + (floods ? (descs[k].flood_reuse ? descs[k].n_src : descs[k].n_gen) : 0);
         pair_off[k + 1] = pair_off[k] + (long long)descs[k].n_vert * descs[k].pair_words;
         bits_off[k + 1] = bits_off[k] + (long long)descs[k].n_vert * descs[k].vis_words;
         vert_off[k + 1] = vert_off[k] + descs[k].n_vert;
@@ -750,6 +801,7 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     bd.bits_off = bupload(b, bits_off, ok);
     bd.vert_off = bupload(b, vert_off, ok);
     bd.gen_off = bupload(b, gen_off, ok);
+    bd.flood_off = bupload(b, flood_off, ok);
     bd.order = bupload(b, order, ok);
     bd.tile_off = bupload(b, tile_off, ok);
     bd.total_tiles = tile_off[n];
@@ -777,6 +829,18 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
         delete b;
         return set_err(nullptr, SPM_ERR_OOM, "batch allocation failed");
     }
+    for (cudaEvent_t &e : b->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->graph_stream, cudaStreamNonBlocking) != cudaSuccess)
+        ok = false;
+    if (!ok) {
+        batch_free(b);
+        delete b;
+        return set_err(nullptr, SPM_ERR_CUDA, "event creation failed");
+    }
+    b->descs = descs;
     *out = b;
     return SPM_OK;
 }
@@ -787,36 +851,69 @@ spm_status spm_batch_compute(spm_batch *b, void *stream) {
     if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
         return set_err(nullptr, SPM_ERR_INVALID_ARG, "batch used on another device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (!b->exec && !b->capture_failed && st != nullptr) {  // capture once into a CUDA graph
-        cudaGraph_t g = nullptr;
-        bool okc = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (okc) {
-            batch_launch(b, st);
-            okc = cudaStreamEndCapture(st, &g) == cudaSuccess && g != nullptr;
+    // a single-scene compute in another flood mode may have replaced a
+    // scene's static lists since: rebuild them before the batch reads them
+    for (size_t k = 0; k < b->scenes.size(); ++k)
+        if (b->descs[k].flood_reuse && !flood_static_matches(b->scenes[k], b->descs[k])) {
+            if (cudaStreamSynchronize(st) != cudaSuccess || !build_flood_static(b->scenes[k], b->descs[k]))
+                return set_err(nullptr, SPM_ERR_CUDA, "static flood rebuild failed");
         }
-        if (okc && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
-            b->graph = g;
-        } else {
-            if (g) cudaGraphDestroy(g);
-            b->exec = nullptr;
-            b->capture_failed = true;
-            cudaGetLastError();  // clear a capture error; fall back to direct launches
-        }
-    }
-    if (b->exec) {
-        if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return set_err(nullptr, SPM_ERR_CUDA, "graph launch failed");
+    // the caller's stream may be the legacy default stream, which cannot be
+    // captured: the graph is captured and replayed on the batch's own
+    // stream, after the caller's prior work and before its later work
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    if (cap != cudaStreamCaptureStatusNone) {  // inside the caller's own capture: record the launches there
+        batch_launch(b, st, true);
     } else {
-        batch_launch(b, st);
+        cudaEventRecord(b->fork, st);
+        cudaStreamWaitEvent(b->graph_stream, b->fork, 0);
+        if (!b->exec && !b->capture_failed) {  // capture once into a CUDA graph
+            cudaGraph_t g = nullptr;
+            bool okc = cudaStreamBeginCapture(b->graph_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (okc) {
+                batch_launch(b, b->graph_stream, true);
+                okc = cudaStreamEndCapture(b->graph_stream, &g) == cudaSuccess && g != nullptr;
+            }
+            if (okc && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+                b->graph = g;
+            } else {
+                if (g) cudaGraphDestroy(g);
+                b->exec = nullptr;
+                b->capture_failed = true;
+                cudaGetLastError();  // clear a capture error; fall back to direct launches
+            }
+        }
+        if (b->exec) {
+            if (cudaGraphLaunch(b->exec, b->graph_stream) != cudaSuccess)
+                return set_err(nullptr, SPM_ERR_CUDA, "graph launch failed");
+        } else {
+            batch_launch(b, b->graph_stream, false);
+        }
+        cudaEventRecord(b->join, b->graph_stream);
+        cudaStreamWaitEvent(st, b->join, 0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(nullptr, SPM_ERR_CUDA, cudaGetErrorString(e));
+    b->ev_valid = true;
     for (size_t k = 0; k < b->scenes.size(); ++k) {
         spm_scene *s = b->scenes[k];
         s->last_dist = nullptr;  // queries need a single-scene compute
         s->last_parent = nullptr;
         s->ev_valid = false;
-        s->flood_static_ok = false;  // the batched flood rewrote the scene's lists
+        // the batched flood rewrote the lists of scenes that flood every generator
+        if (!b->descs[k].flood_reuse && b->descs[k].use_flood && b->descs[k].flood_mode != 2)
+            s->flood_static_ok = false;
     }
+    return SPM_OK;
+}
+
+spm_status spm_batch_phase_ms(spm_batch *b, float *vertex_ms, float *pixel_ms) {
+    if (!b || !vertex_ms || !pixel_ms) return set_err(nullptr, SPM_ERR_INVALID_ARG, "null argument");
+    if (!b->ev_valid) return set_err(nullptr, SPM_ERR_INVALID_ARG, "no batch compute recorded");
+    if (cudaEventSynchronize(b->ev[2]) != cudaSuccess || cudaEventElapsedTime(vertex_ms, b->ev[0], b->ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(pixel_ms, b->ev[1], b->ev[2]) != cudaSuccess)
+        return set_err(nullptr, SPM_ERR_CUDA, "event timing failed");
     return SPM_OK;
 }
 

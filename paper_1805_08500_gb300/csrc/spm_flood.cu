@@ -435,17 +435,17 @@ template <bool ANY_MAPS>  // some scene of the batch keeps depth maps
 __global__ void __launch_bounds__(kFloodThreads, ANY_MAPS ? 6 : 8) k_flood_b(const __grid_constant__ BatchDev b) {
     extern __shared__ unsigned fdyn[];
     __shared__ FloodSmem sm;
-    const int total = b.gen_off[b.n];
-    for (int i = blockIdx.x; i < total; i += gridDim.x) {
-        const int sc = scene_of_b(b.gen_off, b.n, i);
+    const int total = b.flood_off[b.n];
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {  // (scene, generator) tasks: sources only when reusing
+        const int sc = scene_of_b(b.flood_off, b.n, i);
         const DevScene &ds = b.scenes[sc];
         if (!ds.use_flood || ds.flood_mode == 2) continue;
         if (flood_declined(ds)) {
             if (threadIdx.x == 0) ds.flood_counts[2] = 1;
             continue;
         }
-        if (ANY_MAPS && ds.use_maps && ds.gen_maps) flood_one<true>(ds, sm, fdyn, i - b.gen_off[sc]);
-        else flood_one<false>(ds, sm, fdyn, i - b.gen_off[sc]);
+        if (ANY_MAPS && ds.use_maps && ds.gen_maps) flood_one<true>(ds, sm, fdyn, i - b.flood_off[sc]);
+        else flood_one<false>(ds, sm, fdyn, i - b.flood_off[sc]);
     }
 }
 
@@ -456,13 +456,15 @@ __global__ void k_flood_reset_b(const __grid_constant__ BatchDev b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total + b.n; i += gridDim.x * blockDim.x) {
         if (i < total) {
             const int oi = scene_of_b(b.tile_off, b.n, i), sc = b.order[oi];
-            b.scenes[sc].tile_count[i - b.tile_off[oi]] = 0;
+            const DevScene &ds = b.scenes[sc];
+            const int t = i - b.tile_off[oi];
+            ds.tile_count[t] = ds.flood_reuse ? ds.static_tile_count[t] : 0;
         } else {
             const DevScene &ds = b.scenes[i - total];
             const bool on = ds.use_flood && ds.flood_mode != 2;
-            ds.flood_counts[0] = 0;
-            ds.flood_counts[1] = 0;
-            ds.flood_counts[2] = on ? 0 : 1;
+            ds.flood_counts[0] = ds.flood_reuse ? ds.static_counts[0] : 0;
+            ds.flood_counts[1] = ds.flood_reuse ? ds.static_counts[1] : 0;
+            ds.flood_counts[2] = ds.flood_reuse ? ds.static_counts[2] : (on ? 0 : 1);
             ds.flood_counts[3] = 0;
         }
     }

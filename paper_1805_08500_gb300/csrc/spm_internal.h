@@ -165,6 +165,7 @@ struct DevScene {
     // compute floods only the sources
     int32_t *static_tile_count;        // ntiles (small-tile sizing)
     int32_t *static_counts;            // 4
+    int32_t flood_reuse;               // in a batch's copy: flood the sources only, over the static part
 };
 
 // A batch of scenes computed together (device-side descriptor).
@@ -176,6 +177,7 @@ struct BatchDev {
     const long long *bits_off;         // words of the visibility bit matrices: n_vert * vis_words
     const int32_t *vert_off;           // obstacle-vertex generators
     const int32_t *gen_off;            // generators
+    const int32_t *flood_off;          // generators the batched flood takes per scene (sources only when reusing)
     // pixel pass: scenes in processing order (most tiles first)
     const int32_t *order;              // n scene indices
     const int32_t *tile_off;           // n + 1 prefix of tiles in that order

@@ -473,6 +473,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                     }
                     const unsigned long long kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)gc;
                     if (kk < key[k]) {
+                        SPM_CNT(14, 1);  // a pixel-candidate pair that needs a visibility decision
                         if (MAPS && gmap) {
                             const int rx = px[k] - gl.x, ry = py - gl.y;
                             if (rx == 0 && ry == 0) {  // the generator's own pixel
@@ -484,8 +485,12 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                             const int b0 = (int)floorf((a - kAngEps) / kAngW), b1 = (int)floorf((a + kAngEps) / kAngW);
                             const float2 m0 = __ldg(gmap + ((b0 + kAngBins) & (kAngBins - 1)));
                             const float2 m1 = __ldg(gmap + (b1 & (kAngBins - 1)));
-                            if (r2 * (1.f - 1e-5f) >= fmaxf(m0.x, m1.x)) continue;  // hidden
-                            if (r2 * (1.f + 1e-5f) < fminf(m0.y, m1.y)) {           // visible
+                            if (r2 * (1.f - 1e-5f) >= fmaxf(m0.x, m1.x)) {  // hidden
+                                SPM_CNT(13, 1);
+                                continue;
+                            }
+                            if (r2 * (1.f + 1e-5f) < fminf(m0.y, m1.y)) {  // visible
+                                SPM_CNT(12, 1);
                                 key[k] = kk;
                                 continue;
                             }
@@ -550,6 +555,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                             {
                                 vis = !poly_blocks(sm.blk_v[b], sm.blk_m[b], px[k], py, gl.x, gl.y, sm.blk_mask[b]);
                                 SPM_CNT(10, 1);
+                                SPM_CNT(11, sm.blk_m[b]);  // orientations of the polygon's edge pass
                             }
                     }
                     if (vis) key[k] = nk[k];
