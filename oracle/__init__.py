@@ -56,7 +56,7 @@ def _load():
         lib.orc_create.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int,
                                    f64p, ctypes.c_int, f64p, ctypes.c_int, ctypes.c_int,
-                                   ctypes.POINTER(ctypes.c_int), ctypes.c_char_p,
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p,
                                    ctypes.c_int]
         lib.orc_free.argtypes = [P]
         lib.orc_info.argtypes = [P, i32p]
@@ -91,13 +91,21 @@ class Oracle:
     ``use_cone=True`` restricts obstacle-vertex generators to their shadow cone
     behind their parent (the labelling the library must reproduce);
     ``use_cone=False`` is the unrestricted textbook minimum (same distances).
+    ``snap="pixel"`` decides a source's visibility at its position rounded to
+    the coarse lattice (scale ``Sp``, at most 15 bits over the scene) that the
+    GPU library uses; ``snap="fine"`` at its position rounded to the oracle's
+    own lattice (scale ``S``, 24 bits), within 1/(2S) of where it is. Lattice
+    coordinates (``lxy``, ``pixel_lattice``, ``points``) are in units of 1/S.
     """
 
-    def __init__(self, scene, nthreads: int | None = None, use_cone: bool = True):
+    def __init__(self, scene, nthreads: int | None = None, use_cone: bool = True, snap: str = "pixel"):
         lib = _load()
         self.scene = scene
         self.nthreads = nthreads or default_threads()
         self.use_cone = bool(use_cone)
+        if snap not in ("pixel", "fine"):
+            raise ValueError("snap is 'pixel' or 'fine'")
+        self.snap = snap
         off, xy = scene.flat()
         pts = np.ascontiguousarray(scene.points, dtype=np.float64).reshape(-1)
         segs = np.ascontiguousarray(scene.segs, dtype=np.float64).reshape(-1)
@@ -112,14 +120,14 @@ class Oracle:
         self._h = lib.orc_create(scene.world[0], scene.world[1], scene.grid[0],
                                  scene.grid[1], len(scene.polys), off, xy,
                                  len(scene.points), pts, len(scene.segs), segs,
-                                 self.nthreads, int(self.use_cone), ctypes.byref(st),
-                                 err, 256)
+                                 self.nthreads, int(self.use_cone), int(snap == "fine"),
+                                 ctypes.byref(st), err, 256)
         if not self._h:
             raise OracleError(f"oracle rejected scene (code {st.value}): "
                               f"{err.value.decode()}")
-        info = np.zeros(5, np.int32)
+        info = np.zeros(6, np.int32)
         lib.orc_info(self._h, info)
-        self.n_gen, self.n_src, self.n_vert, self.S, self.n_poly = (int(v) for v in info)
+        self.n_gen, self.n_src, self.n_vert, self.S, self.n_poly, self.Sp = (int(v) for v in info)
         n = self.n_gen
         self.kind = np.zeros(n, np.int32)
         self.sidx = np.zeros(n, np.int32)
@@ -195,8 +203,9 @@ class Oracle:
         return bool(_lib.orc_visible(self._h, int(a[0]), int(a[1]), int(b[0]), int(b[1])))
 
     def pixel_lattice(self, i, j):
-        Wx, Wy = self.scene.world
-        Nx, Ny = self.scene.grid
+        Wx, Wy = (int(v) for v in self.scene.world)
+        Nx, Ny = (int(v) for v in self.scene.grid)
+        i, j = int(i), int(j)
         return ((2 * i + 1) * self.S * Wx // (2 * Nx), (2 * j + 1) * self.S * Wy // (2 * Ny))
 
     def root_link(self, i, j, first_parent):

@@ -32,9 +32,19 @@
  * cone behind their parent; ties go to the smaller generator id.
  *
  * Coordinates for predicates are snapped to an integer lattice of scale S
- * (S a power of two, all pixel centres on the lattice, lattice span <= 32767),
- * so every orientation determinant is an exact integer. Distances use the
- * true (unsnapped) coordinates in FP64.
+ * (S a power of two, all pixel centres on the lattice, as fine as keeps every
+ * coordinate within 2^24 lattice units), so every orientation determinant is
+ * an exact integer in int64 and every comparison of two rational parameters
+ * exact in __int128. Distances use the true (unsnapped) coordinates in FP64.
+ * Obstacle vertices and pixel centres lie on the lattice exactly. Sources are
+ * rounded to it: by default (snapping "pixel") to the coarser sub-lattice of
+ * scale Sp, the largest power of two with every pixel centre on it and
+ * Sp * span <= 32767 -- the predicate lattice the GPU library uses, whose
+ * reading of a moved source's visibility this reproduces -- or (snapping
+ * "fine") to the full lattice, which puts a source within 1 / (2 S) of where
+ * it is. Exact predicates do not depend on the scale of the lattice, only on
+ * the points, so both give the same result wherever the sources are
+ * lattice points of both.
  */
 #define _GNU_SOURCE
 #include <math.h>
@@ -54,7 +64,9 @@ enum { CONE_NONE = 0, CONE_LEFT = 1, CONE_RIGHT = 2, CONE_EMPTY = 3 };
 typedef struct {
     ll Wx, Wy;
     int Nx, Ny;
-    ll S;
+    ll S;      /* predicate lattice */
+    ll Sp;     /* the coarser lattice "pixel" snapping rounds sources to (0: none, the scene is too wide) */
+    int fine;  /* snap sources to the full lattice */
     /* polygons, lattice coordinates, counter-clockwise */
     int np;
     int *po;
@@ -201,8 +213,12 @@ static int vis_foot(const orc_t *o, int s, ll qx, ll qy, ll side, ll den, int *s
     const ll *L = o->sl + 4 * s;
     ll ux = L[2] - L[0], uy = L[3] - L[1];
     if (side == 0) return 1; /* q on the segment: zero-length leg */
-    ll Dx = side * uy, Dy = -side * ux;
-    frac_t U = {1, den};
+    /* the open segment q -> foot is q + v * D, D = -sgn(side) perp(u), for
+     * v in (0, |side| / den): both bounded by the lattice, so the rational
+     * comparisons stay within __int128 */
+    const ll sg = side > 0 ? 1 : -1;
+    ll Dx = sg * uy, Dy = -sg * ux;
+    frac_t U = {side > 0 ? side : -side, den};
     return !segment_blocked(o, qx, qy, Dx, Dy, U, stamp, tick);
 }
 
@@ -370,6 +386,13 @@ static int cmp_pos(const void *a, const void *b) {
     return x[2] < y[2] ? -1 : (x[2] > y[2]);
 }
 
+/* A source coordinate on the lattice, rounded half to even: to the coarser
+ * "pixel" lattice Sp (then scaled to S), or to S itself when snapping fine. */
+static ll snap_source(const orc_t *o, double x) {
+    if (!o->fine && o->Sp) return (ll)nearbyint(x * (double)o->Sp) * (o->S / o->Sp);
+    return (ll)nearbyint(x * (double)o->S);
+}
+
 /* pixel centre on the lattice: (2i+1) * S * W / (2N) */
 static ll pix_lat(ll S, ll W, int N, int i) { return (2 * (ll)i + 1) * S * W / (2 * (ll)N); }
 
@@ -394,9 +417,13 @@ static int build(orc_t *o, ll Wx, ll Wy, int Nx, int Ny, int np, const int *poff
         if (y > mxy) mxy = y;
     }
     ll span = (mxx - mnx > mxy - mny) ? mxx - mnx : mxy - mny;
-    if (S * span > 32767) return fail(o, O_EGEOM, "scene too large for the exact lattice");
-    while (2 * S * span <= 32767) S *= 2;
+    if (S * span > (1LL << 24)) return fail(o, O_EGEOM, "scene too large for the exact lattice");
+    ll Sp = 0; /* the coarser lattice of "pixel" snapping */
+    if (S * span <= 32767)
+        for (Sp = S; 2 * Sp * span <= 32767;) Sp *= 2;
+    while (2 * S * span <= (1LL << 24)) S *= 2;
     o->S = S;
+    o->Sp = Sp;
     /* polygons */
     o->np = np;
     o->po = malloc(sizeof(int) * (np + 1));
@@ -466,8 +493,8 @@ static int build(orc_t *o, ll Wx, ll Wy, int Nx, int Ny, int np, const int *poff
     for (int i = 0; i < npt; i++) {
         o->kind[g] = K_POINT; o->sidx[g] = i;
         o->tx[g] = pts[2 * i]; o->ty[g] = pts[2 * i + 1];
-        o->lx[g] = (ll)nearbyint(pts[2 * i] * (double)S);
-        o->ly[g] = (ll)nearbyint(pts[2 * i + 1] * (double)S);
+        o->lx[g] = snap_source(o, pts[2 * i]);
+        o->ly[g] = snap_source(o, pts[2 * i + 1]);
         FREE_CHECK(o->lx[g], o->ly[g], "point source");
         g++;
     }
@@ -477,7 +504,7 @@ static int build(orc_t *o, ll Wx, ll Wy, int Nx, int Ny, int np, const int *poff
     for (int s = 0; s < nseg; s++) {
         for (int c = 0; c < 4; c++) {
             o->sf[4 * s + c] = segs[4 * s + c];
-            o->sl[4 * s + c] = (ll)nearbyint(segs[4 * s + c] * (double)S);
+            o->sl[4 * s + c] = snap_source(o, segs[4 * s + c]);
         }
         if (o->sl[4 * s] == o->sl[4 * s + 2] && o->sl[4 * s + 1] == o->sl[4 * s + 3])
             return fail(o, O_EGEOM, "zero-length segment source");
@@ -881,11 +908,13 @@ void orc_free(void *h) {
 }
 
 /* Builds the scene and the vertex costs. use_cone = 0 relaxes every visible
- * edge (textbook Dijkstra), 1 restricts vertex generators to their cones. */
+ * edge (textbook Dijkstra), 1 restricts vertex generators to their cones.
+ * snap_fine = 1 rounds sources to the full lattice, 0 to the coarser one. */
 void *orc_create(long long Wx, long long Wy, int Nx, int Ny, int np, const int *poff,
                  const int *pxy, int npt, const double *pts, int nseg, const double *segs,
-                 int nthreads, int use_cone, int *status, char *errbuf, int errlen) {
+                 int nthreads, int use_cone, int snap_fine, int *status, char *errbuf, int errlen) {
     orc_t *o = calloc(1, sizeof(orc_t));
+    o->fine = snap_fine != 0;
     int st = build(o, Wx, Wy, Nx, Ny, np, poff, pxy, npt, pts, nseg, segs);
     if (st == O_OK) st = vertex_costs(o, nthreads, use_cone);
     if (status) *status = st;
@@ -900,7 +929,7 @@ void *orc_create(long long Wx, long long Wy, int Nx, int Ny, int np, const int *
 void orc_info(void *h, int *out) {
     orc_t *o = h;
     out[0] = o->ng; out[1] = o->nsrc; out[2] = o->nvert; out[3] = (int)o->S;
-    out[4] = o->np;
+    out[4] = o->np; out[5] = (int)o->Sp;
 }
 
 /* generator table: kind, source index (segment / vertex index), lattice xy,

@@ -195,7 +195,8 @@ def test_vertex_costs_bit_exact(spm, oracle_mod):
         kind, lat, cost, par = s.generators()
         o = oracle_mod.Oracle(scene)
         assert np.array_equal(kind, o.kind)
-        assert np.array_equal(lat, o.lxy.astype(np.int32))
+        f = o.S // s.info()["lattice_scale"]  # the oracle's lattice refines the library's
+        assert np.array_equal(lat.astype(np.int64) * f, o.lxy)
         # generators with a usable shadow cone (sources, tangent arrivals)
         # match bit for bit; vertices reached head-on (empty cone, never a
         # parent) only get an upper bound on the GPU (see the vertex phase)
@@ -759,7 +760,7 @@ def test_exact_point_query(spm, oracle_mod, which):
     rng = np.random.default_rng(11)
     W = scene.world[0]
     lxy = rng.integers(1, W * S - 1, (400, 2))
-    od, op = o.points(lxy)
+    od, op = o.points(lxy * (o.S // S))  # the oracle's lattice refines the library's
     agree = 0
     for (lx, ly), d_ref, p_ref in zip(lxy, od, op):
         g, d = s.query_exact(lx / S, ly / S)
@@ -870,3 +871,33 @@ def test_backward_is_the_gradient_of_its_own_forward(spm, oracle_mod):
         assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
         np.testing.assert_allclose(pts.grad.cpu().numpy(), gp_ref, atol=1e-4)
         np.testing.assert_allclose(segs.grad.cpu().numpy(), gs_ref, atol=1e-4)
+
+
+def test_source_snapping_effect_at_config_size(spm, oracle_mod):
+    """The library decides the visibility of a moved FP32 source at its
+    position rounded to its 15-bit predicate lattice (0.5 units on the
+    2048^2 / 8192-unit differentiable workload); distances use the true
+    position. Against the oracle at the source's true position (its own
+    24-bit lattice, 1/2048 units here) over the whole grid: the labels differ
+    only on shadow boundaries, where the source and the obstacle vertex that
+    bounds its shadow are collinear with the pixel to within the rounding, so
+    either is a parent at the same distance. Measured on the CPU between the
+    oracle's two readings: 1085 of 4.1 M free pixels (0.026%) outside the
+    near-tie rule, distances within 5e-4 units (6.6e-5 relative)."""
+    scene = sg.differentiable(0, n_agents=10)
+    _, gd, gp = gpu_field(spm, scene)
+    o = oracle_mod.Oracle(scene, snap="fine")
+    rd, rp, rd2, _ = o.field()
+    fin = np.isfinite(rd)
+    assert np.array_equal(np.isfinite(gd), fin)
+    h = scene.world[0] / scene.grid[0]
+    rel = np.abs(gd[fin].astype(np.float64) - rd[fin]) / np.maximum(rd[fin], h)
+    with np.errstate(invalid="ignore"):
+        tie = np.where(np.isfinite(rd2), rd2 - rd, np.inf) <= TIE_FRAC * math.hypot(*scene.world)
+    hard = fin & (gp != rp) & ~tie
+    print(f"snapping effect: {int(hard.sum())} of {int(fin.sum())} free pixels change label outside near ties; "
+          f"max relative distance difference {rel.max():.3g}; {int((rel > REL_TOL).sum())} pixels above {REL_TOL}")
+    assert hard.sum() <= MAX_TIE_SHARE * fin.sum()
+    assert rel.max() <= 1e-4
+    # where the label differs the distance is the same path length
+    assert np.all(np.abs(gd[hard].astype(np.float64) - rd[hard]) <= 1e-3)

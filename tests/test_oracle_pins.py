@@ -606,3 +606,35 @@ def test_point_queries_off_centre_match_brute_force(oracle_mod, seed, n_segs):
             assert pp == g1, (x, y)
             checked += 1
     assert checked > 200
+
+
+# ---------------------------------------------------------------------------
+# the oracle's own lattice: no 15-bit limit, sources snapped finely on request
+# ---------------------------------------------------------------------------
+
+def test_source_snapping_modes_agree_on_lattice_sources(oracle_mod):
+    """Exact predicates depend on the points, not on the lattice's scale: with
+    integer sources (lattice points of every lattice) the two snapping modes
+    give the same field, labels and runner-ups."""
+    for s in (sg.plain_polys(2, n_polys=60, n_segs=2, N=256), sg.maze(1, cells=6, N=96)):
+        a = oracle_mod.Oracle(s, snap="pixel")
+        b = oracle_mod.Oracle(s, snap="fine")
+        assert b.S == a.S and a.Sp > 0 and a.S % a.Sp == 0 and a.S >= 256 * a.Sp
+        fa, fb = a.field(), b.field()
+        for x, y in zip(fa, fb):
+            assert np.array_equal(x, y)
+
+
+def test_wide_scene_beyond_the_gpu_lattice(oracle_mod):
+    """A world 40000 units wide (beyond the 15-bit lattice of the GPU
+    library) is accepted, and the field of two point sources with no
+    obstacle is the closed-form distance to the nearer one."""
+    s = sg.empty_scene(W=40000, N=50, points=[(1234.5, 30000.25), (35000.75, 8000.5)])
+    o = oracle_mod.Oracle(s)
+    assert o.Sp == 0  # no coarse lattice: sources snap to the fine one
+    d, p, _, _ = o.field()
+    X, Y = centres(s)
+    D = np.stack([np.hypot(X - px, Y - py) for px, py in s.points])
+    np.testing.assert_allclose(d, D.min(0), rtol=1e-15, atol=0)
+    clear = (np.sort(D, 0)[1] - D.min(0)) > 1e-9
+    assert np.array_equal(p[clear], D.argmin(0)[clear])
