@@ -1059,8 +1059,10 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     info[7] = s->ds.tile;
     info[8] = (s->ds.use_flood && fc[2] == 0) ? 1 : 0;
     info[9] = s->ds.flood_mode;
+    const bool floods = s->ds.use_flood && s->ds.flood_mode != 2;
+    const bool reuse = floods && s->ds.flood_mode == 3 && s->ds.static_tile_count;  // restore + sources' flood
     info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.solo_smem > 0 ? 1 : 0) + 2 +  // vertex phase
-               (s->ds.use_flood && s->ds.flood_mode != 2 ? 3 : 0) + 1;          // flood, pixels
+               (floods ? (reuse ? 4 : 3) : 0) + 1;                                // flood, list scan and fill, pixels
     return SPM_OK;
 }
 

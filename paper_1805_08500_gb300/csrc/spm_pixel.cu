@@ -141,9 +141,14 @@ __device__ __forceinline__ float key_dist(unsigned long long k) { return __uint_
 // Lower bound of cost(g) + distance from g to any pixel of the tile, or -1 if
 // g cannot be valid anywhere in the tile.
 __device__ float tile_lower_bound(const DevScene &ds, int g, int4 box, float4 fbox) {
-    const float cf = ds.gen_costf[g];
+    // every field is loaded up front (independent loads, in flight together)
+    const float cf = __ldg(ds.gen_costf + g);
+    const int kind = __ldg(ds.gen_kind + g);
+    const int ctype = __ldg(ds.gen_ctype + g);
+    const int4 cone = __ldg(ds.gen_cone + g);
+    const int2 gv = __ldg(ds.gen_lat + g);
+    const float2 gpos = __ldg(ds.gen_pos + g);
     if (!(cf < INFINITY)) return -1.f;
-    const int kind = ds.gen_kind[g];
     if (kind == kSegI) {
         const int s = ds.gen_aux[g];
         const int4 L = ds.seg_lat[s];
@@ -172,10 +177,10 @@ __device__ float tile_lower_bound(const DevScene &ds, int g, int4 box, float4 fb
         return (pos && neg) ? 0.f : mn * 0.999999f;
     }
     if (kind == kVert) {
-        const int ct = ds.gen_ctype[g];
+        const int ct = ctype;
         if (ct == kConeEmpty) return -1.f;
-        const int4 c = ds.gen_cone[g];
-        const int2 v = ds.gen_lat[g];
+        const int4 c = cone;
+        const int2 v = gv;
         const int cx[4] = {box.x, box.z, box.x, box.z}, cy[4] = {box.y, box.y, box.w, box.w};
         bool out1 = true, out2 = true;
 #pragma unroll
@@ -186,7 +191,7 @@ __device__ float tile_lower_bound(const DevScene &ds, int g, int4 box, float4 fb
         }
         if (out1 || out2) return -1.f;
     }
-    const float2 p = ds.gen_pos[g];
+    const float2 p = gpos;
     const float dx = fmaxf(fmaxf(fbox.x - p.x, p.x - fbox.z), 0.f);
     const float dy = fmaxf(fmaxf(fbox.y - p.y, p.y - fbox.w), 0.f);
     return (cf + sqrtf(dx * dx + dy * dy)) * 0.999999f;
@@ -444,7 +449,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                     const float fux = segf.z - segf.x, fuy = segf.w - segf.y;
                     seg_il = 1.0f / sqrtf(fux * fux + fuy * fuy);
                 }
-                unsigned need = 0;
+                unsigned need = 0, want = 0;
                 unsigned long long nk[PX];
                 long long num[PX];
                 // the flood's depth map of a point generator decides most pixels:
@@ -454,50 +459,68 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                                              (staged ? sm.rec[c].map_ok : ds.gen_map_ok[gc])
                                          ? ds.gen_maps + (size_t)gc * kAngBins
                                          : nullptr;
+                // first pass: each pixel's key and depth-map bins, without
+                // branches around the loads, so that all of the thread's map
+                // loads are in flight together
+                float r2[PX];
+                int bA[PX], bB[PX];
 #pragma unroll
                 for (int k = 0; k < PX; ++k) {
-                    nk[k] = kUnset;
-                    num[k] = 0;
-                    if (!((live >> k) & 1u) || !(key_dist(key[k]) > lb_c)) continue;
+                    bool ok = ((live >> k) & 1u) && key_dist(key[k]) > lb_c;
                     float d;
+                    num[k] = 0;
                     if (kind == kSegI) {
                         const long long nm = (long long)(px[k] - seg.x) * (seg.z - seg.x) +
                                              (long long)(py - seg.y) * (seg.w - seg.y);
-                        if (!(nm > 0 && nm < den)) continue;
+                        ok = ok && nm > 0 && nm < den;
                         num[k] = nm;
                         d = fabsf((segf.z - segf.x) * (fy - segf.y) - (segf.w - segf.y) * (fx[k] - segf.x)) * seg_il;
                     } else {
-                        if (kind == kVert && !in_cone(ct, cone, px[k] - gl.x, py - gl.y)) continue;
+                        ok = ok && (kind != kVert || in_cone(ct, cone, px[k] - gl.x, py - gl.y));
                         const float ddx = fx[k] - gp.x, ddy = fy - gp.y;
                         d = cf + sqrtf(ddx * ddx + ddy * ddy);
                     }
-                    const unsigned long long kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)gc;
-                    if (kk < key[k]) {
-                        SPM_CNT(14, 1);  // a pixel-candidate pair that needs a visibility decision
-                        if (MAPS && gmap) {
-                            const int rx = px[k] - gl.x, ry = py - gl.y;
-                            if (rx == 0 && ry == 0) {  // the generator's own pixel
-                                key[k] = kk;
-                                continue;
-                            }
-                            const float r2 = (float)((long long)rx * rx + (long long)ry * ry);
-                            const float a = pang((float)rx, (float)ry);
-                            const int b0 = (int)floorf((a - kAngEps) / kAngW), b1 = (int)floorf((a + kAngEps) / kAngW);
-                            const float2 m0 = __ldg(gmap + ((b0 + kAngBins) & (kAngBins - 1)));
-                            const float2 m1 = __ldg(gmap + (b1 & (kAngBins - 1)));
-                            if (r2 * (1.f - 1e-5f) >= fmaxf(m0.x, m1.x)) {  // hidden
-                                SPM_CNT(13, 1);
-                                continue;
-                            }
-                            if (r2 * (1.f + 1e-5f) < fminf(m0.y, m1.y)) {  // visible
-                                SPM_CNT(12, 1);
-                                key[k] = kk;
-                                continue;
-                            }
+                    nk[k] = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)gc;
+                    if (ok && nk[k] < key[k]) want |= 1u << k;
+                    const int rx = px[k] - gl.x, ry = py - gl.y;
+                    r2[k] = (float)((long long)rx * rx + (long long)ry * ry);
+                    const float a = (rx | ry) ? pang((float)rx, (float)ry) : 0.f;
+                    bA[k] = ((int)floorf((a - kAngEps) / kAngW) + kAngBins) & (kAngBins - 1);
+                    bB[k] = (int)floorf((a + kAngEps) / kAngW) & (kAngBins - 1);
+                }
+                if (MAPS && gmap) {
+                    float2 m0[PX], m1[PX];
+#pragma unroll
+                    for (int k = 0; k < PX; ++k) {
+                        m0[k] = make_float2(0.f, 0.f);
+                        m1[k] = m0[k];
+                        if ((want >> k) & 1u) {
+                            m0[k] = __ldg(gmap + bA[k]);
+                            m1[k] = __ldg(gmap + bB[k]);
                         }
-                        nk[k] = kk;
+                    }
+#pragma unroll
+                    for (int k = 0; k < PX; ++k) {
+                        if (!((want >> k) & 1u)) continue;
+                        SPM_CNT(14, 1);  // a pixel-candidate pair that needs a visibility decision
+                        if (px[k] == gl.x && py == gl.y) {  // the generator's own pixel
+                            key[k] = nk[k];
+                            continue;
+                        }
+                        if (r2[k] * (1.f - 1e-5f) >= fmaxf(m0[k].x, m1[k].x)) {  // hidden
+                            SPM_CNT(13, 1);
+                            continue;
+                        }
+                        if (r2[k] * (1.f + 1e-5f) < fminf(m0[k].y, m1[k].y)) {  // visible
+                            SPM_CNT(12, 1);
+                            key[k] = nk[k];
+                            continue;
+                        }
                         need |= 1u << k;
                     }
+                } else {
+                    need = want;
+                    SPM_CNT(14, __popc(want));
                 }
                 if (!__syncthreads_or(need != 0)) {
                     SPM_LAP(4);
