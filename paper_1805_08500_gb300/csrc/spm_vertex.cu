@@ -38,7 +38,10 @@ namespace {
 
 constexpr int kVisThreads = 256;
 constexpr int kSsspThreads = 256;
-constexpr int kSoloThreads = 512;
+#ifndef SPM_SOLO_THREADS
+#define SPM_SOLO_THREADS 512
+#endif
+constexpr int kSoloThreads = SPM_SOLO_THREADS;  // threads of the single-CTA fixpoint
 #ifndef SPM_SOLO_GRP
 #define SPM_SOLO_GRP 8
 #endif
@@ -713,7 +716,15 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 cost[v] = __longlong_as_double(best);  // only this group writes v in this round
                 par[v] = (short)bpar;
             }
-            // mark the out-neighbours: one counter atomic per warp and step
+            // mark the out-neighbours (each newly dirty one once in the next list)
+#ifndef SPM_SOLO_MARK_AGG
+            if (changed)
+                for (int e = o0; e < o1; e += kSoloGrp) {
+                    const int w = e == o0 ? o_first : out_dst[e];
+                    const unsigned bit = 1u << (w & 31);
+                    if (!(atomicOr(&dirty[nxt * dw + (w >> 5)], bit) & bit)) dl[nxt * n + atomicAdd(next_cnt, 1)] = (unsigned short)w;
+                }
+#else
             for (int e = o0; __any_sync(kFull, changed && e < o1); e += kSoloGrp) {
                 bool fresh = false;
                 int w = 0;
@@ -728,12 +739,14 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 base = __shfl_sync(kFull, base, 0);
                 if (fresh) dl[nxt * n + base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)w;
             }
+#endif
 #ifdef SPM_COUNT
             lap[3] = clock_after(changed);  // the marks
 #endif
         }
-        // this round's bitmap is free again (marks went to the other one)
-        for (int w = tid; w < dw; w += kSoloThreads) dirty[cur * dw + w] = 0u;
+        // this round's bitmap is free again (marks went to the other one); the
+        // last threads clear it, whose warps rarely hold a dirty vertex
+        for (int w = kSoloThreads - 1 - tid; w < dw; w += kSoloThreads) dirty[cur * dw + w] = 0u;
 #ifdef SPM_COUNT
         if (lane == 0) SPM_CNT_MAX(6, (unsigned long long)(clock64() - t_round));  // slowest warp, any round
         if (tid == 0) {
