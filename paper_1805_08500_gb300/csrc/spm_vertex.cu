@@ -717,29 +717,12 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
                 par[v] = (short)bpar;
             }
             // mark the out-neighbours (each newly dirty one once in the next list)
-#ifndef SPM_SOLO_MARK_AGG
             if (changed)
                 for (int e = o0; e < o1; e += kSoloGrp) {
                     const int w = e == o0 ? o_first : out_dst[e];
                     const unsigned bit = 1u << (w & 31);
                     if (!(atomicOr(&dirty[nxt * dw + (w >> 5)], bit) & bit)) dl[nxt * n + atomicAdd(next_cnt, 1)] = (unsigned short)w;
                 }
-#else
-            for (int e = o0; __any_sync(kFull, changed && e < o1); e += kSoloGrp) {
-                bool fresh = false;
-                int w = 0;
-                if (changed && e < o1) {
-                    w = e == o0 ? o_first : out_dst[e];
-                    const unsigned bit = 1u << (w & 31);
-                    fresh = !(atomicOr(&dirty[nxt * dw + (w >> 5)], bit) & bit);
-                }
-                const unsigned bal = __ballot_sync(kFull, fresh);
-                int base = 0;
-                if (lane == 0 && bal) base = atomicAdd(next_cnt, __popc(bal));
-                base = __shfl_sync(kFull, base, 0);
-                if (fresh) dl[nxt * n + base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)w;
-            }
-#endif
 #ifdef SPM_COUNT
             lap[3] = clock_after(changed);  // the marks
 #endif
