@@ -37,10 +37,14 @@ FALLBACK_HBM_GBS = 6800.0
 # FP32 lanes per SM x SMs x 2 flops per FMA; clock from the measured peaks file
 FP32_LANES, N_SMS = 128, 152
 FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
-# DRAM bytes (read + write) of one k_pixels launch on the 4096^2 maze, from a
-# single-pass ncu capture of dram__bytes_read.sum + dram__bytes_write.sum; valid
-# for that workload and that kernel version only (re-captured after a change).
-KPIXELS_TRAFFIC = {"maze4096": 107_700_480}
+# One k_pixels launch on the 4096^2 maze, from a single-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, smsp__issue_active and the
+# ALU / FMA pipe shares) and from the instrumentation build's work counters
+# (orientation tests and exact polygon tests per pixel); valid for that
+# workload and that kernel version only (re-captured after a change).
+KPIXELS_TRAFFIC = {"maze4096": 102_310_000}
+KPIXELS_UTIL = {"maze4096": {"issue_frac": 0.440, "alu_pipe_frac": 0.304, "fma_pipe_frac": 0.128,
+                             "orient_per_px": 0.254, "exact_tests_per_px": 0.0636}}
 
 
 def workload(name: str):
@@ -945,8 +949,11 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": KPIXELS_TRAFFIC.get(args.workload),
+                     **KPIXELS_UTIL.get(args.workload, {}),
                      "note": f"algorithmic = {FLOPS_PER_PIXEL} FP32 flops/pixel (winning distance); "
-                             f"peak = FP32 lanes x SMs x 2 x max SM clock ({peak_src})"},
+                             f"peak = FP32 lanes x SMs x 2 x max SM clock ({peak_src}); issue_frac and the "
+                             f"pipe shares: ncu on one launch of this kernel; orient_per_px: counted "
+                             f"orientation tests of the exact visibility per pixel"},
         "hbm_write": {"achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
                       "frac": write_gbs / hbm_peak, "bytes_per_pixel": 8,
                       "peak_source": peak_src},
