@@ -291,7 +291,7 @@ spm_status spm_agents_backward(spm_scene *scene, void *stream, const void *tape_
  * scene (call it before the next compute or source move), writing
  * grad_points_dev (2 * n_points floats) and grad_segs_dev (4 * n_segments
  * floats), asynchronously on `stream`. It calls no allocating function: its
- * scratch is one fixed array inside the library (about 3.3 MB, held on every
+ * scratch is one fixed array inside the library (about 3.8 MB, held on every
  * GPU that loads the library until the process exits), sized for at most
  * SPM_NOALLOC_MAX_AGENTS agents and SPM_NOALLOC_MAX_GENERATORS generators;
  * larger inputs return SPM_ERR_CAPACITY. The first call on each device looks
