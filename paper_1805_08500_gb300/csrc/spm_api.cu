@@ -360,8 +360,10 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
             if (ds.gen_map_ok) cudaMemset(ds.gen_map_ok, 0, hs.n_gen);
         }
         ds.flood_counts = dalloc<int32_t>(s, 4);
-        ds.static_tile_count = ds.use_flood ? dalloc<int32_t>(s, ntiles) : nullptr;
+        ds.static_tile_start = ds.use_flood ? dalloc<int32_t>(s, ntiles + 1) : nullptr;
+        ds.static_tile_items = ds.use_flood ? dalloc<int32_t>(s, ds.pair_cap) : nullptr;
         ds.static_counts = ds.use_flood ? dalloc<int32_t>(s, 4) : nullptr;
+        ds.static_lists = 0;
     }
     ds.free_words = (hs.Nx + 31) / 32;
     uint32_t *free_bits = dalloc<uint32_t>(s, (size_t)hs.Ny * ds.free_words);
@@ -468,6 +470,7 @@ static spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t 
     cudaStreamIsCapturing(cs, &cap);
     const bool timed = cap == cudaStreamCaptureStatusNone;
     const bool side = s->ds.use_flood && s->ds.flood_mode == 3;  // geometric flood beside the vertex phase
+    s->ds.static_lists = side && s->ds.static_tile_start ? 1 : 0;  // the pixel pass reads the kept lists too
     NvtxRange range_all("spm_compute");
     if (timed) cudaEventRecord(s->ev[0], cs);
     // the side flood forks once the visibility graph is built and is
@@ -483,14 +486,14 @@ static spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t 
         // once for this tile size and map setting, then only the sources flood
         const bool maps = s->ds.use_maps && s->ds.gen_maps;
         const bool reuse = s->flood_static_ok && s->flood_static_tile == s->ds.tile &&
-                           s->flood_static_maps == (int)maps && s->ds.static_tile_count;
+                           s->flood_static_maps == (int)maps && s->ds.static_tile_start;
         cudaStreamWaitEvent(s->side, s->fork, 0);
         spm::launch_flood(s->ds, s->side,
-                          !s->ds.static_tile_count ? spm::FloodStatic::kNone
+                          !s->ds.static_tile_start ? spm::FloodStatic::kNone
                           : reuse                  ? spm::FloodStatic::kReuse
                                                    : spm::FloodStatic::kBuild);
         cudaEventRecord(s->join, s->side);
-        s->flood_static_ok = s->ds.static_tile_count != nullptr;
+        s->flood_static_ok = s->ds.static_tile_start != nullptr;
         s->flood_static_tile = s->ds.tile;
         s->flood_static_maps = (int)maps;
     }
@@ -772,13 +775,14 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
         // geometric floods reuse the obstacle vertices' static lists: built
         // here if the scene has none for this tile size and map setting
         descs[k].flood_reuse = 0;
-        if (descs[k].use_flood && descs[k].flood_mode == 3 && descs[k].static_tile_count) {
+        if (descs[k].use_flood && descs[k].flood_mode == 3 && descs[k].static_tile_start) {
             if (!flood_static_matches(scenes[k], descs[k]) && !build_flood_static(scenes[k], descs[k])) {
                 delete b;
                 return set_err(nullptr, SPM_ERR_CUDA, "static flood build failed");
             }
             descs[k].flood_reuse = 1;
         }
+        descs[k].static_lists = descs[k].flood_reuse;
         const bool floods = descs[k].use_flood && descs[k].flood_mode != 2;
         flood_off[k + 1] = flood_off[k] + (floods ? (descs[k].flood_reuse ? descs[k].n_src : descs[k].n_gen) : 0);
         pair_off[k + 1] = pair_off[k] + (long long)descs[k].n_vert * descs[k].pair_words;
@@ -1060,9 +1064,13 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     info[8] = (s->ds.use_flood && fc[2] == 0) ? 1 : 0;
     info[9] = s->ds.flood_mode;
     const bool floods = s->ds.use_flood && s->ds.flood_mode != 2;
-    const bool reuse = floods && s->ds.flood_mode == 3 && s->ds.static_tile_count;  // restore + sources' flood
+    // the geometric mode over kept obstacle-vertex lists: the sources' culling
+    // (list reset, then the walk, or maps from every polygon and the tile
+    // tests) and the list scan and fill
+    const bool reuse = floods && s->ds.flood_mode == 3 && s->ds.static_tile_start;
+    const int src_cull = !spm::flood_sources_direct(s->ds) ? 2 : s->ds.n_poly > 0 ? 3 : 2;
     info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.solo_smem > 0 ? 1 : 0) + 2 +  // vertex phase
-               (floods ? (reuse ? 4 : 3) : 0) + 1;                                // flood, list scan and fill, pixels
+               (floods ? (reuse ? src_cull + 2 : 3) : 0) + 1;                    // flood, list scan and fill, pixels
     return SPM_OK;
 }
 

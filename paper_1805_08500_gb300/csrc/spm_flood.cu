@@ -16,6 +16,8 @@
 // sets a flag and the pixel pass falls back to scanning every generator.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "spm_device.cuh"
 #include "spm_internal.h"
 
@@ -103,7 +105,7 @@ struct FloodSmem {
 // Is the closed box hidden from g (lattice point, not inside the box) by the
 // depth map? One warp: the lanes test 32 of the spanned bins at a time (a
 // tile near g spans hundreds of bins).
-__device__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int lane) {
+__device__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int lane, int stride = 1) {
     const long long dx = max(max(box.x - g.x, g.x - box.z), 0), dy = max(max(box.y - g.y, g.y - box.w), 0);
     const float mind2 = (float)(dx * dx + dy * dy) * (1.f - 1e-6f);
     const float c0 = pang(0.5f * (float)(box.x + box.z) - (float)g.x, 0.5f * (float)(box.y + box.w) - (float)g.y);
@@ -118,7 +120,7 @@ __device__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int l
     const int k0 = (int)floorf((c0 + lo - kAngEps) / kAngW), k1 = (int)floorf((c0 + hi + kAngEps) / kAngW);
     for (int k = k0; k <= k1; k += 32) {
         const int kk = k + lane;
-        const bool h = kk > k1 || depth2[(kk + 2 * kAng) & (kAng - 1)] <= mind2;
+        const bool h = kk > k1 || depth2[stride * ((kk + 2 * kAng) & (kAng - 1))] <= mind2;
         if (!__all_sync(0xffffffffu, h)) return false;
     }
     return true;
@@ -128,7 +130,7 @@ __device__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int l
 // lanes spread over each edge's bins.
 template <bool MAPS>
 __device__ void insert_polygon_warp(const DevScene &ds, float *depth2, float *lo2, int2 g, int q, int lane,
-                                    float plen) {
+                                    float plen, int stride = 1) {
     const int b = ds.poly_off[q], m = ds.poly_off[q + 1] - b;
     const int2 mine = lane < m ? ds.poly_v[b + lane] : make_int2(0, 0);  // vertex `lane`, one load per lane
     for (int i = 0; i < m; ++i) {
@@ -154,7 +156,7 @@ __device__ void insert_polygon_warp(const DevScene &ds, float *depth2, float *lo
             return __fdividef(fN2 * (float)(u.x * u.x + u.y * u.y), fD * fD) * (1.f + 1e-5f);
         };
         for (int k = k0 + lane; k <= k1; k += 32) {
-            int *slot = (int *)&depth2[k & (kAng - 1)];
+            int *slot = (int *)&depth2[stride * (k & (kAng - 1))];
             if (__int_as_float(*slot) <= h2) continue;  // this edge cannot lower the bin
             atomicMin(slot, __float_as_int(fmaxf(bdist2(k), bdist2(k + 1))));  // non-negative floats order as ints
         }
@@ -175,7 +177,8 @@ __device__ void insert_polygon_warp(const DevScene &ds, float *depth2, float *lo
             const float d2 = fmaxf((cx * cx + cy * cy) * (1.f - 2e-5f) - 0.05f, 0.f);
             const float plo = pang(px1, py1), phi = plo + fmodf(pang(px0, py0) - plo + 4.f, 4.f);
             const int b0 = (int)floorf((plo - kAngEps) / kAngW), b1 = (int)floorf((phi + kAngEps) / kAngW);
-            for (int k = b0; k <= b1; ++k) atomicMin((int *)&lo2[(k + 2 * kAng) & (kAng - 1)], __float_as_int(d2));
+            for (int k = b0; k <= b1; ++k)
+                atomicMin((int *)&lo2[stride * ((k + 2 * kAng) & (kAng - 1))], __float_as_int(d2));
         }
     }
 }
@@ -365,6 +368,89 @@ __device__ void flood_one(const DevScene &ds, FloodSmem &sm, unsigned *fdyn, int
     SPM_TFLUSH();
 }
 
+// Direct culling of the sources (generators [0, n_src)) in the geometric
+// mode: few generators, each reaching much of the grid, which one CTA per
+// generator would walk a breadth-first level at a time. Instead every
+// polygon enters each source's depth map at once (a warp per (source,
+// polygon), atomics into the source's map in global memory), and then every
+// tile is tested against the complete map at once (a warp per (source,
+// tile)). A tile that the map does not hide gets the source in its list.
+// That is a superset of what the walk reaches -- the walk also stops at
+// tiles cut off by hidden ones -- and every tile where the source can win is
+// still in it: the map only hides points that lie beyond an obstacle
+// interior on their ray. With every polygon in it the map is complete, and
+// the pixel pass may use it.
+__device__ __forceinline__ bool src_on_grid(const DevScene &ds, int g) {
+    const int2 gl = ds.gen_lat[g];
+    const int px = ds.S * ds.Wx / ds.Nx, py = ds.S * ds.Wy / ds.Ny;
+    return ds.gen_kind[g] != kSegI && gl.x >= 0 && gl.y >= 0 && gl.x <= ds.Nx * px && gl.y <= ds.Ny * py;
+}
+
+// Before the sources' culling: empty maps and lists, the global list after
+// the obstacle vertices' entries, the overflow flag as their flood left it.
+__device__ __forceinline__ void src_prep(const DevScene &ds, int i0, int stride, bool counts) {
+    const int nmap = ds.n_src * kAng, ntiles = ds.tiles_x * ds.tiles_y;
+    for (int i = i0; i < max(nmap, ntiles); i += stride) {
+        if (i < nmap) ds.gen_maps[i] = make_float2(INFINITY, INFINITY);
+        if (i < ntiles) ds.tile_count[i] = 0;
+        if (i < ds.n_src) ds.gen_map_ok[i] = 0;
+    }
+    if (counts && i0 < 4) ds.flood_counts[i0] = i0 == 1 || i0 == 2 ? ds.static_counts[i0] : 0;
+}
+
+template <bool MAPS>
+__device__ __forceinline__ void src_insert(const DevScene &ds, int g, int q, int lane) {
+    if (!src_on_grid(ds, g)) return;
+    const int tpx = ds.tile * (ds.S * ds.Wx / ds.Nx), tpy = ds.tile * (ds.S * ds.Wy / ds.Ny);
+    const float plen = fmaxf(1.f, 0.125f * (float)min(tpx, tpy));  // as in the flood
+    float *mp = reinterpret_cast<float *>(ds.gen_maps + (size_t)g * kAng);
+    insert_polygon_warp<MAPS>(ds, mp, mp + 1, ds.gen_lat[g], q, lane, plen, 2);
+}
+
+template <bool MAPS>
+__device__ __forceinline__ void src_tile(const DevScene &ds, int g, int t, int lane) {
+    if (!src_on_grid(ds, g)) {  // segment interiors and sources off the grid: every tile scans them
+        if (t == 0 && lane == 0) push_global(ds, g);
+        return;
+    }
+    const int2 gl = ds.gen_lat[g];
+    const int4 area = tile_area(ds, t % ds.tiles_x, t / ds.tiles_x);
+    const bool inside = gl.x >= area.x && gl.x <= area.z && gl.y >= area.y && gl.y <= area.w;
+    const float *mp = reinterpret_cast<const float *>(ds.gen_maps + (size_t)g * kAng);
+    if (MAPS && t == 0 && lane == 0) ds.gen_map_ok[g] = 1;  // complete: the pixel pass may read it
+    if (!inside && box_hidden_ang_warp(mp, gl, area, lane, 2)) return;
+    if (lane == 0) {
+        const int slot = atomicAdd(&ds.flood_counts[0], 1);
+        if (slot < ds.pair_cap) {
+            ds.pairs[slot] = make_int2(t, g);
+            atomicAdd(&ds.tile_count[t], 1);
+        } else {
+            atomicOr(&ds.flood_counts[2], 1);
+        }
+    }
+}
+
+__global__ void k_src_prep(DevScene ds) {
+    src_prep(ds, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, true);
+}
+
+template <bool MAPS>
+__global__ void k_src_insert(DevScene ds) {
+    const long long n = (long long)ds.n_src * ds.n_poly;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < n;
+         w += (gridDim.x * (long long)blockDim.x) >> 5)
+        src_insert<MAPS>(ds, (int)(w / ds.n_poly), (int)(w % ds.n_poly), threadIdx.x & 31);
+}
+
+template <bool MAPS>
+__global__ void k_src_tiles(DevScene ds) {
+    const int ntiles = ds.tiles_x * ds.tiles_y;
+    const long long n = (long long)ds.n_src * ntiles;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < n;
+         w += (gridDim.x * (long long)blockDim.x) >> 5)
+        src_tile<MAPS>(ds, (int)(w / ntiles), (int)(w % ntiles), threadIdx.x & 31);
+}
+
 // Automatic mode: flood only sparse visibility graphs (mazes); a dense one
 // marks the lists unavailable and every tile scans every generator.
 __device__ __forceinline__ bool flood_declined(const DevScene &ds) {
@@ -396,28 +482,25 @@ __global__ void __launch_bounds__(kFloodThreads, MAPS ? 6 : 8) k_flood(DevScene 
     }
 }
 
-// The static part of the lists (the obstacle vertices' flood) is kept after
-// that flood, or restored before the sources' flood; either way the work
-// counter starts again from zero.
+// After the obstacle vertices' flood (keep = 1) its counts are saved; before
+// the sources' flood (keep = 0) the lists start empty, the global list after
+// the vertices' entries, the overflow flag as the vertices' flood left it,
+// and the work counter from zero.
 __global__ void k_flood_static(DevScene ds, int keep) {
     const int ntiles = ds.tiles_x * ds.tiles_y;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
-        if (keep) ds.static_tile_count[t] = ds.tile_count[t];
-        else ds.tile_count[t] = ds.static_tile_count[t];
-    }
+    if (!keep)
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) ds.tile_count[t] = 0;
     if (blockIdx.x == 0 && threadIdx.x < 4) {
         const int k = threadIdx.x;
         if (keep) {
             if (k < 3) ds.static_counts[k] = ds.flood_counts[k];
         } else {
-            ds.flood_counts[k] = k < 3 ? ds.static_counts[k] : 0;
+            ds.flood_counts[k] = k == 1 || k == 2 ? ds.static_counts[k] : 0;
         }
     }
 }
 
-__global__ void k_flood_counter_reset(DevScene ds) {
-    if (threadIdx.x == 0) ds.flood_counts[3] = 0;
-}
+
 
 // Batched form: every (scene, generator) of the batch, one CTA each.
 template <class T>
@@ -456,13 +539,11 @@ __global__ void k_flood_reset_b(const __grid_constant__ BatchDev b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total + b.n; i += gridDim.x * blockDim.x) {
         if (i < total) {
             const int oi = scene_of_b(b.tile_off, b.n, i), sc = b.order[oi];
-            const DevScene &ds = b.scenes[sc];
-            const int t = i - b.tile_off[oi];
-            ds.tile_count[t] = ds.flood_reuse ? ds.static_tile_count[t] : 0;
-        } else {
+            b.scenes[sc].tile_count[i - b.tile_off[oi]] = 0;
+        } else {  // reusing scenes: the global list after the vertices' entries
             const DevScene &ds = b.scenes[i - total];
             const bool on = ds.use_flood && ds.flood_mode != 2;
-            ds.flood_counts[0] = ds.flood_reuse ? ds.static_counts[0] : 0;
+            ds.flood_counts[0] = 0;
             ds.flood_counts[1] = ds.flood_reuse ? ds.static_counts[1] : 0;
             ds.flood_counts[2] = ds.flood_reuse ? ds.static_counts[2] : (on ? 0 : 1);
             ds.flood_counts[3] = 0;
@@ -471,8 +552,11 @@ __global__ void k_flood_reset_b(const __grid_constant__ BatchDev b) {
 }
 
 // Exclusive scan of tile_count into tile_start (one CTA), then fill.
-__device__ void tiles_scan_block(const DevScene &ds) {
+// The per-tile CSR of the pairs: the scene's lists, or (to_static) the kept
+// lists of the obstacle vertices' flood.
+__device__ void tiles_scan_block(const DevScene &ds, bool to_static = false) {
     __shared__ long long wsum[32];
+    int32_t *start = to_static ? ds.static_tile_start : ds.tile_start;
     const int n = ds.tiles_x * ds.tiles_y;
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int lo = threadIdx.x * per, hi = min(n, lo + per);
@@ -480,27 +564,29 @@ __device__ void tiles_scan_block(const DevScene &ds) {
     for (int i = lo; i < hi; ++i) s += ds.tile_count[i];
     long long run = cta_exclusive_scan(s, wsum);
     for (int i = lo; i < hi; ++i) {
-        ds.tile_start[i] = (int32_t)run;
+        start[i] = (int32_t)run;
         run += ds.tile_count[i];
         ds.tile_count[i] = 0;  // reused as fill cursor
     }
-    if (hi == n && lo < hi) ds.tile_start[n] = (int32_t)run;
-    if (threadIdx.x == 0 && n == 0) ds.tile_start[0] = 0;
+    if (hi == n && lo < hi) start[n] = (int32_t)run;
+    if (threadIdx.x == 0 && n == 0) start[0] = 0;
 }
 
-__device__ __forceinline__ void tiles_fill(const DevScene &ds, int i0, int stride) {
+__device__ __forceinline__ void tiles_fill(const DevScene &ds, int i0, int stride, bool to_static = false) {
+    const int32_t *start = to_static ? ds.static_tile_start : ds.tile_start;
+    int32_t *items = to_static ? ds.static_tile_items : ds.tile_items;
     const int np = min(ds.flood_counts[0], ds.pair_cap);
     for (int i = i0; i < np; i += stride) {
         const int2 pr = ds.pairs[i];
         const int slot = atomicAdd(&ds.tile_count[pr.x], 1);
-        ds.tile_items[ds.tile_start[pr.x] + slot] = pr.y;
+        items[start[pr.x] + slot] = pr.y;
     }
 }
 
-__global__ void __launch_bounds__(1024) k_tiles_scan(DevScene ds) { tiles_scan_block(ds); }
+__global__ void __launch_bounds__(1024) k_tiles_scan(DevScene ds, int to_static) { tiles_scan_block(ds, to_static); }
 
-__global__ void k_tiles_fill(DevScene ds) {
-    tiles_fill(ds, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+__global__ void k_tiles_fill(DevScene ds, int to_static) {
+    tiles_fill(ds, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, to_static);
 }
 
 // batched: one CTA per scene for the scan, a row of CTAs per scene for the fill
@@ -546,23 +632,41 @@ void launch_flood(const DevScene &ds, cudaStream_t st, FloodStatic how) {
         else k_flood<false><<<blocks, kFloodThreads, smem, st>>>(ds, g0, g1);
     };
     const int sblocks = max(1, min((ntiles + 255) / 256, 152));
-    if (how == FloodStatic::kReuse) {
-        k_flood_static<<<sblocks, 256, 0, st>>>(ds, 0);
-        flood(0, ds.n_src);
-    } else {
+    if (how == FloodStatic::kNone) {
         cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
         cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
-        if (how == FloodStatic::kBuild) {
-            flood(ds.n_src, ds.n_gen);  // the obstacle vertices first: their pairs lead the buffer
+        flood(0, ds.n_gen);
+    } else {
+        if (how == FloodStatic::kBuild) {  // the obstacle vertices' lists, kept for every later compute
+            cudaMemsetAsync(ds.tile_count, 0, sizeof(int32_t) * ntiles, st);
+            cudaMemsetAsync(ds.flood_counts, 0, sizeof(int32_t) * 4, st);
+            flood(ds.n_src, ds.n_gen);
+            k_tiles_scan<<<1, 1024, 0, st>>>(ds, 1);
+            k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds, 1);
             k_flood_static<<<sblocks, 256, 0, st>>>(ds, 1);
-            k_flood_counter_reset<<<1, 32, 0, st>>>(ds);
-            flood(0, ds.n_src);
+        }
+        if (flood_sources_direct(ds)) {  // the sources: the only lists a compute sorts
+            const int nmap = ds.n_src * kAng;
+            k_src_prep<<<max(1, min((max(nmap, ntiles) + 255) / 256, 152 * 4)), 256, 0, st>>>(ds);
+            auto wblocks = [](long long warps) { return (int)std::max(1LL, std::min((warps + 7) / 8, 152LL * 16)); };
+            if (ds.n_poly > 0) {
+                if (maps) k_src_insert<true><<<wblocks((long long)ds.n_src * ds.n_poly), 256, 0, st>>>(ds);
+                else k_src_insert<false><<<wblocks((long long)ds.n_src * ds.n_poly), 256, 0, st>>>(ds);
+            }
+            if (maps) k_src_tiles<true><<<wblocks((long long)ds.n_src * ntiles), 256, 0, st>>>(ds);
+            else k_src_tiles<false><<<wblocks((long long)ds.n_src * ntiles), 256, 0, st>>>(ds);
         } else {
-            flood(0, ds.n_gen);
+            k_flood_static<<<sblocks, 256, 0, st>>>(ds, 0);
+            flood(0, ds.n_src);
         }
     }
-    k_tiles_scan<<<1, 1024, 0, st>>>(ds);
-    k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds);
+    k_tiles_scan<<<1, 1024, 0, st>>>(ds, 0);
+    k_tiles_fill<<<152 * 4, 256, 0, st>>>(ds, 0);
+}
+
+bool flood_sources_direct(const DevScene &ds) {
+    const long long ntiles = (long long)ds.tiles_x * ds.tiles_y;
+    return ds.gen_maps && ds.n_src > 0 && (long long)ds.n_src * (ds.n_poly + ntiles) <= (1LL << 24);
 }
 
 int flood_smem_attr() {

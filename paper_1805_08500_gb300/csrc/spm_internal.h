@@ -159,12 +159,15 @@ struct DevScene {
     int32_t *glob_list;                // generators every tile scans
     int32_t *flood_counts;             // [0] pairs, [1] global list size, [2] overflow, [3] work counter
     // the geometric flood (mode 3) of the obstacle-vertex generators depends
-    // on the obstacles alone: its per-tile counts and flood_counts[0..2] are
-    // kept here, with its pairs at the front of `pairs`, its global entries
-    // at the front of `glob_list` and its depth maps in gen_maps, so that a
-    // compute floods only the sources
-    int32_t *static_tile_count;        // ntiles (small-tile sizing)
+    // on the obstacles alone: its per-tile lists are kept here (CSR), with
+    // its global entries at the front of `glob_list`, its depth maps in
+    // gen_maps and its flood_counts[0..2] in static_counts, so that a compute
+    // floods and sorts only the sources; a tile's candidates are then its
+    // static list, its list of source entries and the global list
+    int32_t *static_tile_start;        // ntiles + 1 (small-tile sizing)
+    int32_t *static_tile_items;        // pair_cap
     int32_t *static_counts;            // 4
+    int32_t static_lists;              // the pixel pass reads the static lists as well (this compute)
     int32_t flood_reuse;               // in a batch's copy: flood the sources only, over the static part
 };
 
@@ -229,6 +232,9 @@ int fixpoint_round_cap(int n_gen);  // rounds the vertex fixpoint may take (test
 bool flood_possible(int tiles, int polys);
 size_t flood_smem_bytes(int tiles, int polys, bool maps);  // dynamic shared memory of one flood CTA
 int flood_smem_attr();
+// the geometric mode culls the sources directly (complete depth maps, every
+// tile tested at once) rather than by the per-generator walk
+bool flood_sources_direct(const DevScene &ds);
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)
 int count_kernel_launches_vertex();

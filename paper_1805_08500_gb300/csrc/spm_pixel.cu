@@ -351,17 +351,22 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
     }
     __syncthreads();
     SPM_LAP(0);
-    // candidate source: the tile's flooded list plus the global list, or every
-    // generator when the lists are unavailable
+    // candidate source: the tile's flooded lists (the obstacle vertices' kept
+    // list, when this compute reuses it, then this flood's list) plus the
+    // global list, or every generator when the lists are unavailable
     const bool lists = allow_lists && ds.use_flood && ds.flood_counts[2] == 0;
+    const bool stat = lists && ds.static_lists;
     const int tix = tile;
+    const int s0 = stat ? ds.static_tile_start[tix] : 0;
+    const int ns = stat ? ds.static_tile_start[tix + 1] - s0 : 0;
     const int l0 = lists ? ds.tile_start[tix] : 0;
-    const int nlist = lists ? ds.tile_start[tix + 1] - l0 : 0;
-    const int ntotal = lists ? nlist + ds.flood_counts[1] : ds.n_gen;
+    const int nl = ns + (lists ? ds.tile_start[tix + 1] - l0 : 0);
+    const int ntotal = lists ? nl + ds.flood_counts[1] : ds.n_gen;
     for (int g0 = 0; any_live && g0 < ntotal; g0 += NT) {
         const int i = g0 + threadIdx.x;
         int g = i;
-        if (lists && i < ntotal) g = i < nlist ? ds.tile_items[l0 + i] : ds.glob_list[i - nlist];
+        if (lists && i < ntotal)
+            g = i < ns ? ds.static_tile_items[s0 + i] : i < nl ? ds.tile_items[l0 + i - ns] : ds.glob_list[i - nl];
         float lb = -1.f;
         if (i < ntotal) lb = tile_lower_bound(ds, g, box, fbox);
         const bool keep = lb >= 0.f && lb <= sm.tile_ub;
