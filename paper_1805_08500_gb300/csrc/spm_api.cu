@@ -364,6 +364,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         ds.static_tile_items = ds.use_flood ? dalloc<int32_t>(s, ds.pair_cap) : nullptr;
         ds.static_counts = ds.use_flood ? dalloc<int32_t>(s, 4) : nullptr;
         ds.static_lists = 0;
+        ds.src_direct = 0;
     }
     ds.free_words = (hs.Nx + 31) / 32;
     uint32_t *free_bits = dalloc<uint32_t>(s, (size_t)hs.Ny * ds.free_words);
@@ -683,6 +684,7 @@ struct spm_batch {
     // event nodes of the batch's graph
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     bool ev_valid = false;
+    long long src_ins = 0, src_tiles = 0;  // warp tasks of the sources' direct culling
 };
 
 namespace {
@@ -742,7 +744,7 @@ void batch_launch(spm_batch *b, cudaStream_t st, bool capturing) {
     };
     rec(b->ev[0]);
     spm::launch_vertex_phase_batched(b->dev, st);
-    spm::launch_flood_batched(b->dev, st);
+    spm::launch_flood_batched(b->dev, st, b->src_ins, b->src_tiles);
     rec(b->ev[1]);
     spm::launch_pixel_phase_batched(b->dev, st);
     rec(b->ev[2]);
@@ -765,7 +767,8 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     b->scenes.assign(scenes, scenes + n);
     b->device = dev;
     std::vector<spm::DevScene> descs(n);
-    std::vector<long long> pair_off(n + 1, 0), bits_off(n + 1, 0);
+    std::vector<long long> pair_off(n + 1, 0), bits_off(n + 1, 0), src_map_off(n + 1, 0), src_ins_off(n + 1, 0),
+        src_tile_off(n + 1, 0);
     std::vector<int32_t> vert_off(n + 1, 0), gen_off(n + 1, 0), order(n), tile_off(n + 1, 0), flood_off(n + 1, 0);
     std::vector<float *> dv(dist, dist + n);
     std::vector<int32_t *> pv(parent, parent + n);
@@ -783,8 +786,16 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
             descs[k].flood_reuse = 1;
         }
         descs[k].static_lists = descs[k].flood_reuse;
-        const bool floods = descs[k].use_flood && descs[k].flood_mode != 2;
-        flood_off[k + 1] = flood_off[k] + (floods ? (descs[k].flood_reuse ? descs[k].n_src : descs[k].n_gen) : 0);
+        // reusing scenes cull their sources directly where the maps allow it
+        const spm::DevScene &d = descs[k];
+        descs[k].src_direct = d.flood_reuse && spm::flood_sources_direct(d) ? 1 : 0;
+        const long long direct = descs[k].src_direct, ntl = (long long)d.tiles_x * d.tiles_y;
+        src_map_off[k + 1] = src_map_off[k] + direct * d.n_src * spm::kAngBins;
+        src_ins_off[k + 1] = src_ins_off[k] + direct * d.n_src * d.n_poly;
+        src_tile_off[k + 1] = src_tile_off[k] + direct * d.n_src * ntl;
+        const bool floods = d.use_flood && d.flood_mode != 2;
+        flood_off[k + 1] =
+            flood_off[k] + (floods && !direct ? (d.flood_reuse ? d.n_src : d.n_gen) : 0);
         pair_off[k + 1] = pair_off[k] + (long long)descs[k].n_vert * descs[k].pair_words;
         bits_off[k + 1] = bits_off[k] + (long long)descs[k].n_vert * descs[k].vis_words;
         vert_off[k + 1] = vert_off[k] + descs[k].n_vert;
@@ -806,6 +817,12 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     bd.vert_off = bupload(b, vert_off, ok);
     bd.gen_off = bupload(b, gen_off, ok);
     bd.flood_off = bupload(b, flood_off, ok);
+    bd.walk_tasks = flood_off[n];
+    bd.src_map_off = bupload(b, src_map_off, ok);
+    bd.src_ins_off = bupload(b, src_ins_off, ok);
+    bd.src_tile_off = bupload(b, src_tile_off, ok);
+    b->src_ins = src_ins_off[n];
+    b->src_tiles = src_tile_off[n];
     bd.order = bupload(b, order, ok);
     bd.tile_off = bupload(b, tile_off, ok);
     bd.total_tiles = tile_off[n];

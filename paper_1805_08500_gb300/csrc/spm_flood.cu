@@ -533,21 +533,62 @@ __global__ void __launch_bounds__(kFloodThreads, ANY_MAPS ? 6 : 8) k_flood_b(con
 }
 
 // Per-scene list state before a batched flood: counts zeroed, or the lists
-// marked unavailable for scenes that scan.
+// marked unavailable for scenes that scan; the depth maps of directly culled
+// sources emptied.
 __global__ void k_flood_reset_b(const __grid_constant__ BatchDev b) {
     const int total = b.tile_off[b.n];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total + b.n; i += gridDim.x * blockDim.x) {
-        if (i < total) {
-            const int oi = scene_of_b(b.tile_off, b.n, i), sc = b.order[oi];
+    const long long nmap = b.src_map_off[b.n];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total + b.n + nmap;
+         i += gridDim.x * (long long)blockDim.x) {
+        if (i >= total + b.n) {
+            const long long m = i - total - b.n;
+            const int sc = scene_of_b(b.src_map_off, b.n, m);
+            const DevScene &ds = b.scenes[sc];
+            const long long e = m - b.src_map_off[sc];
+            ds.gen_maps[e] = make_float2(INFINITY, INFINITY);
+            if (e % kAng == 0) ds.gen_map_ok[e / kAng] = 0;
+        } else if (i < total) {
+            const int oi = scene_of_b(b.tile_off, b.n, (int32_t)i), sc = b.order[oi];
             b.scenes[sc].tile_count[i - b.tile_off[oi]] = 0;
         } else {  // reusing scenes: the global list after the vertices' entries
-            const DevScene &ds = b.scenes[i - total];
+            const DevScene &ds = b.scenes[(int)(i - total)];
             const bool on = ds.use_flood && ds.flood_mode != 2;
             ds.flood_counts[0] = 0;
             ds.flood_counts[1] = ds.flood_reuse ? ds.static_counts[1] : 0;
             ds.flood_counts[2] = ds.flood_reuse ? ds.static_counts[2] : (on ? 0 : 1);
             ds.flood_counts[3] = 0;
         }
+    }
+}
+
+// Batched direct culling of sources: (scene, source, polygon) and then
+// (scene, source, tile) warp tasks over the scenes with src_direct.
+template <bool ANY_MAPS>
+__global__ void k_src_insert_b(const __grid_constant__ BatchDev b) {
+    const long long n = b.src_ins_off[b.n];
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < n;
+         w += (gridDim.x * (long long)blockDim.x) >> 5) {
+        const int sc = scene_of_b(b.src_ins_off, b.n, w);
+        const DevScene &ds = b.scenes[sc];
+        const long long e = w - b.src_ins_off[sc];
+        const int g = (int)(e / ds.n_poly), q = (int)(e % ds.n_poly);
+        if (ANY_MAPS && ds.use_maps) src_insert<true>(ds, g, q, threadIdx.x & 31);
+        else src_insert<false>(ds, g, q, threadIdx.x & 31);
+    }
+}
+
+template <bool ANY_MAPS>
+__global__ void k_src_tiles_b(const __grid_constant__ BatchDev b) {
+    const long long n = b.src_tile_off[b.n];
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < n;
+         w += (gridDim.x * (long long)blockDim.x) >> 5) {
+        const int sc = scene_of_b(b.src_tile_off, b.n, w);
+        const DevScene &ds = b.scenes[sc];
+        const int ntiles = ds.tiles_x * ds.tiles_y;
+        const long long e = w - b.src_tile_off[sc];
+        const int g = (int)(e / ntiles), t = (int)(e % ntiles);
+        if (ANY_MAPS && ds.use_maps) src_tile<true>(ds, g, t, threadIdx.x & 31);
+        else src_tile<false>(ds, g, t, threadIdx.x & 31);
     }
 }
 
@@ -677,11 +718,22 @@ int flood_smem_attr() {
            cudaFuncSetAttribute(k_flood_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
 }
 
-void launch_flood_batched(const BatchDev &b, cudaStream_t st) {
+void launch_flood_batched(const BatchDev &b, cudaStream_t st, long long src_ins, long long src_tiles) {
     k_flood_reset_b<<<152 * 4, 256, 0, st>>>(b);
     if (b.flood_smem <= 0) return;  // every scene scans
-    if (b.any_maps) k_flood_b<true><<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
-    else k_flood_b<false><<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
+    if (b.walk_tasks > 0) {
+        if (b.any_maps) k_flood_b<true><<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
+        else k_flood_b<false><<<152 * 8, kFloodThreads, b.flood_smem, st>>>(b);
+    }
+    auto wblocks = [](long long warps) { return (int)std::max(1LL, std::min((warps + 7) / 8, 152LL * 16)); };
+    if (src_ins > 0) {
+        if (b.any_maps) k_src_insert_b<true><<<wblocks(src_ins), 256, 0, st>>>(b);
+        else k_src_insert_b<false><<<wblocks(src_ins), 256, 0, st>>>(b);
+    }
+    if (src_tiles > 0) {
+        if (b.any_maps) k_src_tiles_b<true><<<wblocks(src_tiles), 256, 0, st>>>(b);
+        else k_src_tiles_b<false><<<wblocks(src_tiles), 256, 0, st>>>(b);
+    }
     k_tiles_scan_b<<<b.n, 1024, 0, st>>>(b);
     k_tiles_fill_b<<<dim3(16, b.n), 256, 0, st>>>(b);
 }

@@ -169,6 +169,7 @@ struct DevScene {
     int32_t *static_counts;            // 4
     int32_t static_lists;              // the pixel pass reads the static lists as well (this compute)
     int32_t flood_reuse;               // in a batch's copy: flood the sources only, over the static part
+    int32_t src_direct;                // in a batch's copy: those sources culled directly (complete maps)
 };
 
 // A batch of scenes computed together (device-side descriptor).
@@ -196,6 +197,11 @@ struct BatchDev {
     int32_t sssp_blocks;
     int32_t flood_smem;                // dynamic shared memory of the batched flood (0: no scene floods)
     int32_t any_maps;                  // some scene keeps depth maps
+    // direct culling of the sources of scenes with src_direct (n + 1 prefixes):
+    const long long *src_map_off;      // map entries: n_src * kAngBins
+    const long long *src_ins_off;      // warp tasks of the map building: n_src * n_poly
+    const long long *src_tile_off;     // warp tasks of the tile tests: n_src * tiles
+    int32_t walk_tasks;                // (scene, generator) walks of the batched flood
 };
 
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
@@ -223,7 +229,8 @@ int sequential_grid_blocks();
 void launch_update_sources(const DevScene &ds, cudaStream_t st, const float *pts, const float *segs);
 void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st);
 void launch_pixel_phase_batched(const BatchDev &b, cudaStream_t st);
-void launch_flood_batched(const BatchDev &b, cudaStream_t st);
+// src_ins / src_tiles: the totals of b.src_ins_off / b.src_tile_off (host copies)
+void launch_flood_batched(const BatchDev &b, cudaStream_t st, long long src_ins, long long src_tiles);
 // exact query at lattice point (qx, qy), world (fx, fy), pixel (i, j) of the last field
 void launch_query_exact(const DevScene &ds, cudaStream_t st, const int32_t *field_parent, int i, int j, int qx,
                         int qy, double fx, double fy, int32_t *out_par, double *out_dist);
