@@ -41,6 +41,12 @@ constexpr int NT = kPixelThreads;
 #ifndef SPM_PIX16_MINB
 #define SPM_PIX16_MINB 4  // resident CTAs per SM the 16 x 16 kernel is compiled for
 #endif
+#ifndef SPM_PIX32_MINB
+#define SPM_PIX32_MINB 4  // the same for the 32 x 32 kernel
+#endif
+#ifndef SPM_PIXB_MINB
+#define SPM_PIXB_MINB 3   // the same for the batched kernel (both tile sizes inlined)
+#endif
 constexpr unsigned long long kUnset = 0x7F800000FFFFFFFFull;  // (+inf, id max)
 
 // Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
@@ -488,7 +494,9 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                     nk[k] = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)gc;
                     if (ok && nk[k] < key[k]) want |= 1u << k;
                     const int rx = px[k] - gl.x, ry = py - gl.y;
-                    r2[k] = (float)((long long)rx * rx + (long long)ry * ry);
+                    // float products (|rx|, |ry| < 2^15: relative error below 2^-22,
+                    // inside the 1e-5 margins of the map tests below)
+                    r2[k] = fmaf((float)rx, (float)rx, (float)ry * (float)ry);
                     const float a = (rx | ry) ? pang((float)rx, (float)ry) : 0.f;
                     bA[k] = ((int)floorf((a - kAngEps) / kAngW) + kAngBins) & (kAngBins - 1);
                     bB[k] = (int)floorf((a + kAngEps) / kAngW) & (kAngBins - 1);
@@ -636,7 +644,7 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
 // One CTA per tile; one kernel per tile size, so each gets its own register
 // allocation (32 x 32 tiles: 4 pixels a thread, 16 x 16: 1).
 template <int PX, bool MAPS>
-__global__ void __launch_bounds__(NT, PX == 4 ? 4 : SPM_PIX16_MINB) k_pixels(const __grid_constant__ DevScene ds,
+__global__ void __launch_bounds__(NT, PX == 4 ? SPM_PIX32_MINB : SPM_PIX16_MINB) k_pixels(const __grid_constant__ DevScene ds,
                                                                          float *__restrict__ dist,
                                                                          int32_t *__restrict__ parent, int tile0) {
     __shared__ PixSmem sm;
@@ -647,7 +655,7 @@ __global__ void __launch_bounds__(NT, PX == 4 ? 4 : SPM_PIX16_MINB) k_pixels(con
 // (scene, tile) from a global counter (scenes ordered largest first), copies
 // that scene's descriptor into shared memory and runs the same tile code.
 template <bool ANY_MAPS>  // some scene of the batch uses depth maps
-__global__ void __launch_bounds__(NT, 3) k_pixels_batched(const __grid_constant__ BatchDev b) {
+__global__ void __launch_bounds__(NT, SPM_PIXB_MINB) k_pixels_batched(const __grid_constant__ BatchDev b) {
     __shared__ PixSmem sm;
     __shared__ DevScene sds;
     __shared__ int cur, cur_scene;
