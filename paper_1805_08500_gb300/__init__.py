@@ -111,6 +111,7 @@ def load_library():
         "spm_last_error": ([P], ctypes.c_char_p),
         "spm_debug_fail_alloc_after": ([I32], None),
         "spm_debug_set_round_cap": ([I32], None),
+        "spm_debug_set_many_cta_fixpoint": ([I32], None),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

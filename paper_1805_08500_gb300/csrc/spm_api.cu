@@ -330,7 +330,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     ds.gen_cone = dalloc<int4>(s, hs.n_gen);
     ds.gen_ctype = dalloc<int32_t>(s, hs.n_gen);
     ds.dirty = dalloc<uint32_t>(s, (hs.n_gen + 31) / 32);
-    ds.counters = dalloc<int32_t>(s, 4);
+    ds.counters = dalloc<int32_t>(s, 8);
     ds.status = dalloc<uint32_t>(s, 1);
     ds.stats = dalloc<int32_t>(s, 4);
     {
@@ -393,6 +393,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     spm::launch_free_mask(ds, nullptr, free_bits);
     if (vert_maps) spm::launch_vert_maps(ds, nullptr, vert_maps);
     spm::launch_vis_static(ds, nullptr, vis_static);  // after the local depth maps it filters with
+    ds.fix_launch = spm::fixpoint_launches(ds);
     if (cudaPeekAtLastError() != cudaSuccess) {
         free_all(s);
         delete s;
@@ -1086,8 +1087,9 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     // tests) and the list scan and fill
     const bool reuse = floods && s->ds.flood_mode == 3 && s->ds.static_tile_start;
     const int src_cull = !spm::flood_sources_direct(s->ds) ? 2 : s->ds.n_poly > 0 ? 3 : 2;
-    info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.solo_smem > 0 ? 1 : 0) + 2 +  // vertex phase
-               (floods ? (reuse ? src_cull + 2 : 3) : 0) + 1;                    // flood, list scan and fill, pixels
+    info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.fix_launch & spm::kFixSolo ? 1 : 0) +
+               (s->ds.fix_launch & spm::kFixCluster ? 1 : 0) + (s->ds.fix_launch & (spm::kFixSoloSure | spm::kFixClusterSure) ? 0 : 1) + 1 +
+               (floods ? (reuse ? src_cull + 2 : 3) : 0) + 1;  // vertex phase; flood, list scan and fill; pixels
     return SPM_OK;
 }
 

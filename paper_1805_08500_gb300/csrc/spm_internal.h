@@ -128,6 +128,7 @@ struct DevScene {
     int32_t *counters;                 // [0,1] frontier sizes, [2,3] dirty-list sizes
     int32_t sssp_blocks;               // cooperative grid size (CTAs)
     int32_t solo_smem;                 // shared memory the single-CTA fixpoint may use (0: not available)
+    int32_t fix_launch;                // fixpoint kernels a compute launches (kFix* bits)
     // finalised generator table (read by the pixel kernel)
     float *gen_costf;                  // n_gen (inf when unreached)
     double *gen_cost;                  // n_gen
@@ -244,6 +245,12 @@ int flood_smem_attr();
 bool flood_sources_direct(const DevScene &ds);
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)
+bool cluster_smem_ok();  // the cluster fixpoint can run (its shared memory was granted)
+// fixpoint kernels of a scene's computes: the single-CTA one, the cluster
+// one, and whether one of them surely takes every compute's graph (then the
+// many-CTA kernel is not launched)
+constexpr int kFixSolo = 1, kFixCluster = 2, kFixSoloSure = 4, kFixClusterSure = 8;
+int fixpoint_launches(const DevScene &ds);  // from the static edge count (synchronous; scene creation)
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();
 // differentiable form (spm_grad.cu): the per-agent contributions of the

@@ -25,6 +25,9 @@
 // Costs are FP64 with explicitly rounded operations, so they match a plain
 // FP64 Dijkstra over the same edges bit for bit.
 #include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
 #include <atomic>
 #include <cuda_runtime.h>
 
@@ -46,6 +49,9 @@ constexpr int kSoloThreads = SPM_SOLO_THREADS;  // threads of the single-CTA fix
 #define SPM_SOLO_GRP 8
 #endif
 constexpr int kSoloGrp = SPM_SOLO_GRP;  // lanes per dirty vertex in the single-CTA fixpoint (in-degrees are small)
+#ifndef SPM_SOLO_MAX_DEG
+#define SPM_SOLO_MAX_DEG 8
+#endif
 constexpr int kSoloSmem = 226 * 1024;  // within the 227 KB opt-in maximum, with the static part
 
 // Static filter for one (u, v) pair: tangency at both ends, or for a
@@ -407,23 +413,27 @@ __device__ __forceinline__ void mark_out_warp(const DevScene &ds, int u, int lan
 // Shared-memory bytes the single-CTA fixpoint needs (0 if it cannot run).
 // Shared memory of the single-CTA fixpoint, 0 when the graph does not fit or
 // is not sparse. with_len: the FP64 edge lengths fit as well.
-__device__ __forceinline__ int solo_bytes(const DevScene &ds, bool &with_len) {
-    const long long n = ds.n_gen, E = ds.in_start[ds.n_vert];
+__host__ __device__ __forceinline__ int solo_bytes_for(long long n, int nv, long long E, long long edge_cap,
+                                                       int solo_smem, bool &with_len) {
     with_len = false;
-    // sparse graphs only (deep, few vertices per round); dense ones need the GPU
-    if (n >= 32768 || E > ds.edge_cap || E > 8 * n) return 0;
+    // sparse graphs only (deep, few vertices per round); dense ones need more SMs
+    if (n >= 32768 || E > edge_cap || E > SPM_SOLO_MAX_DEG * n) return 0;
     // cost 8, parent 2, lattice 4, wedge 8 per generator; CSR in / out with
     // 16-bit ids; two dirty bitmaps and lists; 16-byte alignment slack
-    const long long b = n * (8 + 2 + 4 + 8) + 4 * (ds.n_vert + 1) + 2 * E + 4 * (n + 1) + 2 * E +
+    const long long b = n * (8 + 2 + 4 + 8) + 4 * (nv + 1) + 2 * E + 4 * (n + 1) + 2 * E +
                         2 * 4 * ((n + 31) / 32) + 2 * 2 * n + 16 * 16;
-    if (b > ds.solo_smem) return 0;
-    with_len = b + 8 * E <= ds.solo_smem;
+    if (b > solo_smem) return 0;
+    with_len = b + 8 * E <= solo_smem;
     return (int)(with_len ? b + 8 * E : b);
+}
+__device__ __forceinline__ int solo_bytes(const DevScene &ds, bool &with_len) {
+    return solo_bytes_for(ds.n_gen, ds.n_vert, ds.in_start[ds.n_vert], ds.edge_cap, ds.solo_smem, with_len);
 }
 
 __global__ void __launch_bounds__(256) k_sssp(const __grid_constant__ DevScene ds, int max_rounds) {
     bool solo_len;
     if (solo_bytes(ds, solo_len) > 0) return;  // the single-CTA kernel handles this graph
+    if (ds.counters[4]) return;                // the cluster kernel did
     cg::grid_group grid = cg::this_grid();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsize = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, gwarp = gtid >> 5, nwarps = gsize >> 5;
@@ -767,6 +777,255 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     if (tid == 0) ds.stats[0] = round;
 }
 
+// The fixpoint of graphs too dense for one CTA: one cluster of kClCtas CTAs,
+// one per SM, with the generators' state (cost, parent, lattice position,
+// wedge) replicated in every CTA's shared memory and the obstacle vertices
+// dealt round-robin to the CTAs, each holding the in-lists of its own. A
+// round works as in the single-CTA kernel (a dirty vertex pulls the current
+// state of its in-neighbours, writes a changed value into every CTA's copy
+// and marks its out-neighbours in their owners' next dirty bitmap and list,
+// through distributed shared memory), with one cluster barrier per round in
+// place of the grid barriers of the many-CTA kernel. The argument of the
+// single-CTA kernel carries over: a pull may read a neighbour mid-update,
+// whose change marks the puller again, so the loop stops at the fixpoint of
+// the vertex equations, which is unique.
+constexpr int kClCtas = 8;          // CTAs of the cluster (the portable size)
+constexpr int kClThreads = 1024;
+constexpr int kClGrp = 16;          // lanes per dirty vertex (dense in-lists); at least kClCtas
+constexpr int kClSmem = 200 * 1024; // dynamic shared memory per CTA
+
+// The cluster fixpoint's layout: the replicated state and the dirty lists at
+// offsets every CTA shares, then the CTA's own in-lists.
+struct ClLayout {
+    size_t cost, wedge, par, lat, dirty, dl, lin_start, lin_src, lin_len, end;
+};
+__host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own) {
+    auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const int nmax = (nv + kClCtas - 1) / kClCtas, dw = (nmax + 31) / 32;
+    ClLayout L;
+    L.cost = 0;
+    L.wedge = L.cost + up(8 * (size_t)n);
+    L.par = L.wedge + up(8 * (size_t)n);
+    L.lat = L.par + up(2 * (size_t)n);
+    L.dirty = L.lat + up(4 * (size_t)n);
+    L.dl = L.dirty + up(4 * 2 * (size_t)dw);
+    L.lin_start = L.dl + up(2 * 2 * (size_t)nmax);
+    L.lin_src = L.lin_start + up(4 * ((size_t)nmax + 1));
+    L.lin_len = L.lin_src + up(2 * (size_t)e_own);
+    L.end = L.lin_len + up(8 * (size_t)e_own);
+    return L;
+}
+
+__global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
+    k_sssp_cluster(const __grid_constant__ DevScene ds, int max_rounds) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ int cnt[3];                      // dirty-list counts, by round modulo 3
+    __shared__ long long e_own_sh;              // in-edges of this CTA's vertices
+    __shared__ int total_sh;
+    __shared__ long long wsum[32];
+    __shared__ signed char src_kind[kSoloSrc];
+    __shared__ int4 src_seg[kSoloSrc];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kClThreads / 32;
+    bool solo_len;
+    if (solo_bytes(ds, solo_len) > 0) return;  // the single-CTA kernel handles this graph (every CTA agrees)
+    const int n = ds.n_gen, nv = ds.n_vert, ns = ds.n_src;
+    const long long E = ds.in_start[nv];
+    if (n >= 32768 || E > ds.edge_cap || nv == 0) {
+        if (rank == 0 && tid == 0) ds.counters[4] = 0;  // the many-CTA kernel runs
+        return;
+    }
+    const int C = kClCtas, nmax = (nv + C - 1) / C, dw = (nmax + 31) / 32;
+    const int n_own = rank < nv ? (nv - rank + C - 1) / C : 0;  // vertices vv = rank + C * k
+    // this CTA's in-list offsets: a scan over its vertices, in chunks
+    const int per = (n_own + kClThreads - 1) / kClThreads, lo = min(n_own, tid * per), hi = min(n_own, lo + per);
+    long long mine = 0;
+    for (int k = lo; k < hi; ++k) mine += ds.in_start[rank + C * k + 1] - ds.in_start[rank + C * k];
+    const long long before = cta_exclusive_scan(mine, wsum);
+    if (hi == n_own && lo < hi) e_own_sh = before + mine;
+    if (tid == 0 && n_own == 0) e_own_sh = 0;
+    __syncthreads();
+    // every CTA's list must fit: the largest one decides, the same in all
+    cluster.sync();
+    if (tid == 0) {
+        long long mx = 0;
+        for (int r = 0; r < C; ++r) mx = max(mx, *cluster.map_shared_rank(&e_own_sh, r));
+        total_sh = cl_layout(n, nv, mx).end <= (size_t)kClSmem ? 1 : 0;
+    }
+    cluster.sync();  // the remote reads are done before any CTA leaves
+    if (!total_sh) {
+        if (rank == 0 && tid == 0) ds.counters[4] = 0;
+        return;
+    }
+    if (rank == 0 && tid == 0) ds.counters[4] = 1;  // handled here
+    const ClLayout L = cl_layout(n, nv, e_own_sh);
+    double *cost = (double *)(sm_raw + L.cost);
+    short4 *wedge = (short4 *)(sm_raw + L.wedge);
+    short *par = (short *)(sm_raw + L.par);
+    short2 *lat = (short2 *)(sm_raw + L.lat);
+    unsigned *dirty = (unsigned *)(sm_raw + L.dirty);          // round parity p at p * dw
+    unsigned short *dl = (unsigned short *)(sm_raw + L.dl);    // round parity p at p * nmax
+    int *lin_start = (int *)(sm_raw + L.lin_start);
+    unsigned short *lin_src = (unsigned short *)(sm_raw + L.lin_src);
+    double *lin_len = (double *)(sm_raw + L.lin_len);
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    {
+        long long run = before;
+        for (int k = lo; k < hi; ++k) {
+            lin_start[k] = (int)run;
+            run += ds.in_start[rank + C * k + 1] - ds.in_start[rank + C * k];
+        }
+        if (hi == n_own && lo < hi) lin_start[n_own] = (int)run;
+        if (tid == 0 && n_own == 0) lin_start[0] = 0;
+    }
+    for (int g = tid; g < n; g += kClThreads) {
+        const bool src = g < ns;
+        cost[g] = src ? 0.0 : inf;
+        par[g] = (short)(src ? g : -1);
+        const int2 l = ds.gen_lat[g];
+        lat[g] = make_short2((short)l.x, (short)l.y);
+        const int4 w = ds.gen_wedge[g];
+        wedge[g] = make_short4((short)w.x, (short)w.y, (short)w.z, (short)w.w);
+    }
+    for (int w = tid; w < 2 * dw; w += kClThreads) dirty[w] = 0u;
+    for (int g = tid; g < min(ns, kSoloSrc); g += kClThreads) {
+        const int k = ds.gen_kind[g];
+        src_kind[g] = (signed char)k;
+        src_seg[g] = k == kSegI ? ds.seg_lat[ds.gen_aux[g]] : make_int4(0, 0, 0, 0);
+    }
+    if (tid < 3) cnt[tid] = 0;
+    __syncthreads();  // lin_start
+    for (int k = warp; k < n_own; k += nwarps) {  // this CTA's in-lists, a warp per vertex
+        const int vv = rank + C * k, e0 = ds.in_start[vv], m = ds.in_start[vv + 1] - e0, b = lin_start[k];
+        for (int j = lane; j < m; j += 32) {
+            lin_src[b + j] = (unsigned short)ds.in_src[e0 + j];
+            lin_len[b + j] = ds.in_len[e0 + j];
+        }
+    }
+    cluster.sync();  // every CTA's bitmaps and counts are ready for marks
+    constexpr int kGpw = 32 / kClGrp;
+    const int grp = lane / kClGrp, gl = lane % kClGrp, ngroups = nwarps * kGpw;
+    const unsigned kFull = 0xffffffffu;
+    // mark vertex w (a generator id >= ns) dirty in round parity `par_n` of its owner
+    auto mark = [&](int w, int par_n, int cslot) {
+        const int vv = w - ns, owner = vv % C, lw = vv / C;
+        const unsigned bit = 1u << (lw & 31);
+        unsigned *rd = cluster.map_shared_rank(dirty, owner) + par_n * dw + (lw >> 5);
+        if (!(atomicOr(rd, bit) & bit)) {
+            const int slot = atomicAdd(cluster.map_shared_rank(&cnt[cslot], owner), 1);
+            cluster.map_shared_rank(dl, owner)[par_n * nmax + slot] = (unsigned short)lw;
+        }
+    };
+    // the sources mark their out-neighbours for round 0
+    for (int u = rank * ngroups + warp * kGpw + grp; u < ns; u += C * ngroups)
+        for (int e = ds.out_start[u] + gl; e < ds.out_start[u + 1]; e += kClGrp) mark(ds.out_dst[e], 0, 0);
+    cluster.sync();
+    int round = 0;
+    for (;; ++round) {
+        const int cur = round & 1, nxt = cur ^ 1;
+        if (warp == 0) {  // dirty vertices in the whole cluster this round
+            int t = lane < C ? *cluster.map_shared_rank(&cnt[round % 3], lane) : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+            if (lane == 0) total_sh = t;
+        }
+        __syncthreads();
+        const int total = total_sh;
+        if (total == 0) break;
+        if (round >= max_rounds) {
+            if (rank == 0 && tid == 0) atomicOr(ds.status, kStNotConverged);
+            break;
+        }
+        const int nd = cnt[round % 3];
+        if (tid == 0) cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
+        const int cslot = (round + 1) % 3;
+        for (int i0 = warp * kGpw; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
+            const int i = i0 + grp;
+            const bool act = i < nd;
+            const int lw = dl[cur * nmax + min(i, nmax - 1)];
+            const int lk = act ? lw : 0;
+            const int v = ns + rank + C * lk;
+            const int e0 = lin_start[lk] + gl, e1 = act ? lin_start[lk + 1] : 0;
+            const short2 vl = lat[v];
+            const long long cv = __double_as_longlong(cost[v]);
+            const int pv = par[v];
+            long long best = 0x7ff0000000000000ll;  // +inf bits
+            int bpar = -1;
+            for (int e = e0; e < e1; e += kClGrp) {
+                const double len = lin_len[e];
+                const int u = lin_src[e];
+                const double cu = cost[u];
+                const int pu = par[u];
+                const short2 ul = lat[u];
+                const short4 w = wedge[u];
+                // u's arrival direction: from its parent, or perpendicular to a
+                // segment source whose interior is the parent
+                const int pc = pu < 0 ? 0 : pu, ps = pc < kSoloSrc ? pc : 0;
+                const short2 pl = lat[pc];
+                const int4 Ls = src_seg[ps];
+                int dx = ul.x - pl.x, dy = ul.y - pl.y;
+                if (pu < ns && pu >= kSoloSrc) {
+                    arrival_from(ds, src_kind, src_seg, lat, pu, ul, dx, dy);
+                } else if (pu >= 0 && pu < ns && src_kind[ps] == kSegI) {
+                    const int sx = Ls.z - Ls.x, sy = Ls.w - Ls.y;
+                    const int side = cross32(sx, sy, ul.x - Ls.x, ul.y - Ls.y);
+                    dx = side > 0 ? -sy : sy;
+                    dy = side > 0 ? sx : -sx;
+                }
+                const bool valid = (__double_as_longlong(cu) < 0x7ff0000000000000ll) &
+                                   ((u < ns) | ((pu >= 0) & in_shadow_cone(dx, dy, w, vl.x - ul.x, vl.y - ul.y)));
+                const long long cand = __double_as_longlong(__dadd_rn(cu, len));
+                const bool better = valid & (cand < best);
+                best = better ? cand : best;
+                bpar = better ? u : bpar;
+            }
+#pragma unroll
+            for (int o = kClGrp / 2; o > 0; o >>= 1) {  // within the group
+                const long long ob = __shfl_xor_sync(kFull, best, o);
+                const int op = __shfl_xor_sync(kFull, bpar, o);
+                if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
+                    best = ob;
+                    bpar = op;
+                }
+            }
+            const bool changed = act && (best != cv || bpar != pv);
+            if (changed && gl < C) {  // lane gl writes CTA gl's copy
+                cluster.map_shared_rank(cost, gl)[v] = __longlong_as_double(best);
+                cluster.map_shared_rank(par, gl)[v] = (short)bpar;
+            }
+            if (changed)
+                for (int e = ds.out_start[v] + gl; e < ds.out_start[v + 1]; e += kClGrp) mark(ds.out_dst[e], nxt, cslot);
+        }
+        // this round's bitmap is free again (marks went to the other one)
+        for (int w = kClThreads - 1 - tid; w < dw; w += kClThreads) dirty[cur * dw + w] = 0u;
+        cluster.sync();
+    }
+    cluster.sync();  // the last round's remote reads of the counts are done
+    // the settled state of this CTA's vertices (and, in CTA 0, the sources),
+    // with each vertex's shadow cone from its parent
+    for (int k = tid; k < n_own + (rank == 0 ? ns : 0); k += kClThreads) {
+        const int g = k < n_own ? ns + rank + C * k : k - n_own;
+        const int pg = par[g];
+        int4 c = make_int4(0, 0, 0, 0);
+        int ct = kConeNone;
+        if (g >= ns) {
+            ct = kConeEmpty;
+            if (pg >= 0) {
+                int dx, dy;
+                arrival_from(ds, src_kind, src_seg, lat, pg, lat[g], dx, dy);
+                const short4 w = wedge[g];
+                ct = make_cone(make_int4(w.x, w.y, w.z, w.w), dx, dy, c);
+            }
+        }
+        ds.cost[0][g] = cost[g];
+        ds.par[0][g] = pg;
+        ds.gen_cone[g] = c;
+        ds.gen_ctype[g] = ct;
+    }
+    if (rank == 0 && tid == 0) ds.stats[0] = round;
+}
+
 // Final generator table for the pixel phase: FP32 costs and shadow cones.
 __device__ __forceinline__ void finalize_gen(const DevScene &ds, int g) {
     {
@@ -995,6 +1254,7 @@ int vis_resident_blocks();  // co-resident CTAs of the visibility-pair kernel
 // Round cap of the vertex fixpoint: 4 rounds per generator and 64 more (far
 // above the longest shortest path in links), or the test hook's override.
 std::atomic<int> g_round_cap_override{0};
+std::atomic<int> g_many_cta_override{0};
 int fixpoint_round_cap(int n_gen) {
     const int o = g_round_cap_override.load();
     return o > 0 ? o : 4 * n_gen + 64;
@@ -1026,6 +1286,77 @@ void launch_vis_static(const DevScene &ds, cudaStream_t st, uint32_t *vis_static
     launch_pairs(d, st);
 }
 
+namespace {
+// set bits of each row of a bit matrix (a warp per row)
+__global__ void k_row_bits(const uint32_t *bits, int rows, int words, int32_t *out) {
+    const int lane = threadIdx.x & 31;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += (gridDim.x * blockDim.x) >> 5) {
+        int c = 0;
+        for (int w = lane; w < words; w += 32) c += __popc(bits[(size_t)r * words + w]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) out[r] = c;
+    }
+}
+}  // namespace
+
+// Which fixpoint kernels a compute launches. A vertex's in-edges are its
+// obstacle-vertex pairs in the scene's static bits, fixed, plus at most one
+// from each source; those bounds decide, per kernel, whether it surely takes
+// every compute's graph, surely takes none, or has to see the graph.
+int fixpoint_launches(const DevScene &ds) {
+    int f = (ds.solo_smem > 0 ? kFixSolo : 0) | (cluster_smem_ok() ? kFixCluster : 0);
+    const int nv = ds.n_vert;
+    std::vector<int32_t> deg(nv > 0 ? nv : 1, 0);
+    int32_t *d = nullptr;
+    bool ok = nv > 0 && ds.vis_static && cudaMalloc(&d, sizeof(int32_t) * nv) == cudaSuccess;
+    if (ok) {
+        k_row_bits<<<std::min((nv + 7) / 8, 152 * 8), 256>>>(ds.vis_static, nv, ds.vis_words, d);
+        ok = cudaMemcpy(deg.data(), d, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    if (d) cudaFree(d);
+    if (!ok) return f;  // unknown: the kernels decide on the device
+    long long lo = 0, own_max = 0;
+    for (int r = 0; r < kClCtas; ++r) {
+        long long own = 0;
+        for (int vv = r; vv < nv; vv += kClCtas) own += deg[vv] + ds.n_src;
+        own_max = std::max(own_max, own);
+    }
+    for (int vv = 0; vv < nv; ++vv) lo += deg[vv];
+    const long long hi = lo + (long long)ds.n_src * nv;
+    // the single-CTA kernel's test only gets stricter as the edges grow
+    bool wl;
+    const bool solo_never = solo_bytes_for(ds.n_gen, nv, lo, ds.edge_cap, ds.solo_smem, wl) == 0;
+    const bool solo_sure = solo_bytes_for(ds.n_gen, nv, hi, ds.edge_cap, ds.solo_smem, wl) > 0;
+    const bool cluster_sure = (f & kFixCluster) && ds.n_gen < 32768 && hi <= ds.edge_cap &&
+                              cl_layout(ds.n_gen, nv, own_max).end <= (size_t)kClSmem;
+    if (solo_never) f &= ~kFixSolo;
+    if (solo_sure) f = (f & ~kFixCluster) | kFixSoloSure;
+    if (cluster_sure && !solo_sure) f |= kFixClusterSure;
+    return f;
+}
+
+// the cluster fixpoint's shared memory, granted once per process
+bool cluster_smem_ok() {
+    static const bool ok = [] {
+        if (cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kClCtas);
+        cfg.blockDim = dim3(kClThreads);
+        cfg.dynamicSmemBytes = kClSmem;
+        int clusters = 0;  // the GPU can hold one such cluster at all
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_sssp_cluster, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return clusters > 0;
+    }();
+    return ok;
+}
+
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
     cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
     cudaMemsetAsync(ds.out_fill, 0, sizeof(int32_t) * ds.n_gen, st);
@@ -1047,8 +1378,16 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
     DevScene arg = ds;
     int max_rounds = fixpoint_round_cap(ds.n_gen);
     void *args[] = {&arg, &max_rounds};
-    if (ds.solo_smem > 0) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(ds, max_rounds);
-    cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
+    // each fixpoint kernel checks on the device whether the graph is its
+    // own; the scene's bounds on the edge count skip the launches that
+    // cannot apply
+    int f = ds.fix_launch;
+    if (g_many_cta_override.load() && !(f & kFixSoloSure)) f &= ~(kFixCluster | kFixClusterSure);  // test hook
+    if (f & kFixSolo) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(ds, max_rounds);
+    if (f & kFixCluster) k_sssp_cluster<<<kClCtas, kClThreads, kClSmem, st>>>(ds, max_rounds);
+    else if (!(f & kFixSoloSure)) cudaMemsetAsync(ds.counters + 4, 0, sizeof(int32_t), st);
+    if (!(f & (kFixSoloSure | kFixClusterSure)))
+        cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
     k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
 }
 
@@ -1109,6 +1448,7 @@ void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st) {
 }  // namespace spm
 
 extern "C" void spm_debug_set_round_cap(int32_t n) { spm::g_round_cap_override.store(n > 0 ? n : 0); }
+extern "C" void spm_debug_set_many_cta_fixpoint(int32_t on) { spm::g_many_cta_override.store(on ? 1 : 0); }
 
 #ifdef SPM_COUNT
 // Instrumentation build only: reads and clears this unit's work counters.

@@ -209,6 +209,31 @@ def test_vertex_costs_bit_exact(spm, oracle_mod):
         assert np.all(cost[rest] >= o.cost[rest])
 
 
+def test_fixpoint_kernels_agree(spm):
+    """A graph too dense for the single-CTA fixpoint goes to one cluster of
+    CTAs (state replicated in shared memory, a cluster barrier per round); the
+    many-CTA kernel (synchronous rounds between grid barriers) is the
+    fallback. Both reach the one fixpoint of the vertex equations: the same
+    costs and parents bit for bit, and the same map."""
+    lib = spm.load_library()
+    for scene in (sg.plain_polys(2, n_polys=120, N=256),
+                  sg.differentiable(1, W=2048, N=512, n_polys=60, n_agents=10)):
+        s = spm.Scene(scene)
+        d0, p0 = s.compute()
+        s.sync()
+        g0 = s.generators()
+        try:
+            lib.spm_debug_set_many_cta_fixpoint(1)
+            d1, p1 = s.compute()
+            s.sync()
+            g1 = s.generators()
+        finally:
+            lib.spm_debug_set_many_cta_fixpoint(0)
+        for a, b in zip(g0, g1):
+            assert np.array_equal(a, b), scene.name
+        assert torch.equal(p0, p1) and torch.equal(d0.view(torch.int32), d1.view(torch.int32)), scene.name
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
@@ -819,19 +844,22 @@ def test_round_cap_reports_not_converged(spm):
     library's test hook), a maze that needs hundreds of rounds reports
     SPM_ERR_NOT_CONVERGED at the next sync -- the kernel stops and returns,
     nothing waits -- and the next compute with the default cap gives bit for
-    bit the map of a fresh scene. Also for a dense graph (the multi-SM
-    fixpoint)."""
+    bit the map of a fresh scene. Also for a dense graph, in both multi-SM
+    fixpoints (one cluster of CTAs, and the many-CTA fallback)."""
     lib = spm.load_library()
-    for scene in (sg.maze(6, cells=12, N=768), sg.plain_polys(3, W=4096, N=256, n_polys=150)):
+    dense = sg.plain_polys(3, W=4096, N=256, n_polys=150)
+    for scene, many in ((sg.maze(6, cells=12, N=768), 0), (dense, 0), (dense, 1)):
         s = spm.Scene(scene)
         try:
             lib.spm_debug_set_round_cap(1)
+            lib.spm_debug_set_many_cta_fixpoint(many)
             s.compute()
             with pytest.raises(spm.SpmError) as e:
                 s.sync()
             assert e.value.status == spm.SPM_ERR_NOT_CONVERGED, scene.name
         finally:
             lib.spm_debug_set_round_cap(0)
+            lib.spm_debug_set_many_cta_fixpoint(0)
         d, p = s.compute()
         s.sync()
         fresh = spm.Scene(scene)
