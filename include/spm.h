@@ -378,9 +378,10 @@ void spm_debug_set_round_cap(int32_t n);
 
 /* Test hook (no counterpart in the paper): on != 0 makes every later
  * compute solve the vertex fixpoint of a graph the single-CTA kernel does not
- * take with the many-CTA kernel (synchronous rounds between grid barriers)
- * instead of the cluster kernel, so that tests can compare the two; on == 0
- * restores the default choice. Process-wide; no effect unless called. */
+ * take, and every batch created later solve all its scenes' fixpoints, with
+ * the many-CTA kernel (synchronous rounds between grid barriers) instead of
+ * the cluster kernel, so that tests can compare the two; on == 0 restores
+ * the default choice. Process-wide; no effect unless called. */
 void spm_debug_set_many_cta_fixpoint(int32_t on);
 
 #ifdef __cplusplus

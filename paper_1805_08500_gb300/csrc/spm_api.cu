@@ -835,6 +835,18 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
         bd.frontier[k] = balloc<int2>(b, gen_off[n]);
     }
     bd.counters = balloc<int32_t>(b, 8);
+    {  // the vertex fixpoint on resident clusters, most generators first
+        std::vector<int32_t> cl_order(n);
+        for (int k = 0; k < n; ++k) cl_order[k] = k;
+        std::stable_sort(cl_order.begin(), cl_order.end(),
+                         [&](int a, int c) { return descs[a].n_gen > descs[c].n_gen; });
+        bd.cl_order = bupload(b, cl_order, ok);
+        bd.cl_done = balloc<int32_t>(b, n);
+        bd.cl_counter = balloc<int32_t>(b, 1);
+        bd.cl_grid = spm::cluster_batched_grid();
+        bd.cl_all = bd.cl_grid > 0 ? 1 : 0;
+        for (int k = 0; k < n; ++k) bd.cl_all &= (descs[k].fix_launch & spm::kFixClusterFits) ? 1 : 0;
+    }
     bd.max_rounds = spm::fixpoint_round_cap(max_gen);
     bd.sssp_blocks = spm::sssp_batched_grid_blocks();
     bd.flood_smem = 0;

@@ -203,6 +203,12 @@ struct BatchDev {
     const long long *src_ins_off;      // warp tasks of the map building: n_src * n_poly
     const long long *src_tile_off;     // warp tasks of the tile tests: n_src * tiles
     int32_t walk_tasks;                // (scene, generator) walks of the batched flood
+    // vertex fixpoint on resident clusters, one scene at a time
+    const int32_t *cl_order;           // n scene indices, most generators first
+    int32_t *cl_done;                  // n flags: a cluster took the scene's fixpoint
+    int32_t *cl_counter;               // the clusters' work counter
+    int32_t cl_grid;                   // CTAs of the clusters' launch (0: no cluster kernel)
+    int32_t cl_all;                    // the clusters take every scene: no many-CTA kernel
 };
 
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
@@ -250,7 +256,9 @@ bool cluster_smem_ok();  // the cluster fixpoint can run (its shared memory was 
 // one, and whether one of them surely takes every compute's graph (then the
 // many-CTA kernel is not launched)
 constexpr int kFixSolo = 1, kFixCluster = 2, kFixSoloSure = 4, kFixClusterSure = 8;
+constexpr int kFixClusterFits = 16;  // the cluster kernel takes every compute's graph (batched form)
 int fixpoint_launches(const DevScene &ds);  // from the static edge count (synchronous; scene creation)
+int cluster_batched_grid();  // CTAs of the batched cluster fixpoint's launch (0: unavailable)
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();
 // differentiable form (spm_grad.cu): the per-agent contributions of the

@@ -795,11 +795,12 @@ constexpr int kClGrp = 16;          // lanes per dirty vertex (dense in-lists); 
 constexpr int kClSmem = 200 * 1024; // dynamic shared memory per CTA
 
 // The cluster fixpoint's layout: the replicated state and the dirty lists at
-// offsets every CTA shares, then the CTA's own in-lists.
+// offsets every CTA shares, then the CTA's own in-lists (with their FP64
+// lengths when they fit; else the lengths are read from global memory).
 struct ClLayout {
     size_t cost, wedge, par, lat, dirty, dl, lin_start, lin_src, lin_len, end;
 };
-__host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own) {
+__host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own, bool with_len) {
     auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
     const int nmax = (nv + kClCtas - 1) / kClCtas, dw = (nmax + 31) / 32;
     ClLayout L;
@@ -812,54 +813,67 @@ __host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long 
     L.lin_start = L.dl + up(2 * 2 * (size_t)nmax);
     L.lin_src = L.lin_start + up(4 * ((size_t)nmax + 1));
     L.lin_len = L.lin_src + up(2 * (size_t)e_own);
-    L.end = L.lin_len + up(8 * (size_t)e_own);
+    L.end = L.lin_len + (with_len ? up(8 * (size_t)e_own) : 0);
     return L;
 }
 
-__global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
-    k_sssp_cluster(const __grid_constant__ DevScene ds, int max_rounds) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    __shared__ int cnt[3];                      // dirty-list counts, by round modulo 3
-    __shared__ long long e_own_sh;              // in-edges of this CTA's vertices
-    __shared__ int total_sh;
-    __shared__ long long wsum[32];
-    __shared__ signed char src_kind[kSoloSrc];
-    __shared__ int4 src_seg[kSoloSrc];
-    cg::cluster_group cluster = cg::this_cluster();
+// Per-CTA static shared state of the cluster fixpoint.
+struct ClShared {
+    int cnt[3];                  // dirty-list counts, by round modulo 3
+    long long e_own;             // in-edges of this CTA's vertices
+    int total;                   // a value broadcast to the CTA
+    int next;                    // the batched form's next scene (CTA 0)
+    long long wsum[32];
+    signed char src_kind[kSoloSrc];
+    int4 src_seg[kSoloSrc];
+};
+
+// One scene's fixpoint on the calling cluster (every thread of it calls).
+// Returns false, having written nothing, when the graph cannot be taken
+// (16-bit ids, edge capacity, shared memory); every CTA returns the same.
+__device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &cluster, ClShared &sh,
+                         unsigned char *sm_raw) {
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kClThreads / 32;
-    bool solo_len;
-    if (solo_bytes(ds, solo_len) > 0) return;  // the single-CTA kernel handles this graph (every CTA agrees)
     const int n = ds.n_gen, nv = ds.n_vert, ns = ds.n_src;
-    const long long E = ds.in_start[nv];
-    if (n >= 32768 || E > ds.edge_cap || nv == 0) {
-        if (rank == 0 && tid == 0) ds.counters[4] = 0;  // the many-CTA kernel runs
-        return;
+    if (nv == 0) {  // sources only: nothing to relax
+        if (rank == 0) {
+            for (int g = tid; g < ns; g += kClThreads) {
+                ds.cost[0][g] = 0.0;
+                ds.par[0][g] = g;
+                ds.gen_cone[g] = make_int4(0, 0, 0, 0);
+                ds.gen_ctype[g] = kConeNone;
+            }
+            if (tid == 0) ds.stats[0] = 0;
+        }
+        return true;
     }
+    const long long E = ds.in_start[nv];
+    if (n >= 32768 || E > ds.edge_cap) return false;
     const int C = kClCtas, nmax = (nv + C - 1) / C, dw = (nmax + 31) / 32;
     const int n_own = rank < nv ? (nv - rank + C - 1) / C : 0;  // vertices vv = rank + C * k
     // this CTA's in-list offsets: a scan over its vertices, in chunks
     const int per = (n_own + kClThreads - 1) / kClThreads, lo = min(n_own, tid * per), hi = min(n_own, lo + per);
     long long mine = 0;
     for (int k = lo; k < hi; ++k) mine += ds.in_start[rank + C * k + 1] - ds.in_start[rank + C * k];
-    const long long before = cta_exclusive_scan(mine, wsum);
-    if (hi == n_own && lo < hi) e_own_sh = before + mine;
-    if (tid == 0 && n_own == 0) e_own_sh = 0;
+    const long long before = cta_exclusive_scan(mine, sh.wsum);
+    if (hi == n_own && lo < hi) sh.e_own = before + mine;
+    if (tid == 0 && n_own == 0) sh.e_own = 0;
     __syncthreads();
-    // every CTA's list must fit: the largest one decides, the same in all
+    // every CTA's lists must fit: the largest decides, the same in all
     cluster.sync();
     if (tid == 0) {
         long long mx = 0;
-        for (int r = 0; r < C; ++r) mx = max(mx, *cluster.map_shared_rank(&e_own_sh, r));
-        total_sh = cl_layout(n, nv, mx).end <= (size_t)kClSmem ? 1 : 0;
+        for (int r = 0; r < C; ++r) mx = max(mx, *cluster.map_shared_rank(&sh.e_own, r));
+        sh.total = cl_layout(n, nv, mx, true).end <= (size_t)kClSmem    ? 2
+                   : cl_layout(n, nv, mx, false).end <= (size_t)kClSmem ? 1
+                                                                         : 0;
     }
-    cluster.sync();  // the remote reads are done before any CTA leaves
-    if (!total_sh) {
-        if (rank == 0 && tid == 0) ds.counters[4] = 0;
-        return;
-    }
-    if (rank == 0 && tid == 0) ds.counters[4] = 1;  // handled here
-    const ClLayout L = cl_layout(n, nv, e_own_sh);
+    cluster.sync();  // the remote reads are done before any CTA moves on
+    const int fit = sh.total;
+    if (!fit) return false;
+    const bool with_len = fit == 2;
+    const ClLayout L = cl_layout(n, nv, sh.e_own, with_len);
     double *cost = (double *)(sm_raw + L.cost);
     short4 *wedge = (short4 *)(sm_raw + L.wedge);
     short *par = (short *)(sm_raw + L.par);
@@ -868,7 +882,7 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
     unsigned short *dl = (unsigned short *)(sm_raw + L.dl);    // round parity p at p * nmax
     int *lin_start = (int *)(sm_raw + L.lin_start);
     unsigned short *lin_src = (unsigned short *)(sm_raw + L.lin_src);
-    double *lin_len = (double *)(sm_raw + L.lin_len);
+    double *lin_len = (double *)(sm_raw + L.lin_len);          // with_len only
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     {
         long long run = before;
@@ -891,29 +905,29 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
     for (int w = tid; w < 2 * dw; w += kClThreads) dirty[w] = 0u;
     for (int g = tid; g < min(ns, kSoloSrc); g += kClThreads) {
         const int k = ds.gen_kind[g];
-        src_kind[g] = (signed char)k;
-        src_seg[g] = k == kSegI ? ds.seg_lat[ds.gen_aux[g]] : make_int4(0, 0, 0, 0);
+        sh.src_kind[g] = (signed char)k;
+        sh.src_seg[g] = k == kSegI ? ds.seg_lat[ds.gen_aux[g]] : make_int4(0, 0, 0, 0);
     }
-    if (tid < 3) cnt[tid] = 0;
+    if (tid < 3) sh.cnt[tid] = 0;
     __syncthreads();  // lin_start
     for (int k = warp; k < n_own; k += nwarps) {  // this CTA's in-lists, a warp per vertex
         const int vv = rank + C * k, e0 = ds.in_start[vv], m = ds.in_start[vv + 1] - e0, b = lin_start[k];
         for (int j = lane; j < m; j += 32) {
             lin_src[b + j] = (unsigned short)ds.in_src[e0 + j];
-            lin_len[b + j] = ds.in_len[e0 + j];
+            if (with_len) lin_len[b + j] = ds.in_len[e0 + j];
         }
     }
     cluster.sync();  // every CTA's bitmaps and counts are ready for marks
     constexpr int kGpw = 32 / kClGrp;
     const int grp = lane / kClGrp, gl = lane % kClGrp, ngroups = nwarps * kGpw;
     const unsigned kFull = 0xffffffffu;
-    // mark vertex w (a generator id >= ns) dirty in round parity `par_n` of its owner
+    // mark vertex w (a generator id >= ns) dirty in round parity par_n of its owner
     auto mark = [&](int w, int par_n, int cslot) {
         const int vv = w - ns, owner = vv % C, lw = vv / C;
         const unsigned bit = 1u << (lw & 31);
         unsigned *rd = cluster.map_shared_rank(dirty, owner) + par_n * dw + (lw >> 5);
         if (!(atomicOr(rd, bit) & bit)) {
-            const int slot = atomicAdd(cluster.map_shared_rank(&cnt[cslot], owner), 1);
+            const int slot = atomicAdd(cluster.map_shared_rank(&sh.cnt[cslot], owner), 1);
             cluster.map_shared_rank(dl, owner)[par_n * nmax + slot] = (unsigned short)lw;
         }
     };
@@ -925,35 +939,36 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
     for (;; ++round) {
         const int cur = round & 1, nxt = cur ^ 1;
         if (warp == 0) {  // dirty vertices in the whole cluster this round
-            int t = lane < C ? *cluster.map_shared_rank(&cnt[round % 3], lane) : 0;
+            int t = lane < C ? *cluster.map_shared_rank(&sh.cnt[round % 3], lane) : 0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-            if (lane == 0) total_sh = t;
+            if (lane == 0) sh.total = t;
         }
         __syncthreads();
-        const int total = total_sh;
+        const int total = sh.total;
         if (total == 0) break;
         if (round >= max_rounds) {
             if (rank == 0 && tid == 0) atomicOr(ds.status, kStNotConverged);
             break;
         }
-        const int nd = cnt[round % 3];
-        if (tid == 0) cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
+        const int nd = sh.cnt[round % 3];
+        if (tid == 0) sh.cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
         const int cslot = (round + 1) % 3;
         for (int i0 = warp * kGpw; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
             const int lw = dl[cur * nmax + min(i, nmax - 1)];
             const int lk = act ? lw : 0;
-            const int v = ns + rank + C * lk;
+            const int vv = rank + C * lk, v = ns + vv;
             const int e0 = lin_start[lk] + gl, e1 = act ? lin_start[lk + 1] : 0;
+            const int eg = ds.in_start[vv] - lin_start[lk];  // local -> global edge index (lengths)
             const short2 vl = lat[v];
             const long long cv = __double_as_longlong(cost[v]);
             const int pv = par[v];
             long long best = 0x7ff0000000000000ll;  // +inf bits
             int bpar = -1;
             for (int e = e0; e < e1; e += kClGrp) {
-                const double len = lin_len[e];
+                const double len = with_len ? lin_len[e] : __ldg(ds.in_len + eg + e);
                 const int u = lin_src[e];
                 const double cu = cost[u];
                 const int pu = par[u];
@@ -963,11 +978,11 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
                 // segment source whose interior is the parent
                 const int pc = pu < 0 ? 0 : pu, ps = pc < kSoloSrc ? pc : 0;
                 const short2 pl = lat[pc];
-                const int4 Ls = src_seg[ps];
+                const int4 Ls = sh.src_seg[ps];
                 int dx = ul.x - pl.x, dy = ul.y - pl.y;
                 if (pu < ns && pu >= kSoloSrc) {
-                    arrival_from(ds, src_kind, src_seg, lat, pu, ul, dx, dy);
-                } else if (pu >= 0 && pu < ns && src_kind[ps] == kSegI) {
+                    arrival_from(ds, sh.src_kind, sh.src_seg, lat, pu, ul, dx, dy);
+                } else if (pu >= 0 && pu < ns && sh.src_kind[ps] == kSegI) {
                     const int sx = Ls.z - Ls.x, sy = Ls.w - Ls.y;
                     const int side = cross32(sx, sy, ul.x - Ls.x, ul.y - Ls.y);
                     dx = side > 0 ? -sy : sy;
@@ -1013,7 +1028,7 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
             ct = kConeEmpty;
             if (pg >= 0) {
                 int dx, dy;
-                arrival_from(ds, src_kind, src_seg, lat, pg, lat[g], dx, dy);
+                arrival_from(ds, sh.src_kind, sh.src_seg, lat, pg, lat[g], dx, dy);
                 const short4 w = wedge[g];
                 ct = make_cone(make_int4(w.x, w.y, w.z, w.w), dx, dy, c);
             }
@@ -1024,6 +1039,40 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
         ds.gen_ctype[g] = ct;
     }
     if (rank == 0 && tid == 0) ds.stats[0] = round;
+    cluster.sync();  // this scene's shared memory is no longer read
+    return true;
+}
+
+__global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
+    k_sssp_cluster(const __grid_constant__ DevScene ds, int max_rounds) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ ClShared sh;
+    cg::cluster_group cluster = cg::this_cluster();
+    bool solo_len;
+    if (solo_bytes(ds, solo_len) > 0) return;  // the single-CTA kernel handles this graph (every CTA agrees)
+    const bool done = cl_solve(ds, max_rounds, cluster, sh, sm_raw);
+    if (cluster.block_rank() == 0 && threadIdx.x == 0) ds.counters[4] = done ? 1 : 0;  // else the many-CTA kernel
+}
+
+// Batched form: resident clusters take the batch's scenes from a counter,
+// most generators first, each solving one scene's fixpoint at a time; a
+// scene one cluster cannot take is left to the many-CTA batched kernel.
+__global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
+    k_sssp_cluster_b(const __grid_constant__ BatchDev b) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ ClShared sh;
+    cg::cluster_group cluster = cg::this_cluster();
+    const bool lead = cluster.block_rank() == 0 && threadIdx.x == 0;
+    for (;;) {
+        if (lead) sh.next = atomicAdd(b.cl_counter, 1);
+        cluster.sync();
+        const int k = *cluster.map_shared_rank(&sh.next, 0);
+        cluster.sync();  // every CTA has read it before the next is taken
+        if (k >= b.n) break;
+        const int sc = b.cl_order[k];
+        const bool done = cl_solve(b.scenes[sc], b.max_rounds, cluster, sh, sm_raw);
+        if (lead) b.cl_done[sc] = done ? 1 : 0;
+    }
 }
 
 // Final generator table for the pixel phase: FP32 costs and shadow cones.
@@ -1151,6 +1200,7 @@ __global__ void __launch_bounds__(256) k_sssp_b(const __grid_constant__ BatchDev
     const int total = b.gen_off[b.n];
     for (int i = gtid; i < total; i += gsize) {
         const int s = scene_of(b.gen_off, b.n, i);
+        if (b.cl_done[s]) continue;  // a cluster solved this scene
         const DevScene &ds = b.scenes[s];
         const int g = i - b.gen_off[s];
         const bool src = g < ds.n_src;
@@ -1166,7 +1216,8 @@ __global__ void __launch_bounds__(256) k_sssp_b(const __grid_constant__ BatchDev
         const int s = scene_of(b.gen_off, b.n, i);
         const DevScene &ds = b.scenes[s];
         const int g = i - b.gen_off[s];
-        if (g < ds.n_src && ds.in_start[ds.n_vert] <= ds.edge_cap) mark_out_warp_b(ds, s, g, lane, b.dirtyl[0], &cnt[2]);
+        if (g < ds.n_src && !b.cl_done[s] && ds.in_start[ds.n_vert] <= ds.edge_cap)
+            mark_out_warp_b(ds, s, g, lane, b.dirtyl[0], &cnt[2]);
     }
     grid.sync();
     int round = 0;
@@ -1234,6 +1285,7 @@ __global__ void __launch_bounds__(256) k_sssp_b(const __grid_constant__ BatchDev
         grid.sync();
     }
     for (int s = gtid; s < b.n; s += gsize) {
+        if (b.cl_done[s]) continue;
         const DevScene &ds = b.scenes[s];
         ds.stats[0] = round + 1;
         if (cnt[4] < 0) atomicOr(ds.status, kStNotConverged);
@@ -1309,8 +1361,8 @@ int fixpoint_launches(const DevScene &ds) {
     const int nv = ds.n_vert;
     std::vector<int32_t> deg(nv > 0 ? nv : 1, 0);
     int32_t *d = nullptr;
-    bool ok = nv > 0 && ds.vis_static && cudaMalloc(&d, sizeof(int32_t) * nv) == cudaSuccess;
-    if (ok) {
+    bool ok = nv == 0 || (ds.vis_static && cudaMalloc(&d, sizeof(int32_t) * nv) == cudaSuccess);
+    if (ok && nv > 0) {
         k_row_bits<<<std::min((nv + 7) / 8, 152 * 8), 256>>>(ds.vis_static, nv, ds.vis_words, d);
         ok = cudaMemcpy(deg.data(), d, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost) == cudaSuccess;
     }
@@ -1329,7 +1381,8 @@ int fixpoint_launches(const DevScene &ds) {
     const bool solo_never = solo_bytes_for(ds.n_gen, nv, lo, ds.edge_cap, ds.solo_smem, wl) == 0;
     const bool solo_sure = solo_bytes_for(ds.n_gen, nv, hi, ds.edge_cap, ds.solo_smem, wl) > 0;
     const bool cluster_sure = (f & kFixCluster) && ds.n_gen < 32768 && hi <= ds.edge_cap &&
-                              cl_layout(ds.n_gen, nv, own_max).end <= (size_t)kClSmem;
+                              cl_layout(ds.n_gen, nv, own_max, false).end <= (size_t)kClSmem;
+    if (cluster_sure) f |= kFixClusterFits;
     if (solo_never) f &= ~kFixSolo;
     if (solo_sure) f = (f & ~kFixCluster) | kFixSoloSure;
     if (cluster_sure && !solo_sure) f |= kFixClusterSure;
@@ -1339,7 +1392,8 @@ int fixpoint_launches(const DevScene &ds) {
 // the cluster fixpoint's shared memory, granted once per process
 bool cluster_smem_ok() {
     static const bool ok = [] {
-        if (cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) != cudaSuccess) {
+        if (cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_sssp_cluster_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -1441,8 +1495,29 @@ void launch_vertex_phase_batched(const BatchDev &b, cudaStream_t st) {
     k_edges_fill_b<<<152 * 4, 256, 0, st>>>(b);
     BatchDev arg = b;
     void *args[] = {&arg};
-    cudaLaunchCooperativeKernel((const void *)k_sssp_b, dim3(b.sssp_blocks), dim3(kSsspThreads), args, 0, st);
+    if (b.cl_grid > 0) {  // the clusters first; the many-CTA kernel takes what they leave
+        cudaMemsetAsync(b.cl_counter, 0, sizeof(int32_t), st);
+        k_sssp_cluster_b<<<b.cl_grid, kClThreads, kClSmem, st>>>(b);
+    } else {
+        cudaMemsetAsync(b.cl_done, 0, sizeof(int32_t) * b.n, st);
+    }
+    if (!b.cl_all)
+        cudaLaunchCooperativeKernel((const void *)k_sssp_b, dim3(b.sssp_blocks), dim3(kSsspThreads), args, 0, st);
     k_finalize_b<<<152 * 4, 256, 0, st>>>(b);
+}
+
+int cluster_batched_grid() {
+    if (!cluster_smem_ok() || g_many_cta_override.load()) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClCtas);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = kClSmem;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_sssp_cluster_b, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return clusters * kClCtas;  // resident clusters only: they take scenes from a counter
 }
 
 }  // namespace spm

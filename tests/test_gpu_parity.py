@@ -346,6 +346,31 @@ def test_batched_matches_individual_computes(spm, oracle_mod, tuning):
     batch.close()
 
 
+def test_batched_fixpoint_kernels_agree(spm):
+    """A batch solves its scenes' vertex fixpoints on resident clusters, one
+    scene per cluster at a time; the many-CTA batched kernel (synchronous
+    rounds over every scene) is the fallback. Both give the same maps bit for
+    bit, for dense scenes and a deep maze."""
+    lib = spm.load_library()
+    scenes = sg.batched(6, n_scenes=8, sides=(128, 256), poly_range=(100, 400))
+    scenes.append(sg.maze(5, cells=6, N=192))
+    objs = [spm.Scene(sc) for sc in scenes]
+    outs = []
+    for many in (0, 1):
+        try:
+            lib.spm_debug_set_many_cta_fixpoint(many)
+            batch = spm.Batch(objs)
+        finally:
+            lib.spm_debug_set_many_cta_fixpoint(0)
+        res = batch.compute()
+        torch.cuda.synchronize()
+        outs.append([(d.cpu().numpy(), p.cpu().numpy()) for d, p in res])
+        batch.close()
+    for k in range(len(scenes)):
+        assert np.array_equal(outs[0][k][1], outs[1][k][1]), k
+        assert np.array_equal(outs[0][k][0].view(np.int32), outs[1][k][0].view(np.int32)), k
+
+
 def test_repeat_is_deterministic(spm):
     s = spm.Scene(sg.plain_polys(5, n_polys=100, N=512))
     d1, p1 = s.compute()
