@@ -393,7 +393,66 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
     spm::launch_free_mask(ds, nullptr, free_bits);
     if (vert_maps) spm::launch_vert_maps(ds, nullptr, vert_maps);
     spm::launch_vis_static(ds, nullptr, vis_static);  // after the local depth maps it filters with
-    ds.fix_launch = spm::fixpoint_launches(ds);
+    // the obstacle-vertex edges are fixed: kept as CSR (in-lists with their
+    // lengths, out-lists), so that a compute builds only the sources' edges
+    std::vector<int32_t> deg;
+    if (ok && hs.n_vert > 0) {
+        const int nv = hs.n_vert, ns = hs.n_src, words = ds.vis_words;
+        std::vector<uint32_t> bits((size_t)nv * words);
+        if (cudaMemcpy(bits.data(), vis_static, sizeof(uint32_t) * bits.size(), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            deg.assign(nv, 0);
+            std::vector<int32_t> start(nv + 1, 0), out_start(nv + 1, 0), out_init(hs.n_gen + 1, 0);
+            for (int vv = 0; vv < nv; ++vv) {
+                for (int w = 0; w < words; ++w) {
+                    uint32_t b = bits[(size_t)vv * words + w];
+                    while (b) {
+                        const int u = 32 * w + __builtin_ctz(b);
+                        b &= b - 1;
+                        if (u < ns) continue;  // no source columns are kept
+                        ++deg[vv];
+                        ++out_start[u - ns + 1];
+                    }
+                }
+                start[vv + 1] = start[vv] + deg[vv];
+            }
+            const long long E_s = start[nv];
+            if (E_s <= ds.edge_cap) {
+                for (int uu = 0; uu < nv; ++uu) {
+                    out_init[ns + uu + 1] = out_start[uu + 1];
+                    out_start[uu + 1] += out_start[uu];
+                }
+                std::vector<int32_t> src(E_s > 0 ? E_s : 1), dst(E_s > 0 ? E_s : 1), fill(out_start.begin(), out_start.end() - 1);
+                for (int vv = 0; vv < nv; ++vv) {
+                    int e = start[vv];
+                    for (int w = 0; w < words; ++w) {
+                        uint32_t b = bits[(size_t)vv * words + w];
+                        while (b) {
+                            const int u = 32 * w + __builtin_ctz(b);
+                            b &= b - 1;
+                            if (u < ns) continue;
+                            src[e++] = u;  // increasing generator order, as a compute lists a row
+                            dst[fill[u - ns]++] = ns + vv;
+                        }
+                    }
+                }
+                ds.st_start = dupload(s, start, ok);
+                ds.st_src = dupload(s, src, ok);
+                ds.st_out_start = dupload(s, out_start, ok);
+                ds.st_out_dst = dupload(s, dst, ok);
+                ds.st_out_init = dupload(s, out_init, ok);
+                double *len = dalloc<double>(s, E_s > 0 ? E_s : 1);
+                ok &= len != nullptr && !s->alloc_failed;
+                if (ok) spm::launch_static_lengths(ds, len, nullptr);
+                ds.st_len = len;
+            }
+        }
+    }
+    if (!ok || s->alloc_failed) {
+        free_all(s);
+        delete s;
+        return set_err(nullptr, SPM_ERR_OOM, "device allocation or upload failed");
+    }
+    ds.fix_launch = spm::fixpoint_launches(ds, deg);
     if (cudaPeekAtLastError() != cudaSuccess) {
         free_all(s);
         delete s;

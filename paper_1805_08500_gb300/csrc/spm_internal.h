@@ -119,6 +119,16 @@ struct DevScene {
     int32_t *out_start;                // n_gen + 1 (by source generator)
     int32_t *out_dst;                  // E
     int32_t *out_fill;                 // n_gen cursors
+    // the obstacle-vertex edges, fixed with the obstacles: in-lists with their
+    // FP64 lengths and out-lists, CSR over the obstacle vertices; a compute
+    // builds the sources' edges and copies these after them (null: every
+    // edge is built per compute)
+    const int32_t *st_start;           // n_vert + 1
+    const int32_t *st_src;             // generator ids, increasing within a row
+    const double *st_len;
+    const int32_t *st_out_start;       // n_vert + 1 (by obstacle vertex)
+    const int32_t *st_out_dst;
+    const int32_t *st_out_init;        // n_gen + 1: out_start before the sources' edges are counted
     int64_t edge_cap;
     double *cost[2];                   // Jacobi double buffer
     int32_t *par[2];
@@ -257,7 +267,10 @@ bool cluster_smem_ok();  // the cluster fixpoint can run (its shared memory was 
 // many-CTA kernel is not launched)
 constexpr int kFixSolo = 1, kFixCluster = 2, kFixSoloSure = 4, kFixClusterSure = 8;
 constexpr int kFixClusterFits = 16;  // the cluster kernel takes every compute's graph (batched form)
-int fixpoint_launches(const DevScene &ds);  // from the static edge count (synchronous; scene creation)
+// from the static in-degrees (scene creation)
+int fixpoint_launches(const DevScene &ds, const std::vector<int32_t> &deg);
+// FP64 lengths of the static in-lists (ds.st_start / st_src set), into len
+void launch_static_lengths(const DevScene &ds, double *len, cudaStream_t st);
 int cluster_batched_grid();  // CTAs of the batched cluster fixpoint's launch (0: unavailable)
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();

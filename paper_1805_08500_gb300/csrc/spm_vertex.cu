@@ -258,11 +258,20 @@ __global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant
 
 // In-degree per vertex row and out-degree per generator: one warp per row,
 // lanes over the row's words.
+// With the static lists only the source columns are scanned (their out-
+// degrees counted here; the obstacle vertices' come from st_out_init).
+__device__ __forceinline__ uint32_t src_word_mask(const DevScene &ds, int w) {
+    const int lo = ds.n_src - 32 * w;  // source columns in word w
+    return lo >= 32 ? 0xffffffffu : lo <= 0 ? 0u : (1u << lo) - 1u;
+}
 __device__ __forceinline__ void edges_count_row(const DevScene &ds, int vv, int lane) {
     const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
+    const bool st = ds.st_start != nullptr;
+    const int nw = st ? (ds.n_src + 31) / 32 : ds.vis_words;
     int cnt = 0;
-    for (int w = lane; w < ds.vis_words; w += 32) {
+    for (int w = lane; w < nw; w += 32) {
         uint32_t b = row[w];
+        if (st) b &= src_word_mask(ds, w);
         cnt += __popc(b);
         while (b) {
             const int bit = __ffs(b) - 1;
@@ -272,7 +281,7 @@ __device__ __forceinline__ void edges_count_row(const DevScene &ds, int vv, int 
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0) ds.in_start[vv + 1] = cnt;
+    if (lane == 0) ds.in_start[vv + 1] = cnt + (st ? ds.st_start[vv + 1] - ds.st_start[vv] : 0);
 }
 
 __global__ void k_edges_count(const __grid_constant__ DevScene ds) {
@@ -330,9 +339,12 @@ __device__ __forceinline__ void edges_fill_row(const DevScene &ds, int vv, int l
     const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
     int e0 = ds.in_start[vv];
     const int v = ds.n_src + vv;
-    for (int w0 = 0; w0 < ds.vis_words; w0 += 32) {
+    const bool st = ds.st_start != nullptr;
+    const int nw = st ? (ds.n_src + 31) / 32 : ds.vis_words;
+    for (int w0 = 0; w0 < nw; w0 += 32) {
         const int w = w0 + lane;
-        uint32_t b = w < ds.vis_words ? row[w] : 0u;
+        uint32_t b = w < nw ? row[w] : 0u;
+        if (st) b &= src_word_mask(ds, w);
         const int c = __popc(b);
         int inc = c;
 #pragma unroll
@@ -352,6 +364,19 @@ __device__ __forceinline__ void edges_fill_row(const DevScene &ds, int vv, int l
         }
         e0 += __shfl_sync(0xffffffffu, inc, 31);
     }
+    if (st) {  // then the row's obstacle-vertex edges, as kept
+        const int s0 = ds.st_start[vv], m = ds.st_start[vv + 1] - s0;
+        for (int j = lane; j < m; j += 32) {
+            ds.in_src[e0 + j] = ds.st_src[s0 + j];
+            ds.in_len[e0 + j] = ds.st_len[s0 + j];
+        }
+    }
+}
+
+// An obstacle vertex's out-list, as kept, at its place in this compute's CSR.
+__device__ __forceinline__ void edges_out_copy(const DevScene &ds, int uu, int lane) {
+    const int b = ds.out_start[ds.n_src + uu], s0 = ds.st_out_start[uu], m = ds.st_out_start[uu + 1] - s0;
+    for (int j = lane; j < m; j += 32) ds.out_dst[b + j] = ds.st_out_dst[s0 + j];
 }
 
 __global__ void k_edges_fill(const __grid_constant__ DevScene ds) {
@@ -359,6 +384,17 @@ __global__ void k_edges_fill(const __grid_constant__ DevScene ds) {
     const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
     for (int vv = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vv < ds.n_vert; vv += nw)
         edges_fill_row(ds, vv, lane);
+    if (ds.st_start)
+        for (int uu = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); uu < ds.n_vert; uu += nw)
+            edges_out_copy(ds, uu, lane);
+}
+
+// FP64 lengths of the kept in-lists: the same function as a compute's.
+__global__ void k_static_lengths(const __grid_constant__ DevScene ds, double *len) {
+    const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+    for (int vv = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vv < ds.n_vert; vv += nw)
+        for (int e = ds.st_start[vv] + lane; e < ds.st_start[vv + 1]; e += 32)
+            len[e] = edge_len(ds, ds.st_src[e], ds.n_src + vv);
 }
 
 // Jacobi rounds of the fixpoint on the whole GPU (cooperative launch, two
@@ -1124,7 +1160,7 @@ __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
             const int s = scene_of(b.gen_off, b.n, i);
             const DevScene &ds = b.scenes[s];
             const int g = i - b.gen_off[s];
-            ds.out_start[g + 1] = 0;
+            ds.out_start[g + 1] = ds.st_out_init ? ds.st_out_init[g + 1] : 0;
             ds.out_fill[g] = 0;
         } else {
             const DevScene &ds = b.scenes[i - total];
@@ -1165,6 +1201,7 @@ __global__ void k_edges_fill_b(const __grid_constant__ BatchDev b) {
         const DevScene &ds = b.scenes[s];
         if (ds.in_start[ds.n_vert] > ds.edge_cap) continue;
         edges_fill_row(ds, i - b.vert_off[s], lane);
+        if (ds.st_start) edges_out_copy(ds, i - b.vert_off[s], lane);  // vertex i's kept out-list
     }
 }
 
@@ -1338,36 +1375,15 @@ void launch_vis_static(const DevScene &ds, cudaStream_t st, uint32_t *vis_static
     launch_pairs(d, st);
 }
 
-namespace {
-// set bits of each row of a bit matrix (a warp per row)
-__global__ void k_row_bits(const uint32_t *bits, int rows, int words, int32_t *out) {
-    const int lane = threadIdx.x & 31;
-    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += (gridDim.x * blockDim.x) >> 5) {
-        int c = 0;
-        for (int w = lane; w < words; w += 32) c += __popc(bits[(size_t)r * words + w]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) out[r] = c;
-    }
-}
-}  // namespace
 
 // Which fixpoint kernels a compute launches. A vertex's in-edges are its
 // obstacle-vertex pairs in the scene's static bits, fixed, plus at most one
 // from each source; those bounds decide, per kernel, whether it surely takes
 // every compute's graph, surely takes none, or has to see the graph.
-int fixpoint_launches(const DevScene &ds) {
+int fixpoint_launches(const DevScene &ds, const std::vector<int32_t> &deg) {
     int f = (ds.solo_smem > 0 ? kFixSolo : 0) | (cluster_smem_ok() ? kFixCluster : 0);
     const int nv = ds.n_vert;
-    std::vector<int32_t> deg(nv > 0 ? nv : 1, 0);
-    int32_t *d = nullptr;
-    bool ok = nv == 0 || (ds.vis_static && cudaMalloc(&d, sizeof(int32_t) * nv) == cudaSuccess);
-    if (ok && nv > 0) {
-        k_row_bits<<<std::min((nv + 7) / 8, 152 * 8), 256>>>(ds.vis_static, nv, ds.vis_words, d);
-        ok = cudaMemcpy(deg.data(), d, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost) == cudaSuccess;
-    }
-    if (d) cudaFree(d);
-    if (!ok) return f;  // unknown: the kernels decide on the device
+    if ((int)deg.size() < nv) return f;  // unknown: the kernels decide on the device
     long long lo = 0, own_max = 0;
     for (int r = 0; r < kClCtas; ++r) {
         long long own = 0;
@@ -1387,6 +1403,10 @@ int fixpoint_launches(const DevScene &ds) {
     if (solo_sure) f = (f & ~kFixCluster) | kFixSoloSure;
     if (cluster_sure && !solo_sure) f |= kFixClusterSure;
     return f;
+}
+
+void launch_static_lengths(const DevScene &ds, double *len, cudaStream_t st) {
+    if (ds.n_vert > 0) k_static_lengths<<<std::min((ds.n_vert + 7) / 8, 152 * 8), 256, 0, st>>>(ds, len);
 }
 
 // the cluster fixpoint's shared memory, granted once per process
@@ -1412,7 +1432,10 @@ bool cluster_smem_ok() {
 }
 
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
-    cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
+    if (ds.st_out_init)  // the obstacle vertices' out-degrees are kept; the sources' are counted
+        cudaMemcpyAsync(ds.out_start, ds.st_out_init, sizeof(int32_t) * (ds.n_gen + 1), cudaMemcpyDeviceToDevice, st);
+    else
+        cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
     cudaMemsetAsync(ds.out_fill, 0, sizeof(int32_t) * ds.n_gen, st);
     if (ds.n_vert > 0) {
         const size_t bytes = sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words;
