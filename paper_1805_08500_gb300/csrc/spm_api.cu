@@ -827,7 +827,7 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     b->scenes.assign(scenes, scenes + n);
     b->device = dev;
     std::vector<spm::DevScene> descs(n);
-    std::vector<long long> pair_off(n + 1, 0), bits_off(n + 1, 0), src_map_off(n + 1, 0), src_ins_off(n + 1, 0),
+    std::vector<long long> pair_off(n + 1, 0), src_map_off(n + 1, 0), src_ins_off(n + 1, 0),
         src_tile_off(n + 1, 0);
     std::vector<int32_t> vert_off(n + 1, 0), gen_off(n + 1, 0), order(n), tile_off(n + 1, 0), flood_off(n + 1, 0);
     std::vector<float *> dv(dist, dist + n);
@@ -857,15 +857,19 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
         flood_off[k + 1] =
             flood_off[k] + (floods && !direct ? (d.flood_reuse ? d.n_src : d.n_gen) : 0);
         pair_off[k + 1] = pair_off[k] + (long long)descs[k].n_vert * descs[k].pair_words;
-        bits_off[k + 1] = bits_off[k] + (long long)descs[k].n_vert * descs[k].vis_words;
         vert_off[k + 1] = vert_off[k] + descs[k].n_vert;
         gen_off[k + 1] = gen_off[k] + descs[k].n_gen;
         max_gen = std::max(max_gen, descs[k].n_gen);
         order[k] = k;
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        return (long long)descs[a].tiles_x * descs[a].tiles_y > (long long)descs[c].tiles_x * descs[c].tiles_y;
-    });
+    // the pixel pass takes tiles in this order: the costliest tiles first, so
+    // that the kernel's tail is short. A tile's candidates grow with the
+    // generators and with the share of the scene the tile covers: estimate
+    // its cost by n_gen / sqrt(tiles)
+    auto tile_cost = [&](int k) {
+        return (double)descs[k].n_gen / std::sqrt((double)std::max(1, descs[k].tiles_x * descs[k].tiles_y));
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return tile_cost(a) > tile_cost(c); });
     for (int k = 0; k < n; ++k)
         tile_off[k + 1] = tile_off[k] + descs[order[k]].tiles_x * descs[order[k]].tiles_y;
     bool ok = true;
@@ -873,7 +877,6 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     bd.n = n;
     bd.scenes = bupload(b, descs, ok);
     bd.pair_off = bupload(b, pair_off, ok);
-    bd.bits_off = bupload(b, bits_off, ok);
     bd.vert_off = bupload(b, vert_off, ok);
     bd.gen_off = bupload(b, gen_off, ok);
     bd.flood_off = bupload(b, flood_off, ok);

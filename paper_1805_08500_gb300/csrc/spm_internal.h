@@ -189,11 +189,10 @@ struct BatchDev {
     const DevScene *scenes;            // n descriptors (device memory)
     // prefix offsets over scenes (n + 1 entries each)
     const long long *pair_off;         // warp tasks of the visibility pairs: n_vert * pair_words
-    const long long *bits_off;         // words of the visibility bit matrices: n_vert * vis_words
     const int32_t *vert_off;           // obstacle-vertex generators
     const int32_t *gen_off;            // generators
     const int32_t *flood_off;          // generators the batched flood takes per scene (sources only when reusing)
-    // pixel pass: scenes in processing order (most tiles first)
+    // pixel pass: scenes in processing order (costliest tiles first)
     const int32_t *order;              // n scene indices
     const int32_t *tile_off;           // n + 1 prefix of tiles in that order
     int32_t total_tiles;

@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(NT, PX == 4 ? SPM_PIX32_MINB : SPM_PIX16_MINB)
 }
 
 // Persistent form over a batch of scenes: each CTA takes the next
-// (scene, tile) from a global counter (scenes ordered largest first), copies
+// (scene, tile) from a global counter (costliest tiles first), copies
 // that scene's descriptor into shared memory and runs the same tile code.
 template <bool ANY_MAPS>  // some scene of the batch uses depth maps
 __global__ void __launch_bounds__(NT, SPM_PIXB_MINB) k_pixels_batched(const __grid_constant__ BatchDev b) {

@@ -1144,12 +1144,16 @@ __device__ __forceinline__ int scene_of(const T *off, int n, T x) {
 }
 
 __global__ void k_prepare_b(const __grid_constant__ BatchDev b) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.bits_off[b.n];
-         i += (long long)gridDim.x * blockDim.x) {  // every scene's bit matrix: its static part, or zero
-        const int s = scene_of(b.bits_off, b.n, i);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.vert_off[b.n]; i += gridDim.x * blockDim.x) {
+        // every scene's bit matrix, a row per thread: with kept edge lists
+        // only the source columns are read, and they start empty; else the
+        // row's static part
+        const int s = scene_of(b.vert_off, b.n, i);
         const DevScene &ds = b.scenes[s];
-        const long long k = i - b.bits_off[s];
-        ds.vis_bits[k] = ds.vis_static ? ds.vis_static[k] : 0u;
+        uint32_t *row = ds.vis_bits + (size_t)(i - b.vert_off[s]) * ds.vis_words;
+        const uint32_t *srow = ds.vis_static ? ds.vis_static + (size_t)(i - b.vert_off[s]) * ds.vis_words : nullptr;
+        const int nw = ds.st_start ? (ds.n_src + 31) / 32 : ds.vis_words;
+        for (int w = 0; w < nw; ++w) row[w] = srow && !ds.st_start ? srow[w] : 0u;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         *reinterpret_cast<unsigned long long *>(b.counters + 6) = 0ull;  // visibility-pair work counter
@@ -1441,7 +1445,10 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
         const size_t bytes = sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words;
         // the obstacle-vertex pairs come from the scene's static bits; the
         // pair kernel then tests the source columns only
-        if (ds.vis_static) cudaMemcpyAsync(ds.vis_bits, ds.vis_static, bytes, cudaMemcpyDeviceToDevice, st);
+        if (ds.st_start)  // kept edge lists: only the source columns are read, and they start empty
+            cudaMemset2DAsync(ds.vis_bits, sizeof(uint32_t) * ds.vis_words, 0, sizeof(uint32_t) * ((ds.n_src + 31) / 32),
+                              ds.n_vert, st);
+        else if (ds.vis_static) cudaMemcpyAsync(ds.vis_bits, ds.vis_static, bytes, cudaMemcpyDeviceToDevice, st);
         else cudaMemsetAsync(ds.vis_bits, 0, bytes, st);
         launch_pairs(ds, st);
         const int eb = (ds.n_vert + 7) / 8;  // one warp per row
