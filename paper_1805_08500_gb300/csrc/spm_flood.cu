@@ -103,9 +103,11 @@ struct FloodSmem {
 };
 
 // Is the closed box hidden from g (lattice point, not inside the box) by the
-// depth map? One warp: the lanes test 32 of the spanned bins at a time (a
-// tile near g spans hundreds of bins).
-__device__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int lane, int stride = 1) {
+// depth map? A group of G lanes (lane gl of mask gmask) tests G of the
+// spanned bins at a time (a tile near g spans hundreds of bins, a far one a
+// few).
+template <int G>
+__device__ bool box_hidden_ang(const float *depth2, int2 g, int4 box, int gl, unsigned gmask, int stride) {
     const long long dx = max(max(box.x - g.x, g.x - box.z), 0), dy = max(max(box.y - g.y, g.y - box.w), 0);
     const float mind2 = (float)(dx * dx + dy * dy) * (1.f - 1e-6f);
     const float c0 = pang(0.5f * (float)(box.x + box.z) - (float)g.x, 0.5f * (float)(box.y + box.w) - (float)g.y);
@@ -118,12 +120,15 @@ __device__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int l
         hi = fmaxf(hi, d);
     }
     const int k0 = (int)floorf((c0 + lo - kAngEps) / kAngW), k1 = (int)floorf((c0 + hi + kAngEps) / kAngW);
-    for (int k = k0; k <= k1; k += 32) {
-        const int kk = k + lane;
+    for (int k = k0; k <= k1; k += G) {
+        const int kk = k + gl;
         const bool h = kk > k1 || depth2[stride * ((kk + 2 * kAng) & (kAng - 1))] <= mind2;
-        if (!__all_sync(0xffffffffu, h)) return false;
+        if (!__all_sync(gmask, h)) return false;
     }
     return true;
+}
+__device__ __forceinline__ bool box_hidden_ang_warp(const float *depth2, int2 g, int4 box, int lane, int stride = 1) {
+    return box_hidden_ang<32>(depth2, g, box, lane, 0xffffffffu, stride);
 }
 
 // One warp inserts polygon q's front-facing edges into the depth map, the
@@ -407,8 +412,9 @@ __device__ __forceinline__ void src_insert(const DevScene &ds, int g, int q, int
     insert_polygon_warp<MAPS>(ds, mp, mp + 1, ds.gen_lat[g], q, lane, plen, 2);
 }
 
+constexpr int kSrcGrp = 8;  // lanes per (source, tile) test: most tiles span few bins
 template <bool MAPS>
-__device__ __forceinline__ void src_tile(const DevScene &ds, int g, int t, int lane) {
+__device__ __forceinline__ void src_tile(const DevScene &ds, int g, int t, int lane, unsigned gmask) {
     if (!src_on_grid(ds, g)) {  // segment interiors and sources off the grid: every tile scans them
         if (t == 0 && lane == 0) push_global(ds, g);
         return;
@@ -418,7 +424,7 @@ __device__ __forceinline__ void src_tile(const DevScene &ds, int g, int t, int l
     const bool inside = gl.x >= area.x && gl.x <= area.z && gl.y >= area.y && gl.y <= area.w;
     const float *mp = reinterpret_cast<const float *>(ds.gen_maps + (size_t)g * kAng);
     if (MAPS && t == 0 && lane == 0) ds.gen_map_ok[g] = 1;  // complete: the pixel pass may read it
-    if (!inside && box_hidden_ang_warp(mp, gl, area, lane, 2)) return;
+    if (!inside && box_hidden_ang<kSrcGrp>(mp, gl, area, lane, gmask, 2)) return;
     if (lane == 0) {
         const int slot = atomicAdd(&ds.flood_counts[0], 1);
         if (slot < ds.pair_cap) {
@@ -442,13 +448,19 @@ __global__ void k_src_insert(DevScene ds) {
         src_insert<MAPS>(ds, (int)(w / ds.n_poly), (int)(w % ds.n_poly), threadIdx.x & 31);
 }
 
+// group of kSrcGrp lanes of the calling thread's warp
+__device__ __forceinline__ unsigned src_group_mask() {
+    return ((1u << kSrcGrp) - 1u) << ((threadIdx.x & 31) & ~(kSrcGrp - 1));
+}
+
 template <bool MAPS>
 __global__ void k_src_tiles(DevScene ds) {
     const int ntiles = ds.tiles_x * ds.tiles_y;
     const long long n = (long long)ds.n_src * ntiles;
-    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < n;
-         w += (gridDim.x * (long long)blockDim.x) >> 5)
-        src_tile<MAPS>(ds, (int)(w / ntiles), (int)(w % ntiles), threadIdx.x & 31);
+    const unsigned gmask = src_group_mask();
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / kSrcGrp; w < n;
+         w += (gridDim.x * (long long)blockDim.x) / kSrcGrp)
+        src_tile<MAPS>(ds, (int)(w / ntiles), (int)(w % ntiles), threadIdx.x % kSrcGrp, gmask);
 }
 
 // Automatic mode: flood only sparse visibility graphs (mazes); a dense one
@@ -580,15 +592,16 @@ __global__ void k_src_insert_b(const __grid_constant__ BatchDev b) {
 template <bool ANY_MAPS>
 __global__ void k_src_tiles_b(const __grid_constant__ BatchDev b) {
     const long long n = b.src_tile_off[b.n];
-    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < n;
-         w += (gridDim.x * (long long)blockDim.x) >> 5) {
+    const unsigned gmask = src_group_mask();
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / kSrcGrp; w < n;
+         w += (gridDim.x * (long long)blockDim.x) / kSrcGrp) {
         const int sc = scene_of_b(b.src_tile_off, b.n, w);
         const DevScene &ds = b.scenes[sc];
         const int ntiles = ds.tiles_x * ds.tiles_y;
         const long long e = w - b.src_tile_off[sc];
         const int g = (int)(e / ntiles), t = (int)(e % ntiles);
-        if (ANY_MAPS && ds.use_maps) src_tile<true>(ds, g, t, threadIdx.x & 31);
-        else src_tile<false>(ds, g, t, threadIdx.x & 31);
+        if (ANY_MAPS && ds.use_maps) src_tile<true>(ds, g, t, threadIdx.x % kSrcGrp, gmask);
+        else src_tile<false>(ds, g, t, threadIdx.x % kSrcGrp, gmask);
     }
 }
 
@@ -694,8 +707,9 @@ void launch_flood(const DevScene &ds, cudaStream_t st, FloodStatic how) {
                 if (maps) k_src_insert<true><<<wblocks((long long)ds.n_src * ds.n_poly), 256, 0, st>>>(ds);
                 else k_src_insert<false><<<wblocks((long long)ds.n_src * ds.n_poly), 256, 0, st>>>(ds);
             }
-            if (maps) k_src_tiles<true><<<wblocks((long long)ds.n_src * ntiles), 256, 0, st>>>(ds);
-            else k_src_tiles<false><<<wblocks((long long)ds.n_src * ntiles), 256, 0, st>>>(ds);
+            const long long tgroups = ((long long)ds.n_src * ntiles + 3) / 4;  // warps of four tests
+            if (maps) k_src_tiles<true><<<wblocks(tgroups), 256, 0, st>>>(ds);
+            else k_src_tiles<false><<<wblocks(tgroups), 256, 0, st>>>(ds);
         } else {
             k_flood_static<<<sblocks, 256, 0, st>>>(ds, 0);
             flood(0, ds.n_src);
@@ -730,9 +744,9 @@ void launch_flood_batched(const BatchDev &b, cudaStream_t st, long long src_ins,
         if (b.any_maps) k_src_insert_b<true><<<wblocks(src_ins), 256, 0, st>>>(b);
         else k_src_insert_b<false><<<wblocks(src_ins), 256, 0, st>>>(b);
     }
-    if (src_tiles > 0) {
-        if (b.any_maps) k_src_tiles_b<true><<<wblocks(src_tiles), 256, 0, st>>>(b);
-        else k_src_tiles_b<false><<<wblocks(src_tiles), 256, 0, st>>>(b);
+    if (src_tiles > 0) {  // four tests per warp
+        if (b.any_maps) k_src_tiles_b<true><<<wblocks((src_tiles + 3) / 4), 256, 0, st>>>(b);
+        else k_src_tiles_b<false><<<wblocks((src_tiles + 3) / 4), 256, 0, st>>>(b);
     }
     k_tiles_scan_b<<<b.n, 1024, 0, st>>>(b);
     k_tiles_fill_b<<<dim3(16, b.n), 256, 0, st>>>(b);

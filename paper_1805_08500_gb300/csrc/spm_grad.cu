@@ -39,11 +39,21 @@ __global__ void __launch_bounds__(1024) k_loss(const int32_t *agents, int n, int
                                                const float *dist, float *loss) {
     __shared__ double part[1024];
     double s = 0.0;
-    for (int a = threadIdx.x; a < n; a += blockDim.x) {
-        const int i = agents[2 * a], j = agents[2 * a + 1];
-        if (i < 0 || j < 0 || i >= Nx || j >= Ny) continue;
-        const float d = dist[(size_t)j * Nx + i];
-        if (d < INFINITY) s += (double)d;
+    // each thread sums its agents a = tid, tid + blockDim, ... in that order;
+    // kU of them at a time, their loads issued together (random gathers)
+    constexpr int kU = 8;
+    for (int a0 = threadIdx.x; a0 < n; a0 += kU * blockDim.x) {
+        float d[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int a = a0 + u * blockDim.x;
+            const int i = a < n ? agents[2 * a] : -1, j = a < n ? agents[2 * a + 1] : -1;
+            const bool in = i >= 0 && j >= 0 && i < Nx && j < Ny;
+            d[u] = in ? dist[(size_t)j * Nx + i] : INFINITY;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (d[u] < INFINITY) s += (double)d[u];
     }
     part[threadIdx.x] = s;
     __syncthreads();
