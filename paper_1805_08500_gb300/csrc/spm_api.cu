@@ -31,6 +31,7 @@ struct spm_scene {
     int32_t *root = nullptr;
     float2 *lastpt = nullptr;
     double *grad_partial = nullptr;
+    double *loss_partial = nullptr;  // the forward loss's chunk sums
     // phase timing events (vertex start, pixel start, end)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_valid = false;
@@ -379,6 +380,7 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         s->root = dalloc<int32_t>(s, hs.n_gen);
         s->lastpt = dalloc<float2>(s, hs.n_gen);
         s->grad_partial = dalloc<double>(s, (size_t)std::max(n_out, 1) * spm::grad_chunks(n_out));
+        s->loss_partial = dalloc<double>(s, spm::kLossPartials);
     }
     ds.sssp_blocks = spm::sssp_grid_blocks();
     ds.solo_smem = spm::solo_smem_bytes();
@@ -1275,7 +1277,7 @@ spm_status spm_agents_forward(spm_scene *s, void *stream, const int32_t *agents_
     spm_status st = check_device(s);
     if (st != SPM_OK) return st;
     const cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    spm::launch_agents_forward(s->ds, cs, agents_dev, n, dist_dev, loss_dev);
+    spm::launch_agents_forward(s->ds, cs, agents_dev, n, dist_dev, loss_dev, s->loss_partial);
     if (tape_dev) {
         unsigned char *t = static_cast<unsigned char *>(tape_dev);
         spm::launch_agents_contrib(s->ds, cs, agents_dev, n, parent_dev, s->root, s->lastpt,

@@ -12,6 +12,8 @@
 // All reductions run in a fixed order in FP64, so results are deterministic.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "spm_device.cuh"
@@ -35,19 +37,21 @@ __global__ void k_root_table(DevScene ds, int32_t *root, float2 *lastpt) {
     }
 }
 
-__global__ void __launch_bounds__(1024) k_loss(const int32_t *agents, int n, int Nx, int Ny,
-                                               const float *dist, float *loss) {
-    __shared__ double part[1024];
+// The loss, mean agent distance (FP64 sum, fixed order): chunk c of the
+// agents is summed by CTA c (each thread its agents a, a + blockDim, ...,
+// eight gathers in flight, then a fixed tree), then the chunks in order.
+__global__ void __launch_bounds__(256) k_loss_partial(const int32_t *agents, int n, int Nx, int Ny, const float *dist,
+                                                      double *partial) {
+    __shared__ double part[256];
+    const int per = (n + gridDim.x - 1) / gridDim.x, a_lo = blockIdx.x * per, a_hi = min(n, a_lo + per);
     double s = 0.0;
-    // each thread sums its agents a = tid, tid + blockDim, ... in that order;
-    // kU of them at a time, their loads issued together (random gathers)
     constexpr int kU = 8;
-    for (int a0 = threadIdx.x; a0 < n; a0 += kU * blockDim.x) {
+    for (int a0 = a_lo + threadIdx.x; a0 < a_hi; a0 += kU * blockDim.x) {
         float d[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int a = a0 + u * blockDim.x;
-            const int i = a < n ? agents[2 * a] : -1, j = a < n ? agents[2 * a + 1] : -1;
+            const int i = a < a_hi ? agents[2 * a] : -1, j = a < a_hi ? agents[2 * a + 1] : -1;
             const bool in = i >= 0 && j >= 0 && i < Nx && j < Ny;
             d[u] = in ? dist[(size_t)j * Nx + i] : INFINITY;
         }
@@ -61,7 +65,14 @@ __global__ void __launch_bounds__(1024) k_loss(const int32_t *agents, int n, int
         if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *loss = (float)(part[0] / (double)max(n, 1));
+    if (threadIdx.x == 0) partial[blockIdx.x] = part[0];
+}
+
+__global__ void k_loss_final(const double *partial, int chunks, int n, float *loss) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += partial[c];
+    *loss = (float)(s / (double)max(n, 1));
 }
 
 // Per-agent contribution: output slot base and up to four values.
@@ -151,8 +162,10 @@ __global__ void k_agent_final(const double *partial, int chunks, int n, int n_ou
 int grad_chunks(int n_out) { return n_out <= 0 ? 1 : max(1, min(64, kGradPartials / n_out)); }
 
 void launch_agents_forward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
-                           const float *dist, float *loss) {
-    k_loss<<<1, 1024, 0, st>>>(agents, n, ds.Nx, ds.Ny, dist, loss);
+                           const float *dist, float *loss, double *partial) {
+    const int chunks = std::max(1, std::min(kLossPartials, (n + 2047) / 2048));
+    k_loss_partial<<<chunks, 256, 0, st>>>(agents, n, ds.Nx, ds.Ny, dist, partial);
+    k_loss_final<<<1, 32, 0, st>>>(partial, chunks, n, loss);
 }
 
 void launch_agents_contrib(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,

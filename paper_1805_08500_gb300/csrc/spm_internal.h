@@ -278,8 +278,9 @@ int count_kernel_launches_pixel();
 // their deterministic two-level reduction into the gradient
 constexpr int kGradPartials = 65536;  // partial sums of the reduction (chunks x components)
 int grad_chunks(int n_out);
+constexpr int kLossPartials = 64;  // partial sums of the loss (scratch doubles)
 void launch_agents_forward(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n, const float *dist,
-                           float *loss);
+                           float *loss, double *partial);
 void launch_agents_contrib(const DevScene &ds, cudaStream_t st, const int32_t *agents, int n,
                            const int32_t *parent, int32_t *root, float2 *lastpt, int32_t *slot, float4 *val);
 void launch_agents_reduce(int n_pts, int n_seg, cudaStream_t st, const int32_t *slot, const float4 *val, int n,
