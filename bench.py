@@ -37,14 +37,19 @@ FALLBACK_HBM_GBS = 6800.0
 # FP32 lanes per SM x SMs x 2 flops per FMA; clock from the measured peaks file
 FP32_LANES, N_SMS = 128, 152
 FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
-# One k_pixels launch on the 4096^2 maze, from a single-pass ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, smsp__issue_active and the
-# ALU / FMA pipe shares) and from the instrumentation build's work counters
-# (orientation tests and exact polygon tests per pixel); valid for that
-# workload and that kernel version only (re-captured after a change).
-KPIXELS_TRAFFIC = {"maze4096": 102_310_000}
-KPIXELS_UTIL = {"maze4096": {"issue_frac": 0.440, "alu_pipe_frac": 0.304, "fma_pipe_frac": 0.128,
-                             "orient_per_px": 0.254, "exact_tests_per_px": 0.0636}}
+# One pixel-kernel launch per workload, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, smsp__issue_active and the ALU / FMA pipe shares;
+# single-pass captures of a full-size launch for the maze and the batch, the
+# full-section capture for the polygon scene) and from the instrumentation
+# build's work counters (orientation tests and exact polygon tests per
+# pixel); valid for those workloads and that kernel version only
+# (re-captured after a change).
+KPIXELS_TRAFFIC = {"maze4096": 104_104_960, "batched256": 1_309_082_368, "polys1024": 12_415_488}
+KPIXELS_UTIL = {"maze4096": {"issue_frac": 0.444, "alu_pipe_frac": 0.311, "fma_pipe_frac": 0.128,
+                             "orient_per_px": 0.254, "exact_tests_per_px": 0.0636},
+                "batched256": {"issue_frac": 0.416, "alu_pipe_frac": 0.289, "fma_pipe_frac": 0.123},
+                "polys1024": {"issue_frac": 0.460, "alu_pipe_frac": 0.307, "fma_pipe_frac": 0.110,
+                              "orient_per_px": 0.360, "exact_tests_per_px": 0.0611}}
 
 
 def workload(name: str):
@@ -414,10 +419,13 @@ def run_batched(args, cfg_desc, scenes):
             "mpixel_per_s": npx_all / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
             "phases_ms": {"vertex_and_lists": vert_ms, "pixel": pix_ms},
             "roofline": {"bound": "alu", "kernel": "k_pixels_batched", "achieved": achieved, "peak": peak_tflops,
-                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": KPIXELS_TRAFFIC.get("batched256"), **KPIXELS_UTIL.get("batched256", {}),
                          "note": f"algorithmic = {FLOPS_PER_PIXEL} FP32 flops/pixel (winning distance) over the "
                                  f"persistent pixel kernel's event-timed duration; peak = FP32 lanes x SMs x 2 x max "
-                                 f"SM clock ({peak_src})"},
+                                 f"SM clock ({peak_src}); issue_frac and the pipe shares: ncu on one launch; "
+                                 f"traffic above the 8 B/pixel writes is the scenes' depth maps (several GB "
+                                 f"for 256 scenes, beyond L2) read bin by bin"},
             "hbm_write": {"achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": write_gbs / hbm_peak,
                           "bytes_per_pixel": 8, "peak_source": peak_src},
             "e2e": {"value": len(all_scenes) / e2e_s, "unit": "scenes/s",
