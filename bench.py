@@ -52,6 +52,17 @@ KPIXELS_UTIL = {"maze4096": {"issue_frac": 0.444, "alu_pipe_frac": 0.311, "fma_p
                               "orient_per_px": 0.360, "exact_tests_per_px": 0.0611}}
 
 
+def fixpoint_start(spm, s, args, tuning):
+    """--fixpoint-start: where the vertex fixpoint starts (auto, sources, or
+    the tree of the scene's table of obstacle-vertex geodesic distances), for
+    A/B runs; returns the tuning as the scene now holds it."""
+    choice = {"auto": 0, "sources": 1, "tree": 2}[getattr(args, "fixpoint_start", "auto")]
+    if choice:
+        spm.spm_scene_set_tuning(s.handle, tuning["flood_mode"], tuning["hidden_chunk"], tuning["tile"],
+                                 tuning["maps"], fixpoint_start=choice)
+    return dict(tuning, **s.tuning())
+
+
 def workload(name: str):
     if name == "maze4096":
         return sg.maze(0), "maze 64x64 cells, 4096^2 px, 16384^2 world, 1 segment + 4 points"
@@ -543,6 +554,7 @@ def run_differentiable(args, cfg_desc, scene):
     dev = torch.device("cuda", local)
     s = spm.Scene(scene)
     tuning = s.autotune(cache_key="diff2048_grad")  # set-up, not timed
+    tuning = fixpoint_start(spm, s, args, tuning)
     agents = torch.tensor(np.asarray(scene.agents, np.int32), device=dev)
     n_p, n_s = len(scene.points), len(scene.segs)
     d_out, p_out = s.empty_outputs()
@@ -623,6 +635,7 @@ def run_differentiable(args, cfg_desc, scene):
             "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
             "phases_ms": {"vertex": float(np.mean([p[0] for p in phases])),
                           "cull": float(np.mean([p[1] for p in phases])), "pixel": pix_ms},
+            "fixpoint_rounds": s.info()["rounds"],
             "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
                          "note": f"the forward's map: algorithmic = {FLOPS_PER_PIXEL} FP32 flops/pixel (winning "
@@ -811,6 +824,8 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=40_000,
                     help="oracle pixel sample per step for --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fixpoint-start", default="auto", choices=["auto", "sources", "tree"],
+                    help="where the vertex fixpoint starts (A/B of the warm start)")
     ap.add_argument("--culling", default="autotune", choices=["autotune", "flood", "scan", "auto"],
                     help="culling mode: autotuned at set-up (default) or fixed")
     args = ap.parse_args()
@@ -854,13 +869,14 @@ def main():
     else:
         spm.spm_scene_set_tuning(s.handle, {"auto": 0, "flood": 1, "scan": 2}[args.culling], 32)
         tuning = dict(s.tuning(), source="fixed")
+    tuning = fixpoint_start(spm, s, args, tuning)
     # cold start: a fresh scene with the chosen tuning, created and computed once
     # (scene creation, the obstacles' static structures and the first map)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s_cold = spm.Scene(scene)
     spm.spm_scene_set_tuning(s_cold.handle, tuning["flood_mode"], tuning["hidden_chunk"], tuning["tile"],
-                             tuning["maps"])
+                             tuning["maps"], tuning.get("fixpoint_start", 0))
     s_cold.compute()
     s_cold.sync()
     cold_ms = (time.perf_counter() - t0) * 1e3
@@ -949,11 +965,12 @@ def main():
                    "tuning": tuning,
                    "parallelism": f"replicas x{world}"},
         "phases_ms": {"vertex": vert_ms, "cull": cull_ms, "pixel": pix_ms},
+        "fixpoint_rounds": s.info()["rounds"],
         "setup_ms": {"scene_create": create_ms, "cold_create_and_first_compute": cold_ms,
                      "note": "host wall clock, outside the timed steps: validation, lattice, device "
                              "upload and the obstacles' static structures (free-space mask, vertex depth "
-                             "maps, obstacle-vertex visibility; the obstacle vertices' flood at the first "
-                             "compute)"},
+                             "maps, obstacle-vertex visibility and edges, the table of geodesic distances "
+                             "between obstacle vertices; the obstacle vertices' flood at the first compute)"},
         "roofline": {"bound": "alu", "kernel": "k_pixels", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": KPIXELS_TRAFFIC.get(args.workload),

@@ -332,13 +332,27 @@ spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *cull_ms
  *   pixel pass decides most pixels' visibility from it (exact bounds; only
  *   the undecided pixels take the exact polygon test), 0 = every pixel takes
  *   the exact test (default). Only with a flood (flood_mode != 2) and when
- *   the maps fit (n_gen x 16 KB <= 256 MB). */
+ *   the maps fit (n_gen x 16 KB <= 256 MB).
+ * fixpoint_start: where the vertex fixpoint (Sec. 3.1, Procedures 1 and 4)
+ *   starts. A scene with 256 to 6144 obstacle vertices and at most 7168
+ *   generators whose graph a single fixpoint kernel takes gets, from
+ *   spm_scene_create, a table of the geodesic distances between its obstacle
+ *   vertices (obstacles never move; n_vert^2 doubles of device memory). 2 =
+ *   start from the shortest-path tree that table gives (four extra kernels
+ *   per compute); 1 = start from the sources alone; 0 = automatic (default):
+ *   the tree when the scene has the table and its trees are deep (the table
+ *   build's deepest search took 32 rounds or more, as in mazes), else the
+ *   sources. Every choice reaches the same unique fixpoint, bit for bit; the
+ *   tree saves the rounds a start from the sources spends carrying costs
+ *   down long chains of links. Ignored by the batched form, which always
+ *   starts from the sources. */
 typedef struct {
     int32_t flood_mode;
     int32_t hidden_chunk;
     int32_t tile;
     int32_t maps;
-    int32_t reserved[4];
+    int32_t fixpoint_start;
+    int32_t reserved[3];
 } spm_tuning;
 
 spm_status spm_scene_get_tuning(const spm_scene *scene, spm_tuning *out);

@@ -46,7 +46,8 @@ class SpmError(RuntimeError):
 
 class SpmTuning(ctypes.Structure):
     _fields_ = [("flood_mode", ctypes.c_int32), ("hidden_chunk", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("maps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("tile", ctypes.c_int32), ("maps", ctypes.c_int32), ("fixpoint_start", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Desc(ctypes.Structure):
@@ -330,11 +331,14 @@ def spm_extract_path(handle, x, y, cap=4096):
 def spm_scene_get_tuning(handle):
     t = SpmTuning()
     _check(load_library().spm_scene_get_tuning(handle, ctypes.byref(t)), "spm_scene_get_tuning", handle)
-    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk, "tile": t.tile, "maps": t.maps}
+    return {"flood_mode": t.flood_mode, "hidden_chunk": t.hidden_chunk, "tile": t.tile, "maps": t.maps,
+            "fixpoint_start": t.fixpoint_start}
 
 
-def spm_scene_set_tuning(handle, flood_mode, hidden_chunk, tile=0, maps=0):
-    t = SpmTuning(int(flood_mode), int(hidden_chunk), int(tile), int(maps))
+def spm_scene_set_tuning(handle, flood_mode, hidden_chunk, tile=0, maps=0, fixpoint_start=0):
+    """fixpoint_start: 0 automatic, 1 from the sources, 2 from the tree of the
+    scene's obstacle-vertex geodesic table (when it has one)."""
+    t = SpmTuning(int(flood_mode), int(hidden_chunk), int(tile), int(maps), int(fixpoint_start))
     _check(load_library().spm_scene_set_tuning(handle, ctypes.byref(t)), "spm_scene_set_tuning", handle)
 
 

@@ -59,6 +59,12 @@ struct spm_scene {
     // device for this tile size and depth-map setting
     bool flood_static_ok = false;
     int flood_static_tile = 0, flood_static_maps = 0;
+    // the warm start of the fixpoint: the rounds the table build's deepest
+    // root took, whether that makes the warm start the default, and the
+    // caller's choice (spm_tuning.fixpoint_start)
+    int vtab_depth = 0;
+    bool warm_deep = false;
+    int fix_start = 0;
 };
 
 namespace {
@@ -455,6 +461,36 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         return set_err(nullptr, SPM_ERR_OOM, "device allocation or upload failed");
     }
     ds.fix_launch = spm::fixpoint_launches(ds, deg);
+    // obstacles never move: the geodesic distances between obstacle vertices
+    // are tabled once, and every compute starts its fixpoint from the tree
+    // they give
+    ds.vtab = nullptr;
+    ds.warm = 0;
+    if (spm::vtab_possible(ds)) {
+        const size_t nv = (size_t)hs.n_vert;
+        double *tab = dalloc<double>(s, nv * nv);
+        int32_t *counter = dalloc<int32_t>(s, 2);  // roots taken, the most rounds a root took
+        ds.warm_est = dalloc<double>(s, nv);
+        ds.warm_tpar = dalloc<int32_t>(s, nv);
+        ds.warm_tlen = dalloc<double>(s, nv);
+        ds.warm_cost = dalloc<double>(s, hs.n_gen);
+        ds.warm_par = dalloc<int32_t>(s, hs.n_gen);
+        int32_t rounds[2] = {0, 0};
+        if (!s->alloc_failed && spm::launch_vtab_build(ds, tab, counter, nullptr) == cudaSuccess &&
+            cudaMemcpy(rounds, counter, sizeof(rounds), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            ds.vtab = tab;
+            // a start from the sources takes about as many rounds as the
+            // deepest tree has links: the tree pays for itself on deep graphs
+            s->vtab_depth = rounds[1];
+            s->warm_deep = rounds[1] >= spm::kWarmMinDepth;
+            ds.warm = s->warm_deep ? 1 : 0;
+        }
+    }
+    if (s->alloc_failed) {
+        free_all(s);
+        delete s;
+        return set_err(nullptr, SPM_ERR_OOM, "device allocation or upload failed");
+    }
     if (cudaPeekAtLastError() != cudaSuccess) {
         free_all(s);
         delete s;
@@ -837,6 +873,7 @@ spm_status spm_batch_create(spm_scene *const *scenes, int32_t n, float *const *d
     int max_gen = 0;
     for (int k = 0; k < n; ++k) {
         descs[k] = scenes[k]->ds;
+        descs[k].warm = 0;  // the batched fixpoint starts every scene from its sources
         // geometric floods reuse the obstacle vertices' static lists: built
         // here if the scene has none for this tile size and map setting
         descs[k].flood_reuse = 0;
@@ -1163,7 +1200,7 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     // tests) and the list scan and fill
     const bool reuse = floods && s->ds.flood_mode == 3 && s->ds.static_tile_start;
     const int src_cull = !spm::flood_sources_direct(s->ds) ? 2 : s->ds.n_poly > 0 ? 3 : 2;
-    info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.fix_launch & spm::kFixSolo ? 1 : 0) +
+    info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.warm && s->ds.vtab ? 4 : 0) + (s->ds.fix_launch & spm::kFixSolo ? 1 : 0) +
                (s->ds.fix_launch & spm::kFixCluster ? 1 : 0) + (s->ds.fix_launch & (spm::kFixSoloSure | spm::kFixClusterSure) ? 0 : 1) + 1 +
                (floods ? (reuse ? src_cull + 2 : 3) : 0) + 1;  // vertex phase; flood, list scan and fill; pixels
     return SPM_OK;
@@ -1176,14 +1213,18 @@ spm_status spm_scene_get_tuning(const spm_scene *s, spm_tuning *out) {
     out->hidden_chunk = s->ds.hidden_chunk;
     out->tile = s->ds.tile;
     out->maps = s->ds.use_maps;
+    out->fixpoint_start = s->fix_start;
     return SPM_OK;
 }
 
 spm_status spm_scene_set_tuning(spm_scene *s, const spm_tuning *t) {
     if (!s || !t) return set_err(s, SPM_ERR_INVALID_ARG, "null argument");
     if (t->flood_mode < 0 || t->flood_mode > 3 || t->hidden_chunk < 32 || t->hidden_chunk > 256 ||
-        (t->tile != 0 && t->tile != spm::kTile && t->tile != spm::kTileSmall) || t->maps < 0 || t->maps > 1)
+        (t->tile != 0 && t->tile != spm::kTile && t->tile != spm::kTileSmall) || t->maps < 0 || t->maps > 1 ||
+        t->fixpoint_start < 0 || t->fixpoint_start > 2)
         return set_err(s, SPM_ERR_INVALID_ARG, "tuning out of range");
+    s->fix_start = t->fixpoint_start;
+    s->ds.warm = s->ds.vtab && (t->fixpoint_start == 2 || (t->fixpoint_start == 0 && s->warm_deep)) ? 1 : 0;
     s->ds.flood_mode = t->flood_mode;
     s->ds.hidden_chunk = t->hidden_chunk;
     s->ds.use_maps = t->maps && s->ds.gen_maps ? 1 : 0;
@@ -1208,6 +1249,7 @@ spm_status spm_scene_autotune(spm_scene *s, void *stream, spm_tuning *chosen) {
     pick.hidden_chunk = s->ds.hidden_chunk;
     pick.tile = s->ds.tile;
     pick.maps = s->ds.use_maps;
+    pick.fixpoint_start = s->fix_start;
     for (int ui = 0; ui < 2; ++ui)
     for (int ti = 0; ti < 2; ++ti)
     for (int mi = 0; mi < 3; ++mi) {

@@ -130,6 +130,18 @@ struct DevScene {
     const int32_t *st_out_dst;
     const int32_t *st_out_init;        // n_gen + 1: out_start before the sources' edges are counted
     int64_t edge_cap;
+    // warm start of the fixpoint: geodesic distances between obstacle
+    // vertices over the kept edges (n_vert x n_vert FP64, row-major by the
+    // first vertex; built once per scene, null when the scene has none), the
+    // estimates and tree a compute derives from them, and the state the
+    // fixpoint kernels start from when `warm` is set
+    const double *vtab;
+    int32_t warm;                      // this compute starts from vtab's tree (else from the sources alone)
+    double *warm_est;                  // n_vert estimated costs
+    int32_t *warm_tpar;                // n_vert tree parents (generator ids, -1: none)
+    double *warm_tlen;                 // n_vert FP64 lengths of the tree links
+    double *warm_cost;                 // n_gen costs along the tree
+    int32_t *warm_par;                 // n_gen parents along the tree
     double *cost[2];                   // Jacobi double buffer
     int32_t *par[2];
     int32_t *frontier[2];              // changed-vertex lists, alternating by round
@@ -270,6 +282,14 @@ constexpr int kFixClusterFits = 16;  // the cluster kernel takes every compute's
 int fixpoint_launches(const DevScene &ds, const std::vector<int32_t> &deg);
 // FP64 lengths of the static in-lists (ds.st_start / st_src set), into len
 void launch_static_lengths(const DevScene &ds, double *len, cudaStream_t st);
+// the warm start's geodesic table over the kept obstacle-vertex edges
+// (once per scene; ds.st_* set): tab gets n_vert x n_vert doubles
+constexpr int kVtabMinVert = 256;   // smaller graphs converge in a few rounds from the sources
+constexpr int kVtabMaxVert = 6144;  // the table's size: n_vert^2 doubles (288 MB at the limit)
+constexpr int kWarmMaxGen = 7168;   // generators the tree-fold kernel holds in shared memory
+constexpr int kWarmMinDepth = 32;   // table-build rounds from which the warm start is the default
+bool vtab_possible(const DevScene &ds);
+cudaError_t launch_vtab_build(const DevScene &ds, double *tab, int32_t *counter, cudaStream_t st);
 int cluster_batched_grid();  // CTAs of the batched cluster fixpoint's launch (0: unavailable)
 int count_kernel_launches_vertex();
 int count_kernel_launches_pixel();

@@ -607,6 +607,9 @@ __device__ __forceinline__ void arrival_from(const DevScene &ds, const signed ch
 
 __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
+#ifdef SPM_COUNT
+    const long long t_start = clock64();
+#endif
     bool with_len;
     if (solo_bytes(ds, with_len) == 0) return;
     const int n = ds.n_gen, nv = ds.n_vert, E = ds.in_start[nv];
@@ -637,17 +640,22 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     const int grp = lane / kSoloGrp, gl = lane % kSoloGrp, ngroups = nwarps * kGpw;
     const unsigned kFull = 0xffffffffu;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    // the loads of a loop are independent: unrolled, several are in flight
+#pragma unroll 4
     for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
+#pragma unroll 4
     for (int i = tid; i <= n; i += kSoloThreads) out_start[i] = ds.out_start[i];
+#pragma unroll 4
     for (int i = tid; i < E; i += kSoloThreads) {
         in_src[i] = (unsigned short)ds.in_src[i];
         out_dst[i] = (unsigned short)ds.out_dst[i];
         if (with_len) slen[i] = ds.in_len[i];
     }
+#pragma unroll 4
     for (int g = tid; g < n; g += kSoloThreads) {
         const bool src = g < ds.n_src;
-        cost[g] = src ? 0.0 : inf;
-        par[g] = (short)(src ? g : -1);
+        cost[g] = ds.warm ? ds.warm_cost[g] : src ? 0.0 : inf;  // warm: the tree's state
+        par[g] = (short)(ds.warm ? ds.warm_par[g] : src ? g : -1);
         const int2 l = ds.gen_lat[g];
         lat[g] = make_short2((short)l.x, (short)l.y);
         const int4 w = ds.gen_wedge[g];
@@ -661,14 +669,26 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     }
     if (tid < 3) cnt[tid] = 0;
     __syncthreads();
-    // the sources mark their out-neighbours for round 0
-    for (int u = warp * kGpw + grp; u < ds.n_src; u += ngroups)
-        for (int e = out_start[u] + gl; e < out_start[u + 1]; e += kSoloGrp) {
-            const int v = out_dst[e];
-            const unsigned bit = 1u << (v & 31);
-            if (!(atomicOr(&dirty[v >> 5], bit) & bit)) dl[atomicAdd(&cnt[0], 1)] = (unsigned short)v;
+    if (ds.warm) {  // round 0 pulls the vertices whose equation the tree's state breaks
+        const int m = min(ds.counters[6], nv);
+        for (int i = tid; i < m; i += kSoloThreads) {
+            const int v = ds.dirtyl[0][i];
+            dl[i] = (unsigned short)v;
+            atomicOr(&dirty[v >> 5], 1u << (v & 31));
         }
+        if (tid == 0) cnt[0] = m;
+    } else {  // the sources mark their out-neighbours for round 0
+        for (int u = warp * kGpw + grp; u < ds.n_src; u += ngroups)
+            for (int e = out_start[u] + gl; e < out_start[u + 1]; e += kSoloGrp) {
+                const int v = out_dst[e];
+                const unsigned bit = 1u << (v & 31);
+                if (!(atomicOr(&dirty[v >> 5], bit) & bit)) dl[atomicAdd(&cnt[0], 1)] = (unsigned short)v;
+            }
+    }
     __syncthreads();
+#ifdef SPM_COUNT
+    if (tid == 0) SPM_CNT(15, clock64() - t_start);  // the graph's loads and the first marks
+#endif
     int round = 0;
     for (;; ++round) {
         const int cur = round & 1, nxt = cur ^ 1;
@@ -931,8 +951,8 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     }
     for (int g = tid; g < n; g += kClThreads) {
         const bool src = g < ns;
-        cost[g] = src ? 0.0 : inf;
-        par[g] = (short)(src ? g : -1);
+        cost[g] = ds.warm ? ds.warm_cost[g] : src ? 0.0 : inf;  // warm: the tree's state
+        par[g] = (short)(ds.warm ? ds.warm_par[g] : src ? g : -1);
         const int2 l = ds.gen_lat[g];
         lat[g] = make_short2((short)l.x, (short)l.y);
         const int4 w = ds.gen_wedge[g];
@@ -967,9 +987,19 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
             cluster.map_shared_rank(dl, owner)[par_n * nmax + slot] = (unsigned short)lw;
         }
     };
-    // the sources mark their out-neighbours for round 0
-    for (int u = rank * ngroups + warp * kGpw + grp; u < ns; u += C * ngroups)
-        for (int e = ds.out_start[u] + gl; e < ds.out_start[u + 1]; e += kClGrp) mark(ds.out_dst[e], 0, 0);
+    if (ds.warm) {  // round 0 pulls the vertices whose equation the tree's state breaks; each CTA its own
+        const int m = min(ds.counters[6], nv);
+        for (int i = tid; i < m; i += kClThreads) {
+            const int vv = ds.dirtyl[0][i] - ns;
+            if (vv % C != rank) continue;
+            const int lw = vv / C;
+            atomicOr(&dirty[lw >> 5], 1u << (lw & 31));
+            dl[atomicAdd(&sh.cnt[0], 1)] = (unsigned short)lw;
+        }
+    } else {  // the sources mark their out-neighbours for round 0
+        for (int u = rank * ngroups + warp * kGpw + grp; u < ns; u += C * ngroups)
+            for (int e = ds.out_start[u] + gl; e < ds.out_start[u + 1]; e += kClGrp) mark(ds.out_dst[e], 0, 0);
+    }
     cluster.sync();
     int round = 0;
     for (;; ++round) {
@@ -1435,6 +1465,408 @@ bool cluster_smem_ok() {
     return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Warm start of the fixpoint. Obstacles never move, so the geodesic
+// distances between obstacle vertices over the kept obstacle-vertex edges
+// are computed once per scene (k_vtab_build). A compute then
+//   k_warm_entry: estimates each obstacle vertex's cost as the least
+//       m(u) + tab(u, v) over the vertices u a source links to, m(u) being
+//       u's shortest source link;
+//   k_warm_tree:  picks for each vertex the in-neighbour u with the least
+//       estimate(u) + |u - v| (sources estimate 0), the tree parent;
+//   k_warm_fold:  evaluates the FP64 cost along that tree as the fixpoint
+//       accumulates it, cost(v) = cost(parent) + |parent - v|, from the
+//       sources down (depths by pointer doubling, a counting sort by depth,
+//       one warp folding level by level);
+//   k_warm_verify: lists the vertices whose equation that state breaks
+//       (the fixpoint's pull gives another cost or parent);
+// and the fixpoint kernels start from that state with those vertices dirty.
+// The fixpoint of the vertex equations is unique, so the result is the
+// cold start's bit for bit; the tree only spares the rounds in which a start
+// from the sources alone carries costs down long chains of links (one round
+// a link). Where the tree is wrong (near ties of the estimates, cones) the
+// rounds that follow correct it.
+
+constexpr int kVtabWarps = 4;  // roots in flight per CTA of the table build
+constexpr double kEstNone = 1e300;  // estimates at or above this mean "not reached"
+
+__host__ __device__ __forceinline__ size_t vtab_list_bytes(int nv) { return ((size_t)4 * nv + 15) & ~(size_t)15; }
+__host__ __device__ __forceinline__ size_t vtab_warp_bytes(int nv) {
+    return vtab_list_bytes(nv) + ((((size_t)nv + 31) / 32 * 4 + 15) & ~(size_t)15);
+}
+
+// One warp per root vertex r, roots taken from a counter: Bellman-Ford rounds
+// over the kept edges, the frontier pushing cost(u) + |u - w| into row r by
+// 64-bit atomic minima (non-negative doubles order like their bit patterns).
+// The kept lists are symmetric between obstacle vertices (each pair is tested
+// once and its edge mirrored), so a vertex's in-list is its out-list. The
+// table only guides the start: any order of the sums will do.
+__global__ void __launch_bounds__(32 * kVtabWarps) k_vtab_build(const __grid_constant__ DevScene ds, double *tab,
+                                                                int32_t *counter) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ int cnt[kVtabWarps];
+    const int nv = ds.n_vert, ns = ds.n_src, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int dw = (nv + 31) / 32;
+    unsigned char *base = sm_raw + (size_t)warp * vtab_warp_bytes(nv);
+    unsigned short *list = (unsigned short *)base;                  // two lists of nv entries, by round parity
+    unsigned *inl = (unsigned *)(base + vtab_list_bytes(nv));       // vertex already in the next list
+    const unsigned kFull = 0xffffffffu;
+    const unsigned long long kInfBits = 0x7ff0000000000000ull;
+    for (;;) {
+        int r = 0;
+        if (lane == 0) r = atomicAdd(counter, 1);
+        r = __shfl_sync(kFull, r, 0);
+        if (r >= nv) return;
+        unsigned long long *row = (unsigned long long *)(tab + (size_t)r * nv);
+        for (int v = lane; v < nv; v += 32) row[v] = v == r ? 0ull : kInfBits;
+        for (int w = lane; w < dw; w += 32) inl[w] = 0u;
+        if (lane == 0) list[0] = (unsigned short)r;
+        int nc = 1, cur = 0;
+        __syncwarp();
+        for (int round = 0; nc > 0 && round <= nv; ++round) {
+            const int nxt = cur ^ 1;
+            if (lane == 0) cnt[warp] = 0;
+            for (int i = lane; i < nc; i += 32) {  // the members of this list may enter the next one again
+                const int u = list[cur * nv + i];
+                atomicAnd(&inl[u >> 5], ~(1u << (u & 31)));
+            }
+            __syncwarp();
+            for (int i = lane; i < nc; i += 32) {
+                const int u = list[cur * nv + i];
+                const double cu = __longlong_as_double((long long)__ldcg(row + u));  // minima land in L2
+                const int e1 = __ldg(ds.st_start + u + 1);
+                for (int e = __ldg(ds.st_start + u); e < e1; ++e) {
+                    const int w = __ldg(ds.st_src + e) - ns;
+                    const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(cu, __ldg(ds.st_len + e)));
+                    if (nd < atomicMin(row + w, nd)) {
+                        const unsigned bit = 1u << (w & 31);
+                        if (!(atomicOr(&inl[w >> 5], bit) & bit)) list[nxt * nv + atomicAdd(&cnt[warp], 1)] = (unsigned short)w;
+                    }
+                }
+            }
+            __syncwarp();
+            nc = cnt[warp];
+            cur = nxt;
+            __syncwarp();  // every lane has the count before lane 0 clears it
+            if (nc == 0 && lane == 0) atomicMax(counter + 1, round + 1);  // the deepest root's rounds
+        }
+    }
+}
+
+// Estimated cost of each obstacle vertex v: the least m(u) + tab(u, v) over
+// the vertices u with a source link, m(u) the shortest of them (a compute's
+// in-list of u starts with its source links: sources have the smallest
+// generator ids). Adding a length rounds monotonically, so taking m(u) first
+// loses nothing. Grid: x over 256 targets v, y over 128 candidate vertices u;
+// each CTA folds its share into warm_est (preset to a huge value) by 64-bit
+// atomic minima.
+constexpr int kEntryRows = 128;
+__global__ void __launch_bounds__(256) k_warm_entry(const __grid_constant__ DevScene ds) {
+    __shared__ int eu[kEntryRows];
+    __shared__ double em[kEntryRows];
+    __shared__ int ne;
+    const int nv = ds.n_vert, ns = ds.n_src, tid = threadIdx.x;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    if (tid == 0) ne = 0;
+    __syncthreads();
+    if (tid < kEntryRows) {
+        const int u = blockIdx.y * kEntryRows + tid;
+        if (u < nv) {
+            double m = inf;
+            const int e1 = ds.in_start[u + 1];
+            for (int e = ds.in_start[u]; e < e1 && ds.in_src[e] < ns; ++e) m = fmin(m, ds.in_len[e]);
+            if (m < inf) {
+                const int k = atomicAdd(&ne, 1);
+                eu[k] = u;
+                em[k] = m;
+            }
+        }
+    }
+    __syncthreads();
+    const int m = ne, vv = blockIdx.x * 256 + tid;
+    if (m == 0 || vv >= nv) return;
+    double best = inf;
+#pragma unroll 4
+    for (int k = 0; k < m; ++k) best = fmin(best, __dadd_rn(em[k], __ldg(ds.vtab + (size_t)eu[k] * nv + vv)));
+    if (best < inf) atomicMin((unsigned long long *)(ds.warm_est + vv), (unsigned long long)__double_as_longlong(best));
+}
+
+// Each obstacle vertex's tree parent: the in-neighbour u with the least
+// estimate(u) + |u - v| (the first of equal values, i.e. the smaller id), and
+// that link's FP64 length as the fixpoint adds it. A group of kWarmGrp lanes
+// per vertex, each over every kWarmGrp-th in-edge, then the lexicographic
+// minimum across the group.
+constexpr int kWarmGrp = 8;
+__global__ void __launch_bounds__(256) k_warm_tree(const __grid_constant__ DevScene ds) {
+    const int t = blockIdx.x * 256 + threadIdx.x, vv = t / kWarmGrp, gl = t % kWarmGrp;
+    const bool act = vv < ds.n_vert;  // every lane reaches the shuffles
+    const int ns = ds.n_src;
+    double best = __longlong_as_double(0x7ff0000000000000ll), blen = 0.0;
+    int bp = -1;
+    const int e0 = act ? ds.in_start[vv] : 0, e1 = act ? ds.in_start[vv + 1] : 0;
+    for (int e = e0 + gl; e < e1; e += kWarmGrp) {
+        const int u = ds.in_src[e];
+        const double len = ds.in_len[e];
+        const double est = u < ns ? 0.0 : ds.warm_est[u - ns];
+        const double c = __dadd_rn(est, len);
+        if (est < kEstNone && c < best) {  // no estimate: u is not reached from a source
+            best = c;
+            bp = u;
+            blen = len;
+        }
+    }
+#pragma unroll
+    for (int o = kWarmGrp / 2; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o), ol = __shfl_xor_sync(0xffffffffu, blen, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (ob < best || (ob == best && (unsigned)op < (unsigned)bp)) {
+            best = ob;
+            bp = op;
+            blen = ol;
+        }
+    }
+    if (act && gl == 0) {
+        ds.warm_tpar[vv] = bp;
+        ds.warm_tlen[vv] = blen;
+    }
+}
+
+// Checks every obstacle vertex against the fixpoint's pull from the tree's
+// state: the least (cost(u) + |u - v|, u) over its valid in-edges (u a
+// source, or v inside u's shadow cone, from u's parent), with the arithmetic
+// and the order of the fixpoint kernels' pulls. The vertices whose pull
+// differs from their state are listed (ds.dirtyl[0], count in
+// ds.counters[6]): they are the fixpoint's first round; every other vertex
+// already satisfies its equation.
+__global__ void __launch_bounds__(256) k_warm_verify(const __grid_constant__ DevScene ds) {
+    const int t = blockIdx.x * 256 + threadIdx.x, vv = t / kWarmGrp, gl = t % kWarmGrp;
+    const bool act = vv < ds.n_vert;  // every lane reaches the shuffles
+    const int ns = ds.n_src, v = ns + (act ? vv : 0);
+    const int2 vl = ds.gen_lat[v];
+    long long best = 0x7ff0000000000000ll;  // +inf bits
+    int bpar = -1;
+    const int e0 = act ? ds.in_start[vv] : 0, e1 = act ? ds.in_start[vv + 1] : 0;
+    for (int e = e0 + gl; e < e1; e += kWarmGrp) {  // in generator order within the lane
+        const int u = ds.in_src[e];
+        const double cu = ds.warm_cost[u];
+        const int pu = ds.warm_par[u];
+        const int2 ul = ds.gen_lat[u];
+        const int4 w4 = ds.gen_wedge[u];
+        int dx = 0, dy = 0;
+        if (pu >= 0) arrival_dir(ds, pu, ul, dx, dy);
+        const short4 w = make_short4((short)w4.x, (short)w4.y, (short)w4.z, (short)w4.w);
+        const bool valid = (__double_as_longlong(cu) < 0x7ff0000000000000ll) &
+                           ((u < ns) | ((pu >= 0) & in_shadow_cone(dx, dy, w, vl.x - ul.x, vl.y - ul.y)));
+        const long long cand = __double_as_longlong(__dadd_rn(cu, ds.in_len[e]));
+        if (valid & (cand < best)) {
+            best = cand;
+            bpar = u;
+        }
+    }
+#pragma unroll
+    for (int o = kWarmGrp / 2; o > 0; o >>= 1) {  // the fixpoint's lexicographic minimum over the group
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bpar, o);
+        if (ob < best || (ob == best && (unsigned)op < (unsigned)bpar)) {
+            best = ob;
+            bpar = op;
+        }
+    }
+    if (act && gl == 0 && (best != __double_as_longlong(ds.warm_cost[v]) || bpar != ds.warm_par[v]))
+        ds.dirtyl[0][atomicAdd(ds.counters + 6, 1)] = v;
+}
+
+constexpr int kFoldThreads = 1024;
+constexpr int kFoldPer = (kWarmMaxGen + kFoldThreads - 1) / kFoldThreads;  // generators per thread
+
+// Shared memory of the tree fold for n generators.
+__host__ __device__ __forceinline__ size_t fold_bytes(int n) {
+    auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    return 2 * up(8 * (size_t)n) + 3 * up(2 * (size_t)n) + up(4 * (size_t)n) + up(4 * ((size_t)n + 1));
+}
+
+// Costs along the tree, one CTA: the depth of every generator below its root
+// by pointer doubling; the reached vertices sorted by depth; then one warp
+// adds each level's links onto their parents' costs, level after level.
+// Roots are the sources (cost 0) and vertices without a tree parent (not
+// reached: +inf). A cycle of tree links (none is expected: estimates grow
+// strictly along every link) would never reach a source, so its vertices
+// are left unreached, as are the ones hanging from it.
+__global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constant__ DevScene ds) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ long long wsum[32];
+    __shared__ int s_maxd;
+    const int n = ds.n_gen, ns = ds.n_src, tid = threadIdx.x, lane = tid & 31;
+#ifdef SPM_COUNT
+    long long tf[5];
+    tf[0] = clock64();
+#endif
+    auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    unsigned char *p = sm_raw;
+    double *cost = (double *)p;             p += up(8 * (size_t)n);
+    double *olen = (double *)p;             p += up(8 * (size_t)n);  // tree-link lengths, in `order`
+    short *par = (short *)p;                p += up(2 * (size_t)n);
+    short *anc = (short *)p;                p += up(2 * (size_t)n);
+    unsigned short *dep = (unsigned short *)p;    p += up(2 * (size_t)n);
+    unsigned *order = (unsigned *)p;        p += up(4 * (size_t)n);  // by depth: vertex | parent << 16
+    int *level = (int *)p;                  // n + 1: vertices per depth, then level ends
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    for (int g = tid; g < n; g += kFoldThreads) {
+        const int pg = g < ns ? g : ds.warm_tpar[g - ns];
+        par[g] = (short)pg;
+        anc[g] = (short)(pg < 0 ? g : pg);
+        dep[g] = (unsigned short)(g < ns || pg < 0 ? 0 : 1);
+        cost[g] = g < ns ? 0.0 : inf;
+    }
+    for (int d = tid; d <= n; d += kFoldThreads) level[d] = 0;
+    if (tid == 0) s_maxd = 0;
+    __syncthreads();
+#ifdef SPM_COUNT
+    tf[1] = clock64();
+#endif
+    // pointer doubling: dep[g] = links from g to its root, anc[g] = the root
+    for (int it = 0; it < 16; ++it) {
+        short na[kFoldPer];
+        unsigned nd[kFoldPer];
+#pragma unroll
+        for (int k = 0; k < kFoldPer; ++k) {
+            const int g = tid + k * kFoldThreads;
+            if (g < n) {
+                const int a = anc[g];
+                na[k] = anc[a];
+                nd[k] = (unsigned)dep[g] + dep[a];
+            }
+        }
+        __syncthreads();
+        int ch = 0;
+#pragma unroll
+        for (int k = 0; k < kFoldPer; ++k) {
+            const int g = tid + k * kFoldThreads;
+            if (g < n) {
+                ch |= na[k] != anc[g];
+                anc[g] = na[k];
+                dep[g] = (unsigned short)min(nd[k], 65535u);
+            }
+        }
+        if (!__syncthreads_or(ch)) break;
+    }
+#ifdef SPM_COUNT
+    tf[2] = clock64();
+#endif
+    // a vertex is reached when its chain ends at a source (a chain caught in
+    // a cycle never does); its depth is then at most n
+    int md = 0;
+    for (int g = ns + tid; g < n; g += kFoldThreads)
+        if (anc[g] < ns) {
+            atomicAdd(&level[dep[g] - 1], 1);
+            md = max(md, (int)dep[g]);
+        }
+    if (md) atomicMax(&s_maxd, md);
+    __syncthreads();
+    // exclusive scan of the level sizes, each thread a run of kFoldPer + 1 depths
+    {
+        constexpr int kRun = kFoldPer + 1;
+        const int d0 = tid * kRun;
+        long long mine = 0;
+        for (int d = d0; d < d0 + kRun && d <= n; ++d) mine += level[d];
+        long long run = cta_exclusive_scan(mine, wsum);
+        for (int d = d0; d < d0 + kRun && d <= n; ++d) {
+            const int c = level[d];
+            level[d] = (int)run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int g = ns + tid; g < n; g += kFoldThreads)
+        if (anc[g] < ns) {  // level[k] ends as the end of depth k + 1
+            const int i = atomicAdd(&level[dep[g] - 1], 1);
+            order[i] = (unsigned)g | ((unsigned)par[g] << 16);
+            olen[i] = ds.warm_tlen[g - ns];
+        }
+    __syncthreads();
+#ifdef SPM_COUNT
+    tf[3] = clock64();
+#endif
+    if (tid < 32) {
+        // one level after the other; a lane's first item of the next level
+        // (vertex, parent, length) is loaded before this level's sums, so a
+        // level costs one dependent load, one add and one store
+        const int maxd = s_maxd;
+        int lo = 0, hi = maxd > 0 ? level[0] : 0;
+        unsigned o = lane < hi ? order[lane] : 0u;
+        double l = lane < hi ? olen[lane] : 0.0;
+        for (int k = 0; k < maxd; ++k) {
+            const int nhi = k + 1 < maxd ? level[k + 1] : hi, ni = hi + lane;
+            const unsigned no = ni < nhi ? order[ni] : 0u;
+            const double nl = ni < nhi ? olen[ni] : 0.0;
+            if (lo + lane < hi) cost[o & 0xffffu] = __dadd_rn(cost[o >> 16], l);
+            for (int i = lo + 32 + lane; i < hi; i += 32) {  // levels wider than a warp
+                const unsigned oi = order[i];
+                cost[oi & 0xffffu] = __dadd_rn(cost[oi >> 16], olen[i]);
+            }
+            __syncwarp();
+            lo = hi;
+            hi = nhi;
+            o = no;
+            l = nl;
+        }
+    }
+    __syncthreads();
+#ifdef SPM_COUNT
+    tf[4] = clock64();
+    if (tid == 0) {  // fold phases (SM cycles): loads, doubling, sort, level fold
+        SPM_CNT(2, tf[1] - tf[0]);
+        SPM_CNT(3, tf[2] - tf[1]);
+        SPM_CNT(4, tf[3] - tf[2]);
+        SPM_CNT(12, tf[4] - tf[3]);
+    }
+#endif
+    for (int g = tid; g < n; g += kFoldThreads) {
+        const bool ok = g < ns || anc[g] < ns;
+        ds.warm_cost[g] = ok ? cost[g] : inf;
+        ds.warm_par[g] = ok ? (int)par[g] : -1;
+    }
+}
+
+// shared memory of the tree fold and of the table build, granted once per process
+static bool fold_smem_ok() {
+    static const bool ok = [] {
+        if (cudaFuncSetAttribute(k_warm_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fold_bytes(kWarmMaxGen)) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_vtab_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kVtabWarps * vtab_warp_bytes(kVtabMaxVert))) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }();
+    return ok;
+}
+
+bool vtab_possible(const DevScene &ds) {
+    return ds.st_start && ds.st_len && ds.n_vert >= kVtabMinVert && ds.n_vert <= kVtabMaxVert &&
+           ds.n_gen <= kWarmMaxGen && (ds.fix_launch & (kFixSoloSure | kFixClusterSure)) && fold_smem_ok();
+}
+
+// A compute with these fixpoint launches starts from the table's tree.
+static bool warm_start_used(const DevScene &ds, int fix) {
+    return ds.warm && ds.vtab && ds.n_vert > 0 && (fix & (kFixSoloSure | kFixClusterSure));
+}
+
+cudaError_t launch_vtab_build(const DevScene &ds, double *tab, int32_t *counter, cudaStream_t st) {
+    if (!vtab_possible(ds)) return cudaErrorInvalidValue;
+    const size_t smem = kVtabWarps * vtab_warp_bytes(ds.n_vert);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vtab_build, 32 * kVtabWarps, smem);
+    const int need = (ds.n_vert + kVtabWarps - 1) / kVtabWarps;
+    const int blocks = std::max(1, std::min(need, std::max(sms, 1) * std::max(per_sm, 1)));
+    cudaMemsetAsync(counter, 0, 2 * sizeof(int32_t), st);  // [0] roots taken, [1] the most rounds a root took
+    k_vtab_build<<<blocks, 32 * kVtabWarps, smem, st>>>(ds, tab, counter);
+    return cudaGetLastError();
+}
+
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
     if (ds.st_out_init)  // the obstacle vertices' out-degrees are kept; the sources' are counted
         cudaMemcpyAsync(ds.out_start, ds.st_out_init, sizeof(int32_t) * (ds.n_gen + 1), cudaMemcpyDeviceToDevice, st);
@@ -1467,8 +1899,21 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
     // cannot apply
     int f = ds.fix_launch;
     if (g_many_cta_override.load() && !(f & kFixSoloSure)) f &= ~(kFixCluster | kFixClusterSure);  // test hook
-    if (f & kFixSolo) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(ds, max_rounds);
-    if (f & kFixCluster) k_sssp_cluster<<<kClCtas, kClThreads, kClSmem, st>>>(ds, max_rounds);
+    // the warm start needs a fixpoint kernel that takes it (the many-CTA one
+    // always starts from the sources)
+    arg.warm = warm_start_used(ds, f) ? 1 : 0;
+    if (arg.warm) {
+        const int vb = (ds.n_vert + 255) / 256;
+        cudaMemsetAsync(ds.warm_est, 0x7f, sizeof(double) * ds.n_vert, st);  // 1.4e306: no estimate yet
+        cudaMemsetAsync(ds.counters + 6, 0, sizeof(int32_t), st);
+        k_warm_entry<<<dim3(vb, (ds.n_vert + kEntryRows - 1) / kEntryRows), 256, 0, st>>>(arg);
+        const int gb = (ds.n_vert * kWarmGrp + 255) / 256;
+        k_warm_tree<<<gb, 256, 0, st>>>(arg);
+        k_warm_fold<<<1, kFoldThreads, fold_bytes(ds.n_gen), st>>>(arg);
+        k_warm_verify<<<gb, 256, 0, st>>>(arg);
+    }
+    if (f & kFixSolo) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(arg, max_rounds);
+    if (f & kFixCluster) k_sssp_cluster<<<kClCtas, kClThreads, kClSmem, st>>>(arg, max_rounds);
     else if (!(f & kFixSoloSure)) cudaMemsetAsync(ds.counters + 4, 0, sizeof(int32_t), st);
     if (!(f & (kFixSoloSure | kFixClusterSure)))
         cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);

@@ -234,6 +234,48 @@ def test_fixpoint_kernels_agree(spm):
         assert torch.equal(p0, p1) and torch.equal(d0.view(torch.int32), d1.view(torch.int32)), scene.name
 
 
+def test_warm_start_matches_cold_start(spm):
+    """A scene with 256 to 6144 obstacle vertices tables the geodesic
+    distances between them once; a compute can start the vertex fixpoint from
+    the shortest-path tree that table gives, with costs folded along the tree
+    exactly as the fixpoint adds them and only the vertices whose equation
+    that state breaks pulled in the first round. The fixpoint is unique, so
+    the start from the tree and the start from the sources give the same
+    costs, parents and map bit for bit. On a maze (deep trees) the tree is
+    the automatic choice and needs a few rounds where the sources need the
+    depth of the tree; on open polygon scenes (shallow trees) the sources
+    stay the automatic choice."""
+    scenes = (sg.maze(3, cells=24, N=768), sg.plain_polys(2, n_polys=120, N=256),
+              sg.differentiable(1, W=2048, N=512, n_polys=60, n_agents=10), sg.plain_polys(1))
+    for scene in scenes:
+        s = spm.Scene(scene)
+        t = s.tuning()
+        assert t["fixpoint_start"] == 0
+        auto_kernels = s.info()["kernels_per_compute"]
+        runs = {}
+        for start in (2, 1, 0):
+            spm.spm_scene_set_tuning(s.handle, t["flood_mode"], t["hidden_chunk"], t["tile"], t["maps"],
+                                     fixpoint_start=start)
+            assert s.tuning()["fixpoint_start"] == start
+            d, p = s.compute()
+            s.sync()
+            runs[start] = (d, p, s.generators(), s.info()["rounds"], s.info()["kernels_per_compute"])
+        d0, p0, g0, r_tree, k_tree = runs[2]
+        for start in (1, 0):
+            d1, p1, g1, _, _ = runs[start]
+            for a, b in zip(g0, g1):
+                assert np.array_equal(a, b), (scene.name, start)
+            assert torch.equal(p0, p1) and torch.equal(d0.view(torch.int32), d1.view(torch.int32)), scene.name
+        r_src, k_src = runs[1][3], runs[1][4]
+        assert k_tree == k_src + 4  # the tree's four kernels
+        assert runs[0][4] == auto_kernels
+        if scene.name.startswith("maze"):
+            assert 4 * r_tree < r_src, (scene.name, r_tree, r_src)
+            assert auto_kernels == k_tree  # deep trees: the tree is the automatic start
+        else:
+            assert auto_kernels == k_src, scene.name  # shallow trees: the sources
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
