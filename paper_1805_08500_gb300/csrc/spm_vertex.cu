@@ -605,6 +605,32 @@ __device__ __forceinline__ void arrival_from(const DevScene &ds, const signed ch
     dy = side > 0 ? ux : -ux;
 }
 
+// Copies n 4-byte words from global to shared memory (both 16-byte
+// aligned) by asynchronous 16-byte copies, the tail word by word; the caller
+// waits (cp.async.wait_all) before its barrier.
+__device__ __forceinline__ void async_copy_words(void *dst, const void *src, long long n, int tid, int nthr) {
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
+    const char *s0 = (const char *)src;
+    const long long n4 = n / 4;
+    for (long long i = tid; i < n4; i += nthr)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16 * (uint32_t)i), "l"(s0 + 16 * i) : "memory");
+    for (long long i = 4 * n4 + tid; i < n; i += nthr)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d0 + 4 * (uint32_t)i), "l"(s0 + 4 * i) : "memory");
+}
+
+// n int32 generator ids (global, 16-byte aligned) into 16-bit ids in shared
+// memory (8-byte aligned), four per 16-byte load.
+__device__ __forceinline__ void narrow_ids(unsigned short *dst, const int32_t *src, int n, int tid, int nthr) {
+    const int n4 = n / 4;
+#pragma unroll 4
+    for (int i = tid; i < n4; i += nthr) {
+        const int4 a = __ldg(reinterpret_cast<const int4 *>(src) + i);
+        reinterpret_cast<ushort4 *>(dst)[i] =
+            make_ushort4((unsigned short)a.x, (unsigned short)a.y, (unsigned short)a.z, (unsigned short)a.w);
+    }
+    for (int i = 4 * n4 + tid; i < n; i += nthr) dst[i] = (unsigned short)src[i];
+}
+
 __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
 #ifdef SPM_COUNT
@@ -640,17 +666,13 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     const int grp = lane / kSoloGrp, gl = lane % kSoloGrp, ngroups = nwarps * kGpw;
     const unsigned kFull = 0xffffffffu;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
-    // the loads of a loop are independent: unrolled, several are in flight
-#pragma unroll 4
-    for (int i = tid; i <= nv; i += kSoloThreads) in_start[i] = ds.in_start[i];
-#pragma unroll 4
-    for (int i = tid; i <= n; i += kSoloThreads) out_start[i] = ds.out_start[i];
-#pragma unroll 4
-    for (int i = tid; i < E; i += kSoloThreads) {
-        in_src[i] = (unsigned short)ds.in_src[i];
-        out_dst[i] = (unsigned short)ds.out_dst[i];
-        if (with_len) slen[i] = ds.in_len[i];
-    }
+    // arrays copied as they are go by asynchronous copies (many in flight,
+    // no registers); the 16-bit ids are narrowed from 16-byte loads
+    async_copy_words(in_start, ds.in_start, nv + 1, tid, kSoloThreads);
+    async_copy_words(out_start, ds.out_start, n + 1, tid, kSoloThreads);
+    if (with_len) async_copy_words(slen, ds.in_len, 2 * E, tid, kSoloThreads);
+    narrow_ids(in_src, ds.in_src, E, tid, kSoloThreads);
+    narrow_ids(out_dst, ds.out_dst, E, tid, kSoloThreads);
 #pragma unroll 4
     for (int g = tid; g < n; g += kSoloThreads) {
         const bool src = g < ds.n_src;
@@ -668,6 +690,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         src_seg[g] = k == kSegI ? ds.seg_lat[ds.gen_aux[g]] : make_int4(0, 0, 0, 0);
     }
     if (tid < 3) cnt[tid] = 0;
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (ds.warm) {  // round 0 pulls the vertices whose equation the tree's state breaks
         const int m = min(ds.counters[6], nv);
@@ -1706,16 +1729,14 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
     double *cost = (double *)p;             p += up(8 * (size_t)n);
     double *olen = (double *)p;             p += up(8 * (size_t)n);  // tree-link lengths, in `order`
     short *par = (short *)p;                p += up(2 * (size_t)n);
-    short *anc = (short *)p;                p += up(2 * (size_t)n);
-    unsigned short *dep = (unsigned short *)p;    p += up(2 * (size_t)n);
+    unsigned *ad = (unsigned *)p;           p += 2 * up(2 * (size_t)n);  // root (low 16 bits) | depth (high 16)
     unsigned *order = (unsigned *)p;        p += up(4 * (size_t)n);  // by depth: vertex | parent << 16
     int *level = (int *)p;                  // n + 1: vertices per depth, then level ends
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     for (int g = tid; g < n; g += kFoldThreads) {
         const int pg = g < ns ? g : ds.warm_tpar[g - ns];
         par[g] = (short)pg;
-        anc[g] = (short)(pg < 0 ? g : pg);
-        dep[g] = (unsigned short)(g < ns || pg < 0 ? 0 : 1);
+        ad[g] = (unsigned)(pg < 0 ? g : pg) | (g < ns || pg < 0 ? 0u : 1u << 16);
         cost[g] = g < ns ? 0.0 : inf;
     }
     for (int d = tid; d <= n; d += kFoldThreads) level[d] = 0;
@@ -1724,17 +1745,16 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
 #ifdef SPM_COUNT
     tf[1] = clock64();
 #endif
-    // pointer doubling: dep[g] = links from g to its root, anc[g] = the root
+    // pointer doubling: each word becomes (the root, the links to it)
     for (int it = 0; it < 16; ++it) {
-        short na[kFoldPer];
-        unsigned nd[kFoldPer];
+        unsigned was[kFoldPer], now[kFoldPer];
 #pragma unroll
         for (int k = 0; k < kFoldPer; ++k) {
             const int g = tid + k * kFoldThreads;
             if (g < n) {
-                const int a = anc[g];
-                na[k] = anc[a];
-                nd[k] = (unsigned)dep[g] + dep[a];
+                const unsigned x = ad[g], y = ad[x & 0xffffu];
+                was[k] = x;
+                now[k] = (y & 0xffffu) | (min((x >> 16) + (y >> 16), 65535u) << 16);
             }
         }
         __syncthreads();
@@ -1743,9 +1763,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
         for (int k = 0; k < kFoldPer; ++k) {
             const int g = tid + k * kFoldThreads;
             if (g < n) {
-                ch |= na[k] != anc[g];
-                anc[g] = na[k];
-                dep[g] = (unsigned short)min(nd[k], 65535u);
+                ch |= (now[k] ^ was[k]) & 0xffffu;
+                ad[g] = now[k];
             }
         }
         if (!__syncthreads_or(ch)) break;
@@ -1757,9 +1776,10 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
     // a cycle never does); its depth is then at most n
     int md = 0;
     for (int g = ns + tid; g < n; g += kFoldThreads)
-        if (anc[g] < ns) {
-            atomicAdd(&level[dep[g] - 1], 1);
-            md = max(md, (int)dep[g]);
+        if ((int)(ad[g] & 0xffffu) < ns) {
+            const int d = (int)(ad[g] >> 16);
+            atomicAdd(&level[d - 1], 1);
+            md = max(md, d);
         }
     if (md) atomicMax(&s_maxd, md);
     __syncthreads();
@@ -1778,8 +1798,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
     }
     __syncthreads();
     for (int g = ns + tid; g < n; g += kFoldThreads)
-        if (anc[g] < ns) {  // level[k] ends as the end of depth k + 1
-            const int i = atomicAdd(&level[dep[g] - 1], 1);
+        if ((int)(ad[g] & 0xffffu) < ns) {  // level[k] ends as the end of depth k + 1
+            const int i = atomicAdd(&level[(int)(ad[g] >> 16) - 1], 1);
             order[i] = (unsigned)g | ((unsigned)par[g] << 16);
             olen[i] = ds.warm_tlen[g - ns];
         }
@@ -1792,14 +1812,15 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
         // (vertex, parent, length) is loaded before this level's sums, so a
         // level costs one dependent load, one add and one store
         const int maxd = s_maxd;
-        int lo = 0, hi = maxd > 0 ? level[0] : 0;
+        int lo = 0, hi = maxd > 0 ? level[0] : 0, nhi = maxd > 1 ? level[1] : hi;
         unsigned o = lane < hi ? order[lane] : 0u;
         double l = lane < hi ? olen[lane] : 0.0;
         for (int k = 0; k < maxd; ++k) {
-            const int nhi = k + 1 < maxd ? level[k + 1] : hi, ni = hi + lane;
+            const double cp = cost[o >> 16];  // the one load on the chain, issued first
+            const int ni = hi + lane, nnhi = k + 2 < maxd ? level[k + 2] : nhi;
             const unsigned no = ni < nhi ? order[ni] : 0u;
             const double nl = ni < nhi ? olen[ni] : 0.0;
-            if (lo + lane < hi) cost[o & 0xffffu] = __dadd_rn(cost[o >> 16], l);
+            if (lo + lane < hi) cost[o & 0xffffu] = __dadd_rn(cp, l);
             for (int i = lo + 32 + lane; i < hi; i += 32) {  // levels wider than a warp
                 const unsigned oi = order[i];
                 cost[oi & 0xffffu] = __dadd_rn(cost[oi >> 16], olen[i]);
@@ -1807,6 +1828,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
             __syncwarp();
             lo = hi;
             hi = nhi;
+            nhi = nnhi;
             o = no;
             l = nl;
         }
@@ -1822,7 +1844,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constan
     }
 #endif
     for (int g = tid; g < n; g += kFoldThreads) {
-        const bool ok = g < ns || anc[g] < ns;
+        const bool ok = g < ns || (int)(ad[g] & 0xffffu) < ns;
         ds.warm_cost[g] = ok ? cost[g] : inf;
         ds.warm_par[g] = ok ? (int)par[g] : -1;
     }
