@@ -601,11 +601,11 @@ _AgentLoss = _Lazy()
 
 def debug_read(kind: str):
     """Read and clear an instrumentation build's device counters: kind
-    "pixels", "flood" or "vertex" (16 work counters each, SPM_COUNT build) or
+    "pixels", "flood" or "vertex" (32 work counters each, SPM_COUNT build) or
     "pixel_clocks" / "flood_clocks" (8 phase clocks, SPM_TIME build). Raises
     AttributeError on the product library, which has none."""
-    names = {"pixels": ("spm_debug_counters", 16), "flood": ("spm_debug_counters_flood", 16),
-             "vertex": ("spm_debug_counters_vertex", 16), "pixel_clocks": ("spm_debug_times", 8),
+    names = {"pixels": ("spm_debug_counters", 32), "flood": ("spm_debug_counters_flood", 32),
+             "vertex": ("spm_debug_counters_vertex", 32), "pixel_clocks": ("spm_debug_times", 8),
              "flood_clocks": ("spm_debug_times_flood", 8)}
     name, n = names[kind]
     fn = getattr(load_library(), name)

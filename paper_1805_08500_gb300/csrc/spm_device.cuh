@@ -17,7 +17,7 @@ namespace spm {
 
 // Work counters of an instrumentation build (-DSPM_COUNT); compiled out otherwise.
 #ifdef SPM_COUNT
-static __device__ unsigned long long g_count[16];  // one copy per translation unit
+static __device__ unsigned long long g_count[32];  // one copy per translation unit
 #define SPM_CNT(i, v) atomicAdd(&::spm::g_count[i], (unsigned long long)(v))
 #define SPM_CNT_MAX(i, v) atomicMax(&::spm::g_count[i], (unsigned long long)(v))
 #else

@@ -767,10 +767,10 @@ extern "C" int spm_debug_times_flood(unsigned long long *out8) {
 
 #ifdef SPM_COUNT
 // Instrumentation build only: reads and clears this unit's work counters.
-extern "C" int spm_debug_counters_flood(unsigned long long *out16) {
+extern "C" int spm_debug_counters_flood(unsigned long long *out32) {
     cudaDeviceSynchronize();
-    if (cudaMemcpyFromSymbol(out16, spm::g_count, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
-    unsigned long long z[16] = {0};
+    if (cudaMemcpyFromSymbol(out32, spm::g_count, sizeof(unsigned long long) * 32) != cudaSuccess) return 1;
+    unsigned long long z[32] = {0};
     cudaMemcpyToSymbol(spm::g_count, z, sizeof z);
     return 0;
 }

@@ -825,10 +825,10 @@ int count_kernel_launches_pixel() { return 1; }
 
 #ifdef SPM_COUNT
 // Instrumentation build only: reads and clears the work counters.
-extern "C" int spm_debug_counters(unsigned long long *out16) {
+extern "C" int spm_debug_counters(unsigned long long *out32) {
     cudaDeviceSynchronize();
-    if (cudaMemcpyFromSymbol(out16, spm::g_count, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
-    unsigned long long z[16] = {0};
+    if (cudaMemcpyFromSymbol(out32, spm::g_count, sizeof(unsigned long long) * 32) != cudaSuccess) return 1;
+    unsigned long long z[32] = {0};
     cudaMemcpyToSymbol(spm::g_count, z, sizeof z);
     return 0;
 }

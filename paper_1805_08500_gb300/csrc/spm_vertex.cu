@@ -2024,10 +2024,10 @@ extern "C" void spm_debug_set_many_cta_fixpoint(int32_t on) { spm::g_many_cta_ov
 
 #ifdef SPM_COUNT
 // Instrumentation build only: reads and clears this unit's work counters.
-extern "C" int spm_debug_counters_vertex(unsigned long long *out16) {
+extern "C" int spm_debug_counters_vertex(unsigned long long *out32) {
     cudaDeviceSynchronize();
-    if (cudaMemcpyFromSymbol(out16, spm::g_count, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
-    unsigned long long z[16] = {0};
+    if (cudaMemcpyFromSymbol(out32, spm::g_count, sizeof(unsigned long long) * 32) != cudaSuccess) return 1;
+    unsigned long long z[32] = {0};
     cudaMemcpyToSymbol(spm::g_count, z, sizeof z);
     return 0;
 }
