@@ -1200,9 +1200,12 @@ spm_status spm_scene_info(spm_scene *s, int64_t *info) {
     // tests) and the list scan and fill
     const bool reuse = floods && s->ds.flood_mode == 3 && s->ds.static_tile_start;
     const int src_cull = !spm::flood_sources_direct(s->ds) ? 2 : s->ds.n_poly > 0 ? 3 : 2;
-    info[10] = (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.warm && s->ds.vtab ? 4 : 0) + (s->ds.fix_launch & spm::kFixSolo ? 1 : 0) +
-               (s->ds.fix_launch & spm::kFixCluster ? 1 : 0) + (s->ds.fix_launch & (spm::kFixSoloSure | spm::kFixClusterSure) ? 0 : 1) + 1 +
-               (floods ? (reuse ? src_cull + 2 : 3) : 0) + 1;  // vertex phase; flood, list scan and fill; pixels
+    // vertex phase (prep, pairs, edges, the tree's kernels, fixpoint kernels,
+    // and after the many-CTA one its finalisation); flood, list scan and
+    // fill; pixels
+    const int many_cta = s->ds.fix_launch & (spm::kFixSoloSure | spm::kFixClusterSure) ? 0 : 2;
+    info[10] = 1 + (s->hs.n_vert > 0 ? 4 : 0) + (s->ds.warm && s->ds.vtab ? 4 : 0) + (s->ds.fix_launch & spm::kFixSolo ? 1 : 0) +
+               (s->ds.fix_launch & spm::kFixCluster ? 1 : 0) + many_cta + (floods ? (reuse ? src_cull + 2 : 3) : 0) + 1;
     return SPM_OK;
 }
 

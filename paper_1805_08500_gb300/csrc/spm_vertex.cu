@@ -397,6 +397,13 @@ __global__ void k_static_lengths(const __grid_constant__ DevScene ds, double *le
             len[e] = edge_len(ds, ds.st_src[e], ds.n_src + vv);
 }
 
+// The finalised table entry of generator g (the pixel pass reads FP32 costs).
+__device__ __forceinline__ void finalize_gen(const DevScene &ds, int g, double c, int p) {
+    ds.gen_cost[g] = c;
+    ds.gen_par[g] = p;
+    ds.gen_costf[g] = (float)c;
+}
+
 // Jacobi rounds of the fixpoint on the whole GPU (cooperative launch, two
 // grid barriers per round). cost[0]/par[0] and the cone cache hold the
 // committed state; a round
@@ -852,6 +859,7 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
         ds.par[0][g] = pg;
         ds.gen_cone[g] = c;
         ds.gen_ctype[g] = ct;
+        finalize_gen(ds, g, cost[g], pg);
     }
     if (tid == 0) ds.stats[0] = round;
 }
@@ -922,6 +930,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
                 ds.par[0][g] = g;
                 ds.gen_cone[g] = make_int4(0, 0, 0, 0);
                 ds.gen_ctype[g] = kConeNone;
+                finalize_gen(ds, g, 0.0, g);
             }
             if (tid == 0) ds.stats[0] = 0;
         }
@@ -1126,6 +1135,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
         ds.par[0][g] = pg;
         ds.gen_cone[g] = c;
         ds.gen_ctype[g] = ct;
+        finalize_gen(ds, g, cost[g], pg);
     }
     if (rank == 0 && tid == 0) ds.stats[0] = round;
     cluster.sync();  // this scene's shared memory is no longer read
@@ -1165,19 +1175,11 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
 }
 
 // Final generator table for the pixel phase: FP32 costs and shadow cones.
-__device__ __forceinline__ void finalize_gen(const DevScene &ds, int g) {
-    {
-        const double c = ds.cost[0][g];
-        const int p = ds.par[0][g];
-        ds.gen_cost[g] = c;
-        ds.gen_par[g] = p;
-        ds.gen_costf[g] = (float)c;
-    }
-}
-
+// After the many-CTA fixpoint (the single-CTA and cluster kernels finalise
+// their own results).
 __global__ void k_finalize(const __grid_constant__ DevScene ds) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ds.n_gen; g += gridDim.x * blockDim.x)
-        finalize_gen(ds, g);
+        finalize_gen(ds, g, ds.cost[0][g], ds.par[0][g]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1389,7 +1391,11 @@ __global__ void __launch_bounds__(256) k_sssp_b(const __grid_constant__ BatchDev
 __global__ void k_finalize_b(const __grid_constant__ BatchDev b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.gen_off[b.n]; i += gridDim.x * blockDim.x) {
         const int s = scene_of(b.gen_off, b.n, i);
-        finalize_gen(b.scenes[s], i - b.gen_off[s]);
+        {
+            const DevScene &d = b.scenes[s];
+            const int g = i - b.gen_off[s];
+            finalize_gen(d, g, d.cost[0][g], d.par[0][g]);
+        }
     }
 }
 
@@ -1408,9 +1414,31 @@ int fixpoint_round_cap(int n_gen) {
 
 // Visibility-pair kernel over ds's pair range (resident CTAs, runs sized so
 // that every resident warp takes about two).
-void launch_pairs(const DevScene &ds, cudaStream_t st) {
+// The start values of a compute's vertex phase, in one launch: out-degrees
+// (the kept obstacle vertices', or zero), fill cursors, the source columns of
+// the bit matrix (with kept edge lists), the pair kernel's work counter, the
+// cluster kernel's done flag and, for a warm start, the estimates (a huge
+// value: none yet) and the count of unsatisfied vertices.
+__global__ void k_vertex_prep(const __grid_constant__ DevScene ds) {
+    const int sw = (ds.n_src + 31) / 32;
+    const long long n_bits = ds.st_start ? (long long)ds.n_vert * sw : 0;
+    const long long items = max((long long)ds.n_gen + 1, n_bits);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < items; i += (long long)gridDim.x * blockDim.x) {
+        if (i <= ds.n_gen) ds.out_start[i] = ds.st_out_init ? ds.st_out_init[i] : 0;
+        if (i < ds.n_gen) ds.out_fill[i] = 0;
+        if (i < n_bits) ds.vis_bits[(i / sw) * ds.vis_words + i % sw] = 0u;
+        if (ds.warm && i < ds.n_vert) ds.warm_est[i] = __longlong_as_double(0x7f7f7f7f7f7f7f7fll);  // 1.4e306
+        if (i == 0) {
+            *reinterpret_cast<unsigned long long *>(ds.stats + 2) = 0ull;  // the pair kernel's work counter
+            ds.counters[4] = 0;
+            ds.counters[6] = 0;
+        }
+    }
+}
+
+void launch_pairs(const DevScene &ds, cudaStream_t st, bool reset_counter = true) {
     const long long tasks = (long long)ds.n_vert * ds.pair_words;
-    cudaMemsetAsync(ds.stats + 2, 0, sizeof(unsigned long long), st);  // the pair kernel's work counter
+    if (reset_counter) cudaMemsetAsync(ds.stats + 2, 0, sizeof(unsigned long long), st);  // the pair kernel's work counter
     if (tasks == 0) return;
     const int resident = vis_resident_blocks();
     long long blocks = (tasks + (kVisThreads / 32) - 1) / (kVisThreads / 32);  // a task per warp at least
@@ -1890,21 +1918,30 @@ cudaError_t launch_vtab_build(const DevScene &ds, double *tab, int32_t *counter,
 }
 
 void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
-    if (ds.st_out_init)  // the obstacle vertices' out-degrees are kept; the sources' are counted
-        cudaMemcpyAsync(ds.out_start, ds.st_out_init, sizeof(int32_t) * (ds.n_gen + 1), cudaMemcpyDeviceToDevice, st);
-    else
-        cudaMemsetAsync(ds.out_start, 0, sizeof(int32_t) * (ds.n_gen + 1), st);
-    cudaMemsetAsync(ds.out_fill, 0, sizeof(int32_t) * ds.n_gen, st);
+    int f = ds.fix_launch;
+    if (g_many_cta_override.load() && !(f & kFixSoloSure)) f &= ~(kFixCluster | kFixClusterSure);  // test hook
+    // the warm start needs a fixpoint kernel that takes it (the many-CTA one
+    // always starts from the sources)
+    const bool warm = warm_start_used(ds, f);
+    // one kernel sets every per-compute start value (out-degrees, cursors,
+    // the source columns of the bit matrix, counters, estimates)
+    {
+        DevScene arg = ds;
+        arg.warm = warm ? 1 : 0;
+        const long long items = std::max<long long>(
+            ds.n_gen + 1, ds.st_start ? (long long)ds.n_vert * ((ds.n_src + 31) / 32) : 0);
+        k_vertex_prep<<<(int)std::max(1LL, std::min((items + 255) / 256, 152LL * 4)), 256, 0, st>>>(arg);
+    }
     if (ds.n_vert > 0) {
         const size_t bytes = sizeof(uint32_t) * (size_t)ds.n_vert * ds.vis_words;
         // the obstacle-vertex pairs come from the scene's static bits; the
-        // pair kernel then tests the source columns only
-        if (ds.st_start)  // kept edge lists: only the source columns are read, and they start empty
-            cudaMemset2DAsync(ds.vis_bits, sizeof(uint32_t) * ds.vis_words, 0, sizeof(uint32_t) * ((ds.n_src + 31) / 32),
-                              ds.n_vert, st);
-        else if (ds.vis_static) cudaMemcpyAsync(ds.vis_bits, ds.vis_static, bytes, cudaMemcpyDeviceToDevice, st);
-        else cudaMemsetAsync(ds.vis_bits, 0, bytes, st);
-        launch_pairs(ds, st);
+        // pair kernel then tests the source columns only (with kept edge
+        // lists only they are read: the prep kernel cleared them)
+        if (!ds.st_start) {
+            if (ds.vis_static) cudaMemcpyAsync(ds.vis_bits, ds.vis_static, bytes, cudaMemcpyDeviceToDevice, st);
+            else cudaMemsetAsync(ds.vis_bits, 0, bytes, st);
+        }
+        launch_pairs(ds, st, false);
         const int eb = (ds.n_vert + 7) / 8;  // one warp per row
         k_edges_count<<<eb, 256, 0, st>>>(ds);
         k_edges_scan<<<1, 1024, 0, st>>>(ds);
@@ -1919,15 +1956,9 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
     // each fixpoint kernel checks on the device whether the graph is its
     // own; the scene's bounds on the edge count skip the launches that
     // cannot apply
-    int f = ds.fix_launch;
-    if (g_many_cta_override.load() && !(f & kFixSoloSure)) f &= ~(kFixCluster | kFixClusterSure);  // test hook
-    // the warm start needs a fixpoint kernel that takes it (the many-CTA one
-    // always starts from the sources)
-    arg.warm = warm_start_used(ds, f) ? 1 : 0;
+    arg.warm = warm ? 1 : 0;
     if (arg.warm) {
         const int vb = (ds.n_vert + 255) / 256;
-        cudaMemsetAsync(ds.warm_est, 0x7f, sizeof(double) * ds.n_vert, st);  // 1.4e306: no estimate yet
-        cudaMemsetAsync(ds.counters + 6, 0, sizeof(int32_t), st);
         k_warm_entry<<<dim3(vb, (ds.n_vert + kEntryRows - 1) / kEntryRows), 256, 0, st>>>(arg);
         const int gb = (ds.n_vert * kWarmGrp + 255) / 256;
         k_warm_tree<<<gb, 256, 0, st>>>(arg);
@@ -1936,10 +1967,10 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
     }
     if (f & kFixSolo) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(arg, max_rounds);
     if (f & kFixCluster) k_sssp_cluster<<<kClCtas, kClThreads, kClSmem, st>>>(arg, max_rounds);
-    else if (!(f & kFixSoloSure)) cudaMemsetAsync(ds.counters + 4, 0, sizeof(int32_t), st);
-    if (!(f & (kFixSoloSure | kFixClusterSure)))
+    if (!(f & (kFixSoloSure | kFixClusterSure))) {
         cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
-    k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
+        k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
+    }
 }
 
 int solo_smem_bytes() {
