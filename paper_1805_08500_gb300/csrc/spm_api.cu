@@ -572,12 +572,13 @@ static spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t 
     s->ds.static_lists = side && s->ds.static_tile_start ? 1 : 0;  // the pixel pass reads the kept lists too
     NvtxRange range_all("spm_compute");
     if (timed) cudaEventRecord(s->ev[0], cs);
-    // the side flood forks once the visibility graph is built and is
-    // submitted after the fixpoint kernel, so that the single-CTA fixpoint
-    // gets its SM first and the flood fills the others while it runs
+    // the geometric flood needs nothing from the vertex phase (costs and
+    // cones are applied by the pixel pass): it forks at the start and runs
+    // beside the whole vertex chain
+    if (side) cudaEventRecord(s->fork, cs);
     {
         NvtxRange r("spm vertex phase");
-        spm::launch_vertex_phase(s->ds, cs, side ? s->fork : nullptr);
+        spm::launch_vertex_phase(s->ds, cs);
     }
     if (side) {
         NvtxRange r("spm flood (side stream)");

@@ -233,8 +233,8 @@ struct BatchDev {
 };
 
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
-// vertex phase; graph_done (optional) is recorded once the visibility graph is built
-void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done = nullptr);
+// vertex phase (visibility graph, fixpoint, finalised generator table)
+void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
 // pixel kernel over the tiles of tile rows [tile_row0, tile_row1)
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1);

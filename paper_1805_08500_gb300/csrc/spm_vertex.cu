@@ -34,6 +34,20 @@
 #include "spm_device.cuh"
 #include "spm_internal.h"
 
+namespace spm {
+// Programmatic dependent launch along the vertex phase's chain of small
+// kernels: a kernel launched with programmatic stream serialization may be
+// scheduled while its predecessor in the stream still runs. Each chain
+// kernel first lets its own successor be scheduled (launch_dependents), then
+// waits (griddepcontrol.wait) until its predecessor has completed and that
+// grid's memory is visible, before it reads anything. Launched the ordinary
+// way, both instructions do nothing.
+__device__ __forceinline__ void chain_start() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+}  // namespace spm
+
 namespace cg = cooperative_groups;
 
 namespace spm {
@@ -247,6 +261,7 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, int chu
 
 __global__ void __launch_bounds__(kVisThreads) k_vis_pairs(const __grid_constant__ DevScene ds, int chunk) {
     __shared__ PairQ q;
+    chain_start();
     vis_pairs_run(
         q, (long long)ds.n_vert * ds.pair_words, chunk, reinterpret_cast<unsigned long long *>(ds.stats + 2),
         [&](int) { return &ds; },
@@ -285,6 +300,7 @@ __device__ __forceinline__ void edges_count_row(const DevScene &ds, int vv, int 
 }
 
 __global__ void k_edges_count(const __grid_constant__ DevScene ds) {
+    chain_start();
     const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
     for (int vv = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vv < ds.n_vert; vv += nw)
         edges_count_row(ds, vv, lane);
@@ -316,6 +332,7 @@ __device__ __forceinline__ void edges_scan_block(const DevScene &ds, long long *
 
 __global__ void __launch_bounds__(1024) k_edges_scan(const __grid_constant__ DevScene ds) {
     __shared__ long long part[32];
+    chain_start();
     edges_scan_block(ds, part);
 }
 
@@ -380,6 +397,7 @@ __device__ __forceinline__ void edges_out_copy(const DevScene &ds, int uu, int l
 }
 
 __global__ void k_edges_fill(const __grid_constant__ DevScene ds) {
+    chain_start();
     if (ds.in_start[ds.n_vert] > ds.edge_cap) return;
     const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
     for (int vv = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vv < ds.n_vert; vv += nw)
@@ -640,6 +658,7 @@ __device__ __forceinline__ void narrow_ids(unsigned short *dst, const int32_t *s
 
 __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    chain_start();
 #ifdef SPM_COUNT
     const long long t_start = clock64();
 #endif
@@ -1145,6 +1164,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
 __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
     k_sssp_cluster(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    chain_start();
     __shared__ ClShared sh;
     cg::cluster_group cluster = cg::this_cluster();
     bool solo_len;
@@ -1420,6 +1440,7 @@ int fixpoint_round_cap(int n_gen) {
 // cluster kernel's done flag and, for a warm start, the estimates (a huge
 // value: none yet) and the count of unsatisfied vertices.
 __global__ void k_vertex_prep(const __grid_constant__ DevScene ds) {
+    chain_start();
     const int sw = (ds.n_src + 31) / 32;
     const long long n_bits = ds.st_start ? (long long)ds.n_vert * sw : 0;
     const long long items = max((long long)ds.n_gen + 1, n_bits);
@@ -1436,6 +1457,28 @@ __global__ void k_vertex_prep(const __grid_constant__ DevScene ds) {
     }
 }
 
+// Launches a kernel of the vertex phase's chain with programmatic stream
+// serialization (it may be scheduled while its predecessor runs and waits
+// for it in chain_start); an ordinary launch if the attribute is refused.
+template <typename... KArgs, typename... Args>
+static void launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                           Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, args...) != cudaSuccess) {
+        cudaGetLastError();
+        kern<<<grid, block, smem, st>>>(args...);
+    }
+}
+
 void launch_pairs(const DevScene &ds, cudaStream_t st, bool reset_counter = true) {
     const long long tasks = (long long)ds.n_vert * ds.pair_words;
     if (reset_counter) cudaMemsetAsync(ds.stats + 2, 0, sizeof(unsigned long long), st);  // the pair kernel's work counter
@@ -1445,7 +1488,7 @@ void launch_pairs(const DevScene &ds, cudaStream_t st, bool reset_counter = true
     blocks = blocks > resident ? resident : blocks;
     const long long per_chunk = tasks / (blocks * (kVisThreads / 32) * 2);
     const int chunk = (int)(per_chunk < 1 ? 1 : (per_chunk > 32 ? 32 : per_chunk));
-    k_vis_pairs<<<(int)blocks, kVisThreads, 0, st>>>(ds, chunk);
+    launch_chained(k_vis_pairs, dim3((int)blocks), dim3(kVisThreads), 0, st, ds, chunk);
 }
 
 void launch_vis_static(const DevScene &ds, cudaStream_t st, uint32_t *vis_static) {
@@ -1613,6 +1656,7 @@ __global__ void __launch_bounds__(32 * kVtabWarps) k_vtab_build(const __grid_con
 // atomic minima.
 constexpr int kEntryRows = 128;
 __global__ void __launch_bounds__(256) k_warm_entry(const __grid_constant__ DevScene ds) {
+    chain_start();
     __shared__ int eu[kEntryRows];
     __shared__ double em[kEntryRows];
     __shared__ int ne;
@@ -1649,6 +1693,7 @@ __global__ void __launch_bounds__(256) k_warm_entry(const __grid_constant__ DevS
 // minimum across the group.
 constexpr int kWarmGrp = 8;
 __global__ void __launch_bounds__(256) k_warm_tree(const __grid_constant__ DevScene ds) {
+    chain_start();
     const int t = blockIdx.x * 256 + threadIdx.x, vv = t / kWarmGrp, gl = t % kWarmGrp;
     const bool act = vv < ds.n_vert;  // every lane reaches the shuffles
     const int ns = ds.n_src;
@@ -1690,6 +1735,7 @@ __global__ void __launch_bounds__(256) k_warm_tree(const __grid_constant__ DevSc
 // ds.counters[6]): they are the fixpoint's first round; every other vertex
 // already satisfies its equation.
 __global__ void __launch_bounds__(256) k_warm_verify(const __grid_constant__ DevScene ds) {
+    chain_start();
     const int t = blockIdx.x * 256 + threadIdx.x, vv = t / kWarmGrp, gl = t % kWarmGrp;
     const bool act = vv < ds.n_vert;  // every lane reaches the shuffles
     const int ns = ds.n_src, v = ns + (act ? vv : 0);
@@ -1745,6 +1791,7 @@ __host__ __device__ __forceinline__ size_t fold_bytes(int n) {
 // are left unreached, as are the ones hanging from it.
 __global__ void __launch_bounds__(kFoldThreads) k_warm_fold(const __grid_constant__ DevScene ds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    chain_start();
     __shared__ long long wsum[32];
     __shared__ int s_maxd;
     const int n = ds.n_gen, ns = ds.n_src, tid = threadIdx.x, lane = tid & 31;
@@ -1917,7 +1964,7 @@ cudaError_t launch_vtab_build(const DevScene &ds, double *tab, int32_t *counter,
     return cudaGetLastError();
 }
 
-void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_done) {
+void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
     int f = ds.fix_launch;
     if (g_many_cta_override.load() && !(f & kFixSoloSure)) f &= ~(kFixCluster | kFixClusterSure);  // test hook
     // the warm start needs a fixpoint kernel that takes it (the many-CTA one
@@ -1943,13 +1990,12 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
         }
         launch_pairs(ds, st, false);
         const int eb = (ds.n_vert + 7) / 8;  // one warp per row
-        k_edges_count<<<eb, 256, 0, st>>>(ds);
-        k_edges_scan<<<1, 1024, 0, st>>>(ds);
-        k_edges_fill<<<eb, 256, 0, st>>>(ds);
+        launch_chained(k_edges_count, dim3(eb), dim3(256), 0, st, ds);
+        launch_chained(k_edges_scan, dim3(1), dim3(1024), 0, st, ds);
+        launch_chained(k_edges_fill, dim3(eb), dim3(256), 0, st, ds);
     } else {
         cudaMemsetAsync(ds.in_start, 0, sizeof(int32_t) * (ds.n_vert + 1), st);
     }
-    if (graph_done) cudaEventRecord(graph_done, st);  // the visibility graph is built
     DevScene arg = ds;
     int max_rounds = fixpoint_round_cap(ds.n_gen);
     void *args[] = {&arg, &max_rounds};
@@ -1959,14 +2005,14 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st, cudaEvent_t graph_
     arg.warm = warm ? 1 : 0;
     if (arg.warm) {
         const int vb = (ds.n_vert + 255) / 256;
-        k_warm_entry<<<dim3(vb, (ds.n_vert + kEntryRows - 1) / kEntryRows), 256, 0, st>>>(arg);
+        launch_chained(k_warm_entry, dim3(vb, (ds.n_vert + kEntryRows - 1) / kEntryRows), dim3(256), 0, st, arg);
         const int gb = (ds.n_vert * kWarmGrp + 255) / 256;
-        k_warm_tree<<<gb, 256, 0, st>>>(arg);
-        k_warm_fold<<<1, kFoldThreads, fold_bytes(ds.n_gen), st>>>(arg);
-        k_warm_verify<<<gb, 256, 0, st>>>(arg);
+        launch_chained(k_warm_tree, dim3(gb), dim3(256), 0, st, arg);
+        launch_chained(k_warm_fold, dim3(1), dim3(kFoldThreads), fold_bytes(ds.n_gen), st, arg);
+        launch_chained(k_warm_verify, dim3(gb), dim3(256), 0, st, arg);
     }
-    if (f & kFixSolo) k_sssp_solo<<<1, kSoloThreads, ds.solo_smem, st>>>(arg, max_rounds);
-    if (f & kFixCluster) k_sssp_cluster<<<kClCtas, kClThreads, kClSmem, st>>>(arg, max_rounds);
+    if (f & kFixSolo) launch_chained(k_sssp_solo, dim3(1), dim3(kSoloThreads), (size_t)ds.solo_smem, st, arg, max_rounds);
+    if (f & kFixCluster) launch_chained(k_sssp_cluster, dim3(kClCtas), dim3(kClThreads), (size_t)kClSmem, st, arg, max_rounds);
     if (!(f & (kFixSoloSure | kFixClusterSure))) {
         cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
         k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
