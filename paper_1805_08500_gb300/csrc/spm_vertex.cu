@@ -904,18 +904,18 @@ constexpr int kClSmem = 200 * 1024; // dynamic shared memory per CTA
 // offsets every CTA shares, then the CTA's own in-lists (with their FP64
 // lengths when they fit; else the lengths are read from global memory).
 struct ClLayout {
-    size_t cost, wedge, par, lat, dirty, dl, lin_start, lin_src, lin_len, end;
+    size_t cost, wedge, par, lat, chg, dl, lin_start, lin_src, lin_len, end;
 };
 __host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own, bool with_len) {
     auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    const int nmax = (nv + kClCtas - 1) / kClCtas, dw = (nmax + 31) / 32;
+    const int nmax = (nv + kClCtas - 1) / kClCtas;
     ClLayout L;
     L.cost = 0;
     L.wedge = L.cost + up(8 * (size_t)n);
     L.par = L.wedge + up(8 * (size_t)n);
     L.lat = L.par + up(2 * (size_t)n);
-    L.dirty = L.lat + up(4 * (size_t)n);
-    L.dl = L.dirty + up(4 * 2 * (size_t)dw);
+    L.chg = L.lat + up(4 * (size_t)n);
+    L.dl = L.chg + up(4 * 2 * (((size_t)n + 31) / 32));
     L.lin_start = L.dl + up(2 * 2 * (size_t)nmax);
     L.lin_src = L.lin_start + up(4 * ((size_t)nmax + 1));
     L.lin_len = L.lin_src + up(2 * (size_t)e_own);
@@ -957,7 +957,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     }
     const long long E = ds.in_start[nv];
     if (n >= 32768 || E > ds.edge_cap) return false;
-    const int C = kClCtas, nmax = (nv + C - 1) / C, dw = (nmax + 31) / 32;
+    const int C = kClCtas, nmax = (nv + C - 1) / C;
     const int n_own = rank < nv ? (nv - rank + C - 1) / C : 0;  // vertices vv = rank + C * k
     // this CTA's in-list offsets: a scan over its vertices, in chunks
     const int per = (n_own + kClThreads - 1) / kClThreads, lo = min(n_own, tid * per), hi = min(n_own, lo + per);
@@ -985,7 +985,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     short4 *wedge = (short4 *)(sm_raw + L.wedge);
     short *par = (short *)(sm_raw + L.par);
     short2 *lat = (short2 *)(sm_raw + L.lat);
-    unsigned *dirty = (unsigned *)(sm_raw + L.dirty);          // round parity p at p * dw
+    unsigned *chg = (unsigned *)(sm_raw + L.chg);              // changed generators, round parity p at p * cw
     unsigned short *dl = (unsigned short *)(sm_raw + L.dl);    // round parity p at p * nmax
     int *lin_start = (int *)(sm_raw + L.lin_start);
     unsigned short *lin_src = (unsigned short *)(sm_raw + L.lin_src);
@@ -1009,7 +1009,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
         const int4 w = ds.gen_wedge[g];
         wedge[g] = make_short4((short)w.x, (short)w.y, (short)w.z, (short)w.w);
     }
-    for (int w = tid; w < 2 * dw; w += kClThreads) dirty[w] = 0u;
+    for (int w = tid; w < 2 * ((n + 31) / 32); w += kClThreads) chg[w] = 0u;
     for (int g = tid; g < min(ns, kSoloSrc); g += kClThreads) {
         const int k = ds.gen_kind[g];
         sh.src_kind[g] = (signed char)k;
@@ -1028,49 +1028,51 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     constexpr int kGpw = 32 / kClGrp;
     const int grp = lane / kClGrp, gl = lane % kClGrp, ngroups = nwarps * kGpw;
     const unsigned kFull = 0xffffffffu;
-    // mark vertex w (a generator id >= ns) dirty in round parity par_n of its owner
-    auto mark = [&](int w, int par_n, int cslot) {
-        const int vv = w - ns, owner = vv % C, lw = vv / C;
-        const unsigned bit = 1u << (lw & 31);
-        unsigned *rd = cluster.map_shared_rank(dirty, owner) + par_n * dw + (lw >> 5);
-        if (!(atomicOr(rd, bit) & bit)) {
-            const int slot = atomicAdd(cluster.map_shared_rank(&sh.cnt[cslot], owner), 1);
-            cluster.map_shared_rank(dl, owner)[par_n * nmax + slot] = (unsigned short)lw;
-        }
-    };
+    // A round's changes are broadcast as bits: a changed vertex sets its bit
+    // in every CTA's bitmap of the round's parity (remote ORs whose result
+    // nobody waits for), so after the cluster barrier every CTA holds the
+    // same set of changed generators and finds its own dirty vertices --
+    // those with a changed in-neighbour -- by scanning its in-lists locally.
+    const int cw = (n + 31) / 32;
     if (ds.warm) {  // round 0 pulls the vertices whose equation the tree's state breaks; each CTA its own
         const int m = min(ds.counters[6], nv);
         for (int i = tid; i < m; i += kClThreads) {
             const int vv = ds.dirtyl[0][i] - ns;
-            if (vv % C != rank) continue;
-            const int lw = vv / C;
-            atomicOr(&dirty[lw >> 5], 1u << (lw & 31));
-            dl[atomicAdd(&sh.cnt[0], 1)] = (unsigned short)lw;
+            if (vv % C == rank) dl[atomicAdd(&sh.cnt[0], 1)] = (unsigned short)(vv / C);
         }
-    } else {  // the sources mark their out-neighbours for round 0
-        for (int u = rank * ngroups + warp * kGpw + grp; u < ns; u += C * ngroups)
-            for (int e = ds.out_start[u] + gl; e < ds.out_start[u + 1]; e += kClGrp) mark(ds.out_dst[e], 0, 0);
+    } else {  // round 0 pulls the vertices with a source in-neighbour: the sources count as changed
+        for (int g = tid; g < ns; g += kClThreads) atomicOr(&chg[g >> 5], 1u << (g & 31));
     }
-    cluster.sync();
+    __syncthreads();
     int round = 0;
     for (;; ++round) {
         const int cur = round & 1, nxt = cur ^ 1;
-        if (warp == 0) {  // dirty vertices in the whole cluster this round
-            int t = lane < C ? *cluster.map_shared_rank(&sh.cnt[round % 3], lane) : 0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-            if (lane == 0) sh.total = t;
+        unsigned *chc = chg + cur * cw;  // changed in the last round (the same bits in every CTA)
+        if (round > 0 || !ds.warm) {
+            int any = 0;
+            for (int w = tid; w < cw; w += kClThreads) any |= chc[w] != 0u;
+            if (!__syncthreads_or(any)) break;  // no change anywhere: every CTA stops here
+            if (round >= max_rounds) {
+                if (rank == 0 && tid == 0) atomicOr(ds.status, kStNotConverged);
+                break;
+            }
+            for (int k0 = warp * kGpw; k0 < n_own; k0 += ngroups) {  // warp-uniform trip count
+                const int k = k0 + grp;
+                bool hit = false;
+                if (k < n_own)
+                    for (int e = lin_start[k] + gl, e1 = lin_start[k + 1]; e < e1 && !hit; e += kClGrp) {
+                        const int u = lin_src[e];
+                        hit = (chc[u >> 5] >> (u & 31)) & 1u;
+                    }
+                const unsigned bal = __ballot_sync(kFull, hit);
+                if (gl == 0 && ((bal >> (grp * kClGrp)) & ((1u << kClGrp) - 1u)))
+                    dl[cur * nmax + atomicAdd(&sh.cnt[cur], 1)] = (unsigned short)k;
+            }
+            __syncthreads();
+            // read: free again (this round's changes go to the other parity)
+            for (int w = tid; w < cw; w += kClThreads) chc[w] = 0u;
         }
-        __syncthreads();
-        const int total = sh.total;
-        if (total == 0) break;
-        if (round >= max_rounds) {
-            if (rank == 0 && tid == 0) atomicOr(ds.status, kStNotConverged);
-            break;
-        }
-        const int nd = sh.cnt[round % 3];
-        if (tid == 0) sh.cnt[(round + 2) % 3] = 0;  // read last round, marked into next round
-        const int cslot = (round + 1) % 3;
+        const int nd = sh.cnt[cur];
         for (int i0 = warp * kGpw; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
@@ -1122,15 +1124,13 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
                 }
             }
             const bool changed = act && (best != cv || bpar != pv);
-            if (changed && gl < C) {  // lane gl writes CTA gl's copy
+            if (changed && gl < C) {  // lane gl writes CTA gl's copy and its changed bit
                 cluster.map_shared_rank(cost, gl)[v] = __longlong_as_double(best);
                 cluster.map_shared_rank(par, gl)[v] = (short)bpar;
+                atomicOr(cluster.map_shared_rank(chg, gl) + nxt * cw + (v >> 5), 1u << (v & 31));
             }
-            if (changed)
-                for (int e = ds.out_start[v] + gl; e < ds.out_start[v + 1]; e += kClGrp) mark(ds.out_dst[e], nxt, cslot);
         }
-        // this round's bitmap is free again (marks went to the other one)
-        for (int w = kClThreads - 1 - tid; w < dw; w += kClThreads) dirty[cur * dw + w] = 0u;
+        if (tid == 0) sh.cnt[nxt] = 0;  // the next round's list (last read two rounds ago)
         cluster.sync();
     }
     cluster.sync();  // the last round's remote reads of the counts are done
