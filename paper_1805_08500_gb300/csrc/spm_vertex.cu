@@ -941,6 +941,9 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
                          unsigned char *sm_raw) {
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kClThreads / 32;
+#ifdef SPM_COUNT
+    const long long t_cl0 = clock64();
+#endif
     const int n = ds.n_gen, nv = ds.n_vert, ns = ds.n_src;
     if (nv == 0) {  // sources only: nothing to relax
         if (rank == 0) {
@@ -1044,6 +1047,10 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
         for (int g = tid; g < ns; g += kClThreads) atomicOr(&chg[g >> 5], 1u << (g & 31));
     }
     __syncthreads();
+#ifdef SPM_COUNT
+    const long long t_cl1 = clock64();
+    if (rank == 0 && tid == 0) SPM_CNT(17, t_cl1 - t_cl0);  // prologue: layout checks, state and in-lists staged
+#endif
     int round = 0;
     for (;; ++round) {
         const int cur = round & 1, nxt = cur ^ 1;
@@ -1133,6 +1140,12 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
         if (tid == 0) sh.cnt[nxt] = 0;  // the next round's list (last read two rounds ago)
         cluster.sync();
     }
+#ifdef SPM_COUNT
+    if (rank == 0 && tid == 0) {
+        SPM_CNT(18, clock64() - t_cl1);  // the rounds
+        SPM_CNT(19, round);
+    }
+#endif
     cluster.sync();  // the last round's remote reads of the counts are done
     // the settled state of this CTA's vertices (and, in CTA 0, the sources),
     // with each vertex's shadow cone from its parent
