@@ -204,7 +204,38 @@ __device__ float tile_lower_bound(const DevScene &ds, int g, int4 box, float4 fb
 }
 
 // Bitonic sort of (lb, id) pairs, n padded to a power of two with +inf.
+// Up to 32 pairs (nearly every tile) are sorted by the first warp in
+// registers with shuffles, a network of the next power of two above n; the
+// CTA waits once.
 __device__ void sort_candidates(PixSmem &sm, int n) {
+    if (n <= 32) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            float lb = lane < n ? sm.cand_lb[lane] : INFINITY;
+            int id = lane < n ? sm.cand_id[lane] : 0x7fffffff;
+            int P = 1;
+            while (P < n) P <<= 1;
+            for (int k = 2; k <= P; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const float olb = __shfl_xor_sync(0xffffffffu, lb, j);
+                    const int oid = __shfl_xor_sync(0xffffffffu, id, j);
+                    // the lower lane of a pair keeps the smaller key in an
+                    // ascending run ((lane & k) == 0), the larger otherwise
+                    const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+                    const bool o_less = olb < lb || (olb == lb && oid < id);
+                    if (o_less == (lower == up)) {
+                        lb = olb;
+                        id = oid;
+                    }
+                }
+            if (lane < n) {
+                sm.cand_lb[lane] = lb;
+                sm.cand_id[lane] = id;
+            }
+        }
+        __syncthreads();
+        return;
+    }
     int P = 1;
     while (P < n) P <<= 1;
     for (int i = n + threadIdx.x; i < P; i += NT) {
