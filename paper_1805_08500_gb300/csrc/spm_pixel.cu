@@ -203,39 +203,9 @@ __device__ float tile_lower_bound(const DevScene &ds, int g, int4 box, float4 fb
     return (cf + sqrtf(dx * dx + dy * dy)) * 0.999999f;
 }
 
-// Bitonic sort of (lb, id) pairs, n padded to a power of two with +inf.
-// Up to 32 pairs (nearly every tile) are sorted by the first warp in
-// registers with shuffles, a network of the next power of two above n; the
-// CTA waits once.
+// Bitonic sort of (lb, id) pairs, n padded to a power of two with +inf
+// (lists of more than 32; shorter ones take sort_small_warp).
 __device__ void sort_candidates(PixSmem &sm, int n) {
-    if (n <= 32) {
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            float lb = lane < n ? sm.cand_lb[lane] : INFINITY;
-            int id = lane < n ? sm.cand_id[lane] : 0x7fffffff;
-            int P = 1;
-            while (P < n) P <<= 1;
-            for (int k = 2; k <= P; k <<= 1)
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    const float olb = __shfl_xor_sync(0xffffffffu, lb, j);
-                    const int oid = __shfl_xor_sync(0xffffffffu, id, j);
-                    // the lower lane of a pair keeps the smaller key in an
-                    // ascending run ((lane & k) == 0), the larger otherwise
-                    const bool lower = (lane & j) == 0, up = (lane & k) == 0;
-                    const bool o_less = olb < lb || (olb == lb && oid < id);
-                    if (o_less == (lower == up)) {
-                        lb = olb;
-                        id = oid;
-                    }
-                }
-            if (lane < n) {
-                sm.cand_lb[lane] = lb;
-                sm.cand_id[lane] = id;
-            }
-        }
-        __syncthreads();
-        return;
-    }
     int P = 1;
     while (P < n) P <<= 1;
     for (int i = n + threadIdx.x; i < P; i += NT) {
@@ -260,6 +230,54 @@ __device__ void sort_candidates(PixSmem &sm, int n) {
             }
             __syncthreads();
         }
+}
+
+// The generator data the candidate loop reads, staged in shared memory.
+template <bool MAPS>
+__device__ __forceinline__ CandRec stage_candidate(const DevScene &ds, int g) {
+    CandRec r;
+    r.kind = ds.gen_kind[g];
+    r.cf = ds.gen_costf[g];
+    r.lat = ds.gen_lat[g];
+    r.pos = ds.gen_pos[g];
+    r.ctype = r.kind == kVert ? ds.gen_ctype[g] : kConeNone;
+    r.cone = r.kind == kVert ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
+    r.map_ok = MAPS && ds.gen_map_ok ? ds.gen_map_ok[g] : 0;
+    return r;
+}
+
+// Up to 32 (lb, id) pairs, nearly every tile's list, sorted by the first warp
+// in registers with shuffles (a bitonic network of the next power of two
+// above n), each lane then staging its candidate's generator data; the CTA
+// waits once.
+template <bool MAPS>
+__device__ void sort_small_warp(const DevScene &ds, PixSmem &sm, int n) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        float lb = lane < n ? sm.cand_lb[lane] : INFINITY;
+        int id = lane < n ? sm.cand_id[lane] : 0x7fffffff;
+        int P = 1;
+        while (P < n) P <<= 1;
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const float olb = __shfl_xor_sync(0xffffffffu, lb, j);
+                const int oid = __shfl_xor_sync(0xffffffffu, id, j);
+                // the lower lane of a pair keeps the smaller key in an
+                // ascending run ((lane & k) == 0), the larger otherwise
+                const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+                const bool o_less = olb < lb || (olb == lb && oid < id);
+                if (o_less == (lower == up)) {
+                    lb = olb;
+                    id = oid;
+                }
+            }
+        if (lane < n) {
+            sm.cand_lb[lane] = lb;
+            sm.cand_id[lane] = id;
+            sm.rec[lane] = stage_candidate<MAPS>(ds, id);  // kStage >= 32
+        }
+    }
+    __syncthreads();
 }
 
 // Conservative bin enumeration for the thick segment c->t (lattice units,
@@ -421,20 +439,14 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
         const int nc = sm.n_cand;
         const bool last = g0 + NT >= ntotal;
         if (nc > kCandCap - NT || (last && nc > 0)) {
-            sort_candidates(sm, nc);
-            for (int t = threadIdx.x; t < min(nc, kStage); t += NT) {
-                const int g = sm.cand_id[t];
-                CandRec r;
-                r.kind = ds.gen_kind[g];
-                r.cf = ds.gen_costf[g];
-                r.lat = ds.gen_lat[g];
-                r.pos = ds.gen_pos[g];
-                r.ctype = r.kind == kVert ? ds.gen_ctype[g] : kConeNone;
-                r.cone = r.kind == kVert ? ds.gen_cone[g] : make_int4(0, 0, 0, 0);
-                r.map_ok = MAPS && ds.gen_map_ok ? ds.gen_map_ok[g] : 0;
-                sm.rec[t] = r;
+            static_assert(kStage >= 32, "a warp-sorted list is staged whole");
+            if (nc <= 32) {
+                sort_small_warp<MAPS>(ds, sm, nc);
+            } else {
+                sort_candidates(sm, nc);
+                for (int t = threadIdx.x; t < min(nc, kStage); t += NT) sm.rec[t] = stage_candidate<MAPS>(ds, sm.cand_id[t]);
+                __syncthreads();
             }
-            __syncthreads();
             SPM_LAP(2);
             if (threadIdx.x == 0) SPM_CNT(1, nc);
             bool done = false;
@@ -450,20 +462,20 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                     break;
                 }
                 SPM_LAP(3);
-                if (c == tested) {  // hidden-tile test for the next chunk, in parallel
+                // flooded lists were already tested on the whole tile area:
+                // no hidden-tile tests (nor their barriers) with lists
+                if (!lists && c == tested) {  // hidden-tile test for the next chunk, in parallel
                     const int cc = c + threadIdx.x;
                     if (threadIdx.x < chunk && cc < nc) {
                         SPM_CNT(2, 1);
                         const int g2 = sm.cand_id[cc];
-                        // flooded lists were already tested on the whole tile area
-                        sm.hidden[cc] = !lists && ds.gen_kind[g2] != kSegI &&
-                                        box_hidden(ds, ds.gen_lat[g2], box, bcx, bcy, brad);
+                        sm.hidden[cc] = ds.gen_kind[g2] != kSegI && box_hidden(ds, ds.gen_lat[g2], box, bcx, bcy, brad);
                     }
                     tested += chunk;
                     chunk = min(2 * chunk, NT);  // most tiles exit within the first chunk
                     __syncthreads();
                 }
-                if (sm.hidden[c]) {
+                if (!lists && sm.hidden[c]) {
                     if (threadIdx.x == 0) SPM_CNT(3, 1);
                     continue;
                 }
@@ -630,20 +642,23 @@ __device__ __forceinline__ void pixel_tile(const DevScene &ds, const int tile, f
                 __syncthreads();
                 SPM_LAP(6);
             }
-            // tile upper bound for candidate pruning: worst best over live pixels
-            float worst = 0.f;
+            // tile upper bound for the next batch's candidate pruning (worst
+            // best over live pixels); after the last batch nothing reads it
+            if (!last) {
+                float worst = 0.f;
 #pragma unroll
-            for (int k = 0; k < PX; ++k)
-                if ((live >> k) & 1u) worst = fmaxf(worst, key_dist(key[k]));
-            for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                sm.n_cand = 0;
-                sm.tile_ub = 0.f;
+                for (int k = 0; k < PX; ++k)
+                    if ((live >> k) & 1u) worst = fmaxf(worst, key_dist(key[k]));
+                for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    sm.n_cand = 0;
+                    sm.tile_ub = 0.f;
+                }
+                __syncthreads();
+                if ((threadIdx.x & 31) == 0) atomicMax((int *)&sm.tile_ub, __float_as_int(worst));
+                __syncthreads();
             }
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) atomicMax((int *)&sm.tile_ub, __float_as_int(worst));
-            __syncthreads();
         }
     }
 
