@@ -37,18 +37,17 @@ FALLBACK_HBM_GBS = 6800.0
 # FP32 lanes per SM x SMs x 2 flops per FMA; clock from the measured peaks file
 FP32_LANES, N_SMS = 128, 152
 FLOPS_PER_PIXEL = 7  # winning-generator distance: 2 sub, mul, fma(2), sqrt, add
-# One pixel-kernel launch per workload, from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, smsp__issue_active and the ALU / FMA pipe shares;
-# single-pass captures of a full-size launch for the maze and the batch, the
-# full-section capture for the polygon scene) and from the instrumentation
-# build's work counters (orientation tests and exact polygon tests per
-# pixel); valid for those workloads and that kernel version only
-# (re-captured after a change).
-KPIXELS_TRAFFIC = {"maze4096": 104_104_960, "batched256": 1_309_082_368, "polys1024": 12_415_488}
-KPIXELS_UTIL = {"maze4096": {"issue_frac": 0.444, "alu_pipe_frac": 0.311, "fma_pipe_frac": 0.128,
+# One pixel-kernel launch per workload, from a single-pass ncu capture of a
+# full-size launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# smsp__issue_active and the ALU / FMA pipe shares; the first timed step,
+# right after the L2 flush) and from the instrumentation build's work
+# counters (orientation tests and exact polygon tests per pixel); valid for
+# those workloads and that kernel version only (re-captured after a change).
+KPIXELS_TRAFFIC = {"maze4096": 104_169_728, "batched256": 1_310_612_480, "polys1024": 6_548_736}
+KPIXELS_UTIL = {"maze4096": {"issue_frac": 0.437, "alu_pipe_frac": 0.304, "fma_pipe_frac": 0.131,
                              "orient_per_px": 0.254, "exact_tests_per_px": 0.0636},
-                "batched256": {"issue_frac": 0.416, "alu_pipe_frac": 0.289, "fma_pipe_frac": 0.123},
-                "polys1024": {"issue_frac": 0.460, "alu_pipe_frac": 0.307, "fma_pipe_frac": 0.110,
+                "batched256": {"issue_frac": 0.414, "alu_pipe_frac": 0.289, "fma_pipe_frac": 0.123},
+                "polys1024": {"issue_frac": 0.452, "alu_pipe_frac": 0.296, "fma_pipe_frac": 0.117,
                               "orient_per_px": 0.360, "exact_tests_per_px": 0.0611}}
 
 
