@@ -310,9 +310,11 @@ spm_status spm_agents_backward_noalloc(spm_scene *scene, void *stream,
  * milliseconds, from CUDA events the library records between them on the
  * compute stream (not recorded while the stream is being captured into a
  * CUDA graph): vertex_ms = vertex-cost fixpoint (Sec. 3.1 Procedures 1, 2
- * and 4), cull_ms = per-tile candidate lists (the flood, 0 when the scene
- * scans every generator), pixel_ms = the pixel kernel (Procedure 3).
- * Waits for the compute. */
+ * and 4), cull_ms = the per-tile candidate lists after the vertex phase (the
+ * flood; in flood mode 3 it runs beside the vertex phase from the start of
+ * the compute, so only the part that outlasts the vertex phase counts; 0
+ * when the scene scans every generator), pixel_ms = the pixel kernel
+ * (Procedure 3). Waits for the compute. */
 spm_status spm_scene_phase_ms(spm_scene *scene, float *vertex_ms, float *cull_ms,
                               float *pixel_ms);
 
