@@ -904,7 +904,7 @@ constexpr int kClSmem = 200 * 1024; // dynamic shared memory per CTA
 // offsets every CTA shares, then the CTA's own in-lists (with their FP64
 // lengths when they fit; else the lengths are read from global memory).
 struct ClLayout {
-    size_t cost, wedge, par, lat, chg, dl, lin_start, lin_src, lin_len, end;
+    size_t cost, wedge, par, lat, ldir, chg, dl, lin_start, lin_src, lin_len, end;
 };
 __host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own, bool with_len) {
     auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
@@ -914,7 +914,8 @@ __host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long 
     L.wedge = L.cost + up(8 * (size_t)n);
     L.par = L.wedge + up(8 * (size_t)n);
     L.lat = L.par + up(2 * (size_t)n);
-    L.chg = L.lat + up(4 * (size_t)n);
+    L.ldir = L.lat + up(4 * (size_t)n);
+    L.chg = L.ldir + up(8 * (size_t)n);
     L.dl = L.chg + up(4 * 2 * (((size_t)n + 31) / 32));
     L.lin_start = L.dl + up(2 * 2 * (size_t)nmax);
     L.lin_src = L.lin_start + up(4 * ((size_t)nmax + 1));
@@ -988,6 +989,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     short4 *wedge = (short4 *)(sm_raw + L.wedge);
     short *par = (short *)(sm_raw + L.par);
     short2 *lat = (short2 *)(sm_raw + L.lat);
+    short4 *ldir = (short4 *)(sm_raw + L.ldir);                // lattice position, arrival direction from the parent
     unsigned *chg = (unsigned *)(sm_raw + L.chg);              // changed generators, round parity p at p * cw
     unsigned short *dl = (unsigned short *)(sm_raw + L.dl);    // round parity p at p * nmax
     int *lin_start = (int *)(sm_raw + L.lin_start);
@@ -1019,7 +1021,15 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
         sh.src_seg[g] = k == kSegI ? ds.seg_lat[ds.gen_aux[g]] : make_int4(0, 0, 0, 0);
     }
     if (tid < 3) sh.cnt[tid] = 0;
-    __syncthreads();  // lin_start
+    __syncthreads();  // lin_start, lat, par, the sources' segments
+    // each generator's arrival direction from its parent ((0, 0) while it
+    // has none: no shadow cone then holds it)
+    for (int g = tid; g < n; g += kClThreads) {
+        const int p = par[g];
+        int dx = 0, dy = 0;
+        if (p >= 0) arrival_from(ds, sh.src_kind, sh.src_seg, lat, p, lat[g], dx, dy);
+        ldir[g] = make_short4(lat[g].x, lat[g].y, (short)dx, (short)dy);
+    }
     for (int k = warp; k < n_own; k += nwarps) {  // this CTA's in-lists, a warp per vertex
         const int vv = rank + C * k, e0 = ds.in_start[vv], m = ds.in_start[vv + 1] - e0, b = lin_start[k];
         for (int j = lane; j < m; j += 32) {
@@ -1063,6 +1073,9 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
                 if (rank == 0 && tid == 0) atomicOr(ds.status, kStNotConverged);
                 break;
             }
+#ifdef SPM_COUNT
+            const long long t_r0 = clock64();
+#endif
             for (int k0 = warp * kGpw; k0 < n_own; k0 += ngroups) {  // warp-uniform trip count
                 const int k = k0 + grp;
                 bool hit = false;
@@ -1076,10 +1089,17 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
                     dl[cur * nmax + atomicAdd(&sh.cnt[cur], 1)] = (unsigned short)k;
             }
             __syncthreads();
+#ifdef SPM_COUNT
+            if (rank == 0 && tid == 0) SPM_CNT(20, clock64() - t_r0);  // finding the dirty vertices
+#endif
             // read: free again (this round's changes go to the other parity)
             for (int w = tid; w < cw; w += kClThreads) chc[w] = 0u;
         }
         const int nd = sh.cnt[cur];
+#ifdef SPM_COUNT
+        const long long t_p0 = clock64();
+        if (rank == 0 && tid == 0) SPM_CNT(22, nd);
+#endif
         for (int i0 = warp * kGpw; i0 < nd; i0 += ngroups) {  // warp-uniform trip count
             const int i = i0 + grp;
             const bool act = i < nd;
@@ -1097,25 +1117,10 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
                 const double len = with_len ? lin_len[e] : __ldg(ds.in_len + eg + e);
                 const int u = lin_src[e];
                 const double cu = cost[u];
-                const int pu = par[u];
-                const short2 ul = lat[u];
+                const short4 q = ldir[u];  // u's position and arrival direction
                 const short4 w = wedge[u];
-                // u's arrival direction: from its parent, or perpendicular to a
-                // segment source whose interior is the parent
-                const int pc = pu < 0 ? 0 : pu, ps = pc < kSoloSrc ? pc : 0;
-                const short2 pl = lat[pc];
-                const int4 Ls = sh.src_seg[ps];
-                int dx = ul.x - pl.x, dy = ul.y - pl.y;
-                if (pu < ns && pu >= kSoloSrc) {
-                    arrival_from(ds, sh.src_kind, sh.src_seg, lat, pu, ul, dx, dy);
-                } else if (pu >= 0 && pu < ns && sh.src_kind[ps] == kSegI) {
-                    const int sx = Ls.z - Ls.x, sy = Ls.w - Ls.y;
-                    const int side = cross32(sx, sy, ul.x - Ls.x, ul.y - Ls.y);
-                    dx = side > 0 ? -sy : sy;
-                    dy = side > 0 ? sx : -sx;
-                }
                 const bool valid = (__double_as_longlong(cu) < 0x7ff0000000000000ll) &
-                                   ((u < ns) | ((pu >= 0) & in_shadow_cone(dx, dy, w, vl.x - ul.x, vl.y - ul.y)));
+                                   ((u < ns) | in_shadow_cone(q.z, q.w, w, vl.x - q.x, vl.y - q.y));
                 const long long cand = __double_as_longlong(__dadd_rn(cu, len));
                 const bool better = valid & (cand < best);
                 best = better ? cand : best;
@@ -1132,13 +1137,24 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
             }
             const bool changed = act && (best != cv || bpar != pv);
             if (changed && gl < C) {  // lane gl writes CTA gl's copy and its changed bit
+                int dx = 0, dy = 0;
+                if (bpar >= 0) arrival_from(ds, sh.src_kind, sh.src_seg, lat, bpar, vl, dx, dy);
                 cluster.map_shared_rank(cost, gl)[v] = __longlong_as_double(best);
                 cluster.map_shared_rank(par, gl)[v] = (short)bpar;
+                cluster.map_shared_rank(ldir, gl)[v] = make_short4(vl.x, vl.y, (short)dx, (short)dy);
                 atomicOr(cluster.map_shared_rank(chg, gl) + nxt * cw + (v >> 5), 1u << (v & 31));
             }
         }
         if (tid == 0) sh.cnt[nxt] = 0;  // the next round's list (last read two rounds ago)
+#ifdef SPM_COUNT
+        __syncthreads();
+        const long long t_p1 = clock64();
+        if (rank == 0 && tid == 0) SPM_CNT(21, t_p1 - t_p0);  // the pulls
+#endif
         cluster.sync();
+#ifdef SPM_COUNT
+        if (rank == 0 && tid == 0) SPM_CNT(23, clock64() - t_p1);  // the cluster barrier
+#endif
     }
 #ifdef SPM_COUNT
     if (rank == 0 && tid == 0) {
