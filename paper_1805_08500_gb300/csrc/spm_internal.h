@@ -273,11 +273,13 @@ bool flood_sources_direct(const DevScene &ds);
 int sssp_grid_blocks();  // co-resident CTAs for the cooperative fixpoint kernel
 int solo_smem_bytes();   // shared memory granted to the single-CTA fixpoint kernel (0 if refused)
 bool cluster_smem_ok();  // the cluster fixpoint can run (its shared memory was granted)
+int cluster_ctas();      // CTAs of a single scene's cluster fixpoint (16, or 8 where 16 do not fit; 0: unavailable)
 // fixpoint kernels of a scene's computes: the single-CTA one, the cluster
 // one, and whether one of them surely takes every compute's graph (then the
 // many-CTA kernel is not launched)
 constexpr int kFixSolo = 1, kFixCluster = 2, kFixSoloSure = 4, kFixClusterSure = 8;
 constexpr int kFixClusterFits = 16;  // the cluster kernel takes every compute's graph (batched form)
+constexpr int kFixClusterWide = 32;  // the cluster kernel runs on 16 CTAs (else 8)
 // from the static in-degrees (scene creation)
 int fixpoint_launches(const DevScene &ds, const std::vector<int32_t> &deg);
 // FP64 lengths of the static in-lists (ds.st_start / st_src set), into len

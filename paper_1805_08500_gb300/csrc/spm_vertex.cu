@@ -883,21 +883,25 @@ __global__ void __launch_bounds__(kSoloThreads) k_sssp_solo(const __grid_constan
     if (tid == 0) ds.stats[0] = round;
 }
 
-// The fixpoint of graphs too dense for one CTA: one cluster of kClCtas CTAs,
-// one per SM, with the generators' state (cost, parent, lattice position,
-// wedge) replicated in every CTA's shared memory and the obstacle vertices
-// dealt round-robin to the CTAs, each holding the in-lists of its own. A
-// round works as in the single-CTA kernel (a dirty vertex pulls the current
-// state of its in-neighbours, writes a changed value into every CTA's copy
-// and marks its out-neighbours in their owners' next dirty bitmap and list,
-// through distributed shared memory), with one cluster barrier per round in
-// place of the grid barriers of the many-CTA kernel. The argument of the
-// single-CTA kernel carries over: a pull may read a neighbour mid-update,
-// whose change marks the puller again, so the loop stops at the fixpoint of
-// the vertex equations, which is unique.
-constexpr int kClCtas = 8;          // CTAs of the cluster (the portable size)
+// The fixpoint of graphs too dense for one CTA: one cluster of C CTAs (16
+// where the GPU holds such a cluster, else 8; the batched form's are 8), one
+// per SM, with the generators' state (cost, parent, lattice position, wedge,
+// arrival direction) replicated in every CTA's shared memory and the
+// obstacle vertices dealt round-robin to the CTAs, each holding the in-lists
+// of its own. A round works as in the single-CTA kernel (a dirty vertex pulls
+// the current state of its in-neighbours), but a changed vertex writes its
+// value into every CTA's copy and sets its bit in every CTA's bitmap of
+// changed generators, through distributed shared memory; after the round's
+// cluster barrier each CTA finds its own dirty vertices by scanning their
+// in-lists against that bitmap. One cluster barrier per round replaces the
+// grid barriers of the many-CTA kernel. The argument of the single-CTA
+// kernel carries over: a pull may read a neighbour mid-update, whose change
+// marks the puller again, so the loop stops at the fixpoint of the vertex
+// equations, which is unique.
+constexpr int kClCtas = 8;          // CTAs of the batched form's clusters (the portable size)
+constexpr int kClCtasWide = 16;     // CTAs of a single scene's cluster where the GPU holds one (non-portable)
 constexpr int kClThreads = 1024;
-constexpr int kClGrp = 16;          // lanes per dirty vertex (dense in-lists); at least kClCtas
+constexpr int kClGrp = 16;          // lanes per dirty vertex (dense in-lists); at least the cluster's CTAs
 constexpr int kClSmem = 200 * 1024; // dynamic shared memory per CTA
 
 // The cluster fixpoint's layout: the replicated state and the dirty lists at
@@ -906,9 +910,9 @@ constexpr int kClSmem = 200 * 1024; // dynamic shared memory per CTA
 struct ClLayout {
     size_t cost, wedge, par, lat, ldir, chg, dl, lin_start, lin_src, lin_len, end;
 };
-__host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own, bool with_len) {
+__host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own, bool with_len, int C) {
     auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    const int nmax = (nv + kClCtas - 1) / kClCtas;
+    const int nmax = (nv + C - 1) / C;
     ClLayout L;
     L.cost = 0;
     L.wedge = L.cost + up(8 * (size_t)n);
@@ -935,9 +939,10 @@ struct ClShared {
     int4 src_seg[kSoloSrc];
 };
 
-// One scene's fixpoint on the calling cluster (every thread of it calls).
-// Returns false, having written nothing, when the graph cannot be taken
-// (16-bit ids, edge capacity, shared memory); every CTA returns the same.
+// One scene's fixpoint on the calling cluster of C CTAs (every thread of it
+// calls). Returns false, having written nothing, when the graph cannot be
+// taken (16-bit ids, edge capacity, shared memory); every CTA returns the same.
+template <int C>
 __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &cluster, ClShared &sh,
                          unsigned char *sm_raw) {
     const int rank = (int)cluster.block_rank();
@@ -961,7 +966,8 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     }
     const long long E = ds.in_start[nv];
     if (n >= 32768 || E > ds.edge_cap) return false;
-    const int C = kClCtas, nmax = (nv + C - 1) / C;
+    static_assert(C <= kClGrp, "a changed vertex's group writes every CTA's copy");
+    const int nmax = (nv + C - 1) / C;
     const int n_own = rank < nv ? (nv - rank + C - 1) / C : 0;  // vertices vv = rank + C * k
     // this CTA's in-list offsets: a scan over its vertices, in chunks
     const int per = (n_own + kClThreads - 1) / kClThreads, lo = min(n_own, tid * per), hi = min(n_own, lo + per);
@@ -976,15 +982,15 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     if (tid == 0) {
         long long mx = 0;
         for (int r = 0; r < C; ++r) mx = max(mx, *cluster.map_shared_rank(&sh.e_own, r));
-        sh.total = cl_layout(n, nv, mx, true).end <= (size_t)kClSmem    ? 2
-                   : cl_layout(n, nv, mx, false).end <= (size_t)kClSmem ? 1
+        sh.total = cl_layout(n, nv, mx, true, C).end <= (size_t)kClSmem    ? 2
+                   : cl_layout(n, nv, mx, false, C).end <= (size_t)kClSmem ? 1
                                                                          : 0;
     }
     cluster.sync();  // the remote reads are done before any CTA moves on
     const int fit = sh.total;
     if (!fit) return false;
     const bool with_len = fit == 2;
-    const ClLayout L = cl_layout(n, nv, sh.e_own, with_len);
+    const ClLayout L = cl_layout(n, nv, sh.e_own, with_len, C);
     double *cost = (double *)(sm_raw + L.cost);
     short4 *wedge = (short4 *)(sm_raw + L.wedge);
     short *par = (short *)(sm_raw + L.par);
@@ -1190,7 +1196,8 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     return true;
 }
 
-__global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
+template <int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClThreads)
     k_sssp_cluster(const __grid_constant__ DevScene ds, int max_rounds) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     chain_start();
@@ -1198,7 +1205,7 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
     cg::cluster_group cluster = cg::this_cluster();
     bool solo_len;
     if (solo_bytes(ds, solo_len) > 0) return;  // the single-CTA kernel handles this graph (every CTA agrees)
-    const bool done = cl_solve(ds, max_rounds, cluster, sh, sm_raw);
+    const bool done = cl_solve<C>(ds, max_rounds, cluster, sh, sm_raw);
     if (cluster.block_rank() == 0 && threadIdx.x == 0) ds.counters[4] = done ? 1 : 0;  // else the many-CTA kernel
 }
 
@@ -1218,7 +1225,7 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(kClThreads)
         cluster.sync();  // every CTA has read it before the next is taken
         if (k >= b.n) break;
         const int sc = b.cl_order[k];
-        const bool done = cl_solve(b.scenes[sc], b.max_rounds, cluster, sh, sm_raw);
+        const bool done = cl_solve<kClCtas>(b.scenes[sc], b.max_rounds, cluster, sh, sm_raw);
         if (lead) b.cl_done[sc] = done ? 1 : 0;
     }
 }
@@ -1541,22 +1548,36 @@ int fixpoint_launches(const DevScene &ds, const std::vector<int32_t> &deg) {
     int f = (ds.solo_smem > 0 ? kFixSolo : 0) | (cluster_smem_ok() ? kFixCluster : 0);
     const int nv = ds.n_vert;
     if ((int)deg.size() < nv) return f;  // unknown: the kernels decide on the device
-    long long lo = 0, own_max = 0;
-    for (int r = 0; r < kClCtas; ++r) {
-        long long own = 0;
-        for (int vv = r; vv < nv; vv += kClCtas) own += deg[vv] + ds.n_src;
-        own_max = std::max(own_max, own);
-    }
+    // the most in-edges one CTA of a C-CTA cluster holds (vertices dealt round-robin)
+    auto own_max = [&](int C) {
+        long long m = 0;
+        for (int r = 0; r < C; ++r) {
+            long long own = 0;
+            for (int vv = r; vv < nv; vv += C) own += deg[vv] + ds.n_src;
+            m = std::max(m, own);
+        }
+        return m;
+    };
+    long long lo = 0;
     for (int vv = 0; vv < nv; ++vv) lo += deg[vv];
     const long long hi = lo + (long long)ds.n_src * nv;
     // the single-CTA kernel's test only gets stricter as the edges grow
     bool wl;
     const bool solo_never = solo_bytes_for(ds.n_gen, nv, lo, ds.edge_cap, ds.solo_smem, wl) == 0;
     const bool solo_sure = solo_bytes_for(ds.n_gen, nv, hi, ds.edge_cap, ds.solo_smem, wl) > 0;
-    const bool cluster_sure = (f & kFixCluster) && ds.n_gen < 32768 && hi <= ds.edge_cap &&
-                              cl_layout(ds.n_gen, nv, own_max, false).end <= (size_t)kClSmem;
-    if (cluster_sure) f |= kFixClusterFits;
     if (solo_never) f &= ~kFixSolo;
+    // Beside a single-CTA launch the cluster kernel only stands by (it
+    // returns when the single-CTA kernel took the graph). As that kernel's
+    // dependent launch it is resident while the other runs and holds its
+    // SMs, which the sources' culling on the side stream would use: it takes
+    // the portable size there.
+    const int C = (f & kFixSolo) && !solo_sure ? kClCtas : cluster_ctas();
+    const bool cluster_ok = (f & kFixCluster) && ds.n_gen < 32768 && hi <= ds.edge_cap;
+    const bool cluster_sure = cluster_ok && cl_layout(ds.n_gen, nv, own_max(C), false, C).end <= (size_t)kClSmem;
+    if (C == kClCtasWide) f |= kFixClusterWide;
+    // the batched form's clusters are of the portable size
+    if (cluster_ok && cl_layout(ds.n_gen, nv, own_max(kClCtas), false, kClCtas).end <= (size_t)kClSmem)
+        f |= kFixClusterFits;
     if (solo_sure) f = (f & ~kFixCluster) | kFixSoloSure;
     if (cluster_sure && !solo_sure) f |= kFixClusterSure;
     return f;
@@ -1566,27 +1587,44 @@ void launch_static_lengths(const DevScene &ds, double *len, cudaStream_t st) {
     if (ds.n_vert > 0) k_static_lengths<<<std::min((ds.n_vert + 7) / 8, 152 * 8), 256, 0, st>>>(ds, len);
 }
 
-// the cluster fixpoint's shared memory, granted once per process
-bool cluster_smem_ok() {
-    static const bool ok = [] {
-        if (cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) != cudaSuccess ||
-            cudaFuncSetAttribute(k_sssp_cluster_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(kClCtas);
-        cfg.blockDim = dim3(kClThreads);
-        cfg.dynamicSmemBytes = kClSmem;
-        int clusters = 0;  // the GPU can hold one such cluster at all
-        if (cudaOccupancyMaxActiveClusters(&clusters, k_sssp_cluster, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        return clusters > 0;
-    }();
-    return ok;
+// The GPU can hold at least one cluster of C CTAs of the kernel.
+static bool cluster_holds(const void *kern, int C) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = kClSmem;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters > 0;
 }
+
+// The single-scene cluster fixpoint's CTAs: 16 (a non-portable cluster
+// size, twice the SMs a round) where the GPU holds such a cluster, else the
+// portable 8, 0 when neither can run. Shared memory is granted once per
+// process, to the batched kernel too.
+int cluster_ctas() {
+    static const int ctas = [] {
+        const void *k16 = (const void *)k_sssp_cluster<kClCtasWide>, *k8 = (const void *)k_sssp_cluster<kClCtas>;
+        if (cudaFuncSetAttribute(k8, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) != cudaSuccess ||
+            cudaFuncSetAttribute((const void *)k_sssp_cluster_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        if (cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, kClSmem) == cudaSuccess &&
+            cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cluster_holds(k16, kClCtasWide))
+            return kClCtasWide;
+        cudaGetLastError();
+        return cluster_holds(k8, kClCtas) ? kClCtas : 0;
+    }();
+    return ctas;
+}
+
+bool cluster_smem_ok() { return cluster_ctas() > 0; }
 
 // ---------------------------------------------------------------------------
 // Warm start of the fixpoint. Obstacles never move, so the geodesic
@@ -2041,7 +2079,13 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
         launch_chained(k_warm_verify, dim3(gb), dim3(256), 0, st, arg);
     }
     if (f & kFixSolo) launch_chained(k_sssp_solo, dim3(1), dim3(kSoloThreads), (size_t)ds.solo_smem, st, arg, max_rounds);
-    if (f & kFixCluster) launch_chained(k_sssp_cluster, dim3(kClCtas), dim3(kClThreads), (size_t)kClSmem, st, arg, max_rounds);
+    if (f & kFixCluster) {
+        if (f & kFixClusterWide)
+            launch_chained(k_sssp_cluster<kClCtasWide>, dim3(kClCtasWide), dim3(kClThreads), (size_t)kClSmem, st, arg,
+                           max_rounds);
+        else
+            launch_chained(k_sssp_cluster<kClCtas>, dim3(kClCtas), dim3(kClThreads), (size_t)kClSmem, st, arg, max_rounds);
+    }
     if (!(f & (kFixSoloSure | kFixClusterSure))) {
         cudaLaunchCooperativeKernel((const void *)k_sssp, dim3(ds.sssp_blocks), dim3(kSsspThreads), args, 0, st);
         k_finalize<<<(ds.n_gen + 255) / 256, 256, 0, st>>>(ds);
