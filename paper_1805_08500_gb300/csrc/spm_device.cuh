@@ -236,9 +236,11 @@ __device__ __forceinline__ bool visible_points(const DevScene &ds, int px, int p
 }
 
 // Exact visibility between lattice point p and its perpendicular foot on
-// segment source s (0 < num < den), one thread.
+// segment source s (0 < num < den), one thread. The bins are walked from p,
+// or from the foot (from_foot); the result is the same (each bin's test is
+// the whole segment's, and the walks cover every bin the segment crosses).
 __device__ __forceinline__ bool visible_foot(const DevScene &ds, int s, int px, int py, long long num,
-                                             long long den) {
+                                             long long den, bool from_foot = false) {
     int4 L = ds.seg_lat[s];
     int ux = L.z - L.x, uy = L.w - L.y;
     int side = cross32(ux, uy, px - L.x, py - L.y);
@@ -248,7 +250,9 @@ __device__ __forceinline__ bool visible_foot(const DevScene &ds, int s, int px, 
     int4 sb = make_int4((int)floorf(fminf((float)px, fx)) - 1, (int)floorf(fminf((float)py, fy)) - 1,
                         (int)ceilf(fmaxf((float)px, fx)) + 1, (int)ceilf(fmaxf((float)py, fy)) + 1);
     const int nx = -uy, ny = ux;
-    bool blocked = walk_bins(ds, (float)px, (float)py, fx, fy, 0.f, [&](int bin) {
+    const float wx0 = from_foot ? fx : (float)px, wy0 = from_foot ? fy : (float)py;
+    const float wx1 = from_foot ? (float)px : fx, wy1 = from_foot ? (float)py : fy;
+    bool blocked = walk_bins(ds, wx0, wy0, wx1, wy1, 0.f, [&](int bin) {
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
             const BinRec rec = ds.bin_recs[it];
             const int4 bx = rec.box;

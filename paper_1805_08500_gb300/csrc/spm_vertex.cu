@@ -173,17 +173,20 @@ __device__ __forceinline__ bool loc_hidden(const DevScene &ds, int v, int2 vl, i
                                        __ldg(map + (b1 & (kLocBins - 1))));
 }
 
-// Exact visibility of a pair that passed the filter.
+// Exact visibility of a pair that passed the filter. The predicate is
+// symmetric in the two ends; a source's pairs are walked from the source,
+// since the vertex end already passed its local depth map (what blocks such
+// a pair lies farther from the vertex, often near the source).
 __device__ bool pair_visible(const DevScene &ds, int u, int v) {
     const int2 vl = ds.gen_lat[v];
     if (ds.gen_kind[u] == kSegI) {
         const int s = ds.gen_aux[u];
         const int4 L = ds.seg_lat[s];
         const long long ux = L.z - L.x, uy = L.w - L.y;
-        return visible_foot(ds, s, vl.x, vl.y, (vl.x - L.x) * ux + (vl.y - L.y) * uy, ux * ux + uy * uy);
+        return visible_foot(ds, s, vl.x, vl.y, (vl.x - L.x) * ux + (vl.y - L.y) * uy, ux * ux + uy * uy, true);
     }
     const int2 ul = ds.gen_lat[u];
-    return visible_points(ds, vl.x, vl.y, ul.x, ul.y);
+    return u < ds.n_src ? visible_points(ds, ul.x, ul.y, vl.x, vl.y) : visible_points(ds, vl.x, vl.y, ul.x, ul.y);
 }
 
 // Sets the bit of edge u -> v (row v) and, between two obstacle vertices,
