@@ -39,6 +39,7 @@ struct spm_scene {
     // side stream of the geometric flood (flood mode 3), with fork/join events
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    spm::VertexSide vside = {nullptr, nullptr, nullptr};  // the edge lists beside the warm start's kernels
     // host-buffer computes: copy stream, one event per pixel-pass slab, and
     // one for the end of the copies
     cudaStream_t copy = nullptr;
@@ -128,7 +129,7 @@ void free_all(spm_scene *s) {
             cudaEventDestroy(e);
             e = nullptr;
         }
-    for (cudaEvent_t *e : {&s->fork, &s->join, &s->copy_done})
+    for (cudaEvent_t *e : {&s->fork, &s->join, &s->copy_done, &s->vside.fork, &s->vside.join})
         if (*e) {
             cudaEventDestroy(*e);
             *e = nullptr;
@@ -155,6 +156,10 @@ void free_all(spm_scene *s) {
     if (s->side) {
         cudaStreamDestroy(s->side);
         s->side = nullptr;
+    }
+    if (s->vside.st) {
+        cudaStreamDestroy(s->vside.st);
+        s->vside.st = nullptr;
     }
 }
 
@@ -502,7 +507,10 @@ spm_status spm_scene_create(const spm_scene_desc *desc, spm_scene **out) {
         cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->vside.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->vside.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->vside.join, cudaEventDisableTiming) != cudaSuccess)
         ok = false;
     for (cudaEvent_t &e : s->slab_ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) ok = false;
@@ -578,7 +586,7 @@ static spm_status compute_impl(spm_scene *s, void *stream, float *dist, int32_t 
     if (side) cudaEventRecord(s->fork, cs);
     {
         NvtxRange r("spm vertex phase");
-        spm::launch_vertex_phase(s->ds, cs);
+        spm::launch_vertex_phase(s->ds, cs, &s->vside);
     }
     if (side) {
         NvtxRange r("spm flood (side stream)");

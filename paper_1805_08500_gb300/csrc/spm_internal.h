@@ -234,7 +234,13 @@ struct BatchDev {
 
 // Kernel launchers (spm_vertex.cu / spm_pixel.cu / spm_grad.cu).
 // vertex phase (visibility graph, fixpoint, finalised generator table)
-void launch_vertex_phase(const DevScene &ds, cudaStream_t st);
+// A second stream for work of the vertex phase that can run beside its
+// chain, with the events that fork it from and join it to the chain.
+struct VertexSide {
+    cudaStream_t st;
+    cudaEvent_t fork, join;
+};
+void launch_vertex_phase(const DevScene &ds, cudaStream_t st, const VertexSide *side = nullptr);
 // pixel kernel over the tiles of tile rows [tile_row0, tile_row1)
 void launch_pixel_phase(const DevScene &ds, cudaStream_t st, float *dist, int32_t *parent, int tile_row0,
                         int tile_row1);

@@ -1737,9 +1737,13 @@ __global__ void __launch_bounds__(256) k_warm_entry(const __grid_constant__ DevS
     if (tid < kEntryRows) {
         const int u = blockIdx.y * kEntryRows + tid;
         if (u < nv) {
+            // u's source links, from the source columns of its bit row (the
+            // edge lists need not be built yet)
             double m = inf;
-            const int e1 = ds.in_start[u + 1];
-            for (int e = ds.in_start[u]; e < e1 && ds.in_src[e] < ns; ++e) m = fmin(m, ds.in_len[e]);
+            const uint32_t *row = ds.vis_bits + (size_t)u * ds.vis_words;
+            for (int w = 0; w * 32 < ns; ++w)
+                for (uint32_t b = row[w] & src_word_mask(ds, w); b; b &= b - 1)
+                    m = fmin(m, edge_len(ds, w * 32 + __ffs(b) - 1, ns + u));
             if (m < inf) {
                 const int k = atomicAdd(&ne, 1);
                 eu[k] = u;
@@ -1757,10 +1761,12 @@ __global__ void __launch_bounds__(256) k_warm_entry(const __grid_constant__ DevS
 }
 
 // Each obstacle vertex's tree parent: the in-neighbour u with the least
-// estimate(u) + |u - v| (the first of equal values, i.e. the smaller id), and
-// that link's FP64 length as the fixpoint adds it. A group of kWarmGrp lanes
-// per vertex, each over every kWarmGrp-th in-edge, then the lexicographic
-// minimum across the group.
+// estimate(u) + |u - v| (of equal values the smaller id), and that link's
+// FP64 length as the fixpoint adds it. The in-edges are read where the edge
+// lists take them from (the source columns of the vertex's bit row, then its
+// kept obstacle-vertex list), so the lists can be built meanwhile. A group of
+// kWarmGrp lanes per vertex, each over every kWarmGrp-th source and kept
+// edge, then the lexicographic minimum across the group.
 constexpr int kWarmGrp = 8;
 __global__ void __launch_bounds__(256) k_warm_tree(const __grid_constant__ DevScene ds) {
     chain_start();
@@ -1769,17 +1775,20 @@ __global__ void __launch_bounds__(256) k_warm_tree(const __grid_constant__ DevSc
     const int ns = ds.n_src;
     double best = __longlong_as_double(0x7ff0000000000000ll), blen = 0.0;
     int bp = -1;
-    const int e0 = act ? ds.in_start[vv] : 0, e1 = act ? ds.in_start[vv + 1] : 0;
-    for (int e = e0 + gl; e < e1; e += kWarmGrp) {
-        const int u = ds.in_src[e];
-        const double len = ds.in_len[e];
+    auto take = [&](int u, double len) {
         const double est = u < ns ? 0.0 : ds.warm_est[u - ns];
         const double c = __dadd_rn(est, len);
-        if (est < kEstNone && c < best) {  // no estimate: u is not reached from a source
+        if (est < kEstNone && (c < best || (c == best && u < bp))) {  // no estimate: u is not reached
             best = c;
             bp = u;
             blen = len;
         }
+    };
+    if (act) {
+        const uint32_t *row = ds.vis_bits + (size_t)vv * ds.vis_words;
+        for (int u = gl; u < ns; u += kWarmGrp)
+            if ((row[u >> 5] >> (u & 31)) & 1u) take(u, edge_len(ds, u, ns + vv));
+        for (int j = ds.st_start[vv] + gl, j1 = ds.st_start[vv + 1]; j < j1; j += kWarmGrp) take(ds.st_src[j], ds.st_len[j]);
     }
 #pragma unroll
     for (int o = kWarmGrp / 2; o > 0; o >>= 1) {
@@ -2034,7 +2043,7 @@ cudaError_t launch_vtab_build(const DevScene &ds, double *tab, int32_t *counter,
     return cudaGetLastError();
 }
 
-void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
+void launch_vertex_phase(const DevScene &ds, cudaStream_t st, const VertexSide *side) {
     int f = ds.fix_launch;
     if (g_many_cta_override.load() && !(f & kFixSoloSure)) f &= ~(kFixCluster | kFixClusterSure);  // test hook
     // the warm start needs a fixpoint kernel that takes it (the many-CTA one
@@ -2060,9 +2069,21 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
         }
         launch_pairs(ds, st, false);
         const int eb = (ds.n_vert + 7) / 8;  // one warp per row
-        launch_chained(k_edges_count, dim3(eb), dim3(256), 0, st, ds);
-        launch_chained(k_edges_scan, dim3(1), dim3(1024), 0, st, ds);
-        launch_chained(k_edges_fill, dim3(eb), dim3(256), 0, st, ds);
+        if (warm && side) {
+            // the tree's estimates, parents and fold read the source columns
+            // and kept lists themselves: the edge lists, which only the
+            // verification and the fixpoint read, are built beside them
+            cudaEventRecord(side->fork, st);
+            cudaStreamWaitEvent(side->st, side->fork, 0);
+            k_edges_count<<<eb, 256, 0, side->st>>>(ds);
+            launch_chained(k_edges_scan, dim3(1), dim3(1024), 0, side->st, ds);
+            launch_chained(k_edges_fill, dim3(eb), dim3(256), 0, side->st, ds);
+            cudaEventRecord(side->join, side->st);
+        } else {
+            launch_chained(k_edges_count, dim3(eb), dim3(256), 0, st, ds);
+            launch_chained(k_edges_scan, dim3(1), dim3(1024), 0, st, ds);
+            launch_chained(k_edges_fill, dim3(eb), dim3(256), 0, st, ds);
+        }
     } else {
         cudaMemsetAsync(ds.in_start, 0, sizeof(int32_t) * (ds.n_vert + 1), st);
     }
@@ -2079,7 +2100,12 @@ void launch_vertex_phase(const DevScene &ds, cudaStream_t st) {
         const int gb = (ds.n_vert * kWarmGrp + 255) / 256;
         launch_chained(k_warm_tree, dim3(gb), dim3(256), 0, st, arg);
         launch_chained(k_warm_fold, dim3(1), dim3(kFoldThreads), fold_bytes(ds.n_gen), st, arg);
-        launch_chained(k_warm_verify, dim3(gb), dim3(256), 0, st, arg);
+        if (side && ds.n_vert > 0) {  // the edge lists are complete before the verification reads them
+            cudaStreamWaitEvent(st, side->join, 0);
+            k_warm_verify<<<gb, 256, 0, st>>>(arg);
+        } else {
+            launch_chained(k_warm_verify, dim3(gb), dim3(256), 0, st, arg);
+        }
     }
     if (f & kFixSolo) launch_chained(k_sssp_solo, dim3(1), dim3(kSoloThreads), (size_t)ds.solo_smem, st, arg, max_rounds);
     if (f & kFixCluster) {
