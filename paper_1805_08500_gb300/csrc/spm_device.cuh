@@ -221,12 +221,12 @@ __device__ __forceinline__ bool visible_points(const DevScene &ds, int px, int p
     if (px == qx && py == qy) return true;
     int4 sb = make_int4(min(px, qx), min(py, qy), max(px, qx), max(py, qy));
     bool blocked = walk_bins(ds, (float)px, (float)py, (float)qx, (float)qy, 0.f, [&](int bin) {
-        SPM_CNT(15, 1);
+        SPM_CNT(24, 1);  // a bin walked
         for (int it = ds.bin_start[bin]; it < ds.bin_start[bin + 1]; ++it) {
             const BinRec rec = ds.bin_recs[it];
             const int4 bx = rec.box;
             if (bx.z < sb.x || bx.x > sb.z || bx.w < sb.y || bx.y > sb.w) continue;
-            SPM_CNT(12, 1);
+            SPM_CNT(25, 1);  // a polygon tested
             const int2 *V = ds.poly_v + rec.voff;
             if (poly_blocks(V, rec.m, px, py, qx, qy, edge_mask(V, rec.m, qx, qy))) return true;
         }
