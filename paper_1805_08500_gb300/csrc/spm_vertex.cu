@@ -911,7 +911,7 @@ constexpr int kClSmem = 200 * 1024; // dynamic shared memory per CTA
 // offsets every CTA shares, then the CTA's own in-lists (with their FP64
 // lengths when they fit; else the lengths are read from global memory).
 struct ClLayout {
-    size_t cost, wedge, par, lat, ldir, chg, dl, lin_start, lin_src, lin_len, end;
+    size_t cost, wedge, par, lat, ldir, chg, dl, lin_start, gstart, lin_src, lin_len, end;
 };
 __host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long e_own, bool with_len, int C) {
     auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
@@ -925,7 +925,8 @@ __host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long 
     L.chg = L.ldir + up(8 * (size_t)n);
     L.dl = L.chg + up(4 * 2 * (((size_t)n + 31) / 32));
     L.lin_start = L.dl + up(2 * 2 * (size_t)nmax);
-    L.lin_src = L.lin_start + up(4 * ((size_t)nmax + 1));
+    L.gstart = L.lin_start + up(4 * ((size_t)nmax + 1));
+    L.lin_src = L.gstart + up(4 * (size_t)nmax);
     L.lin_len = L.lin_src + up(2 * (size_t)e_own);
     L.end = L.lin_len + (with_len ? up(8 * (size_t)e_own) : 0);
     return L;
@@ -934,8 +935,7 @@ __host__ __device__ __forceinline__ ClLayout cl_layout(int n, int nv, long long 
 // Per-CTA static shared state of the cluster fixpoint.
 struct ClShared {
     int cnt[3];                  // dirty-list counts, by round modulo 3
-    long long e_own;             // in-edges of this CTA's vertices
-    int total;                   // a value broadcast to the CTA
+    long long own_e[kClCtasWide]; // in-edges of each CTA's vertices
     int next;                    // the batched form's next scene (CTA 0)
     long long wsum[32];
     signed char src_kind[kSoloSrc];
@@ -972,28 +972,38 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     static_assert(C <= kClGrp, "a changed vertex's group writes every CTA's copy");
     const int nmax = (nv + C - 1) / C;
     const int n_own = rank < nv ? (nv - rank + C - 1) / C : 0;  // vertices vv = rank + C * k
-    // this CTA's in-list offsets: a scan over its vertices, in chunks
+    // the state and the offset arrays sit at offsets that do not depend on
+    // the in-list sizes; when even they do not fit, nothing does
+    const ClLayout L0 = cl_layout(n, nv, 0, false, C);
+    if (L0.lin_src > (size_t)kClSmem) return false;
+    // every CTA's in-edge count, in each CTA (warp r sums CTA r's vertices):
+    // the largest decides the layout, the same in all, with no exchange
+    if (warp < C) {
+        long long m = 0;
+        for (int vv = warp + C * lane; vv < nv; vv += 32 * C) m += ds.in_start[vv + 1] - ds.in_start[vv];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (lane == 0) sh.own_e[warp] = m;
+    }
+    // this CTA's in-list offsets: a scan over its vertices, in chunks, with
+    // their global starts kept
+    int *gstart = (int *)(sm_raw + L0.gstart);
     const int per = (n_own + kClThreads - 1) / kClThreads, lo = min(n_own, tid * per), hi = min(n_own, lo + per);
     long long mine = 0;
-    for (int k = lo; k < hi; ++k) mine += ds.in_start[rank + C * k + 1] - ds.in_start[rank + C * k];
-    const long long before = cta_exclusive_scan(mine, sh.wsum);
-    if (hi == n_own && lo < hi) sh.e_own = before + mine;
-    if (tid == 0 && n_own == 0) sh.e_own = 0;
-    __syncthreads();
-    // every CTA's lists must fit: the largest decides, the same in all
-    cluster.sync();
-    if (tid == 0) {
-        long long mx = 0;
-        for (int r = 0; r < C; ++r) mx = max(mx, *cluster.map_shared_rank(&sh.e_own, r));
-        sh.total = cl_layout(n, nv, mx, true, C).end <= (size_t)kClSmem    ? 2
-                   : cl_layout(n, nv, mx, false, C).end <= (size_t)kClSmem ? 1
-                                                                         : 0;
+    int *lin_start = (int *)(sm_raw + L0.lin_start);
+    for (int k = lo; k < hi; ++k) {
+        const int a = ds.in_start[rank + C * k], d = ds.in_start[rank + C * k + 1] - a;
+        gstart[k] = a;
+        lin_start[k] = d;  // the degree, until the offsets replace it
+        mine += d;
     }
-    cluster.sync();  // the remote reads are done before any CTA moves on
-    const int fit = sh.total;
+    const long long before = cta_exclusive_scan(mine, sh.wsum);  // its barriers publish own_e too
+    long long mx = 0;
+    for (int r = 0; r < C; ++r) mx = max(mx, sh.own_e[r]);
+    const int fit = cl_layout(n, nv, mx, true, C).end <= (size_t)kClSmem ? 2 : cl_layout(n, nv, mx, false, C).end <= (size_t)kClSmem ? 1 : 0;
     if (!fit) return false;
     const bool with_len = fit == 2;
-    const ClLayout L = cl_layout(n, nv, sh.e_own, with_len, C);
+    const ClLayout L = cl_layout(n, nv, sh.own_e[rank], with_len, C);
     double *cost = (double *)(sm_raw + L.cost);
     short4 *wedge = (short4 *)(sm_raw + L.wedge);
     short *par = (short *)(sm_raw + L.par);
@@ -1001,15 +1011,15 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
     short4 *ldir = (short4 *)(sm_raw + L.ldir);                // lattice position, arrival direction from the parent
     unsigned *chg = (unsigned *)(sm_raw + L.chg);              // changed generators, round parity p at p * cw
     unsigned short *dl = (unsigned short *)(sm_raw + L.dl);    // round parity p at p * nmax
-    int *lin_start = (int *)(sm_raw + L.lin_start);
     unsigned short *lin_src = (unsigned short *)(sm_raw + L.lin_src);
     double *lin_len = (double *)(sm_raw + L.lin_len);          // with_len only
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     {
         long long run = before;
         for (int k = lo; k < hi; ++k) {
+            const int d = lin_start[k];
             lin_start[k] = (int)run;
-            run += ds.in_start[rank + C * k + 1] - ds.in_start[rank + C * k];
+            run += d;
         }
         if (hi == n_own && lo < hi) lin_start[n_own] = (int)run;
         if (tid == 0 && n_own == 0) lin_start[0] = 0;
@@ -1040,7 +1050,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
         ldir[g] = make_short4(lat[g].x, lat[g].y, (short)dx, (short)dy);
     }
     for (int k = warp; k < n_own; k += nwarps) {  // this CTA's in-lists, a warp per vertex
-        const int vv = rank + C * k, e0 = ds.in_start[vv], m = ds.in_start[vv + 1] - e0, b = lin_start[k];
+        const int e0 = gstart[k], b = lin_start[k], m = lin_start[k + 1] - b;
         for (int j = lane; j < m; j += 32) {
             lin_src[b + j] = (unsigned short)ds.in_src[e0 + j];
             if (with_len) lin_len[b + j] = ds.in_len[e0 + j];
@@ -1116,7 +1126,7 @@ __device__ bool cl_solve(const DevScene &ds, int max_rounds, cg::cluster_group &
             const int lk = act ? lw : 0;
             const int vv = rank + C * lk, v = ns + vv;
             const int e0 = lin_start[lk] + gl, e1 = act ? lin_start[lk + 1] : 0;
-            const int eg = ds.in_start[vv] - lin_start[lk];  // local -> global edge index (lengths)
+            const int eg = gstart[lk] - lin_start[lk];  // local -> global edge index (lengths)
             const short2 vl = lat[v];
             const long long cv = __double_as_longlong(cost[v]);
             const int pv = par[v];
