@@ -844,13 +844,20 @@ def test_host_buffer_compute_matches_device_compute(spm, pinned):
         assert np.array_equal(gd.view(np.int32), d_ref.cpu().numpy().view(np.int32))
 
 
-def test_compute_captured_in_a_cuda_graph(spm, oracle_mod):
+@pytest.mark.parametrize("start", [1, 2])
+def test_compute_captured_in_a_cuda_graph(spm, oracle_mod, start):
     """spm_compute records into a user's CUDA graph -- including the
-    geometric flood on the scene's side stream and the depth maps -- and the
-    replay reproduces a direct compute bit for bit."""
+    geometric flood on the scene's side stream, the depth maps and, with the
+    fixpoint started from the geodesic table's tree, the edge lists built on
+    the vertex phase's second stream -- and the replay reproduces a direct
+    compute bit for bit."""
     scene = sg.maze(4, cells=12, N=768)
     s = spm.Scene(scene)
-    spm.spm_scene_set_tuning(s.handle, 3, 32, 32, 1)
+    spm.spm_scene_set_tuning(s.handle, 3, 32, 32, 1, fixpoint_start=1)
+    k_src = s.info()["kernels_per_compute"]
+    spm.spm_scene_set_tuning(s.handle, 3, 32, 32, 1, fixpoint_start=start)
+    if start == 2:  # the tree's four kernels run (and fork the edge lists)
+        assert s.info()["kernels_per_compute"] == k_src + 4
     d_ref, p_ref = s.compute()
     s.sync()
     d, p = s.empty_outputs()
