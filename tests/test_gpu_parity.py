@@ -851,7 +851,8 @@ def test_compute_captured_in_a_cuda_graph(spm, oracle_mod, start):
     fixpoint started from the geodesic table's tree, the edge lists built on
     the vertex phase's second stream -- and the replay reproduces a direct
     compute bit for bit."""
-    scene = sg.maze(4, cells=12, N=768)
+    # 24 x 24 cells: enough obstacle vertices (256 or more) for the table
+    scene = sg.maze(4, cells=12 if start == 1 else 24, N=768)
     s = spm.Scene(scene)
     spm.spm_scene_set_tuning(s.handle, 3, 32, 32, 1, fixpoint_start=1)
     k_src = s.info()["kernels_per_compute"]
