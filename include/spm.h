@@ -160,7 +160,12 @@ spm_status spm_compute_sequential(spm_scene *scene, void *stream, float *dist_de
  * buffers (cudaHostAlloc, torch pin_memory) receive the map directly from the
  * pixel pass. Pageable ones receive it through device staging planes,
  * allocated on the first call, in row slabs copied while the next slab
- * computes. */
+ * computes. The scene keeps no pointer to the host buffers: the caller may
+ * unpin or free them once the call returns. After a compute into page-locked
+ * buffers the field queries (spm_query_parent, spm_query_exact,
+ * spm_extract_path) have no field to read and return SPM_ERR_INVALID_ARG
+ * until the next device compute; after one into pageable buffers they read
+ * the staging planes. */
 spm_status spm_compute_host(spm_scene *scene, void *stream, float *dist_host,
                             int32_t *parent_host);
 
