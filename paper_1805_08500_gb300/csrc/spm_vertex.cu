@@ -19,9 +19,14 @@
 //      and out-lists (by u) for frontier marking.
 //   3. k_sssp_solo: for sparse graphs, one CTA with the graph in shared
 //      memory runs rounds over the vertices whose in-neighbours changed, each
-//      pulling its in-neighbours' current state; k_sssp: otherwise, the same
-//      rounds (synchronous) on every SM with a cooperative launch. Both stop
-//      at the fixpoint (bounded round count -> status bit).
+//      pulling its in-neighbours' current state; k_sssp_cluster: for denser
+//      ones, the same rounds on one thread-block cluster with the state
+//      replicated in every CTA; k_sssp: otherwise, the rounds (synchronous)
+//      on every SM with a cooperative launch. All stop at the fixpoint
+//      (bounded round count -> status bit).
+// On deep graphs the rounds start from a shortest-path tree of the obstacle
+// vertices' geodesic table (k_warm_*, below), whose first three kernels run
+// while the edge lists are built on a second stream.
 // Costs are FP64 with explicitly rounded operations, so they match a plain
 // FP64 Dijkstra over the same edges bit for bit.
 #include <cooperative_groups.h>
