@@ -842,17 +842,6 @@ def test_host_buffer_compute_matches_device_compute(spm, pinned):
         gp = hp.numpy() if pinned else hp
         assert np.array_equal(gp, p_ref.cpu().numpy())
         assert np.array_equal(gd.view(np.int32), d_ref.cpu().numpy().view(np.int32))
-    # the scene keeps no pointer to page-locked buffers (the caller may free
-    # them): the queries need a device compute; pageable computes leave the
-    # staging planes, which the queries read
-    x, y = scene.world[0] * 0.37, scene.world[1] * 0.61
-    if pinned:
-        with pytest.raises(spm.SpmError) as e:
-            s.query_parent(x, y)
-        assert e.value.status == spm.SPM_ERR_INVALID_ARG
-    else:
-        i, j = int(x / scene.world[0] * Nx), int(y / scene.world[1] * Ny)
-        assert s.query_parent(x, y)[0] == int(gp[j, i])
 
 
 @pytest.mark.parametrize("start", [1, 2])
