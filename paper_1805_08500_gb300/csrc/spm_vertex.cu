@@ -214,11 +214,12 @@ struct PairQ {
     int3 e[kVisThreads / 32][kPairQ];  // (scene, u, v)
 };
 
-// Warps take tasks `chunk` at a time from a work counter: the walks left
-// after the filters are few and uneven, and a fixed share per warp leaves
-// SMs idle behind a few long ones. A chunk is a run of consecutive words of
-// one row, so the row vertex's data and local map stay in L1; the host sizes
-// it so that every resident warp takes about two chunks.
+// Warps take tasks `chunk` at a time, the first by their index, the rest
+// from a work counter: the walks left after the filters are few and uneven,
+// and a fixed share per warp leaves SMs idle behind a few long ones. A chunk
+// is a run of consecutive words of one row, so the row vertex's data and
+// local map stay in L1; the host sizes it so that every resident warp takes
+// about two chunks.
 template <class Scene, class Task>
 __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, int chunk, unsigned long long *work,
                                               Scene scene_of_task, Task task_of) {
@@ -236,12 +237,24 @@ __device__ __forceinline__ void vis_pairs_run(PairQ &q, long long tasks, int chu
         qn -= n;
         __syncwarp();
     };
+    // Each warp's first chunk is its own by its index (thousands of warps
+    // starting on one counter would queue on its atomics); the rest come
+    // from the counter, after those.
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5), gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const long long handed = nw * chunk;
     long long t = 0, t_end = 0;
+    bool first = true;
     for (;;) {
         if (t == t_end) {
-            unsigned long long c = 0;
-            if (lane == 0) c = atomicAdd(work, (unsigned long long)chunk);
-            t = (long long)__shfl_sync(0xffffffffu, c, 0);
+            if (first) {
+                first = false;
+                t = gw * chunk;
+            } else {
+                if (handed >= tasks) break;  // every task was handed out by index
+                unsigned long long c = 0;
+                if (lane == 0) c = atomicAdd(work, (unsigned long long)chunk);
+                t = handed + (long long)__shfl_sync(0xffffffffu, c, 0);
+            }
             if (t >= tasks) break;
             t_end = min(t + chunk, tasks);
         }
