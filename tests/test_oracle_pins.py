@@ -586,6 +586,37 @@ def test_runner_up_matches_brute_force(oracle_mod, seed, n_segs, use_cone):
     assert n_seconds >= 300
 
 
+@pytest.mark.parametrize("seed,n_segs", [(1, 1), (4, 2)])
+def test_keys_match_brute_force_per_generator(oracle_mod, seed, n_segs):
+    """orc_keys, generator by generator (the keys the tie analysis compares):
+    at every pixel centre of tiny scenes, a generator has a finite key
+    exactly when the brute force finds it valid (reached, the pixel free and
+    seeing it, inside its shadow cone), and then the same key."""
+    s = sg.tiny(seed, W=32, N=32, n_polys=3, n_points=1 + (seed % 2), n_segs=n_segs)
+    o = oracle_mod.Oracle(s)
+    bf = _BruteField(s, o)
+    (Wx, Wy), (Nx, Ny) = s.world, s.grid
+    S = bf.q.S
+    ng = len(o.kind)
+    jj, ii = np.meshgrid(np.arange(Ny), np.arange(Nx), indexing="ij")
+    ij = np.repeat(np.stack([ii.reshape(-1), jj.reshape(-1)], 1), ng, axis=0)
+    k = o.keys(ij, np.tile(np.arange(ng), Nx * Ny)).reshape(Ny, Nx, ng)
+    n_valid = 0
+    for j in range(Ny):
+        for i in range(Nx):
+            q = ((2 * i + 1) * S * Wx // (2 * Nx), (2 * j + 1) * S * Wy // (2 * Ny))
+            qt = ((i + 0.5) * Wx / Nx, (j + 0.5) * Wy / Ny)
+            want = dict((g, key) for key, g in bf.keys(q, qt))
+            for g in range(ng):
+                got = k[j, i, g]
+                if g in want:
+                    n_valid += 1
+                    assert abs(got - want[g]) <= 1e-12 * max(want[g], 1.0), (i, j, g, got, want[g])
+                else:
+                    assert math.isinf(got), (i, j, g, got)
+    assert n_valid >= 2000
+
+
 @pytest.mark.parametrize("seed,n_segs", [(0, 0), (1, 1), (3, 2)])
 def test_point_queries_off_centre_match_brute_force(oracle_mod, seed, n_segs):
     """orc_points at lattice points that are not pixel centres (the exact
